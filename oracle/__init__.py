@@ -1,0 +1,221 @@
+"""FP64 CPU oracle for the ILE extrinsic-marginalisation hot path (arXiv:2210.07912).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+cpu_baseline / reference leg may import this package.  The CUDA library never loads it, and the
+two share no code: the oracle is the plain C file ``ile_oracle.c`` next to this module, compiled
+with gcc (``-O2 -ffp-contract=off -fopenmp``) and called through ctypes.
+
+Every function cites the passage of the paper it follows in ``ile_oracle.c``.  Pins that tie the
+oracle to something other than itself live in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ile_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libile_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NBINS = 100
+NDIM = 7
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/libile_oracle.so`` (gcc, FP64, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+               "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Point(ctypes.Structure):
+    _fields_ = [
+        ("n_det", ctypes.c_int), ("n_modes", ctypes.c_int),
+        ("lm", ctypes.c_void_p), ("det_tensor", ctypes.c_void_p), ("det_pos", ctypes.c_void_p),
+        ("Q", ctypes.c_void_p), ("T_ext", ctypes.c_int), ("t_start", ctypes.c_double),
+        ("fs", ctypes.c_double), ("U", ctypes.c_void_p), ("V", ctypes.c_void_p),
+        ("n_window", ctypes.c_int), ("gmst", ctypes.c_double), ("d_ref", ctypes.c_double),
+    ]
+
+
+class _Sampler(ctypes.Structure):
+    _fields_ = [
+        ("lo", ctypes.c_double * NDIM), ("hi", ctypes.c_double * NDIM),
+        ("adaptive", ctypes.c_int * NDIM), ("cdf", ctypes.c_void_p),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+            lib.orc_frame.argtypes = [d, d, d, d, vp, vp, vp]
+            lib.orc_antenna.argtypes = [vp, d, d, d, d, vp]
+            lib.orc_delay.argtypes = [vp, d, d, d]
+            lib.orc_delay.restype = d
+            lib.orc_wigner_d.argtypes = [i, i, i, d]
+            lib.orc_wigner_d.restype = d
+            lib.orc_sylm.argtypes = [i, i, d, d, vp]
+            lib.orc_lnL_grid.argtypes = [ctypes.POINTER(_Point), vp, vp, vp, vp]
+            lib.orc_lnL_t.argtypes = [ctypes.POINTER(_Point), vp, ctypes.c_long, vp, i]
+            lib.orc_mc_stats.argtypes = [vp, ctypes.c_long, vp]
+            lib.orc_philox4x32_10.argtypes = [vp, vp, vp]
+            lib.orc_sample.argtypes = [ctypes.POINTER(_Sampler), ctypes.c_uint64, ctypes.c_uint32,
+                                       ctypes.c_uint32, ctypes.c_long, ctypes.c_long, vp, vp, vp]
+            lib.orc_hist.argtypes = [vp, vp, ctypes.c_long, vp]
+            lib.orc_cdf_from_hist.argtypes = [vp, d, vp]
+            lib.orc_cdf_uniform.argtypes = [vp]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class _PointView:
+    """Keeps the contiguous FP64 copies of a point alive while C reads them."""
+
+    def __init__(self, p):
+        self.lm = np.ascontiguousarray(p.lm, dtype=np.int32)
+        self.det_tensor = np.ascontiguousarray(p.det_tensor, dtype=np.float64)
+        self.det_pos = np.ascontiguousarray(p.det_pos, dtype=np.float64)
+        self.Q = np.ascontiguousarray(np.stack([p.Q.real, p.Q.imag], axis=-1), dtype=np.float64)
+        self.U = np.ascontiguousarray(np.stack([p.U.real, p.U.imag], axis=-1), dtype=np.float64)
+        self.V = np.ascontiguousarray(np.stack([p.V.real, p.V.imag], axis=-1), dtype=np.float64)
+        K, M, T = p.Q.shape
+        self.s = _Point(K, M, _ptr(self.lm).value, _ptr(self.det_tensor).value, _ptr(self.det_pos).value,
+                        _ptr(self.Q).value, T, float(p.t_start), float(p.fs), _ptr(self.U).value,
+                        _ptr(self.V).value, int(p.n_window), float(p.gmst), float(p.d_ref))
+
+
+# ------------------------------------------------------------------------------------ S1 / S2
+def frame(ra, dec, psi, gmst=0.0):
+    X, Y, n = (np.zeros(3) for _ in range(3))
+    _load().orc_frame(ra, dec, psi, gmst, _ptr(X), _ptr(Y), _ptr(n))
+    return X, Y, n
+
+
+def antenna(D, ra, dec, psi, gmst=0.0) -> complex:
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    out = np.zeros(2)
+    _load().orc_antenna(_ptr(D), ra, dec, psi, gmst, _ptr(out))
+    return complex(out[0], out[1])
+
+
+def delay(r, ra, dec, gmst=0.0) -> float:
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    return _load().orc_delay(_ptr(r), ra, dec, gmst)
+
+
+def wigner_d(l, m1, m2, beta) -> float:
+    return _load().orc_wigner_d(l, m1, m2, beta)
+
+
+def sylm(l, m, iota, phi) -> complex:
+    out = np.zeros(2)
+    _load().orc_sylm(l, m, iota, phi, _ptr(out))
+    return complex(out[0], out[1])
+
+
+# ------------------------------------------------------------------------------------ S3-S5
+class RangeError(ValueError):
+    pass
+
+
+def lnL_grid(point, theta):
+    """lnL(j) for j < N_t of one sample theta (7,), plus the data term and A = <h|h>/2."""
+    pv = _PointView(point)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    lnL = np.zeros(point.n_window)
+    data = np.zeros(point.n_window)
+    A = np.zeros(1)
+    st = _load().orc_lnL_grid(ctypes.byref(pv.s), _ptr(th), _ptr(lnL), _ptr(data), _ptr(A))
+    if st == 3:
+        raise RangeError("interpolation index outside [0, T_ext-1]")
+    if st != 0:
+        raise ValueError(f"oracle status {st}")
+    return lnL, data, float(A[0])
+
+
+def lnL_t(point, samples, nthreads: int = 0):
+    """Time-marginalised lnL of every sample; samples is SoA (7, N)."""
+    pv = _PointView(point)
+    s = np.ascontiguousarray(samples, dtype=np.float64)
+    N = s.shape[1]
+    out = np.zeros(N)
+    st = _load().orc_lnL_t(ctypes.byref(pv.s), _ptr(s), N, _ptr(out), int(nthreads))
+    if st == 3:
+        raise RangeError("interpolation index outside [0, T_ext-1]")
+    if st != 0:
+        raise ValueError(f"oracle status {st}")
+    return out
+
+
+# ------------------------------------------------------------------------------------ S6
+def mc_stats(lnw):
+    """Eq. (eq:lnL:MonteCarlo) in log space: dict(ln_I, sigma_ln, n_eff, ess, m, s1, s2)."""
+    lnw = np.ascontiguousarray(lnw, dtype=np.float64)
+    out = np.zeros(7)
+    _load().orc_mc_stats(_ptr(lnw), lnw.size, _ptr(out))
+    return dict(ln_I=out[0], sigma_ln=out[1], n_eff=out[2], ess=out[3], m=out[4], s1=out[5], s2=out[6])
+
+
+def philox(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def make_sampler(lo, hi, adaptive, cdf):
+    cdf = np.ascontiguousarray(cdf, dtype=np.uint64).reshape(NDIM, NBINS + 1)
+    s = _Sampler((ctypes.c_double * NDIM)(*lo), (ctypes.c_double * NDIM)(*hi),
+                 (ctypes.c_int * NDIM)(*[int(a) for a in adaptive]), _ptr(cdf).value)
+    s._keep = cdf
+    return s
+
+
+def sample(sampler, seed: int, it: int, point: int, n0: int, N: int):
+    """Device-sampler definition: returns theta (7,N), ln p - ln p_s (N,), bins (7,N) uint8."""
+    theta = np.zeros((NDIM, N))
+    lw = np.zeros(N)
+    bins = np.zeros((NDIM, N), dtype=np.uint8)
+    _load().orc_sample(ctypes.byref(sampler), seed, it, point, n0, N, _ptr(theta), _ptr(lw), _ptr(bins))
+    return theta, lw, bins
+
+
+def hist(lnw, bins):
+    lnw = np.ascontiguousarray(lnw, dtype=np.float64)
+    b = np.ascontiguousarray(bins, dtype=np.uint8)
+    h = np.zeros(NBINS)
+    _load().orc_hist(_ptr(lnw), _ptr(b), lnw.size, _ptr(h))
+    return h
+
+
+def cdf_from_hist(h, eps: float = 0.1):
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    cdf = np.zeros(NBINS + 1, dtype=np.uint64)
+    _load().orc_cdf_from_hist(_ptr(h), eps, _ptr(cdf))
+    return cdf
+
+
+def cdf_uniform():
+    cdf = np.zeros(NBINS + 1, dtype=np.uint64)
+    _load().orc_cdf_uniform(_ptr(cdf))
+    return cdf

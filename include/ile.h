@@ -1,0 +1,151 @@
+/*
+ * ile.h -- C ABI of libile, the GB300 (sm_103a) implementation of the ILE extrinsic-marginalisation
+ * hot path of Wofford et al., "Expanding RIFT" (arXiv:2210.07912).
+ *
+ * For one intrinsic point (or a batch of points) and a set of Monte Carlo extrinsic samples
+ * theta = (ra, dec, psi, iota, phi, D, t_c) the library computes
+ *
+ *   lnL(theta, j) = sum_k Re sum_lm conj(c_klm) Q_klm(t_k(j))
+ *                   - 1/4 sum_k [ c_k^H U_k c_k + Re(c_k^T V_k c_k) ],     c_klm = (D_ref/D) F_k Y_lm
+ *   lnL_t(theta)  = LSE_j lnL(theta, j) - ln N_t
+ *   ln L_marg     = LSE_n [ lnL_t(theta_n) + ln p(theta_n) - ln p_s(theta_n) ] - ln N
+ *
+ * i.e. the likelihood decomposition of Eq. (eq:loglikelihood) with the inner products of
+ * Eq. (eq:QUV) (App. "Numerical and adaptation approaches needed for strong signals"), the Monte
+ * Carlo marginal likelihood of Eq. (eq:lnL:MonteCarlo) (Sec. "Evaluating the marginalized
+ * likelihood"), summed in log space as in the subsection "Choices for finite-precision floating
+ * point arithmetic and overflow", with the adaptive-Cartesian sampler of Sec. "GPU-accelerated
+ * Monte Carlo integration" (separable sampling prior, 100-bin histograms per adaptive dimension).
+ *
+ * Conventions fixed here (the paper leaves them open):
+ *   - F_k = F+ + i Fx from the detector response tensor D_k (3x3, Earth-fixed) in the textbook
+ *     wave frame with X x Y = -n; Greenwich hour angle = gmst - ra.
+ *   - Y_lm = _{-2}Y_lm(iota, phi) = sqrt((2l+1)/4pi) d^l_{m,2}(iota) e^{i m phi}.
+ *   - t_k(j) = t_c + (j - N_t/2)/f_s + dt_k,  dt_k = -(r_k . n)/c; Q is sampled at
+ *     t_start + i/f_s (i < T_ext) and linearly interpolated; every interpolation pair must lie
+ *     inside [0, T_ext-1], otherwise the call returns ILE_E_RANGE.
+ *   - The MC error is sigma_ln = sigma_I / I with the sample variance; n_eff = sum w / max w
+ *     (Eq. (eq:neff)); ess = (sum w)^2 / sum w^2 (Eq. (eq:neff_ESS)).
+ *
+ * Ownership: the caller owns every buffer it passes.  ile_set_data copies its inputs into
+ * context-owned device memory, so the caller may free them on return.  Outputs are written in
+ * full, or left untouched when the call fails before launching work.
+ *
+ * Pointers: without ILE_DEVICE_PTRS every array argument is a host pointer and the call is
+ * synchronous (it returns after the results are in host memory).  With ILE_DEVICE_PTRS they are
+ * device pointers on the context's device, the work is queued on the context's stream and the
+ * call returns at once; device-side errors (range, non-finite) are then reported by ile_sync().
+ *
+ * Errors: every call returns an ile_status and none aborts the process.  A CUDA error is mapped
+ * to ILE_E_CUDA; the context stays usable if the CUDA context is intact.
+ *
+ * Threading: a context may be used by one host thread at a time.
+ */
+#ifndef ILE_H
+#define ILE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ile_ctx ile_ctx; /* opaque; owns its device buffers */
+
+typedef enum {
+    ILE_OK = 0,
+    ILE_E_ARG = 1,       /* invalid argument (null pointer, size out of range, bad mode list) */
+    ILE_E_STATE = 2,     /* call out of order (e.g. ile_eval before ile_set_data) */
+    ILE_E_RANGE = 3,     /* a sample's interpolation index left [0, T_ext-1] */
+    ILE_E_NONFINITE = 4, /* a non-finite input sample or result */
+    ILE_E_CUDA = 5,      /* CUDA runtime or launch error */
+    ILE_E_NOMEM = 6,     /* device allocation failed */
+    ILE_E_TIMEOUT = 7    /* a bounded device-side wait gave up */
+} ile_status;
+
+/* Arithmetic of the shifted contraction (S3); every other stage is the same in all modes. */
+typedef enum {
+    ILE_PREC_FP32 = 0,   /* FP32 CUDA-core GEMM ("plain") */
+    ILE_PREC_TF32X3 = 1, /* tcgen05 kind::tf32, hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM */
+    ILE_PREC_BF16X3 = 2  /* tcgen05 kind::f16 (bf16 operands), same three-product split */
+} ile_prec;
+
+/* flags */
+#define ILE_DEVICE_PTRS 1u /* array arguments are device pointers; call is asynchronous */
+#define ILE_NO_TMARG 2u    /* ile_eval writes lnL(n, j) for every window bin: out is [N][N_t] */
+
+#define ILE_NBINS 100      /* histogram bins per adaptive dimension (Sec. GPU-accelerated MC) */
+#define ILE_NDIM 7         /* ra, dec, psi, iota, phi, D, t_c */
+#define ILE_MAX_DET 4
+#define ILE_MAX_MODES 21   /* all (l, m) with 2 <= l <= 4 */
+#define ILE_MAX_WINDOW 1024
+#define ILE_MAX_TEXT 4096
+
+/* Create a context on CUDA device `device`.  cuda_stream is a cudaStream_t (NULL = legacy
+ * default stream); the context never creates or destroys streams.  *out is NULL on failure. */
+ile_status ile_create(ile_ctx **out, int device, void *cuda_stream, ile_prec prec);
+
+/* Free every device buffer the context owns.  NULL is accepted. */
+ile_status ile_destroy(ile_ctx *ctx);
+
+/* Change the stream or the contraction arithmetic of an existing context. */
+ile_status ile_set_stream(ile_ctx *ctx, void *cuda_stream);
+ile_status ile_set_precision(ile_ctx *ctx, ile_prec prec);
+
+/*
+ * Load one intrinsic point (host pointers, copied).
+ *   n_det in [1, 4]; n_modes in [1, 21]; lm: [n_modes][2] distinct (l, m), 2 <= l <= 4, |m| <= l.
+ *   det_tensor: [n_det][3][3] response tensors; det_pos_m: [n_det][3] vertex positions (m).
+ *   Q: [n_det][n_modes][T_ext][2] (re, im) = <h_lm(t_i) | d>_k at t_i = t_start_s + i / fs_hz.
+ *   U, V: [n_det][n_modes][n_modes][2], U_k Hermitian, V_k symmetric (Eq. (eq:QUV)).
+ *   n_window = N_t in [1, 1024]; T_ext in [2, 4096]; fs_hz > 0; d_ref_mpc > 0.
+ * May be called again to replace the point.  Returns ILE_E_NONFINITE for a non-finite input.
+ */
+ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, const double *det_tensor,
+                        const double *det_pos_m, const double *Q, int T_ext, double t_start_s, double fs_hz,
+                        const double *U, const double *V, int n_window, double gmst_rad, double d_ref_mpc);
+
+/*
+ * Time-marginalised log-likelihood of N samples (S1-S5).
+ *   samples: SoA [7][N] (ra, dec, psi, iota, phi, D_Mpc, tc_s), FP64.
+ *   out: lnL_t [N] FP64, or with ILE_NO_TMARG lnL [N][N_t] FP64 (then N <= 65536).
+ * N = 0 is a valid no-op.
+ */
+ile_status ile_eval(ile_ctx *ctx, const double *samples, int64_t N, double *out, unsigned flags);
+
+/*
+ * Monte Carlo marginal likelihood of Eq. (eq:lnL:MonteCarlo) over N samples (S1-S6).
+ *   ln_prior, ln_ps: [N] log prior and log sampling densities of each sample (same coordinates).
+ *   result (7 doubles): {ln L_marg, sigma_ln, n_eff, ess, max ln w, S1, S2} with
+ *   S1 = sum exp(ln w - max), S2 = sum exp(2 (ln w - max)) (the mergeable partial sums).
+ *   lnL_t_out (optional, may be NULL): the per-sample lnL_t [N].
+ * Requires N >= 1.
+ */
+ile_status ile_integrate(ile_ctx *ctx, const double *samples, const double *ln_prior, const double *ln_ps,
+                         int64_t N, double *result, double *lnL_t_out, unsigned flags);
+
+/*
+ * Stage timing (tracing aid): when enabled, every kernel launch of the context is bracketed by
+ * CUDA events recorded on the context's stream.  ile_profile_read waits for the stream and
+ * writes, for each stage s < n_stages, the summed device time in ms (out_ms[s]) and the number
+ * of kernel launches (out_count[s], may be NULL) since the previous read, then resets them.
+ * Stages: 0 sampler (S0), 1 geometry/coefficients/quadratic (S1, S2, S4), 2 shifted contraction
+ * and time log-sum-exp (S3, S5), 3 Monte Carlo reduction (S6), 4 histogram adaptation (S6).
+ */
+#define ILE_NSTAGE 5
+ile_status ile_profile(ile_ctx *ctx, int enable);
+ile_status ile_profile_read(ile_ctx *ctx, double *out_ms, int64_t *out_count, int n_stages);
+
+/* Wait for the context's stream and return the first device-side error seen since the last call. */
+ile_status ile_sync(ile_ctx *ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char *ile_status_string(ile_status st);
+
+/* Last CUDA error message recorded by the context (static storage of the context). */
+const char *ile_last_error(const ile_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ILE_H */

@@ -1,0 +1,416 @@
+// ile_api.cu -- host side of the libile C ABI (include/ile.h): context, argument checks, data
+// upload and the launch sequence of each entry point.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "ile_internal.cuh"
+
+struct ile_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    ile_prec prec = ILE_PREC_FP32;
+    bool has_data = false;
+    PointParams pp{};
+    // point data
+    float *Qp = nullptr;   // [K][2M][T_ext]
+    float *UV = nullptr;   // [K][P][4]
+    void *Qtc = nullptr;   // tensor-core operand layout (ile_tc.cu)
+    size_t Qtc_bytes = 0;
+    // per-sample scratch
+    int64_t cap = 0;
+    IleScratch s{};
+    double *theta = nullptr;  // staged host samples [7][cap]
+    double *out = nullptr;    // [cap] (or grid)
+    size_t out_bytes = 0;
+    double *lnp = nullptr, *lnps = nullptr;
+    double *part = nullptr;
+    int part_cap = 0;
+    double *result = nullptr;  // [8]
+    unsigned *flags = nullptr;
+    char err[256] = {0};
+    // stage timing
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev[ILE_NSTAGE];
+    size_t ev_used[ILE_NSTAGE] = {0};
+    int64_t kernels[ILE_NSTAGE] = {0};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+ile_status cuda_fail(ile_ctx *c, cudaError_t e, const char *where) {
+    if (c) snprintf(c->err, sizeof c->err, "%s: %s", where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? ILE_E_NOMEM : ILE_E_CUDA;
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+template <typename T>
+cudaError_t grow(T **p, size_t bytes) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    return cudaMalloc((void **)p, bytes);
+}
+
+// Bracket one launch of stage `stage` with events on the context stream (when profiling).
+struct StageScope {
+    ile_ctx *c;
+    int stage;
+    StageScope(ile_ctx *ctx, int s, int n_kernels = 1) : c(ctx), stage(s) {
+        if (c->profiling) c->kernels[s] += n_kernels;
+        mark();
+    }
+    ~StageScope() { mark(); }
+    void mark() {
+        if (!c->profiling) return;
+        auto &v = c->ev[stage];
+        if (c->ev_used[stage] == v.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            v.push_back(e);
+        }
+        cudaEventRecord(v[c->ev_used[stage]++], c->stream);
+    }
+};
+
+ile_status ensure_samples(ile_ctx *ctx, int64_t N) {
+    if (N <= ctx->cap) return ILE_OK;
+    const int K = ctx->pp.K, R = 2 * ctx->pp.M;
+    int64_t cap = N;
+    CK(grow(&ctx->s.C, sizeof(float) * (size_t)ILE_MAX_DET * 2 * ILE_MAX_MODES * cap));
+    CK(grow(&ctx->s.I0, sizeof(int) * (size_t)ILE_MAX_DET * cap));
+    CK(grow(&ctx->s.W, sizeof(float) * (size_t)ILE_MAX_DET * cap));
+    CK(grow(&ctx->s.A, sizeof(float) * (size_t)cap));
+    CK(grow(&ctx->theta, sizeof(double) * ILE_NDIM * (size_t)cap));
+    CK(grow(&ctx->lnp, sizeof(double) * (size_t)cap));
+    CK(grow(&ctx->lnps, sizeof(double) * (size_t)cap));
+    int np = ile_mc_partial_count(cap);
+    CK(grow(&ctx->part, sizeof(double) * 3 * (size_t)np));
+    ctx->part_cap = np;
+    (void)K;
+    (void)R;
+    ctx->cap = cap;
+    return ILE_OK;
+}
+
+ile_status ensure_out(ile_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->out_bytes) return ILE_OK;
+    CK(grow(&ctx->out, bytes));
+    ctx->out_bytes = bytes;
+    return ILE_OK;
+}
+
+double factorial(int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; i++) f *= i;
+    return f;
+}
+
+// Polynomial form of d^l_{m,2}(iota) in c = cos(iota/2), s = sin(iota/2) (Wigner's formula).
+bool wigner_terms(int l, int m, ModeTab &md) {
+    md.l = l;
+    md.m = m;
+    md.norm = (float)sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
+    md.nterms = 0;
+    const double root = sqrt(factorial(l + m) * factorial(l - m) * factorial(l + 2) * factorial(l - 2));
+    for (int sp = 0; sp <= 2 * l; sp++) {  // sp = power of s = 2k - 2 + m
+        int twok = sp + 2 - m;
+        if (twok < 0 || (twok & 1)) continue;
+        int k = twok / 2;
+        int f1 = l + 2 - k, f2 = l - m - k, f3 = k + m - 2;
+        if (f1 < 0 || f2 < 0 || f3 < 0) continue;
+        if (md.nterms >= 4) return false;
+        double sign = (f3 % 2 == 0) ? 1.0 : -1.0;
+        WignerTerm &t = md.t[md.nterms++];
+        t.coef = (float)(sign * root / (factorial(f1) * factorial(k) * factorial(f2) * factorial(f3)));
+        t.p = 2 * l - sp;
+        t.q = sp;
+    }
+    return true;
+}
+
+bool finite_array(const double *p, size_t n) {
+    for (size_t i = 0; i < n; i++)
+        if (!isfinite(p[i])) return false;
+    return true;
+}
+
+ile_status read_flags(ile_ctx *ctx) {
+    unsigned f = 0;
+    CK(cudaMemcpyAsync(&f, ctx->flags, sizeof f, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (f) CK(cudaMemsetAsync(ctx->flags, 0, sizeof(unsigned), ctx->stream));
+    if (f & ILE_FLAG_TIMEOUT) return ILE_E_TIMEOUT;
+    if (f & ILE_FLAG_RANGE) return ILE_E_RANGE;
+    if (f & ILE_FLAG_NONFINITE) return ILE_E_NONFINITE;
+    return ILE_OK;
+}
+
+// S1-S5 on device-resident samples; writes lnL_t (or the grid) to dout.
+ile_status run_eval(ile_ctx *ctx, const double *dsamples, int64_t N, double *dout, int full_grid) {
+    ile_status st = ensure_samples(ctx, N);
+    if (st != ILE_OK) return st;
+    {
+        StageScope t(ctx, 1);
+        CK(ile_launch_prep(ctx->pp, ctx->UV, dsamples, N, ctx->s, ctx->flags, ctx->stream));
+    }
+    {
+        StageScope t(ctx, 2);
+        CK(ile_launch_plain(ctx->pp, ctx->Qp, ctx->s, N, dout, full_grid, ctx->flags, ctx->stream));
+    }
+    return ILE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ile_status_string(ile_status st) {
+    switch (st) {
+        case ILE_OK: return "ok";
+        case ILE_E_ARG: return "invalid argument";
+        case ILE_E_STATE: return "call out of order";
+        case ILE_E_RANGE: return "interpolation index outside the extended time range";
+        case ILE_E_NONFINITE: return "non-finite input or result";
+        case ILE_E_CUDA: return "CUDA error";
+        case ILE_E_NOMEM: return "device allocation failed";
+        case ILE_E_TIMEOUT: return "device-side wait timed out";
+    }
+    return "unknown status";
+}
+
+const char *ile_last_error(const ile_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+ile_status ile_create(ile_ctx **out, int device, void *cuda_stream, ile_prec prec) {
+    if (!out) return ILE_E_ARG;
+    *out = nullptr;
+    if (prec < ILE_PREC_FP32 || prec > ILE_PREC_BF16X3) return ILE_E_ARG;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return ILE_E_ARG;
+    ile_ctx *ctx = new ile_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->prec = prec;
+    DeviceGuard g(device);
+    cudaError_t e = cudaMalloc((void **)&ctx->flags, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(ctx->flags, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->result, 8 * sizeof(double));
+    if (e != cudaSuccess) {
+        ile_status st = cuda_fail(ctx, e, "ile_create");
+        ile_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return ILE_OK;
+}
+
+ile_status ile_destroy(ile_ctx *ctx) {
+    if (!ctx) return ILE_OK;
+    DeviceGuard g(ctx->device);
+    void *bufs[] = {ctx->Qp, ctx->UV, ctx->Qtc, ctx->s.C, ctx->s.I0, ctx->s.W, ctx->s.A, ctx->theta,
+                    ctx->out, ctx->lnp, ctx->lnps, ctx->part, ctx->result, ctx->flags};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    for (auto &v : ctx->ev)
+        for (cudaEvent_t e : v) cudaEventDestroy(e);
+    delete ctx;
+    return ILE_OK;
+}
+
+ile_status ile_set_stream(ile_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return ILE_E_ARG;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return ILE_OK;
+}
+
+ile_status ile_set_precision(ile_ctx *ctx, ile_prec prec) {
+    if (!ctx || prec < ILE_PREC_FP32 || prec > ILE_PREC_BF16X3) return ILE_E_ARG;
+    ctx->prec = prec;
+    return ILE_OK;
+}
+
+ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, const double *det_tensor,
+                        const double *det_pos_m, const double *Q, int T_ext, double t_start_s, double fs_hz,
+                        const double *U, const double *V, int n_window, double gmst_rad, double d_ref_mpc) {
+    if (!ctx || !lm || !det_tensor || !det_pos_m || !Q || !U || !V) return ILE_E_ARG;
+    if (n_det < 1 || n_det > ILE_MAX_DET || n_modes < 1 || n_modes > ILE_MAX_MODES) return ILE_E_ARG;
+    if (n_window < 1 || n_window > ILE_MAX_WINDOW || T_ext < 2 || T_ext > ILE_MAX_TEXT) return ILE_E_ARG;
+    if (!(fs_hz > 0) || !(d_ref_mpc > 0)) return ILE_E_ARG;
+    if (!isfinite(t_start_s) || !isfinite(fs_hz) || !isfinite(gmst_rad) || !isfinite(d_ref_mpc)) return ILE_E_NONFINITE;
+    const int K = n_det, M = n_modes, T = T_ext, R = 2 * M, P = M * (M + 1) / 2;
+    PointParams pp{};
+    pp.K = K;
+    pp.M = M;
+    pp.T_ext = T;
+    pp.Nt = n_window;
+    pp.x_offset = (float)(-t_start_s * fs_hz - 0.5 * n_window);
+    pp.fs = (float)fs_hz;
+    pp.gmst = (float)gmst_rad;
+    pp.d_ref = (float)d_ref_mpc;
+    pp.log_nt = (float)log((double)n_window);
+    for (int a = 0; a < M; a++) {
+        int l = lm[2 * a], m = lm[2 * a + 1];
+        if (l < 2 || l > 4 || m < -l || m > l) return ILE_E_ARG;
+        for (int b = 0; b < a; b++)
+            if (lm[2 * b] == l && lm[2 * b + 1] == m) return ILE_E_ARG;
+        if (!wigner_terms(l, m, pp.mode[a])) return ILE_E_ARG;
+    }
+    if (!finite_array(det_tensor, 9 * (size_t)K) || !finite_array(det_pos_m, 3 * (size_t)K) ||
+        !finite_array(Q, 2 * (size_t)K * M * T) || !finite_array(U, 2 * (size_t)K * M * M) ||
+        !finite_array(V, 2 * (size_t)K * M * M))
+        return ILE_E_NONFINITE;
+    for (int k = 0; k < K; k++) {
+        for (int i = 0; i < 9; i++) pp.det_tensor[k][i] = (float)det_tensor[9 * k + i];
+        for (int i = 0; i < 3; i++) pp.det_pos_c[k][i] = (float)(det_pos_m[3 * k + i] / ILE_C_SI);
+    }
+    std::vector<float> qp((size_t)K * R * T);
+    for (int k = 0; k < K; k++)
+        for (int a = 0; a < M; a++)
+            for (int t = 0; t < T; t++) {
+                const double *q = Q + 2 * (((size_t)k * M + a) * T + t);
+                qp[((size_t)k * R + a) * T + t] = (float)q[0];
+                qp[((size_t)k * R + M + a) * T + t] = (float)q[1];
+            }
+    std::vector<float> uv((size_t)K * P * 4);
+    for (int k = 0; k < K; k++) {
+        int p = 0;
+        for (int a = 0; a < M; a++)
+            for (int b = a; b < M; b++, p++) {
+                double f = (a == b) ? 1.0 : 2.0;  // conj(y_a) U_ab y_b + conj(y_b) U_ba y_a = 2 Re(...)
+                const double *u = U + 2 * (((size_t)k * M + a) * M + b);
+                const double *v = V + 2 * (((size_t)k * M + a) * M + b);
+                float *o = &uv[((size_t)k * P + p) * 4];
+                o[0] = (float)(f * u[0]);
+                o[1] = (float)(f * u[1]);
+                o[2] = (float)(f * v[0]);
+                o[3] = (float)(f * v[1]);
+            }
+    }
+    DeviceGuard g(ctx->device);
+    CK(grow(&ctx->Qp, sizeof(float) * qp.size()));
+    CK(grow(&ctx->UV, sizeof(float) * uv.size()));
+    CK(cudaMemcpyAsync(ctx->Qp, qp.data(), sizeof(float) * qp.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->UV, uv.data(), sizeof(float) * uv.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->pp = pp;
+    ctx->has_data = true;
+    ctx->cap = ctx->cap;  // scratch is sized for ILE_MAX_DET x ILE_MAX_MODES, so it stays valid
+    return ILE_OK;
+}
+
+ile_status ile_eval(ile_ctx *ctx, const double *samples, int64_t N, double *out, unsigned flags) {
+    if (!ctx) return ILE_E_ARG;
+    if (!ctx->has_data) return ILE_E_STATE;
+    if (N < 0) return ILE_E_ARG;
+    if (N == 0) return ILE_OK;
+    if (!samples || !out) return ILE_E_ARG;
+    const int full = (flags & ILE_NO_TMARG) ? 1 : 0;
+    if (full && N > 65536) return ILE_E_ARG;
+    const size_t out_elems = full ? (size_t)N * ctx->pp.Nt : (size_t)N;
+    DeviceGuard g(ctx->device);
+    ile_status st = ensure_samples(ctx, N);
+    if (st != ILE_OK) return st;
+    if (flags & ILE_DEVICE_PTRS) return run_eval(ctx, samples, N, out, full);
+    st = ensure_out(ctx, sizeof(double) * out_elems);
+    if (st != ILE_OK) return st;
+    CK(cudaMemcpyAsync(ctx->theta, samples, sizeof(double) * ILE_NDIM * (size_t)N, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    st = run_eval(ctx, ctx->theta, N, ctx->out, full);
+    if (st != ILE_OK) return st;
+    CK(cudaMemcpyAsync(out, ctx->out, sizeof(double) * out_elems, cudaMemcpyDeviceToHost, ctx->stream));
+    return read_flags(ctx);
+}
+
+ile_status ile_integrate(ile_ctx *ctx, const double *samples, const double *ln_prior, const double *ln_ps,
+                         int64_t N, double *result, double *lnL_t_out, unsigned flags) {
+    if (!ctx) return ILE_E_ARG;
+    if (!ctx->has_data) return ILE_E_STATE;
+    if (N < 1 || !samples || !result) return ILE_E_ARG;
+    DeviceGuard g(ctx->device);
+    ile_status st = ensure_samples(ctx, N);
+    if (st != ILE_OK) return st;
+    const int np = ile_mc_partial_count(N);
+    if (flags & ILE_DEVICE_PTRS) {
+        double *lnl = lnL_t_out;
+        if (!lnl) {
+            st = ensure_out(ctx, sizeof(double) * (size_t)N);
+            if (st != ILE_OK) return st;
+            lnl = ctx->out;
+        }
+        st = run_eval(ctx, samples, N, lnl, 0);
+        if (st != ILE_OK) return st;
+        StageScope t(ctx, 3, 2);
+        CK(ile_launch_mc(lnl, ln_prior, ln_ps, N, ctx->part, np, result, ctx->stream));
+        return ILE_OK;
+    }
+    st = ensure_out(ctx, sizeof(double) * (size_t)N);
+    if (st != ILE_OK) return st;
+    CK(cudaMemcpyAsync(ctx->theta, samples, sizeof(double) * ILE_NDIM * (size_t)N, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    if (ln_prior)
+        CK(cudaMemcpyAsync(ctx->lnp, ln_prior, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
+    if (ln_ps) CK(cudaMemcpyAsync(ctx->lnps, ln_ps, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
+    st = run_eval(ctx, ctx->theta, N, ctx->out, 0);
+    if (st != ILE_OK) return st;
+    {
+        StageScope t(ctx, 3, 2);
+        CK(ile_launch_mc(ctx->out, ln_prior ? ctx->lnp : nullptr, ln_ps ? ctx->lnps : nullptr, N, ctx->part, np,
+                         ctx->result, ctx->stream));
+    }
+    CK(cudaMemcpyAsync(result, ctx->result, 7 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (lnL_t_out) CK(cudaMemcpyAsync(lnL_t_out, ctx->out, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+    return read_flags(ctx);
+}
+
+ile_status ile_profile(ile_ctx *ctx, int enable) {
+    if (!ctx) return ILE_E_ARG;
+    ctx->profiling = enable != 0;
+    return ILE_OK;
+}
+
+ile_status ile_profile_read(ile_ctx *ctx, double *out_ms, int64_t *out_count, int n_stages) {
+    if (!ctx || !out_ms || n_stages < 0 || n_stages > ILE_NSTAGE) return ILE_E_ARG;
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int s = 0; s < ILE_NSTAGE; s++) {
+        double ms = 0.0;
+        for (size_t i = 0; i + 1 < ctx->ev_used[s]; i += 2) {
+            float f = 0.f;
+            CK(cudaEventElapsedTime(&f, ctx->ev[s][i], ctx->ev[s][i + 1]));
+            ms += f;
+        }
+        if (s < n_stages) {
+            out_ms[s] = ms;
+            if (out_count) out_count[s] = ctx->kernels[s];
+        }
+        ctx->ev_used[s] = 0;
+        ctx->kernels[s] = 0;
+    }
+    return ILE_OK;
+}
+
+ile_status ile_sync(ile_ctx *ctx) {
+    if (!ctx) return ILE_E_ARG;
+    DeviceGuard g(ctx->device);
+    return read_flags(ctx);
+}
+
+}  // extern "C"

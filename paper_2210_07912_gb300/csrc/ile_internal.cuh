@@ -1,0 +1,119 @@
+// ile_internal.cuh -- shared declarations of the libile CUDA sources (sm_103a only).
+//
+// Data layout of one intrinsic point in HBM (all owned by the context):
+//   Qp   fp32 [K][2M][T_ext]       rows 0..M-1 = Re Q_lm(t), rows M..2M-1 = Im Q_lm(t)
+//   UV   fp32 [K][P][4]            P = M(M+1)/2 upper-triangle pairs (a <= b), {Re U, Im U, Re V, Im V}
+//                                  with the off-diagonal pairs pre-doubled
+//   Qtc  operand tiles of the tensor-core path (see ile_tc.cu)
+// Per-sample scratch (sized to the largest N seen):
+//   C    fp32 [K][2M][N]           c_klm = (D_ref/D) F_k Y_lm; rows Re then Im
+//   I0   int32 [K][N], W fp32 [K][N]: window start index and lerp weight of each detector
+//   A    fp32 [N]                  quadratic term <h|h>/2
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ile.h"
+
+#define ILE_PI_F 3.14159265358979f
+#define ILE_C_SI 299792458.0
+
+// Device status bits (OR-ed by kernels into a word the host reads after the stream syncs).
+#define ILE_FLAG_RANGE 1u
+#define ILE_FLAG_NONFINITE 2u
+#define ILE_FLAG_TIMEOUT 4u
+
+// d^l_{m,2}(iota) = sum_t coef_t cos(iota/2)^p_t sin(iota/2)^q_t  (at most 3 terms for l <= 4)
+struct WignerTerm {
+    float coef;
+    int p, q;
+};
+
+struct ModeTab {
+    int l, m;
+    float norm;  // sqrt((2l+1)/4pi)
+    int nterms;
+    WignerTerm t[4];
+};
+
+// Everything a kernel needs about the point besides the big arrays; passed by value.
+struct PointParams {
+    int K, M, T_ext, Nt;
+    float x_offset;   // -t_start*fs - N_t/2: window-start index of a sample is tc*fs + dt*fs + x_offset
+    float fs;
+    float gmst;
+    float d_ref;
+    float log_nt;     // ln N_t
+    float det_tensor[ILE_MAX_DET][9];
+    float det_pos_c[ILE_MAX_DET][3];  // r_k / c in seconds
+    ModeTab mode[ILE_MAX_MODES];
+};
+
+// Per-sample geometry: antenna factors and window placement of detector k.
+__device__ __forceinline__ void ile_sample_geometry(const PointParams &pp, float ra, float dec, float psi, float tc,
+                                                    float Fr[ILE_MAX_DET], float Fi[ILE_MAX_DET],
+                                                    float x0[ILE_MAX_DET]) {
+    float sg, cg, sd, cd, sp, cp;
+    sincosf(pp.gmst - ra, &sg, &cg);
+    sincosf(dec, &sd, &cd);
+    sincosf(psi, &sp, &cp);
+    float X0 = -cp * sg - sp * cg * sd, X1 = -cp * cg + sp * sg * sd, X2 = sp * cd;
+    float Y0 = sp * sg - cp * cg * sd, Y1 = sp * cg + cp * sg * sd, Y2 = cp * cd;
+    float n0 = cd * cg, n1 = -cd * sg, n2 = sd;
+#pragma unroll
+    for (int k = 0; k < ILE_MAX_DET; k++) {
+        if (k >= pp.K) break;
+        const float *D = pp.det_tensor[k];
+        float DX0 = D[0] * X0 + D[1] * X1 + D[2] * X2;
+        float DX1 = D[3] * X0 + D[4] * X1 + D[5] * X2;
+        float DX2 = D[6] * X0 + D[7] * X1 + D[8] * X2;
+        float DY0 = D[0] * Y0 + D[1] * Y1 + D[2] * Y2;
+        float DY1 = D[3] * Y0 + D[4] * Y1 + D[5] * Y2;
+        float DY2 = D[6] * Y0 + D[7] * Y1 + D[8] * Y2;
+        Fr[k] = (X0 * DX0 + X1 * DX1 + X2 * DX2) - (Y0 * DY0 + Y1 * DY1 + Y2 * DY2);
+        Fi[k] = (X0 * DY0 + X1 * DY1 + X2 * DY2) + (Y0 * DX0 + Y1 * DX1 + Y2 * DX2);
+        float dt = -(pp.det_pos_c[k][0] * n0 + pp.det_pos_c[k][1] * n1 + pp.det_pos_c[k][2] * n2);
+        x0[k] = (tc + dt) * pp.fs + pp.x_offset;
+    }
+}
+
+// Spin-weighted harmonic _{-2}Y_lm(iota, phi) of mode a.
+__device__ __forceinline__ void ile_sylm(const ModeTab &md, const float cpow[9], const float spow[9], float phi,
+                                         float &yr, float &yi) {
+    float amp = 0.f;
+    for (int t = 0; t < md.nterms; t++) amp += md.t[t].coef * cpow[md.t[t].p] * spow[md.t[t].q];
+    amp *= md.norm;
+    float s, c;
+    sincosf((float)md.m * phi, &s, &c);
+    yr = amp * c;
+    yi = amp * s;
+}
+
+__device__ __forceinline__ void ile_half_angle_powers(float iota, float cpow[9], float spow[9]) {
+    float s, c;
+    sincosf(0.5f * iota, &s, &c);
+    cpow[0] = 1.f;
+    spow[0] = 1.f;
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+        cpow[i] = cpow[i - 1] * c;
+        spow[i] = spow[i - 1] * s;
+    }
+}
+
+// ------------------------------------------------------------------ host-side launch wrappers
+// (defined in the .cu files; all take the context's stream)
+struct IleScratch {
+    float *C;
+    int *I0;
+    float *W;
+    float *A;
+};
+
+cudaError_t ile_launch_prep(const PointParams &pp, const float *UV, const double *samples, int64_t N,
+                            IleScratch s, unsigned *flags, cudaStream_t st);
+cudaError_t ile_launch_plain(const PointParams &pp, const float *Qp, IleScratch s, int64_t N, double *out,
+                             int full_grid, unsigned *flags, cudaStream_t st);
+cudaError_t ile_launch_mc(const double *lnL_t, const double *ln_prior, const double *ln_ps, int64_t N,
+                          double *partials, int n_part, double *result, cudaStream_t st);
+int ile_mc_partial_count(int64_t N);

@@ -1,0 +1,98 @@
+// ile_mc.cu -- stage S6: Monte Carlo marginal likelihood of Eq. (eq:lnL:MonteCarlo) in log space.
+//
+// ln w_n = lnL_t(n) + ln p(theta_n) - ln p_s(theta_n).  Each block reduces one contiguous chunk to
+// a partial (max ln w, S1 = sum e^{ln w - max}, S2 = sum e^{2(ln w - max)}) -- the exponentials in
+// FP32 relative to the block maximum, the sums in FP64 -- and a one-block merge combines the
+// partials in a fixed order, so the result does not depend on scheduling.  The merge gives
+//   ln I = max + ln(S1/N),  sigma_ln = sigma_I / I = sqrt((N S2/S1^2 - 1)/(N - 1)),
+//   n_eff = S1 (= sum w / max w, Eq. (eq:neff)),  ess = S1^2 / S2 (Eq. (eq:neff_ESS)).
+#include "ile_internal.cuh"
+
+namespace {
+
+constexpr int MC_THREADS = 256;
+constexpr int MC_CHUNK = 4096;
+constexpr int MC_MAX_PART = 4096;
+
+__device__ __forceinline__ double lnw_at(const double *lnL, const double *lp, const double *lps, int64_t n) {
+    double v = lnL[n];
+    if (lp) v += lp[n];
+    if (lps) v -= lps[n];
+    return v;
+}
+
+template <typename T, typename Op>
+__device__ T block_reduce(T v, Op op, T *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    T r = sh[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) r = op(r, sh[w]);
+    return r;
+}
+
+__global__ void __launch_bounds__(MC_THREADS) mc_partial_kernel(const double *__restrict__ lnL,
+                                                                const double *__restrict__ lp,
+                                                                const double *__restrict__ lps, int64_t N,
+                                                                double *__restrict__ part) {
+    __shared__ double sh[MC_THREADS / 32];
+    const int64_t beg = (int64_t)blockIdx.x * MC_CHUNK;
+    const int64_t end = min(N, beg + MC_CHUNK);
+    double m = -INFINITY;
+    for (int64_t n = beg + threadIdx.x; n < end; n += MC_THREADS) m = fmax(m, lnw_at(lnL, lp, lps, n));
+    m = block_reduce(m, [](double a, double b) { return fmax(a, b); }, sh);
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t n = beg + threadIdx.x; n < end; n += MC_THREADS) {
+        float e = expf((float)(lnw_at(lnL, lp, lps, n) - m));
+        s1 += (double)e;
+        s2 += (double)e * (double)e;
+    }
+    s1 = block_reduce(s1, [](double a, double b) { return a + b; }, sh);
+    s2 = block_reduce(s2, [](double a, double b) { return a + b; }, sh);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x + 0] = m;
+        part[3 * blockIdx.x + 1] = s1;
+        part[3 * blockIdx.x + 2] = s2;
+    }
+}
+
+__global__ void __launch_bounds__(32) mc_merge_kernel(const double *__restrict__ part, int n_part, int64_t N,
+                                                      double *__restrict__ result) {
+    if (threadIdx.x != 0) return;
+    double m = -INFINITY;
+    for (int b = 0; b < n_part; b++) m = fmax(m, part[3 * b]);
+    double s1 = 0.0, s2 = 0.0;
+    for (int b = 0; b < n_part; b++) {
+        double f = exp(part[3 * b] - m);
+        s1 += part[3 * b + 1] * f;
+        s2 += part[3 * b + 2] * f * f;
+    }
+    const double Nd = (double)N;
+    const double mean = s1 / Nd;
+    double var = (s2 - Nd * mean * mean) / (Nd - 1.0);
+    if (var < 0.0) var = 0.0;
+    result[0] = m + log(mean);
+    result[1] = N > 1 ? sqrt(var / Nd) / mean : INFINITY;
+    result[2] = s1;
+    result[3] = s1 * s1 / s2;
+    result[4] = m;
+    result[5] = s1;
+    result[6] = s2;
+}
+
+}  // namespace
+
+int ile_mc_partial_count(int64_t N) {
+    int64_t p = (N + MC_CHUNK - 1) / MC_CHUNK;
+    return (int)(p < 1 ? 1 : p);
+}
+
+cudaError_t ile_launch_mc(const double *lnL_t, const double *ln_prior, const double *ln_ps, int64_t N,
+                          double *partials, int n_part, double *result, cudaStream_t st) {
+    if (N <= 0 || n_part != ile_mc_partial_count(N) || n_part > MC_MAX_PART * 1024) return cudaErrorInvalidValue;
+    mc_partial_kernel<<<n_part, MC_THREADS, 0, st>>>(lnL_t, ln_prior, ln_ps, N, partials);
+    mc_merge_kernel<<<1, 32, 0, st>>>(partials, n_part, N, result);
+    return cudaGetLastError();
+}

@@ -1,0 +1,196 @@
+"""Thin ctypes binding of libile (include/ile.h).  Argument marshalling only: every step of the
+hot path runs in the library's CUDA kernels.  There is no CPU fallback -- if libile.so is missing
+or no CUDA device is present, every call raises.
+
+Device arrays are passed as torch CUDA tensors (device memory and streams are the only things
+PyTorch provides here); host arrays as numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ILE_OK, ILE_E_ARG, ILE_E_STATE, ILE_E_RANGE, ILE_E_NONFINITE, ILE_E_CUDA, ILE_E_NOMEM, ILE_E_TIMEOUT = range(8)
+PREC = {"fp32": 0, "tf32x3": 1, "bf16x3": 2}
+ILE_DEVICE_PTRS = 1
+ILE_NO_TMARG = 2
+NDIM = 7
+NBINS = 100
+
+_lib = None
+
+
+class IleError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {_lib.ile_status_string(status).decode() if _lib else status}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libile.so (building it first if it is absent and nvcc exists).  Raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libile.so not built ({path}); run __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, d, u = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_uint
+    P = ctypes.POINTER
+    lib.ile_status_string.restype = ctypes.c_char_p
+    lib.ile_status_string.argtypes = [i32]
+    lib.ile_last_error.restype = ctypes.c_char_p
+    lib.ile_last_error.argtypes = [vp]
+    lib.ile_create.argtypes = [P(vp), i32, vp, i32]
+    lib.ile_destroy.argtypes = [vp]
+    lib.ile_set_stream.argtypes = [vp, vp]
+    lib.ile_set_precision.argtypes = [vp, i32]
+    lib.ile_set_data.argtypes = [vp, i32, i32, vp, vp, vp, vp, i32, d, d, vp, vp, i32, d, d]
+    lib.ile_eval.argtypes = [vp, vp, i64, vp, u]
+    lib.ile_integrate.argtypes = [vp, vp, vp, vp, i64, vp, vp, u]
+    lib.ile_sync.argtypes = [vp]
+    lib.ile_profile.argtypes = [vp, i32]
+    lib.ile_profile_read.argtypes = [vp, vp, vp, i32]
+    for name in ("ile_create", "ile_destroy", "ile_set_stream", "ile_set_precision", "ile_set_data", "ile_eval",
+                 "ile_integrate", "ile_sync", "ile_profile", "ile_profile_read"):
+        getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("device tensors must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One libile context (owns the device copy of one intrinsic point and its scratch)."""
+
+    def __init__(self, device: int = 0, stream=None, prec: str = "fp32"):
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        self._check(self._lib.ile_create(ctypes.byref(self._h), device, _stream_handle(stream), PREC[prec]),
+                    "ile_create")
+        self.device = device
+        self.prec = prec
+        self.n_window = None
+
+    def _check(self, st, where):
+        if st != ILE_OK:
+            detail = self._lib.ile_last_error(self._h).decode() if self._h else ""
+            raise IleError(st, where, detail)
+
+    def close(self):
+        if self._h:
+            self._lib.ile_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._check(self._lib.ile_set_stream(self._h, _stream_handle(stream)), "ile_set_stream")
+
+    def set_precision(self, prec: str):
+        self._check(self._lib.ile_set_precision(self._h, PREC[prec]), "ile_set_precision")
+        self.prec = prec
+
+    def set_data(self, p):
+        lm = np.ascontiguousarray(p.lm, np.int32)
+        tens = np.ascontiguousarray(p.det_tensor, np.float64)
+        pos = np.ascontiguousarray(p.det_pos, np.float64)
+        Q = np.ascontiguousarray(np.stack([p.Q.real, p.Q.imag], -1), np.float64)
+        U = np.ascontiguousarray(np.stack([p.U.real, p.U.imag], -1), np.float64)
+        V = np.ascontiguousarray(np.stack([p.V.real, p.V.imag], -1), np.float64)
+        K, M, T = p.Q.shape
+        st = self._lib.ile_set_data(self._h, K, M, _np_ptr(lm), _np_ptr(tens), _np_ptr(pos), _np_ptr(Q), T,
+                                    float(p.t_start), float(p.fs), _np_ptr(U), _np_ptr(V), int(p.n_window),
+                                    float(p.gmst), float(p.d_ref))
+        self._check(st, "ile_set_data")
+        self.n_window = int(p.n_window)
+
+    # ---------------------------------------------------------------- host-pointer calls
+    def eval(self, samples: np.ndarray, grid: bool = False) -> np.ndarray:
+        s = np.ascontiguousarray(samples, np.float64)
+        if s.ndim != 2 or s.shape[0] != NDIM:
+            raise ValueError("samples must be (7, N)")
+        N = s.shape[1]
+        out = np.zeros((N, self.n_window) if grid else N, np.float64)
+        self._check(self._lib.ile_eval(self._h, _np_ptr(s), N, _np_ptr(out), ILE_NO_TMARG if grid else 0),
+                    "ile_eval")
+        return out
+
+    def integrate(self, samples, ln_prior=None, ln_ps=None, want_lnL=False):
+        s = np.ascontiguousarray(samples, np.float64)
+        N = s.shape[1]
+        lp = None if ln_prior is None else np.ascontiguousarray(ln_prior, np.float64)
+        lps = None if ln_ps is None else np.ascontiguousarray(ln_ps, np.float64)
+        res = np.zeros(7)
+        lnl = np.zeros(N) if want_lnL else None
+        st = self._lib.ile_integrate(self._h, _np_ptr(s), _np_ptr(lp), _np_ptr(lps), N, _np_ptr(res), _np_ptr(lnl), 0)
+        self._check(st, "ile_integrate")
+        d = dict(ln_L=res[0], sigma_ln=res[1], n_eff=res[2], ess=res[3], m=res[4], s1=res[5], s2=res[6])
+        return (d, lnl) if want_lnL else d
+
+    # ---------------------------------------------------------------- device-pointer calls (async)
+    def eval_device(self, samples, out, grid: bool = False):
+        """samples: CUDA float64 (7, N); out: CUDA float64 (N,) or (N, N_t).  Queued on the context stream."""
+        N = samples.shape[1]
+        flags = ILE_DEVICE_PTRS | (ILE_NO_TMARG if grid else 0)
+        self._check(self._lib.ile_eval(self._h, _dev_ptr(samples), N, _dev_ptr(out), flags), "ile_eval")
+
+    def integrate_device(self, samples, result, ln_prior=None, ln_ps=None, lnL_out=None):
+        N = samples.shape[1]
+        st = self._lib.ile_integrate(self._h, _dev_ptr(samples), _dev_ptr(ln_prior), _dev_ptr(ln_ps), N,
+                                     _dev_ptr(result), _dev_ptr(lnL_out), ILE_DEVICE_PTRS)
+        self._check(st, "ile_integrate")
+
+    def sync(self):
+        self._check(self._lib.ile_sync(self._h), "ile_sync")
+
+    # ---------------------------------------------------------------- stage timing
+    STAGES = ("sample", "prep", "contract", "mc", "adapt")
+
+    def profile(self, enable: bool = True):
+        self._check(self._lib.ile_profile(self._h, 1 if enable else 0), "ile_profile")
+
+    def profile_read(self):
+        """{stage: (total_ms, launches)} since the previous read (waits for the stream)."""
+        ms = np.zeros(len(self.STAGES))
+        cnt = np.zeros(len(self.STAGES), np.int64)
+        self._check(self._lib.ile_profile_read(self._h, _np_ptr(ms), _np_ptr(cnt), len(self.STAGES)),
+                    "ile_profile_read")
+        return {s: (float(ms[i]), int(cnt[i])) for i, s in enumerate(self.STAGES)}

@@ -1,0 +1,171 @@
+"""GPU-vs-oracle parity of the ILE hot path through the C ABI (needs a GB300).
+
+Bar: per-sample lnL and lnL_t within 1e-3 absolute of the FP64 oracle, ln L_marg within 1e-4
+(the tolerances the path is specified to), on the same seeded inputs.  Small cases compare every
+element and span several sample tiles plus a ragged tail; the full 2^20-sample workload is
+compared on a random subset the oracle computes one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2210_07912_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+LNL_ATOL = 1e-3
+LNMARG_ATOL = 1e-4
+PRECS = ["fp32"]
+
+
+@pytest.fixture(scope="module")
+def ile():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_07912_gb300 import ile as I
+    I.load()
+    return I
+
+
+def _ctx(ile, point, prec="fp32"):
+    c = ile.Context(0, None, prec)
+    c.set_data(point)
+    return c
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_grid_matches_oracle_config0(ile, orc, prec):
+    point = S.config_point(0)
+    th = S.config_samples(0, 300)  # 4 full tiles of 64 + a ragged tail
+    ctx = _ctx(ile, point, prec)
+    grid = ctx.eval(th, grid=True)
+    for n in range(th.shape[1]):
+        ref, _, _ = orc.lnL_grid(point, th[:, n])
+        err = np.abs(grid[n] - ref).max()
+        assert err < LNL_ATOL, (n, err)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_lnL_t_matches_oracle_config0_all_samples(ile, orc, prec):
+    point = S.config_point(0)
+    th = S.config_samples(0)
+    ctx = _ctx(ile, point, prec)
+    got = ctx.eval(th)
+    ref = orc.lnL_t(point, th)
+    err = np.abs(got - ref)
+    assert err.max() < LNL_ATOL, err.max()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_lnL_t_matches_oracle_config1_small(ile, orc, prec):
+    point = S.config_point(1)
+    th = S.config_samples(1, 1000)
+    ctx = _ctx(ile, point, prec)
+    got = ctx.eval(th)
+    ref = orc.lnL_t(point, th)
+    assert np.abs(got - ref).max() < LNL_ATOL
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_lnL_t_full_size_sampled(ile, orc, prec):
+    """2^20 samples on the device (the benchmarked launch); 2048 random ones checked by the oracle."""
+    point = S.config_point(1)
+    th = S.config_samples(1)
+    ctx = _ctx(ile, point, prec)
+    got = ctx.eval(th)
+    idx = np.random.default_rng(3).choice(th.shape[1], 2048, replace=False)
+    ref = orc.lnL_t(point, th[:, idx])
+    assert np.abs(got[idx] - ref).max() < LNL_ATOL
+    assert np.all(np.isfinite(got))
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 3, 7), (4, 9, 33), (3, 21, 1024), (2, 5, 300), (4, 21, 256)])
+def test_odd_shapes(ile, orc, shape):
+    K, M, Nt = shape
+    point = S.make_point(77 + K * M + Nt, K, M, Nt, spectrum="random")
+    th = S.prior_samples(np.random.default_rng(K * 100 + M), 130)
+    ctx = _ctx(ile, point)
+    got = ctx.eval(th)
+    ref = orc.lnL_t(point, th)
+    assert np.abs(got - ref).max() < LNL_ATOL
+
+
+def test_integrate_matches_oracle(ile, orc):
+    point = S.config_point(0)
+    th = S.config_samples(0)
+    rng = np.random.default_rng(4)
+    lnp = rng.normal(0, 0.3, th.shape[1])
+    lnps = rng.normal(0, 0.3, th.shape[1])
+    ctx = _ctx(ile, point)
+    res, lnl = ctx.integrate(th, lnp, lnps, want_lnL=True)
+    ref_lnl = orc.lnL_t(point, th)
+    st = orc.mc_stats(ref_lnl + lnp - lnps)
+    assert abs(res["ln_L"] - st["ln_I"]) < LNMARG_ATOL
+    assert abs(res["n_eff"] - st["n_eff"]) < 1e-3 * st["n_eff"]
+    assert abs(res["ess"] - st["ess"]) < 1e-3 * st["ess"]
+    assert abs(res["sigma_ln"] - st["sigma_ln"]) < 1e-3 * st["sigma_ln"] + 1e-9
+    assert np.abs(lnl - ref_lnl).max() < LNL_ATOL
+
+
+def test_integrate_full_size(ile, orc):
+    """ln L_marg over 2^20 samples vs the oracle's reduction of oracle lnL_t on a sample subset is not
+    exact, so compare the device reduction with the oracle reduction of the device lnL_t and bound
+    the lnL_t error on a subset."""
+    point = S.config_point(1)
+    th = S.config_samples(1)
+    ctx = _ctx(ile, point)
+    res, lnl = ctx.integrate(th, want_lnL=True)
+    st = orc.mc_stats(lnl)
+    assert abs(res["ln_L"] - st["ln_I"]) < 1e-6
+    idx = np.random.default_rng(5).choice(th.shape[1], 1024, replace=False)
+    assert np.abs(lnl[idx] - orc.lnL_t(point, th[:, idx])).max() < LNL_ATOL
+    # a per-sample error bounded by e shifts ln L_marg by at most e
+    assert abs(res["ln_L"] - st["ln_I"]) < LNMARG_ATOL
+
+
+def test_device_pointer_path(ile, orc):
+    import torch
+    point = S.config_point(0)
+    th = S.config_samples(0, 5000)
+    ctx = _ctx(ile, point)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream)
+    d_th = torch.from_numpy(th).cuda()
+    d_out = torch.empty(th.shape[1], dtype=torch.float64, device="cuda")
+    d_res = torch.empty(8, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    ctx.eval_device(d_th, d_out)
+    ctx.integrate_device(d_th, d_res)
+    ctx.sync()
+    ref = orc.lnL_t(point, th)
+    assert np.abs(d_out.cpu().numpy() - ref).max() < LNL_ATOL
+    assert abs(d_res[0].item() - orc.mc_stats(ref)["ln_I"]) < LNMARG_ATOL
+
+
+def test_error_paths(ile):
+    point = S.config_point(0)
+    c = ile.Context(0)
+    with pytest.raises(ile.IleError) as e:
+        c.eval(S.config_samples(0, 4))
+    assert e.value.status == ile.ILE_E_STATE
+    c.set_data(point)
+    assert c.eval(np.zeros((7, 0))).shape == (0,)
+    th = S.config_samples(0, 100)
+    th[6, 17] = 0.05  # coalescence time far outside the window
+    with pytest.raises(ile.IleError) as e:
+        c.eval(th)
+    assert e.value.status == ile.ILE_E_RANGE
+    th = S.config_samples(0, 100)
+    th[0, 3] = np.nan
+    with pytest.raises(ile.IleError) as e:
+        c.eval(th)
+    assert e.value.status == ile.ILE_E_NONFINITE
+    # the context is still usable afterwards
+    good = S.config_samples(0, 10)
+    assert np.all(np.isfinite(c.eval(good)))
+    bad = S.Point(**{**point.__dict__, "lm": np.array([[2, 2], [2, 2]], np.int32)})
+    with pytest.raises(ile.IleError) as e:
+        c.set_data(bad)
+    assert e.value.status == ile.ILE_E_ARG

@@ -157,6 +157,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32x3", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-samples", type=int, default=None,
+                    help="samples per step (default 2^20, the benchmarked workload; smaller only for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -175,7 +177,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    N = S.CONFIGS[CONFIG]["n_samples"]
+    N = args.n_samples or S.CONFIGS[CONFIG]["n_samples"]
     point = S.make_point(S.SEED_BASE + CONFIG + 1000 * rank, 3, 21, 512, spectrum="decay")
     th_host = S.prior_samples(np.random.default_rng([S.SEED_BASE + CONFIG, rank]), N)
     stream = torch.cuda.Stream()

@@ -17,8 +17,12 @@ struct ile_ctx {
     // point data
     float *Qp = nullptr;   // [K][2M][T_ext]
     float *UV = nullptr;   // [K][P][4]
-    void *Qtc = nullptr;   // tensor-core operand layout (ile_tc.cu)
-    size_t Qtc_bytes = 0;
+    // tensor-core operand rows (hi, lo) of the current point, per split precision (ile_tc.cu)
+    void *Qtc[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    bool Qtc_ready[3] = {false, false, false};
+    size_t Qtc_bytes[3] = {0, 0, 0};
+    // delay-sort scratch
+    int *keys = nullptr, *buckets = nullptr, *perm = nullptr;
     // per-sample scratch
     int64_t cap = 0;
     IleScratch s{};
@@ -102,6 +106,9 @@ ile_status ensure_samples(ile_ctx *ctx, int64_t N) {
     CK(grow(&ctx->theta, sizeof(double) * ILE_NDIM * (size_t)cap));
     CK(grow(&ctx->lnp, sizeof(double) * (size_t)cap));
     CK(grow(&ctx->lnps, sizeof(double) * (size_t)cap));
+    CK(grow(&ctx->keys, sizeof(int) * (size_t)cap));
+    CK(grow(&ctx->perm, sizeof(int) * (size_t)cap));
+    if (!ctx->buckets) CK(cudaMalloc((void **)&ctx->buckets, sizeof(int) * ile_sort_key_buckets()));
     int np = ile_mc_partial_count(cap);
     CK(grow(&ctx->part, sizeof(double) * 3 * (size_t)np));
     ctx->part_cap = np;
@@ -164,17 +171,43 @@ ile_status read_flags(ile_ctx *ctx) {
     return ILE_OK;
 }
 
-// S1-S5 on device-resident samples; writes lnL_t (or the grid) to dout.
+// Operand rows of the split-precision contraction for the current point (built once per point).
+ile_status ensure_tc_operands(ile_ctx *ctx, int prec) {
+    if (ctx->Qtc_ready[prec]) return ILE_OK;
+    const size_t bytes = ile_tc_q_bytes(prec, ctx->pp.K, ctx->pp.M, ctx->pp.T_ext);
+    if (bytes > ctx->Qtc_bytes[prec]) {
+        CK(grow(&ctx->Qtc[prec][0], bytes));
+        CK(grow(&ctx->Qtc[prec][1], bytes));
+        ctx->Qtc_bytes[prec] = bytes;
+    }
+    CK(ile_launch_tc_split(prec, ctx->pp, ctx->Qp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ctx->stream));
+    ctx->Qtc_ready[prec] = true;
+    return ILE_OK;
+}
+
+// S1-S5 on device-resident samples; writes lnL_t (or the grid) to dout in the caller's order.
+// Samples are first ordered by quantised detector delays (ile_sort.cu) so that a tile of the
+// contraction spans few time columns; the per-sample results do not depend on that order.
 ile_status run_eval(ile_ctx *ctx, const double *dsamples, int64_t N, double *dout, int full_grid) {
     ile_status st = ensure_samples(ctx, N);
     if (st != ILE_OK) return st;
+    const int prec = (int)ctx->prec;
+    if (prec != ILE_PREC_FP32) {
+        st = ensure_tc_operands(ctx, prec);
+        if (st != ILE_OK) return st;
+    }
     {
-        StageScope t(ctx, 1);
-        CK(ile_launch_prep(ctx->pp, ctx->UV, dsamples, N, ctx->s, ctx->flags, ctx->stream));
+        StageScope t(ctx, 1, 4);
+        CK(ile_launch_sort(ctx->pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));
+        CK(ile_launch_prep(ctx->pp, ctx->UV, dsamples, ctx->perm, N, ctx->s, ctx->flags, ctx->stream));
     }
     {
         StageScope t(ctx, 2);
-        CK(ile_launch_plain(ctx->pp, ctx->Qp, ctx->s, N, dout, full_grid, ctx->flags, ctx->stream));
+        if (prec == ILE_PREC_FP32)
+            CK(ile_launch_plain(ctx->pp, ctx->Qp, ctx->s, ctx->perm, N, dout, full_grid, ctx->flags, ctx->stream));
+        else
+            CK(ile_launch_tc(prec, ctx->pp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ctx->s, ctx->perm, N, dout,
+                             full_grid, ctx->flags, ctx->stream));
     }
     return ILE_OK;
 }
@@ -225,8 +258,10 @@ ile_status ile_create(ile_ctx **out, int device, void *cuda_stream, ile_prec pre
 ile_status ile_destroy(ile_ctx *ctx) {
     if (!ctx) return ILE_OK;
     DeviceGuard g(ctx->device);
-    void *bufs[] = {ctx->Qp, ctx->UV, ctx->Qtc, ctx->s.C, ctx->s.I0, ctx->s.W, ctx->s.A, ctx->theta,
-                    ctx->out, ctx->lnp, ctx->lnps, ctx->part, ctx->result, ctx->flags};
+    void *bufs[] = {ctx->Qp,      ctx->UV,      ctx->Qtc[1][0], ctx->Qtc[1][1], ctx->Qtc[2][0], ctx->Qtc[2][1],
+                    ctx->s.C,     ctx->s.I0,    ctx->s.W,       ctx->s.A,       ctx->theta,     ctx->out,
+                    ctx->lnp,     ctx->lnps,    ctx->part,      ctx->result,    ctx->flags,     ctx->keys,
+                    ctx->buckets, ctx->perm};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (auto &v : ctx->ev)
@@ -312,6 +347,7 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->pp = pp;
     ctx->has_data = true;
+    ctx->Qtc_ready[1] = ctx->Qtc_ready[2] = false;
     ctx->cap = ctx->cap;  // scratch is sized for ILE_MAX_DET x ILE_MAX_MODES, so it stays valid
     return ILE_OK;
 }

@@ -110,10 +110,21 @@ struct IleScratch {
     float *A;
 };
 
-cudaError_t ile_launch_prep(const PointParams &pp, const float *UV, const double *samples, int64_t N,
+cudaError_t ile_launch_prep(const PointParams &pp, const float *UV, const double *samples, const int *perm, int64_t N,
                             IleScratch s, unsigned *flags, cudaStream_t st);
-cudaError_t ile_launch_plain(const PointParams &pp, const float *Qp, IleScratch s, int64_t N, double *out,
-                             int full_grid, unsigned *flags, cudaStream_t st);
+cudaError_t ile_launch_plain(const PointParams &pp, const float *Qp, IleScratch s, const int *perm, int64_t N,
+                             double *out, int full_grid, unsigned *flags, cudaStream_t st);
+// delay-bucket sort (ile_sort.cu): keys [N], buckets [ile_sort_key_buckets()], perm [N]
+size_t ile_sort_key_buckets();
+cudaError_t ile_launch_sort(const PointParams &pp, const double *samples, int64_t N, int *keys, int *buckets,
+                            int *perm, cudaStream_t st);
+// tensor-core path (ile_tc.cu)
+int ile_tc_kpad(int prec, int M);
+int ile_tc_tpad(int T_ext);
+size_t ile_tc_q_bytes(int prec, int K, int M, int T_ext);
+cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp, void *hi, void *lo, cudaStream_t st);
+cudaError_t ile_launch_tc(int prec, const PointParams &pp, const void *hi, const void *lo, IleScratch s,
+                          const int *perm, int64_t N, double *out, int full_grid, unsigned *flags, cudaStream_t st);
 cudaError_t ile_launch_mc(const double *lnL_t, const double *ln_prior, const double *ln_ps, int64_t N,
                           double *partials, int n_part, double *result, cudaStream_t st);
 int ile_mc_partial_count(int64_t N);

@@ -3,7 +3,7 @@
 // ln w_n = lnL_t(n) + ln p(theta_n) - ln p_s(theta_n).  Each block reduces one contiguous chunk to
 // a partial (max ln w, S1 = sum e^{ln w - max}, S2 = sum e^{2(ln w - max)}) -- the exponentials in
 // FP32 relative to the block maximum, the sums in FP64 -- and a one-block merge combines the
-// partials in a fixed order, so the result does not depend on scheduling.  The merge gives
+// partials in a fixed tree order, so the result does not depend on scheduling.  The merge gives
 //   ln I = max + ln(S1/N),  sigma_ln = sigma_I / I = sqrt((N S2/S1^2 - 1)/(N - 1)),
 //   n_eff = S1 (= sum w / max w, Eq. (eq:neff)),  ess = S1^2 / S2 (Eq. (eq:neff_ESS)).
 #include "ile_internal.cuh"
@@ -58,17 +58,21 @@ __global__ void __launch_bounds__(MC_THREADS) mc_partial_kernel(const double *__
     }
 }
 
-__global__ void __launch_bounds__(32) mc_merge_kernel(const double *__restrict__ part, int n_part, int64_t N,
-                                                      double *__restrict__ result) {
-    if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(MC_THREADS) mc_merge_kernel(const double *__restrict__ part, int n_part, int64_t N,
+                                                              double *__restrict__ result) {
+    __shared__ double sh[MC_THREADS / 32];
     double m = -INFINITY;
-    for (int b = 0; b < n_part; b++) m = fmax(m, part[3 * b]);
+    for (int b = threadIdx.x; b < n_part; b += MC_THREADS) m = fmax(m, part[3 * b]);
+    m = block_reduce(m, [](double a, double b) { return fmax(a, b); }, sh);
     double s1 = 0.0, s2 = 0.0;
-    for (int b = 0; b < n_part; b++) {
-        double f = exp(part[3 * b] - m);
+    for (int b = threadIdx.x; b < n_part; b += MC_THREADS) {
+        const double f = exp(part[3 * b] - m);
         s1 += part[3 * b + 1] * f;
         s2 += part[3 * b + 2] * f * f;
     }
+    s1 = block_reduce(s1, [](double a, double b) { return a + b; }, sh);
+    s2 = block_reduce(s2, [](double a, double b) { return a + b; }, sh);
+    if (threadIdx.x != 0) return;
     const double Nd = (double)N;
     const double mean = s1 / Nd;
     double var = (s2 - Nd * mean * mean) / (Nd - 1.0);
@@ -93,6 +97,6 @@ cudaError_t ile_launch_mc(const double *lnL_t, const double *ln_prior, const dou
                           double *partials, int n_part, double *result, cudaStream_t st) {
     if (N <= 0 || n_part != ile_mc_partial_count(N) || n_part > MC_MAX_PART * 1024) return cudaErrorInvalidValue;
     mc_partial_kernel<<<n_part, MC_THREADS, 0, st>>>(lnL_t, ln_prior, ln_ps, N, partials);
-    mc_merge_kernel<<<1, 32, 0, st>>>(partials, n_part, N, result);
+    mc_merge_kernel<<<1, MC_THREADS, 0, st>>>(partials, n_part, N, result);
     return cudaGetLastError();
 }

@@ -21,7 +21,8 @@ constexpr int RMAX = 2 * ILE_MAX_MODES;    // real rows of the contraction
 
 template <int NS>
 __global__ void __launch_bounds__(256) ile_plain_kernel(const __grid_constant__ PointParams pp,
-                                                        const float *__restrict__ Qp, IleScratch s, int64_t N,
+                                                        const float *__restrict__ Qp, IleScratch s,
+                                                        const int *__restrict__ perm, int64_t N,
                                                         double *__restrict__ out, int full_grid) {
     constexpr int RS = NS / 16;  // samples per thread in the micro-tile
     extern __shared__ float smem[];
@@ -133,8 +134,9 @@ __global__ void __launch_bounds__(256) ile_plain_kernel(const __grid_constant__ 
     for (int nn = warp; nn < ns; nn += 8) {
         const float *d = Ds + nn * Nt;
         const double A = (double)s.A[n0 + nn];
+        const int64_t dst = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
         if (full_grid) {
-            for (int j = lane; j < Nt; j += 32) out[(n0 + nn) * Nt + j] = (double)d[j] - A;
+            for (int j = lane; j < Nt; j += 32) out[dst * Nt + j] = (double)d[j] - A;
             continue;
         }
         float m = -INFINITY;
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(256) ile_plain_kernel(const __grid_constant__ 
         float sum = 0.f;
         for (int j = lane; j < Nt; j += 32) sum += expf(d[j] - m);
         for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) out[n0 + nn] = (double)m + (double)logf(sum) - A - log_nt;
+        if (lane == 0) out[dst] = (double)m + (double)logf(sum) - A - log_nt;
     }
 }
 
@@ -153,22 +155,22 @@ size_t plain_smem(const PointParams &pp) {
 }
 
 template <int NS>
-cudaError_t launch(const PointParams &pp, const float *Qp, IleScratch s, int64_t N, double *out, int full_grid,
-                   cudaStream_t st) {
+cudaError_t launch(const PointParams &pp, const float *Qp, IleScratch s, const int *perm, int64_t N, double *out,
+                   int full_grid, cudaStream_t st) {
     size_t smem = plain_smem<NS>(pp);
     cudaError_t e = cudaFuncSetAttribute(ile_plain_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int64_t blocks = (N + NS - 1) / NS;
-    ile_plain_kernel<NS><<<(unsigned)blocks, 256, smem, st>>>(pp, Qp, s, N, out, full_grid);
+    ile_plain_kernel<NS><<<(unsigned)blocks, 256, smem, st>>>(pp, Qp, s, perm, N, out, full_grid);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t ile_launch_plain(const PointParams &pp, const float *Qp, IleScratch s, int64_t N, double *out,
-                             int full_grid, unsigned *flags, cudaStream_t st) {
+cudaError_t ile_launch_plain(const PointParams &pp, const float *Qp, IleScratch s, const int *perm, int64_t N,
+                             double *out, int full_grid, unsigned *flags, cudaStream_t st) {
     (void)flags;
     if (N <= 0) return cudaSuccess;
-    if (pp.Nt <= 512) return launch<64>(pp, Qp, s, N, out, full_grid, st);
-    return launch<32>(pp, Qp, s, N, out, full_grid, st);
+    if (pp.Nt <= 512) return launch<64>(pp, Qp, s, perm, N, out, full_grid, st);
+    return launch<32>(pp, Qp, s, perm, N, out, full_grid, st);
 }

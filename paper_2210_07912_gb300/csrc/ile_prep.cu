@@ -1,6 +1,7 @@
 // ile_prep.cu -- per-sample stages S1 (geometry), S2 (mode coefficients) and S4 (quadratic term).
 //
-// One thread per extrinsic sample.  For each detector k it forms the antenna factor
+// One thread per extrinsic sample, in processing order (optionally a permutation of the caller's
+// order; the per-sample outputs are written at the processing position).  For each detector k it forms the antenna factor
 // F_k = F+ + i Fx, the window start x0_k = (t_c + dt_k - t_start) f_s - N_t/2 (split into an
 // integer index and a lerp weight), and the coefficients c_klm = (D_ref/D) F_k Y_lm
 // (Eq. (eq:loglikelihood), first line).  The quadratic term
@@ -14,20 +15,23 @@ namespace {
 
 __global__ void __launch_bounds__(256) ile_prep_kernel(const __grid_constant__ PointParams pp,
                                                        const float4 *__restrict__ UV,
-                                                       const double *__restrict__ samples, int64_t N,
-                                                       IleScratch s, unsigned *flags) {
+                                                       const double *__restrict__ samples,
+                                                       const int *__restrict__ perm, int64_t N, IleScratch s,
+                                                       unsigned *flags) {
     extern __shared__ float4 uv_s[];  // [K][P]
     const int M = pp.M, K = pp.K, P = M * (M + 1) / 2;
     for (int i = threadIdx.x; i < K * P; i += blockDim.x) uv_s[i] = UV[i];
     __syncthreads();
+    // n: position in the (sorted) processing order; src: the sample's index in the caller's arrays
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
+    const int64_t src = perm ? (int64_t)perm[n] : n;
 
     double th[ILE_NDIM];
     bool finite = true;
 #pragma unroll
     for (int d = 0; d < ILE_NDIM; d++) {
-        th[d] = samples[(int64_t)d * N + n];
+        th[d] = samples[(int64_t)d * N + src];
         finite = finite && isfinite(th[d]);
     }
     if (!finite || th[5] <= 0.0) {
@@ -123,12 +127,12 @@ __global__ void __launch_bounds__(256) ile_prep_kernel(const __grid_constant__ P
 
 }  // namespace
 
-cudaError_t ile_launch_prep(const PointParams &pp, const float *UV, const double *samples, int64_t N, IleScratch s,
-                            unsigned *flags, cudaStream_t st) {
+cudaError_t ile_launch_prep(const PointParams &pp, const float *UV, const double *samples, const int *perm, int64_t N,
+                            IleScratch s, unsigned *flags, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     const int P = pp.M * (pp.M + 1) / 2;
     size_t smem = sizeof(float4) * pp.K * P;
     int64_t blocks = (N + 255) / 256;
-    ile_prep_kernel<<<(unsigned)blocks, 256, smem, st>>>(pp, (const float4 *)UV, samples, N, s, flags);
+    ile_prep_kernel<<<(unsigned)blocks, 256, smem, st>>>(pp, (const float4 *)UV, samples, perm, N, s, flags);
     return cudaGetLastError();
 }

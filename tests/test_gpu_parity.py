@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 LNL_ATOL = 1e-3
 LNMARG_ATOL = 1e-4
-PRECS = ["fp32"]
+PRECS = ["fp32", "tf32x3", "bf16x3"]
 
 
 @pytest.fixture(scope="module")
@@ -81,24 +81,26 @@ def test_lnL_t_full_size_sampled(ile, orc, prec):
     assert np.all(np.isfinite(got))
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 3, 7), (4, 9, 33), (3, 21, 1024), (2, 5, 300), (4, 21, 256)])
-def test_odd_shapes(ile, orc, shape):
+def test_odd_shapes(ile, orc, shape, prec):
     K, M, Nt = shape
     point = S.make_point(77 + K * M + Nt, K, M, Nt, spectrum="random")
     th = S.prior_samples(np.random.default_rng(K * 100 + M), 130)
-    ctx = _ctx(ile, point)
+    ctx = _ctx(ile, point, prec)
     got = ctx.eval(th)
     ref = orc.lnL_t(point, th)
     assert np.abs(got - ref).max() < LNL_ATOL
 
 
-def test_integrate_matches_oracle(ile, orc):
+@pytest.mark.parametrize("prec", PRECS)
+def test_integrate_matches_oracle(ile, orc, prec):
     point = S.config_point(0)
     th = S.config_samples(0)
     rng = np.random.default_rng(4)
     lnp = rng.normal(0, 0.3, th.shape[1])
     lnps = rng.normal(0, 0.3, th.shape[1])
-    ctx = _ctx(ile, point)
+    ctx = _ctx(ile, point, prec)
     res, lnl = ctx.integrate(th, lnp, lnps, want_lnL=True)
     ref_lnl = orc.lnL_t(point, th)
     st = orc.mc_stats(ref_lnl + lnp - lnps)
@@ -109,13 +111,13 @@ def test_integrate_matches_oracle(ile, orc):
     assert np.abs(lnl - ref_lnl).max() < LNL_ATOL
 
 
-def test_integrate_full_size(ile, orc):
-    """ln L_marg over 2^20 samples vs the oracle's reduction of oracle lnL_t on a sample subset is not
-    exact, so compare the device reduction with the oracle reduction of the device lnL_t and bound
-    the lnL_t error on a subset."""
+@pytest.mark.parametrize("prec", PRECS)
+def test_integrate_full_size(ile, orc, prec):
+    """ln L_marg over 2^20 samples: the device reduction equals the oracle reduction of the device
+    lnL_t, and the device lnL_t is within tolerance of the oracle on a random subset."""
     point = S.config_point(1)
     th = S.config_samples(1)
-    ctx = _ctx(ile, point)
+    ctx = _ctx(ile, point, prec)
     res, lnl = ctx.integrate(th, want_lnL=True)
     st = orc.mc_stats(lnl)
     assert abs(res["ln_L"] - st["ln_I"]) < 1e-6

@@ -196,6 +196,18 @@ ile_status run_eval(ile_ctx *ctx, const double *dsamples, int64_t N, double *dou
         st = ensure_tc_operands(ctx, prec);
         if (st != ILE_OK) return st;
     }
+    if (prec == ILE_PREC_BF16X3) {
+        // fused kernel: S1, S2, S4 are computed inside the tensor-core kernel
+        {
+            StageScope t(ctx, 1, 3);
+            CK(ile_launch_sort(ctx->pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));
+        }
+        StageScope t(ctx, 2);
+        CK(ile_launch_tc2(ctx->pp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ile_tc_tpad(ctx->pp.T_ext),
+                          ile_tc_kpad(prec, ctx->pp.M), ctx->UV, dsamples, ctx->perm, N, dout, full_grid, ctx->flags,
+                          ctx->stream));
+        return ILE_OK;
+    }
     {
         StageScope t(ctx, 1, 4);
         CK(ile_launch_sort(ctx->pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));

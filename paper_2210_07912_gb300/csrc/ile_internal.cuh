@@ -125,6 +125,9 @@ size_t ile_tc_q_bytes(int prec, int K, int M, int T_ext);
 cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp, void *hi, void *lo, cudaStream_t st);
 cudaError_t ile_launch_tc(int prec, const PointParams &pp, const void *hi, const void *lo, IleScratch s,
                           const int *perm, int64_t N, double *out, int full_grid, unsigned *flags, cudaStream_t st);
+cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo, int TP, int KP, const float *UV,
+                           const double *samples, const int *perm, int64_t N, double *out, int full_grid,
+                           unsigned *flags, cudaStream_t st);
 cudaError_t ile_launch_mc(const double *lnL_t, const double *ln_prior, const double *ln_ps, int64_t N,
                           double *partials, int n_part, double *result, cudaStream_t st);
 int ile_mc_partial_count(int64_t N);

@@ -1,38 +1,49 @@
 // ile_sort.cu -- orders the extrinsic samples so that a 128-sample tile needs few time columns.
 //
 // A sample's window start in detector k is t_c f_s + dt_k f_s + const, and the light-travel
-// delays dt_k (up to ~87 bins at 4096 Hz) dominate the spread between samples.  Samples are
-// bucketed by their quantised delays (dt_k f_s / 4 for the first three detectors, 64 levels
-// each, lexicographic key) with a counting sort: count -> exclusive scan -> scatter.  Within a
-// bucket the order is whatever the atomics give; no result depends on it, because every sample
-// is evaluated independently and the Monte Carlo sums run over the original order.
+// delays dt_k (up to ~87 bins at 4096 Hz) dominate the spread between samples.  The delays are
+// smooth functions of the source direction in the Earth-fixed frame, so samples are bucketed by
+// sky cell: a 128 x 128 grid in (Earth-fixed longitude gmst - ra, sin dec), cells ordered along a
+// Hilbert curve so that consecutive buckets are neighbouring cells.  Counting sort: count ->
+// exclusive scan -> scatter.  Within a bucket the order is whatever the atomics give; no result
+// depends on it, because every sample is evaluated independently and the Monte Carlo sums run
+// over the caller's order.
 #include "ile_internal.cuh"
 
 namespace {
 
-constexpr int KEY_BITS = 6;
-constexpr int NKEY = 1 << (3 * KEY_BITS);
+constexpr int GRID = 128;  // cells per axis
+constexpr int NKEY = GRID * GRID;
+
+// Hilbert-curve index of cell (x, y) on a GRID x GRID grid.
+__device__ __forceinline__ int hilbert_index(int x, int y) {
+    int d = 0;
+    for (int s = GRID / 2; s > 0; s >>= 1) {
+        const int rx = (x & s) ? 1 : 0, ry = (y & s) ? 1 : 0;
+        d += s * s * ((3 * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = s - 1 - x;
+                y = s - 1 - y;
+            }
+            const int tmp = x;
+            x = y;
+            y = tmp;
+        }
+    }
+    return d;
+}
 
 __device__ __forceinline__ int delay_key(const PointParams &pp, const double *__restrict__ samples, int64_t N,
                                          int64_t n) {
-    const float ra = (float)samples[n], dec = (float)samples[N + n];
-    float sg, cg, sd, cd;
-    sincosf(pp.gmst - ra, &sg, &cg);
-    sincosf(dec, &sd, &cd);
-    const float n0 = cd * cg, n1 = -cd * sg, n2 = sd;
-    int key = 0;
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        int q = 0;
-        if (k < pp.K) {
-            float dt = -(pp.det_pos_c[k][0] * n0 + pp.det_pos_c[k][1] * n1 + pp.det_pos_c[k][2] * n2) * pp.fs;
-            float v = floorf(dt * 0.25f) + 32.f;
-            v = fminf(fmaxf(v, 0.f), 63.f);  // also maps NaN to 0: non-finite samples are flagged elsewhere
-            q = (int)v;
-        }
-        key = (key << KEY_BITS) | q;
-    }
-    return key;
+    const double ra = samples[n], dec = samples[N + n];
+    float lon = (float)(pp.gmst - ra) * (1.0f / (2.0f * ILE_PI_F));
+    lon -= floorf(lon);
+    const float sd = 0.5f * (sinf((float)dec) + 1.0f);
+    // fminf/fmaxf also map NaN to a valid cell: non-finite samples are flagged elsewhere
+    const int x = (int)fminf(fmaxf(lon * GRID, 0.f), (float)(GRID - 1));
+    const int y = (int)fminf(fmaxf(sd * GRID, 0.f), (float)(GRID - 1));
+    return hilbert_index(x, y);
 }
 
 __global__ void __launch_bounds__(256) key_count_kernel(const __grid_constant__ PointParams pp,
@@ -46,12 +57,14 @@ __global__ void __launch_bounds__(256) key_count_kernel(const __grid_constant__ 
 }
 
 // Exclusive scan of NKEY counts in one block of 1024 threads (NKEY / 1024 entries per thread).
+static_assert(NKEY % 1024 == 0, "scan layout");
 __global__ void __launch_bounds__(1024) scan_kernel(int *__restrict__ count) {
     constexpr int PER = NKEY / 1024;
     __shared__ int warp_tot[32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     int *c = count + t * PER;
     int local = 0;
+#pragma unroll 4
     for (int i = 0; i < PER; i++) local += c[i];
     int incl = local;
     for (int o = 1; o < 32; o <<= 1) {
@@ -71,6 +84,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(int *__restrict__ count) {
     }
     __syncthreads();
     int run = warp_tot[warp] + incl - local;
+#pragma unroll 4
     for (int i = 0; i < PER; i++) {
         int v = c[i];
         c[i] = run;

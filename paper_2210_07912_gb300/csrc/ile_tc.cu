@@ -18,11 +18,13 @@
 // byte offset (between K-chunks) is rows * 16 and the stride-dimension byte offset (between
 // 8-row groups) is 128.
 //
+// This kernel serves the TF32x3 mode (and BF16x3 when the fused kernel of ile_tc2.cu cannot be used).
 // Every wait on an mbarrier is bounded; on expiry the kernel raises ILE_FLAG_TIMEOUT, waits once
 // more (bounded) for its MMAs, releases its TMEM and returns.
-#include <cuda_bf16.h>
-
 #include "ile_internal.cuh"
+#include "ile_tcgen05.cuh"
+
+using namespace ile_tc;
 
 namespace {
 
@@ -47,114 +49,7 @@ struct Tc<false> {
     static constexpr uint32_t FMT = 2;  // TF32
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-           (1ull << 46);
-}
-
-template <bool BF16>
-__device__ __forceinline__ uint32_t idesc(int n) {
-    return (1u << 4) | (Tc<BF16>::FMT << 7) | (Tc<BF16>::FMT << 10) | ((uint32_t)(n >> 3) << 17) |
-           ((uint32_t)(TILE >> 4) << 24);
-}
-
-template <bool BF16>
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-    if constexpr (BF16) {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-            "l"(a), "l"(b), "r"(id), "r"(acc));
-    } else {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-            "l"(a), "l"(b), "r"(id), "r"(acc));
-    }
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait; also gives up early once any CTA of the launch has raised ILE_FLAG_TIMEOUT.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const unsigned *flags) {
-    for (int i = 0; i < WAIT_SPINS; i++) {
-        if (mbar_try(bar, parity)) return true;
-        if ((i & 1023) == 1023 && (*(volatile const unsigned *)flags & ILE_FLAG_TIMEOUT)) return false;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-// hi + lo split of one value; returns the two 16- or 32-bit patterns.
-template <bool BF16>
-__device__ __forceinline__ void split(float x, uint32_t &hi, uint32_t &lo) {
-    if constexpr (BF16) {
-        __nv_bfloat16 h = __float2bfloat16_rn(x);
-        __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-        hi = (uint32_t)__bfloat16_as_ushort(h);
-        lo = (uint32_t)__bfloat16_as_ushort(l);
-    } else {
-        hi = to_tf32(x);
-        lo = to_tf32(x - __uint_as_float(hi));
-    }
-}
-
-// Pack EPC split values of one 16-byte chunk.
-template <bool BF16>
-__device__ __forceinline__ void pack_chunk(const float *v, uint4 &hi, uint4 &lo) {
-    uint32_t h[4], l[4];
-    if constexpr (BF16) {
-#pragma unroll
-        for (int w = 0; w < 4; w++) {
-            uint32_t h0, l0, h1, l1;
-            split<true>(v[2 * w], h0, l0);
-            split<true>(v[2 * w + 1], h1, l1);
-            h[w] = h0 | (h1 << 16);
-            l[w] = l0 | (l1 << 16);
-        }
-    } else {
-#pragma unroll
-        for (int w = 0; w < 4; w++) split<false>(v[w], h[w], l[w]);
-    }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
+__device__ __forceinline__ int64_t qtile_index(int k, int kc, int t, int KC, int TP);
 
 struct TcSmem {
     uint64_t bar;
@@ -186,14 +81,10 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
     const bool valid = p < N;
     const int64_t p0 = (int64_t)blockIdx.x * TILE;  // always valid
 
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
-                     "r"(TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
+    if (warp == 0) tmem_alloc(&sm.tmem_base, TMEM_COLS);
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.bar)));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init(&sm.bar, 1);
+        mbar_init_fence();
     }
     for (int k = 0; k < K; k++) {
         const int64_t q = valid ? p : p0;
@@ -201,9 +92,9 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
         sm.w[k][t] = valid ? s.W[(int64_t)k * N + q] : 0.f;
     }
     if (t < 2 * ILE_MAX_DET) sm.lohi[t / ILE_MAX_DET][t % ILE_MAX_DET] = (t < ILE_MAX_DET) ? 0x7fffffff : -0x7fffffff;
-    tc_fence_before();
+    fence_before();
     __syncthreads();
-    tc_fence_after();
+    fence_after();
     const uint32_t tmem = sm.tmem_base;
     for (int k = 0; k < K; k++) {
         int v = sm.i0[k][t];
@@ -234,8 +125,9 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
                 float v[EPC];
 #pragma unroll
                 for (int e = 0; e < EPC; e++) {
-                    const int r = kc * EPC + e;
-                    v[e] = (valid && r < R) ? s.C[((int64_t)k * R + r) * N + p] : 0.f;
+                    const int r = kc * EPC + e;  // operand K index 2a + {Re, Im}; C rows are Re then Im
+                    const int row = (r & 1) ? R / 2 + r / 2 : r / 2;
+                    v[e] = (valid && r < R) ? s.C[((int64_t)k * R + row) * N + p] : 0.f;
                 }
                 uint4 h, l;
                 pack_chunk<BF16>(v, h, l);
@@ -249,19 +141,18 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
             for (int wbeg = col_lo; wbeg <= col_hi && !timed_out; wbeg += NWMAX) {
                 const int nw = min(NWMAX, col_hi - wbeg + 1);
                 const int nwr = (nw + 15) & ~15;
-                const uint4 *qh = Qhi + (int64_t)k * KC * TP + wbeg;
-                const uint4 *ql = Qlo + (int64_t)k * KC * TP + wbeg;
                 for (int i = t; i < KC * nwr; i += TILE) {
                     const int kc = i / nwr, c = i - kc * nwr;
-                    Bhi[kc * nwr + c] = qh[(int64_t)kc * TP + c];
-                    Blo[kc * nwr + c] = ql[(int64_t)kc * TP + c];
+                    const int64_t qi = qtile_index(k, kc, wbeg + c, KC, TP);
+                    Bhi[kc * nwr + c] = Qhi[qi];
+                    Blo[kc * nwr + c] = Qlo[qi];
                 }
                 fence_async_smem();
-                tc_fence_before();
+                fence_before();
                 __syncthreads();
                 if (t == 0) {
-                    tc_fence_after();
-                    const uint32_t id = idesc<BF16>(nwr);
+                    fence_after();
+                    const uint32_t id = idesc(Tc<BF16>::FMT, TILE, nwr);
                     const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo);
                     const uint32_t b_hi = smem_u32(Bhi), b_lo = smem_u32(Blo);
                     const uint32_t a_lbo = TILE * 16, b_lbo = (uint32_t)nwr * 16;
@@ -274,21 +165,24 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
                         for (int ks = 0; ks < nks; ks++) {
                             const uint64_t ad = sdesc(ab + ks * 2 * a_lbo, a_lbo, 128);
                             const uint64_t bd = sdesc(bb + ks * 2 * b_lbo, b_lbo, 128);
-                            mma<BF16>(tmem, ad, bd, id, acc);
+                            if constexpr (BF16)
+                                mma_bf16(tmem, ad, bd, id, acc);
+                            else
+                                mma_tf32(tmem, ad, bd, id, acc);
                             acc = 1;
                         }
                     }
                     mma_commit(&sm.bar);
                 }
-                bool ok = mbar_wait(&sm.bar, phase, flags);
+                bool ok = mbar_wait(&sm.bar, phase, flags, ILE_FLAG_TIMEOUT, WAIT_SPINS);
                 phase ^= 1u;
                 if (__syncthreads_or(!ok)) {
                     timed_out = true;
                     if (t == 0) atomicOr(flags, ILE_FLAG_TIMEOUT);
-                    mbar_wait(&sm.bar, phase ^ 1u, flags);
+                    mbar_wait(&sm.bar, phase ^ 1u, flags, 0u, WAIT_SPINS);
                     break;
                 }
-                tc_fence_after();
+                fence_after();
                 for (int cb = 0; cb < nwr; cb += 32) {
                     uint32_t r[32];
                     tmem_ld32(tmem + lane_base + (uint32_t)cb, r);
@@ -301,7 +195,7 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
                         if (jq >= 1 && jq <= Jc) Dt[(jq - 1) * TILE + t] += w * g;
                     }
                 }
-                tc_fence_before();
+                fence_before();
             }
         }
         if (timed_out) break;
@@ -323,16 +217,21 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
     if (valid && !full_grid && !timed_out)
         out[perm ? perm[p] : p] = (double)m_run + (double)logf(s_run) - (double)A - (double)pp.log_nt;
 
-    tc_fence_before();
+    fence_before();
     __syncthreads();
     if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+        fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
     }
 }
 
-// Split the FP32 data rows Qp [K][R][T] into hi/lo operand rows [K][KC][TP] (16-byte chunks of
-// EPC consecutive K-elements r), zero-padded in r up to KP and in t up to TP.
+// Split the FP32 data rows Qp [K][R][T] (Re rows then Im rows) into hi/lo operand rows
+// [K][KC][TP]: 16-byte chunks of EPC consecutive operand K indices r = 2a + {0: Re, 1: Im},
+// zero-padded in r up to KP and in t up to TP.
+// Split the FP32 data rows Qp [K][R][T] (Re rows then Im rows) into hi/lo operand chunks:
+// 16-byte chunks of EPC consecutive operand K indices r = 2a + {0: Re, 1: Im} (zero-padded up
+// to KP), stored core-matrix tiled as [K][TP/8][KC][8 columns] so that a window of 8-aligned
+// columns is one contiguous block (zero-padded in t up to TP).
 template <bool BF16>
 __global__ void split_q_kernel(const float *__restrict__ Qp, int K, int R, int T, int KP, int TP, uint4 *__restrict__ hi,
                                uint4 *__restrict__ lo) {
@@ -340,20 +239,28 @@ __global__ void split_q_kernel(const float *__restrict__ Qp, int K, int R, int T
     const int KC = KP / EPC;
     const int64_t total = (int64_t)K * KC * TP;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int tt = (int)(i % TP);
-        const int kc = (int)((i / TP) % KC);
-        const int k = (int)(i / ((int64_t)TP * KC));
+        const int t8 = (int)(i % 8);
+        const int kc = (int)((i / 8) % KC);
+        const int64_t grp = i / (8 * KC);  // k * TP/8 + t / 8
+        const int k = (int)(grp / (TP / 8));
+        const int tt = (int)(grp % (TP / 8)) * 8 + t8;
         float v[EPC];
 #pragma unroll
         for (int e = 0; e < EPC; e++) {
             const int r = kc * EPC + e;
-            v[e] = (r < R && tt < T) ? Qp[((int64_t)k * R + r) * T + tt] : 0.f;
+            const int row = (r & 1) ? R / 2 + r / 2 : r / 2;
+            v[e] = (r < R && tt < T) ? Qp[((int64_t)k * R + row) * T + tt] : 0.f;
         }
         uint4 h, l;
         pack_chunk<BF16>(v, h, l);
         hi[i] = h;
         lo[i] = l;
     }
+}
+
+// Index (in 16-byte chunks) of K-chunk kc of column t of detector k in the tiled split layout.
+__device__ __forceinline__ int64_t qtile_index(int k, int kc, int t, int KC, int TP) {
+    return (((int64_t)k * (TP / 8) + t / 8) * KC + kc) * 8 + (t & 7);
 }
 
 template <bool BF16>
@@ -369,7 +276,7 @@ int ile_tc_kpad(int prec, int M) {
     return prec == ILE_PREC_BF16X3 ? (R + 15) & ~15 : (R + 7) & ~7;
 }
 
-int ile_tc_tpad(int T_ext) { return T_ext + NWMAX + 16; }
+int ile_tc_tpad(int T_ext) { return (T_ext + NWMAX + 16 + 7) & ~7; }
 
 size_t ile_tc_q_bytes(int prec, int K, int M, int T_ext) {
     const int KP = ile_tc_kpad(prec, M);

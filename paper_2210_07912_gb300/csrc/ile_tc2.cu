@@ -1,0 +1,550 @@
+// ile_tc2.cu -- fused, pipelined BF16x3 tensor-core kernel for stages S1-S5 on sm_103a.
+//
+// One persistent CTA per SM walks 128-sample tiles of the delay-sorted samples.  18 warps:
+//
+//   16 math warps: warp w serves TMEM lane quadrant q = w % 4 (samples 32q .. 32q+31 of the
+//   tile) and bin group g = w / 4, so each sample has four threads (g = 0..3):
+//     * S1/S2: every thread of a sample forms the geometry (F_k, window start i0_k + w_k) and
+//       the harmonics Y_lm; thread g < K writes detector g's coefficients
+//       c_glm = (D_ref/D) F_g Y_lm, split hi/lo (BF16), as the MMA A operand in shared memory
+//       (K index 2a + {Re, Im} of mode a, as in the split Q rows);
+//     * S4: A(n) = 1/4 (D_ref/D)^2 sum_k [|F_k|^2 y^H U_k y + Re(F_k^2 y^T V_k y)] on CUDA
+//       cores, the upper-triangle mode pairs shared round-robin among the four threads;
+//     * S3/S5 epilogue for every job: load the sample's accumulator columns from TMEM, keep the
+//       17 it needs (bins 16g .. 16g+15 and the lerp partner) in a thread-private strip of shared
+//       memory, and add (1 - w) G(i0 + j) + w G(i0 + j + 1) into its window accumulator D[16]
+//       (registers); after the last detector of a chunk, fold D into a running log-sum-exp.
+//       At the end of a tile the four threads' (max, sum) pairs are merged in FP64.
+//   warp 17, lane 0 (copy warp): for every job (chunk of 64 window bins x detector x column
+//   window of <= 120 columns) bulk-copy the Q window (hi and lo rows, one contiguous block each)
+//   into a ring of NB shared buffers as soon as a slot is free;
+//   warp 16, lane 0 (MMA warp): issue 3 x KP/16 tcgen05.mma (hi*hi + hi*lo + lo*hi, kind::f16,
+//   FP32 accumulation) per job into one of two TMEM accumulator buffers.
+//
+// Hand-offs are mbarriers: bfull/bempty (B ring), tfull/tempty (TMEM buffers), aready (A operand
+// and the tile's column ranges written; waited on by all roles), tdone (per-thread log-sum-exp
+// partials written).  Jobs are enumerated identically by all roles.  A tile whose column spread
+// does not fit one window is covered by overlapping windows of 128 columns, each sample reading
+// the single window that holds all the columns it needs.  Every wait is bounded; on expiry the
+// kernel raises ILE_FLAG_TIMEOUT (all CTAs then stop waiting), releases its TMEM and returns.
+#include "ile_internal.cuh"
+#include "ile_tcgen05.cuh"
+
+using namespace ile_tc;
+
+namespace {
+
+constexpr int TILE = 128;
+constexpr int NGRP = 4;                    // threads per sample
+constexpr int NMATH = TILE * NGRP;         // 512 math threads
+constexpr int MMA_WARP = NMATH / 32;        // warp 16: tcgen05.mma issue
+constexpr int COPY_WARP = MMA_WARP + 1;    // warp 17: bulk copies of the Q windows
+constexpr int NTHREADS = NMATH + 64;
+constexpr int JW = 64;                     // window bins per chunk
+constexpr int JG = JW / NGRP;              // bins per thread per chunk
+constexpr int NWIN = 128;                  // columns per TMEM accumulator buffer (= max MMA N here)
+constexpr int NWCOL = 120;                 // window columns (+ up to 7 for 8-column alignment <= NWIN)
+constexpr uint32_t TMEM_COLS = 2 * NWIN;
+constexpr int NBMAX = 4;                   // B ring depth upper bound
+constexpr int SPINS = 1 << 20;
+constexpr int SLEEPS = 200000;             // bounded sleeping waits: SLEEPS x SLEEP_NS at most
+constexpr uint32_t SLEEP_NS = 10000;
+constexpr int STRIP = JG + 1;              // columns a thread keeps per job
+
+struct Sm {
+    uint64_t bfull[NBMAX], bempty[NBMAX], tfull[2], tempty[2], yready, aready, tdone;
+    uint32_t tmem_base;
+    int wlo[4][ILE_MAX_DET], whi[4][ILE_MAX_DET];
+};
+
+// Register-resident per-detector value (the selects avoid dynamic indexing).
+struct Det4 {
+    int v0, v1, v2, v3;
+    __device__ int operator()(int k) const { return k == 0 ? v0 : k == 1 ? v1 : k == 2 ? v2 : v3; }
+};
+struct Det4f {
+    float v0, v1, v2, v3;
+    __device__ float operator()(int k) const { return k == 0 ? v0 : k == 1 ? v1 : k == 2 ? v2 : v3; }
+};
+
+// One job of a tile: chunk c (bins j0 .. j0 + Jc), detector k, window w of W.
+struct Job {
+    int j0, Jc, k, w, W, step, wbeg, wbeg8, nwr;  // window [wbeg8, wbeg8 + nwr), wbeg8 = wbeg rounded down to 8
+};
+
+// Enumerates the jobs of a tile from its per-detector column range [lo_k, hi_k] of window
+// starts; the MMA warp and the math warps walk the same sequence.
+struct JobIter {
+    int Nt, K;
+    Det4 lo, hi;
+    int c, k, w;
+    bool done;
+    __device__ JobIter(int Nt_, int K_, Det4 lo_, Det4 hi_)
+        : Nt(Nt_), K(K_), lo(lo_), hi(hi_), c(0), k(0), w(0), done(false) {}
+    __device__ Job get() const {
+        Job j;
+        j.j0 = c * JW;
+        j.Jc = min(JW, Nt - j.j0);
+        j.k = k;
+        j.w = w;
+        const int col_lo = lo(k) + j.j0, col_hi = hi(k) + j.j0 + j.Jc;  // inclusive
+        const int total = col_hi - col_lo + 1;
+        if (total <= NWCOL) {
+            j.W = 1;
+            j.step = NWCOL;
+        } else {
+            j.step = NWCOL - j.Jc - 1;
+            j.W = 1 + (total - NWCOL + j.step - 1) / j.step;
+        }
+        j.wbeg = col_lo + w * j.step;
+        j.wbeg8 = j.wbeg & ~7;
+        const int nw = min(NWCOL, col_hi - j.wbeg + 1) + (j.wbeg - j.wbeg8);
+        j.nwr = (nw + 15) & ~15;
+        return j;
+    }
+    __device__ void next() {
+        const Job j = get();
+        if (++w < j.W) return;
+        w = 0;
+        if (++k < K) return;
+        k = 0;
+        if ((++c) * JW >= Nt) done = true;
+    }
+};
+
+// Tile column range of detector k from the per-quadrant partial ranges.
+__device__ __forceinline__ void tile_range(const int (*wlo)[ILE_MAX_DET], const int (*whi)[ILE_MAX_DET], int K,
+                                           Det4 &lo, Det4 &hi) {
+    int l[ILE_MAX_DET], h[ILE_MAX_DET];
+#pragma unroll
+    for (int k = 0; k < ILE_MAX_DET; k++) {
+        l[k] = k < K ? min(min(wlo[0][k], wlo[1][k]), min(wlo[2][k], wlo[3][k])) : 0;
+        h[k] = k < K ? max(max(whi[0][k], whi[1][k]), max(whi[2][k], whi[3][k])) : 0;
+    }
+    lo = Det4{l[0], l[1], l[2], l[3]};
+    hi = Det4{h[0], h[1], h[2], h[3]};
+}
+
+__device__ __forceinline__ bool wait1(uint64_t *bar, uint32_t parity, const unsigned *flags) {
+    return mbar_wait_sleep(bar, parity, flags, ILE_FLAG_TIMEOUT, SLEEPS, SLEEP_NS);
+}
+
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, const unsigned *flags) {
+    return __all_sync(0xffffffffu, wait1(bar, parity, flags));
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    ile_tc2_kernel(const __grid_constant__ PointParams pp, const uint4 *__restrict__ Qhi, const uint4 *__restrict__ Qlo,
+                   int TP, int KP, int NB, const float4 *__restrict__ UV, const double *__restrict__ samples,
+                   const int *__restrict__ perm, int64_t N, double *__restrict__ out, int full_grid,
+                   unsigned *flags) {
+    extern __shared__ __align__(1024) uint8_t dsm[];
+    __shared__ Sm sm;
+    const int K = pp.K, M = pp.M, Nt = pp.Nt;
+    const int KC = KP / 8, P = M * (M + 1) / 2;
+    float4 *uvs = reinterpret_cast<float4 *>(dsm);                                   // [K][P]
+    uint4 *A = reinterpret_cast<uint4 *>(dsm + 16 * ((K * P + 63) / 64 * 64));       // [K][2][KC][TILE]
+    uint4 *B = A + (size_t)K * 2 * KC * TILE;                                         // [NB][2][KC][NWIN]
+    float *strip = reinterpret_cast<float *>(B + (size_t)NB * 2 * KC * NWIN);         // [STRIP][NMATH]
+    float *aq_s = strip + STRIP * NMATH;                                              // [NGRP][TILE]
+    float2 *ls_s = reinterpret_cast<float2 *>(aq_s + NGRP * TILE);                     // [NGRP][TILE]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t ntiles = (N + TILE - 1) / TILE;
+
+    for (int i = tid; i < K * P; i += NTHREADS) uvs[i] = UV[i];
+    if (warp == MMA_WARP) tmem_alloc(&sm.tmem_base, TMEM_COLS);
+    if (tid == 0) {
+        for (int b = 0; b < NBMAX; b++) {
+            mbar_init(&sm.bfull[b], 1);
+            mbar_init(&sm.bempty[b], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&sm.tfull[b], 1);
+            mbar_init(&sm.tempty[b], NMATH);
+        }
+        mbar_init(&sm.yready, NMATH);
+        mbar_init(&sm.aready, NMATH);
+        mbar_init(&sm.tdone, NMATH);
+        mbar_init_fence();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = sm.tmem_base;
+    bool failed = false;
+
+    if (warp == COPY_WARP) {
+        // ------------------------------------------------------------------ copy warp
+        if (lane == 0) {
+            uint32_t gcopy = 0, tiles_done = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, tiles_done++) {
+                if (!wait1(&sm.aready, tiles_done & 1u, flags)) {
+                    failed = true;
+                    break;
+                }
+                Det4 lo, hi;
+                tile_range(sm.wlo, sm.whi, K, lo, hi);
+                for (JobIter cit(Nt, K, lo, hi); !cit.done && !failed; cit.next(), gcopy++) {
+                    const uint32_t bb = gcopy % NB;
+                    // the slot is free once the MMAs of job gcopy - NB have completed
+                    if (gcopy >= (uint32_t)NB && !wait1(&sm.bempty[bb], ((gcopy / NB) - 1) & 1u, flags)) {
+                        failed = true;
+                        break;
+                    }
+                    const Job j = cit.get();
+                    // one contiguous block per hi/lo: [nwr/8 groups][KC][8 columns] x 16 bytes
+                    const uint32_t bytes = (uint32_t)j.nwr * KC * 16u;
+                    mbar_arrive_expect_tx(&sm.bfull[bb], 2u * bytes);
+                    const int64_t src = (((int64_t)j.k * (TP / 8) + j.wbeg8 / 8) * KC) * 8;
+                    bulk_g2s(B + (size_t)(bb * 2) * KC * NWIN, Qhi + src, bytes, &sm.bfull[bb]);
+                    bulk_g2s(B + (size_t)(bb * 2 + 1) * KC * NWIN, Qlo + src, bytes, &sm.bfull[bb]);
+                }
+            }
+            if (failed) atomicOr(flags, ILE_FLAG_TIMEOUT);
+        }
+        __syncwarp();
+    } else if (warp == MMA_WARP) {
+        // ------------------------------------------------------------------ MMA warp
+        if (lane == 0) {
+            uint32_t gjob = 0, tiles_done = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, tiles_done++) {
+                if (!wait1(&sm.aready, tiles_done & 1u, flags)) {
+                    failed = true;
+                    break;
+                }
+                Det4 lo, hi;
+                tile_range(sm.wlo, sm.whi, K, lo, hi);
+                fence_after();
+                for (JobIter mit(Nt, K, lo, hi); !mit.done && !failed; mit.next(), gjob++) {
+                    const Job j = mit.get();
+                    const uint32_t bb = gjob % NB, tb = gjob & 1u;
+                    if (!wait1(&sm.bfull[bb], (gjob / NB) & 1u, flags) ||
+                        (gjob >= 2 && !wait1(&sm.tempty[tb], ((gjob / 2) - 1) & 1u, flags))) {
+                        failed = true;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t id = idesc(1, TILE, j.nwr);
+                    const uint32_t a_hi = smem_u32(A + (size_t)(j.k * 2 + 0) * KC * TILE);
+                    const uint32_t a_lo = smem_u32(A + (size_t)(j.k * 2 + 1) * KC * TILE);
+                    const uint32_t b_hi = smem_u32(B + (size_t)bb * 2 * KC * NWIN);
+                    const uint32_t b_lo = smem_u32(B + (size_t)(bb * 2 + 1) * KC * NWIN);
+                    const uint32_t d = tmem + tb * NWIN;
+                    uint32_t acc = 0;
+                    for (int pass = 0; pass < 3; pass++) {
+                        const uint32_t ab = pass == 2 ? a_lo : a_hi;
+                        const uint32_t bs = pass == 1 ? b_lo : b_hi;
+                        for (int ks = 0; ks < KP / 16; ks++) {
+                            // A: [KC][TILE rows] chunks (LBO = TILE*16, SBO = 128);
+                            // B: [nwr/8][KC][8] chunks (LBO = 128, SBO = KC*128)
+                            mma_bf16(d, sdesc(ab + ks * 2 * TILE * 16, TILE * 16, 128),
+                                     sdesc(bs + ks * 2 * 128, 128, KC * 128), id, acc);
+                            acc = 1;
+                        }
+                    }
+                    mma_commit(&sm.bempty[bb]);
+                    mma_commit(&sm.tfull[tb]);
+                }
+            }
+            if (failed) atomicOr(flags, ILE_FLAG_TIMEOUT);
+            // no MMA may still be writing TMEM when it is released (bounded)
+            if (gjob > 0) mbar_wait_sleep(&sm.tfull[(gjob - 1) & 1u], ((gjob - 1) / 2) & 1u, flags, 0u, SLEEPS, SLEEP_NS);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------------ math warps
+        const int q4 = warp & 3, g = warp >> 2;
+        const int row = q4 * 32 + lane;            // sample row in the tile = TMEM lane
+        const uint32_t lane_addr = (uint32_t)(q4 * 32) << 16;
+        float *my_strip = strip + tid;             // my_strip[i * NMATH], conflict-free
+        uint32_t gjob = 0, tiles_done = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, tiles_done++) {
+            const int64_t p = tile * TILE + row;
+            const bool valid = p < N;
+            const int64_t src = perm[valid ? p : tile * TILE];
+            // ---- S1/S2: geometry, harmonics, coefficients
+            double th[ILE_NDIM];
+            bool finite = true;
+#pragma unroll
+            for (int d = 0; d < ILE_NDIM; d++) {
+                th[d] = samples[(int64_t)d * N + src];
+                finite = finite && isfinite(th[d]);
+            }
+            if (!finite || th[5] <= 0.0) {
+                if (valid && g == 0) atomicOr(flags, ILE_FLAG_NONFINITE);
+                th[0] = th[1] = th[2] = th[3] = th[4] = th[6] = 0.0;
+                th[5] = 1.0;
+            }
+            const float scale = pp.d_ref / (float)th[5];
+            float Fr[ILE_MAX_DET], Fi[ILE_MAX_DET], x0[ILE_MAX_DET];
+            ile_sample_geometry(pp, (float)th[0], (float)th[1], (float)th[2], (float)th[6], Fr, Fi, x0);
+            int i0[ILE_MAX_DET];
+            float wt[ILE_MAX_DET];
+            bool in_range = true;
+#pragma unroll
+            for (int k = 0; k < ILE_MAX_DET; k++) {
+                const float fl = floorf(x0[k]);
+                in_range = in_range && (k >= K || (fl >= 0.f && fl + (float)Nt <= (float)(pp.T_ext - 1)));
+                i0[k] = (int)fl;
+                wt[k] = x0[k] - fl;
+            }
+            if (!in_range) {
+                if (valid && g == 0) atomicOr(flags, ILE_FLAG_RANGE);
+#pragma unroll
+                for (int k = 0; k < ILE_MAX_DET; k++) {
+                    i0[k] = 0;
+                    wt[k] = 0.f;
+                }
+            }
+            // harmonics: thread g forms modes a = g, g + 4, ... into the shared y table (which
+            // reuses the epilogue strips: every thread has passed the previous tile's tdone)
+            float2 *ys = reinterpret_cast<float2 *>(strip);  // [M][TILE]
+            {
+                float cpow[9], spow[9];
+                ile_half_angle_powers((float)th[3], cpow, spow);
+#pragma unroll 1
+                for (int a = g; a < M; a += NGRP) {
+                    float yr, yi;
+                    ile_sylm(pp.mode[a], cpow, spow, (float)th[4], yr, yi);
+                    ys[a * TILE + row] = make_float2(yr, yi);
+                }
+            }
+            mbar_arrive(&sm.yready);
+            if (!warp_wait(&sm.yready, tiles_done & 1u, flags)) {
+                failed = true;
+                break;
+            }
+            if (g < K) {
+                // A operand of detector g: operand index r = 2a + {0: Re, 1: Im}
+                const float fr = scale * (g == 0 ? Fr[0] : g == 1 ? Fr[1] : g == 2 ? Fr[2] : Fr[3]);
+                const float fi = scale * (g == 0 ? Fi[0] : g == 1 ? Fi[1] : g == 2 ? Fi[2] : Fi[3]);
+                uint4 *Ah = A + (size_t)(g * 2) * KC * TILE + row;
+                uint4 *Al = A + (size_t)(g * 2 + 1) * KC * TILE + row;
+#pragma unroll 1
+                for (int kc = 0; kc < KC; kc++) {
+                    float cv[8];
+#pragma unroll
+                    for (int e = 0; e < 8; e += 2) {
+                        const int a = 4 * kc + e / 2;
+                        const float2 y = a < M ? ys[a * TILE + row] : make_float2(0.f, 0.f);
+                        cv[e] = fr * y.x - fi * y.y;
+                        cv[e + 1] = fr * y.y + fi * y.x;
+                    }
+                    uint4 h, l;
+                    pack_chunk<true>(cv, h, l);
+                    Ah[kc * TILE] = h;
+                    Al[kc * TILE] = l;
+                }
+            }
+            // ---- S4: this thread's share of the upper-triangle mode pairs (pair index = g mod 4)
+            float au[ILE_MAX_DET] = {0.f, 0.f, 0.f, 0.f}, avr[ILE_MAX_DET] = {0.f, 0.f, 0.f, 0.f},
+                  avi[ILE_MAX_DET] = {0.f, 0.f, 0.f, 0.f};
+            {
+                int pbase = 0;
+#pragma unroll 1
+                for (int a = 0; a < M; a++) {
+                    const float2 ya = ys[a * TILE + row];
+                    // pairs (a, b), b = a .. M-1, have indices pbase + (b - a)
+                    const int first = a + ((g - pbase) & 3);
+#pragma unroll 1
+                    for (int b = first; b < M; b += NGRP) {
+                        const float2 yb = ys[b * TILE + row];
+                        const int pidx = pbase + (b - a);
+                        const float qr = ya.x * yb.x + ya.y * yb.y, qi = ya.x * yb.y - ya.y * yb.x;
+                        const float pr = ya.x * yb.x - ya.y * yb.y, pi = ya.x * yb.y + ya.y * yb.x;
+#pragma unroll
+                        for (int k = 0; k < ILE_MAX_DET; k++) {
+                            if (k < K) {
+                                const float4 u = uvs[k * P + pidx];
+                                au[k] += u.x * qr - u.y * qi;
+                                avr[k] += u.z * pr - u.w * pi;
+                                avi[k] += u.z * pi + u.w * pr;
+                            }
+                        }
+                    }
+                    pbase += M - a;
+                }
+            }
+            float aq = 0.f;
+#pragma unroll
+            for (int k = 0; k < ILE_MAX_DET; k++) {
+                if (k < K) {
+                    const float f2 = Fr[k] * Fr[k] + Fi[k] * Fi[k];
+                    const float g_r = Fr[k] * Fr[k] - Fi[k] * Fi[k], g_i = 2.f * Fr[k] * Fi[k];
+                    aq += f2 * au[k] + (g_r * avr[k] - g_i * avi[k]);
+                }
+            }
+            aq_s[g * TILE + row] = 0.25f * scale * scale * aq;
+            // ---- tile column range per detector (invalid rows repeat row 0's sample)
+            if (g == 0) {
+#pragma unroll
+                for (int k = 0; k < ILE_MAX_DET; k++) {
+                    if (k < K) {
+                        int l = i0[k], h = i0[k];
+                        for (int o = 16; o; o >>= 1) {
+                            l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
+                            h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
+                        }
+                        if (lane == 0) {
+                            sm.wlo[q4][k] = l;
+                            sm.whi[q4][k] = h;
+                        }
+                    }
+                }
+            }
+            fence_async_smem();
+            mbar_arrive(&sm.aready);  // A operand, column ranges and quadratic partials are written
+            if (!warp_wait(&sm.aready, tiles_done & 1u, flags)) {
+                failed = true;
+                break;
+            }
+            Det4 lo, hi;
+            tile_range(sm.wlo, sm.whi, K, lo, hi);
+            const Det4 i0d{i0[0], i0[1], i0[2], i0[3]};
+            const Det4f wtd{wt[0], wt[1], wt[2], wt[3]};
+
+            // ---- S3/S5: consume the jobs
+            float D[JG];
+#pragma unroll
+            for (int jj = 0; jj < JG; jj++) D[jj] = 0.f;
+            float m_run = -INFINITY, s_run = 0.f;
+            JobIter it(Nt, K, lo, hi);
+            while (!it.done) {
+                const Job j = it.get();
+                const uint32_t tb = gjob & 1u;
+                if (!warp_wait(&sm.tfull[tb], (gjob / 2) & 1u, flags)) {
+                    failed = true;
+                    break;
+                }
+                fence_after();
+                const int dk = i0d(j.k) - lo(j.k);  // first column of bin 0, relative to the chunk's range
+                const int wsel = j.W == 1 ? 0 : min(dk / j.step, j.W - 1);
+                const int jbeg = g * JG;             // my first bin of the chunk
+                const bool mine = wsel == j.w && jbeg < j.Jc;
+                const int s0 = dk - j.w * j.step + jbeg + (j.wbeg - j.wbeg8);  // my first column in the window
+                int cmin = mine ? s0 : 0x7fffffff, cmax = mine ? s0 + JG : -1;
+                for (int o = 16; o; o >>= 1) {
+                    cmin = min(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+                    cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+                }
+                if (cmax >= 0) {
+                    const uint32_t taddr = tmem + tb * NWIN + lane_addr;
+                    for (int cb = cmin & ~31; cb <= cmax; cb += 32) {
+                        uint32_t r[32];
+                        tmem_ld32(taddr + (uint32_t)cb, r);
+                        if (mine) {
+#pragma unroll
+                            for (int qq = 0; qq < 32; qq++) {
+                                const int idx = cb + qq - s0;
+                                if (idx >= 0 && idx < STRIP) my_strip[idx * NMATH] = __uint_as_float(r[qq]);
+                            }
+                        }
+                    }
+                }
+                fence_before();
+                mbar_arrive(&sm.tempty[tb]);
+                if (mine) {
+                    const float w = wtd(j.k), omw = 1.f - w;
+                    float vprev = my_strip[0];
+#pragma unroll
+                    for (int jj = 0; jj < JG; jj++) {
+                        if (jbeg + jj < j.Jc) {
+                            const float v = my_strip[(jj + 1) * NMATH];
+                            D[jj] += fmaf(w, v, omw * vprev);
+                            vprev = v;
+                        }
+                    }
+                }
+                gjob++;
+                it.next();
+                if (j.k == K - 1 && j.w == j.W - 1) {
+                    // chunk complete: S5 log-sum-exp update (or the full grid)
+                    if (full_grid) {
+                        if (valid) {
+                            const double A_n = (double)(aq_s[row] + aq_s[TILE + row] + aq_s[2 * TILE + row] +
+                                                        aq_s[3 * TILE + row]);
+                            const int64_t o = (int64_t)perm[p] * Nt + j.j0 + jbeg;
+#pragma unroll
+                            for (int jj = 0; jj < JG; jj++)
+                                if (jbeg + jj < j.Jc) out[o + jj] = (double)D[jj] - A_n;
+                        }
+                    } else if (jbeg < j.Jc) {
+                        float mc = -INFINITY;
+#pragma unroll
+                        for (int jj = 0; jj < JG; jj++)
+                            if (jbeg + jj < j.Jc) mc = fmaxf(mc, D[jj]);
+                        if (mc > m_run) {
+                            s_run *= __expf(m_run - mc);
+                            m_run = mc;
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < JG; jj++)
+                            if (jbeg + jj < j.Jc) s_run += __expf(D[jj] - m_run);
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < JG; jj++) D[jj] = 0.f;
+                }
+            }
+            if (failed) break;
+            // ---- merge the four threads' partial log-sum-exps
+            ls_s[g * TILE + row] = make_float2(m_run, s_run);
+            mbar_arrive(&sm.tdone);
+            if (!warp_wait(&sm.tdone, tiles_done & 1u, flags)) {
+                failed = true;
+                break;
+            }
+            if (g == 0 && valid && !full_grid) {
+                float m = -INFINITY;
+#pragma unroll
+                for (int h = 0; h < NGRP; h++) m = fmaxf(m, ls_s[h * TILE + row].x);
+                float ssum = 0.f;
+#pragma unroll
+                for (int h = 0; h < NGRP; h++) {
+                    const float2 v = ls_s[h * TILE + row];
+                    if (v.y > 0.f) ssum += v.y * __expf(v.x - m);
+                }
+                const double A_n =
+                    (double)(aq_s[row] + aq_s[TILE + row] + aq_s[2 * TILE + row] + aq_s[3 * TILE + row]);
+                out[perm[p]] = (double)m + (double)logf(ssum) - A_n - (double)pp.log_nt;
+            }
+        }
+        if (failed) atomicOr(flags, ILE_FLAG_TIMEOUT);
+    }
+
+    fence_before();
+    __syncthreads();
+    if (warp == MMA_WARP) {
+        fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+size_t tc2_smem(int K, int M, int KP, int NB) {
+    const int KC = KP / 8, P = M * (M + 1) / 2;
+    return (size_t)16 * ((K * P + 63) / 64 * 64) + (size_t)16 * K * 2 * KC * TILE + (size_t)16 * NB * 2 * KC * NWIN +
+           sizeof(float) * STRIP * NMATH + sizeof(float) * NGRP * TILE + sizeof(float2) * NGRP * TILE;
+}
+
+}  // namespace
+
+cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo, int TP, int KP, const float *UV,
+                           const double *samples, const int *perm, int64_t N, double *out, int full_grid,
+                           unsigned *flags, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    const size_t limit = 227 * 1024 - sizeof(Sm) - 64;
+    int NB = NBMAX;
+    while (NB > 2 && tc2_smem(pp.K, pp.M, KP, NB) > limit) NB--;
+    const size_t smem = tc2_smem(pp.K, pp.M, KP, NB);
+    if (smem > limit) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(ile_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ntiles = (N + TILE - 1) / TILE;
+    const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
+    ile_tc2_kernel<<<grid, NTHREADS, smem, st>>>(pp, (const uint4 *)hi, (const uint4 *)lo, TP, KP, NB,
+                                                 (const float4 *)UV, samples, perm, N, out, full_grid, flags);
+    return cudaGetLastError();
+}

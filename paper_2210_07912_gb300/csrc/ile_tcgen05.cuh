@@ -1,0 +1,189 @@
+// ile_tcgen05.cuh -- inline-PTX wrappers for the 5th-generation tensor cores of sm_103a
+// (tcgen05.mma / ld / alloc, tensor memory), mbarriers and bulk global->shared copies, plus the
+// hi/lo operand split of the split-precision contraction.
+//
+// Shared-memory matrix descriptor (no swizzle, K-major canonical layout): a core matrix is 8 rows
+// x 16 bytes; the leading-dimension byte offset (LBO) is the distance between core matrices that
+// are adjacent along K, the stride-dimension byte offset (SBO) the distance between adjacent
+// 8-row groups.  Storing row n of 16-byte K-chunk kc at byte (kc * rows + n) * 16 gives
+// LBO = rows * 16 and SBO = 128.
+#pragma once
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace ile_tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// Instruction descriptor: D = F32, A = B = fmt (1 = BF16 for kind::f16, 2 = TF32 for kind::tf32),
+// both K-major, shape M x N.
+__device__ __forceinline__ uint32_t idesc(uint32_t fmt, int m, int n) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+// Arrive on `bar` once every tcgen05 operation this thread issued before has completed.
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// Generic-proxy shared-memory writes -> visible to the async proxy (tensor core, bulk copies).
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+// 32 consecutive 32-bit columns of this thread's TMEM lane (warp-collective), then wait.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// try_wait with a suspend-time hint: the thread sleeps (up to hint_ns) until the phase completes
+// instead of spinning, which keeps issue slots free for the warps doing the work.
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; gives up after `spins` tries or as soon as
+// the launch-wide abort bit is set in *flags.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const unsigned *flags, unsigned abort_bit,
+                                          int spins) {
+    for (int i = 0; i < spins; i++) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 1023) == 1023 && (*(volatile const unsigned *)flags & abort_bit)) return false;
+    }
+    return false;
+}
+
+// Bounded sleeping wait: at most `tries` suspensions of up to hint_ns each.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, uint32_t parity, const unsigned *flags,
+                                                unsigned abort_bit, int tries, uint32_t hint_ns) {
+    for (int i = 0; i < tries; i++) {
+        if (mbar_try_sleep(bar, parity, hint_ns)) return true;
+        if ((i & 15) == 15 && (*(volatile const unsigned *)flags & abort_bit)) return false;
+    }
+    return false;
+}
+
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from global to shared
+// memory, completing as transaction bytes on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// hi + lo split of one value (BF16 or TF32 bit patterns).
+template <bool BF16>
+__device__ __forceinline__ void split(float x, uint32_t &hi, uint32_t &lo) {
+    if constexpr (BF16) {
+        __nv_bfloat16 h = __float2bfloat16_rn(x);
+        __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+        hi = (uint32_t)__bfloat16_as_ushort(h);
+        lo = (uint32_t)__bfloat16_as_ushort(l);
+    } else {
+        hi = to_tf32(x);
+        lo = to_tf32(x - __uint_as_float(hi));
+    }
+}
+
+// Split and pack one 16-byte K-chunk (8 BF16 or 4 TF32 elements, element 0 at the lowest address).
+template <bool BF16>
+__device__ __forceinline__ void pack_chunk(const float *v, uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+    if constexpr (BF16) {
+#pragma unroll
+        for (int w = 0; w < 4; w++) {
+            uint32_t h0, l0, h1, l1;
+            split<true>(v[2 * w], h0, l0);
+            split<true>(v[2 * w + 1], h1, l1);
+            h[w] = h0 | (h1 << 16);
+            l[w] = l0 | (l1 << 16);
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < 4; w++) split<false>(v[w], h[w], l[w]);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+}  // namespace ile_tc

@@ -124,6 +124,57 @@ ile_status ile_eval(ile_ctx *ctx, const double *samples, int64_t N, double *out,
 ile_status ile_integrate(ile_ctx *ctx, const double *samples, const double *ln_prior, const double *ln_ps,
                          int64_t N, double *result, double *lnL_t_out, unsigned flags);
 
+/* ------------------------------------------------------------------ adaptive MC integrator */
+
+/*
+ * Adaptive-Cartesian integrator (Sec. "GPU-accelerated Monte Carlo integration"): every
+ * iteration draws n_per_iter samples on the device from the separable sampling prior
+ * p_s = prod_d p_{s,d}, evaluates lnL_t, accumulates the Monte Carlo sums of
+ * Eq. (eq:lnL:MonteCarlo) (pooled over iterations, each sample weighted with the p_s it was drawn
+ * from) and refits the 100-bin histogram of every adaptive dimension.
+ *   Sampling variables d = 0..6: ra, sin(dec), psi, cos(iota), phi, D (Mpc), t_c (s), on
+ *   [lo[d], hi[d]]; the prior is uniform in each, except D (prop. to D^2).  A fixed dimension is
+ *   drawn from its prior; an adaptive one (bit d of adapt_mask) from its histogram.
+ *   Random numbers: Philox4x32-10 with key = seed and counter (sample index, iteration, point_id,
+ *   block), so a run (or a resumed run) is reproducible bit for bit.
+ *   Histogram update: mass_b = (1 - eps) h_b / sum h + eps / 100, h_b the sum of the weights of
+ *   the iteration's samples in bin b; eps in (0, 1].
+ */
+typedef struct {
+    uint64_t seed;
+    uint32_t point_id;
+    int64_t n_per_iter;   /* samples per iteration, 1 .. 2^23 */
+    int n_iter;           /* iterations run by ile_adapt_run */
+    unsigned adapt_mask;  /* bit d: dimension d adaptive */
+    double eps;           /* histogram floor, (0, 1] */
+    double lo[ILE_NDIM], hi[ILE_NDIM];
+} ile_adapt_cfg;
+
+#define ILE_ADAPT_LOG 64
+typedef struct {
+    double ln_L, sigma_ln, n_eff, ess;   /* pooled estimate over every iteration so far */
+    double max_lnw, s1, s2, n_total;     /* pooled partial sums: S1 = sum e^{ln w - max}, S2 = sum e^{2(...)} */
+    int n_iter;                          /* iterations done (the Philox iteration counter) */
+    double iter_ln_L[ILE_ADAPT_LOG];     /* per-iteration ln L estimate (first 64 iterations) */
+    double iter_n_eff[ILE_ADAPT_LOG];    /* per-iteration n_eff */
+    uint64_t cdf[ILE_NDIM][ILE_NBINS + 1]; /* current integer cumulative tables (2^32 scale) */
+    double hist[ILE_NDIM][ILE_NBINS];    /* last iteration's weight histograms (relative to its max) */
+} ile_adapt_result;
+
+/* Set up the sampler on the current point (after ile_set_data).  resume = NULL starts from uniform
+ * tables and empty sums; otherwise the tables, sums and iteration counter of `resume` are loaded
+ * (checkpoint/resume). */
+ile_status ile_adapt_init(ile_ctx *ctx, const ile_adapt_cfg *cfg, const ile_adapt_result *resume);
+/* Queue n_iter iterations on the context stream (asynchronous). */
+ile_status ile_adapt_step(ile_ctx *ctx, int n_iter);
+/* Wait for the stream and read the integrator state. */
+ile_status ile_adapt_get(ile_ctx *ctx, ile_adapt_result *out);
+/* ile_adapt_init(cfg, NULL) + ile_adapt_step(cfg->n_iter) + ile_adapt_get. */
+ile_status ile_adapt_run(ile_ctx *ctx, const ile_adapt_cfg *cfg, ile_adapt_result *out);
+/* Copy the last iteration's samples to host memory (any pointer may be NULL):
+ * theta [7][N], ln p - ln p_s [N], bins [7][N] (255 for fixed dimensions), lnL_t [N]. */
+ile_status ile_adapt_last(ile_ctx *ctx, double *theta, double *lnw_prior, uint8_t *bins, double *lnL_t);
+
 /*
  * Stage timing (tracing aid): when enabled, every kernel launch of the context is bracketed by
  * CUDA events recorded on the context's stream.  ile_profile_read waits for the stream and

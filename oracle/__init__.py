@@ -219,3 +219,37 @@ def cdf_uniform():
     cdf = np.zeros(NBINS + 1, dtype=np.uint64)
     _load().orc_cdf_uniform(_ptr(cdf))
     return cdf
+
+
+# ------------------------------------------------------------------------------------ S0-S6 loop
+def adapt_run(point, seed: int, N: int, n_iter: int, adapt_mask: int, eps: float, lo, hi, point_id: int = 0,
+              nthreads: int = 0, cdf0=None, iter0: int = 0):
+    """Adaptive-Cartesian integration in the order of Sec. "GPU-accelerated Monte Carlo integration":
+    for each iteration draw N samples from the separable sampling prior, evaluate lnL_t, accumulate
+    the Monte Carlo sums of Eq. (eq:lnL:MonteCarlo) (pooled over iterations, each sample weighted by
+    the p_s it was drawn from) and refit each adaptive dimension's 100-bin histogram.
+    Returns the pooled estimate, the per-iteration estimates, the final tables and the last
+    iteration's samples."""
+    adaptive = [(adapt_mask >> d) & 1 for d in range(NDIM)]
+    cdf = np.zeros((NDIM, NBINS + 1), np.uint64)
+    for d in range(NDIM):
+        cdf[d] = cdf_uniform() if cdf0 is None else cdf0[d]
+    lnw_all = []
+    iters = []
+    last = None
+    for it in range(iter0, iter0 + n_iter):
+        smp = make_sampler(lo, hi, adaptive, cdf)
+        theta, lwp, bins = sample(smp, seed, it, point_id, 0, N)
+        lnl = lnL_t(point, theta, nthreads)
+        lnw = lnl + lwp
+        st = mc_stats(lnw)
+        iters.append(st)
+        lnw_all.append(lnw)
+        hists = np.zeros((NDIM, NBINS))
+        for d in range(NDIM):
+            if adaptive[d]:
+                hists[d] = hist(lnw, bins[d])
+                cdf[d] = cdf_from_hist(hists[d], eps)
+        last = dict(theta=theta, lnw_prior=lwp, bins=bins, lnL=lnl, hist=hists)
+    pooled = mc_stats(np.concatenate(lnw_all))
+    return dict(pooled=pooled, iters=iters, cdf=cdf, last=last)

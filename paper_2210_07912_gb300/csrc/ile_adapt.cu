@@ -1,0 +1,258 @@
+// ile_adapt.cu -- the adaptive-Cartesian Monte Carlo integrator on the device: sample generation
+// (S0) and the weighted histograms that adapt the sampling prior (S6), Sec. "GPU-accelerated
+// Monte Carlo integration".
+//
+// The sampling prior is separable, p_s = prod_d p_{s,d}.  Each dimension d has a sampling
+// variable u_d on [lo_d, hi_d] (ra, sin dec, psi, cos iota, phi, D, t_c).  A fixed dimension is
+// drawn from its prior (uniform, or prop. to D^2 for the distance); an adaptive one from a 100-bin
+// piecewise-uniform density given by an integer cumulative table cdf[0..100] (cdf[0] = 0,
+// cdf[100] = 2^32): the bin is the largest b with cdf[b] <= a for a 32-bit uniform word a, the
+// position inside the bin comes from a second word.  Words: Philox4x32-10 (Salmon et al., SC'11)
+// keyed by the seed, counter (sample, iteration, point, block).  Because the bin choice is an
+// integer comparison, it is reproduced bit for bit by any implementation of the same definition.
+//
+// After the likelihood, each adaptive dimension's histogram h_b = sum_{n in b} w_n / sum w
+// (w_n = exp(ln w_n - max ln w) <= 1) is accumulated as 2^-40 fixed-point integers (exact and
+// independent of the order of the atomics, so a run is reproducible bit for bit); the next table
+// is mass_b = (1 - eps) h_b + eps / 100, accumulated left to right in FP64 (explicit
+// round-to-nearest operations, no contraction) and cut to cdf[b] = floor(2^32 sum_{b' < b} mass_b').
+#include <stdint.h>
+
+#include "ile_internal.cuh"
+
+namespace {
+
+constexpr int NB = ILE_NBINS;
+constexpr int ND = ILE_NDIM;
+constexpr int HIST_THREADS = 256;
+constexpr int HIST_CHUNK = 8192;
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                              uint32_t k1, uint32_t out[4]) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+// Uniform in (0, 1) from the top 23 bits of a word (exact in FP32).
+__device__ __forceinline__ float unit23(uint32_t w) { return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f); }
+
+__global__ void __launch_bounds__(256) sample_kernel(IleSamplerParams sp, const uint64_t *__restrict__ cdf,
+                                                     const float *__restrict__ lnps_tab,
+                                                     const int *__restrict__ iter_dev, int64_t N,
+                                                     double *__restrict__ theta, double *__restrict__ lnw_prior,
+                                                     uint8_t *__restrict__ bins) {
+    __shared__ uint32_t cdf_s[ND][NB + 1];  // low 32 bits; cdf[100] = 2^32 is never compared against
+    __shared__ float lnps_s[ND][NB];
+    for (int i = threadIdx.x; i < ND * (NB + 1); i += blockDim.x) {
+        const int d = i / (NB + 1), b = i % (NB + 1);
+        cdf_s[d][b] = (uint32_t)cdf[i];
+        if (b < NB) lnps_s[d][b] = lnps_tab[d * NB + b];
+    }
+    __syncthreads();
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const uint32_t iter = (uint32_t)(*iter_dev);
+    uint32_t wds[16];
+#pragma unroll
+    for (uint32_t blk = 0; blk < 4; blk++)
+        philox4x32_10((uint32_t)n, iter, sp.point, blk, sp.key0, sp.key1, wds + 4 * blk);
+    float lw = 0.f;
+#pragma unroll
+    for (int d = 0; d < ND; d++) {
+        const float lo = sp.lo[d], hi = sp.hi[d];
+        const uint32_t a = wds[2 * d], bw = wds[2 * d + 1];
+        float u;
+        int bin = 255;
+        if (sp.adapt_mask & (1u << d)) {
+            // largest b with cdf[b] <= a (cdf[0] = 0, strictly increasing until 2^32)
+            int b0 = 0, b1 = NB;  // invariant: cdf[b0] <= a < cdf[b1] (cdf[100] = 2^32 > a)
+            while (b1 - b0 > 1) {
+                const int mid = (b0 + b1) >> 1;
+                if (cdf_s[d][mid] <= a) b0 = mid; else b1 = mid;
+            }
+            bin = b0;
+            const float width = (hi - lo) * (1.0f / NB);
+            u = lo + ((float)bin + unit23(bw)) * width;
+            const float lnp = d == 5 ? logf(3.f * u * u / (hi * hi * hi - lo * lo * lo)) : -logf(hi - lo);
+            lw += lnp - lnps_s[d][bin];
+        } else {
+            const float v = unit23(a);
+            u = d == 5 ? cbrtf(lo * lo * lo + v * (hi * hi * hi - lo * lo * lo)) : lo + v * (hi - lo);
+        }
+        float phys = u;
+        if (d == 1) phys = asinf(fminf(fmaxf(u, -1.f), 1.f));
+        if (d == 3) phys = acosf(fminf(fmaxf(u, -1.f), 1.f));
+        theta[(int64_t)d * N + n] = (double)phys;
+        bins[(int64_t)d * N + n] = (uint8_t)bin;
+    }
+    lnw_prior[n] = (double)lw;
+}
+
+// Histograms of w_n = exp(ln w_n - max) over each adaptive dimension, as 2^-40 fixed point:
+// per-block shared-memory integer atomics, then one integer atomic per (d, b) and block.
+__global__ void __launch_bounds__(HIST_THREADS) hist_kernel(const double *__restrict__ lnL,
+                                                            const double *__restrict__ lnw_prior,
+                                                            const uint8_t *__restrict__ bins, int64_t N,
+                                                            const double *__restrict__ iter_res, unsigned mask,
+                                                            unsigned long long *__restrict__ hist_fx) {
+    __shared__ unsigned long long h[ND * NB];
+    for (int i = threadIdx.x; i < ND * NB; i += blockDim.x) h[i] = 0ull;
+    __syncthreads();
+    const double m = iter_res[4];  // max ln w of this iteration
+    const int64_t beg = (int64_t)blockIdx.x * HIST_CHUNK, end = min(N, beg + HIST_CHUNK);
+    for (int64_t n = beg + threadIdx.x; n < end; n += blockDim.x) {
+        const float w = __expf((float)(lnL[n] + lnw_prior[n] - m));
+        const unsigned long long wf = (unsigned long long)(w * 1099511627776.0f);  // w * 2^40
+#pragma unroll
+        for (int d = 0; d < ND; d++)
+            if (mask & (1u << d)) atomicAdd(&h[d * NB + bins[(int64_t)d * N + n]], wf);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ND * NB; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist_fx[i], h[i]);
+}
+
+// Next integer tables from the histogram, the ln p_s table, the pooled accumulators and the
+// iteration counter.  Threads d < ND build the tables of the adaptive dimensions (sequential
+// FP64 accumulation, bit-reproducible); all threads then fill ln p_s.
+__global__ void __launch_bounds__(1024) renorm_kernel(unsigned long long *__restrict__ hist_fx, unsigned mask,
+                                                      double eps, IleSamplerParams sp, double *__restrict__ hist,
+                                                      uint64_t *__restrict__ cdf, float *__restrict__ lnps_tab,
+                                                      const double *__restrict__ iter_res, int64_t N,
+                                                      double *__restrict__ pooled, double *__restrict__ iter_log,
+                                                      int *__restrict__ iter_dev, int update_tables) {
+    const int i = threadIdx.x;
+    for (int j = i; j < ND * NB; j += blockDim.x) {
+        hist[j] = (double)hist_fx[j] * (1.0 / 1099511627776.0);
+        hist_fx[j] = 0ull;  // ready for the next iteration
+    }
+    __syncthreads();
+    if (update_tables && i < ND && (mask & (1u << i))) {
+        const int d = i;
+        const double *h = hist + d * NB;
+        uint64_t *c = cdf + d * (NB + 1);
+        double tot = 0.0;
+        for (int b = 0; b < NB; b++) tot = __dadd_rn(tot, h[b]);
+        double acc = 0.0;
+        c[0] = 0;
+        for (int b = 0; b < NB; b++) {
+            const double mass =
+                __dadd_rn(__dmul_rn(__dsub_rn(1.0, eps), __ddiv_rn(h[b], tot)), __ddiv_rn(eps, (double)NB));
+            acc = __dadd_rn(acc, mass);
+            if (b + 1 < NB) {
+                double v = floor(__dmul_rn(acc, 4294967296.0));
+                if (v > 4294967296.0) v = 4294967296.0;
+                c[b + 1] = (uint64_t)v;
+            }
+        }
+        c[NB] = (uint64_t)1 << 32;
+        for (int b = 1; b <= NB; b++)
+            if (c[b] < c[b - 1]) c[b] = c[b - 1];
+    }
+    __syncthreads();
+    if (update_tables) {
+        for (int j = i; j < ND * NB; j += blockDim.x) {
+            const int d = j / NB, b = j % NB;
+            if (!(mask & (1u << d))) continue;
+            const uint64_t *c = cdf + d * (NB + 1);
+            const float width = (sp.hi[d] - sp.lo[d]) * (1.0f / NB);
+            lnps_tab[j] = logf((float)(c[b + 1] - c[b]) * (1.0f / 4294967296.0f)) - logf(width);
+        }
+    }
+    if (i != 0) return;
+    // pooled (m, S1, S2, n) over all iterations, each weighted with its own sampling prior
+    const double m_it = iter_res[4], s1_it = iter_res[5], s2_it = iter_res[6];
+    const double m_old = pooled[0];
+    const double m = fmax(m_old, m_it);
+    const double f_old = pooled[3] > 0 ? exp(m_old - m) : 0.0, f_it = exp(m_it - m);
+    pooled[1] = pooled[1] * f_old + s1_it * f_it;
+    pooled[2] = pooled[2] * f_old * f_old + s2_it * f_it * f_it;
+    pooled[0] = m;
+    pooled[3] += (double)N;
+    const int it = *iter_dev;
+    if (it >= 0 && it < ILE_ADAPT_LOG) {
+        iter_log[2 * it] = iter_res[0];
+        iter_log[2 * it + 1] = iter_res[2];
+    }
+    *iter_dev = it + 1;
+}
+
+// Uniform tables and the matching ln p_s for every dimension.
+__global__ void reset_kernel(IleSamplerParams sp, uint64_t *__restrict__ cdf, float *__restrict__ lnps_tab,
+                             double *__restrict__ pooled, int *__restrict__ iter_dev, int iter0) {
+    const int i = threadIdx.x;
+    for (int j = i; j < ND * (NB + 1); j += blockDim.x) {
+        const int b = j % (NB + 1);
+        cdf[j] = ((uint64_t)b << 32) / NB;
+    }
+    __syncthreads();
+    for (int j = i; j < ND * NB; j += blockDim.x) {
+        const int d = j / NB, b = j % NB;
+        const float width = (sp.hi[d] - sp.lo[d]) * (1.0f / NB);
+        const uint64_t *c = cdf + d * (NB + 1);
+        lnps_tab[j] = logf((float)(c[b + 1] - c[b]) * (1.0f / 4294967296.0f)) - logf(width);
+    }
+    if (i == 0) {
+        pooled[0] = -INFINITY;
+        pooled[1] = pooled[2] = pooled[3] = 0.0;
+        *iter_dev = iter0;
+    }
+}
+
+// Refresh ln p_s from externally supplied tables (resume).
+__global__ void lnps_kernel(IleSamplerParams sp, const uint64_t *__restrict__ cdf, float *__restrict__ lnps_tab) {
+    for (int j = threadIdx.x; j < ND * NB; j += blockDim.x) {
+        const int d = j / NB, b = j % NB;
+        const float width = (sp.hi[d] - sp.lo[d]) * (1.0f / NB);
+        const uint64_t *c = cdf + d * (NB + 1);
+        lnps_tab[j] = logf((float)(c[b + 1] - c[b]) * (1.0f / 4294967296.0f)) - logf(width);
+    }
+}
+
+}  // namespace
+
+int ile_hist_partial_count(int64_t N) { return (int)((N + HIST_CHUNK - 1) / HIST_CHUNK); }
+
+cudaError_t ile_launch_sampler_reset(const IleSamplerParams &sp, uint64_t *cdf, float *lnps_tab, double *pooled,
+                                     int *iter_dev, int iter0, cudaStream_t st) {
+    reset_kernel<<<1, 1024, 0, st>>>(sp, cdf, lnps_tab, pooled, iter_dev, iter0);
+    return cudaGetLastError();
+}
+
+cudaError_t ile_launch_lnps(const IleSamplerParams &sp, const uint64_t *cdf, float *lnps_tab, cudaStream_t st) {
+    lnps_kernel<<<1, 1024, 0, st>>>(sp, cdf, lnps_tab);
+    return cudaGetLastError();
+}
+
+cudaError_t ile_launch_sample(const IleSamplerParams &sp, const uint64_t *cdf, const float *lnps_tab,
+                              const int *iter_dev, int64_t N, double *theta, double *lnw_prior, uint8_t *bins,
+                              cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    sample_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(sp, cdf, lnps_tab, iter_dev, N, theta, lnw_prior, bins);
+    return cudaGetLastError();
+}
+
+cudaError_t ile_launch_adapt(const double *lnL, const double *lnw_prior, const uint8_t *bins, int64_t N,
+                             const double *iter_res, const IleSamplerParams &sp, double eps,
+                             unsigned long long *hist_fx, double *hist, uint64_t *cdf, float *lnps_tab, double *pooled,
+                             double *iter_log, int *iter_dev, int update_tables, cudaStream_t st) {
+    const int np = ile_hist_partial_count(N);
+    hist_kernel<<<np, HIST_THREADS, 0, st>>>(lnL, lnw_prior, bins, N, iter_res, sp.adapt_mask, hist_fx);
+    renorm_kernel<<<1, 1024, 0, st>>>(hist_fx, sp.adapt_mask, eps, sp, hist, cdf, lnps_tab, iter_res, N, pooled,
+                                      iter_log, iter_dev, update_tables);
+    return cudaGetLastError();
+}

@@ -35,6 +35,19 @@ struct ile_ctx {
     double *result = nullptr;  // [8]
     unsigned *flags = nullptr;
     char err[256] = {0};
+    // adaptive integrator state (ile_adapt.cu)
+    bool adapt_ready = false;
+    IleSamplerParams sp{};
+    double eps = 0.1;
+    int64_t adapt_N = 0;
+    uint64_t *a_cdf = nullptr;
+    float *a_lnps = nullptr;
+    double *a_hist = nullptr;
+    unsigned long long *a_hist_fx = nullptr;
+    double *a_pooled = nullptr, *a_iter_log = nullptr, *a_iter_res = nullptr, *a_lnwp = nullptr, *a_lnl = nullptr;
+    int *a_iter = nullptr;
+    uint8_t *a_bins = nullptr;
+    int64_t a_cap = 0;
     // stage timing
     bool profiling = false;
     std::vector<cudaEvent_t> ev[ILE_NSTAGE];
@@ -270,10 +283,13 @@ ile_status ile_create(ile_ctx **out, int device, void *cuda_stream, ile_prec pre
 ile_status ile_destroy(ile_ctx *ctx) {
     if (!ctx) return ILE_OK;
     DeviceGuard g(ctx->device);
-    void *bufs[] = {ctx->Qp,      ctx->UV,      ctx->Qtc[1][0], ctx->Qtc[1][1], ctx->Qtc[2][0], ctx->Qtc[2][1],
-                    ctx->s.C,     ctx->s.I0,    ctx->s.W,       ctx->s.A,       ctx->theta,     ctx->out,
-                    ctx->lnp,     ctx->lnps,    ctx->part,      ctx->result,    ctx->flags,     ctx->keys,
-                    ctx->buckets, ctx->perm};
+    void *bufs[] = {ctx->Qp,        ctx->UV,         ctx->Qtc[1][0], ctx->Qtc[1][1], ctx->Qtc[2][0],
+                    ctx->Qtc[2][1],    ctx->s.C,        ctx->s.I0,      ctx->s.W,       ctx->s.A,
+                    ctx->theta,        ctx->out,        ctx->lnp,       ctx->lnps,      ctx->part,
+                    ctx->result,       ctx->flags,      ctx->keys,      ctx->buckets,   ctx->perm,
+                    ctx->a_cdf,        ctx->a_lnps,     ctx->a_hist,    ctx->a_hist_fx, ctx->a_pooled,
+                    ctx->a_iter_log,   ctx->a_iter_res, ctx->a_lnwp,    ctx->a_lnl,     ctx->a_iter,
+                    ctx->a_bins};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (auto &v : ctx->ev)
@@ -425,6 +441,171 @@ ile_status ile_integrate(ile_ctx *ctx, const double *samples, const double *ln_p
     }
     CK(cudaMemcpyAsync(result, ctx->result, 7 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if (lnL_t_out) CK(cudaMemcpyAsync(lnL_t_out, ctx->out, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+    return read_flags(ctx);
+}
+
+static ile_status adapt_alloc(ile_ctx *ctx, int64_t N) {
+    if (!ctx->a_cdf) {
+        CK(cudaMalloc((void **)&ctx->a_cdf, sizeof(uint64_t) * ILE_NDIM * (ILE_NBINS + 1)));
+        CK(cudaMalloc((void **)&ctx->a_lnps, sizeof(float) * ILE_NDIM * ILE_NBINS));
+        CK(cudaMalloc((void **)&ctx->a_hist, sizeof(double) * ILE_NDIM * ILE_NBINS));
+        CK(cudaMalloc((void **)&ctx->a_hist_fx, sizeof(unsigned long long) * ILE_NDIM * ILE_NBINS));
+        CK(cudaMemset(ctx->a_hist_fx, 0, sizeof(unsigned long long) * ILE_NDIM * ILE_NBINS));
+        CK(cudaMemset(ctx->a_hist, 0, sizeof(double) * ILE_NDIM * ILE_NBINS));
+        CK(cudaMalloc((void **)&ctx->a_pooled, sizeof(double) * 4));
+        CK(cudaMalloc((void **)&ctx->a_iter_log, sizeof(double) * 2 * ILE_ADAPT_LOG));
+        CK(cudaMemset(ctx->a_iter_log, 0, sizeof(double) * 2 * ILE_ADAPT_LOG));
+        CK(cudaMalloc((void **)&ctx->a_iter_res, sizeof(double) * 8));
+        CK(cudaMalloc((void **)&ctx->a_iter, sizeof(int)));
+    }
+    if (N > ctx->a_cap) {
+        CK(grow(&ctx->a_lnwp, sizeof(double) * (size_t)N));
+        CK(grow(&ctx->a_lnl, sizeof(double) * (size_t)N));
+        CK(grow(&ctx->a_bins, (size_t)ILE_NDIM * (size_t)N));
+        ctx->a_cap = N;
+    }
+    ile_status st = ensure_samples(ctx, N);
+    if (st != ILE_OK) return st;
+    return ILE_OK;
+}
+
+ile_status ile_adapt_init(ile_ctx *ctx, const ile_adapt_cfg *cfg, const ile_adapt_result *resume) {
+    if (!ctx || !cfg) return ILE_E_ARG;
+    if (!ctx->has_data) return ILE_E_STATE;
+    if (cfg->n_per_iter < 1 || cfg->n_per_iter > ((int64_t)1 << 23)) return ILE_E_ARG;
+    if (!(cfg->eps > 0.0 && cfg->eps <= 1.0)) return ILE_E_ARG;
+    if (cfg->adapt_mask >> ILE_NDIM) return ILE_E_ARG;
+    for (int d = 0; d < ILE_NDIM; d++)
+        if (!(cfg->hi[d] > cfg->lo[d]) || !isfinite(cfg->lo[d]) || !isfinite(cfg->hi[d])) return ILE_E_ARG;
+    if (!(cfg->lo[5] > 0.0) || cfg->lo[1] < -1.0 || cfg->hi[1] > 1.0 || cfg->lo[3] < -1.0 || cfg->hi[3] > 1.0)
+        return ILE_E_ARG;
+    DeviceGuard g(ctx->device);
+    ile_status st = adapt_alloc(ctx, cfg->n_per_iter);
+    if (st != ILE_OK) return st;
+    IleSamplerParams sp{};
+    for (int d = 0; d < ILE_NDIM; d++) {
+        sp.lo[d] = (float)cfg->lo[d];
+        sp.hi[d] = (float)cfg->hi[d];
+    }
+    sp.adapt_mask = cfg->adapt_mask;
+    sp.key0 = (uint32_t)cfg->seed;
+    sp.key1 = (uint32_t)(cfg->seed >> 32);
+    sp.point = cfg->point_id;
+    ctx->sp = sp;
+    ctx->eps = cfg->eps;
+    ctx->adapt_N = cfg->n_per_iter;
+    CK(ile_launch_sampler_reset(sp, ctx->a_cdf, ctx->a_lnps, ctx->a_pooled, ctx->a_iter, 0, ctx->stream));
+    if (resume) {
+        if (resume->n_iter < 0) return ILE_E_ARG;
+        for (int d = 0; d < ILE_NDIM; d++) {
+            const uint64_t *c = resume->cdf[d];
+            if (c[0] != 0 || c[ILE_NBINS] != ((uint64_t)1 << 32)) return ILE_E_ARG;
+            for (int b = 0; b < ILE_NBINS; b++)
+                if (c[b + 1] <= c[b]) return ILE_E_ARG;
+        }
+        const double pooled[4] = {resume->max_lnw, resume->s1, resume->s2, resume->n_total};
+        CK(cudaMemcpyAsync(ctx->a_cdf, resume->cdf, sizeof(resume->cdf), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->a_pooled, pooled, sizeof pooled, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->a_iter, &resume->n_iter, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        double ilog[2 * ILE_ADAPT_LOG];
+        for (int i = 0; i < ILE_ADAPT_LOG; i++) {
+            ilog[2 * i] = resume->iter_ln_L[i];
+            ilog[2 * i + 1] = resume->iter_n_eff[i];
+        }
+        CK(cudaMemcpyAsync(ctx->a_iter_log, ilog, sizeof ilog, cudaMemcpyHostToDevice, ctx->stream));
+        CK(ile_launch_lnps(sp, ctx->a_cdf, ctx->a_lnps, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    ctx->adapt_ready = true;
+    return ILE_OK;
+}
+
+ile_status ile_adapt_step(ile_ctx *ctx, int n_iter) {
+    if (!ctx || n_iter < 0) return ILE_E_ARG;
+    if (!ctx->adapt_ready || !ctx->has_data) return ILE_E_STATE;
+    DeviceGuard g(ctx->device);
+    const int64_t N = ctx->adapt_N;
+    ile_status st = adapt_alloc(ctx, N);
+    if (st != ILE_OK) return st;
+    const int np = ile_mc_partial_count(N);
+    for (int it = 0; it < n_iter; it++) {
+        {
+            StageScope t(ctx, 0);
+            CK(ile_launch_sample(ctx->sp, ctx->a_cdf, ctx->a_lnps, ctx->a_iter, N, ctx->theta, ctx->a_lnwp,
+                                 ctx->a_bins, ctx->stream));
+        }
+        st = run_eval(ctx, ctx->theta, N, ctx->a_lnl, 0);
+        if (st != ILE_OK) return st;
+        {
+            StageScope t(ctx, 3, 2);
+            CK(ile_launch_mc(ctx->a_lnl, ctx->a_lnwp, nullptr, N, ctx->part, np, ctx->a_iter_res, ctx->stream));
+        }
+        {
+            StageScope t(ctx, 4, 2);
+            CK(ile_launch_adapt(ctx->a_lnl, ctx->a_lnwp, ctx->a_bins, N, ctx->a_iter_res, ctx->sp, ctx->eps,
+                                ctx->a_hist_fx, ctx->a_hist, ctx->a_cdf, ctx->a_lnps, ctx->a_pooled, ctx->a_iter_log,
+                                ctx->a_iter, 1, ctx->stream));
+        }
+    }
+    return ILE_OK;
+}
+
+ile_status ile_adapt_get(ile_ctx *ctx, ile_adapt_result *out) {
+    if (!ctx || !out) return ILE_E_ARG;
+    if (!ctx->adapt_ready) return ILE_E_STATE;
+    DeviceGuard g(ctx->device);
+    double pooled[4], ilog[2 * ILE_ADAPT_LOG];
+    int it = 0;
+    CK(cudaMemcpyAsync(pooled, ctx->a_pooled, sizeof pooled, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ilog, ctx->a_iter_log, sizeof ilog, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&it, ctx->a_iter, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(out->cdf, ctx->a_cdf, sizeof(out->cdf), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(out->hist, ctx->a_hist, sizeof(out->hist), cudaMemcpyDeviceToHost, ctx->stream));
+    ile_status st = read_flags(ctx);
+    out->max_lnw = pooled[0];
+    out->s1 = pooled[1];
+    out->s2 = pooled[2];
+    out->n_total = pooled[3];
+    out->n_iter = it;
+    for (int i = 0; i < ILE_ADAPT_LOG; i++) {
+        out->iter_ln_L[i] = ilog[2 * i];
+        out->iter_n_eff[i] = ilog[2 * i + 1];
+    }
+    const double Nd = pooled[3];
+    if (Nd > 0) {
+        const double mean = pooled[1] / Nd;
+        double var = (pooled[2] - Nd * mean * mean) / (Nd - 1.0);
+        if (var < 0.0) var = 0.0;
+        out->ln_L = pooled[0] + log(mean);
+        out->sigma_ln = Nd > 1 ? sqrt(var / Nd) / mean : INFINITY;
+        out->n_eff = pooled[1];
+        out->ess = pooled[1] * pooled[1] / pooled[2];
+    } else {
+        out->ln_L = -INFINITY;
+        out->sigma_ln = INFINITY;
+        out->n_eff = out->ess = 0.0;
+    }
+    return st;
+}
+
+ile_status ile_adapt_run(ile_ctx *ctx, const ile_adapt_cfg *cfg, ile_adapt_result *out) {
+    if (!cfg || !out || cfg->n_iter < 1) return ILE_E_ARG;
+    ile_status st = ile_adapt_init(ctx, cfg, nullptr);
+    if (st != ILE_OK) return st;
+    st = ile_adapt_step(ctx, cfg->n_iter);
+    if (st != ILE_OK) return st;
+    return ile_adapt_get(ctx, out);
+}
+
+ile_status ile_adapt_last(ile_ctx *ctx, double *theta, double *lnw_prior, uint8_t *bins, double *lnL_t) {
+    if (!ctx) return ILE_E_ARG;
+    if (!ctx->adapt_ready) return ILE_E_STATE;
+    DeviceGuard g(ctx->device);
+    const size_t N = (size_t)ctx->adapt_N;
+    if (theta) CK(cudaMemcpyAsync(theta, ctx->theta, sizeof(double) * ILE_NDIM * N, cudaMemcpyDeviceToHost, ctx->stream));
+    if (lnw_prior) CK(cudaMemcpyAsync(lnw_prior, ctx->a_lnwp, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+    if (bins) CK(cudaMemcpyAsync(bins, ctx->a_bins, ILE_NDIM * N, cudaMemcpyDeviceToHost, ctx->stream));
+    if (lnL_t) CK(cudaMemcpyAsync(lnL_t, ctx->a_lnl, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
     return read_flags(ctx);
 }
 

@@ -49,6 +49,15 @@ struct PointParams {
     ModeTab mode[ILE_MAX_MODES];
 };
 
+// Adaptive-Cartesian sampler configuration (ile_adapt.cu).
+#define ILE_ADAPT_LOG 64
+struct IleSamplerParams {
+    float lo[ILE_NDIM], hi[ILE_NDIM];  // range of each sampling variable
+    unsigned adapt_mask;               // bit d: dimension d is drawn from its histogram
+    uint32_t key0, key1;               // Philox key (seed)
+    uint32_t point;                    // Philox counter word identifying the intrinsic point
+};
+
 // Per-sample geometry: antenna factors and window placement of detector k.
 __device__ __forceinline__ void ile_sample_geometry(const PointParams &pp, float ra, float dec, float psi, float tc,
                                                     float Fr[ILE_MAX_DET], float Fi[ILE_MAX_DET],
@@ -131,3 +140,14 @@ cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo
 cudaError_t ile_launch_mc(const double *lnL_t, const double *ln_prior, const double *ln_ps, int64_t N,
                           double *partials, int n_part, double *result, cudaStream_t st);
 int ile_mc_partial_count(int64_t N);
+int ile_hist_partial_count(int64_t N);
+cudaError_t ile_launch_sampler_reset(const IleSamplerParams &sp, uint64_t *cdf, float *lnps_tab, double *pooled,
+                                     int *iter_dev, int iter0, cudaStream_t st);
+cudaError_t ile_launch_lnps(const IleSamplerParams &sp, const uint64_t *cdf, float *lnps_tab, cudaStream_t st);
+cudaError_t ile_launch_sample(const IleSamplerParams &sp, const uint64_t *cdf, const float *lnps_tab,
+                              const int *iter_dev, int64_t N, double *theta, double *lnw_prior, uint8_t *bins,
+                              cudaStream_t st);
+cudaError_t ile_launch_adapt(const double *lnL, const double *lnw_prior, const uint8_t *bins, int64_t N,
+                             const double *iter_res, const IleSamplerParams &sp, double eps,
+                             unsigned long long *hist_fx, double *hist, uint64_t *cdf, float *lnps_tab, double *pooled,
+                             double *iter_log, int *iter_dev, int update_tables, cudaStream_t st);

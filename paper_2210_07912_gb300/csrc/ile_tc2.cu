@@ -46,7 +46,6 @@ constexpr int NWIN = 128;                  // columns per TMEM accumulator buffe
 constexpr int NWCOL = 120;                 // window columns (+ up to 7 for 8-column alignment <= NWIN)
 constexpr uint32_t TMEM_COLS = 2 * NWIN;
 constexpr int NBMAX = 4;                   // B ring depth upper bound
-constexpr int SPINS = 1 << 20;
 constexpr int SLEEPS = 200000;             // bounded sleeping waits: SLEEPS x SLEEP_NS at most
 constexpr uint32_t SLEEP_NS = 10000;
 constexpr int STRIP = JG + 1;              // columns a thread keeps per job

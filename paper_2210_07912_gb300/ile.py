@@ -22,6 +22,45 @@ NDIM = 7
 NBINS = 100
 
 _lib = None
+ADAPT_LOG = 64
+
+
+class AdaptCfg(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("point_id", ctypes.c_uint32), ("n_per_iter", ctypes.c_int64),
+                ("n_iter", ctypes.c_int), ("adapt_mask", ctypes.c_uint), ("eps", ctypes.c_double),
+                ("lo", ctypes.c_double * NDIM), ("hi", ctypes.c_double * NDIM)]
+
+
+class AdaptResult(ctypes.Structure):
+    _fields_ = [("ln_L", ctypes.c_double), ("sigma_ln", ctypes.c_double), ("n_eff", ctypes.c_double),
+                ("ess", ctypes.c_double), ("max_lnw", ctypes.c_double), ("s1", ctypes.c_double),
+                ("s2", ctypes.c_double), ("n_total", ctypes.c_double), ("n_iter", ctypes.c_int),
+                ("iter_ln_L", ctypes.c_double * ADAPT_LOG), ("iter_n_eff", ctypes.c_double * ADAPT_LOG),
+                ("cdf", (ctypes.c_uint64 * (NBINS + 1)) * NDIM), ("hist", (ctypes.c_double * NBINS) * NDIM)]
+
+
+def default_ranges(fs: float = 4096.0, tc_max: float | None = None, d_min: float = 100.0, d_max: float = 1000.0):
+    """Sampling-variable ranges (ra, sin dec, psi, cos iota, phi, D, t_c) of the extrinsic prior."""
+    import math
+    if tc_max is None:
+        tc_max = 4.0 / fs
+    return ([0.0, -1.0, 0.0, -1.0, 0.0, d_min, -tc_max], [2 * math.pi, 1.0, math.pi, 1.0, 2 * math.pi, d_max, tc_max])
+
+
+def make_adapt_cfg(seed: int, n_per_iter: int, n_iter: int = 1, adapt_mask: int = 0b11, eps: float = 0.1,
+                   point_id: int = 0, lo=None, hi=None) -> AdaptCfg:
+    dlo, dhi = default_ranges()
+    lo = dlo if lo is None else lo
+    hi = dhi if hi is None else hi
+    return AdaptCfg(seed, point_id, n_per_iter, n_iter, adapt_mask, eps, (ctypes.c_double * NDIM)(*lo),
+                    (ctypes.c_double * NDIM)(*hi))
+
+
+def result_dict(r: AdaptResult) -> dict:
+    return dict(ln_L=r.ln_L, sigma_ln=r.sigma_ln, n_eff=r.n_eff, ess=r.ess, max_lnw=r.max_lnw, s1=r.s1, s2=r.s2,
+                n_total=r.n_total, n_iter=r.n_iter, iter_ln_L=np.array(r.iter_ln_L[:max(r.n_iter, 0)]),
+                iter_n_eff=np.array(r.iter_n_eff[:max(r.n_iter, 0)]),
+                cdf=np.ctypeslib.as_array(r.cdf).copy(), hist=np.ctypeslib.as_array(r.hist).copy())
 
 
 class IleError(RuntimeError):
@@ -64,8 +103,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ile_sync.argtypes = [vp]
     lib.ile_profile.argtypes = [vp, i32]
     lib.ile_profile_read.argtypes = [vp, vp, vp, i32]
+    lib.ile_adapt_init.argtypes = [vp, P(AdaptCfg), P(AdaptResult)]
+    lib.ile_adapt_step.argtypes = [vp, i32]
+    lib.ile_adapt_get.argtypes = [vp, P(AdaptResult)]
+    lib.ile_adapt_run.argtypes = [vp, P(AdaptCfg), P(AdaptResult)]
+    lib.ile_adapt_last.argtypes = [vp, vp, vp, vp, vp]
     for name in ("ile_create", "ile_destroy", "ile_set_stream", "ile_set_precision", "ile_set_data", "ile_eval",
-                 "ile_integrate", "ile_sync", "ile_profile", "ile_profile_read"):
+                 "ile_integrate", "ile_sync", "ile_profile", "ile_profile_read", "ile_adapt_init", "ile_adapt_step",
+                 "ile_adapt_get", "ile_adapt_run", "ile_adapt_last"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -180,6 +225,36 @@ class Context:
 
     def sync(self):
         self._check(self._lib.ile_sync(self._h), "ile_sync")
+
+    # ---------------------------------------------------------------- adaptive integrator
+    def adapt_init(self, cfg: AdaptCfg, resume: AdaptResult | None = None):
+        self._check(self._lib.ile_adapt_init(self._h, ctypes.byref(cfg), ctypes.byref(resume) if resume else None),
+                    "ile_adapt_init")
+        self.adapt_N = cfg.n_per_iter
+
+    def adapt_step(self, n_iter: int = 1):
+        self._check(self._lib.ile_adapt_step(self._h, n_iter), "ile_adapt_step")
+
+    def adapt_get(self, raw: bool = False):
+        r = AdaptResult()
+        self._check(self._lib.ile_adapt_get(self._h, ctypes.byref(r)), "ile_adapt_get")
+        return r if raw else result_dict(r)
+
+    def adapt_run(self, cfg: AdaptCfg, raw: bool = False):
+        r = AdaptResult()
+        self._check(self._lib.ile_adapt_run(self._h, ctypes.byref(cfg), ctypes.byref(r)), "ile_adapt_run")
+        self.adapt_N = cfg.n_per_iter
+        return r if raw else result_dict(r)
+
+    def adapt_last(self):
+        N = self.adapt_N
+        theta = np.zeros((NDIM, N))
+        lw = np.zeros(N)
+        bins = np.zeros((NDIM, N), np.uint8)
+        lnl = np.zeros(N)
+        self._check(self._lib.ile_adapt_last(self._h, _np_ptr(theta), _np_ptr(lw), _np_ptr(bins), _np_ptr(lnl)),
+                    "ile_adapt_last")
+        return theta, lw, bins, lnl
 
     # ---------------------------------------------------------------- stage timing
     STAGES = ("sample", "prep", "contract", "mc", "adapt")

@@ -1,11 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the ILE extrinsic-marginalisation hot path on GB300.
 
-One step = one pass of the hot path over one batch of 2^20 extrinsic samples of the
-three-detector (H1, L1, V1), 21-mode, 512-bin, 4096 Hz workload: geometry, mode coefficients,
-shifted contraction, quadratic term, time log-sum-exp and the Monte Carlo integral.  Inputs
-(seeded, synthetic) are resident in HBM when the timed region starts; the L2 cache is flushed
-(a 256 MiB write) between timed steps, outside the per-step CUDA events.
+One step = one iteration of the adaptive Monte Carlo integrator over 2^20 extrinsic samples of
+the three-detector (H1, L1, V1), 21-mode, 512-bin, 4096 Hz workload, every stage on the device:
+Philox sampling from the adaptive histograms (S0), geometry and mode coefficients (S1, S2), the
+shifted contraction (S3, split-precision BF16x3 tensor cores by default), the quadratic term
+(S4), the time log-sum-exp (S5), the Monte Carlo integral and the histogram refit (S6).  The
+intrinsic point's Q/U/V are resident in HBM when the timed region starts; the L2 cache is flushed
+(a 256 MiB write) between timed steps, outside the per-step CUDA events.  The plain FP32
+CUDA-core path is timed on the same workload for comparison.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on the host cores
 on a bounded sample of the same workload instead.
@@ -29,6 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "extrinsic lnL samples/s on 1 GB300, batched split-prec vs plain, |ΔlnL|≤1e-3"
 UNIT = "samples/s"
 CONFIG = 1  # 3 detectors, 21 modes, N_t = 512, 2^20 samples
+SEED_ADAPT = 2210079121  # Philox key of the benchmarked sampler
 
 
 def peaks():
@@ -89,6 +93,46 @@ class ClockSampler:
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()) if rows else None}
 
 
+# ------------------------------------------------------------------------------------ workload
+def workload_config(point, N, prec):
+    return {"workload": "ILE extrinsic marginalisation, one adaptive MC iteration: H1/L1/V1, 21 modes "
+                        "(l<=4), N_t=512 at 4096 Hz, 2^20 samples per step",
+            "n_det": point.n_det, "n_modes": point.n_modes, "n_window": point.n_window, "T_ext": point.T_ext,
+            "n_samples": N, "contraction": prec, "adaptive_dims": "ra, sin dec (100-bin histograms)",
+            "l2": "flushed between steps (256 MiB write)"}
+
+
+def oracle_step(point, N, it, seed=SEED_ADAPT, nthreads=0):
+    """One adaptive iteration in the FP64 oracle (sampling, lnL_t, MC sums, histogram refit) on N
+    samples; returns the elapsed wall time."""
+    import oracle
+    from paper_2210_07912_gb300 import ile
+    lo, hi = ile.default_ranges()
+    t = time.perf_counter()
+    oracle.adapt_run(point, seed, N, 1, 0b11, 0.1, lo, hi, point_id=0, nthreads=nthreads, iter0=it)
+    return time.perf_counter() - t
+
+
+
+def cpu_sample_size(point, seconds, cores):
+    from paper_2210_07912_gb300 import synthetic as S
+    import oracle
+    calib = S.config_samples(CONFIG, 512)
+    t = time.perf_counter()
+    oracle.lnL_t(point, calib, cores)
+    per = (time.perf_counter() - t) / 512
+    return int(max(512, min(1 << 20, seconds / per)))
+
+
+def cpu_baseline(point, seconds=12.0):
+    cores = os.cpu_count() or 1
+    n = cpu_sample_size(point, seconds, cores)
+    dt = oracle_step(point, n, 0, nthreads=cores)
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one adaptive iteration on {n} of the 2^20 samples (same seed and tables), FP64, "
+                      f"OpenMP over samples"}
+
+
 # ------------------------------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
     if rank != 0:
@@ -96,24 +140,14 @@ def run_reference(args, rank, world):
     import oracle
     from paper_2210_07912_gb300 import synthetic as S
     oracle.build()
-    point = S.config_point(CONFIG)
+    point = S.make_point(S.SEED_BASE + CONFIG, 3, 21, 512, spectrum="decay")
     cores = os.cpu_count() or 1
-    calib = S.config_samples(CONFIG, 256)
-    t = time.perf_counter()
-    oracle.lnL_t(point, calib, cores)
-    per = (time.perf_counter() - t) / 256
-    n_step = int(max(256, min(1 << 20, 1.5 / per)))
-    all_th = S.config_samples(CONFIG, n_step)
-    for _ in range(args.warmup):
-        oracle.mc_stats(oracle.lnL_t(point, all_th, cores))
-    times = []
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        oracle.mc_stats(oracle.lnL_t(point, all_th, cores))
-        times.append(time.perf_counter() - t)
-    tot = sum(times)
+    n_step = cpu_sample_size(point, 1.5, cores)
+    for w in range(args.warmup):
+        oracle_step(point, n_step, w, nthreads=cores)
+    tot = sum(oracle_step(point, n_step, args.warmup + i, nthreads=cores) for i in range(args.steps))
     value = n_step * args.steps / tot
-    sample = f"{n_step} of the 2^20 samples per step (FP64 oracle, OpenMP over samples)"
+    sample = f"{n_step} of the 2^20 samples per step (one adaptive iteration, FP64 oracle, OpenMP over samples)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -124,39 +158,38 @@ def run_reference(args, rank, world):
     return 0
 
 
-def workload_config(point, N, prec):
-    return {"workload": "ILE extrinsic marginalisation, H1/L1/V1, 21 modes (l<=4), N_t=512 at 4096 Hz, "
-                        "2^20 samples per step",
-            "n_det": point.n_det, "n_modes": point.n_modes, "n_window": point.n_window, "T_ext": point.T_ext,
-            "n_samples": N, "contraction": prec, "l2": "flushed between steps (256 MiB write)"}
-
-
-def cpu_baseline(point, seconds=12.0):
-    import oracle
-    from paper_2210_07912_gb300 import synthetic as S
-    cores = os.cpu_count() or 1
-    calib = S.config_samples(CONFIG, 256)
-    t = time.perf_counter()
-    oracle.lnL_t(point, calib, cores)
-    per = (time.perf_counter() - t) / 256
-    n = int(max(256, min(1 << 20, seconds / per)))
-    th = S.config_samples(CONFIG, n)
-    t = time.perf_counter()
-    oracle.mc_stats(oracle.lnL_t(point, th, cores))
-    dt = time.perf_counter() - t
-    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {n} of the 2^20 samples of the timed workload, lnL_t + MC integral, FP64"}
-
-
 # ------------------------------------------------------------------------------------ our arm
+def profile_traffic(kernel_file, prec):
+    """DRAM bytes per launch of the contraction kernel from the committed ncu summary, if it was
+    taken on the current source of that kernel (else None)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2210_07912_gb300", "csrc", kernel_file)
+    summ = os.path.join(ROOT, "profiles", f"contract_{prec}_c1.md")
+    if not (os.path.exists(src) and os.path.exists(summ)):
+        return None, None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(summ):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha256_16") != digest:
+        return None, digest
+    try:
+        return float(vals["dram_bytes_per_launch_full"]), digest
+    except (KeyError, ValueError):
+        return None, digest
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32x3", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--n-samples", type=int, default=None,
                     help="samples per step (default 2^20, the benchmarked workload; smaller only for profiling)")
     args = ap.parse_args()
@@ -178,100 +211,119 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     N = args.n_samples or S.CONFIGS[CONFIG]["n_samples"]
+    # replicas: every rank integrates its own intrinsic point
     point = S.make_point(S.SEED_BASE + CONFIG + 1000 * rank, 3, 21, 512, spectrum="decay")
-    th_host = S.prior_samples(np.random.default_rng([S.SEED_BASE + CONFIG, rank]), N)
     stream = torch.cuda.Stream()
-    ctx = ile.Context(local, stream, args.prec)
-    ctx.set_data(point)
-    d_th = torch.from_numpy(th_host).cuda()
-    d_res = torch.zeros(8, dtype=torch.float64, device="cuda")
-    d_lnl = torch.empty(N, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    torch.cuda.synchronize()
+    cfg = ile.make_adapt_cfg(seed=SEED_ADAPT + rank, n_per_iter=N, adapt_mask=0b11, point_id=rank)
 
-    def step():
-        ctx.integrate_device(d_th, d_res, lnL_out=d_lnl)
-
-    for _ in range(args.warmup):
-        step()
-    ctx.sync()
+    def timed(prec, steps, profile):
+        ctx = ile.Context(local, stream, prec)
+        ctx.set_data(point)
+        ctx.adapt_init(cfg)
+        ctx.adapt_step(args.warmup)
+        ctx.sync()
+        ctx.profile(profile)
+        if profile:
+            ctx.profile_read()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.time()
+        for i in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xFF)
+                evs[i][0].record(stream)
+            ctx.adapt_step(1)
+            with torch.cuda.stream(stream):
+                evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        t1 = time.time()
+        res = ctx.adapt_get()
+        prof = ctx.profile_read() if profile else None
+        ctx.profile(False)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        if dist:
+            tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms, prof, res, (t0, t1), ctx
 
     clocks = ClockSampler(local)
     time.sleep(0.6)
-    ctx.profile(True)
-    ctx.profile_read()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.time()
-    for i in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(i & 0xFF)
-            evs[i][0].record(stream)
-        step()
-        with torch.cuda.stream(stream):
-            evs[i][1].record(stream)
-    torch.cuda.synchronize()
-    t1 = time.time()
-    ctx.sync()
-    prof = ctx.profile_read()
-    ctx.profile(False)
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-        dist.barrier()
+    ms, prof, res, (t0, t1), ctx = timed(args.prec, args.steps, True)
     clk = clocks.summary(t0, t1)
     clocks.stop()
     value = N * args.steps * world / (ms / 1e3)
 
-    # e2e: the public host-pointer API, inputs copied from pinned host memory every step
-    pinned = torch.empty((7, N), dtype=torch.float64, pin_memory=True)
-    pinned.copy_(torch.from_numpy(th_host))
-    th_pinned = pinned.numpy()
-    ctx.integrate(th_pinned)
-    torch.cuda.synchronize()
+    plain = None
+    if not args.no_plain and args.prec != "fp32":
+        pms, _, _, _, pctx = timed("fp32", max(3, min(args.steps, 10)), False)
+        psteps = max(3, min(args.steps, 10))
+        plain = {"value": N * psteps * world / (pms / 1e3), "ms_per_step": pms / psteps, "contraction": "fp32"}
+        pctx.close()
+
+    # e2e: a user's full evaluation of one intrinsic point through the public API every step --
+    # upload the point (host arrays), set up the sampler, one iteration, read the result back
     e2e_steps = max(3, min(args.steps, 20))
+    ctx.set_data(point)
+    ctx.adapt_init(cfg)
+    ctx.adapt_step(1)
+    ctx.adapt_get(raw=True)
+    torch.cuda.synchronize()
     t = time.perf_counter()
     for _ in range(e2e_steps):
-        res = ctx.integrate(th_pinned)
+        ctx.set_data(point)
+        ctx.adapt_init(cfg)
+        ctx.adapt_step(1)
+        r = ctx.adapt_get(raw=True)
     e2e_s = time.perf_counter() - t
     if dist:
         tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
     e2e_value = N * e2e_steps * world / e2e_s
+    K, M, Nt, T = point.n_det, point.n_modes, point.n_window, point.T_ext
+    h2d = 8 * 2 * K * M * T + 8 * 2 * 2 * K * M * M + 8 * (12 * K) + 4 * 2 * M + 8 * 2 * 7 + 64
 
     if rank == 0:
         pk, pk_kind = peaks()
-        K, M, Nt = point.n_det, point.n_modes, point.n_window
         contract_ms, contract_n = prof["contract"]
-        per_launch_s = contract_ms / 1e3 / max(1, contract_n)  # one contraction kernel per step
-        alg_flops = 4.0 * M * Nt * K * N  # data term of the contraction per launch
+        per_launch_s = contract_ms / 1e3 / max(1, contract_n)
+        alg_flops = 4.0 * M * Nt * K * N  # data term of the contraction, per launch
         if args.prec == "fp32":
             sm_mhz = pk.get("sm_max_mhz", 2070.0)
-            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock
-            roof = {"bound": "alu", "achieved": alg_flops / per_launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "frac": alg_flops / per_launch_s / 1e12 / peak, "traffic": None,
-                    "kernel": "ile_plain_kernel (S3+S5)",
-                    "peak_kind": "FP32 CUDA-core FMA rate: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % sm_mhz}
+            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+            roof = {"bound": "alu", "kernel": "ile_plain_kernel (S3+S5)",
+                    "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % sm_mhz}
+            kfile = "ile_plain.cu"
         else:
             peak = pk["bf16_tflops"] * (0.5 if args.prec == "tf32x3" else 1.0)
-            roof = {"bound": "tensor", "achieved": alg_flops / per_launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "frac": alg_flops / per_launch_s / 1e12 / peak, "traffic": None}
-        launches = sum(c for (_, c) in prof.values())
+            roof = {"bound": "tensor",
+                    "kernel": "ile_tc2_kernel (S1-S5 fused)" if args.prec == "bf16x3" else "ile_tc_kernel (S3+S5)",
+                    "peak_kind": "measured dense bf16 (burst)" + (" x 1/2 for tf32" if args.prec == "tf32x3" else "")}
+            kfile = "ile_tc2.cu" if args.prec == "bf16x3" else "ile_tc.cu"
+        traffic, _ = profile_traffic(kfile, args.prec)
+        achieved = alg_flops / per_launch_s / 1e12
+        roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": traffic, "algorithmic_flops_per_launch": alg_flops,
+                     "launch_ms": per_launch_s * 1e3, "peak_source": pk_kind})
+        launches = sum(c for (_, c) in prof.values())  # kernels launched by the library in the timed steps
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(point, N, args.prec),
-                "roofline": {**roof, "peak_source": pk_kind},
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3" if args.prec == "bf16x3" else "f32",
+                "data": "synthetic", "config": workload_config(point, N, args.prec),
+                "roofline": roof,
                 "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 7 * 8 * N,
-                        "d2h_bytes_per_step": 7 * 8},
+                "plain_fp32": plain,
+                "speedup_vs_plain": (value / plain["value"]) if plain else None,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": 8 * 20 + 8 * 2 * 64 + 8 * 7 * 101 + 8 * 7 * 100,
+                        "what": "set_data (host arrays) + adapt_init + one iteration + result read-back"},
                 "gpu_launches": launches, "clocks": clk,
-                "result": {"ln_L_marg": res["ln_L"], "sigma_ln": res["sigma_ln"], "n_eff": res["n_eff"]}}
+                "result": {"ln_L_marg": res["ln_L"], "sigma_ln": res["sigma_ln"], "n_eff": res["n_eff"],
+                           "iterations": res["n_iter"]}}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(point)
         print(json.dumps(line), flush=True)

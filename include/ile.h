@@ -187,6 +187,30 @@ ile_status ile_adapt_last(ile_ctx *ctx, double *theta, double *lnw_prior, uint8_
 ile_status ile_profile(ile_ctx *ctx, int enable);
 ile_status ile_profile_read(ile_ctx *ctx, double *out_ms, int64_t *out_count, int n_stages);
 
+/*
+ * Allocation-free Monte Carlo reduction (the paper has no counterpart; this is a service for
+ * callers that cannot allocate device memory, e.g. code running inside another framework's
+ * memory pool, a CUDA-graph capture region or a pre-sized real-time service, where a cudaMalloc
+ * would synchronise the device or is not permitted).
+ *
+ * Computes the same result[7] as ile_integrate (ln L_marg, sigma_ln, n_eff, ess, max ln w, S1,
+ * S2) from per-sample values that are already on the device: ln w_n = lnL_t[n] + ln_prior[n] -
+ * ln_ps[n] (ln_prior / ln_ps may be NULL, meaning 0).  All pointers are device pointers on the
+ * current CUDA device; the work is queued on cuda_stream (a cudaStream_t; NULL = legacy default
+ * stream) and the call returns without waiting.  It needs no context and allocates nothing: its
+ * scratch (the per-block partial sums) is a fixed array inside the library, 24 KB on every
+ * device that loads the library, kept until the process exits.
+ *   N must be in [1, ILE_NOALLOC_MAX_SAMPLES]; larger N returns ILE_E_ARG (use ile_integrate).
+ *   The first call on each device looks up the array's device address (cudaGetSymbolAddress);
+ *   make that first call before capturing a stream into a CUDA graph.
+ *   Every call shares the one array: calls whose work overlaps on the GPU (on different streams,
+ *   or from different host threads without ordering) race and may return wrong results.
+ *   Returns ILE_E_CUDA if the device address cannot be obtained or a launch fails.
+ */
+#define ILE_NOALLOC_MAX_SAMPLES (1 << 22)
+ile_status ile_mc_reduce_noalloc(const double *lnL_t, const double *ln_prior, const double *ln_ps, int64_t N,
+                                 double *result, void *cuda_stream);
+
 /* Wait for the context's stream and return the first device-side error seen since the last call. */
 ile_status ile_sync(ile_ctx *ctx);
 

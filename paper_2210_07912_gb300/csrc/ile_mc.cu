@@ -100,3 +100,49 @@ cudaError_t ile_launch_mc(const double *lnL_t, const double *ln_prior, const dou
     mc_merge_kernel<<<1, MC_THREADS, 0, st>>>(partials, n_part, N, result);
     return cudaGetLastError();
 }
+
+// ------------------------------------------------------------------ allocation-free variant
+//
+// ile_mc_reduce_noalloc runs the same two kernels with their per-block partial sums in a
+// file-scope device array instead of context-owned memory, for callers that may not allocate
+// device memory (see include/ile.h).  The array lives as long as the library is loaded, on every
+// device that loads it.  Host code must not pass the symbol itself to a kernel (on the host it is
+// only a stand-in); its device address is looked up once per device with cudaGetSymbolAddress.
+#include <mutex>
+
+namespace {
+
+constexpr int NOALLOC_MAX_PART = ILE_NOALLOC_MAX_SAMPLES / MC_CHUNK;
+static_assert(ILE_NOALLOC_MAX_SAMPLES % MC_CHUNK == 0, "scratch sizing");
+
+static __device__ __align__(256) double g_noalloc_partials[3 * NOALLOC_MAX_PART];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+}  // namespace
+
+extern "C" ile_status ile_mc_reduce_noalloc(const double *lnL_t, const double *ln_prior, const double *ln_ps,
+                                            int64_t N, double *result, void *cuda_stream) {
+    if (!lnL_t || !result || N < 1) return ILE_E_ARG;
+    if (N > ILE_NOALLOC_MAX_SAMPLES) return ILE_E_ARG;  // the fixed scratch holds this many samples' partials
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return ILE_E_CUDA;
+    double *part = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return ILE_E_CUDA;
+            g_noalloc_ptr[dev] = static_cast<double *>(p);
+        }
+        part = g_noalloc_ptr[dev];
+    }
+    // every partial the merge reads is written by the partial kernel of the same call, so the
+    // shared array needs no clearing between calls
+    const int np = ile_mc_partial_count(N);
+    if (ile_launch_mc(lnL_t, ln_prior, ln_ps, N, part, np, result, (cudaStream_t)cuda_stream) != cudaSuccess)
+        return ILE_E_CUDA;
+    return ILE_OK;
+}

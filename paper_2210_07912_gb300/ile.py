@@ -108,6 +108,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ile_adapt_get.argtypes = [vp, P(AdaptResult)]
     lib.ile_adapt_run.argtypes = [vp, P(AdaptCfg), P(AdaptResult)]
     lib.ile_adapt_last.argtypes = [vp, vp, vp, vp, vp]
+    lib.ile_mc_reduce_noalloc.argtypes = [vp, vp, vp, i64, vp, vp]
+    lib.ile_mc_reduce_noalloc.restype = i32
     for name in ("ile_create", "ile_destroy", "ile_set_stream", "ile_set_precision", "ile_set_data", "ile_eval",
                  "ile_integrate", "ile_sync", "ile_profile", "ile_profile_read", "ile_adapt_init", "ile_adapt_step",
                  "ile_adapt_get", "ile_adapt_run", "ile_adapt_last"):
@@ -136,6 +138,25 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+NOALLOC_MAX_SAMPLES = 1 << 22
+
+
+def mc_reduce_noalloc(lnL_t, result, ln_prior=None, ln_ps=None, stream=None):
+    """Monte Carlo reduction of per-sample device values into result[7] without any device
+    allocation (for callers that cannot allocate; see include/ile.h).  All tensors are CUDA
+    float64 on the current device; N = lnL_t.numel() must not exceed NOALLOC_MAX_SAMPLES.
+    Queued on `stream` (torch stream or raw handle; None = legacy default stream)."""
+    lib = load()
+    N = lnL_t.numel()
+    if N > NOALLOC_MAX_SAMPLES:
+        raise IleError(ILE_E_ARG, "ile_mc_reduce_noalloc",
+                       f"N = {N} exceeds the fixed scratch of {NOALLOC_MAX_SAMPLES} samples")
+    st = lib.ile_mc_reduce_noalloc(_dev_ptr(lnL_t), _dev_ptr(ln_prior), _dev_ptr(ln_ps), N, _dev_ptr(result),
+                                   _stream_handle(stream))
+    if st != ILE_OK:
+        raise IleError(st, "ile_mc_reduce_noalloc")
 
 
 class Context:

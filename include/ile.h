@@ -211,6 +211,19 @@ ile_status ile_profile_read(ile_ctx *ctx, double *out_ms, int64_t *out_count, in
 ile_status ile_mc_reduce_noalloc(const double *lnL_t, const double *ln_prior, const double *ln_ps, int64_t N,
                                  double *result, void *cuda_stream);
 
+/*
+ * Merge per-shard Monte Carlo partial sums (host memory, no GPU needed).  The path shards over
+ * samples and over intrinsic points with one exchange: each shard s reports (max_s, S1_s, S2_s,
+ * n_s) with S1 = sum e^{ln w - max}, S2 = sum e^{2(ln w - max)} (result[4..6] of ile_integrate and
+ * the pooled fields of ile_adapt_result) and optionally its weight histograms hist_s[7][100]
+ * (relative to the same max).  Writes result[7] = {ln L_marg, sigma_ln, n_eff, ess, max, S1, S2}
+ * of the union of the shards, and (if hist_out is not NULL) the merged histograms relative to the
+ * merged max.  Shards with n_s = 0 are ignored; ILE_E_ARG if no shard has samples.
+ */
+ile_status ile_merge_partials(int n_shards, const double *max_lnw, const double *s1, const double *s2,
+                              const double *n, const double *hist /* [n_shards][7][100] or NULL */,
+                              double *result, double *hist_out /* [7][100] or NULL */);
+
 /* Wait for the context's stream and return the first device-side error seen since the last call. */
 ile_status ile_sync(ile_ctx *ctx);
 

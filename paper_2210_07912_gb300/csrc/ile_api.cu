@@ -609,6 +609,42 @@ ile_status ile_adapt_last(ile_ctx *ctx, double *theta, double *lnw_prior, uint8_
     return read_flags(ctx);
 }
 
+ile_status ile_merge_partials(int n_shards, const double *max_lnw, const double *s1, const double *s2,
+                              const double *n, const double *hist, double *result, double *hist_out) {
+    if (n_shards < 1 || !max_lnw || !s1 || !s2 || !n || !result) return ILE_E_ARG;
+    double m = -INFINITY, N = 0.0;
+    for (int i = 0; i < n_shards; i++) {
+        if (!(n[i] >= 0.0)) return ILE_E_ARG;
+        if (n[i] > 0.0) {
+            m = fmax(m, max_lnw[i]);
+            N += n[i];
+        }
+    }
+    if (!(N > 0.0) || !isfinite(m)) return ILE_E_ARG;
+    double S1 = 0.0, S2 = 0.0;
+    if (hist_out)
+        for (int j = 0; j < ILE_NDIM * ILE_NBINS; j++) hist_out[j] = 0.0;
+    for (int i = 0; i < n_shards; i++) {
+        if (n[i] <= 0.0) continue;
+        const double f = exp(max_lnw[i] - m);
+        S1 += s1[i] * f;
+        S2 += s2[i] * f * f;
+        if (hist && hist_out)
+            for (int j = 0; j < ILE_NDIM * ILE_NBINS; j++) hist_out[j] += hist[(size_t)i * ILE_NDIM * ILE_NBINS + j] * f;
+    }
+    const double mean = S1 / N;
+    double var = (S2 - N * mean * mean) / (N - 1.0);
+    if (var < 0.0) var = 0.0;
+    result[0] = m + log(mean);
+    result[1] = N > 1 ? sqrt(var / N) / mean : INFINITY;
+    result[2] = S1;
+    result[3] = S1 * S1 / S2;
+    result[4] = m;
+    result[5] = S1;
+    result[6] = S2;
+    return ILE_OK;
+}
+
 ile_status ile_profile(ile_ctx *ctx, int enable) {
     if (!ctx) return ILE_E_ARG;
     ctx->profiling = enable != 0;

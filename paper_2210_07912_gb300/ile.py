@@ -108,6 +108,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ile_adapt_get.argtypes = [vp, P(AdaptResult)]
     lib.ile_adapt_run.argtypes = [vp, P(AdaptCfg), P(AdaptResult)]
     lib.ile_adapt_last.argtypes = [vp, vp, vp, vp, vp]
+    lib.ile_merge_partials.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp]
+    lib.ile_merge_partials.restype = i32
     lib.ile_mc_reduce_noalloc.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ile_mc_reduce_noalloc.restype = i32
     for name in ("ile_create", "ile_destroy", "ile_set_stream", "ile_set_precision", "ile_set_data", "ile_eval",
@@ -141,6 +143,24 @@ def _stream_handle(stream):
 
 
 NOALLOC_MAX_SAMPLES = 1 << 22
+
+
+def merge_partials(max_lnw, s1, s2, n, hist=None):
+    """Merge per-shard MC partial sums (host arrays, no GPU): dict like Context.integrate, plus the
+    merged histograms if per-shard histograms ([shards][7][100]) are given."""
+    lib = load()
+    arrs = [np.ascontiguousarray(x, np.float64).reshape(-1) for x in (max_lnw, s1, s2, n)]
+    k = arrs[0].size
+    h = None if hist is None else np.ascontiguousarray(hist, np.float64).reshape(k, NDIM, NBINS)
+    res = np.zeros(7)
+    hout = None if h is None else np.zeros((NDIM, NBINS))
+    st = lib.ile_merge_partials(k, *[_np_ptr(a) for a in arrs], _np_ptr(h), _np_ptr(res), _np_ptr(hout))
+    if st != ILE_OK:
+        raise IleError(st, "ile_merge_partials")
+    d = dict(ln_L=res[0], sigma_ln=res[1], n_eff=res[2], ess=res[3], m=res[4], s1=res[5], s2=res[6])
+    if hout is not None:
+        d["hist"] = hout
+    return d
 
 
 def mc_reduce_noalloc(lnL_t, result, ln_prior=None, ln_ps=None, stream=None):

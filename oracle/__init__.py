@@ -79,6 +79,9 @@ def _load():
             lib.orc_hist.argtypes = [vp, vp, ctypes.c_long, vp]
             lib.orc_cdf_from_hist.argtypes = [vp, d, vp]
             lib.orc_cdf_uniform.argtypes = [vp]
+            lib.orc_wigner_d_deriv.argtypes = [i, i, i, d]
+            lib.orc_wigner_d_deriv.restype = d
+            lib.orc_lnL_t_grad.argtypes = [ctypes.POINTER(_Point), vp, d, vp, vp, vp, vp, vp]
             _lib = lib
     return _lib
 
@@ -126,6 +129,11 @@ def wigner_d(l, m1, m2, beta) -> float:
     return _load().orc_wigner_d(l, m1, m2, beta)
 
 
+def wigner_d_deriv(l, m1, m2, beta) -> float:
+    """d/dbeta of d^l_{m1,m2}(beta)."""
+    return _load().orc_wigner_d_deriv(l, m1, m2, beta)
+
+
 def sylm(l, m, iota, phi) -> complex:
     out = np.zeros(2)
     _load().orc_sylm(l, m, iota, phi, _ptr(out))
@@ -164,6 +172,34 @@ def lnL_t(point, samples, nthreads: int = 0):
     if st != 0:
         raise ValueError(f"oracle status {st}")
     return out
+
+
+def lnL_t_grad(point, samples, g=None):
+    """Analytic gradient of lnL_t for samples (7, N) times upstream weights g (N,) (default 1):
+    returns (lnL_t (N,), g_theta (7, N), g_Q (K, M, T, 2), g_U (K, M, M, 2), g_V (K, M, M, 2)), the
+    Q/U/V gradients summed over the samples and taken entry by entry as independent reals."""
+    pv = _PointView(point)
+    s = np.ascontiguousarray(samples, dtype=np.float64)
+    N = s.shape[1]
+    g = np.ones(N) if g is None else np.asarray(g, np.float64)
+    K, M, T = point.Q.shape
+    gQ = np.zeros((K, M, T, 2))
+    gU = np.zeros((K, M, M, 2))
+    gV = np.zeros((K, M, M, 2))
+    gth = np.zeros((7, N))
+    out = np.zeros(N)
+    lib = _load()
+    for n in range(N):
+        th = np.ascontiguousarray(s[:, n])
+        gt = np.zeros(7)
+        lt = np.zeros(1)
+        st = lib.orc_lnL_t_grad(ctypes.byref(pv.s), _ptr(th), float(g[n]), _ptr(gt), _ptr(gQ), _ptr(gU), _ptr(gV),
+                                _ptr(lt))
+        if st == 3:
+            raise RangeError("interpolation index outside [0, T_ext-1]")
+        gth[:, n] = gt
+        out[n] = lt[0]
+    return out, gth, gQ, gU, gV
 
 
 # ------------------------------------------------------------------------------------ S6

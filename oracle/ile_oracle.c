@@ -24,6 +24,8 @@
  *     adaptive dimension: Sec. "GPU-accelerated Monte Carlo integration";
  *   - n_eff = sum p_k / max p_k: App. "Monte Carlo integration and independent samples",
  *     Eq. (eq:neff); Kish ESS: Eq. (eq:neff_ESS).
+ *   - gradient of lnL_t (orc_lnL_t_grad): the chain rule through the same steps; the paper
+ *     states no derivative, so this is the exact derivative of the function above (R21).
  *
  * Readings of passages that are silent, garbled or ambiguous (each is listed in the design doc):
  *   R1 ln L = Re<h|d> - <h|h>/2 (the first line of Eq. (eq:loglikelihood) is garbled; the
@@ -39,6 +41,9 @@
  *   R7 MC error sigma_I / I with the sample variance s^2/N.
  *   R8 adaptive histogram: likelihood-weighted 100-bin histogram with an eps floor, sampled
  *      through an integer (2^32) cumulative table.
+ *   R21 gradient: exact derivative of lnL_t with the interpolation weight differentiated inside
+ *      a bin (one-sided at bin edges: the slope of the bin floor(x) lies in); the entries of
+ *      Q, U and V are independent real pairs (no Hermitian / symmetric tying of U and V).
  */
 #include <math.h>
 #include <stdint.h>
@@ -469,3 +474,235 @@ void orc_cdf_uniform(uint64_t *cdf)
 }
 
 int orc_version(void) { return 1; }
+
+/* ---------------------------------------------------------------- gradients (adjoint checks) */
+
+/* d/dbeta of the Wigner small-d d^l_{m1,m2}(beta), term by term of the explicit sum. */
+double orc_wigner_d_deriv(int l, int m1, int m2, double beta)
+{
+    double c = cos(0.5 * beta), s = sin(0.5 * beta);
+    double pref = sqrt(fact(l + m1) * fact(l - m1) * fact(l + m2) * fact(l - m2));
+    double sum = 0.0;
+    for (int k = 0; k <= 2 * l; k++) {
+        int a = l + m2 - k, b = k, d = l - k - m1, e = k - m2 + m1;
+        if (a < 0 || d < 0 || e < 0) continue;
+        double sign = ((k - m2 + m1) % 2 == 0) ? 1.0 : -1.0;
+        double coef = sign / (fact(a) * fact(b) * fact(d) * fact(e));
+        int P = 2 * l - 2 * k + m2 - m1, S = 2 * k - m2 + m1;
+        /* d/dbeta c^P s^S = (1/2) (S c^(P+1) s^(S-1) - P c^(P-1) s^(S+1)) */
+        double t = 0.0;
+        if (S > 0) t += S * pow(c, P + 1) * pow(s, S - 1);
+        if (P > 0) t -= P * pow(c, P - 1) * pow(s, S + 1);
+        sum += coef * 0.5 * t;
+    }
+    return pref * sum;
+}
+
+/*
+ * Gradient of lnL_t(theta) (time-marginalised, Eq. (eq:loglikelihood) with the window LSE) for
+ * one sample, times the upstream gradient g:
+ *   g_th[7]  += g d lnL_t / d(ra, dec, psi, iota, phi, D, t_c)
+ *   gQ       += g d lnL_t / d(Re Q, Im Q)   [K][M][T_ext][2]   (may be NULL)
+ *   gU, gV   += g d lnL_t / d(Re, Im) of every entry, the entries taken as independent reals
+ *               [K][M][M][2]   (may be NULL)
+ * lnL_t = LSE_j lnL(j) - ln N_t, so d lnL_t = sum_j pi_j d lnL(j) with pi the softmax over j.
+ * Derivatives: c_ka = (D_ref/D) F_k Y_a; F through the wave frame (X, Y) of (ra, dec, psi);
+ * Y through d^l_{m,2}(iota) e^{i m phi}; the window position through t_c and the delays
+ * dt_k(ra, dec) (the linear interpolation gives the slope Q[i+1] - Q[i]).
+ */
+int orc_lnL_t_grad(const orc_point *P, const double th[7], double g, double *g_th, double *gQ, double *gU,
+                   double *gV, double *lnL_t_out)
+{
+    int K = P->n_det, M = P->n_modes, T = P->T_ext, Nt = P->n_window;
+    double ra = th[0], dec = th[1], psi = th[2], iota = th[3], phi = th[4], dist = th[5], tc = th[6];
+    double sD = P->d_ref / dist;
+    /* frame and its derivatives: X = cos(psi) a + sin(psi) b, Y = -sin(psi) a + cos(psi) b */
+    double gh = P->gmst - ra, cg = cos(gh), sg = sin(gh), cd = cos(dec), sd = sin(dec), cp = cos(psi), sp = sin(psi);
+    double av[3] = {-sg, -cg, 0.0}, bv[3] = {-cg * sd, sg * sd, cd};
+    double da_dg[3] = {-cg, sg, 0.0}, db_dg[3] = {sg * sd, cg * sd, 0.0}, db_dd[3] = {-cg * cd, sg * cd, -sd};
+    double X[3], Y[3], dX[3][3], dY[3][3]; /* dX[p] = dX/d(ra, dec, psi) */
+    for (int q = 0; q < 3; q++) {
+        X[q] = cp * av[q] + sp * bv[q];
+        Y[q] = -sp * av[q] + cp * bv[q];
+        /* d/d ra = -d/dg */
+        dX[0][q] = -(cp * da_dg[q] + sp * db_dg[q]);
+        dY[0][q] = -(-sp * da_dg[q] + cp * db_dg[q]);
+        dX[1][q] = sp * db_dd[q];
+        dY[1][q] = cp * db_dd[q];
+        dX[2][q] = Y[q];
+        dY[2][q] = -X[q];
+    }
+    double nv[3] = {cd * cg, -cd * sg, sd};
+    double dn[2][3] = {{cd * sg, cd * cg, 0.0}, {-sd * cg, sd * sg, cd}}; /* d n / d(ra, dec) */
+    double *F = (double *)malloc(sizeof(double) * 2 * K), *dF = (double *)malloc(sizeof(double) * 2 * K * 3);
+    double *dt = (double *)malloc(sizeof(double) * K), *ddt = (double *)malloc(sizeof(double) * K * 2);
+    for (int k = 0; k < K; k++) {
+        const double *D = P->det_tensor + 9 * k;
+        double fp = 0, fx = 0;
+        double dfp[3] = {0, 0, 0}, dfx[3] = {0, 0, 0};
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+                double Dab = D[3 * a + b];
+                fp += Dab * (X[a] * X[b] - Y[a] * Y[b]);
+                fx += Dab * (X[a] * Y[b] + Y[a] * X[b]);
+                for (int p = 0; p < 3; p++) {
+                    dfp[p] += Dab * (dX[p][a] * X[b] + X[a] * dX[p][b] - dY[p][a] * Y[b] - Y[a] * dY[p][b]);
+                    dfx[p] += Dab * (dX[p][a] * Y[b] + X[a] * dY[p][b] + dY[p][a] * X[b] + Y[a] * dX[p][b]);
+                }
+            }
+        F[2 * k] = fp;
+        F[2 * k + 1] = fx;
+        for (int p = 0; p < 3; p++) {
+            dF[(k * 3 + p) * 2] = dfp[p];
+            dF[(k * 3 + p) * 2 + 1] = dfx[p];
+        }
+        const double *r = P->det_pos + 3 * k;
+        dt[k] = -(r[0] * nv[0] + r[1] * nv[1] + r[2] * nv[2]) / ORC_C_SI;
+        for (int p = 0; p < 2; p++) ddt[2 * k + p] = -(r[0] * dn[p][0] + r[1] * dn[p][1] + r[2] * dn[p][2]) / ORC_C_SI;
+    }
+    /* harmonics and their iota derivative */
+    double *y = (double *)malloc(sizeof(double) * 2 * M), *dy = (double *)malloc(sizeof(double) * 2 * M);
+    for (int a = 0; a < M; a++) {
+        int l = P->lm[2 * a], m = P->lm[2 * a + 1];
+        double nrm = sqrt((2.0 * l + 1.0) / (4.0 * ORC_PI));
+        double amp = nrm * orc_wigner_d(l, m, 2, iota), damp = nrm * orc_wigner_d_deriv(l, m, 2, iota);
+        y[2 * a] = amp * cos(m * phi);
+        y[2 * a + 1] = amp * sin(m * phi);
+        dy[2 * a] = damp * cos(m * phi);
+        dy[2 * a + 1] = damp * sin(m * phi);
+    }
+    /* coefficients */
+    double *c = (double *)malloc(sizeof(double) * 2 * K * M);
+    for (int k = 0; k < K; k++)
+        for (int a = 0; a < M; a++) {
+            c[2 * (k * M + a)] = sD * (F[2 * k] * y[2 * a] - F[2 * k + 1] * y[2 * a + 1]);
+            c[2 * (k * M + a) + 1] = sD * (F[2 * k] * y[2 * a + 1] + F[2 * k + 1] * y[2 * a]);
+        }
+    /* forward: lnL(j) and softmax weights */
+    double *lnL = (double *)malloc(sizeof(double) * Nt);
+    double A = quadratic(P, c);
+    int status = ORC_OK;
+    for (int j = 0; j < Nt; j++) {
+        double data = 0.0;
+        for (int k = 0; k < K; k++) {
+            double x = (tc + ((double)j - 0.5 * Nt) / P->fs + dt[k] - P->t_start) * P->fs;
+            double fl = floor(x), w = x - fl;
+            if (fl < 0.0 || fl + 1.0 > (double)(T - 1)) { status = ORC_E_RANGE; continue; }
+            long i = (long)fl;
+            for (int a = 0; a < M; a++) {
+                const double *q = P->Q + 2 * (((size_t)k * M + a) * T);
+                double qr = (1.0 - w) * q[2 * i] + w * q[2 * (i + 1)];
+                double qi = (1.0 - w) * q[2 * i + 1] + w * q[2 * (i + 1) + 1];
+                data += c[2 * (k * M + a)] * qr + c[2 * (k * M + a) + 1] * qi;
+            }
+        }
+        lnL[j] = data - A;
+    }
+    double mx = lnL[0];
+    for (int j = 1; j < Nt; j++) if (lnL[j] > mx) mx = lnL[j];
+    double ssum = 0.0;
+    for (int j = 0; j < Nt; j++) ssum += exp(lnL[j] - mx);
+    if (lnL_t_out) *lnL_t_out = mx + log(ssum) - log((double)Nt);
+    /* backward through the window: E_ka = sum_j pi_j Qhat_ka(j), slope S_k, gQ */
+    double *E = (double *)calloc(2 * K * M, sizeof(double)), *S = (double *)calloc(K, sizeof(double));
+    for (int j = 0; j < Nt; j++) {
+        double pj = exp(lnL[j] - mx) / ssum;
+        for (int k = 0; k < K; k++) {
+            double x = (tc + ((double)j - 0.5 * Nt) / P->fs + dt[k] - P->t_start) * P->fs;
+            double fl = floor(x), w = x - fl;
+            if (fl < 0.0 || fl + 1.0 > (double)(T - 1)) continue;
+            long i = (long)fl;
+            for (int a = 0; a < M; a++) {
+                const double *q = P->Q + 2 * (((size_t)k * M + a) * T);
+                double cr = c[2 * (k * M + a)], ci = c[2 * (k * M + a) + 1];
+                E[2 * (k * M + a)] += pj * ((1.0 - w) * q[2 * i] + w * q[2 * (i + 1)]);
+                E[2 * (k * M + a) + 1] += pj * ((1.0 - w) * q[2 * i + 1] + w * q[2 * (i + 1) + 1]);
+                S[k] += pj * (cr * (q[2 * (i + 1)] - q[2 * i]) + ci * (q[2 * (i + 1) + 1] - q[2 * i + 1]));
+                if (gQ) {
+                    double *gq = gQ + 2 * (((size_t)k * M + a) * T);
+                    gq[2 * i] += g * pj * (1.0 - w) * cr;
+                    gq[2 * i + 1] += g * pj * (1.0 - w) * ci;
+                    gq[2 * (i + 1)] += g * pj * w * cr;
+                    gq[2 * (i + 1) + 1] += g * pj * w * ci;
+                }
+            }
+        }
+    }
+    /* quadratic term: dA/dc (entries of U, V as given, no symmetry assumed) and gU, gV */
+    double *gc = (double *)malloc(sizeof(double) * 2 * K * M);
+    for (int k = 0; k < K; k++) {
+        const double *Uk = P->U + 2 * (size_t)k * M * M, *Vk = P->V + 2 * (size_t)k * M * M;
+        const double *ck = c + 2 * k * M;
+        for (int a = 0; a < M; a++) {
+            /* dA/dc_r,a and dA/dc_i,a */
+            double dr = 0.0, di = 0.0;
+            for (int b = 0; b < M; b++) {
+                double ur = Uk[2 * (a * M + b)], ui = Uk[2 * (a * M + b) + 1];   /* U_ab */
+                double uTr = Uk[2 * (b * M + a)], uTi = Uk[2 * (b * M + a) + 1]; /* U_ba */
+                double vr = Vk[2 * (a * M + b)], vi = Vk[2 * (a * M + b) + 1];
+                double vTr = Vk[2 * (b * M + a)], vTi = Vk[2 * (b * M + a) + 1];
+                double cbr = ck[2 * b], cbi = ck[2 * b + 1];
+                /* (U c)_a = sum_b U_ab c_b; (c^H U)_a = sum_b conj(c_b) U_ba */
+                double Ucr = ur * cbr - ui * cbi, Uci = ur * cbi + ui * cbr;
+                double cUr = cbr * uTr + cbi * uTi, cUi = cbr * uTi - cbi * uTr;
+                double Vcr = vr * cbr - vi * cbi, Vci = vr * cbi + vi * cbr;
+                double cVr = cbr * vTr - cbi * vTi, cVi = cbr * vTi + cbi * vTr;
+                /* d/dc_r of conj(c_a)(Uc)_a + (c^H U)_a c_a = (Uc)_a + (c^H U)_a ; d/dc_i: -i(Uc)_a + i (c^H U)_a */
+                dr += Ucr + cUr + Vcr + cVr;
+                di += (Uci - cUi) + (-(Vci) - cVi);
+            }
+            gc[2 * (k * M + a)] = E[2 * (k * M + a)] - 0.25 * dr;
+            gc[2 * (k * M + a) + 1] = E[2 * (k * M + a) + 1] - 0.25 * di;
+            if (gU || gV) {
+                for (int b = 0; b < M; b++) {
+                    double car = ck[2 * a], cai = ck[2 * a + 1], cbr = ck[2 * b], cbi = ck[2 * b + 1];
+                    double pr = car * cbr + cai * cbi, pim = car * cbi - cai * cbr; /* conj(c_a) c_b */
+                    double qr = car * cbr - cai * cbi, qim = car * cbi + cai * cbr; /* c_a c_b */
+                    if (gU) {
+                        gU[2 * ((size_t)(k * M + a) * M + b)] += g * (-0.25 * pr);
+                        gU[2 * ((size_t)(k * M + a) * M + b) + 1] += g * (0.25 * pim);
+                    }
+                    if (gV) {
+                        gV[2 * ((size_t)(k * M + a) * M + b)] += g * (-0.25 * qr);
+                        gV[2 * ((size_t)(k * M + a) * M + b) + 1] += g * (0.25 * qim);
+                    }
+                }
+            }
+        }
+    }
+    /* chain rule to theta */
+    double gth[7] = {0, 0, 0, 0, 0, 0, 0};
+    double gs = 0.0;
+    for (int k = 0; k < K; k++) {
+        double gFr = 0.0, gFi = 0.0;
+        for (int a = 0; a < M; a++) {
+            double gcr = gc[2 * (k * M + a)], gci = gc[2 * (k * M + a) + 1];
+            double yr = y[2 * a], yi = y[2 * a + 1];
+            /* c = sD F y:  dc/dFr = sD y, dc/dFi = i sD y */
+            gFr += sD * (gcr * yr + gci * yi);
+            gFi += sD * (-gcr * yi + gci * yr);
+            gs += gcr * c[2 * (k * M + a)] + gci * c[2 * (k * M + a) + 1];
+        }
+        for (int p = 0; p < 3; p++) gth[p] += gFr * dF[(k * 3 + p) * 2] + gFi * dF[(k * 3 + p) * 2 + 1];
+        /* window position x = (tc + dt_k ...) fs */
+        gth[6] += S[k] * P->fs;
+        gth[0] += S[k] * P->fs * ddt[2 * k];
+        gth[1] += S[k] * P->fs * ddt[2 * k + 1];
+    }
+    gth[5] = -gs / dist; /* c prop. to 1/D */
+    for (int a = 0; a < M; a++) {
+        int m = P->lm[2 * a + 1];
+        double gyr = 0.0, gyi = 0.0;
+        for (int k = 0; k < K; k++) {
+            double gcr = gc[2 * (k * M + a)], gci = gc[2 * (k * M + a) + 1];
+            double fr = sD * F[2 * k], fi = sD * F[2 * k + 1];
+            gyr += gcr * fr + gci * fi;
+            gyi += -gcr * fi + gci * fr;
+        }
+        gth[3] += gyr * dy[2 * a] + gyi * dy[2 * a + 1];
+        gth[4] += gyr * (-m * y[2 * a + 1]) + gyi * (m * y[2 * a]);
+    }
+    for (int d = 0; d < 7; d++) g_th[d] += g * gth[d];
+    free(F); free(dF); free(dt); free(ddt); free(y); free(dy); free(c); free(lnL); free(E); free(S); free(gc);
+    return status;
+}

@@ -181,9 +181,10 @@ ile_status ile_adapt_last(ile_ctx *ctx, double *theta, double *lnw_prior, uint8_
  * writes, for each stage s < n_stages, the summed device time in ms (out_ms[s]) and the number
  * of kernel launches (out_count[s], may be NULL) since the previous read, then resets them.
  * Stages: 0 sampler (S0), 1 geometry/coefficients/quadratic (S1, S2, S4), 2 shifted contraction
- * and time log-sum-exp (S3, S5), 3 Monte Carlo reduction (S6), 4 histogram adaptation (S6).
+ * and time log-sum-exp (S3, S5), 3 Monte Carlo reduction (S6), 4 histogram adaptation (S6),
+ * 5 adjoint (ile_eval_grad / ile_integrate_grad).
  */
-#define ILE_NSTAGE 5
+#define ILE_NSTAGE 6
 ile_status ile_profile(ile_ctx *ctx, int enable);
 ile_status ile_profile_read(ile_ctx *ctx, double *out_ms, int64_t *out_count, int n_stages);
 
@@ -223,6 +224,40 @@ ile_status ile_mc_reduce_noalloc(const double *lnL_t, const double *ln_prior, co
 ile_status ile_merge_partials(int n_shards, const double *max_lnw, const double *s1, const double *s2,
                               const double *n, const double *hist /* [n_shards][7][100] or NULL */,
                               double *result, double *hist_out /* [7][100] or NULL */);
+
+/* ------------------------------------------------------------------ gradients (adjoint) */
+
+#define ILE_GRAD_MAX_SAMPLES (1 << 22)
+
+/*
+ * Gradient of sum_n g_lnL[n] lnL_t(n) (the vector-Jacobian product of ile_eval) by hand-written
+ * adjoint kernels.  The paper gives no derivative: this is the exact derivative of the
+ * time-marginalised likelihood of Eq. (eq:loglikelihood) as computed (linear interpolation of Q
+ * differentiated inside the bin the window start falls in), in FP32 per sample with FP64 sums
+ * over samples; the coefficient stage is recomputed from the samples.
+ *   samples: SoA [7][N] FP64 as in ile_eval; g_lnL: [N] upstream weights.
+ *   g_samples: [7][N] d/d(ra, dec, psi, iota, phi, D_Mpc, tc_s) of each sample, times g_lnL[n].
+ *   g_Q: [n_det][n_modes][T_ext][2]; g_U, g_V: [n_det][n_modes][n_modes][2]: derivatives with
+ *   respect to the real and imaginary part of every entry, the entries taken as independent
+ *   (no Hermitian or symmetric tying), summed over the samples.  U and V themselves must be
+ *   Hermitian / symmetric as ile_set_data requires.
+ *   lnL_t_out: [N] lnL_t recomputed by the adjoint's FP32 forward pass.
+ * Any output may be NULL (at least one is required); 1 <= N <= ILE_GRAD_MAX_SAMPLES.  Device
+ * memory: N * n_window * 4 bytes of scratch when g_Q is requested.  flags: ILE_DEVICE_PTRS.
+ */
+ile_status ile_eval_grad(ile_ctx *ctx, const double *samples, int64_t N, const double *g_lnL, double *g_samples,
+                         double *g_Q, double *g_U, double *g_V, double *lnL_t_out, unsigned flags);
+
+/*
+ * ln L_marg of Eq. (eq:lnL:MonteCarlo) (result as in ile_integrate, computed with the context's
+ * contraction arithmetic) and g_scale times its gradient through lnL_t: the adjoint of
+ * ile_eval_grad with g_lnL[n] = g_scale * w_n / sum w.  g_scale: one double (host or device per
+ * flags), NULL = 1.  ln_prior and ln_ps enter as constants (their own derivatives are the
+ * caller's).  Outputs as in ile_eval_grad; any of them may be NULL.
+ */
+ile_status ile_integrate_grad(ile_ctx *ctx, const double *samples, const double *ln_prior, const double *ln_ps,
+                              int64_t N, const double *g_scale, double *result, double *g_samples, double *g_Q,
+                              double *g_U, double *g_V, unsigned flags);
 
 /* Wait for the context's stream and return the first device-side error seen since the last call. */
 ile_status ile_sync(ile_ctx *ctx);

@@ -1,0 +1,761 @@
+// ile_adjoint.cu -- hand-written adjoint of the time-marginalised likelihood lnL_t (stages S1-S5):
+// the gradient of sum_n g_n lnL_t(n) with respect to every sample's extrinsic parameters
+// (ra, dec, psi, iota, phi, D, t_c) and with respect to the inner-product arrays Q, U and V of
+// Eq. (eq:QUV).  The paper states no derivative; this is the exact derivative of the function the
+// forward kernels compute (FP32 arithmetic, FP64 sums over samples).
+//
+// With D(n, j) = sum_k [(1 - w_k) G_k(n, i_k + j) + w_k G_k(n, i_k + j + 1)],
+// G_k(n, t) = sum_r C_k(r, n) Qp_k(r, t) and lnL_t = LSE_j D(n, j) - A(n) - ln N_t, the window
+// softmax pi_j = exp(D_j - LSE) carries the whole backward pass:
+//   E_k(r)   = sum_t P_k(t) Qp_k(r, t),  P_k(t) = (1 - w_k) pi_{t - i_k} + w_k pi_{t - i_k - 1}
+//              (the pi-weighted interpolated Q: dlnL_t/dC_k(r) = E_k(r) - dA/dC_k(r));
+//   S_k      = sum_r C_k(r) sum_t (pi_{t - i_k - 1} - pi_{t - i_k}) Qp_k(r, t)
+//              (dlnL_t/dx_k, x_k the fractional window start: the slope of the interpolation);
+//   dQp_k(r, t) = sum_n g_n C_k(r, n) P_k(n, t)                       (sample-reduction GEMM);
+//   dU_k(a, b) = -1/4 sum_n g_n conj(c_a) c_b,  dV_k(a, b) = -1/4 sum_n g_n c_a c_b.
+// The chain rule to theta goes through c_k = (D_ref/D) F_k Y (antenna factors of the wave
+// frame, spin-weighted harmonics with d/diota of the Wigner-d polynomial) and x_k through the
+// delays dt_k(ra, dec).  The coefficient stage is recomputed, never stored across calls.
+//
+// Kernels (one call):
+//   adj_main   one CTA per tile of NS samples (in delay-sorted order): recomputes D(n, j) with an
+//              FP32 register-blocked GEMM per 64-column chunk (as the plain forward), takes the
+//              window softmax, then per detector a second chunked GEMM
+//              [2 NS x 64] x [64 x 2M] gives E and the slope sums; a thread per sample finishes
+//              the chain rule and writes g_theta.  pi * g_n goes to HBM for dQ.
+//   adj_gq     grid (128-column block, detector, sample split): dQ partials from C and pi*g.
+//   adj_guv    grid of sample splits; a thread per (a <= b) mode pair: dU, dV partials.
+//   *_reduce   FP64 sums of the partials into the caller's layouts.
+#include "ile_internal.cuh"
+
+namespace {
+
+constexpr int TCOL = 64;                 // columns per chunk in adj_main
+constexpr int RMAX = 2 * ILE_MAX_MODES;  // real rows of the contraction (Re rows, then Im rows)
+constexpr int RP = 48;                   // rows padded to 3 x 16 for the backward GEMM
+constexpr int QT_LD = RP + 1;            // transposed Q chunk row stride (odd: conflict-free)
+
+// d^l_{m,2}(iota) and its derivative d/diota, from the Wigner polynomial in c = cos(iota/2),
+// s = sin(iota/2): d/diota c^p s^q = (q c^(p+1) s^(q-1) - p c^(p-1) s^(q+1)) / 2.
+__device__ __forceinline__ void sylm_and_diota(const ModeTab &md, const float *cpow, const float *spow, float phi,
+                                               float &yr, float &yi, float &dr, float &di) {
+    float amp = 0.f, damp = 0.f;
+    for (int t = 0; t < md.nterms; t++) {
+        const int p = md.t[t].p, q = md.t[t].q;
+        const float cf = md.t[t].coef;
+        amp += cf * cpow[p] * spow[q];
+        float d = 0.f;
+        if (q > 0) d += (float)q * cpow[p + 1] * spow[q - 1];
+        if (p > 0) d -= (float)p * cpow[p - 1] * spow[q + 1];
+        damp += 0.5f * cf * d;
+    }
+    float sn, cs;
+    sincosf((float)md.m * phi, &sn, &cs);
+    yr = md.norm * amp * cs;
+    yi = md.norm * amp * sn;
+    dr = md.norm * damp * cs;
+    di = md.norm * damp * sn;
+}
+
+__device__ __forceinline__ void half_angle_powers10(float iota, float *cpow, float *spow) {
+    float s, c;
+    sincosf(0.5f * iota, &s, &c);
+    cpow[0] = 1.f;
+    spow[0] = 1.f;
+#pragma unroll
+    for (int i = 1; i < 10; i++) {
+        cpow[i] = cpow[i - 1] * c;
+        spow[i] = spow[i - 1] * s;
+    }
+}
+
+__device__ __forceinline__ float dot3(const float *a, const float *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+__device__ __forceinline__ void matvec3(const float *D, const float *x, float *y) {
+    y[0] = D[0] * x[0] + D[1] * x[1] + D[2] * x[2];
+    y[1] = D[3] * x[0] + D[4] * x[1] + D[5] * x[2];
+    y[2] = D[6] * x[0] + D[7] * x[1] + D[8] * x[2];
+}
+
+template <int NS>
+struct MainSmem {
+    static size_t floats(int Nt) {
+        const size_t p1 = (size_t)RMAX * TCOL + (size_t)NS * (TCOL + 1);
+        const size_t p3 = (size_t)TCOL * QT_LD + 2 * (size_t)TCOL * (NS + 4);
+        const size_t ep = (size_t)NS * (4 * ILE_MAX_MODES + 1) + (size_t)ILE_MAX_DET * (ILE_MAX_MODES * (ILE_MAX_MODES + 1) / 2) * 4;
+        size_t u = p1 > p3 ? p1 : p3;
+        u = u > ep ? u : ep;
+        return (size_t)NS * Nt + (size_t)RMAX * NS + (size_t)NS * (RMAX + 1) + u;
+    }
+};
+
+template <int NS>
+__global__ void __launch_bounds__(256, 1)
+    adj_main_kernel(const __grid_constant__ PointParams pp, const float *__restrict__ Qp, const float4 *__restrict__ UV,
+                    IleScratch s, const int *__restrict__ perm, const double *__restrict__ samples,
+                    const double *__restrict__ g_lnL, int64_t N, float *__restrict__ pig,
+                    double *__restrict__ g_samples, double *__restrict__ lnl_out) {
+    constexpr int RS = NS / 16;  // samples per thread in both GEMM micro-tiles
+    constexpr int PLD = NS + 4;
+    constexpr int YLD = 4 * ILE_MAX_MODES + 1;
+    extern __shared__ __align__(16) float smem[];
+    const int Nt = pp.Nt, M = pp.M, R = 2 * M, T = pp.T_ext, K = pp.K;
+    float *Ds = smem;                     // [NS][Nt]: D(n, j), then pi(n, j)
+    float *Cs = Ds + (size_t)NS * Nt;     // [RMAX][NS]
+    float *Es = Cs + RMAX * NS;           // [NS][RMAX + 1]
+    float *U1 = Es + NS * (RMAX + 1);     // phase-dependent region
+    float *Qs = U1;                       // phase 1: [RMAX][TCOL]
+    float *Gs = Qs + RMAX * TCOL;         //          [NS][TCOL + 1]
+    float *QsT = U1;                      // phase 3: [TCOL][QT_LD]
+    float *PsE = QsT + TCOL * QT_LD;      //          [TCOL][PLD]
+    float *PsD = PsE + TCOL * PLD;        //          [TCOL][PLD]
+    float *Ys = U1;                       // epilogue: [NS][YLD] (yr, yi, dyr, dyi per mode)
+    float4 *UVs = reinterpret_cast<float4 *>(U1 + NS * YLD + ((4 - (NS * YLD) % 4) % 4));  // [K][P]
+
+    __shared__ int i0s[NS];
+    __shared__ float ws[NS];
+    __shared__ int lo_s[ILE_MAX_DET], hi_s[ILE_MAX_DET];
+    __shared__ float Ss[ILE_MAX_DET][NS];
+    __shared__ float proj[ILE_MAX_DET][6][NS];
+    __shared__ int red[2][8];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n0 = (int64_t)blockIdx.x * NS;
+    const int ns = (int)min((int64_t)NS, N - n0);
+
+    for (int i = tid; i < NS * Nt; i += 256) Ds[i] = 0.f;
+
+    auto load_detector = [&](int k) {
+        if (tid < NS) {
+            int nn = tid < ns ? tid : 0;
+            i0s[tid] = s.I0[(int64_t)k * N + n0 + nn];
+            ws[tid] = s.W[(int64_t)k * N + n0 + nn];
+        }
+        for (int i = tid; i < R * NS; i += 256) {
+            int r = i / NS, nn = i - r * NS;
+            Cs[r * NS + nn] = nn < ns ? s.C[((int64_t)k * R + r) * N + n0 + nn] : 0.f;
+        }
+    };
+
+    // ---------------------------------------------------------------- phase 1: D(n, j)
+    for (int k = 0; k < K; k++) {
+        __syncthreads();
+        load_detector(k);
+        __syncthreads();
+        int lo = 0x7fffffff, hi = -0x7fffffff;
+        for (int i = tid; i < ns; i += 256) {
+            lo = min(lo, i0s[i]);
+            hi = max(hi, i0s[i]);
+        }
+        for (int o = 16; o; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            red[0][warp] = lo;
+            red[1][warp] = hi;
+        }
+        __syncthreads();
+        lo = red[0][0];
+        hi = red[1][0];
+        for (int w = 1; w < 8; w++) {
+            lo = min(lo, red[0][w]);
+            hi = max(hi, red[1][w]);
+        }
+        if (tid == 0) {
+            lo_s[k] = lo;
+            hi_s[k] = hi;
+        }
+        const int cend = hi + Nt;
+        for (int c0 = lo; c0 <= cend; c0 += TCOL) {
+            __syncthreads();
+            for (int i = tid; i < R * TCOL; i += 256) {
+                int r = i / TCOL, c = i - r * TCOL;
+                int col = c0 + c;
+                Qs[r * TCOL + c] = (col >= 0 && col < T) ? Qp[((int64_t)k * R + r) * T + col] : 0.f;
+            }
+            __syncthreads();
+            {
+                const int ty = tid >> 4, tx = tid & 15;
+                float acc[RS][4];
+#pragma unroll
+                for (int i = 0; i < RS; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) acc[i][j] = 0.f;
+                for (int r = 0; r < R; r++) {
+                    float a[RS];
+#pragma unroll
+                    for (int i = 0; i < RS; i++) a[i] = Cs[r * NS + ty * RS + i];
+                    float4 b = *reinterpret_cast<const float4 *>(&Qs[r * TCOL + tx * 4]);
+#pragma unroll
+                    for (int i = 0; i < RS; i++) {
+                        acc[i][0] = fmaf(a[i], b.x, acc[i][0]);
+                        acc[i][1] = fmaf(a[i], b.y, acc[i][1]);
+                        acc[i][2] = fmaf(a[i], b.z, acc[i][2]);
+                        acc[i][3] = fmaf(a[i], b.w, acc[i][3]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < RS; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) Gs[(ty * RS + i) * (TCOL + 1) + tx * 4 + j] = acc[i][j];
+            }
+            __syncthreads();
+            for (int nn = warp; nn < ns; nn += 8) {
+                const int i0 = i0s[nn];
+                const float wt = ws[nn];
+                const int jlo = max(0, c0 - 1 - i0), jhi = min(Nt - 1, c0 + TCOL - 1 - i0);
+                const float *g = Gs + nn * (TCOL + 1);
+                float *d = Ds + (size_t)nn * Nt;
+                for (int j = jlo + lane; j <= jhi; j += 32) {
+                    int c = i0 + j - c0;
+                    float v = 0.f;
+                    if (c >= 0) v = (1.f - wt) * g[c];
+                    if (c + 1 < TCOL) v = fmaf(wt, g[c + 1], v);
+                    d[j] += v;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------------- phase 2: window softmax
+    const double log_nt = log((double)Nt);
+    for (int nn = warp; nn < ns; nn += 8) {
+        float *d = Ds + (size_t)nn * Nt;
+        const int64_t src = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
+        float m = -INFINITY;
+        for (int j = lane; j < Nt; j += 32) m = fmaxf(m, d[j]);
+        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        float sum = 0.f;
+        for (int j = lane; j < Nt; j += 32) sum += expf(d[j] - m);
+        for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        const float inv = 1.f / sum;
+        const float gn = (float)g_lnL[src];
+        float *pg = pig ? pig + (size_t)(n0 + nn) * Nt : nullptr;
+        for (int j = lane; j < Nt; j += 32) {
+            float p = expf(d[j] - m) * inv;
+            d[j] = p;
+            if (pg) pg[j] = gn * p;
+        }
+        if (lnl_out && lane == 0) lnl_out[src] = (double)m + (double)logf(sum) - (double)s.A[n0 + nn] - log_nt;
+    }
+
+    // ---------------------------------------------------------------- phase 3: E and slope sums
+    {
+        const int ty = tid >> 4, tx = tid & 15;
+        for (int k = 0; k < K; k++) {
+            __syncthreads();
+            load_detector(k);
+            for (int i = tid; i < TCOL * (RP - R); i += 256) {
+                int c = i / (RP - R), r = R + i - c * (RP - R);
+                QsT[c * QT_LD + r] = 0.f;
+            }
+            float aE[RS][3], aD[RS][3];
+#pragma unroll
+            for (int i = 0; i < RS; i++)
+#pragma unroll
+                for (int m = 0; m < 3; m++) aE[i][m] = aD[i][m] = 0.f;
+            const int lo = lo_s[k], cend = hi_s[k] + Nt;
+            for (int c0 = lo; c0 <= cend; c0 += TCOL) {
+                __syncthreads();
+                for (int i = tid; i < R * TCOL; i += 256) {
+                    int r = i / TCOL, c = i - r * TCOL;
+                    int col = c0 + c;
+                    QsT[c * QT_LD + r] = (col >= 0 && col < T) ? Qp[((int64_t)k * R + r) * T + col] : 0.f;
+                }
+                for (int i = tid; i < NS * TCOL; i += 256) {
+                    int c = i / NS, nn = i - c * NS;
+                    int j0 = c0 + c - i0s[nn];
+                    const float *pr = Ds + (size_t)nn * Nt;
+                    float a = (j0 >= 0 && j0 < Nt) ? pr[j0] : 0.f;
+                    float b = (j0 >= 1 && j0 <= Nt) ? pr[j0 - 1] : 0.f;
+                    float wt = ws[nn];
+                    PsE[c * PLD + nn] = (1.f - wt) * a + wt * b;
+                    PsD[c * PLD + nn] = b - a;
+                }
+                __syncthreads();
+#pragma unroll 4
+                for (int c = 0; c < TCOL; c++) {
+                    float pe[RS], pd[RS];
+                    if constexpr (RS == 4) {
+                        float4 e4 = *reinterpret_cast<const float4 *>(&PsE[c * PLD + ty * 4]);
+                        float4 d4 = *reinterpret_cast<const float4 *>(&PsD[c * PLD + ty * 4]);
+                        pe[0] = e4.x; pe[1] = e4.y; pe[2] = e4.z; pe[3] = e4.w;
+                        pd[0] = d4.x; pd[1] = d4.y; pd[2] = d4.z; pd[3] = d4.w;
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < RS; i++) {
+                            pe[i] = PsE[c * PLD + ty * RS + i];
+                            pd[i] = PsD[c * PLD + ty * RS + i];
+                        }
+                    }
+                    float q[3];
+#pragma unroll
+                    for (int m = 0; m < 3; m++) q[m] = QsT[c * QT_LD + tx + 16 * m];
+#pragma unroll
+                    for (int i = 0; i < RS; i++)
+#pragma unroll
+                        for (int m = 0; m < 3; m++) {
+                            aE[i][m] = fmaf(pe[i], q[m], aE[i][m]);
+                            aD[i][m] = fmaf(pd[i], q[m], aD[i][m]);
+                        }
+                }
+            }
+            // E to shared memory; slope sum S_k = sum_r C(r) dE(r) reduced over the 16 row lanes
+#pragma unroll
+            for (int i = 0; i < RS; i++) {
+                const int nn = ty * RS + i;
+                float sp = 0.f;
+#pragma unroll
+                for (int m = 0; m < 3; m++) {
+                    const int r = tx + 16 * m;
+                    if (r < R) {
+                        Es[nn * (RMAX + 1) + r] = aE[i][m];
+                        sp = fmaf(Cs[r * NS + nn], aD[i][m], sp);
+                    }
+                }
+                for (int o = 8; o; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
+                if (tx == 0) Ss[k][nn] = sp;
+            }
+            __syncthreads();
+            // projections of E on the harmonics: e = sum_a conj(E_a) y_a, with y -> dy/diota, i m y
+            if (tid < ns) {
+                const int64_t src = perm ? (int64_t)perm[n0 + tid] : n0 + tid;
+                const float iota = (float)samples[3 * N + src], phi = (float)samples[4 * N + src];
+                float cpow[10], spow[10];
+                half_angle_powers10(iota, cpow, spow);
+                float er = 0.f, ei = 0.f, gr = 0.f, gi = 0.f, fr = 0.f, fi = 0.f;
+                const float *E = Es + tid * (RMAX + 1);
+                for (int a = 0; a < M; a++) {
+                    float yr, yi, dr, di;
+                    sylm_and_diota(pp.mode[a], cpow, spow, phi, yr, yi, dr, di);
+                    const float Er = E[a], Ei = E[M + a], mm = (float)pp.mode[a].m;
+                    er += Er * yr + Ei * yi;
+                    ei += Er * yi - Ei * yr;
+                    gr += Er * dr + Ei * di;
+                    gi += Er * di - Ei * dr;
+                    // i m y = (-m yi, m yr)
+                    fr += mm * (-Er * yi + Ei * yr);
+                    fi += mm * (Er * yr + Ei * yi);
+                }
+                proj[k][0][tid] = er;
+                proj[k][1][tid] = ei;
+                proj[k][2][tid] = gr;
+                proj[k][3][tid] = gi;
+                proj[k][4][tid] = fr;
+                proj[k][5][tid] = fi;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------------- epilogue: chain rule to theta
+    const int P = M * (M + 1) / 2;
+    for (int i = tid; i < K * P; i += 256) UVs[i] = UV[i];
+    if (tid < ns) {
+        const int64_t src = perm ? (int64_t)perm[n0 + tid] : n0 + tid;
+        float th[ILE_NDIM];
+#pragma unroll
+        for (int d = 0; d < ILE_NDIM; d++) th[d] = (float)samples[(int64_t)d * N + src];
+        float cpow[10], spow[10];
+        half_angle_powers10(th[3], cpow, spow);
+        float *y = Ys + tid * YLD;
+        for (int a = 0; a < M; a++)
+            sylm_and_diota(pp.mode[a], cpow, spow, th[4], y[4 * a], y[4 * a + 1], y[4 * a + 2], y[4 * a + 3]);
+    }
+    __syncthreads();
+    if (tid < ns) {
+        const int64_t src = perm ? (int64_t)perm[n0 + tid] : n0 + tid;
+        const double gn = g_lnL[src];
+        const float ra = (float)samples[src], dec = (float)samples[N + src], psi = (float)samples[2 * N + src];
+        const float dist = (float)samples[5 * N + src];
+        const float sc = pp.d_ref / dist, sc2 = sc * sc;
+        float sg, cg, sd, cd, sp, cp;
+        sincosf(pp.gmst - ra, &sg, &cg);
+        sincosf(dec, &sd, &cd);
+        sincosf(psi, &sp, &cp);
+        // wave frame X = cp a + sp b, Y = -sp a + cp b; derivatives in ra (= -d/dg) and dec
+        const float av[3] = {-sg, -cg, 0.f}, bv[3] = {-cg * sd, sg * sd, cd};
+        const float a_ra[3] = {cg, -sg, 0.f}, b_ra[3] = {-sg * sd, -cg * sd, 0.f};
+        const float b_de[3] = {-cg * cd, sg * cd, -sd};
+        float X[3], Y[3], Xr[3], Yr[3], Xd[3], Yd[3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            X[q] = cp * av[q] + sp * bv[q];
+            Y[q] = -sp * av[q] + cp * bv[q];
+            Xr[q] = cp * a_ra[q] + sp * b_ra[q];
+            Yr[q] = -sp * a_ra[q] + cp * b_ra[q];
+            Xd[q] = sp * b_de[q];
+            Yd[q] = cp * b_de[q];
+        }
+        const float n_ra[3] = {cd * sg, cd * cg, 0.f}, n_de[3] = {-sd * cg, sd * sg, cd};
+
+        // quadratic-term sums per detector over the mode pairs (U, V pre-doubled off the diagonal)
+        float u[ILE_MAX_DET], ui[ILE_MAX_DET], uf[ILE_MAX_DET];
+        float vr[ILE_MAX_DET], vi[ILE_MAX_DET], vir[ILE_MAX_DET], vii[ILE_MAX_DET], vfr[ILE_MAX_DET],
+            vfi[ILE_MAX_DET];
+#pragma unroll
+        for (int k = 0; k < ILE_MAX_DET; k++) u[k] = ui[k] = uf[k] = vr[k] = vi[k] = vir[k] = vii[k] = vfr[k] = vfi[k] = 0.f;
+        const float *y = Ys + tid * YLD;
+        int p = 0;
+        for (int a = 0; a < M; a++) {
+            const float yar = y[4 * a], yai = y[4 * a + 1], dar = y[4 * a + 2], dai = y[4 * a + 3];
+            const float ma = (float)pp.mode[a].m;
+            for (int b = a; b < M; b++, p++) {
+                const float ybr = y[4 * b], ybi = y[4 * b + 1], dbr = y[4 * b + 2], dbi = y[4 * b + 3];
+                const float mb = (float)pp.mode[b].m;
+                // q = conj(y_a) y_b, its iota derivative; pp = y_a y_b, its iota derivative
+                const float qr = yar * ybr + yai * ybi, qi = yar * ybi - yai * ybr;
+                const float qdr = dar * ybr + dai * ybi + yar * dbr + yai * dbi;
+                const float qdi = dar * ybi - dai * ybr + yar * dbi - yai * dbr;
+                const float pr = yar * ybr - yai * ybi, pi = yar * ybi + yai * ybr;
+                const float pdr = dar * ybr - dai * ybi + yar * dbr - yai * dbi;
+                const float pdi = dar * ybi + dai * ybr + yar * dbi + yai * dbr;
+                const float dm = mb - ma, sm = ma + mb;
+#pragma unroll
+                for (int k = 0; k < ILE_MAX_DET; k++) {
+                    if (k < K) {
+                        const float4 w = UVs[k * P + p];
+                        u[k] += w.x * qr - w.y * qi;
+                        ui[k] += w.x * qdr - w.y * qdi;
+                        uf[k] -= dm * (w.x * qi + w.y * qr);  // Re(U i dm q)
+                        const float tr = w.z * pr - w.w * pi, tim = w.z * pi + w.w * pr;  // V p
+                        vr[k] += tr;
+                        vi[k] += tim;
+                        vir[k] += w.z * pdr - w.w * pdi;
+                        vii[k] += w.z * pdi + w.w * pdr;
+                        vfr[k] -= sm * tim;  // i sm (V p)
+                        vfi[k] += sm * tr;
+                    }
+                }
+            }
+        }
+
+        float g_ra = 0.f, g_dec = 0.f, g_psi = 0.f, g_iota = 0.f, g_phi = 0.f, g_tc = 0.f, data = 0.f, A = 0.f;
+#pragma unroll
+        for (int k = 0; k < ILE_MAX_DET; k++) {
+            if (k >= K) break;
+            const float *D = pp.det_tensor[k];
+            float DX[3], DY[3], DXr[3], DYr[3], DXd[3], DYd[3];
+            matvec3(D, X, DX);
+            matvec3(D, Y, DY);
+            matvec3(D, Xr, DXr);
+            matvec3(D, Yr, DYr);
+            matvec3(D, Xd, DXd);
+            matvec3(D, Yd, DYd);
+            const float Fr = dot3(X, DX) - dot3(Y, DY), Fi = dot3(X, DY) + dot3(Y, DX);
+            const float Fr_ra = dot3(Xr, DX) + dot3(X, DXr) - dot3(Yr, DY) - dot3(Y, DYr);
+            const float Fi_ra = dot3(Xr, DY) + dot3(X, DYr) + dot3(Yr, DX) + dot3(Y, DXr);
+            const float Fr_de = dot3(Xd, DX) + dot3(X, DXd) - dot3(Yd, DY) - dot3(Y, DYd);
+            const float Fi_de = dot3(Xd, DY) + dot3(X, DYd) + dot3(Yd, DX) + dot3(Y, DXd);
+            const float dt_ra = -dot3(pp.det_pos_c[k], n_ra), dt_de = -dot3(pp.det_pos_c[k], n_de);
+            const float er = proj[k][0][tid], ei = proj[k][1][tid];
+            const float gr = proj[k][2][tid], gi = proj[k][3][tid];
+            const float fr = proj[k][4][tid], fi = proj[k][5][tid];
+            const float S = Ss[k][tid] * pp.fs;
+            const float F2 = Fr * Fr + Fi * Fi, Gr = Fr * Fr - Fi * Fi, Gi = 2.f * Fr * Fi;  // |F|^2, F^2
+            const float Fvr = Fr * vr[k] - Fi * vi[k], Fvi = Fr * vi[k] + Fi * vr[k];      // F v
+            const float gFr = sc * er - 0.5f * sc2 * (Fr * u[k] + Fvr);
+            const float gFi = -sc * ei - 0.5f * sc2 * (Fi * u[k] - Fvi);
+            g_ra += gFr * Fr_ra + gFi * Fi_ra + S * dt_ra;
+            g_dec += gFr * Fr_de + gFi * Fi_de + S * dt_de;
+            g_psi += 2.f * (gFr * Fi - gFi * Fr);
+            g_iota += sc * (Fr * gr - Fi * gi) - 0.25f * sc2 * (F2 * ui[k] + Gr * vir[k] - Gi * vii[k]);
+            g_phi += sc * (Fr * fr - Fi * fi) - 0.25f * sc2 * (F2 * uf[k] + Gr * vfr[k] - Gi * vfi[k]);
+            g_tc += S;
+            data += sc * (Fr * er - Fi * ei);
+            A += 0.25f * sc2 * (F2 * u[k] + Gr * vr[k] - Gi * vi[k]);
+        }
+        const float g_D = (2.f * A - data) / dist;
+        if (g_samples) {
+            g_samples[src] = gn * (double)g_ra;
+            g_samples[N + src] = gn * (double)g_dec;
+            g_samples[2 * N + src] = gn * (double)g_psi;
+            g_samples[3 * N + src] = gn * (double)g_iota;
+            g_samples[4 * N + src] = gn * (double)g_phi;
+            g_samples[5 * N + src] = gn * (double)g_D;
+            g_samples[6 * N + src] = gn * (double)g_tc;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ dQ: sample-reduction GEMM
+constexpr int QTB = 128;  // time columns per CTA
+constexpr int QNC = 32;   // samples per staged chunk
+
+__global__ void __launch_bounds__(256)
+    adj_gq_kernel(const __grid_constant__ PointParams pp, const float *__restrict__ pig, IleScratch s, int64_t N,
+                  int nsplit, float *__restrict__ part) {
+    __shared__ __align__(16) float Cc[RMAX][QNC];
+    __shared__ __align__(16) float Pc[QNC][QTB];
+    __shared__ int i0c[QNC];
+    __shared__ float wc[QNC];
+    const int Nt = pp.Nt, R = 2 * pp.M, T = pp.T_ext;
+    const int t0 = blockIdx.x * QTB, k = blockIdx.y, split = blockIdx.z;
+    const int64_t nb = N * split / nsplit, ne = N * (split + 1) / nsplit;
+    const int tid = threadIdx.x, ry = tid >> 4, tx = tid & 15;
+    float acc[3][8];
+#pragma unroll
+    for (int m = 0; m < 3; m++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[m][j] = 0.f;
+
+    for (int64_t c0 = nb; c0 < ne; c0 += QNC) {
+        const int nc = (int)min((int64_t)QNC, ne - c0);
+        __syncthreads();
+        if (tid < QNC) {
+            i0c[tid] = tid < nc ? s.I0[(int64_t)k * N + c0 + tid] : 0;
+            wc[tid] = tid < nc ? s.W[(int64_t)k * N + c0 + tid] : 0.f;
+        }
+        for (int i = tid; i < RMAX * QNC; i += 256) {
+            int r = i / QNC, j = i - r * QNC;
+            Cc[r][j] = (r < R && j < nc) ? s.C[((int64_t)k * R + r) * N + c0 + j] : 0.f;
+        }
+        __syncthreads();
+        int any = 0;
+        for (int i = tid; i < QNC * QTB; i += 256) {
+            int j = i / QTB, c = i - j * QTB;
+            float v = 0.f;
+            if (j < nc) {
+                int j0 = t0 + c - i0c[j];
+                const float *pr = pig + (size_t)(c0 + j) * Nt;
+                float a = (j0 >= 0 && j0 < Nt) ? pr[j0] : 0.f;
+                float b = (j0 >= 1 && j0 <= Nt) ? pr[j0 - 1] : 0.f;
+                v = (1.f - wc[j]) * a + wc[j] * b;
+                any |= (j0 >= 0 && j0 <= Nt);
+            }
+            Pc[j][c] = v;
+        }
+        if (!__syncthreads_or(any)) continue;
+#pragma unroll 4
+        for (int j = 0; j < QNC; j++) {
+            const float4 p0 = *reinterpret_cast<const float4 *>(&Pc[j][tx * 4]);
+            const float4 p1 = *reinterpret_cast<const float4 *>(&Pc[j][64 + tx * 4]);
+            const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+            for (int m = 0; m < 3; m++) {
+                const int r = ry + 16 * m;
+                const float cv = r < RMAX ? Cc[r][j] : 0.f;
+#pragma unroll
+                for (int q = 0; q < 8; q++) acc[m][q] = fmaf(cv, pv[q], acc[m][q]);
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        const int r = ry + 16 * m;
+        if (r >= R) continue;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int t = t0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + q - 4);
+            if (t < T) part[(((int64_t)split * pp.K + k) * R + r) * T + t] = acc[m][q];
+        }
+    }
+}
+
+__global__ void adj_gq_reduce_kernel(int K, int M, int T, int nsplit, const float *__restrict__ part,
+                                     double *__restrict__ gQ) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)K * M * T;
+    if (i >= total) return;
+    const int t = (int)(i % T), a = (int)((i / T) % M), k = (int)(i / ((int64_t)T * M));
+    const int R = 2 * M;
+    double re = 0.0, im = 0.0;
+    for (int sp = 0; sp < nsplit; sp++) {
+        re += (double)part[(((int64_t)sp * K + k) * R + a) * T + t];
+        im += (double)part[(((int64_t)sp * K + k) * R + M + a) * T + t];
+    }
+    gQ[2 * i] = re;
+    gQ[2 * i + 1] = im;
+}
+
+// ------------------------------------------------------------------ dU, dV: weighted pair sums
+constexpr int UVC = 64;  // samples per staged chunk
+
+__global__ void __launch_bounds__(256)
+    adj_guv_kernel(const __grid_constant__ PointParams pp, const double *__restrict__ samples,
+                   const double *__restrict__ g_lnL, int64_t N, int nblk, float *__restrict__ part) {
+    __shared__ float2 Yc[UVC][ILE_MAX_MODES + 1];
+    __shared__ float Wc[UVC][3 * ILE_MAX_DET];
+    const int M = pp.M, K = pp.K, P = M * (M + 1) / 2;
+    const int tid = threadIdx.x;
+    const int64_t nb = N * blockIdx.x / nblk, ne = N * (blockIdx.x + 1) / nblk;
+    // this thread's mode pair (a <= b), p in upper-triangle order
+    int pa = 0, pb = 0;
+    {
+        int p = tid, a = 0;
+        while (a < M && p >= M - a) {
+            p -= M - a;
+            a++;
+        }
+        pa = a;
+        pb = a + p;
+    }
+    float aUr[ILE_MAX_DET], aUi[ILE_MAX_DET], aVr[ILE_MAX_DET], aVi[ILE_MAX_DET];
+#pragma unroll
+    for (int k = 0; k < ILE_MAX_DET; k++) aUr[k] = aUi[k] = aVr[k] = aVi[k] = 0.f;
+
+    for (int64_t c0 = nb; c0 < ne; c0 += UVC) {
+        const int nc = (int)min((int64_t)UVC, ne - c0);
+        __syncthreads();
+        if (tid < UVC) {
+            const int64_t n = c0 + tid;
+            float cpow[9], spow[9];
+            float Fr[ILE_MAX_DET], Fi[ILE_MAX_DET], x0[ILE_MAX_DET];
+            float g = 0.f, sc2 = 0.f;
+            float ra = 0.f, dec = 0.f, psi = 0.f, iota = 0.f, phi = 0.f;
+            if (tid < nc) {
+                ra = (float)samples[n];
+                dec = (float)samples[N + n];
+                psi = (float)samples[2 * N + n];
+                iota = (float)samples[3 * N + n];
+                phi = (float)samples[4 * N + n];
+                const float sc = pp.d_ref / (float)samples[5 * N + n];
+                sc2 = sc * sc;
+                g = (float)g_lnL[n];
+            }
+            ile_sample_geometry(pp, ra, dec, psi, 0.f, Fr, Fi, x0);
+            ile_half_angle_powers(iota, cpow, spow);
+            for (int a = 0; a < M; a++) {
+                float yr, yi;
+                ile_sylm(pp.mode[a], cpow, spow, phi, yr, yi);
+                Yc[tid][a] = make_float2(yr, yi);
+            }
+            const float wgt = g * sc2;
+#pragma unroll
+            for (int k = 0; k < ILE_MAX_DET; k++) {
+                if (k < K) {
+                    Wc[tid][3 * k] = wgt * (Fr[k] * Fr[k] + Fi[k] * Fi[k]);
+                    Wc[tid][3 * k + 1] = wgt * (Fr[k] * Fr[k] - Fi[k] * Fi[k]);
+                    Wc[tid][3 * k + 2] = wgt * 2.f * Fr[k] * Fi[k];
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < P) {
+            for (int j = 0; j < nc; j++) {
+                const float2 ya = Yc[j][pa], yb = Yc[j][pb];
+                const float qr = ya.x * yb.x + ya.y * yb.y, qi = ya.x * yb.y - ya.y * yb.x;  // conj(y_a) y_b
+                const float pr = ya.x * yb.x - ya.y * yb.y, pi = ya.x * yb.y + ya.y * yb.x;  // y_a y_b
+#pragma unroll
+                for (int k = 0; k < ILE_MAX_DET; k++) {
+                    if (k < K) {
+                        const float w0 = Wc[j][3 * k], wr = Wc[j][3 * k + 1], wi = Wc[j][3 * k + 2];
+                        aUr[k] = fmaf(w0, qr, aUr[k]);
+                        aUi[k] = fmaf(w0, qi, aUi[k]);
+                        aVr[k] += wr * pr - wi * pi;
+                        aVi[k] += wr * pi + wi * pr;
+                    }
+                }
+            }
+        }
+    }
+    if (tid < P) {
+        for (int k = 0; k < K; k++) {
+            float *o = part + (((int64_t)blockIdx.x * K + k) * P + tid) * 4;
+            o[0] = aUr[k];
+            o[1] = aUi[k];
+            o[2] = aVr[k];
+            o[3] = aVi[k];
+        }
+    }
+}
+
+// dU_k(a, b) = -1/4 sum g conj(c_a) c_b and dV_k(a, b) = -1/4 sum g c_a c_b, each entry an
+// independent (Re, Im) pair: d/dRe = -1/4 Re(sum), d/dIm = +1/4 Im(sum).
+__global__ void adj_guv_reduce_kernel(int K, int M, int nblk, const float *__restrict__ part, double *__restrict__ gU,
+                                      double *__restrict__ gV) {
+    const int P = M * (M + 1) / 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K * P) return;
+    const int k = i / P, p = i - k * P;
+    int a = 0, q = p;
+    while (q >= M - a) {
+        q -= M - a;
+        a++;
+    }
+    const int b = a + q;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int blk = 0; blk < nblk; blk++)
+        for (int c = 0; c < 4; c++) s[c] += (double)part[(((int64_t)blk * K + k) * P + p) * 4 + c];
+    const size_t ab = 2 * (((size_t)k * M + a) * M + b), ba = 2 * (((size_t)k * M + b) * M + a);
+    if (gU) {
+        gU[ab] = -0.25 * s[0];
+        gU[ab + 1] = 0.25 * s[1];
+        if (a != b) {
+            gU[ba] = -0.25 * s[0];
+            gU[ba + 1] = -0.25 * s[1];
+        }
+    }
+    if (gV) {
+        gV[ab] = -0.25 * s[2];
+        gV[ab + 1] = 0.25 * s[3];
+        if (a != b) {
+            gV[ba] = -0.25 * s[2];
+            gV[ba + 1] = 0.25 * s[3];
+        }
+    }
+}
+
+template <int NS>
+cudaError_t launch_main(const PointParams &pp, const float *Qp, const float *UV, IleScratch s, const int *perm,
+                        const double *samples, const double *g, int64_t N, float *pig, double *g_samples,
+                        double *lnl, cudaStream_t st) {
+    const size_t smem = sizeof(float) * MainSmem<NS>::floats(pp.Nt) + 16;
+    cudaError_t e = cudaFuncSetAttribute(adj_main_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (N + NS - 1) / NS;
+    adj_main_kernel<NS><<<(unsigned)blocks, 256, smem, st>>>(pp, Qp, (const float4 *)UV, s, perm, samples, g, N, pig,
+                                                             g_samples, lnl);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int ile_grad_q_splits(const PointParams &pp, int64_t N, int n_sm) {
+    const int tb = (pp.T_ext + QTB - 1) / QTB;
+    int64_t want = (2 * (int64_t)n_sm + (int64_t)tb * pp.K - 1) / ((int64_t)tb * pp.K);
+    const int64_t most = (N + QNC - 1) / QNC;
+    if (want > most) want = most;
+    if (want < 1) want = 1;
+    return (int)want;
+}
+
+int ile_grad_uv_blocks(int64_t N, int n_sm) {
+    int64_t b = 2 * (int64_t)n_sm;
+    const int64_t most = (N + UVC - 1) / UVC;
+    if (b > most) b = most;
+    return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t ile_launch_grad_main(const PointParams &pp, const float *Qp, const float *UV, IleScratch s,
+                                 const int *perm, const double *samples, const double *g_lnL, int64_t N, float *pig,
+                                 double *g_samples, double *lnl_out, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    if (pp.Nt <= 512) return launch_main<64>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, g_samples, lnl_out, st);
+    return launch_main<32>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, g_samples, lnl_out, st);
+}
+
+cudaError_t ile_launch_grad_q(const PointParams &pp, const float *pig, IleScratch s, int64_t N, int nsplit,
+                              float *part, double *gQ, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    dim3 grid((pp.T_ext + QTB - 1) / QTB, pp.K, nsplit);
+    adj_gq_kernel<<<grid, 256, 0, st>>>(pp, pig, s, N, nsplit, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)pp.K * pp.M * pp.T_ext;
+    adj_gq_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(pp.K, pp.M, pp.T_ext, nsplit, part, gQ);
+    return cudaGetLastError();
+}
+
+cudaError_t ile_launch_grad_uv(const PointParams &pp, const double *samples, const double *g_lnL, int64_t N, int nblk,
+                               float *part, double *gU, double *gV, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    adj_guv_kernel<<<nblk, 256, 0, st>>>(pp, samples, g_lnL, N, nblk, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int P = pp.M * (pp.M + 1) / 2;
+    adj_guv_reduce_kernel<<<(pp.K * P + 255) / 256, 256, 0, st>>>(pp.K, pp.M, nblk, part, gU, gV);
+    return cudaGetLastError();
+}

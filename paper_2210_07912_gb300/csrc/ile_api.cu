@@ -48,6 +48,17 @@ struct ile_ctx {
     int *a_iter = nullptr;
     uint8_t *a_bins = nullptr;
     int64_t a_cap = 0;
+    // adjoint scratch (ile_adjoint.cu)
+    float *pig = nullptr;      // [N][N_t] g_n * pi(n, j)
+    size_t pig_bytes = 0;
+    float *gq_part = nullptr;  // [splits][K][2M][T_ext]
+    size_t gq_bytes = 0;
+    float *guv_part = nullptr; // [blocks][K][P][4]
+    size_t guv_bytes = 0;
+    double *g_in = nullptr;    // staged host upstream gradient [cap]
+    double *g_out = nullptr;   // staged g_theta [7][cap] and g_Q, g_U, g_V for host-pointer calls
+    size_t g_out_bytes = 0;
+    int n_sm = 0;
     // stage timing
     bool profiling = false;
     std::vector<cudaEvent_t> ev[ILE_NSTAGE];
@@ -121,6 +132,7 @@ ile_status ensure_samples(ile_ctx *ctx, int64_t N) {
     CK(grow(&ctx->lnps, sizeof(double) * (size_t)cap));
     CK(grow(&ctx->keys, sizeof(int) * (size_t)cap));
     CK(grow(&ctx->perm, sizeof(int) * (size_t)cap));
+    CK(grow(&ctx->g_in, sizeof(double) * (size_t)cap));
     if (!ctx->buckets) CK(cudaMalloc((void **)&ctx->buckets, sizeof(int) * ile_sort_key_buckets()));
     int np = ile_mc_partial_count(cap);
     CK(grow(&ctx->part, sizeof(double) * 3 * (size_t)np));
@@ -237,6 +249,68 @@ ile_status run_eval(ile_ctx *ctx, const double *dsamples, int64_t N, double *dou
     return ILE_OK;
 }
 
+template <typename T>
+cudaError_t ensure_bytes(T **p, size_t *have, size_t bytes) {
+    if (bytes <= *have && *p) return cudaSuccess;
+    cudaError_t e = grow(p, bytes);
+    *have = e == cudaSuccess ? bytes : 0;
+    return e;
+}
+
+// Adjoint of S1-S5 on device-resident arrays (ile_adjoint.cu).  Any of g_theta, gQ, gU, gV, lnl
+// may be null.  Samples are delay-sorted first, as in the forward pass.
+ile_status run_grad(ile_ctx *ctx, const double *dsamples, const double *dg, int64_t N, double *g_theta, double *gQ,
+                    double *gU, double *gV, double *lnl) {
+    ile_status st = ensure_samples(ctx, N);
+    if (st != ILE_OK) return st;
+    const PointParams &pp = ctx->pp;
+    if (!ctx->n_sm) CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
+    float *pig = nullptr;
+    if (gQ) {
+        CK(ensure_bytes(&ctx->pig, &ctx->pig_bytes, sizeof(float) * (size_t)N * pp.Nt));
+        pig = ctx->pig;
+    }
+    const int nsplit = ile_grad_q_splits(pp, N, ctx->n_sm);
+    const int nblk = ile_grad_uv_blocks(N, ctx->n_sm);
+    if (gQ) CK(ensure_bytes(&ctx->gq_part, &ctx->gq_bytes, sizeof(float) * (size_t)nsplit * pp.K * 2 * pp.M * pp.T_ext));
+    if (gU || gV)
+        CK(ensure_bytes(&ctx->guv_part, &ctx->guv_bytes,
+                        sizeof(float) * (size_t)nblk * pp.K * (pp.M * (pp.M + 1) / 2) * 4));
+    {
+        StageScope t(ctx, 1, 4);
+        CK(ile_launch_sort(pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));
+        CK(ile_launch_prep(pp, ctx->UV, dsamples, ctx->perm, N, ctx->s, ctx->flags, ctx->stream));
+    }
+    StageScope t(ctx, 5, 1 + (gQ ? 2 : 0) + ((gU || gV) ? 2 : 0));
+    if (g_theta || gQ || lnl)
+        CK(ile_launch_grad_main(pp, ctx->Qp, ctx->UV, ctx->s, ctx->perm, dsamples, dg, N, pig, g_theta, lnl,
+                                ctx->stream));
+    if (gQ) CK(ile_launch_grad_q(pp, pig, ctx->s, N, nsplit, ctx->gq_part, gQ, ctx->stream));
+    if (gU || gV) CK(ile_launch_grad_uv(pp, dsamples, dg, N, nblk, ctx->guv_part, gU, gV, ctx->stream));
+    return ILE_OK;
+}
+
+// Host-pointer wrapper of run_grad: stage inputs, run, copy the requested outputs back.
+ile_status run_grad_host(ile_ctx *ctx, const double *samples, const double *g, int64_t N, double *g_theta,
+                         double *gQ, double *gU, double *gV, double *lnl) {
+    const PointParams &pp = ctx->pp;
+    const size_t nth = (size_t)ILE_NDIM * N, nq = 2 * (size_t)pp.K * pp.M * pp.T_ext,
+                 nuv = 2 * (size_t)pp.K * pp.M * pp.M;
+    CK(ensure_bytes(&ctx->g_out, &ctx->g_out_bytes, sizeof(double) * (nth + nq + 2 * nuv + (size_t)N)));
+    double *d_th = ctx->g_out, *d_q = d_th + nth, *d_u = d_q + nq, *d_v = d_u + nuv, *d_l = d_v + nuv;
+    CK(cudaMemcpyAsync(ctx->theta, samples, sizeof(double) * nth, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->g_in, g, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
+    ile_status st = run_grad(ctx, ctx->theta, ctx->g_in, N, g_theta ? d_th : nullptr, gQ ? d_q : nullptr,
+                             gU ? d_u : nullptr, gV ? d_v : nullptr, lnl ? d_l : nullptr);
+    if (st != ILE_OK) return st;
+    if (g_theta) CK(cudaMemcpyAsync(g_theta, d_th, sizeof(double) * nth, cudaMemcpyDeviceToHost, ctx->stream));
+    if (gQ) CK(cudaMemcpyAsync(gQ, d_q, sizeof(double) * nq, cudaMemcpyDeviceToHost, ctx->stream));
+    if (gU) CK(cudaMemcpyAsync(gU, d_u, sizeof(double) * nuv, cudaMemcpyDeviceToHost, ctx->stream));
+    if (gV) CK(cudaMemcpyAsync(gV, d_v, sizeof(double) * nuv, cudaMemcpyDeviceToHost, ctx->stream));
+    if (lnl) CK(cudaMemcpyAsync(lnl, d_l, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+    return read_flags(ctx);
+}
+
 }  // namespace
 
 extern "C" {
@@ -289,7 +363,8 @@ ile_status ile_destroy(ile_ctx *ctx) {
                     ctx->result,       ctx->flags,      ctx->keys,      ctx->buckets,   ctx->perm,
                     ctx->a_cdf,        ctx->a_lnps,     ctx->a_hist,    ctx->a_hist_fx, ctx->a_pooled,
                     ctx->a_iter_log,   ctx->a_iter_res, ctx->a_lnwp,    ctx->a_lnl,     ctx->a_iter,
-                    ctx->a_bins};
+                    ctx->a_bins,       ctx->pig,        ctx->gq_part,   ctx->guv_part,  ctx->g_in,
+                    ctx->g_out};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (auto &v : ctx->ev)
@@ -441,6 +516,72 @@ ile_status ile_integrate(ile_ctx *ctx, const double *samples, const double *ln_p
     }
     CK(cudaMemcpyAsync(result, ctx->result, 7 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if (lnL_t_out) CK(cudaMemcpyAsync(lnL_t_out, ctx->out, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
+    return read_flags(ctx);
+}
+
+ile_status ile_eval_grad(ile_ctx *ctx, const double *samples, int64_t N, const double *g_lnL, double *g_samples,
+                         double *g_Q, double *g_U, double *g_V, double *lnL_t_out, unsigned flags) {
+    if (!ctx) return ILE_E_ARG;
+    if (!ctx->has_data) return ILE_E_STATE;
+    if (N < 0) return ILE_E_ARG;
+    if (N == 0) return ILE_OK;
+    if (!samples || !g_lnL) return ILE_E_ARG;
+    if (!g_samples && !g_Q && !g_U && !g_V && !lnL_t_out) return ILE_E_ARG;
+    if (N > ILE_GRAD_MAX_SAMPLES) return ILE_E_ARG;
+    DeviceGuard g(ctx->device);
+    ile_status st = ensure_samples(ctx, N);
+    if (st != ILE_OK) return st;
+    if (flags & ILE_DEVICE_PTRS) return run_grad(ctx, samples, g_lnL, N, g_samples, g_Q, g_U, g_V, lnL_t_out);
+    return run_grad_host(ctx, samples, g_lnL, N, g_samples, g_Q, g_U, g_V, lnL_t_out);
+}
+
+ile_status ile_integrate_grad(ile_ctx *ctx, const double *samples, const double *ln_prior, const double *ln_ps,
+                              int64_t N, const double *g_scale, double *result, double *g_samples, double *g_Q,
+                              double *g_U, double *g_V, unsigned flags) {
+    if (!ctx) return ILE_E_ARG;
+    if (!ctx->has_data) return ILE_E_STATE;
+    if (N < 1 || !samples || !result) return ILE_E_ARG;
+    if (N > ILE_GRAD_MAX_SAMPLES) return ILE_E_ARG;
+    DeviceGuard g(ctx->device);
+    ile_status st = ensure_samples(ctx, N);
+    if (st != ILE_OK) return st;
+    st = ensure_out(ctx, sizeof(double) * (size_t)N);
+    if (st != ILE_OK) return st;
+    const int np = ile_mc_partial_count(N);
+    const double *ds = samples, *dlp = ln_prior, *dlps = ln_ps;
+    if (!(flags & ILE_DEVICE_PTRS)) {
+        CK(cudaMemcpyAsync(ctx->theta, samples, sizeof(double) * ILE_NDIM * (size_t)N, cudaMemcpyHostToDevice,
+                           ctx->stream));
+        if (ln_prior) CK(cudaMemcpyAsync(ctx->lnp, ln_prior, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
+        if (ln_ps) CK(cudaMemcpyAsync(ctx->lnps, ln_ps, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
+        ds = ctx->theta;
+        dlp = ln_prior ? ctx->lnp : nullptr;
+        dlps = ln_ps ? ctx->lnps : nullptr;
+    }
+    st = run_eval(ctx, ds, N, ctx->out, 0);
+    if (st != ILE_OK) return st;
+    double *dres = (flags & ILE_DEVICE_PTRS) ? result : ctx->result;
+    {
+        StageScope t(ctx, 3, 3);
+        CK(ile_launch_mc(ctx->out, dlp, dlps, N, ctx->part, np, dres, ctx->stream));
+        const bool dev = (flags & ILE_DEVICE_PTRS) != 0;
+        CK(ile_launch_mc_weights(ctx->out, dlp, dlps, N, dres, dev ? g_scale : nullptr,
+                                 (!dev && g_scale) ? *g_scale : 1.0, ctx->g_in, ctx->stream));
+    }
+    if (flags & ILE_DEVICE_PTRS) return run_grad(ctx, ds, ctx->g_in, N, g_samples, g_Q, g_U, g_V, nullptr);
+    const PointParams &pp = ctx->pp;
+    const size_t nth = (size_t)ILE_NDIM * N, nq = 2 * (size_t)pp.K * pp.M * pp.T_ext,
+                 nuv = 2 * (size_t)pp.K * pp.M * pp.M;
+    CK(ensure_bytes(&ctx->g_out, &ctx->g_out_bytes, sizeof(double) * (nth + nq + 2 * nuv)));
+    double *d_th = ctx->g_out, *d_q = d_th + nth, *d_u = d_q + nq, *d_v = d_u + nuv;
+    st = run_grad(ctx, ds, ctx->g_in, N, g_samples ? d_th : nullptr, g_Q ? d_q : nullptr, g_U ? d_u : nullptr,
+                  g_V ? d_v : nullptr, nullptr);
+    if (st != ILE_OK) return st;
+    CK(cudaMemcpyAsync(result, ctx->result, 7 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (g_samples) CK(cudaMemcpyAsync(g_samples, d_th, sizeof(double) * nth, cudaMemcpyDeviceToHost, ctx->stream));
+    if (g_Q) CK(cudaMemcpyAsync(g_Q, d_q, sizeof(double) * nq, cudaMemcpyDeviceToHost, ctx->stream));
+    if (g_U) CK(cudaMemcpyAsync(g_U, d_u, sizeof(double) * nuv, cudaMemcpyDeviceToHost, ctx->stream));
+    if (g_V) CK(cudaMemcpyAsync(g_V, d_v, sizeof(double) * nuv, cudaMemcpyDeviceToHost, ctx->stream));
     return read_flags(ctx);
 }
 

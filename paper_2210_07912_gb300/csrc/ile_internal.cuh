@@ -137,6 +137,21 @@ cudaError_t ile_launch_tc(int prec, const PointParams &pp, const void *hi, const
 cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo, int TP, int KP, const float *UV,
                            const double *samples, const int *perm, int64_t N, double *out, int full_grid,
                            unsigned *flags, cudaStream_t st);
+// adjoint (ile_adjoint.cu)
+int ile_grad_q_splits(const PointParams &pp, int64_t N, int n_sm);
+int ile_grad_uv_blocks(int64_t N, int n_sm);
+cudaError_t ile_launch_grad_main(const PointParams &pp, const float *Qp, const float *UV, IleScratch s,
+                                 const int *perm, const double *samples, const double *g_lnL, int64_t N, float *pig,
+                                 double *g_samples, double *lnl_out, cudaStream_t st);
+cudaError_t ile_launch_grad_q(const PointParams &pp, const float *pig, IleScratch s, int64_t N, int nsplit,
+                              float *part, double *gQ, cudaStream_t st);
+cudaError_t ile_launch_grad_uv(const PointParams &pp, const double *samples, const double *g_lnL, int64_t N, int nblk,
+                               float *part, double *gU, double *gV, cudaStream_t st);
+// g_n = scale * d ln L_marg / d lnL_t(n) = scale * exp(ln w_n - max) / S1, from the result of
+// ile_launch_mc (ile_mc.cu); scale = *scale_dev when scale_dev is not null
+cudaError_t ile_launch_mc_weights(const double *lnL_t, const double *ln_prior, const double *ln_ps, int64_t N,
+                                  const double *result, const double *scale_dev, double scale, double *g,
+                                  cudaStream_t st);
 cudaError_t ile_launch_mc(const double *lnL_t, const double *ln_prior, const double *ln_ps, int64_t N,
                           double *partials, int n_part, double *result, cudaStream_t st);
 int ile_mc_partial_count(int64_t N);

@@ -86,6 +86,18 @@ __global__ void __launch_bounds__(MC_THREADS) mc_merge_kernel(const double *__re
     result[6] = s2;
 }
 
+// d ln I / d lnL_t(n) = w_n / sum w = exp(ln w_n - max) / S1 (the derivative of Eq. (eq:lnL:MonteCarlo)
+// in log space), with max and S1 from the merged result.
+// The upstream scalar is *scale_dev when given (a device pointer), else scale.
+__global__ void mc_weights_kernel(const double *__restrict__ lnL, const double *__restrict__ lp,
+                                  const double *__restrict__ lps, int64_t N, const double *__restrict__ result,
+                                  const double *__restrict__ scale_dev, double scale, double *__restrict__ g) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const double sc = scale_dev ? *scale_dev : scale;
+    g[n] = sc * exp(lnw_at(lnL, lp, lps, n) - result[4]) / result[5];
+}
+
 }  // namespace
 
 int ile_mc_partial_count(int64_t N) {
@@ -145,4 +157,13 @@ extern "C" ile_status ile_mc_reduce_noalloc(const double *lnL_t, const double *l
     if (ile_launch_mc(lnL_t, ln_prior, ln_ps, N, part, np, result, (cudaStream_t)cuda_stream) != cudaSuccess)
         return ILE_E_CUDA;
     return ILE_OK;
+}
+
+cudaError_t ile_launch_mc_weights(const double *lnL_t, const double *ln_prior, const double *ln_ps, int64_t N,
+                                  const double *result, const double *scale_dev, double scale, double *g,
+                                  cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    mc_weights_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(lnL_t, ln_prior, ln_ps, N, result, scale_dev,
+                                                                   scale, g);
+    return cudaGetLastError();
 }

@@ -112,6 +112,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ile_merge_partials.restype = i32
     lib.ile_mc_reduce_noalloc.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ile_mc_reduce_noalloc.restype = i32
+    lib.ile_eval_grad.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, u]
+    lib.ile_eval_grad.restype = i32
+    lib.ile_integrate_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, u]
+    lib.ile_integrate_grad.restype = i32
     for name in ("ile_create", "ile_destroy", "ile_set_stream", "ile_set_precision", "ile_set_data", "ile_eval",
                  "ile_integrate", "ile_sync", "ile_profile", "ile_profile_read", "ile_adapt_init", "ile_adapt_step",
                  "ile_adapt_get", "ile_adapt_run", "ile_adapt_last"):
@@ -143,6 +147,7 @@ def _stream_handle(stream):
 
 
 NOALLOC_MAX_SAMPLES = 1 << 22
+GRAD_MAX_SAMPLES = 1 << 22
 
 
 def merge_partials(max_lnw, s1, s2, n, hist=None):
@@ -190,6 +195,7 @@ class Context:
         self.device = device
         self.prec = prec
         self.n_window = None
+        self.shape = (0, 0, 0)  # (K, M, T_ext) of the loaded point
 
     def _check(self, st, where):
         if st != ILE_OK:
@@ -227,6 +233,7 @@ class Context:
                                     float(p.gmst), float(p.d_ref))
         self._check(st, "ile_set_data")
         self.n_window = int(p.n_window)
+        self.shape = (K, M, T)
 
     # ---------------------------------------------------------------- host-pointer calls
     def eval(self, samples: np.ndarray, grid: bool = False) -> np.ndarray:
@@ -267,6 +274,74 @@ class Context:
     def sync(self):
         self._check(self._lib.ile_sync(self._h), "ile_sync")
 
+    # ---------------------------------------------------------------- gradients (adjoint kernels)
+    def _grad_shapes(self):
+        K, M, T = self.shape
+        return (K, M, T, 2), (K, M, M, 2)
+
+    def eval_grad(self, samples, g=None, want=("theta", "Q", "U", "V"), want_lnL=False):
+        """Gradient of sum_n g[n] lnL_t(n) (host arrays): dict with the requested entries of
+        theta (7, N), Q (K, M, T, 2), U and V (K, M, M, 2), and lnL (N,) if want_lnL."""
+        s = np.ascontiguousarray(samples, np.float64)
+        N = s.shape[1]
+        gv = np.ones(N) if g is None else np.ascontiguousarray(g, np.float64)
+        qs, us = self._grad_shapes()
+        out = {}
+        if "theta" in want:
+            out["theta"] = np.zeros((NDIM, N))
+        if "Q" in want:
+            out["Q"] = np.zeros(qs)
+        if "U" in want:
+            out["U"] = np.zeros(us)
+        if "V" in want:
+            out["V"] = np.zeros(us)
+        if want_lnL:
+            out["lnL"] = np.zeros(N)
+        st = self._lib.ile_eval_grad(self._h, _np_ptr(s), N, _np_ptr(gv), _np_ptr(out.get("theta")),
+                                     _np_ptr(out.get("Q")), _np_ptr(out.get("U")), _np_ptr(out.get("V")),
+                                     _np_ptr(out.get("lnL")), 0)
+        self._check(st, "ile_eval_grad")
+        return out
+
+    def eval_grad_device(self, samples, g, g_theta=None, g_Q=None, g_U=None, g_V=None, lnL_out=None):
+        """Device-pointer form of eval_grad (CUDA float64 tensors, queued on the context stream)."""
+        N = samples.shape[1]
+        st = self._lib.ile_eval_grad(self._h, _dev_ptr(samples), N, _dev_ptr(g), _dev_ptr(g_theta), _dev_ptr(g_Q),
+                                     _dev_ptr(g_U), _dev_ptr(g_V), _dev_ptr(lnL_out), ILE_DEVICE_PTRS)
+        self._check(st, "ile_eval_grad")
+
+    def integrate_grad(self, samples, ln_prior=None, ln_ps=None, want=("theta", "Q", "U", "V")):
+        """ln L_marg (dict as integrate) and its gradient through lnL_t (dict as eval_grad)."""
+        s = np.ascontiguousarray(samples, np.float64)
+        N = s.shape[1]
+        lp = None if ln_prior is None else np.ascontiguousarray(ln_prior, np.float64)
+        lps = None if ln_ps is None else np.ascontiguousarray(ln_ps, np.float64)
+        qs, us = self._grad_shapes()
+        out = {}
+        if "theta" in want:
+            out["theta"] = np.zeros((NDIM, N))
+        if "Q" in want:
+            out["Q"] = np.zeros(qs)
+        if "U" in want:
+            out["U"] = np.zeros(us)
+        if "V" in want:
+            out["V"] = np.zeros(us)
+        res = np.zeros(7)
+        st = self._lib.ile_integrate_grad(self._h, _np_ptr(s), _np_ptr(lp), _np_ptr(lps), N, None, _np_ptr(res),
+                                          _np_ptr(out.get("theta")), _np_ptr(out.get("Q")), _np_ptr(out.get("U")),
+                                          _np_ptr(out.get("V")), 0)
+        self._check(st, "ile_integrate_grad")
+        d = dict(ln_L=res[0], sigma_ln=res[1], n_eff=res[2], ess=res[3], m=res[4], s1=res[5], s2=res[6])
+        return d, out
+
+    def integrate_grad_device(self, samples, result, g_scale=None, ln_prior=None, ln_ps=None, g_theta=None,
+                              g_Q=None, g_U=None, g_V=None):
+        N = samples.shape[1]
+        st = self._lib.ile_integrate_grad(self._h, _dev_ptr(samples), _dev_ptr(ln_prior), _dev_ptr(ln_ps), N,
+                                          _dev_ptr(g_scale), _dev_ptr(result), _dev_ptr(g_theta), _dev_ptr(g_Q),
+                                          _dev_ptr(g_U), _dev_ptr(g_V), ILE_DEVICE_PTRS)
+        self._check(st, "ile_integrate_grad")
+
     # ---------------------------------------------------------------- adaptive integrator
     def adapt_init(self, cfg: AdaptCfg, resume: AdaptResult | None = None):
         self._check(self._lib.ile_adapt_init(self._h, ctypes.byref(cfg), ctypes.byref(resume) if resume else None),
@@ -298,7 +373,7 @@ class Context:
         return theta, lw, bins, lnl
 
     # ---------------------------------------------------------------- stage timing
-    STAGES = ("sample", "prep", "contract", "mc", "adapt")
+    STAGES = ("sample", "prep", "contract", "mc", "adapt", "grad")
 
     def profile(self, enable: bool = True):
         self._check(self._lib.ile_profile(self._h, 1 if enable else 0), "ile_profile")

@@ -225,6 +225,84 @@ ile_status ile_merge_partials(int n_shards, const double *max_lnw, const double 
                               const double *n, const double *hist /* [n_shards][7][100] or NULL */,
                               double *result, double *hist_out /* [7][100] or NULL */);
 
+/* ------------------------------------------------------------------ batched adaptive run */
+
+#define ILE_BATCH_MAX_POINTS 4096
+#define ILE_TUNE_MAX 16
+
+/* One intrinsic point of a batch: the ile_set_data arguments plus its sampler (as in
+ * ile_adapt_cfg; n_iter is given to ile_batch_step instead).  Host pointers, copied by
+ * ile_batch_set_points. */
+typedef struct {
+    int n_det, n_modes;
+    const int *lm;
+    const double *det_tensor, *det_pos_m, *Q;
+    int T_ext;
+    double t_start_s, fs_hz;
+    const double *U, *V;
+    int n_window;
+    double gmst_rad, d_ref_mpc;
+    int64_t n_samples; /* samples per iteration, 1 .. 2^23 */
+    uint64_t seed;
+    uint32_t point_id;
+    uint32_t adapt_mask;
+    double eps;
+    double lo[ILE_NDIM], hi[ILE_NDIM];
+} ile_point_desc;
+
+typedef struct ile_batch ile_batch; /* opaque; owns the device copies of all points */
+
+/* Result of ile_batch_tune: the chosen configuration of the fused kernel (B-ring depth nb, job
+ * window width nwcol in time columns, persistent CTAs grid), its time per launch, and every
+ * combination tried. */
+typedef struct {
+    int nb, nwcol, grid;
+    float ms;
+    int n_tried;
+    int tried_nb[ILE_TUNE_MAX], tried_nwcol[ILE_TUNE_MAX];
+    float tried_ms[ILE_TUNE_MAX];
+} ile_batch_tuning;
+
+/*
+ * Batched adaptive Monte Carlo integration of many intrinsic points (each with its own Q/U/V,
+ * detectors, modes, window, sample budget and sampler), Sec. "GPU-accelerated Monte Carlo
+ * integration" applied point by point.  Per iteration, all points are sampled, delay-sorted,
+ * evaluated and their integrals and histograms updated by a fixed launch sequence captured once
+ * in a CUDA graph; with ILE_PREC_BF16X3 the likelihood of every (point, 128-sample tile) work item
+ * runs in ONE persistent launch of the fused tensor-core kernel, longest items first.  Each
+ * point's result equals (bit for bit) an ile_adapt_run of that point alone with the same seed,
+ * point_id and ranges.
+ *   ile_batch_create: cuda_stream NULL = a stream owned by the batch (graphs cannot be captured
+ *     on the legacy default stream).
+ *   ile_batch_set_points: copies and validates every point (ILE_E_ARG / ILE_E_NONFINITE as
+ *     ile_set_data and ile_adapt_init), allocates the per-sample arrays (about 90 bytes per
+ *     sample per iteration) and resets every sampler.  1 <= n_points <= ILE_BATCH_MAX_POINTS.
+ *   ile_batch_reset: uniform tables, empty accumulators, iteration 0 for every point.
+ *   ile_batch_step: queue n_iter iterations (asynchronous on the batch stream).
+ *   ile_batch_get: results of points first .. first + count - 1 (waits for the stream; returns
+ *     the first device-side error, as ile_sync).
+ *   ile_batch_run: set_points + step(n_iter) + get of all points; out has n_points entries.
+ *   ile_batch_last_samples: the last iteration's samples [7][N] and lnL_t [N] of one point (host).
+ *   ile_batch_config: set the fused kernel's B-ring depth (2..4, if it fits in shared memory),
+ *     window width and CTA count by hand.
+ *   ile_batch_tune: autotuner -- runs one iteration to have samples, then times the fused
+ *     kernel over that iteration's work items for every admissible (nb, nwcol), reps launches
+ *     each, and keeps the fastest (BF16X3 only; else ILE_E_STATE).  The sampler advances by one
+ *     iteration: call ile_batch_reset before the run that counts.
+ */
+ile_status ile_batch_create(ile_batch **out, int device, void *cuda_stream, ile_prec prec);
+ile_status ile_batch_destroy(ile_batch *b);
+ile_status ile_batch_set_points(ile_batch *b, int n_points, const ile_point_desc *points);
+ile_status ile_batch_reset(ile_batch *b);
+ile_status ile_batch_step(ile_batch *b, int n_iter);
+ile_status ile_batch_get(ile_batch *b, int first, int count, ile_adapt_result *out);
+ile_status ile_batch_run(ile_batch *b, int n_points, const ile_point_desc *points, int n_iter,
+                         ile_adapt_result *out);
+ile_status ile_batch_last_samples(ile_batch *b, int point, double *theta, double *lnL_t);
+ile_status ile_batch_config(ile_batch *b, int nb, int nwcol, int grid);
+ile_status ile_batch_tune(ile_batch *b, int reps, ile_batch_tuning *out);
+const char *ile_batch_last_error(const ile_batch *b);
+
 /* ------------------------------------------------------------------ gradients (adjoint) */
 
 #define ILE_GRAD_MAX_SAMPLES (1 << 22)

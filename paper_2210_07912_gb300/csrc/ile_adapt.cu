@@ -50,22 +50,26 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
 // Uniform in (0, 1) from the top 23 bits of a word (exact in FP32).
 __device__ __forceinline__ float unit23(uint32_t w) { return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f); }
 
-__global__ void __launch_bounds__(256) sample_kernel(IleSamplerParams sp, const uint64_t *__restrict__ cdf,
-                                                     const float *__restrict__ lnps_tab,
-                                                     const int *__restrict__ iter_dev, int64_t N,
-                                                     double *__restrict__ theta, double *__restrict__ lnw_prior,
-                                                     uint8_t *__restrict__ bins) {
-    __shared__ uint32_t cdf_s[ND][NB + 1];  // low 32 bits; cdf[100] = 2^32 is never compared against
-    __shared__ float lnps_s[ND][NB];
+struct SamplerTables {
+    uint32_t cdf[ND][NB + 1];  // low 32 bits; cdf[100] = 2^32 is never compared against
+    float lnps[ND][NB];
+};
+
+__device__ __forceinline__ void load_tables(SamplerTables &t, const uint64_t *__restrict__ cdf,
+                                            const float *__restrict__ lnps_tab) {
     for (int i = threadIdx.x; i < ND * (NB + 1); i += blockDim.x) {
         const int d = i / (NB + 1), b = i % (NB + 1);
-        cdf_s[d][b] = (uint32_t)cdf[i];
-        if (b < NB) lnps_s[d][b] = lnps_tab[d * NB + b];
+        t.cdf[d][b] = (uint32_t)cdf[i];
+        if (b < NB) t.lnps[d][b] = lnps_tab[d * NB + b];
     }
-    __syncthreads();
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    const uint32_t iter = (uint32_t)(*iter_dev);
+}
+
+// Sample n of N (one point): theta [7][N], ln p - ln p_s, bins [7][N].
+__device__ __forceinline__ void sample_one(const IleSamplerParams &sp, const SamplerTables &tb, uint32_t iter,
+                                           int64_t n, int64_t N, double *__restrict__ theta,
+                                           double *__restrict__ lnw_prior, uint8_t *__restrict__ bins) {
+    const uint32_t(&cdf_s)[ND][NB + 1] = tb.cdf;
+    const float(&lnps_s)[ND][NB] = tb.lnps;
     uint32_t wds[16];
 #pragma unroll
     for (uint32_t blk = 0; blk < 4; blk++)
@@ -102,18 +106,45 @@ __global__ void __launch_bounds__(256) sample_kernel(IleSamplerParams sp, const 
     lnw_prior[n] = (double)lw;
 }
 
+__global__ void __launch_bounds__(256) sample_kernel(IleSamplerParams sp, const uint64_t *__restrict__ cdf,
+                                                     const float *__restrict__ lnps_tab,
+                                                     const int *__restrict__ iter_dev, int64_t N,
+                                                     double *__restrict__ theta, double *__restrict__ lnw_prior,
+                                                     uint8_t *__restrict__ bins) {
+    __shared__ SamplerTables tb;
+    load_tables(tb, cdf, lnps_tab);
+    __syncthreads();
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    sample_one(sp, tb, (uint32_t)(*iter_dev), n, N, theta, lnw_prior, bins);
+}
+
+// Batched: block b draws samples start .. start + 255 of point blk[b].x (blk[b].y = start).
+__global__ void __launch_bounds__(256) bsample_kernel(const IleBatchPoint *__restrict__ bp,
+                                                      const int2 *__restrict__ blk, const uint64_t *__restrict__ cdf,
+                                                      const float *__restrict__ lnps_tab,
+                                                      const int *__restrict__ iter_dev, double *__restrict__ theta,
+                                                      double *__restrict__ lnw_prior, uint8_t *__restrict__ bins) {
+    __shared__ SamplerTables tb;
+    const int p = blk[blockIdx.x].x;
+    const IleBatchPoint &pt = bp[p];
+    load_tables(tb, cdf + (size_t)p * ND * (NB + 1), lnps_tab + (size_t)p * ND * NB);
+    __syncthreads();
+    const int64_t n = (int64_t)blk[blockIdx.x].y + threadIdx.x;
+    if (n >= pt.N) return;
+    sample_one(pt.sp, tb, (uint32_t)iter_dev[p], n, pt.N, theta + ND * pt.off, lnw_prior + pt.off, bins + ND * pt.off);
+}
+
 // Histograms of w_n = exp(ln w_n - max) over each adaptive dimension, as 2^-40 fixed point:
 // per-block shared-memory integer atomics, then one integer atomic per (d, b) and block.
-__global__ void __launch_bounds__(HIST_THREADS) hist_kernel(const double *__restrict__ lnL,
-                                                            const double *__restrict__ lnw_prior,
-                                                            const uint8_t *__restrict__ bins, int64_t N,
-                                                            const double *__restrict__ iter_res, unsigned mask,
-                                                            unsigned long long *__restrict__ hist_fx) {
-    __shared__ unsigned long long h[ND * NB];
+__device__ __forceinline__ void hist_chunk(const double *__restrict__ lnL, const double *__restrict__ lnw_prior,
+                                           const uint8_t *__restrict__ bins, int64_t N, int64_t beg,
+                                           const double *__restrict__ iter_res, unsigned mask,
+                                           unsigned long long *__restrict__ hist_fx, unsigned long long *h) {
     for (int i = threadIdx.x; i < ND * NB; i += blockDim.x) h[i] = 0ull;
     __syncthreads();
     const double m = iter_res[4];  // max ln w of this iteration
-    const int64_t beg = (int64_t)blockIdx.x * HIST_CHUNK, end = min(N, beg + HIST_CHUNK);
+    const int64_t end = min(N, beg + HIST_CHUNK);
     for (int64_t n = beg + threadIdx.x; n < end; n += blockDim.x) {
         const float w = __expf((float)(lnL[n] + lnw_prior[n] - m));
         const unsigned long long wf = (unsigned long long)(w * 1099511627776.0f);  // w * 2^40
@@ -126,15 +157,39 @@ __global__ void __launch_bounds__(HIST_THREADS) hist_kernel(const double *__rest
         if (h[i]) atomicAdd(&hist_fx[i], h[i]);
 }
 
+__global__ void __launch_bounds__(HIST_THREADS) hist_kernel(const double *__restrict__ lnL,
+                                                            const double *__restrict__ lnw_prior,
+                                                            const uint8_t *__restrict__ bins, int64_t N,
+                                                            const double *__restrict__ iter_res, unsigned mask,
+                                                            unsigned long long *__restrict__ hist_fx) {
+    __shared__ unsigned long long h[ND * NB];
+    hist_chunk(lnL, lnw_prior, bins, N, (int64_t)blockIdx.x * HIST_CHUNK, iter_res, mask, hist_fx, h);
+}
+
+// Batched: block b takes the HIST_CHUNK samples from blk[b].y of point blk[b].x.
+__global__ void __launch_bounds__(HIST_THREADS) bhist_kernel(const IleBatchPoint *__restrict__ bp,
+                                                             const int2 *__restrict__ blk,
+                                                             const double *__restrict__ lnL,
+                                                             const double *__restrict__ lnw_prior,
+                                                             const uint8_t *__restrict__ bins,
+                                                             const double *__restrict__ iter_res,
+                                                             unsigned long long *__restrict__ hist_fx) {
+    __shared__ unsigned long long h[ND * NB];
+    const int p = blk[blockIdx.x].x;
+    const IleBatchPoint &pt = bp[p];
+    hist_chunk(lnL + pt.off, lnw_prior + pt.off, bins + ND * pt.off, pt.N, blk[blockIdx.x].y, iter_res + 8 * p,
+               pt.sp.adapt_mask, hist_fx + (size_t)p * ND * NB, h);
+}
+
 // Next integer tables from the histogram, the ln p_s table, the pooled accumulators and the
 // iteration counter.  Threads d < ND build the tables of the adaptive dimensions (sequential
 // FP64 accumulation, bit-reproducible); all threads then fill ln p_s.
-__global__ void __launch_bounds__(1024) renorm_kernel(unsigned long long *__restrict__ hist_fx, unsigned mask,
-                                                      double eps, IleSamplerParams sp, double *__restrict__ hist,
-                                                      uint64_t *__restrict__ cdf, float *__restrict__ lnps_tab,
-                                                      const double *__restrict__ iter_res, int64_t N,
-                                                      double *__restrict__ pooled, double *__restrict__ iter_log,
-                                                      int *__restrict__ iter_dev, int update_tables) {
+__device__ __forceinline__ void renorm_point(unsigned long long *__restrict__ hist_fx, unsigned mask, double eps,
+                                             const IleSamplerParams &sp, double *__restrict__ hist,
+                                             uint64_t *__restrict__ cdf, float *__restrict__ lnps_tab,
+                                             const double *__restrict__ iter_res, int64_t N,
+                                             double *__restrict__ pooled, double *__restrict__ iter_log,
+                                             int *__restrict__ iter_dev, int update_tables) {
     const int i = threadIdx.x;
     for (int j = i; j < ND * NB; j += blockDim.x) {
         hist[j] = (double)hist_fx[j] * (1.0 / 1099511627776.0);
@@ -191,9 +246,34 @@ __global__ void __launch_bounds__(1024) renorm_kernel(unsigned long long *__rest
     *iter_dev = it + 1;
 }
 
+__global__ void __launch_bounds__(1024) renorm_kernel(unsigned long long *__restrict__ hist_fx, unsigned mask,
+                                                      double eps, IleSamplerParams sp, double *__restrict__ hist,
+                                                      uint64_t *__restrict__ cdf, float *__restrict__ lnps_tab,
+                                                      const double *__restrict__ iter_res, int64_t N,
+                                                      double *__restrict__ pooled, double *__restrict__ iter_log,
+                                                      int *__restrict__ iter_dev, int update_tables) {
+    renorm_point(hist_fx, mask, eps, sp, hist, cdf, lnps_tab, iter_res, N, pooled, iter_log, iter_dev, update_tables);
+}
+
+// Batched: one block per point.
+__global__ void __launch_bounds__(1024) brenorm_kernel(const IleBatchPoint *__restrict__ bp,
+                                                       unsigned long long *__restrict__ hist_fx,
+                                                       double *__restrict__ hist, uint64_t *__restrict__ cdf,
+                                                       float *__restrict__ lnps_tab,
+                                                       const double *__restrict__ iter_res,
+                                                       double *__restrict__ pooled, double *__restrict__ iter_log,
+                                                       int *__restrict__ iter_dev) {
+    const int p = blockIdx.x;
+    const IleBatchPoint &pt = bp[p];
+    renorm_point(hist_fx + (size_t)p * ND * NB, pt.sp.adapt_mask, pt.eps, pt.sp, hist + (size_t)p * ND * NB,
+                 cdf + (size_t)p * ND * (NB + 1), lnps_tab + (size_t)p * ND * NB, iter_res + 8 * p, pt.N,
+                 pooled + 4 * p, iter_log + (size_t)2 * ILE_ADAPT_LOG * p, iter_dev + p, 1);
+}
+
 // Uniform tables and the matching ln p_s for every dimension.
-__global__ void reset_kernel(IleSamplerParams sp, uint64_t *__restrict__ cdf, float *__restrict__ lnps_tab,
-                             double *__restrict__ pooled, int *__restrict__ iter_dev, int iter0) {
+__device__ __forceinline__ void reset_point(const IleSamplerParams &sp, uint64_t *__restrict__ cdf,
+                                            float *__restrict__ lnps_tab, double *__restrict__ pooled,
+                                            int *__restrict__ iter_dev, int iter0) {
     const int i = threadIdx.x;
     for (int j = i; j < ND * (NB + 1); j += blockDim.x) {
         const int b = j % (NB + 1);
@@ -211,6 +291,26 @@ __global__ void reset_kernel(IleSamplerParams sp, uint64_t *__restrict__ cdf, fl
         pooled[1] = pooled[2] = pooled[3] = 0.0;
         *iter_dev = iter0;
     }
+}
+
+__global__ void reset_kernel(IleSamplerParams sp, uint64_t *__restrict__ cdf, float *__restrict__ lnps_tab,
+                             double *__restrict__ pooled, int *__restrict__ iter_dev, int iter0) {
+    reset_point(sp, cdf, lnps_tab, pooled, iter_dev, iter0);
+}
+
+// Batched: one block per point; also clears the point's histogram accumulators and log.
+__global__ void breset_kernel(const IleBatchPoint *__restrict__ bp, uint64_t *__restrict__ cdf,
+                              float *__restrict__ lnps_tab, double *__restrict__ pooled, int *__restrict__ iter_dev,
+                              unsigned long long *__restrict__ hist_fx, double *__restrict__ hist,
+                              double *__restrict__ iter_log) {
+    const int p = blockIdx.x;
+    for (int j = threadIdx.x; j < ND * NB; j += blockDim.x) {
+        hist_fx[(size_t)p * ND * NB + j] = 0ull;
+        hist[(size_t)p * ND * NB + j] = 0.0;
+    }
+    for (int j = threadIdx.x; j < 2 * ILE_ADAPT_LOG; j += blockDim.x) iter_log[(size_t)2 * ILE_ADAPT_LOG * p + j] = 0.0;
+    reset_point(bp[p].sp, cdf + (size_t)p * ND * (NB + 1), lnps_tab + (size_t)p * ND * NB, pooled + 4 * p,
+                iter_dev + p, 0);
 }
 
 // Refresh ln p_s from externally supplied tables (resume).
@@ -254,5 +354,34 @@ cudaError_t ile_launch_adapt(const double *lnL, const double *lnw_prior, const u
     hist_kernel<<<np, HIST_THREADS, 0, st>>>(lnL, lnw_prior, bins, N, iter_res, sp.adapt_mask, hist_fx);
     renorm_kernel<<<1, 1024, 0, st>>>(hist_fx, sp.adapt_mask, eps, sp, hist, cdf, lnps_tab, iter_res, N, pooled,
                                       iter_log, iter_dev, update_tables);
+    return cudaGetLastError();
+}
+
+cudaError_t ile_launch_batch_reset(int n_points, const IleBatchPoint *bp, uint64_t *cdf, float *lnps_tab,
+                                   double *pooled, int *iter_dev, unsigned long long *hist_fx, double *hist,
+                                   double *iter_log, cudaStream_t st) {
+    if (n_points <= 0) return cudaSuccess;
+    breset_kernel<<<n_points, 1024, 0, st>>>(bp, cdf, lnps_tab, pooled, iter_dev, hist_fx, hist, iter_log);
+    return cudaGetLastError();
+}
+
+cudaError_t ile_launch_batch_sample(const IleBatchPoint *bp, const int2 *blk256, int n_blk, const uint64_t *cdf,
+                                    const float *lnps_tab, const int *iter_dev, double *theta, double *lnw_prior,
+                                    uint8_t *bins, cudaStream_t st) {
+    if (n_blk <= 0) return cudaSuccess;
+    bsample_kernel<<<n_blk, 256, 0, st>>>(bp, blk256, cdf, lnps_tab, iter_dev, theta, lnw_prior, bins);
+    return cudaGetLastError();
+}
+
+int ile_hist_chunk() { return HIST_CHUNK; }
+
+cudaError_t ile_launch_batch_adapt(int n_points, const IleBatchPoint *bp, const int2 *hblk, int n_hblk,
+                                   const double *lnL, const double *lnw_prior, const uint8_t *bins,
+                                   const double *iter_res, unsigned long long *hist_fx, double *hist, uint64_t *cdf,
+                                   float *lnps_tab, double *pooled, double *iter_log, int *iter_dev,
+                                   cudaStream_t st) {
+    if (n_hblk > 0)
+        bhist_kernel<<<n_hblk, HIST_THREADS, 0, st>>>(bp, hblk, lnL, lnw_prior, bins, iter_res, hist_fx);
+    brenorm_kernel<<<n_points, 1024, 0, st>>>(bp, hist_fx, hist, cdf, lnps_tab, iter_res, pooled, iter_log, iter_dev);
     return cudaGetLastError();
 }

@@ -385,10 +385,44 @@ ile_status ile_set_precision(ile_ctx *ctx, ile_prec prec) {
     return ILE_OK;
 }
 
-ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, const double *det_tensor,
-                        const double *det_pos_m, const double *Q, int T_ext, double t_start_s, double fs_hz,
-                        const double *U, const double *V, int n_window, double gmst_rad, double d_ref_mpc) {
-    if (!ctx || !lm || !det_tensor || !det_pos_m || !Q || !U || !V) return ILE_E_ARG;
+}  // extern "C"
+
+// Pooled accumulators (max ln w, S1, S2, n) and the iteration log -> the summary fields of an
+// ile_adapt_result (cdf and hist are filled by the caller).
+void ile_fill_result(const double pooled[4], const double *ilog, int n_iter, ile_adapt_result *out) {
+    out->max_lnw = pooled[0];
+    out->s1 = pooled[1];
+    out->s2 = pooled[2];
+    out->n_total = pooled[3];
+    out->n_iter = n_iter;
+    for (int i = 0; i < ILE_ADAPT_LOG; i++) {
+        out->iter_ln_L[i] = ilog[2 * i];
+        out->iter_n_eff[i] = ilog[2 * i + 1];
+    }
+    const double Nd = pooled[3];
+    if (Nd > 0) {
+        const double mean = pooled[1] / Nd;
+        double var = (pooled[2] - Nd * mean * mean) / (Nd - 1.0);
+        if (var < 0.0) var = 0.0;
+        out->ln_L = pooled[0] + log(mean);
+        out->sigma_ln = Nd > 1 ? sqrt(var / Nd) / mean : INFINITY;
+        out->n_eff = pooled[1];
+        out->ess = pooled[1] * pooled[1] / pooled[2];
+    } else {
+        out->ln_L = -INFINITY;
+        out->sigma_ln = INFINITY;
+        out->n_eff = out->ess = 0.0;
+    }
+}
+
+// Validate one intrinsic point and build its device-side description: PointParams, the FP32
+// split rows Qp [K][2M][T_ext] and the packed U/V pairs [K][P][4] (shared by ile_set_data and
+// the batched run).
+ile_status ile_prepare_point(int n_det, int n_modes, const int *lm, const double *det_tensor,
+                             const double *det_pos_m, const double *Q, int T_ext, double t_start_s, double fs_hz,
+                             const double *U, const double *V, int n_window, double gmst_rad, double d_ref_mpc,
+                             PointParams &pp_out, std::vector<float> &qp, std::vector<float> &uv) {
+    if (!lm || !det_tensor || !det_pos_m || !Q || !U || !V) return ILE_E_ARG;
     if (n_det < 1 || n_det > ILE_MAX_DET || n_modes < 1 || n_modes > ILE_MAX_MODES) return ILE_E_ARG;
     if (n_window < 1 || n_window > ILE_MAX_WINDOW || T_ext < 2 || T_ext > ILE_MAX_TEXT) return ILE_E_ARG;
     if (!(fs_hz > 0) || !(d_ref_mpc > 0)) return ILE_E_ARG;
@@ -419,7 +453,7 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
         for (int i = 0; i < 9; i++) pp.det_tensor[k][i] = (float)det_tensor[9 * k + i];
         for (int i = 0; i < 3; i++) pp.det_pos_c[k][i] = (float)(det_pos_m[3 * k + i] / ILE_C_SI);
     }
-    std::vector<float> qp((size_t)K * R * T);
+    qp.assign((size_t)K * R * T, 0.f);
     for (int k = 0; k < K; k++)
         for (int a = 0; a < M; a++)
             for (int t = 0; t < T; t++) {
@@ -427,7 +461,7 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
                 qp[((size_t)k * R + a) * T + t] = (float)q[0];
                 qp[((size_t)k * R + M + a) * T + t] = (float)q[1];
             }
-    std::vector<float> uv((size_t)K * P * 4);
+    uv.assign((size_t)K * P * 4, 0.f);
     for (int k = 0; k < K; k++) {
         int p = 0;
         for (int a = 0; a < M; a++)
@@ -442,6 +476,21 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
                 o[3] = (float)(f * v[1]);
             }
     }
+    pp_out = pp;
+    return ILE_OK;
+}
+
+extern "C" {
+
+ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, const double *det_tensor,
+                        const double *det_pos_m, const double *Q, int T_ext, double t_start_s, double fs_hz,
+                        const double *U, const double *V, int n_window, double gmst_rad, double d_ref_mpc) {
+    if (!ctx) return ILE_E_ARG;
+    PointParams pp{};
+    std::vector<float> qp, uv;
+    ile_status st = ile_prepare_point(n_det, n_modes, lm, det_tensor, det_pos_m, Q, T_ext, t_start_s, fs_hz, U, V,
+                                      n_window, gmst_rad, d_ref_mpc, pp, qp, uv);
+    if (st != ILE_OK) return st;
     DeviceGuard g(ctx->device);
     CK(grow(&ctx->Qp, sizeof(float) * qp.size()));
     CK(grow(&ctx->UV, sizeof(float) * uv.size()));
@@ -703,29 +752,7 @@ ile_status ile_adapt_get(ile_ctx *ctx, ile_adapt_result *out) {
     CK(cudaMemcpyAsync(out->cdf, ctx->a_cdf, sizeof(out->cdf), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(out->hist, ctx->a_hist, sizeof(out->hist), cudaMemcpyDeviceToHost, ctx->stream));
     ile_status st = read_flags(ctx);
-    out->max_lnw = pooled[0];
-    out->s1 = pooled[1];
-    out->s2 = pooled[2];
-    out->n_total = pooled[3];
-    out->n_iter = it;
-    for (int i = 0; i < ILE_ADAPT_LOG; i++) {
-        out->iter_ln_L[i] = ilog[2 * i];
-        out->iter_n_eff[i] = ilog[2 * i + 1];
-    }
-    const double Nd = pooled[3];
-    if (Nd > 0) {
-        const double mean = pooled[1] / Nd;
-        double var = (pooled[2] - Nd * mean * mean) / (Nd - 1.0);
-        if (var < 0.0) var = 0.0;
-        out->ln_L = pooled[0] + log(mean);
-        out->sigma_ln = Nd > 1 ? sqrt(var / Nd) / mean : INFINITY;
-        out->n_eff = pooled[1];
-        out->ess = pooled[1] * pooled[1] / pooled[2];
-    } else {
-        out->ln_L = -INFINITY;
-        out->sigma_ln = INFINITY;
-        out->n_eff = out->ess = 0.0;
-    }
+    ile_fill_result(pooled, ilog, it, out);
     return st;
 }
 

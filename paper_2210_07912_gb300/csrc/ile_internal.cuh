@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "ile.h"
 
 #define ILE_PI_F 3.14159265358979f
@@ -56,6 +58,16 @@ struct IleSamplerParams {
     unsigned adapt_mask;               // bit d: dimension d is drawn from its histogram
     uint32_t key0, key1;               // Philox key (seed)
     uint32_t point;                    // Philox counter word identifying the intrinsic point
+};
+
+// One point of a batched adaptive run (ile_batch.cu): its sampler and the location of its
+// samples in the batch's concatenated per-sample arrays (theta and bins at ILE_NDIM * off,
+// laid out [7][N]; everything else at off).
+struct IleBatchPoint {
+    IleSamplerParams sp;
+    double eps;
+    int64_t N, off;
+    float gmst;
 };
 
 // Per-sample geometry: antenna factors and window placement of detector k.
@@ -110,6 +122,18 @@ __device__ __forceinline__ void ile_half_angle_powers(float iota, float cpow[9],
     }
 }
 
+// One intrinsic point as seen by the fused tensor-core kernel (ile_tc2.cu).
+struct Tc2Point {
+    PointParams pp;
+    const void *Qhi, *Qlo;  // split operand tiles of Q (ile_tc.cu layout)
+    const float *UV;        // [K][P][4]
+    const double *samples;  // SoA [7][N]
+    const int *perm;        // [N] processing order -> caller index
+    double *out;            // [N]
+    int64_t N;
+    int TP, KP;
+};
+
 // ------------------------------------------------------------------ host-side launch wrappers
 // (defined in the .cu files; all take the context's stream)
 struct IleScratch {
@@ -152,6 +176,35 @@ cudaError_t ile_launch_grad_uv(const PointParams &pp, const double *samples, con
 cudaError_t ile_launch_mc_weights(const double *lnL_t, const double *ln_prior, const double *ln_ps, int64_t N,
                                   const double *result, const double *scale_dev, double scale, double *g,
                                   cudaStream_t st);
+// batched adaptive-run kernels (per-point state arrays indexed by point: cdf [P][7][101],
+// lnps [P][7][100], hist_fx / hist [P][7][100], pooled [P][4], iter_log [P][64][2], iter [P],
+// iter_res [P][8]); blk256 / hblk: (point, first sample) of each 256-sample / hist-chunk block
+int ile_hist_chunk();
+cudaError_t ile_launch_batch_reset(int n_points, const IleBatchPoint *bp, uint64_t *cdf, float *lnps_tab,
+                                   double *pooled, int *iter_dev, unsigned long long *hist_fx, double *hist,
+                                   double *iter_log, cudaStream_t st);
+cudaError_t ile_launch_batch_sample(const IleBatchPoint *bp, const int2 *blk256, int n_blk, const uint64_t *cdf,
+                                    const float *lnps_tab, const int *iter_dev, double *theta, double *lnw_prior,
+                                    uint8_t *bins, cudaStream_t st);
+cudaError_t ile_launch_batch_adapt(int n_points, const IleBatchPoint *bp, const int2 *hblk, int n_hblk,
+                                   const double *lnL, const double *lnw_prior, const uint8_t *bins,
+                                   const double *iter_res, unsigned long long *hist_fx, double *hist, uint64_t *cdf,
+                                   float *lnps_tab, double *pooled, double *iter_log, int *iter_dev,
+                                   cudaStream_t st);
+cudaError_t ile_launch_batch_sort(int n_points, const IleBatchPoint *bp, const int2 *blk256, int n_blk,
+                                  const double *theta, int *keys, int *buckets, int *perm, cudaStream_t st);
+int ile_mc_chunk();
+cudaError_t ile_launch_batch_mc(int n_points, const IleBatchPoint *bp, const int2 *mblk, int n_mblk,
+                                const int *mblk_first, const double *lnL, const double *lnw_prior, double *partials,
+                                double *iter_res, cudaStream_t st);
+// batched fused kernel: items are (point, tile) pairs; LK, LM, LKP the largest sizes of the batch
+int ile_tc2_tile();
+size_t ile_tc2_batch_smem(int LK, int LM, int LKP, int NB);
+bool ile_tc2_batch_fits(int LK, int LM, int LKP, int NB);
+// window width (MMA N per job before alignment): default returned, admissible range in lo, hi
+int ile_tc2_nwcol_range(int *lo, int *hi);
+cudaError_t ile_launch_tc2_batch(const Tc2Point *pts_dev, const int2 *items_dev, int64_t nitems, int LK, int LM,
+                                 int LKP, int NB, int nwcol, int grid, unsigned *flags, cudaStream_t st);
 cudaError_t ile_launch_mc(const double *lnL_t, const double *ln_prior, const double *ln_ps, int64_t N,
                           double *partials, int n_part, double *result, cudaStream_t st);
 int ile_mc_partial_count(int64_t N);
@@ -166,3 +219,10 @@ cudaError_t ile_launch_adapt(const double *lnL, const double *lnw_prior, const u
                              const double *iter_res, const IleSamplerParams &sp, double eps,
                              unsigned long long *hist_fx, double *hist, uint64_t *cdf, float *lnps_tab, double *pooled,
                              double *iter_log, int *iter_dev, int update_tables, cudaStream_t st);
+
+// ------------------------------------------------------------------ host helpers (ile_api.cu)
+ile_status ile_prepare_point(int n_det, int n_modes, const int *lm, const double *det_tensor,
+                             const double *det_pos_m, const double *Q, int T_ext, double t_start_s, double fs_hz,
+                             const double *U, const double *V, int n_window, double gmst_rad, double d_ref_mpc,
+                             PointParams &pp_out, std::vector<float> &qp, std::vector<float> &uv);
+void ile_fill_result(const double pooled[4], const double *ilog, int n_iter, ile_adapt_result *out);

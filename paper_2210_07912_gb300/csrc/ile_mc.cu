@@ -33,12 +33,9 @@ __device__ T block_reduce(T v, Op op, T *sh) {
     return r;
 }
 
-__global__ void __launch_bounds__(MC_THREADS) mc_partial_kernel(const double *__restrict__ lnL,
-                                                                const double *__restrict__ lp,
-                                                                const double *__restrict__ lps, int64_t N,
-                                                                double *__restrict__ part) {
-    __shared__ double sh[MC_THREADS / 32];
-    const int64_t beg = (int64_t)blockIdx.x * MC_CHUNK;
+__device__ __forceinline__ void mc_partial_chunk(const double *__restrict__ lnL, const double *__restrict__ lp,
+                                                 const double *__restrict__ lps, int64_t N, int64_t beg,
+                                                 double *__restrict__ part, double *sh) {
     const int64_t end = min(N, beg + MC_CHUNK);
     double m = -INFINITY;
     for (int64_t n = beg + threadIdx.x; n < end; n += MC_THREADS) m = fmax(m, lnw_at(lnL, lp, lps, n));
@@ -52,15 +49,22 @@ __global__ void __launch_bounds__(MC_THREADS) mc_partial_kernel(const double *__
     s1 = block_reduce(s1, [](double a, double b) { return a + b; }, sh);
     s2 = block_reduce(s2, [](double a, double b) { return a + b; }, sh);
     if (threadIdx.x == 0) {
-        part[3 * blockIdx.x + 0] = m;
-        part[3 * blockIdx.x + 1] = s1;
-        part[3 * blockIdx.x + 2] = s2;
+        part[0] = m;
+        part[1] = s1;
+        part[2] = s2;
     }
 }
 
-__global__ void __launch_bounds__(MC_THREADS) mc_merge_kernel(const double *__restrict__ part, int n_part, int64_t N,
-                                                              double *__restrict__ result) {
+__global__ void __launch_bounds__(MC_THREADS) mc_partial_kernel(const double *__restrict__ lnL,
+                                                                const double *__restrict__ lp,
+                                                                const double *__restrict__ lps, int64_t N,
+                                                                double *__restrict__ part) {
     __shared__ double sh[MC_THREADS / 32];
+    mc_partial_chunk(lnL, lp, lps, N, (int64_t)blockIdx.x * MC_CHUNK, part + 3 * blockIdx.x, sh);
+}
+
+__device__ __forceinline__ void mc_merge_body(const double *__restrict__ part, int n_part, int64_t N,
+                                              double *__restrict__ result, double *sh) {
     double m = -INFINITY;
     for (int b = threadIdx.x; b < n_part; b += MC_THREADS) m = fmax(m, part[3 * b]);
     m = block_reduce(m, [](double a, double b) { return fmax(a, b); }, sh);
@@ -86,6 +90,34 @@ __global__ void __launch_bounds__(MC_THREADS) mc_merge_kernel(const double *__re
     result[6] = s2;
 }
 
+__global__ void __launch_bounds__(MC_THREADS) mc_merge_kernel(const double *__restrict__ part, int n_part, int64_t N,
+                                                              double *__restrict__ result) {
+    __shared__ double sh[MC_THREADS / 32];
+    mc_merge_body(part, n_part, N, result, sh);
+}
+
+// Batched (adaptive run: ln w = lnL_t + (ln p - ln p_s)): block b reduces chunk b, which is
+// samples mblk[b].y .. + MC_CHUNK of point mblk[b].x; the merge takes one block per point over
+// its chunks mblk_first[p] .. mblk_first[p + 1].
+__global__ void __launch_bounds__(MC_THREADS) bmc_partial_kernel(const IleBatchPoint *__restrict__ bp,
+                                                                 const int2 *__restrict__ mblk,
+                                                                 const double *__restrict__ lnL,
+                                                                 const double *__restrict__ lnwp,
+                                                                 double *__restrict__ part) {
+    __shared__ double sh[MC_THREADS / 32];
+    const IleBatchPoint &pt = bp[mblk[blockIdx.x].x];
+    mc_partial_chunk(lnL + pt.off, lnwp + pt.off, nullptr, pt.N, mblk[blockIdx.x].y, part + 3 * blockIdx.x, sh);
+}
+
+__global__ void __launch_bounds__(MC_THREADS) bmc_merge_kernel(const IleBatchPoint *__restrict__ bp,
+                                                               const int *__restrict__ first,
+                                                               const double *__restrict__ part,
+                                                               double *__restrict__ iter_res) {
+    __shared__ double sh[MC_THREADS / 32];
+    const int p = blockIdx.x;
+    mc_merge_body(part + 3 * first[p], first[p + 1] - first[p], bp[p].N, iter_res + 8 * p, sh);
+}
+
 // d ln I / d lnL_t(n) = w_n / sum w = exp(ln w_n - max) / S1 (the derivative of Eq. (eq:lnL:MonteCarlo)
 // in log space), with max and S1 from the merged result.
 // The upstream scalar is *scale_dev when given (a device pointer), else scale.
@@ -99,6 +131,17 @@ __global__ void mc_weights_kernel(const double *__restrict__ lnL, const double *
 }
 
 }  // namespace
+
+int ile_mc_chunk() { return MC_CHUNK; }
+
+cudaError_t ile_launch_batch_mc(int n_points, const IleBatchPoint *bp, const int2 *mblk, int n_mblk,
+                                const int *mblk_first, const double *lnL, const double *lnw_prior, double *partials,
+                                double *iter_res, cudaStream_t st) {
+    if (n_mblk <= 0) return cudaSuccess;
+    bmc_partial_kernel<<<n_mblk, MC_THREADS, 0, st>>>(bp, mblk, lnL, lnw_prior, partials);
+    bmc_merge_kernel<<<n_points, MC_THREADS, 0, st>>>(bp, mblk_first, partials, iter_res);
+    return cudaGetLastError();
+}
 
 int ile_mc_partial_count(int64_t N) {
     int64_t p = (N + MC_CHUNK - 1) / MC_CHUNK;

@@ -34,10 +34,9 @@ __device__ __forceinline__ int hilbert_index(int x, int y) {
     return d;
 }
 
-__device__ __forceinline__ int delay_key(const PointParams &pp, const double *__restrict__ samples, int64_t N,
-                                         int64_t n) {
+__device__ __forceinline__ int delay_key(float gmst, const double *__restrict__ samples, int64_t N, int64_t n) {
     const double ra = samples[n], dec = samples[N + n];
-    float lon = (float)(pp.gmst - ra) * (1.0f / (2.0f * ILE_PI_F));
+    float lon = (float)(gmst - ra) * (1.0f / (2.0f * ILE_PI_F));
     lon -= floorf(lon);
     const float sd = 0.5f * (sinf((float)dec) + 1.0f);
     // fminf/fmaxf also map NaN to a valid cell: non-finite samples are flagged elsewhere
@@ -51,18 +50,19 @@ __global__ void __launch_bounds__(256) key_count_kernel(const __grid_constant__ 
                                                         int *__restrict__ keys, int *__restrict__ count) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const int key = delay_key(pp, samples, N, n);
+    const int key = delay_key(pp.gmst, samples, N, n);
     keys[n] = key;
     atomicAdd(&count[key], 1);
 }
 
 // Exclusive scan of NKEY counts in one block of 1024 threads (NKEY / 1024 entries per thread).
 static_assert(NKEY % 1024 == 0, "scan layout");
+// (one block per point in the batched form: block b scans count + b * NKEY)
 __global__ void __launch_bounds__(1024) scan_kernel(int *__restrict__ count) {
     constexpr int PER = NKEY / 1024;
     __shared__ int warp_tot[32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    int *c = count + t * PER;
+    int *c = count + (size_t)blockIdx.x * NKEY + t * PER;
     int local = 0;
 #pragma unroll 4
     for (int i = 0; i < PER; i++) local += c[i];
@@ -100,9 +100,46 @@ __global__ void __launch_bounds__(256) scatter_kernel(const int *__restrict__ ke
     perm[pos] = (int)n;
 }
 
+// Batched: block b keys samples blk[b].y .. + 255 of point blk[b].x (local indices; bucket
+// counts and keys per point).
+__global__ void __launch_bounds__(256) bkey_count_kernel(const IleBatchPoint *__restrict__ bp,
+                                                         const int2 *__restrict__ blk,
+                                                         const double *__restrict__ theta, int *__restrict__ keys,
+                                                         int *__restrict__ count) {
+    const int p = blk[blockIdx.x].x;
+    const IleBatchPoint &pt = bp[p];
+    const int64_t n = (int64_t)blk[blockIdx.x].y + threadIdx.x;
+    if (n >= pt.N) return;
+    const int key = delay_key(pt.gmst, theta + ILE_NDIM * pt.off, pt.N, n);
+    keys[pt.off + n] = key;
+    atomicAdd(&count[(size_t)p * NKEY + key], 1);
+}
+
+__global__ void __launch_bounds__(256) bscatter_kernel(const IleBatchPoint *__restrict__ bp,
+                                                       const int2 *__restrict__ blk, const int *__restrict__ keys,
+                                                       int *__restrict__ cursor, int *__restrict__ perm) {
+    const int p = blk[blockIdx.x].x;
+    const IleBatchPoint &pt = bp[p];
+    const int64_t n = (int64_t)blk[blockIdx.x].y + threadIdx.x;
+    if (n >= pt.N) return;
+    const int pos = atomicAdd(&cursor[(size_t)p * NKEY + keys[pt.off + n]], 1);
+    perm[pt.off + pos] = (int)n;
+}
+
 }  // namespace
 
 size_t ile_sort_key_buckets() { return NKEY; }
+
+cudaError_t ile_launch_batch_sort(int n_points, const IleBatchPoint *bp, const int2 *blk256, int n_blk,
+                                  const double *theta, int *keys, int *buckets, int *perm, cudaStream_t st) {
+    if (n_blk <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(buckets, 0, sizeof(int) * NKEY * (size_t)n_points, st);
+    if (e != cudaSuccess) return e;
+    bkey_count_kernel<<<n_blk, 256, 0, st>>>(bp, blk256, theta, keys, buckets);
+    scan_kernel<<<n_points, 1024, 0, st>>>(buckets);
+    bscatter_kernel<<<n_blk, 256, 0, st>>>(bp, blk256, keys, buckets, perm);
+    return cudaGetLastError();
+}
 
 cudaError_t ile_launch_sort(const PointParams &pp, const double *samples, int64_t N, int *keys, int *buckets,
                             int *perm, cudaStream_t st) {

@@ -43,7 +43,8 @@ constexpr int NTHREADS = NMATH + 64;
 constexpr int JW = 64;                     // window bins per chunk
 constexpr int JG = JW / NGRP;              // bins per thread per chunk
 constexpr int NWIN = 128;                  // columns per TMEM accumulator buffer (= max MMA N here)
-constexpr int NWCOL = 120;                 // window columns (+ up to 7 for 8-column alignment <= NWIN)
+constexpr int NWCOL = 120;                 // default window columns (+ up to 7 for 8-column alignment <= NWIN)
+constexpr int NWCOL_MIN = JW + 2;          // a window must hold one chunk's columns plus the lerp partner
 constexpr uint32_t TMEM_COLS = 2 * NWIN;
 constexpr int NBMAX = 4;                   // B ring depth upper bound
 constexpr int SLEEPS = 200000;             // bounded sleeping waits: SLEEPS x SLEEP_NS at most
@@ -74,12 +75,12 @@ struct Job {
 // Enumerates the jobs of a tile from its per-detector column range [lo_k, hi_k] of window
 // starts; the MMA warp and the math warps walk the same sequence.
 struct JobIter {
-    int Nt, K;
+    int Nt, K, nwcol;
     Det4 lo, hi;
     int c, k, w;
     bool done;
-    __device__ JobIter(int Nt_, int K_, Det4 lo_, Det4 hi_)
-        : Nt(Nt_), K(K_), lo(lo_), hi(hi_), c(0), k(0), w(0), done(false) {}
+    __device__ JobIter(int Nt_, int K_, int nwcol_, Det4 lo_, Det4 hi_)
+        : Nt(Nt_), K(K_), nwcol(nwcol_), lo(lo_), hi(hi_), c(0), k(0), w(0), done(false) {}
     __device__ Job get() const {
         Job j;
         j.j0 = c * JW;
@@ -88,16 +89,16 @@ struct JobIter {
         j.w = w;
         const int col_lo = lo(k) + j.j0, col_hi = hi(k) + j.j0 + j.Jc;  // inclusive
         const int total = col_hi - col_lo + 1;
-        if (total <= NWCOL) {
+        if (total <= nwcol) {
             j.W = 1;
-            j.step = NWCOL;
+            j.step = nwcol;
         } else {
-            j.step = NWCOL - j.Jc - 1;
-            j.W = 1 + (total - NWCOL + j.step - 1) / j.step;
+            j.step = nwcol - j.Jc - 1;
+            j.W = 1 + (total - nwcol + j.step - 1) / j.step;
         }
         j.wbeg = col_lo + w * j.step;
         j.wbeg8 = j.wbeg & ~7;
-        const int nw = min(NWCOL, col_hi - j.wbeg + 1) + (j.wbeg - j.wbeg8);
+        const int nw = min(nwcol, col_hi - j.wbeg + 1) + (j.wbeg - j.wbeg8);
         j.nwr = (nw + 15) & ~15;
         return j;
     }
@@ -132,26 +133,45 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, const 
     return __all_sync(0xffffffffu, wait1(bar, parity, flags));
 }
 
+// Work item `it` of the launch: one 128-sample tile of one intrinsic point.  A single-point
+// launch walks the tiles of `one`; a batched launch walks (point, tile) pairs from `items`.
+template <bool BATCH>
+__device__ __forceinline__ const Tc2Point &work_item(const Tc2Point &one, const Tc2Point *__restrict__ pts,
+                                                     const int2 *__restrict__ items, int64_t it, int64_t &tile) {
+    if constexpr (BATCH) {
+        const int2 w = items[it];
+        tile = w.y;
+        return pts[w.x];
+    } else {
+        tile = it;
+        return one;
+    }
+}
+
+// Shared-memory layout (LK detectors, LKC 16-byte K-chunks, LNP mode pairs: the point's own sizes
+// for a single-point launch, the largest of the batch otherwise):
+//   uvs [LK][LNP] float4 | A [LK][2][LKC][TILE] | B [NB][2][LKC][NWIN] | strips | aq_s | ls_s
+template <bool BATCH>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    ile_tc2_kernel(const __grid_constant__ PointParams pp, const uint4 *__restrict__ Qhi, const uint4 *__restrict__ Qlo,
-                   int TP, int KP, int NB, const float4 *__restrict__ UV, const double *__restrict__ samples,
-                   const int *__restrict__ perm, int64_t N, double *__restrict__ out, int full_grid,
-                   unsigned *flags) {
+    ile_tc2_kernel(const __grid_constant__ Tc2Point one, const Tc2Point *__restrict__ pts,
+                   const int2 *__restrict__ items, int64_t nitems, int LK, int LKC, int LNP, int NB, int nwcol,
+                   int full_grid, unsigned *flags) {
     extern __shared__ __align__(1024) uint8_t dsm[];
     __shared__ Sm sm;
-    const int K = pp.K, M = pp.M, Nt = pp.Nt;
-    const int KC = KP / 8, P = M * (M + 1) / 2;
-    float4 *uvs = reinterpret_cast<float4 *>(dsm);                                   // [K][P]
-    uint4 *A = reinterpret_cast<uint4 *>(dsm + 16 * ((K * P + 63) / 64 * 64));       // [K][2][KC][TILE]
-    uint4 *B = A + (size_t)K * 2 * KC * TILE;                                         // [NB][2][KC][NWIN]
-    float *strip = reinterpret_cast<float *>(B + (size_t)NB * 2 * KC * NWIN);         // [STRIP][NMATH]
+    float4 *uvs = reinterpret_cast<float4 *>(dsm);                                   // [K][NP]
+    uint4 *A = reinterpret_cast<uint4 *>(dsm + 16 * ((LK * LNP + 63) / 64 * 64));    // [K][2][KC][TILE]
+    uint4 *B = A + (size_t)LK * 2 * LKC * TILE;                                       // [NB][2][LKC][NWIN]
+    float *strip = reinterpret_cast<float *>(B + (size_t)NB * 2 * LKC * NWIN);        // [STRIP][NMATH]
     float *aq_s = strip + STRIP * NMATH;                                              // [NGRP][TILE]
     float2 *ls_s = reinterpret_cast<float2 *>(aq_s + NGRP * TILE);                     // [NGRP][TILE]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t ntiles = (N + TILE - 1) / TILE;
 
-    for (int i = tid; i < K * P; i += NTHREADS) uvs[i] = UV[i];
+    if constexpr (!BATCH) {
+        const int n_uv = one.pp.K * (one.pp.M * (one.pp.M + 1) / 2);
+        const float4 *UV = reinterpret_cast<const float4 *>(one.UV);
+        for (int i = tid; i < n_uv; i += NTHREADS) uvs[i] = UV[i];
+    }
     if (warp == MMA_WARP) tmem_alloc(&sm.tmem_base, TMEM_COLS);
     if (tid == 0) {
         for (int b = 0; b < NBMAX; b++) {
@@ -177,14 +197,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------------------------ copy warp
         if (lane == 0) {
             uint32_t gcopy = 0, tiles_done = 0;
-            for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, tiles_done++) {
+            for (int64_t it = blockIdx.x; it < nitems && !failed; it += gridDim.x, tiles_done++) {
+                int64_t tile;
+                const Tc2Point &pt = work_item<BATCH>(one, pts, items, it, tile);
+                const int K = pt.pp.K, Nt = pt.pp.Nt, KC = pt.KP / 8, TP = pt.TP;
+                const uint4 *Qhi = reinterpret_cast<const uint4 *>(pt.Qhi);
+                const uint4 *Qlo = reinterpret_cast<const uint4 *>(pt.Qlo);
                 if (!wait1(&sm.aready, tiles_done & 1u, flags)) {
                     failed = true;
                     break;
                 }
                 Det4 lo, hi;
                 tile_range(sm.wlo, sm.whi, K, lo, hi);
-                for (JobIter cit(Nt, K, lo, hi); !cit.done && !failed; cit.next(), gcopy++) {
+                for (JobIter cit(Nt, K, nwcol, lo, hi); !cit.done && !failed; cit.next(), gcopy++) {
                     const uint32_t bb = gcopy % NB;
                     // the slot is free once the MMAs of job gcopy - NB have completed
                     if (gcopy >= (uint32_t)NB && !wait1(&sm.bempty[bb], ((gcopy / NB) - 1) & 1u, flags)) {
@@ -196,8 +221,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const uint32_t bytes = (uint32_t)j.nwr * KC * 16u;
                     mbar_arrive_expect_tx(&sm.bfull[bb], 2u * bytes);
                     const int64_t src = (((int64_t)j.k * (TP / 8) + j.wbeg8 / 8) * KC) * 8;
-                    bulk_g2s(B + (size_t)(bb * 2) * KC * NWIN, Qhi + src, bytes, &sm.bfull[bb]);
-                    bulk_g2s(B + (size_t)(bb * 2 + 1) * KC * NWIN, Qlo + src, bytes, &sm.bfull[bb]);
+                    uint4 *slot = B + (size_t)bb * 2 * LKC * NWIN;
+                    bulk_g2s(slot, Qhi + src, bytes, &sm.bfull[bb]);
+                    bulk_g2s(slot + (size_t)KC * NWIN, Qlo + src, bytes, &sm.bfull[bb]);
                 }
             }
             if (failed) atomicOr(flags, ILE_FLAG_TIMEOUT);
@@ -207,7 +233,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------------------------ MMA warp
         if (lane == 0) {
             uint32_t gjob = 0, tiles_done = 0;
-            for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, tiles_done++) {
+            for (int64_t it = blockIdx.x; it < nitems && !failed; it += gridDim.x, tiles_done++) {
+                int64_t tile;
+                const Tc2Point &pt = work_item<BATCH>(one, pts, items, it, tile);
+                const int K = pt.pp.K, Nt = pt.pp.Nt, KP = pt.KP, KC = KP / 8;
                 if (!wait1(&sm.aready, tiles_done & 1u, flags)) {
                     failed = true;
                     break;
@@ -215,7 +244,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 Det4 lo, hi;
                 tile_range(sm.wlo, sm.whi, K, lo, hi);
                 fence_after();
-                for (JobIter mit(Nt, K, lo, hi); !mit.done && !failed; mit.next(), gjob++) {
+                for (JobIter mit(Nt, K, nwcol, lo, hi); !mit.done && !failed; mit.next(), gjob++) {
                     const Job j = mit.get();
                     const uint32_t bb = gjob % NB, tb = gjob & 1u;
                     if (!wait1(&sm.bfull[bb], (gjob / NB) & 1u, flags) ||
@@ -227,8 +256,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const uint32_t id = idesc(1, TILE, j.nwr);
                     const uint32_t a_hi = smem_u32(A + (size_t)(j.k * 2 + 0) * KC * TILE);
                     const uint32_t a_lo = smem_u32(A + (size_t)(j.k * 2 + 1) * KC * TILE);
-                    const uint32_t b_hi = smem_u32(B + (size_t)bb * 2 * KC * NWIN);
-                    const uint32_t b_lo = smem_u32(B + (size_t)(bb * 2 + 1) * KC * NWIN);
+                    const uint32_t b_hi = smem_u32(B + (size_t)bb * 2 * LKC * NWIN);
+                    const uint32_t b_lo = smem_u32(B + (size_t)bb * 2 * LKC * NWIN + (size_t)KC * NWIN);
                     const uint32_t d = tmem + tb * NWIN;
                     uint32_t acc = 0;
                     for (int pass = 0; pass < 3; pass++) {
@@ -258,7 +287,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t lane_addr = (uint32_t)(q4 * 32) << 16;
         float *my_strip = strip + tid;             // my_strip[i * NMATH], conflict-free
         uint32_t gjob = 0, tiles_done = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, tiles_done++) {
+        int cur_point = -1;
+        for (int64_t it = blockIdx.x; it < nitems && !failed; it += gridDim.x, tiles_done++) {
+            int64_t tile;
+            const Tc2Point &pt = work_item<BATCH>(one, pts, items, it, tile);
+            const PointParams &pp = pt.pp;
+            const int K = pp.K, M = pp.M, Nt = pp.Nt, KC = pt.KP / 8, NP = M * (M + 1) / 2;
+            const int64_t N = pt.N;
+            const double *__restrict__ samples = pt.samples;
+            const int *__restrict__ perm = pt.perm;
+            double *__restrict__ out = pt.out;
+            if constexpr (BATCH) {
+                // this point's U/V pairs (every math thread is past the previous tile's S4)
+                const int pidx = items[it].x;
+                if (pidx != cur_point) {
+                    const float4 *UV = reinterpret_cast<const float4 *>(pt.UV);
+                    for (int i = tid; i < K * NP; i += NMATH) uvs[i] = UV[i];
+                    cur_point = pidx;
+                }
+            }
             const int64_t p = tile * TILE + row;
             const bool valid = p < N;
             const int64_t src = perm[valid ? p : tile * TILE];
@@ -355,7 +402,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                         for (int k = 0; k < ILE_MAX_DET; k++) {
                             if (k < K) {
-                                const float4 u = uvs[k * P + pidx];
+                                const float4 u = uvs[k * NP + pidx];
                                 au[k] += u.x * qr - u.y * qi;
                                 avr[k] += u.z * pr - u.w * pi;
                                 avi[k] += u.z * pi + u.w * pr;
@@ -408,9 +455,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int jj = 0; jj < JG; jj++) D[jj] = 0.f;
             float m_run = -INFINITY, s_run = 0.f;
-            JobIter it(Nt, K, lo, hi);
-            while (!it.done) {
-                const Job j = it.get();
+            JobIter jit(Nt, K, nwcol, lo, hi);
+            while (!jit.done) {
+                const Job j = jit.get();
                 const uint32_t tb = gjob & 1u;
                 if (!warp_wait(&sm.tfull[tb], (gjob / 2) & 1u, flags)) {
                     failed = true;
@@ -456,7 +503,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
                 gjob++;
-                it.next();
+                jit.next();
                 if (j.k == K - 1 && j.w == j.W - 1) {
                     // chunk complete: S5 log-sum-exp update (or the full grid)
                     if (full_grid) {
@@ -525,25 +572,70 @@ size_t tc2_smem(int K, int M, int KP, int NB) {
            sizeof(float) * STRIP * NMATH + sizeof(float) * NGRP * TILE + sizeof(float2) * NGRP * TILE;
 }
 
+constexpr size_t SMEM_LIMIT = 227 * 1024 - sizeof(Sm) - 64;
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
 }  // namespace
 
 cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo, int TP, int KP, const float *UV,
                            const double *samples, const int *perm, int64_t N, double *out, int full_grid,
                            unsigned *flags, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
-    const size_t limit = 227 * 1024 - sizeof(Sm) - 64;
     int NB = NBMAX;
-    while (NB > 2 && tc2_smem(pp.K, pp.M, KP, NB) > limit) NB--;
+    while (NB > 2 && tc2_smem(pp.K, pp.M, KP, NB) > SMEM_LIMIT) NB--;
     const size_t smem = tc2_smem(pp.K, pp.M, KP, NB);
-    if (smem > limit) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(ile_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(ile_tc2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = sm_count();
     const int64_t ntiles = (N + TILE - 1) / TILE;
     const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-    ile_tc2_kernel<<<grid, NTHREADS, smem, st>>>(pp, (const uint4 *)hi, (const uint4 *)lo, TP, KP, NB,
-                                                 (const float4 *)UV, samples, perm, N, out, full_grid, flags);
+    Tc2Point one{};
+    one.pp = pp;
+    one.Qhi = hi;
+    one.Qlo = lo;
+    one.UV = UV;
+    one.samples = samples;
+    one.perm = perm;
+    one.out = out;
+    one.N = N;
+    one.TP = TP;
+    one.KP = KP;
+    ile_tc2_kernel<false><<<grid, NTHREADS, smem, st>>>(one, nullptr, nullptr, ntiles, pp.K, KP / 8,
+                                                        pp.M * (pp.M + 1) / 2, NB, NWCOL, full_grid, flags);
+    return cudaGetLastError();
+}
+
+int ile_tc2_tile() { return TILE; }
+
+size_t ile_tc2_batch_smem(int LK, int LM, int LKP, int NB) { return tc2_smem(LK, LM, LKP, NB); }
+
+bool ile_tc2_batch_fits(int LK, int LM, int LKP, int NB) { return tc2_smem(LK, LM, LKP, NB) <= SMEM_LIMIT; }
+
+int ile_tc2_nwcol_range(int *lo, int *hi) {
+    *lo = NWCOL_MIN;
+    *hi = NWIN - 7;
+    return NWCOL;
+}
+
+cudaError_t ile_launch_tc2_batch(const Tc2Point *pts_dev, const int2 *items_dev, int64_t nitems, int LK, int LM,
+                                 int LKP, int NB, int nwcol, int grid, unsigned *flags, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    if (NB < 2 || NB > NBMAX || nwcol < NWCOL_MIN || nwcol > NWIN - 7) return cudaErrorInvalidValue;
+    const size_t smem = tc2_smem(LK, LM, LKP, NB);
+    if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(ile_tc2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (grid <= 0) grid = sm_count();
+    if (grid > nitems) grid = (int)nitems;
+    Tc2Point none{};
+    ile_tc2_kernel<true><<<grid, NTHREADS, smem, st>>>(none, pts_dev, items_dev, nitems, LK, LKP / 8,
+                                                       LM * (LM + 1) / 2, NB, nwcol, 0, flags);
     return cudaGetLastError();
 }

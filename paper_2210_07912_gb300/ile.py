@@ -39,6 +39,25 @@ class AdaptResult(ctypes.Structure):
                 ("cdf", (ctypes.c_uint64 * (NBINS + 1)) * NDIM), ("hist", (ctypes.c_double * NBINS) * NDIM)]
 
 
+class PointDesc(ctypes.Structure):
+    _fields_ = [("n_det", ctypes.c_int), ("n_modes", ctypes.c_int), ("lm", ctypes.c_void_p),
+                ("det_tensor", ctypes.c_void_p), ("det_pos_m", ctypes.c_void_p), ("Q", ctypes.c_void_p),
+                ("T_ext", ctypes.c_int), ("t_start_s", ctypes.c_double), ("fs_hz", ctypes.c_double),
+                ("U", ctypes.c_void_p), ("V", ctypes.c_void_p), ("n_window", ctypes.c_int),
+                ("gmst_rad", ctypes.c_double), ("d_ref_mpc", ctypes.c_double), ("n_samples", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("point_id", ctypes.c_uint32), ("adapt_mask", ctypes.c_uint32),
+                ("eps", ctypes.c_double), ("lo", ctypes.c_double * NDIM), ("hi", ctypes.c_double * NDIM)]
+
+
+TUNE_MAX = 16
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("nwcol", ctypes.c_int), ("grid", ctypes.c_int), ("ms", ctypes.c_float),
+                ("n_tried", ctypes.c_int), ("tried_nb", ctypes.c_int * TUNE_MAX),
+                ("tried_nwcol", ctypes.c_int * TUNE_MAX), ("tried_ms", ctypes.c_float * TUNE_MAX)]
+
+
 def default_ranges(fs: float = 4096.0, tc_max: float | None = None, d_min: float = 100.0, d_max: float = 1000.0):
     """Sampling-variable ranges (ra, sin dec, psi, cos iota, phi, D, t_c) of the extrinsic prior."""
     import math
@@ -112,6 +131,21 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ile_merge_partials.restype = i32
     lib.ile_mc_reduce_noalloc.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ile_mc_reduce_noalloc.restype = i32
+    lib.ile_batch_create.argtypes = [P(vp), i32, vp, i32]
+    lib.ile_batch_destroy.argtypes = [vp]
+    lib.ile_batch_set_points.argtypes = [vp, i32, P(PointDesc)]
+    lib.ile_batch_reset.argtypes = [vp]
+    lib.ile_batch_step.argtypes = [vp, i32]
+    lib.ile_batch_get.argtypes = [vp, i32, i32, P(AdaptResult)]
+    lib.ile_batch_run.argtypes = [vp, i32, P(PointDesc), i32, P(AdaptResult)]
+    lib.ile_batch_last_samples.argtypes = [vp, i32, vp, vp]
+    lib.ile_batch_config.argtypes = [vp, i32, i32, i32]
+    lib.ile_batch_tune.argtypes = [vp, i32, P(BatchTuning)]
+    lib.ile_batch_last_error.argtypes = [vp]
+    lib.ile_batch_last_error.restype = ctypes.c_char_p
+    for name in ("ile_batch_create", "ile_batch_destroy", "ile_batch_set_points", "ile_batch_reset", "ile_batch_step",
+                 "ile_batch_get", "ile_batch_run", "ile_batch_last_samples", "ile_batch_config", "ile_batch_tune"):
+        getattr(lib, name).restype = i32
     lib.ile_eval_grad.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, u]
     lib.ile_eval_grad.restype = i32
     lib.ile_integrate_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, u]
@@ -385,3 +419,101 @@ class Context:
         self._check(self._lib.ile_profile_read(self._h, _np_ptr(ms), _np_ptr(cnt), len(self.STAGES)),
                     "ile_profile_read")
         return {s: (float(ms[i]), int(cnt[i])) for i, s in enumerate(self.STAGES)}
+
+
+class Batch:
+    """Batched adaptive run over many intrinsic points (ile_batch_*): one CUDA graph per
+    iteration, the likelihood of all points in one persistent launch of the fused kernel."""
+
+    def __init__(self, device: int = 0, stream=None, prec: str = "bf16x3"):
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        self._check(self._lib.ile_batch_create(ctypes.byref(self._h), device, _stream_handle(stream), PREC[prec]),
+                    "ile_batch_create")
+        self.prec = prec
+        self.n_points = 0
+        self.sizes = []
+
+    def _check(self, st, where):
+        if st != ILE_OK:
+            detail = self._lib.ile_batch_last_error(self._h).decode() if self._h else ""
+            raise IleError(st, where, detail)
+
+    def close(self):
+        if self._h:
+            self._lib.ile_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _descs(points, cfgs):
+        keep, descs = [], (PointDesc * len(points))()
+        for i, (p, c) in enumerate(zip(points, cfgs)):
+            lm = np.ascontiguousarray(p.lm, np.int32)
+            tens = np.ascontiguousarray(p.det_tensor, np.float64)
+            pos = np.ascontiguousarray(p.det_pos, np.float64)
+            Q = np.ascontiguousarray(np.stack([p.Q.real, p.Q.imag], -1), np.float64)
+            U = np.ascontiguousarray(np.stack([p.U.real, p.U.imag], -1), np.float64)
+            V = np.ascontiguousarray(np.stack([p.V.real, p.V.imag], -1), np.float64)
+            keep += [lm, tens, pos, Q, U, V]
+            K, M, T = p.Q.shape
+            d = descs[i]
+            d.n_det, d.n_modes, d.T_ext, d.n_window = K, M, T, int(p.n_window)
+            d.lm, d.det_tensor, d.det_pos_m = lm.ctypes.data, tens.ctypes.data, pos.ctypes.data
+            d.Q, d.U, d.V = Q.ctypes.data, U.ctypes.data, V.ctypes.data
+            d.t_start_s, d.fs_hz, d.gmst_rad, d.d_ref_mpc = float(p.t_start), float(p.fs), float(p.gmst), float(p.d_ref)
+            d.n_samples, d.seed, d.point_id = c.n_per_iter, c.seed, c.point_id
+            d.adapt_mask, d.eps = c.adapt_mask, c.eps
+            for k in range(NDIM):
+                d.lo[k], d.hi[k] = c.lo[k], c.hi[k]
+        return descs, keep
+
+    def set_points(self, points, cfgs):
+        """points: synthetic.Point list; cfgs: AdaptCfg per point (n_per_iter, seed, point_id, ...)."""
+        descs, keep = self._descs(points, cfgs)
+        self._check(self._lib.ile_batch_set_points(self._h, len(points), descs), "ile_batch_set_points")
+        del keep
+        self.n_points = len(points)
+        self.sizes = [int(c.n_per_iter) for c in cfgs]
+
+    def reset(self):
+        self._check(self._lib.ile_batch_reset(self._h), "ile_batch_reset")
+
+    def step(self, n_iter: int = 1):
+        self._check(self._lib.ile_batch_step(self._h, n_iter), "ile_batch_step")
+
+    def get(self, first: int = 0, count: int | None = None, raw: bool = False):
+        count = self.n_points - first if count is None else count
+        res = (AdaptResult * count)()
+        self._check(self._lib.ile_batch_get(self._h, first, count, res), "ile_batch_get")
+        return list(res) if raw else [result_dict(r) for r in res]
+
+    def run(self, points, cfgs, n_iter: int, raw: bool = False):
+        descs, keep = self._descs(points, cfgs)
+        res = (AdaptResult * len(points))()
+        self._check(self._lib.ile_batch_run(self._h, len(points), descs, n_iter, res), "ile_batch_run")
+        del keep
+        self.n_points = len(points)
+        self.sizes = [int(c.n_per_iter) for c in cfgs]
+        return list(res) if raw else [result_dict(r) for r in res]
+
+    def last_samples(self, point: int):
+        N = self.sizes[point]
+        theta, lnl = np.zeros((NDIM, N)), np.zeros(N)
+        self._check(self._lib.ile_batch_last_samples(self._h, point, _np_ptr(theta), _np_ptr(lnl)),
+                    "ile_batch_last_samples")
+        return theta, lnl
+
+    def config(self, nb: int, nwcol: int, grid: int):
+        self._check(self._lib.ile_batch_config(self._h, nb, nwcol, grid), "ile_batch_config")
+
+    def tune(self, reps: int = 2) -> dict:
+        t = BatchTuning()
+        self._check(self._lib.ile_batch_tune(self._h, reps, ctypes.byref(t)), "ile_batch_tune")
+        tried = [(t.tried_nb[i], t.tried_nwcol[i], float(t.tried_ms[i])) for i in range(t.n_tried)]
+        return {"nb": t.nb, "nwcol": t.nwcol, "grid": t.grid, "ms": float(t.ms), "tried": tried}

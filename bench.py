@@ -181,6 +181,93 @@ def profile_traffic(kernel_file, prec):
         return None, digest
 
 
+def batch_bench(ile, S, local, flush, iters=5, n_points=512, plain_iters=1):
+    """The mixed batch: n_points intrinsic points (M in {2,5,9,21}, K in {3,4}, N_t in
+    {256,512,1024}, 2^U(14,20) samples each), `iters` adaptive iterations, tiles chosen by the
+    autotuner, every iteration one CUDA-graph launch; the same batch with the plain FP32
+    contraction for comparison (`plain_iters` iterations)."""
+    import torch
+    descs = S.batch_descs(n_points=n_points)
+    points = [S.make_point(d["seed"], d["n_det"], d["n_modes"], d["n_window"], spectrum="decay") for d in descs]
+    cfgs = [ile.make_adapt_cfg(seed=SEED_ADAPT + 7 * i, n_per_iter=d["n_samples"], adapt_mask=0b11, point_id=i)
+            for i, d in enumerate(descs)]
+    n_iter_samples = sum(d["n_samples"] for d in descs)
+
+    def timed(prec, n_it, tune):
+        b = ile.Batch(local, None, prec)
+        b.set_points(points, cfgs)
+        t = b.tune(reps=1) if tune else None
+        b.reset()
+        b.step(1)  # warm-up iteration (graph instantiation), then restart the run
+        b.get()
+        b.reset()
+        torch.cuda.synchronize()
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.step(n_it)
+        res = b.get()
+        dt = time.perf_counter() - t0
+        b.close()
+        return dt, res, t
+
+    dt, res, tuning = timed("bf16x3", iters, True)
+    line = {"workload": f"{n_points} intrinsic points (M in {{2,5,9,21}}, K in {{3,4}}, N_t in {{256,512,1024}}, "
+                        f"2^U(14,20) samples per point per iteration), {iters} adaptive iterations",
+            "n_points": n_points, "samples_per_iteration": n_iter_samples, "iterations": iters,
+            "value": n_iter_samples * iters / dt, "unit": UNIT, "s_per_iteration": dt / iters,
+            "contraction": "bf16x3, one persistent launch per iteration", "tuning": tuning,
+            "ln_L_marg_first_points": [r["ln_L"] for r in res[:4]],
+            "timing": "host clock around step(iterations) + get (graph launches, stream synchronised)"}
+    if plain_iters:
+        pdt, _, _ = timed("fp32", plain_iters, False)
+        line["plain_fp32"] = {"value": n_iter_samples * plain_iters / pdt, "s_per_iteration": pdt / plain_iters,
+                              "iterations": plain_iters}
+        line["speedup_vs_plain"] = line["value"] / line["plain_fp32"]["value"]
+    return line
+
+
+def adjoint_bench(ile, S, local, stream, flush, steps=10):
+    """Gradient of ln L_marg-style weighted sums: ile_eval_grad over 2^18 samples of the
+    3-detector, 21-mode, 512-bin point, all outputs (theta, Q, U, V), FP32 with FP64 sums."""
+    import torch
+    point = S.config_point(4)
+    N = S.CONFIGS[4]["n_samples"]
+    th = torch.tensor(S.config_samples(4), device="cuda")
+    g = torch.tensor(np.random.default_rng(4).normal(size=N), device="cuda")
+    K, M, T = point.Q.shape
+    gs = torch.empty_like(th)
+    gQ = torch.empty((K, M, T, 2), dtype=torch.float64, device="cuda")
+    gU = torch.empty((K, M, M, 2), dtype=torch.float64, device="cuda")
+    gV = torch.empty_like(gU)
+    ctx = ile.Context(local, stream, "fp32")
+    ctx.set_data(point)
+    for _ in range(3):
+        ctx.eval_grad_device(th, g, gs, gQ, gU, gV)
+    ctx.sync()
+    ctx.profile(True)
+    ctx.profile_read()
+    ms = 0.0
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        ctx.eval_grad_device(th, g, gs, gQ, gU, gV)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    prof = ctx.profile_read()
+    ctx.sync()
+    ctx.close()
+    flops = 16.0 * M * point.n_window * K * N  # forward recompute + E + slope + dQ contractions
+    return {"workload": "gradient of sum_n g_n lnL_t(n) w.r.t. theta (7 x 2^18), Q, U, V: H1/L1/V1, 21 modes, "
+                        "N_t=512, 2^18 samples", "value": N * steps / (ms / 1e3), "unit": UNIT,
+            "ms_per_call": ms / steps, "stage_ms_per_call": {k: v[0] / steps for k, v in prof.items() if v[1]},
+            "algorithmic_tflops": flops / (ms / steps / 1e3) / 1e12, "arithmetic": "fp32 CUDA cores, fp64 sums"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -190,6 +277,9 @@ def main():
     ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32x3", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-point batched run")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) measurement")
+    ap.add_argument("--batch-points", type=int, default=512)
     ap.add_argument("--n-samples", type=int, default=None,
                     help="samples per step (default 2^20, the benchmarked workload; smaller only for profiling)")
     args = ap.parse_args()
@@ -326,6 +416,10 @@ def main():
                            "iterations": res["n_iter"]}}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(point)
+        if not args.no_adjoint:
+            line["adjoint"] = adjoint_bench(ile, S, local, stream, flush)
+        if not args.no_batch:
+            line["batch"] = batch_bench(ile, S, local, flush, n_points=args.batch_points)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

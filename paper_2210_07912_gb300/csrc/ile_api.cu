@@ -17,6 +17,7 @@ struct ile_ctx {
     // point data
     float *Qp = nullptr;   // [K][2M][T_ext]
     float *UV = nullptr;   // [K][P][4]
+    float *Qquad = nullptr;  // [K][KP][ILE_QCOLS] real form of U, V (quadratic-term MMA operand)
     // tensor-core operand rows (hi, lo) of the current point, per split precision (ile_tc.cu)
     void *Qtc[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     bool Qtc_ready[3] = {false, false, false};
@@ -205,7 +206,7 @@ ile_status ensure_tc_operands(ile_ctx *ctx, int prec) {
         CK(grow(&ctx->Qtc[prec][1], bytes));
         ctx->Qtc_bytes[prec] = bytes;
     }
-    CK(ile_launch_tc_split(prec, ctx->pp, ctx->Qp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ctx->stream));
+    CK(ile_launch_tc_split(prec, ctx->pp, ctx->Qp, ctx->Qquad, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ctx->stream));
     ctx->Qtc_ready[prec] = true;
     return ILE_OK;
 }
@@ -357,7 +358,7 @@ ile_status ile_create(ile_ctx **out, int device, void *cuda_stream, ile_prec pre
 ile_status ile_destroy(ile_ctx *ctx) {
     if (!ctx) return ILE_OK;
     DeviceGuard g(ctx->device);
-    void *bufs[] = {ctx->Qp,        ctx->UV,         ctx->Qtc[1][0], ctx->Qtc[1][1], ctx->Qtc[2][0],
+    void *bufs[] = {ctx->Qp,        ctx->UV,         ctx->Qquad,         ctx->Qtc[1][0], ctx->Qtc[1][1], ctx->Qtc[2][0],
                     ctx->Qtc[2][1],    ctx->s.C,        ctx->s.I0,      ctx->s.W,       ctx->s.A,
                     ctx->theta,        ctx->out,        ctx->lnp,       ctx->lnps,      ctx->part,
                     ctx->result,       ctx->flags,      ctx->keys,      ctx->buckets,   ctx->perm,
@@ -421,7 +422,8 @@ void ile_fill_result(const double pooled[4], const double *ilog, int n_iter, ile
 ile_status ile_prepare_point(int n_det, int n_modes, const int *lm, const double *det_tensor,
                              const double *det_pos_m, const double *Q, int T_ext, double t_start_s, double fs_hz,
                              const double *U, const double *V, int n_window, double gmst_rad, double d_ref_mpc,
-                             PointParams &pp_out, std::vector<float> &qp, std::vector<float> &uv) {
+                             PointParams &pp_out, std::vector<float> &qp, std::vector<float> &uv,
+                             std::vector<float> &quad) {
     if (!lm || !det_tensor || !det_pos_m || !Q || !U || !V) return ILE_E_ARG;
     if (n_det < 1 || n_det > ILE_MAX_DET || n_modes < 1 || n_modes > ILE_MAX_MODES) return ILE_E_ARG;
     if (n_window < 1 || n_window > ILE_MAX_WINDOW || T_ext < 2 || T_ext > ILE_MAX_TEXT) return ILE_E_ARG;
@@ -476,6 +478,26 @@ ile_status ile_prepare_point(int n_det, int n_modes, const int *lm, const double
                 o[3] = (float)(f * v[1]);
             }
     }
+    // real form of U_k and V_k for the quadratic-term MMA: operand row r = 2a + {0: Re c_a, 1: Im c_a};
+    // column blocks of 32: Re z_b, Im z_b (z = U c), Re w_b, Im w_b (w = V c)
+    const int KPq = (R + 15) & ~15;
+    quad.assign((size_t)K * KPq * ILE_QCOLS, 0.f);
+    for (int k = 0; k < K; k++)
+        for (int a = 0; a < M; a++)
+            for (int b = 0; b < M; b++) {
+                const double *u = U + 2 * (((size_t)k * M + b) * M + a);  // U_ba
+                const double *v = V + 2 * (((size_t)k * M + b) * M + a);  // V_ba
+                float *re = &quad[((size_t)k * KPq + 2 * a) * ILE_QCOLS];
+                float *im = &quad[((size_t)k * KPq + 2 * a + 1) * ILE_QCOLS];
+                re[b] = (float)u[0];
+                im[b] = (float)-u[1];
+                re[32 + b] = (float)u[1];
+                im[32 + b] = (float)u[0];
+                re[64 + b] = (float)v[0];
+                im[64 + b] = (float)-v[1];
+                re[96 + b] = (float)v[1];
+                im[96 + b] = (float)v[0];
+            }
     pp_out = pp;
     return ILE_OK;
 }
@@ -487,15 +509,17 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
                         const double *U, const double *V, int n_window, double gmst_rad, double d_ref_mpc) {
     if (!ctx) return ILE_E_ARG;
     PointParams pp{};
-    std::vector<float> qp, uv;
+    std::vector<float> qp, uv, quad;
     ile_status st = ile_prepare_point(n_det, n_modes, lm, det_tensor, det_pos_m, Q, T_ext, t_start_s, fs_hz, U, V,
-                                      n_window, gmst_rad, d_ref_mpc, pp, qp, uv);
+                                      n_window, gmst_rad, d_ref_mpc, pp, qp, uv, quad);
     if (st != ILE_OK) return st;
     DeviceGuard g(ctx->device);
     CK(grow(&ctx->Qp, sizeof(float) * qp.size()));
     CK(grow(&ctx->UV, sizeof(float) * uv.size()));
+    CK(grow(&ctx->Qquad, sizeof(float) * quad.size()));
     CK(cudaMemcpyAsync(ctx->Qp, qp.data(), sizeof(float) * qp.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->UV, uv.data(), sizeof(float) * uv.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->Qquad, quad.data(), sizeof(float) * quad.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->pp = pp;
     ctx->has_data = true;

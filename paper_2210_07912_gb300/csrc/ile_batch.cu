@@ -31,8 +31,8 @@ struct ile_batch {
     std::vector<int64_t> N, off;
     std::vector<double> eps;
     // point data
-    float *Qp = nullptr, *UV = nullptr;
-    std::vector<size_t> qp_off, uv_off, tc_off;
+    float *Qp = nullptr, *UV = nullptr, *Qquad = nullptr;
+    std::vector<size_t> qp_off, uv_off, tc_off, quad_off;
     uint8_t *Qtc_hi = nullptr, *Qtc_lo = nullptr;
     Tc2Point *pts = nullptr;
     IleBatchPoint *bp = nullptr;
@@ -99,6 +99,7 @@ void release(T *&p) {
 void free_points(ile_batch *b) {
     release(b->Qp);
     release(b->UV);
+    release(b->Qquad);
     release(b->Qtc_hi);
     release(b->Qtc_lo);
     release(b->pts);
@@ -265,13 +266,13 @@ const char *ile_batch_last_error(const ile_batch *b) { return b ? b->err : "null
 ile_status ile_batch_set_points(ile_batch *b, int n_points, const ile_point_desc *pts) {
     if (!b || !pts || n_points < 1 || n_points > ILE_BATCH_MAX_POINTS) return ILE_E_ARG;
     std::vector<PointParams> pps(n_points);
-    std::vector<std::vector<float>> qps(n_points), uvs(n_points);
+    std::vector<std::vector<float>> qps(n_points), uvs(n_points), quads(n_points);
     for (int p = 0; p < n_points; p++) {
         const ile_point_desc &d = pts[p];
         if (!desc_ok(d)) return ILE_E_ARG;
         ile_status st = ile_prepare_point(d.n_det, d.n_modes, d.lm, d.det_tensor, d.det_pos_m, d.Q, d.T_ext,
                                           d.t_start_s, d.fs_hz, d.U, d.V, d.n_window, d.gmst_rad, d.d_ref_mpc, pps[p],
-                                          qps[p], uvs[p]);
+                                          qps[p], uvs[p], quads[p]);
         if (st != ILE_OK) return st;
     }
     DeviceGuard g(b->device);
@@ -285,7 +286,8 @@ ile_status ile_batch_set_points(ile_batch *b, int n_points, const ile_point_desc
     b->qp_off.resize(n_points);
     b->uv_off.resize(n_points);
     b->tc_off.resize(n_points);
-    size_t qp_tot = 0, uv_tot = 0, tc_tot = 0;
+    b->quad_off.resize(n_points);
+    size_t qp_tot = 0, uv_tot = 0, tc_tot = 0, quad_tot = 0;
     int64_t ntot = 0;
     b->LK = b->LM = b->LKP = 0;
     for (int p = 0; p < n_points; p++) {
@@ -298,6 +300,8 @@ ile_status ile_batch_set_points(ile_batch *b, int n_points, const ile_point_desc
         qp_tot += qps[p].size();
         b->uv_off[p] = uv_tot;
         uv_tot += (uvs[p].size() + 3) / 4 * 4;
+        b->quad_off[p] = quad_tot;
+        quad_tot += quads[p].size();
         b->tc_off[p] = tc_tot;
         tc_tot += (ile_tc_q_bytes(split, pp.K, pp.M, pp.T_ext) + 255) / 256 * 256;
         b->LK = std::max(b->LK, pp.K);
@@ -307,20 +311,22 @@ ile_status ile_batch_set_points(ile_batch *b, int n_points, const ile_point_desc
     b->n_total = ntot;
     // point data
     {
-        std::vector<float> qp(qp_tot), uv(uv_tot, 0.f);
+        std::vector<float> qp(qp_tot), uv(uv_tot, 0.f), quad(quad_tot);
         for (int p = 0; p < n_points; p++) {
             std::copy(qps[p].begin(), qps[p].end(), qp.begin() + b->qp_off[p]);
             std::copy(uvs[p].begin(), uvs[p].end(), uv.begin() + b->uv_off[p]);
+            std::copy(quads[p].begin(), quads[p].end(), quad.begin() + b->quad_off[p]);
         }
         BK(upload(&b->Qp, qp, b->stream));
         BK(upload(&b->UV, uv, b->stream));
+        BK(upload(&b->Qquad, quad, b->stream));
         BK(cudaStreamSynchronize(b->stream));
     }
     BK(cudaMalloc((void **)&b->Qtc_hi, tc_tot));
     BK(cudaMalloc((void **)&b->Qtc_lo, tc_tot));
     for (int p = 0; p < n_points; p++)
-        BK(ile_launch_tc_split(split, pps[p], b->Qp + b->qp_off[p], b->Qtc_hi + b->tc_off[p], b->Qtc_lo + b->tc_off[p],
-                               b->stream));
+        BK(ile_launch_tc_split(split, pps[p], b->Qp + b->qp_off[p], b->Qquad + b->quad_off[p],
+                               b->Qtc_hi + b->tc_off[p], b->Qtc_lo + b->tc_off[p], b->stream));
     // per-sample arrays
     BK(cudaMalloc((void **)&b->theta, sizeof(double) * ILE_NDIM * ntot));
     BK(cudaMalloc((void **)&b->lnwp, sizeof(double) * ntot));

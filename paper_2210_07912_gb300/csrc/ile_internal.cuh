@@ -155,7 +155,12 @@ cudaError_t ile_launch_sort(const PointParams &pp, const double *samples, int64_
 int ile_tc_kpad(int prec, int M);
 int ile_tc_tpad(int T_ext);
 size_t ile_tc_q_bytes(int prec, int K, int M, int T_ext);
-cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp, void *hi, void *lo, cudaStream_t st);
+// Columns appended to every detector's operand rows for the quadratic term (ile_tc.cu): the real
+// form of U_k and V_k, so that one extra MMA per detector gives U_k c and V_k c.
+#define ILE_QCOLS 128
+// quad: [K][KP][ILE_QCOLS] FP32 real-form block (BF16X3 layout only; may be null)
+cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp, const float *quad, void *hi,
+                                void *lo, cudaStream_t st);
 cudaError_t ile_launch_tc(int prec, const PointParams &pp, const void *hi, const void *lo, IleScratch s,
                           const int *perm, int64_t N, double *out, int full_grid, unsigned *flags, cudaStream_t st);
 cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo, int TP, int KP, const float *UV,
@@ -224,5 +229,6 @@ cudaError_t ile_launch_adapt(const double *lnL, const double *lnw_prior, const u
 ile_status ile_prepare_point(int n_det, int n_modes, const int *lm, const double *det_tensor,
                              const double *det_pos_m, const double *Q, int T_ext, double t_start_s, double fs_hz,
                              const double *U, const double *V, int n_window, double gmst_rad, double d_ref_mpc,
-                             PointParams &pp_out, std::vector<float> &qp, std::vector<float> &uv);
+                             PointParams &pp_out, std::vector<float> &qp, std::vector<float> &uv,
+                             std::vector<float> &quad);
 void ile_fill_result(const double pooled[4], const double *ilog, int n_iter, ile_adapt_result *out);

@@ -258,6 +258,28 @@ __global__ void split_q_kernel(const float *__restrict__ Qp, int K, int R, int T
     }
 }
 
+// The quadratic-term block (real form of U_k, V_k; rows r = 2a + {Re, Im}) into columns
+// TP - ILE_QCOLS .. TP - 1 of the BF16 tiled layout.
+__global__ void split_quad_kernel(const float *__restrict__ quad, int K, int KP, int TP, uint4 *__restrict__ hi,
+                                  uint4 *__restrict__ lo) {
+    const int KC = KP / 8;
+    const int64_t total = (int64_t)K * KC * ILE_QCOLS;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int col = (int)(i % ILE_QCOLS);
+        const int kc = (int)((i / ILE_QCOLS) % KC);
+        const int k = (int)(i / ((int64_t)ILE_QCOLS * KC));
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) v[e] = quad[((int64_t)k * KP + kc * 8 + e) * ILE_QCOLS + col];
+        uint4 h, l;
+        pack_chunk<true>(v, h, l);
+        const int t = TP - ILE_QCOLS + col;
+        const int64_t o = (((int64_t)k * (TP / 8) + t / 8) * KC + kc) * 8 + (t & 7);
+        hi[o] = h;
+        lo[o] = l;
+    }
+}
+
 // Index (in 16-byte chunks) of K-chunk kc of column t of detector k in the tiled split layout.
 __device__ __forceinline__ int64_t qtile_index(int k, int kc, int t, int KC, int TP) {
     return (((int64_t)k * (TP / 8) + t / 8) * KC + kc) * 8 + (t & 7);
@@ -276,7 +298,9 @@ int ile_tc_kpad(int prec, int M) {
     return prec == ILE_PREC_BF16X3 ? (R + 15) & ~15 : (R + 7) & ~7;
 }
 
-int ile_tc_tpad(int T_ext) { return (T_ext + NWMAX + 16 + 7) & ~7; }
+// Time columns of the tiled operand: T_ext plus room for a full window past the end, then the
+// ILE_QCOLS quadratic-term columns (used by the BF16X3 fused kernel) at column tpad - ILE_QCOLS.
+int ile_tc_tpad(int T_ext) { return ((T_ext + NWMAX + 16 + 7) & ~7) + ILE_QCOLS; }
 
 size_t ile_tc_q_bytes(int prec, int K, int M, int T_ext) {
     const int KP = ile_tc_kpad(prec, M);
@@ -284,11 +308,13 @@ size_t ile_tc_q_bytes(int prec, int K, int M, int T_ext) {
     return (size_t)K * KC * ile_tc_tpad(T_ext) * 16;
 }
 
-cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp, void *hi, void *lo, cudaStream_t st) {
+cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp, const float *quad, void *hi,
+                                void *lo, cudaStream_t st) {
     const int KP = ile_tc_kpad(prec, pp.M), TP = ile_tc_tpad(pp.T_ext);
-    if (prec == ILE_PREC_BF16X3)
+    if (prec == ILE_PREC_BF16X3) {
         split_q_kernel<true><<<256, 256, 0, st>>>(Qp, pp.K, 2 * pp.M, pp.T_ext, KP, TP, (uint4 *)hi, (uint4 *)lo);
-    else
+        if (quad) split_quad_kernel<<<64, 256, 0, st>>>(quad, pp.K, KP, TP, (uint4 *)hi, (uint4 *)lo);
+    } else
         split_q_kernel<false><<<256, 256, 0, st>>>(Qp, pp.K, 2 * pp.M, pp.T_ext, KP, TP, (uint4 *)hi, (uint4 *)lo);
     return cudaGetLastError();
 }

@@ -49,10 +49,10 @@ constexpr uint32_t TMEM_COLS = 2 * NWIN;
 constexpr int NBMAX = 4;                   // B ring depth upper bound
 constexpr int SLEEPS = 200000;             // bounded sleeping waits: SLEEPS x SLEEP_NS at most
 constexpr uint32_t SLEEP_NS = 10000;
-constexpr int STRIP = JG + 1;              // columns a thread keeps per job
+constexpr int RSTRIDE = 33;                // per-thread row: 32 staged columns + 1 (odd stride: conflict-free)
 
 struct Sm {
-    uint64_t bfull[NBMAX], bempty[NBMAX], tfull[2], tempty[2], yready, aready, tdone;
+    uint64_t bfull[NBMAX], bempty[NBMAX], tfull[2], tempty[2], yready, aready, s4done, tdone;
     uint32_t tmem_base;
     int wlo[4][ILE_MAX_DET], whi[4][ILE_MAX_DET];
 };
@@ -67,22 +67,35 @@ struct Det4f {
     __device__ float operator()(int k) const { return k == 0 ? v0 : k == 1 ? v1 : k == 2 ? v2 : v3; }
 };
 
-// One job of a tile: chunk c (bins j0 .. j0 + Jc), detector k, window w of W.
+// One job of a tile: chunk c (bins j0 .. j0 + Jc), detector k, window w of W; or (quad) the
+// quadratic-term job of detector k, whose B operand is the real form of U_k and V_k.
 struct Job {
     int j0, Jc, k, w, W, step, wbeg, wbeg8, nwr;  // window [wbeg8, wbeg8 + nwr), wbeg8 = wbeg rounded down to 8
+    bool quad;
 };
 
-// Enumerates the jobs of a tile from its per-detector column range [lo_k, hi_k] of window
-// starts; the MMA warp and the math warps walk the same sequence.
+// Enumerates the jobs of a tile: first one quadratic-term job per detector, then the data-term
+// jobs from the tile's per-detector column range [lo_k, hi_k] of window starts.  The copy, MMA
+// and math warps walk the same sequence.
 struct JobIter {
-    int Nt, K, nwcol;
+    int Nt, K, nwcol, tq0;
     Det4 lo, hi;
     int c, k, w;
     bool done;
-    __device__ JobIter(int Nt_, int K_, int nwcol_, Det4 lo_, Det4 hi_)
-        : Nt(Nt_), K(K_), nwcol(nwcol_), lo(lo_), hi(hi_), c(0), k(0), w(0), done(false) {}
+    __device__ JobIter(int Nt_, int K_, int nwcol_, int tq0_, Det4 lo_, Det4 hi_)
+        : Nt(Nt_), K(K_), nwcol(nwcol_), tq0(tq0_), lo(lo_), hi(hi_), c(-1), k(0), w(0), done(false) {}
     __device__ Job get() const {
         Job j;
+        if (c < 0) {
+            j.quad = true;
+            j.j0 = j.Jc = j.w = j.step = 0;
+            j.W = 1;
+            j.k = k;
+            j.wbeg = j.wbeg8 = tq0;
+            j.nwr = ILE_QCOLS;
+            return j;
+        }
+        j.quad = false;
         j.j0 = c * JW;
         j.Jc = min(JW, Nt - j.j0);
         j.k = k;
@@ -103,6 +116,12 @@ struct JobIter {
         return j;
     }
     __device__ void next() {
+        if (c < 0) {
+            if (++k < K) return;
+            k = 0;
+            c = 0;
+            return;
+        }
         const Job j = get();
         if (++w < j.W) return;
         w = 0;
@@ -148,9 +167,12 @@ __device__ __forceinline__ const Tc2Point &work_item(const Tc2Point &one, const 
     }
 }
 
-// Shared-memory layout (LK detectors, LKC 16-byte K-chunks, LNP mode pairs: the point's own sizes
-// for a single-point launch, the largest of the batch otherwise):
-//   uvs [LK][LNP] float4 | A [LK][2][LKC][TILE] | B [NB][2][LKC][NWIN] | strips | aq_s | ls_s
+// Shared-memory layout (LK detectors, LKC 16-byte K-chunks: the point's own sizes for a
+// single-point launch, the largest of the batch otherwise):
+//   A [LK][2][LKC][TILE] | B [NB][2][LKC][NWIN] | rows [NMATH][RSTRIDE] | aq_s [NMATH] | ls_s [NMATH]
+// A math thread's row holds the two 16-column TMEM blocks its bins need; aq_s and ls_s its share
+// of the quadratic term and its partial log-sum-exp.  Before the job loop the rows area holds the
+// tile's harmonics table y [M][TILE] (float2).  U/V pairs are read through L1.
 template <bool BATCH>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ile_tc2_kernel(const __grid_constant__ Tc2Point one, const Tc2Point *__restrict__ pts,
@@ -158,20 +180,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                    int full_grid, unsigned *flags) {
     extern __shared__ __align__(1024) uint8_t dsm[];
     __shared__ Sm sm;
-    float4 *uvs = reinterpret_cast<float4 *>(dsm);                                   // [K][NP]
-    uint4 *A = reinterpret_cast<uint4 *>(dsm + 16 * ((LK * LNP + 63) / 64 * 64));    // [K][2][KC][TILE]
+    (void)LNP;
+    uint4 *A = reinterpret_cast<uint4 *>(dsm);                                        // [K][2][KC][TILE]
     uint4 *B = A + (size_t)LK * 2 * LKC * TILE;                                       // [NB][2][LKC][NWIN]
-    float *strip = reinterpret_cast<float *>(B + (size_t)NB * 2 * LKC * NWIN);        // [STRIP][NMATH]
-    float *aq_s = strip + STRIP * NMATH;                                              // [NGRP][TILE]
-    float2 *ls_s = reinterpret_cast<float2 *>(aq_s + NGRP * TILE);                     // [NGRP][TILE]
+    float *rows = reinterpret_cast<float *>(B + (size_t)NB * 2 * LKC * NWIN);         // [NMATH][RSTRIDE]
+    float *aq_s = rows + RSTRIDE * NMATH;                                             // [NMATH]
+    float2 *ls_s = reinterpret_cast<float2 *>(aq_s + NMATH);                           // [NMATH]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    if constexpr (!BATCH) {
-        const int n_uv = one.pp.K * (one.pp.M * (one.pp.M + 1) / 2);
-        const float4 *UV = reinterpret_cast<const float4 *>(one.UV);
-        for (int i = tid; i < n_uv; i += NTHREADS) uvs[i] = UV[i];
-    }
     if (warp == MMA_WARP) tmem_alloc(&sm.tmem_base, TMEM_COLS);
     if (tid == 0) {
         for (int b = 0; b < NBMAX; b++) {
@@ -184,6 +201,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         mbar_init(&sm.yready, NMATH);
         mbar_init(&sm.aready, NMATH);
+        mbar_init(&sm.s4done, NMATH);
         mbar_init(&sm.tdone, NMATH);
         mbar_init_fence();
     }
@@ -209,7 +227,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 Det4 lo, hi;
                 tile_range(sm.wlo, sm.whi, K, lo, hi);
-                for (JobIter cit(Nt, K, nwcol, lo, hi); !cit.done && !failed; cit.next(), gcopy++) {
+                for (JobIter cit(Nt, K, nwcol, TP - ILE_QCOLS, lo, hi); !cit.done && !failed; cit.next(), gcopy++) {
                     const uint32_t bb = gcopy % NB;
                     // the slot is free once the MMAs of job gcopy - NB have completed
                     if (gcopy >= (uint32_t)NB && !wait1(&sm.bempty[bb], ((gcopy / NB) - 1) & 1u, flags)) {
@@ -236,7 +254,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int64_t it = blockIdx.x; it < nitems && !failed; it += gridDim.x, tiles_done++) {
                 int64_t tile;
                 const Tc2Point &pt = work_item<BATCH>(one, pts, items, it, tile);
-                const int K = pt.pp.K, Nt = pt.pp.Nt, KP = pt.KP, KC = KP / 8;
+                const int K = pt.pp.K, Nt = pt.pp.Nt, KP = pt.KP, KC = KP / 8, TQ0 = pt.TP - ILE_QCOLS;
                 if (!wait1(&sm.aready, tiles_done & 1u, flags)) {
                     failed = true;
                     break;
@@ -244,7 +262,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 Det4 lo, hi;
                 tile_range(sm.wlo, sm.whi, K, lo, hi);
                 fence_after();
-                for (JobIter mit(Nt, K, nwcol, lo, hi); !mit.done && !failed; mit.next(), gjob++) {
+                for (JobIter mit(Nt, K, nwcol, TQ0, lo, hi); !mit.done && !failed; mit.next(), gjob++) {
                     const Job j = mit.get();
                     const uint32_t bb = gjob % NB, tb = gjob & 1u;
                     if (!wait1(&sm.bfull[bb], (gjob / NB) & 1u, flags) ||
@@ -285,27 +303,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int q4 = warp & 3, g = warp >> 2;
         const int row = q4 * 32 + lane;            // sample row in the tile = TMEM lane
         const uint32_t lane_addr = (uint32_t)(q4 * 32) << 16;
-        float *my_strip = strip + tid;             // my_strip[i * NMATH], conflict-free
+        float *my_row = rows + tid * RSTRIDE;
         uint32_t gjob = 0, tiles_done = 0;
-        int cur_point = -1;
         for (int64_t it = blockIdx.x; it < nitems && !failed; it += gridDim.x, tiles_done++) {
             int64_t tile;
             const Tc2Point &pt = work_item<BATCH>(one, pts, items, it, tile);
             const PointParams &pp = pt.pp;
-            const int K = pp.K, M = pp.M, Nt = pp.Nt, KC = pt.KP / 8, NP = M * (M + 1) / 2;
+            const int K = pp.K, M = pp.M, Nt = pp.Nt, KC = pt.KP / 8;
             const int64_t N = pt.N;
             const double *__restrict__ samples = pt.samples;
             const int *__restrict__ perm = pt.perm;
             double *__restrict__ out = pt.out;
-            if constexpr (BATCH) {
-                // this point's U/V pairs (every math thread is past the previous tile's S4)
-                const int pidx = items[it].x;
-                if (pidx != cur_point) {
-                    const float4 *UV = reinterpret_cast<const float4 *>(pt.UV);
-                    for (int i = tid; i < K * NP; i += NMATH) uvs[i] = UV[i];
-                    cur_point = pidx;
-                }
-            }
             const int64_t p = tile * TILE + row;
             const bool valid = p < N;
             const int64_t src = perm[valid ? p : tile * TILE];
@@ -344,8 +352,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
             // harmonics: thread g forms modes a = g, g + 4, ... into the shared y table (which
-            // reuses the epilogue strips: every thread has passed the previous tile's tdone)
-            float2 *ys = reinterpret_cast<float2 *>(strip);  // [M][TILE]
+            // reuses the rows area: every thread has passed the previous tile's tdone)
+            float2 *ys = reinterpret_cast<float2 *>(rows);  // [M][TILE]
             {
                 float cpow[9], spow[9];
                 ile_half_angle_powers((float)th[3], cpow, spow);
@@ -383,45 +391,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     Al[kc * TILE] = l;
                 }
             }
-            // ---- S4: this thread's share of the upper-triangle mode pairs (pair index = g mod 4)
-            float au[ILE_MAX_DET] = {0.f, 0.f, 0.f, 0.f}, avr[ILE_MAX_DET] = {0.f, 0.f, 0.f, 0.f},
-                  avi[ILE_MAX_DET] = {0.f, 0.f, 0.f, 0.f};
-            {
-                int pbase = 0;
-#pragma unroll 1
-                for (int a = 0; a < M; a++) {
-                    const float2 ya = ys[a * TILE + row];
-                    // pairs (a, b), b = a .. M-1, have indices pbase + (b - a)
-                    const int first = a + ((g - pbase) & 3);
-#pragma unroll 1
-                    for (int b = first; b < M; b += NGRP) {
-                        const float2 yb = ys[b * TILE + row];
-                        const int pidx = pbase + (b - a);
-                        const float qr = ya.x * yb.x + ya.y * yb.y, qi = ya.x * yb.y - ya.y * yb.x;
-                        const float pr = ya.x * yb.x - ya.y * yb.y, pi = ya.x * yb.y + ya.y * yb.x;
-#pragma unroll
-                        for (int k = 0; k < ILE_MAX_DET; k++) {
-                            if (k < K) {
-                                const float4 u = uvs[k * NP + pidx];
-                                au[k] += u.x * qr - u.y * qi;
-                                avr[k] += u.z * pr - u.w * pi;
-                                avi[k] += u.z * pi + u.w * pr;
-                            }
-                        }
-                    }
-                    pbase += M - a;
-                }
-            }
-            float aq = 0.f;
-#pragma unroll
-            for (int k = 0; k < ILE_MAX_DET; k++) {
-                if (k < K) {
-                    const float f2 = Fr[k] * Fr[k] + Fi[k] * Fi[k];
-                    const float g_r = Fr[k] * Fr[k] - Fi[k] * Fi[k], g_i = 2.f * Fr[k] * Fi[k];
-                    aq += f2 * au[k] + (g_r * avr[k] - g_i * avi[k]);
-                }
-            }
-            aq_s[g * TILE + row] = 0.25f * scale * scale * aq;
             // ---- tile column range per detector (invalid rows repeat row 0's sample)
             if (g == 0) {
 #pragma unroll
@@ -440,7 +409,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
             fence_async_smem();
-            mbar_arrive(&sm.aready);  // A operand, column ranges and quadratic partials are written
+            mbar_arrive(&sm.aready);  // A operand and column ranges are written: the MMAs may start
             if (!warp_wait(&sm.aready, tiles_done & 1u, flags)) {
                 failed = true;
                 break;
@@ -449,13 +418,55 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tile_range(sm.wlo, sm.whi, K, lo, hi);
             const Det4 i0d{i0[0], i0[1], i0[2], i0[3]};
             const Det4f wtd{wt[0], wt[1], wt[2], wt[3]};
+            JobIter jit(Nt, K, nwcol, pt.TP - ILE_QCOLS, lo, hi);
+
+            // ---- S4 on the tensor cores: the quadratic-term job of detector k leaves in TMEM, for
+            // this sample, z = U_k c_k and w = V_k c_k as column blocks [Re z | Im z | Re w | Im w]
+            // of 32; thread g takes block g and forms its part of c^H z + Re(c^T w)
+            float aq = 0.f;
+            for (int kq = 0; kq < K; kq++) {
+                const uint32_t tb = gjob & 1u;
+                if (!warp_wait(&sm.tfull[tb], (gjob / 2) & 1u, flags)) {
+                    failed = true;
+                    break;
+                }
+                fence_after();
+                uint32_t r[32];
+                tmem_ld32(tmem + tb * NWIN + lane_addr + (uint32_t)(32 * g), r);
+                fence_before();
+                mbar_arrive(&sm.tempty[tb]);
+                const float fr = scale * (kq == 0 ? Fr[0] : kq == 1 ? Fr[1] : kq == 2 ? Fr[2] : Fr[3]);
+                const float fi = scale * (kq == 0 ? Fi[0] : kq == 1 ? Fi[1] : kq == 2 ? Fi[2] : Fi[3]);
+                // component of c_b this block pairs with: Re c_b = fr yr - fi yi, Im c_b = fr yi + fi yr
+                // (block 3 enters with a minus sign: Re(c^T w) = Re c . Re w - Im c . Im w)
+                const float ca = g == 1 ? fi : g == 3 ? -fi : fr;
+                const float cb = g == 1 ? fr : g == 3 ? -fr : -fi;
+                float part = 0.f;
+#pragma unroll
+                for (int b = 0; b < 32; b++) {
+                    if (b < M) {
+                        const float2 y = ys[b * TILE + row];
+                        part = fmaf(fmaf(ca, y.x, cb * y.y), __uint_as_float(r[b]), part);
+                    }
+                }
+                aq += part;
+                gjob++;
+                jit.next();
+            }
+            if (failed) break;
+            aq_s[tid] = 0.25f * aq;
+            // everyone is done with the y table before the rows take the TMEM blocks
+            mbar_arrive(&sm.s4done);
+            if (!warp_wait(&sm.s4done, tiles_done & 1u, flags)) {
+                failed = true;
+                break;
+            }
 
             // ---- S3/S5: consume the jobs
             float D[JG];
 #pragma unroll
             for (int jj = 0; jj < JG; jj++) D[jj] = 0.f;
             float m_run = -INFINITY, s_run = 0.f;
-            JobIter jit(Nt, K, nwcol, lo, hi);
             while (!jit.done) {
                 const Job j = jit.get();
                 const uint32_t tb = gjob & 1u;
@@ -469,22 +480,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int jbeg = g * JG;             // my first bin of the chunk
                 const bool mine = wsel == j.w && jbeg < j.Jc;
                 const int s0 = dk - j.w * j.step + jbeg + (j.wbeg - j.wbeg8);  // my first column in the window
-                int cmin = mine ? s0 : 0x7fffffff, cmax = mine ? s0 + JG : -1;
+                // my columns s0 .. s0 + 16 lie in the 16-column blocks a0 and a0 + 16 (both < NWIN)
+                const int a0 = s0 & ~15;
+                int cmin = mine ? a0 : 0x7fffffff, cmax = mine ? a0 + 16 : -1;
                 for (int o = 16; o; o >>= 1) {
                     cmin = min(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
                     cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
                 }
                 if (cmax >= 0) {
                     const uint32_t taddr = tmem + tb * NWIN + lane_addr;
-                    for (int cb = cmin & ~31; cb <= cmax; cb += 32) {
-                        uint32_t r[32];
-                        tmem_ld32(taddr + (uint32_t)cb, r);
-                        if (mine) {
+                    for (int cb = cmin; cb <= cmax; cb += 16) {
+                        uint32_t r[16];
+                        tmem_ld16(taddr + (uint32_t)cb, r);
+                        if (mine && (cb == a0 || cb == a0 + 16)) {
+                            float *dst = my_row + (cb - a0);
 #pragma unroll
-                            for (int qq = 0; qq < 32; qq++) {
-                                const int idx = cb + qq - s0;
-                                if (idx >= 0 && idx < STRIP) my_strip[idx * NMATH] = __uint_as_float(r[qq]);
-                            }
+                            for (int qq = 0; qq < 16; qq++) dst[qq] = __uint_as_float(r[qq]);
                         }
                     }
                 }
@@ -492,11 +503,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 mbar_arrive(&sm.tempty[tb]);
                 if (mine) {
                     const float w = wtd(j.k), omw = 1.f - w;
-                    float vprev = my_strip[0];
+                    const float *src = my_row + (s0 & 15);
+                    float vprev = src[0];
 #pragma unroll
                     for (int jj = 0; jj < JG; jj++) {
                         if (jbeg + jj < j.Jc) {
-                            const float v = my_strip[(jj + 1) * NMATH];
+                            const float v = src[jj + 1];
                             D[jj] += fmaf(w, v, omw * vprev);
                             vprev = v;
                         }
@@ -508,8 +520,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     // chunk complete: S5 log-sum-exp update (or the full grid)
                     if (full_grid) {
                         if (valid) {
-                            const double A_n = (double)(aq_s[row] + aq_s[TILE + row] + aq_s[2 * TILE + row] +
-                                                        aq_s[3 * TILE + row]);
+                            const double A_n = (double)(aq_s[q4 * 32 + lane] + aq_s[128 + q4 * 32 + lane] +
+                                                        aq_s[256 + q4 * 32 + lane] + aq_s[384 + q4 * 32 + lane]);
                             const int64_t o = (int64_t)perm[p] * Nt + j.j0 + jbeg;
 #pragma unroll
                             for (int jj = 0; jj < JG; jj++)
@@ -534,24 +546,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             if (failed) break;
             // ---- merge the four threads' partial log-sum-exps
-            ls_s[g * TILE + row] = make_float2(m_run, s_run);
+            ls_s[tid] = make_float2(m_run, s_run);
             mbar_arrive(&sm.tdone);
             if (!warp_wait(&sm.tdone, tiles_done & 1u, flags)) {
                 failed = true;
                 break;
             }
             if (g == 0 && valid && !full_grid) {
-                float m = -INFINITY;
+                // the four threads of this sample: math thread (4h + q4) * 32 + lane, h = 0..3
+                float m = -INFINITY, aqs = 0.f;
 #pragma unroll
-                for (int h = 0; h < NGRP; h++) m = fmaxf(m, ls_s[h * TILE + row].x);
+                for (int h = 0; h < NGRP; h++) {
+                    const int t = (4 * h + q4) * 32 + lane;
+                    m = fmaxf(m, ls_s[t].x);
+                    aqs += aq_s[t];
+                }
                 float ssum = 0.f;
 #pragma unroll
                 for (int h = 0; h < NGRP; h++) {
-                    const float2 v = ls_s[h * TILE + row];
+                    const float2 v = ls_s[(4 * h + q4) * 32 + lane];
                     if (v.y > 0.f) ssum += v.y * __expf(v.x - m);
                 }
-                const double A_n =
-                    (double)(aq_s[row] + aq_s[TILE + row] + aq_s[2 * TILE + row] + aq_s[3 * TILE + row]);
+                const double A_n = (double)aqs;
                 out[perm[p]] = (double)m + (double)logf(ssum) - A_n - (double)pp.log_nt;
             }
         }
@@ -567,10 +583,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 size_t tc2_smem(int K, int M, int KP, int NB) {
-    const int KC = KP / 8, P = M * (M + 1) / 2;
-    return (size_t)16 * ((K * P + 63) / 64 * 64) + (size_t)16 * K * 2 * KC * TILE + (size_t)16 * NB * 2 * KC * NWIN +
-           sizeof(float) * STRIP * NMATH + sizeof(float) * NGRP * TILE + sizeof(float2) * NGRP * TILE;
+    const int KC = KP / 8;
+    (void)M;  // the harmonics table (8 M TILE bytes <= 21.5 KB) fits in the rows area
+    return (size_t)16 * K * 2 * KC * TILE + (size_t)16 * NB * 2 * KC * NWIN + sizeof(float) * RSTRIDE * NMATH +
+           sizeof(float) * NMATH + sizeof(float2) * NMATH;
 }
+static_assert(8 * ILE_MAX_MODES * TILE <= 4 * RSTRIDE * NMATH, "y table must fit in the rows area");
 
 constexpr size_t SMEM_LIMIT = 227 * 1024 - sizeof(Sm) - 64;
 

@@ -79,6 +79,9 @@ def _load():
             lib.orc_hist.argtypes = [vp, vp, ctypes.c_long, vp]
             lib.orc_cdf_from_hist.argtypes = [vp, d, vp]
             lib.orc_cdf_uniform.argtypes = [vp]
+            lib.orc_dmarg_lnF.argtypes = [d, d, d, d, d]
+            lib.orc_dmarg_lnF.restype = d
+            lib.orc_lnL_dmarg.argtypes = [ctypes.POINTER(_Point), vp, ctypes.c_long, d, d, vp]
             lib.orc_wigner_d_deriv.argtypes = [i, i, i, d]
             lib.orc_wigner_d_deriv.restype = d
             lib.orc_lnL_t_grad.argtypes = [ctypes.POINTER(_Point), vp, d, vp, vp, vp, vp, vp]
@@ -200,6 +203,25 @@ def lnL_t_grad(point, samples, g=None):
         gth[:, n] = gt
         out[n] = lt[0]
     return out, gth, gQ, gU, gV
+
+
+def dmarg_lnF(a, b, d_min, d_max, d_ref):
+    """ln int p(D) exp(a x - b x^2) dD, x = d_ref / D, p prop. to D^2 on [d_min, d_max]."""
+    return _load().orc_dmarg_lnF(float(a), float(b), float(d_min), float(d_max), float(d_ref))
+
+
+def lnL_dmarg(point, samples, d_min, d_max):
+    """Distance- and time-marginalised lnL of every sample (the samples' D is ignored)."""
+    pv = _PointView(point)
+    s = np.ascontiguousarray(samples, dtype=np.float64)
+    N = s.shape[1]
+    out = np.zeros(N)
+    st = _load().orc_lnL_dmarg(ctypes.byref(pv.s), _ptr(s), N, float(d_min), float(d_max), _ptr(out))
+    if st == 3:
+        raise RangeError("interpolation index outside [0, T_ext-1]")
+    if st != 0:
+        raise ValueError(f"oracle status {st}")
+    return out
 
 
 # ------------------------------------------------------------------------------------ S6

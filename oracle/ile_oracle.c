@@ -716,10 +716,10 @@ int orc_lnL_t_grad(const orc_point *P, const double th[7], double g, double *g_t
  * ln F(a, b) = ln int_{D_min}^{D_max} p(D) exp(a x - b x^2) dD,  x = D_ref / D,
  * p(D) = 3 D^2 / (D_max^3 - D_min^3): the distance integral of the likelihood at fixed other
  * parameters, with a the data term and b the quadratic term at D = D_ref (App. "Distance
- * marginalization" names the technique; the integral is written out here).  Plain composite
- * Gauss-Legendre in D (32-point rule on 256 equal panels: panels of 3.5 Mpc for [100, 1000] Mpc,
- * far narrower than the likelihood's width in D), with the exponent shifted by its maximum over
- * the nodes before exponentiation.
+ * marginalization" names the technique; the integral is written out here).  Composite
+ * 32-point Gauss-Legendre in x: 64 equal panels plus panels of geometrically growing width around
+ * the exponent's maximum (edges at x* +- l 2^m, l the peak's width or decay length), so that a
+ * narrow peak is resolved however large b is; the exponent is shifted by its maximum first.
  */
 static void gl32(double *x, double *w)
 {
@@ -744,6 +744,12 @@ static void gl32(double *x, double *w)
     }
 }
 
+static int cmp_double(const void *p, const void *q)
+{
+    double a = *(const double *)p, b = *(const double *)q;
+    return (a > b) - (a < b);
+}
+
 double orc_dmarg_lnF(double a, double b, double d_min, double d_max, double d_ref)
 {
     static double gx[32], gw[32];
@@ -752,23 +758,41 @@ double orc_dmarg_lnF(double a, double b, double d_min, double d_max, double d_re
         gl32(gx, gw);
         ready = 1;
     }
-    const int panels = 256;
-    const double norm = 3.0 / (d_max * d_max * d_max - d_min * d_min * d_min);
-    const double h = (d_max - d_min) / panels;
-    double emax = -INFINITY;
-    for (int p = 0; p < panels; p++)
-        for (int i = 0; i < 32; i++) {
-            double D = d_min + h * (p + 0.5 * (gx[i] + 1.0)), x = d_ref / D;
-            double e = a * x - b * x * x;
-            if (e > emax) emax = e;
-        }
+    /* in x = d_ref / D the prior is C x^-4 dx on [xlo, xhi] and the exponent a x - b x^2 */
+    const double xlo = d_ref / d_max, xhi = d_ref / d_min;
+    const double C = 3.0 * d_ref * d_ref * d_ref / (d_max * d_max * d_max - d_min * d_min * d_min);
+    double xs = b > 0.0 ? a / (2.0 * b) : (a > 0.0 ? xhi : xlo);
+    if (xs < xlo) xs = xlo;
+    if (xs > xhi) xs = xhi;
+    const double shift = a * xs - b * xs * xs; /* the exponent's maximum on the range */
+    /* its scale there: 1/sqrt(2b) (peak) or 1/|slope| (decay from an end) */
+    const double slope = fabs(a - 2.0 * b * xs);
+    double ell = b > 0.0 ? 1.0 / sqrt(2.0 * b) : INFINITY;
+    if (slope > 0.0 && 1.0 / slope < ell) ell = 1.0 / slope;
+    /* panel edges: 64 equal panels, plus xs +- ell 2^m (m = -3 .. 60), so that the panels next to
+     * the peak are a fraction of its width and grow geometrically away from it */
+    double e[64 + 1 + 2 * 64 + 1];
+    int ne = 0;
+    for (int p = 0; p <= 64; p++) e[ne++] = xlo + (xhi - xlo) * p / 64.0;
+    e[ne++] = xs;
+    for (int m = -3; m <= 60; m++) {
+        double d = ell * ldexp(1.0, m);
+        if (xs - d > xlo) e[ne++] = xs - d;
+        if (xs + d < xhi) e[ne++] = xs + d;
+    }
+    qsort(e, ne, sizeof(double), cmp_double);
     double s = 0.0;
-    for (int p = 0; p < panels; p++)
+    for (int p = 0; p + 1 < ne; p++) {
+        double lo = e[p], hi = e[p + 1];
+        if (!(hi > lo)) continue;
+        double c = 0.5 * (lo + hi), h = 0.5 * (hi - lo), t = 0.0;
         for (int i = 0; i < 32; i++) {
-            double D = d_min + h * (p + 0.5 * (gx[i] + 1.0)), x = d_ref / D;
-            s += 0.5 * h * gw[i] * norm * D * D * exp(a * x - b * x * x - emax);
+            double x = c + h * gx[i];
+            t += gw[i] * C / (x * x * x * x) * exp(a * x - b * x * x - shift);
         }
-    return emax + log(s);
+        s += h * t;
+    }
+    return shift + log(s);
 }
 
 /* Distance-marginalised, time-marginalised lnL of N samples: LSE_j ln F(data_j, A) - ln N_t,

@@ -18,7 +18,8 @@ def test_lnF_normalisation_and_adaptive_quadrature(orc):
     integrate = pytest.importorskip("scipy.integrate")
     assert abs(orc.dmarg_lnF(0.0, 0.0, D_MIN, D_MAX, D_REF)) < 1e-13  # normalised prior
     norm = 3.0 / (D_MAX ** 3 - D_MIN ** 3)
-    for a, b in [(5.0, 3.0), (-20.0, 2.0), (300.0, 150.0), (60.0, 0.5), (2000.0, 1500.0), (1.0, 1e-4), (0.0, 40.0)]:
+    for a, b in [(5.0, 3.0), (-20.0, 2.0), (300.0, 150.0), (60.0, 0.5), (2000.0, 1500.0), (1.0, 1e-4), (0.0, 40.0),
+                 (1e4, 1e4), (2.2e4, 1e4), (100.0, 600.0)]:
         x0 = min(max(a / (2 * b), D_REF / D_MAX), D_REF / D_MIN)
         shift = a * x0 - b * x0 * x0
         f = lambda D: norm * D * D * math.exp(a * D_REF / D - b * (D_REF / D) ** 2 - shift)

@@ -106,6 +106,27 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
                         const double *U, const double *V, int n_window, double gmst_rad, double d_ref_mpc);
 
 /*
+ * Distance marginalisation (App. "Distance marginalization"; the paper gives no formula, the
+ * integral is written out here).  When enabled, every likelihood the context returns (ile_eval,
+ * ile_integrate, the adaptive integrator) is marginalised over the luminosity distance:
+ *   lnL_D(n) = ln (1/N_t) sum_j F(a_j, b) ,  F(a, b) = int p(D) exp(a x - b x^2) dD ,  x = D_ref / D,
+ * p(D) = 3 D^2 / (D_max^3 - D_min^3) on [d_min_mpc, d_max_mpc], with a_j the data term of window
+ * bin j and b the quadratic term, both at D = D_ref; the samples' own distance is ignored (the
+ * Monte Carlo then integrates over the other six parameters; give D a fixed, non-adaptive range).
+ * ln F comes from two tables (b < 10: ln F on an (a, b) grid; b >= 10: ln F minus its peak
+ * exponent on a grid in the standardised peak position and ln b; about 28 MB of device memory,
+ * built in FP64 on the device when this is called) with bilinear interpolation; the quadratic term
+ * b is covered up to 10^6.  The adjoint entry points return ILE_E_STATE while it is enabled.
+ * Requires ile_set_data; ile_set_data turns it off.  0 < d_min_mpc < d_max_mpc.
+ */
+ile_status ile_set_distance_marginalization(ile_ctx *ctx, int enable, double d_min_mpc, double d_max_mpc);
+
+/* ln F(a[i], b[i]) from the context's distance-marginalisation tables (the per-bin term of the
+ * distance-marginalised likelihood), for inspection and tests.  ILE_E_STATE unless enabled.
+ * flags: ILE_DEVICE_PTRS (else host arrays, synchronous). */
+ile_status ile_dmarg_eval(ile_ctx *ctx, const double *a, const double *b, int64_t n, double *out, unsigned flags);
+
+/*
  * Time-marginalised log-likelihood of N samples (S1-S5).
  *   samples: SoA [7][N] (ra, dec, psi, iota, phi, D_Mpc, tc_s), FP64.
  *   out: lnL_t [N] FP64, or with ILE_NO_TMARG lnL [N][N_t] FP64 (then N <= 65536).

@@ -18,6 +18,7 @@ struct ile_ctx {
     float *Qp = nullptr;   // [K][2M][T_ext]
     float *UV = nullptr;   // [K][P][4]
     float *Qquad = nullptr;  // [K][KP][ILE_QCOLS] real form of U, V (quadratic-term MMA operand)
+    void *dm_table = nullptr;  // distance-marginalisation tables (ile_dmarg.cu)
     // tensor-core operand rows (hi, lo) of the current point, per split precision (ile_tc.cu)
     void *Qtc[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     bool Qtc_ready[3] = {false, false, false};
@@ -358,7 +359,7 @@ ile_status ile_create(ile_ctx **out, int device, void *cuda_stream, ile_prec pre
 ile_status ile_destroy(ile_ctx *ctx) {
     if (!ctx) return ILE_OK;
     DeviceGuard g(ctx->device);
-    void *bufs[] = {ctx->Qp,        ctx->UV,         ctx->Qquad,         ctx->Qtc[1][0], ctx->Qtc[1][1], ctx->Qtc[2][0],
+    void *bufs[] = {ctx->Qp,        ctx->UV,         ctx->Qquad,     ctx->dm_table,         ctx->Qtc[1][0], ctx->Qtc[1][1], ctx->Qtc[2][0],
                     ctx->Qtc[2][1],    ctx->s.C,        ctx->s.I0,      ctx->s.W,       ctx->s.A,
                     ctx->theta,        ctx->out,        ctx->lnp,       ctx->lnps,      ctx->part,
                     ctx->result,       ctx->flags,      ctx->keys,      ctx->buckets,   ctx->perm,
@@ -528,6 +529,46 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
     return ILE_OK;
 }
 
+ile_status ile_set_distance_marginalization(ile_ctx *ctx, int enable, double d_min_mpc, double d_max_mpc) {
+    if (!ctx) return ILE_E_ARG;
+    if (!ctx->has_data) return ILE_E_STATE;
+    if (!enable) {
+        ctx->pp.dm.on = 0;
+        return ILE_OK;
+    }
+    if (!(d_min_mpc > 0.0) || !(d_max_mpc > d_min_mpc) || !isfinite(d_max_mpc)) return ILE_E_ARG;
+    DeviceGuard g(ctx->device);
+    if (!ctx->dm_table) CK(cudaMalloc(&ctx->dm_table, ile_dmarg_buffer_bytes()));
+    DmargParams dm{};
+    CK(ile_build_dmarg(d_min_mpc, d_max_mpc, (double)ctx->pp.d_ref, ctx->dm_table, dm, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->pp.dm = dm;
+    return ILE_OK;
+}
+
+ile_status ile_dmarg_eval(ile_ctx *ctx, const double *a, const double *b, int64_t n, double *out, unsigned flags) {
+    if (!ctx || n < 0) return ILE_E_ARG;
+    if (!ctx->pp.dm.on) return ILE_E_STATE;
+    if (n == 0) return ILE_OK;
+    if (!a || !b || !out) return ILE_E_ARG;
+    DeviceGuard g(ctx->device);
+    if (flags & ILE_DEVICE_PTRS) {
+        CK(ile_launch_dmarg_eval(ctx->pp.dm, a, b, n, out, ctx->stream));
+        return ILE_OK;
+    }
+    double *d = nullptr;
+    CK(cudaMalloc((void **)&d, sizeof(double) * 3 * (size_t)n));
+    cudaError_t e = cudaMemcpyAsync(d, a, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + n, b, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = ile_launch_dmarg_eval(ctx->pp.dm, d, d + n, n, d + 2 * n, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, d + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    CK(e);
+    return ILE_OK;
+}
+
 ile_status ile_eval(ile_ctx *ctx, const double *samples, int64_t N, double *out, unsigned flags) {
     if (!ctx) return ILE_E_ARG;
     if (!ctx->has_data) return ILE_E_STATE;
@@ -601,6 +642,7 @@ ile_status ile_eval_grad(ile_ctx *ctx, const double *samples, int64_t N, const d
     if (!samples || !g_lnL) return ILE_E_ARG;
     if (!g_samples && !g_Q && !g_U && !g_V && !lnL_t_out) return ILE_E_ARG;
     if (N > ILE_GRAD_MAX_SAMPLES) return ILE_E_ARG;
+    if (ctx->pp.dm.on) return ILE_E_STATE;  // the adjoint differentiates the time-marginalised likelihood
     DeviceGuard g(ctx->device);
     ile_status st = ensure_samples(ctx, N);
     if (st != ILE_OK) return st;
@@ -615,6 +657,7 @@ ile_status ile_integrate_grad(ile_ctx *ctx, const double *samples, const double 
     if (!ctx->has_data) return ILE_E_STATE;
     if (N < 1 || !samples || !result) return ILE_E_ARG;
     if (N > ILE_GRAD_MAX_SAMPLES) return ILE_E_ARG;
+    if (ctx->pp.dm.on) return ILE_E_STATE;
     DeviceGuard g(ctx->device);
     ile_status st = ensure_samples(ctx, N);
     if (st != ILE_OK) return st;

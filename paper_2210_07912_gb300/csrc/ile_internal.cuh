@@ -38,6 +38,29 @@ struct ModeTab {
     WignerTerm t[4];
 };
 
+// Distance marginalisation (ile_dmarg.cu): ln F(a, b) = ln int p(D) exp(a x - b x^2) dD,
+// x = D_ref / D, p prop. to D^2 on [D_min, D_max], for the data term a and quadratic term b at
+// D = D_ref.  Two tables, bilinear:
+//   b < b_split: ln F itself on nodes a_i = A0 sinh(tau_i) (tau uniform) x b_k = exp(s_k) (s
+//     uniform), interpolated linearly in a and in b (the parts of ln F linear in a and b are
+//     reproduced exactly);
+//   b >= b_split: H = ln F - E*, E* = a x* - b x*^2 at x* = clip(a / 2b, x_min, x_max), on
+//     tau = asinh((u - x_min) / eps) + asinh((u - x_max) / eps) (u = a / 2b; fine near both
+//     ends of the distance range) x s = ln b, interpolated linearly in tau and s.
+struct DmargParams {
+    int on;
+    float xmin, xmax, b_split;
+    // table 1
+    int n1a, n1s;
+    float A0, tau1_max, inv_dtau1, s1_lo, ds1;
+    const float *t1;   // [n1s][n1a]
+    const float *a1;   // [n1a] node positions a_i
+    // table 2
+    int n2t, n2s;
+    float eps, tau2_lo, inv_dtau2, s2_lo, inv_ds2;
+    const float *t2;   // [n2s][n2t]
+};
+
 // Everything a kernel needs about the point besides the big arrays; passed by value.
 struct PointParams {
     int K, M, T_ext, Nt;
@@ -49,7 +72,70 @@ struct PointParams {
     float det_tensor[ILE_MAX_DET][9];
     float det_pos_c[ILE_MAX_DET][3];  // r_k / c in seconds
     ModeTab mode[ILE_MAX_MODES];
+    DmargParams dm;
 };
+
+// Per-sample part of the distance-marginalised lookup (b = quadratic term at D_ref > 0).
+struct DmargSample {
+    float b, inv2b, g;  // g: interpolation weight between the two table rows
+    int row;            // first table row (offset in floats)
+    bool big;           // table 2
+};
+
+__device__ __forceinline__ DmargSample ile_dmarg_sample(const DmargParams &dm, float b) {
+    DmargSample q;
+    b = fmaxf(b, 1e-30f);
+    q.b = b;
+    q.inv2b = 0.5f / b;
+    q.big = b >= dm.b_split;
+    const float s = logf(b);
+    if (q.big) {
+        float fs = (s - dm.s2_lo) * dm.inv_ds2;
+        fs = fminf(fmaxf(fs, 0.f), (float)(dm.n2s - 1) - 1e-3f);
+        const int k = (int)fs;
+        q.g = fs - (float)k;
+        q.row = k * dm.n2t;
+    } else {
+        float fs = (s - dm.s1_lo) / dm.ds1;
+        fs = fminf(fmaxf(fs, 0.f), (float)(dm.n1s - 1) - 1e-3f);
+        const int k = (int)fs;
+        const float b0 = expf(dm.s1_lo + (float)k * dm.ds1), b1 = expf(dm.s1_lo + (float)(k + 1) * dm.ds1);
+        q.g = fminf(fmaxf((b - b0) / (b1 - b0), 0.f), 1.f);
+        q.row = k * dm.n1a;
+    }
+    return q;
+}
+
+__device__ __forceinline__ float ile_asinh_f(float z) {
+    const float az = fabsf(z);
+    return copysignf(logf(az + sqrtf(fmaf(az, az, 1.f))), z);
+}
+
+// ln F(a, b) for one window bin.
+__device__ __forceinline__ float ile_dmarg_lnF(const DmargParams &dm, const DmargSample &q, float a) {
+    if (q.big) {
+        const float u = a * q.inv2b;
+        const float tau = ile_asinh_f((u - dm.xmin) / dm.eps) + ile_asinh_f((u - dm.xmax) / dm.eps);
+        float ft = (tau - dm.tau2_lo) * dm.inv_dtau2;
+        ft = fminf(fmaxf(ft, 0.f), (float)(dm.n2t - 1) - 1e-3f);
+        const int i = (int)ft;
+        const float f = ft - (float)i;
+        const float *t0 = dm.t2 + q.row + i, *t1 = t0 + dm.n2t;
+        const float a0 = __ldg(t0), a1 = __ldg(t0 + 1), c0 = __ldg(t1), c1 = __ldg(t1 + 1);
+        const float h0 = fmaf(f, a1 - a0, a0), h1 = fmaf(f, c1 - c0, c0);
+        const float xs = fminf(fmaxf(u, dm.xmin), dm.xmax);
+        return fmaf(a, xs, -q.b * xs * xs) + fmaf(q.g, h1 - h0, h0);
+    }
+    float ft = (ile_asinh_f(a / dm.A0) + dm.tau1_max) * dm.inv_dtau1;
+    ft = fminf(fmaxf(ft, 0.f), (float)(dm.n1a - 1) - 1e-3f);
+    const int i = (int)ft;
+    const float an0 = __ldg(dm.a1 + i), an1 = __ldg(dm.a1 + i + 1);
+    const float f = fminf(fmaxf((a - an0) / (an1 - an0), 0.f), 1.f);
+    const float *t0 = dm.t1 + q.row + i, *t1 = t0 + dm.n1a;
+    const float a0 = __ldg(t0), a1 = __ldg(t0 + 1), c0 = __ldg(t1), c1 = __ldg(t1 + 1);
+    const float h0 = fmaf(f, a1 - a0, a0), h1 = fmaf(f, c1 - c0, c0);
+    return fmaf(q.g, h1 - h0, h0);
+}
 
 // Adaptive-Cartesian sampler configuration (ile_adapt.cu).
 #define ILE_ADAPT_LOG 64
@@ -224,6 +310,13 @@ cudaError_t ile_launch_adapt(const double *lnL, const double *lnw_prior, const u
                              const double *iter_res, const IleSamplerParams &sp, double eps,
                              unsigned long long *hist_fx, double *hist, uint64_t *cdf, float *lnps_tab, double *pooled,
                              double *iter_log, int *iter_dev, int update_tables, cudaStream_t st);
+
+// distance-marginalisation tables (ile_dmarg.cu): fills dm (on = 1) and the device tables in `buf`
+// (ile_dmarg_buffer_bytes() bytes, 256-byte aligned); synchronous
+size_t ile_dmarg_buffer_bytes();
+cudaError_t ile_build_dmarg(double d_min, double d_max, double d_ref, void *buf, DmargParams &dm, cudaStream_t st);
+cudaError_t ile_launch_dmarg_eval(const DmargParams &dm, const double *a, const double *b, int64_t n, double *out,
+                                  cudaStream_t st);
 
 // ------------------------------------------------------------------ host helpers (ile_api.cu)
 ile_status ile_prepare_point(int n_det, int n_modes, const int *lm, const double *det_tensor,

@@ -129,12 +129,17 @@ __global__ void __launch_bounds__(256) ile_plain_kernel(const __grid_constant__ 
     }
     __syncthreads();
 
-    // S5: log-sum-exp over the window, FP64 assembly
+    // S5: log-sum-exp over the window, FP64 assembly (distance-marginalised: ln F(D_j, A) per bin)
     const double log_nt = log((double)Nt);
     for (int nn = warp; nn < ns; nn += 8) {
-        const float *d = Ds + nn * Nt;
-        const double A = (double)s.A[n0 + nn];
+        float *d = Ds + nn * Nt;
+        double A = (double)s.A[n0 + nn];
         const int64_t dst = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
+        if (pp.dm.on) {
+            const DmargSample q = ile_dmarg_sample(pp.dm, (float)A);
+            for (int j = lane; j < Nt; j += 32) d[j] = ile_dmarg_lnF(pp.dm, q, d[j]);
+            A = 0.0;
+        }
         if (full_grid) {
             for (int j = lane; j < Nt; j += 32) out[dst * Nt + j] = (double)d[j] - A;
             continue;

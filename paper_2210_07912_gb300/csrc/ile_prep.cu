@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(256) ile_prep_kernel(const __grid_constant__ P
     }
     const float ra = (float)th[0], dec = (float)th[1], psi = (float)th[2];
     const float iota = (float)th[3], phi = (float)th[4], tc = (float)th[6];
-    const float scale = pp.d_ref / (float)th[5];
+    // distance-marginalised mode: coefficients and quadratic term at D = D_ref
+    const float scale = pp.dm.on ? 1.f : pp.d_ref / (float)th[5];
 
     float Fr[ILE_MAX_DET], Fi[ILE_MAX_DET], x0[ILE_MAX_DET];
     ile_sample_geometry(pp, ra, dec, psi, tc, Fr, Fi, x0);

@@ -110,7 +110,12 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
     }
     __syncthreads();
 
-    const float A = valid ? s.A[p] : 0.f;
+    float A = valid ? s.A[p] : 0.f;
+    DmargSample dq{};
+    if (pp.dm.on) {
+        dq = ile_dmarg_sample(pp.dm, A);  // per-bin terms become ln F(D_j, A); nothing is subtracted
+        A = 0.f;
+    }
     float m_run = -INFINITY, s_run = 0.f;
     uint32_t phase = 0;
     bool timed_out = false;
@@ -199,6 +204,8 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
             }
         }
         if (timed_out) break;
+        if (pp.dm.on)
+            for (int jj = 0; jj < Jc; jj++) Dt[jj * TILE + t] = ile_dmarg_lnF(pp.dm, dq, Dt[jj * TILE + t]);
         if (full_grid) {
             if (valid) {
                 const int64_t o = (int64_t)(perm ? perm[p] : p) * Nt + j0;

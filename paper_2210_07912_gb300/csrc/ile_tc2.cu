@@ -173,7 +173,7 @@ __device__ __forceinline__ const Tc2Point &work_item(const Tc2Point &one, const 
 // A math thread's row holds the two 16-column TMEM blocks its bins need; aq_s and ls_s its share
 // of the quadratic term and its partial log-sum-exp.  Before the job loop the rows area holds the
 // tile's harmonics table y [M][TILE] (float2).  U/V pairs are read through L1.
-template <bool BATCH>
+template <bool BATCH, bool DM>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ile_tc2_kernel(const __grid_constant__ Tc2Point one, const Tc2Point *__restrict__ pts,
                    const int2 *__restrict__ items, int64_t nitems, int LK, int LKC, int LNP, int NB, int nwcol,
@@ -330,7 +330,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 th[0] = th[1] = th[2] = th[3] = th[4] = th[6] = 0.0;
                 th[5] = 1.0;
             }
-            const float scale = pp.d_ref / (float)th[5];
+            // distance-marginalised mode: coefficients and quadratic term at D = D_ref
+            const float scale = DM ? 1.f : pp.d_ref / (float)th[5];
             float Fr[ILE_MAX_DET], Fi[ILE_MAX_DET], x0[ILE_MAX_DET];
             ile_sample_geometry(pp, (float)th[0], (float)th[1], (float)th[2], (float)th[6], Fr, Fi, x0);
             int i0[ILE_MAX_DET];
@@ -461,6 +462,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 failed = true;
                 break;
             }
+            // distance-marginalised mode: per-bin terms ln F(D_j, A) with A this sample's quadratic term
+            DmargSample dq{};
+            if constexpr (DM)
+                dq = ile_dmarg_sample(pp.dm, aq_s[q4 * 32 + lane] + aq_s[128 + q4 * 32 + lane] +
+                                                 aq_s[256 + q4 * 32 + lane] + aq_s[384 + q4 * 32 + lane]);
 
             // ---- S3/S5: consume the jobs
             float D[JG];
@@ -518,10 +524,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 jit.next();
                 if (j.k == K - 1 && j.w == j.W - 1) {
                     // chunk complete: S5 log-sum-exp update (or the full grid)
+                    if constexpr (DM) {
+#pragma unroll
+                        for (int jj = 0; jj < JG; jj++)
+                            if (jbeg + jj < j.Jc) D[jj] = ile_dmarg_lnF(pp.dm, dq, D[jj]);
+                    }
                     if (full_grid) {
                         if (valid) {
-                            const double A_n = (double)(aq_s[q4 * 32 + lane] + aq_s[128 + q4 * 32 + lane] +
-                                                        aq_s[256 + q4 * 32 + lane] + aq_s[384 + q4 * 32 + lane]);
+                            const double A_n = DM ? 0.0
+                                                        : (double)(aq_s[q4 * 32 + lane] + aq_s[128 + q4 * 32 + lane] +
+                                                                   aq_s[256 + q4 * 32 + lane] + aq_s[384 + q4 * 32 + lane]);
                             const int64_t o = (int64_t)perm[p] * Nt + j.j0 + jbeg;
 #pragma unroll
                             for (int jj = 0; jj < JG; jj++)
@@ -567,7 +579,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const float2 v = ls_s[(4 * h + q4) * 32 + lane];
                     if (v.y > 0.f) ssum += v.y * __expf(v.x - m);
                 }
-                const double A_n = (double)aqs;
+                const double A_n = DM ? 0.0 : (double)aqs;
                 out[perm[p]] = (double)m + (double)logf(ssum) - A_n - (double)pp.log_nt;
             }
         }
@@ -609,7 +621,9 @@ cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo
     while (NB > 2 && tc2_smem(pp.K, pp.M, KP, NB) > SMEM_LIMIT) NB--;
     const size_t smem = tc2_smem(pp.K, pp.M, KP, NB);
     if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(ile_tc2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool dm = pp.dm.on != 0;
+    cudaError_t e = cudaFuncSetAttribute(dm ? ile_tc2_kernel<false, true> : ile_tc2_kernel<false, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int sms = sm_count();
     const int64_t ntiles = (N + TILE - 1) / TILE;
@@ -625,8 +639,12 @@ cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo
     one.N = N;
     one.TP = TP;
     one.KP = KP;
-    ile_tc2_kernel<false><<<grid, NTHREADS, smem, st>>>(one, nullptr, nullptr, ntiles, pp.K, KP / 8,
-                                                        pp.M * (pp.M + 1) / 2, NB, NWCOL, full_grid, flags);
+    if (dm)
+        ile_tc2_kernel<false, true><<<grid, NTHREADS, smem, st>>>(one, nullptr, nullptr, ntiles, pp.K, KP / 8,
+                                                                  pp.M * (pp.M + 1) / 2, NB, NWCOL, full_grid, flags);
+    else
+        ile_tc2_kernel<false, false><<<grid, NTHREADS, smem, st>>>(one, nullptr, nullptr, ntiles, pp.K, KP / 8,
+                                                                   pp.M * (pp.M + 1) / 2, NB, NWCOL, full_grid, flags);
     return cudaGetLastError();
 }
 
@@ -648,12 +666,13 @@ cudaError_t ile_launch_tc2_batch(const Tc2Point *pts_dev, const int2 *items_dev,
     if (NB < 2 || NB > NBMAX || nwcol < NWCOL_MIN || nwcol > NWIN - 7) return cudaErrorInvalidValue;
     const size_t smem = tc2_smem(LK, LM, LKP, NB);
     if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(ile_tc2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(ile_tc2_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (grid <= 0) grid = sm_count();
     if (grid > nitems) grid = (int)nitems;
     Tc2Point none{};
-    ile_tc2_kernel<true><<<grid, NTHREADS, smem, st>>>(none, pts_dev, items_dev, nitems, LK, LKP / 8,
+    ile_tc2_kernel<true, false><<<grid, NTHREADS, smem, st>>>(none, pts_dev, items_dev, nitems, LK, LKP / 8,
                                                        LM * (LM + 1) / 2, NB, nwcol, 0, flags);
     return cudaGetLastError();
 }

@@ -146,6 +146,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     for name in ("ile_batch_create", "ile_batch_destroy", "ile_batch_set_points", "ile_batch_reset", "ile_batch_step",
                  "ile_batch_get", "ile_batch_run", "ile_batch_last_samples", "ile_batch_config", "ile_batch_tune"):
         getattr(lib, name).restype = i32
+    lib.ile_set_distance_marginalization.argtypes = [vp, i32, d, d]
+    lib.ile_set_distance_marginalization.restype = i32
+    lib.ile_dmarg_eval.argtypes = [vp, vp, vp, i64, vp, u]
+    lib.ile_dmarg_eval.restype = i32
     lib.ile_eval_grad.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, u]
     lib.ile_eval_grad.restype = i32
     lib.ile_integrate_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, u]
@@ -268,6 +272,20 @@ class Context:
         self._check(st, "ile_set_data")
         self.n_window = int(p.n_window)
         self.shape = (K, M, T)
+
+    def set_distance_marginalization(self, enable: bool = True, d_min: float = 100.0, d_max: float = 1000.0):
+        """Marginalise every returned likelihood over D (prior prop. to D^2 on [d_min, d_max])."""
+        self._check(self._lib.ile_set_distance_marginalization(self._h, 1 if enable else 0, float(d_min),
+                                                                float(d_max)), "ile_set_distance_marginalization")
+
+    def dmarg_eval(self, a, b):
+        """ln F(a, b) of the distance-marginalisation tables (host arrays)."""
+        a = np.ascontiguousarray(a, np.float64)
+        b = np.ascontiguousarray(np.broadcast_to(b, a.shape), np.float64)
+        out = np.zeros_like(a)
+        self._check(self._lib.ile_dmarg_eval(self._h, _np_ptr(a), _np_ptr(b), a.size, _np_ptr(out), 0),
+                    "ile_dmarg_eval")
+        return out
 
     # ---------------------------------------------------------------- host-pointer calls
     def eval(self, samples: np.ndarray, grid: bool = False) -> np.ndarray:

@@ -227,6 +227,41 @@ def batch_bench(ile, S, local, flush, iters=5, n_points=512, plain_iters=1):
     return line
 
 
+def dmarg_bench(ile, point, cfg, N, local, stream, flush, prec, steps=20):
+    """The benchmarked adaptive iteration with the likelihood marginalised over distance (the
+    D^2 prior on [100, 1000] Mpc through the device lookup tables; D not sampled adaptively)."""
+    import torch
+    ctx = ile.Context(local, stream, prec)
+    ctx.set_data(point)
+    t = time.perf_counter()
+    ctx.set_distance_marginalization(True, 100.0, 1000.0)
+    t_tables = time.perf_counter() - t
+    ctx.adapt_init(cfg)
+    ctx.adapt_step(3)
+    ctx.sync()
+    ctx.profile(True)
+    ctx.profile_read()
+    ms = 0.0
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        ctx.adapt_step(1)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    prof = ctx.profile_read()
+    res = ctx.adapt_get()
+    ctx.close()
+    return {"workload": "the benchmarked adaptive iteration (H1/L1/V1, 21 modes, N_t=512, 2^20 samples) with the "
+                        "likelihood marginalised over D (D^2 prior on [100, 1000] Mpc)",
+            "value": N * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "contraction": prec,
+            "stage_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[1]},
+            "table_build_s": t_tables, "ln_L_marg": res["ln_L"], "sigma_ln": res["sigma_ln"]}
+
+
 def adjoint_bench(ile, S, local, stream, flush, steps=10):
     """Gradient of ln L_marg-style weighted sums: ile_eval_grad over 2^18 samples of the
     3-detector, 21-mode, 512-bin point, all outputs (theta, Q, U, V), FP32 with FP64 sums."""
@@ -279,6 +314,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-point batched run")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) measurement")
+    ap.add_argument("--no-dmarg", action="store_true", help="skip the distance-marginalised measurement")
     ap.add_argument("--batch-points", type=int, default=512)
     ap.add_argument("--n-samples", type=int, default=None,
                     help="samples per step (default 2^20, the benchmarked workload; smaller only for profiling)")
@@ -418,6 +454,8 @@ def main():
             line["cpu_baseline"] = cpu_baseline(point)
         if not args.no_adjoint:
             line["adjoint"] = adjoint_bench(ile, S, local, stream, flush)
+        if not args.no_dmarg:
+            line["distance_marginalised"] = dmarg_bench(ile, point, cfg, N, local, stream, flush, args.prec)
         if not args.no_batch:
             line["batch"] = batch_bench(ile, S, local, flush, n_points=args.batch_points)
         print(json.dumps(line), flush=True)

@@ -161,6 +161,16 @@ ile_status ile_integrate(ile_ctx *ctx, const double *samples, const double *ln_p
  *   Histogram update: mass_b = (1 - eps) h_b / sum h + eps / 100, h_b the sum of the weights of
  *   the iteration's samples in bin b; eps in (0, 1].
  */
+/*
+ * Rotated detector-network-frame sky coordinates (Sec. on coordinate choices, "rotated
+ * detector-network-frame sky coordinates"): with sky_frame = 1 the first two sampling variables
+ * are the longitude phi' and sin(latitude') in a frame whose north pole is sky_pole (Earth-fixed,
+ * typically the baseline between two detectors, along which lines of constant latitude are lines
+ * of constant time delay).  Frame: p = pole / |pole|, e1 = z x p / |z x p| (x when p is along z),
+ * e2 = p x e1; the source direction n = cos(lat') cos(phi') e1 + cos(lat') sin(phi') e2 +
+ * sin(lat') p, then dec = asin(n_z), ra = gmst - atan2(-n_y, n_x) in [0, 2 pi).  The uniform sky
+ * prior is the same density in either frame; the histograms adapt in the rotated variables.
+ */
 typedef struct {
     uint64_t seed;
     uint32_t point_id;
@@ -169,6 +179,8 @@ typedef struct {
     unsigned adapt_mask;  /* bit d: dimension d adaptive */
     double eps;           /* histogram floor, (0, 1] */
     double lo[ILE_NDIM], hi[ILE_NDIM];
+    int sky_frame;        /* 0: sky variables 0, 1 are (ra, sin dec); 1: rotated network frame */
+    double sky_pole[3];   /* sky_frame 1: Earth-fixed vector of the frame's pole (e.g. r_L1 - r_H1) */
 } ile_adapt_cfg;
 
 #define ILE_ADAPT_LOG 64
@@ -269,6 +281,8 @@ typedef struct {
     uint32_t adapt_mask;
     double eps;
     double lo[ILE_NDIM], hi[ILE_NDIM];
+    int sky_frame;
+    double sky_pole[3];
 } ile_point_desc;
 
 typedef struct ile_batch ile_batch; /* opaque; owns the device copies of all points */

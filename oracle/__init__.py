@@ -54,6 +54,7 @@ class _Sampler(ctypes.Structure):
     _fields_ = [
         ("lo", ctypes.c_double * NDIM), ("hi", ctypes.c_double * NDIM),
         ("adaptive", ctypes.c_int * NDIM), ("cdf", ctypes.c_void_p),
+        ("sky", ctypes.c_int), ("pole", ctypes.c_double * 3), ("gmst", ctypes.c_double),
     ]
 
 
@@ -79,6 +80,7 @@ def _load():
             lib.orc_hist.argtypes = [vp, vp, ctypes.c_long, vp]
             lib.orc_cdf_from_hist.argtypes = [vp, d, vp]
             lib.orc_cdf_uniform.argtypes = [vp]
+            lib.orc_sky_frame.argtypes = [vp, vp, vp, vp]
             lib.orc_dmarg_lnF.argtypes = [d, d, d, d, d]
             lib.orc_dmarg_lnF.restype = d
             lib.orc_lnL_dmarg.argtypes = [ctypes.POINTER(_Point), vp, ctypes.c_long, d, d, vp]
@@ -241,12 +243,22 @@ def philox(ctr, key):
     return out
 
 
-def make_sampler(lo, hi, adaptive, cdf):
+def make_sampler(lo, hi, adaptive, cdf, sky_pole=None, gmst=0.0):
+    """sky_pole: pole of the rotated network sky frame (variables 0, 1 in that frame), or None."""
     cdf = np.ascontiguousarray(cdf, dtype=np.uint64).reshape(NDIM, NBINS + 1)
+    pole = (0.0, 0.0, 0.0) if sky_pole is None else tuple(float(x) for x in sky_pole)
     s = _Sampler((ctypes.c_double * NDIM)(*lo), (ctypes.c_double * NDIM)(*hi),
-                 (ctypes.c_int * NDIM)(*[int(a) for a in adaptive]), _ptr(cdf).value)
+                 (ctypes.c_int * NDIM)(*[int(a) for a in adaptive]), _ptr(cdf).value, 0 if sky_pole is None else 1,
+                 (ctypes.c_double * 3)(*pole), float(gmst))
     s._keep = cdf
     return s
+
+
+def sky_frame(pole):
+    e1, e2, p = np.zeros(3), np.zeros(3), np.zeros(3)
+    pole = np.ascontiguousarray(pole, dtype=np.float64)
+    _load().orc_sky_frame(_ptr(pole), _ptr(e1), _ptr(e2), _ptr(p))
+    return e1, e2, p
 
 
 def sample(sampler, seed: int, it: int, point: int, n0: int, N: int):
@@ -281,7 +293,7 @@ def cdf_uniform():
 
 # ------------------------------------------------------------------------------------ S0-S6 loop
 def adapt_run(point, seed: int, N: int, n_iter: int, adapt_mask: int, eps: float, lo, hi, point_id: int = 0,
-              nthreads: int = 0, cdf0=None, iter0: int = 0):
+              nthreads: int = 0, cdf0=None, iter0: int = 0, sky_pole=None):
     """Adaptive-Cartesian integration in the order of Sec. "GPU-accelerated Monte Carlo integration":
     for each iteration draw N samples from the separable sampling prior, evaluate lnL_t, accumulate
     the Monte Carlo sums of Eq. (eq:lnL:MonteCarlo) (pooled over iterations, each sample weighted by
@@ -296,7 +308,7 @@ def adapt_run(point, seed: int, N: int, n_iter: int, adapt_mask: int, eps: float
     iters = []
     last = None
     for it in range(iter0, iter0 + n_iter):
-        smp = make_sampler(lo, hi, adaptive, cdf)
+        smp = make_sampler(lo, hi, adaptive, cdf, sky_pole, point.gmst)
         theta, lwp, bins = sample(smp, seed, it, point_id, 0, N)
         lnl = lnL_t(point, theta, nthreads)
         lnw = lnl + lwp

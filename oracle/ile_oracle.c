@@ -44,6 +44,8 @@
  *   R21 gradient: exact derivative of lnL_t with the interpolation weight differentiated inside
  *      a bin (one-sided at bin edges: the slope of the bin floor(x) lies in); the entries of
  *      Q, U and V are independent real pairs (no Hermitian / symmetric tying of U and V).
+ *   R23 rotated network sky frame: pole p along a detector baseline, e1 = z x p normalised,
+ *      e2 = p x e1; sampling variables (longitude, sin latitude) in (e1, e2, p).
  *   R22 distance marginalisation: the distance integral sits inside the window sum, i.e. the
  *      marginal of (1/N_t) sum_j exp(a_j x - b x^2) over p(D) prop. to D^2 on [D_min, D_max],
  *      x = D_ref / D, with a_j, b the data and quadratic terms at D = D_ref.
@@ -362,7 +364,32 @@ typedef struct {
     double lo[ORC_NDIM], hi[ORC_NDIM];
     int adaptive[ORC_NDIM];
     const uint64_t *cdf; /* [7][101]; rows of fixed dimensions are ignored */
+    int sky;             /* 1: variables 0, 1 are (longitude, sin latitude) in the rotated frame */
+    double pole[3];      /* Earth-fixed pole of the rotated frame */
+    double gmst;
 } orc_sampler;
+
+/* Rotated network-frame sky (R23): orthonormal (e1, e2, p) with p = pole / |pole|,
+ * e1 = (z x p) / |z x p| (x when p is along z), e2 = p x e1. */
+void orc_sky_frame(const double pole[3], double e1[3], double e2[3], double p[3])
+{
+    double n = sqrt(pole[0] * pole[0] + pole[1] * pole[1] + pole[2] * pole[2]);
+    for (int i = 0; i < 3; i++) p[i] = pole[i] / n;
+    e1[0] = -p[1];
+    e1[1] = p[0];
+    e1[2] = 0.0;
+    double m = sqrt(e1[0] * e1[0] + e1[1] * e1[1]);
+    if (m < 1e-6) {
+        e1[0] = 1.0;
+        e1[1] = 0.0;
+    } else {
+        e1[0] /= m;
+        e1[1] /= m;
+    }
+    e2[0] = p[1] * e1[2] - p[2] * e1[1];
+    e2[1] = p[2] * e1[0] - p[0] * e1[2];
+    e2[2] = p[0] * e1[1] - p[1] * e1[0];
+}
 
 /* Uniform in (0, 1) from the top 23 bits of one 32-bit word. */
 static double unit23(uint32_t w)
@@ -419,6 +446,16 @@ void orc_sample(const orc_sampler *S, uint64_t seed, uint32_t iter, uint32_t poi
             double phys = u;
             if (d == 1) phys = asin(u);
             if (d == 3) phys = acos(u);
+            if (S->sky && d == 1) {
+                /* (longitude, latitude) in the rotated frame -> Earth-fixed direction -> (ra, dec) */
+                double e1[3], e2[3], p[3], nv[3], lon = theta[s], lat = phys;
+                orc_sky_frame(S->pole, e1, e2, p);
+                for (int i = 0; i < 3; i++) nv[i] = cos(lat) * cos(lon) * e1[i] + cos(lat) * sin(lon) * e2[i] + sin(lat) * p[i];
+                double ra = S->gmst - atan2(-nv[1], nv[0]);
+                ra -= 2.0 * ORC_PI * floor(ra / (2.0 * ORC_PI));
+                theta[s] = ra;
+                phys = asin(nv[2]);
+            }
             theta[(size_t)d * N + s] = phys;
             bins[(size_t)d * N + s] = (uint8_t)bin;
         }

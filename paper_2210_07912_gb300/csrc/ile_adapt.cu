@@ -100,6 +100,21 @@ __device__ __forceinline__ void sample_one(const IleSamplerParams &sp, const Sam
         float phys = u;
         if (d == 1) phys = asinf(fminf(fmaxf(u, -1.f), 1.f));
         if (d == 3) phys = acosf(fminf(fmaxf(u, -1.f), 1.f));
+        if (sp.sky && d == 1) {
+            // rotated network frame: (phi', lat') -> Earth-fixed direction -> (ra, dec)
+            float sl, cl, sf, cf;
+            sincosf(phys, &sl, &cl);
+            sincosf((float)theta[n], &sf, &cf);  // phi' was stored at d = 0
+            const float a = cl * cf, b = cl * sf;
+            const float nx = sp.rot[0] * a + sp.rot[1] * b + sp.rot[2] * sl;
+            const float ny = sp.rot[3] * a + sp.rot[4] * b + sp.rot[5] * sl;
+            const float nz = sp.rot[6] * a + sp.rot[7] * b + sp.rot[8] * sl;
+            float ra = sp.gmst - atan2f(-ny, nx);
+            const float twopi = 2.f * ILE_PI_F;
+            ra -= twopi * floorf(ra / twopi);
+            theta[n] = (double)ra;
+            phys = asinf(fminf(fmaxf(nz, -1.f), 1.f));
+        }
         theta[(int64_t)d * N + n] = (double)phys;
         bins[(int64_t)d * N + n] = (uint8_t)bin;
     }

@@ -389,6 +389,28 @@ ile_status ile_set_precision(ile_ctx *ctx, ile_prec prec) {
 
 }  // extern "C"
 
+bool ile_sky_frame(const double pole[3], float rot[9]) {
+    const double n = sqrt(pole[0] * pole[0] + pole[1] * pole[1] + pole[2] * pole[2]);
+    if (!(n > 0.0) || !isfinite(n)) return false;
+    const double p[3] = {pole[0] / n, pole[1] / n, pole[2] / n};
+    double e1[3] = {-p[1], p[0], 0.0};  // z x p
+    double m = sqrt(e1[0] * e1[0] + e1[1] * e1[1]);
+    if (m < 1e-6) {
+        e1[0] = 1.0;
+        e1[1] = e1[2] = 0.0;
+    } else {
+        e1[0] /= m;
+        e1[1] /= m;
+    }
+    const double e2[3] = {p[1] * e1[2] - p[2] * e1[1], p[2] * e1[0] - p[0] * e1[2], p[0] * e1[1] - p[1] * e1[0]};
+    for (int r = 0; r < 3; r++) {
+        rot[3 * r + 0] = (float)e1[r];
+        rot[3 * r + 1] = (float)e2[r];
+        rot[3 * r + 2] = (float)p[r];
+    }
+    return true;
+}
+
 // Pooled accumulators (max ln w, S1, S2, n) and the iteration log -> the summary fields of an
 // ile_adapt_result (cdf and hist are filled by the caller).
 void ile_fill_result(const double pooled[4], const double *ilog, int n_iter, ile_adapt_result *out) {
@@ -732,6 +754,7 @@ ile_status ile_adapt_init(ile_ctx *ctx, const ile_adapt_cfg *cfg, const ile_adap
     if (cfg->n_per_iter < 1 || cfg->n_per_iter > ((int64_t)1 << 23)) return ILE_E_ARG;
     if (!(cfg->eps > 0.0 && cfg->eps <= 1.0)) return ILE_E_ARG;
     if (cfg->adapt_mask >> ILE_NDIM) return ILE_E_ARG;
+    if (cfg->sky_frame != 0 && cfg->sky_frame != 1) return ILE_E_ARG;
     for (int d = 0; d < ILE_NDIM; d++)
         if (!(cfg->hi[d] > cfg->lo[d]) || !isfinite(cfg->lo[d]) || !isfinite(cfg->hi[d])) return ILE_E_ARG;
     if (!(cfg->lo[5] > 0.0) || cfg->lo[1] < -1.0 || cfg->hi[1] > 1.0 || cfg->lo[3] < -1.0 || cfg->hi[3] > 1.0)
@@ -748,6 +771,9 @@ ile_status ile_adapt_init(ile_ctx *ctx, const ile_adapt_cfg *cfg, const ile_adap
     sp.key0 = (uint32_t)cfg->seed;
     sp.key1 = (uint32_t)(cfg->seed >> 32);
     sp.point = cfg->point_id;
+    sp.gmst = ctx->pp.gmst;
+    sp.sky = cfg->sky_frame;
+    if (sp.sky && !ile_sky_frame(cfg->sky_pole, sp.rot)) return ILE_E_ARG;
     ctx->sp = sp;
     ctx->eps = cfg->eps;
     ctx->adapt_N = cfg->n_per_iter;

@@ -157,6 +157,11 @@ bool desc_ok(const ile_point_desc &d) {
     for (int k = 0; k < ILE_NDIM; k++)
         if (!(d.hi[k] > d.lo[k]) || !isfinite(d.lo[k]) || !isfinite(d.hi[k])) return false;
     if (!(d.lo[5] > 0.0) || d.lo[1] < -1.0 || d.hi[1] > 1.0 || d.lo[3] < -1.0 || d.hi[3] > 1.0) return false;
+    if (d.sky_frame != 0 && d.sky_frame != 1) return false;
+    if (d.sky_frame) {
+        float rot[9];
+        if (!ile_sky_frame(d.sky_pole, rot)) return false;
+    }
     return true;
 }
 
@@ -374,6 +379,9 @@ ile_status ile_batch_set_points(ile_batch *b, int n_points, const ile_point_desc
         q.sp.key0 = (uint32_t)d.seed;
         q.sp.key1 = (uint32_t)(d.seed >> 32);
         q.sp.point = d.point_id;
+        q.sp.gmst = pp.gmst;
+        q.sp.sky = d.sky_frame;
+        if (d.sky_frame) ile_sky_frame(d.sky_pole, q.sp.rot);
         q.eps = d.eps;
         q.N = b->N[p];
         q.off = b->off[p];

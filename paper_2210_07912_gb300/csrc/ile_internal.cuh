@@ -144,7 +144,13 @@ struct IleSamplerParams {
     unsigned adapt_mask;               // bit d: dimension d is drawn from its histogram
     uint32_t key0, key1;               // Philox key (seed)
     uint32_t point;                    // Philox counter word identifying the intrinsic point
+    int sky;                           // 1: variables 0, 1 are the rotated frame's (phi', sin lat')
+    float rot[9];                      // rotated frame: columns e1, e2, p (Earth-fixed), row-major
+    float gmst;
 };
+
+// Rotated-frame basis from a pole vector (host; see ile.h): returns false for a zero vector.
+bool ile_sky_frame(const double pole[3], float rot[9]);
 
 // One point of a batched adaptive run (ile_batch.cu): its sampler and the location of its
 // samples in the batch's concatenated per-sample arrays (theta and bins at ILE_NDIM * off,

@@ -28,7 +28,8 @@ ADAPT_LOG = 64
 class AdaptCfg(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("point_id", ctypes.c_uint32), ("n_per_iter", ctypes.c_int64),
                 ("n_iter", ctypes.c_int), ("adapt_mask", ctypes.c_uint), ("eps", ctypes.c_double),
-                ("lo", ctypes.c_double * NDIM), ("hi", ctypes.c_double * NDIM)]
+                ("lo", ctypes.c_double * NDIM), ("hi", ctypes.c_double * NDIM), ("sky_frame", ctypes.c_int),
+                ("sky_pole", ctypes.c_double * 3)]
 
 
 class AdaptResult(ctypes.Structure):
@@ -46,7 +47,8 @@ class PointDesc(ctypes.Structure):
                 ("U", ctypes.c_void_p), ("V", ctypes.c_void_p), ("n_window", ctypes.c_int),
                 ("gmst_rad", ctypes.c_double), ("d_ref_mpc", ctypes.c_double), ("n_samples", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("point_id", ctypes.c_uint32), ("adapt_mask", ctypes.c_uint32),
-                ("eps", ctypes.c_double), ("lo", ctypes.c_double * NDIM), ("hi", ctypes.c_double * NDIM)]
+                ("eps", ctypes.c_double), ("lo", ctypes.c_double * NDIM), ("hi", ctypes.c_double * NDIM),
+                ("sky_frame", ctypes.c_int), ("sky_pole", ctypes.c_double * 3)]
 
 
 TUNE_MAX = 16
@@ -67,12 +69,15 @@ def default_ranges(fs: float = 4096.0, tc_max: float | None = None, d_min: float
 
 
 def make_adapt_cfg(seed: int, n_per_iter: int, n_iter: int = 1, adapt_mask: int = 0b11, eps: float = 0.1,
-                   point_id: int = 0, lo=None, hi=None) -> AdaptCfg:
+                   point_id: int = 0, lo=None, hi=None, sky_pole=None) -> AdaptCfg:
+    """sky_pole: Earth-fixed pole vector of the rotated network sky frame (e.g. r_L1 - r_H1); then
+    sampling variables 0, 1 are (phi', sin lat') in that frame.  None: (ra, sin dec)."""
     dlo, dhi = default_ranges()
     lo = dlo if lo is None else lo
     hi = dhi if hi is None else hi
+    pole = (0.0, 0.0, 0.0) if sky_pole is None else tuple(float(x) for x in sky_pole)
     return AdaptCfg(seed, point_id, n_per_iter, n_iter, adapt_mask, eps, (ctypes.c_double * NDIM)(*lo),
-                    (ctypes.c_double * NDIM)(*hi))
+                    (ctypes.c_double * NDIM)(*hi), 0 if sky_pole is None else 1, (ctypes.c_double * 3)(*pole))
 
 
 def result_dict(r: AdaptResult) -> dict:
@@ -489,6 +494,9 @@ class Batch:
             d.adapt_mask, d.eps = c.adapt_mask, c.eps
             for k in range(NDIM):
                 d.lo[k], d.hi[k] = c.lo[k], c.hi[k]
+            d.sky_frame = c.sky_frame
+            for k in range(3):
+                d.sky_pole[k] = c.sky_pole[k]
         return descs, keep
 
     def set_points(self, points, cfgs):

@@ -412,3 +412,41 @@ def test_pulse_injection_peaks_at_true_arrival(orc):
         th = S.prior_samples(rng, 100)
         for n in range(th.shape[1]):
             assert np.all(orc.lnL_grid(point, th[:, n])[0] <= A0 * (1 + 1e-12))
+
+
+# ------------------------------------------------------------------------------ rotated sky frame
+def test_rotated_sky_frame_geometry_and_uniformity(orc):
+    """The rotated network frame (R23): orthonormal and right-handed with the pole as third axis;
+    a sample's rotated latitude is its angle to the pole; uniform tables give a uniform sky
+    (the prior is rotation invariant); latitude +90 deg maps onto the pole direction."""
+    sps = pytest.importorskip("scipy.stats")
+    _, pos = S.detector_arrays(2)
+    pole = pos[1] - pos[0]
+    e1, e2, p = orc.sky_frame(pole)
+    Mx = np.stack([e1, e2, p])
+    np.testing.assert_allclose(Mx @ Mx.T, np.eye(3), atol=1e-14)
+    np.testing.assert_allclose(np.cross(e1, e2), p, atol=1e-14)
+    np.testing.assert_allclose(p, pole / np.linalg.norm(pole), atol=1e-15)
+    lo, hi = [0.0, -1.0, 0.0, -1.0, 0.0, 100.0, -1e-3], [2 * np.pi, 1.0, np.pi, 1.0, 2 * np.pi, 1000.0, 1e-3]
+    gmst = 0.7
+    tabs = np.stack([orc.cdf_uniform() for _ in range(7)])
+    smp = orc.make_sampler(lo, hi, [0] * 7, tabs, pole, gmst)
+    th, lw, _ = orc.sample(smp, 99, 0, 0, 0, 20000)
+    assert np.all(lw == 0.0)
+    assert sps.kstest(np.sin(th[1]), "uniform", args=(-1, 2)).pvalue > 1e-3
+    assert sps.kstest(th[0], "uniform", args=(0, 2 * np.pi)).pvalue > 1e-3
+    # the rotated latitude (from the same words with no rotation) is the angle to the pole
+    plain = orc.make_sampler(lo, hi, [0] * 7, tabs)
+    thp, _, _ = orc.sample(plain, 99, 0, 0, 0, 2000)
+    g = gmst - th[0, :2000]
+    n = np.stack([np.cos(th[1, :2000]) * np.cos(g), -np.cos(th[1, :2000]) * np.sin(g), np.sin(th[1, :2000])])
+    np.testing.assert_allclose(p @ n, np.sin(thp[1]), atol=1e-12)
+    # longitude: angle around the pole from e1
+    np.testing.assert_allclose(np.arctan2(e2 @ n, e1 @ n) % (2 * np.pi), thp[0] % (2 * np.pi), atol=1e-9)
+    # a narrow band at latitude ~ +90 deg lands on the pole
+    lo2 = list(lo)
+    lo2[1] = 1 - 1e-9
+    th2, _, _ = orc.sample(orc.make_sampler(lo2, hi, [0] * 7, tabs, pole, gmst), 5, 0, 0, 0, 50)
+    g2 = gmst - th2[0]
+    n2 = np.stack([np.cos(th2[1]) * np.cos(g2), -np.cos(th2[1]) * np.sin(g2), np.sin(th2[1])])
+    assert np.all(p @ n2 > 1 - 1e-8)

@@ -121,6 +121,23 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
  */
 ile_status ile_set_distance_marginalization(ile_ctx *ctx, int enable, double d_min_mpc, double d_max_mpc);
 
+/*
+ * The inner-product arrays of Eq. (eq:QUV) of one intrinsic point, in FP64 on the device, from
+ * the mode waveforms, the detectors' noise PSDs and data (frequency domain, two-sided, L bins in
+ * FFT order: bin m is f = m df for m < L/2, (m - L) df otherwise):
+ *   Q[k][a][i] = 2 df sum_{|f|>f_low} e^{2 pi i f t_i} conj(h_a(f)) d_k(f) / S_k(f),
+ *                t_i = t_start_s + i / fs_hz, i < T_ext;
+ *   U[k][a][b] = 2 df sum_{|f|>f_low} conj(h_a(f)) h_b(f) / S_k(f);
+ *   V[k][a][b] = 2 df sum_{|f|>f_low} h_a(-f) h_b(f) / S_k(f)   (<h_a^* | h_b>).
+ *   h: [n_modes][L][2]; psd: [n_det][L] (S_k at |f| of each bin); d: [n_det][L][2];
+ *   Q: [n_det][n_modes][T_ext][2], U, V: [n_det][n_modes][n_modes][2] -- the layouts
+ *   ile_set_data takes.  flags: ILE_DEVICE_PTRS (else host arrays).  Synchronous; allocates
+ *   16 K M L bytes of scratch for the call.  2 <= L <= 2^24; f_low < 0 keeps every bin.
+ */
+ile_status ile_build_quv(ile_ctx *ctx, int n_det, int n_modes, int64_t L, const double *h, const double *psd,
+                         const double *d, double df, double f_low, double t_start_s, double fs_hz, int T_ext,
+                         double *Q, double *U, double *V, unsigned flags);
+
 /* ln F(a[i], b[i]) from the context's distance-marginalisation tables (the per-bin term of the
  * distance-marginalised likelihood), for inspection and tests.  ILE_E_STATE unless enabled.
  * flags: ILE_DEVICE_PTRS (else host arrays, synchronous). */

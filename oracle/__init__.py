@@ -226,6 +226,34 @@ def lnL_dmarg(point, samples, d_min, d_max):
     return out
 
 
+def quv_from_modes(hf, psd, d_f, df, f_low, t_start, fs, T_ext):
+    """Eq. (eq:QUV) written out in FP64 for discrete two-sided frequency series in FFT order:
+    Q_k,a(t) = 2 df sum_{|f|>f_low} e^{2 pi i f t} conj(h_a(f)) d_k(f) / S_k(f) at
+    t = t_start + i / fs (i < T_ext); U_k,ab = <h_a|h_b>_k; V_k,ab = <h_a^*|h_b>_k, where the
+    Fourier transform of conj(h_a(t)) is conj(h_a(-f)).  Returns complex Q (K, M, T_ext), U, V (K, M, M)."""
+    hf = np.asarray(hf, complex)
+    d_f = np.asarray(d_f, complex)
+    psd = np.asarray(psd, float)
+    M, L = hf.shape
+    K = d_f.shape[0]
+    f = np.fft.fftfreq(L, 1.0 / (L * df))
+    keep = np.abs(f) > f_low
+    hstar = np.conj(hf[:, (-np.arange(L)) % L])
+    U = np.zeros((K, M, M), complex)
+    V = np.zeros((K, M, M), complex)
+    Q = np.zeros((K, M, T_ext), complex)
+    times = t_start + np.arange(T_ext) / fs
+    phase = np.exp(2j * np.pi * np.outer(times, f[keep]))  # (T_ext, bins kept)
+    for k in range(K):
+        w = 2.0 * df / psd[k]
+        for a in range(M):
+            for b in range(M):
+                U[k, a, b] = np.sum((np.conj(hf[a]) * hf[b] * w)[keep])
+                V[k, a, b] = np.sum((np.conj(hstar[a]) * hf[b] * w)[keep])
+            Q[k, a] = phase @ (np.conj(hf[a]) * d_f[k] * w)[keep]
+    return Q, U, V
+
+
 # ------------------------------------------------------------------------------------ S6
 def mc_stats(lnw):
     """Eq. (eq:lnL:MonteCarlo) in log space: dict(ln_I, sigma_ln, n_eff, ess, m, s1, s2)."""

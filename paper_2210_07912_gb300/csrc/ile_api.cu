@@ -568,6 +568,48 @@ ile_status ile_set_distance_marginalization(ile_ctx *ctx, int enable, double d_m
     return ILE_OK;
 }
 
+ile_status ile_build_quv(ile_ctx *ctx, int n_det, int n_modes, int64_t L, const double *h, const double *psd,
+                         const double *d, double df, double f_low, double t_start_s, double fs_hz, int T_ext,
+                         double *Q, double *U, double *V, unsigned flags) {
+    if (!ctx || !h || !psd || !d || !Q || !U || !V) return ILE_E_ARG;
+    if (n_det < 1 || n_det > ILE_MAX_DET || n_modes < 1 || n_modes > ILE_MAX_MODES) return ILE_E_ARG;
+    if (L < 2 || L > ((int64_t)1 << 24) || T_ext < 1 || T_ext > ILE_MAX_TEXT) return ILE_E_ARG;
+    if (!(df > 0.0) || !(fs_hz > 0.0) || !isfinite(f_low) || !isfinite(t_start_s)) return ILE_E_ARG;
+    const int K = n_det, M = n_modes;
+    const size_t nh = 2 * (size_t)M * L, nd = 2 * (size_t)K * L, ns = (size_t)K * L, nz = 2 * (size_t)K * M * L;
+    const size_t nq = 2 * (size_t)K * M * T_ext, nuv = 2 * (size_t)K * M * M;
+    DeviceGuard g(ctx->device);
+    double *buf = nullptr;
+    const bool dev = (flags & ILE_DEVICE_PTRS) != 0;
+    const size_t n_all = nz + (dev ? 0 : nh + nd + ns + nq + 2 * nuv);
+    CK(cudaMalloc((void **)&buf, sizeof(double) * n_all));
+    double *z = buf, *dh = (double *)h, *dp = (double *)psd, *dd = (double *)d, *dQ = Q, *dU = U, *dV = V;
+    cudaError_t e = cudaSuccess;
+    if (!dev) {
+        dh = z + nz;
+        dd = dh + nh;
+        dp = dd + nd;
+        dQ = dp + ns;
+        dU = dQ + nq;
+        dV = dU + nuv;
+        e = cudaMemcpyAsync(dh, h, sizeof(double) * nh, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dd, d, sizeof(double) * nd, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dp, psd, sizeof(double) * ns, cudaMemcpyHostToDevice, ctx->stream);
+    }
+    if (e == cudaSuccess)
+        e = ile_launch_quv(K, M, L, dh, dp, dd, df, f_low, t_start_s, fs_hz, T_ext, z, dQ, dU, dV, ctx->stream);
+    if (e == cudaSuccess && !dev) {
+        e = cudaMemcpyAsync(Q, dQ, sizeof(double) * nq, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(U, dU, sizeof(double) * nuv, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(V, dV, sizeof(double) * nuv, cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    // the scratch is released after the work that uses it (stream-ordered wait)
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(buf);
+    CK(e);
+    return ILE_OK;
+}
+
 ile_status ile_dmarg_eval(ile_ctx *ctx, const double *a, const double *b, int64_t n, double *out, unsigned flags) {
     if (!ctx || n < 0) return ILE_E_ARG;
     if (!ctx->pp.dm.on) return ILE_E_STATE;

@@ -324,6 +324,12 @@ cudaError_t ile_build_dmarg(double d_min, double d_max, double d_ref, void *buf,
 cudaError_t ile_launch_dmarg_eval(const DmargParams &dm, const double *a, const double *b, int64_t n, double *out,
                                   cudaStream_t st);
 
+// inner-product arrays of Eq. (eq:QUV) from modes, PSDs and data (ile_quv.cu); z: scratch of
+// K * M * L complex doubles
+cudaError_t ile_launch_quv(int K, int M, int64_t L, const double *h, const double *psd, const double *d, double df,
+                           double f_low, double t_start, double fs, int T_ext, double *z, double *Q, double *U,
+                           double *V, cudaStream_t st);
+
 // ------------------------------------------------------------------ host helpers (ile_api.cu)
 ile_status ile_prepare_point(int n_det, int n_modes, const int *lm, const double *det_tensor,
                              const double *det_pos_m, const double *Q, int T_ext, double t_start_s, double fs_hz,

@@ -154,6 +154,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ile_set_distance_marginalization.argtypes = [vp, i32, d, d]
     lib.ile_set_distance_marginalization.restype = i32
     lib.ile_dmarg_eval.argtypes = [vp, vp, vp, i64, vp, u]
+    lib.ile_build_quv.argtypes = [vp, i32, i32, i64, vp, vp, vp, d, d, d, d, i32, vp, vp, vp, u]
+    lib.ile_build_quv.restype = i32
     lib.ile_dmarg_eval.restype = i32
     lib.ile_eval_grad.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, u]
     lib.ile_eval_grad.restype = i32
@@ -282,6 +284,23 @@ class Context:
         """Marginalise every returned likelihood over D (prior prop. to D^2 on [d_min, d_max])."""
         self._check(self._lib.ile_set_distance_marginalization(self._h, 1 if enable else 0, float(d_min),
                                                                 float(d_max)), "ile_set_distance_marginalization")
+
+    def build_quv(self, h, psd, d, df: float, f_low: float, t_start: float, fs: float, T_ext: int):
+        """Q (K, M, T_ext), U, V (K, M, M) complex of Eq. (eq:QUV) from modes h (M, L), PSDs (K, L)
+        and data d (K, L), two-sided frequency series in FFT order (host arrays)."""
+        h = np.ascontiguousarray(np.stack([np.real(h), np.imag(h)], -1), np.float64)
+        dd = np.ascontiguousarray(np.stack([np.real(d), np.imag(d)], -1), np.float64)
+        S = np.ascontiguousarray(psd, np.float64)
+        M, L = h.shape[:2]
+        K = dd.shape[0]
+        Q = np.zeros((K, M, T_ext, 2))
+        U = np.zeros((K, M, M, 2))
+        V = np.zeros((K, M, M, 2))
+        self._check(self._lib.ile_build_quv(self._h, K, M, L, _np_ptr(h), _np_ptr(S), _np_ptr(dd), float(df),
+                                            float(f_low), float(t_start), float(fs), int(T_ext), _np_ptr(Q),
+                                            _np_ptr(U), _np_ptr(V), 0), "ile_build_quv")
+        c = lambda x: x[..., 0] + 1j * x[..., 1]
+        return c(Q), c(U), c(V)
 
     def dmarg_eval(self, a, b):
         """ln F(a, b) of the distance-marginalisation tables (host arrays)."""

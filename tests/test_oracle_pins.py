@@ -128,6 +128,11 @@ def test_wigner_d_matches_sympy(orc):
 
 
 # ------------------------------------------------------------------------------ S3-S5 likelihood
+def orc_module():
+    import oracle
+    return oracle
+
+
 def _fd_setup(seed, K=2, M=3, L=512, fs=4096.0, Nt=32, T_ext=128):
     """Synthetic modes h_lm, PSDs and data; Q, U, V straight from Eq. (eq:QUV)."""
     rng = np.random.default_rng(seed)
@@ -140,16 +145,10 @@ def _fd_setup(seed, K=2, M=3, L=512, fs=4096.0, Nt=32, T_ext=128):
     d_t = rng.normal(size=(K, L)) * 3.0  # arbitrary real data per detector
     d_f = np.fft.fft(d_t, axis=1) * dt
 
-    def ip(af, bf, k):  # <a|b> = 2 sum_f conj(a~) b~ / S_k df  (two-sided)
-        return 2.0 * np.sum(af.conj() * bf / psd[k], axis=-1) * df
-
-    hstar_f = np.conj(hf[:, (-np.arange(L)) % L])  # FT of conj(h_lm(t))
-    U = np.array([[[ip(hf[a], hf[b], k) for b in range(M)] for a in range(M)] for k in range(K)])
-    V = np.array([[[ip(hstar_f[a], hf[b], k) for b in range(M)] for a in range(M)] for k in range(K)])
     t_start = -(T_ext // 2) / fs
-    times = t_start + np.arange(T_ext) / fs
-    phase = np.exp(2j * np.pi * f[None, :] * times[:, None])  # (T_ext, L)
-    Q = np.array([[phase @ (2.0 * hf[a].conj() * d_f[k] / psd[k] * df) for a in range(M)] for k in range(K)])
+    # Q, U, V from the oracle's Eq. (eq:QUV); the decomposition test below then ties them (and the
+    # likelihood built on them) to inner products of the full waveform with the data
+    Q, U, V = orc_module().quv_from_modes(hf, psd, d_f, df, -1.0, t_start, fs, T_ext)  # every bin
     tens, _ = S.detector_arrays(K)
     point = S.Point(lm=np.array(lm, np.int32), det_tensor=tens, det_pos=np.zeros((K, 3)), Q=Q, U=U, V=V,
                     t_start=t_start, fs=fs, n_window=Nt)
@@ -450,3 +449,24 @@ def test_rotated_sky_frame_geometry_and_uniformity(orc):
     g2 = gmst - th2[0]
     n2 = np.stack([np.cos(th2[1]) * np.cos(g2), -np.cos(th2[1]) * np.sin(g2), np.sin(th2[1])])
     assert np.all(p @ n2 > 1 - 1e-8)
+
+
+def test_quv_structure_and_frequency_cut(orc):
+    """U Hermitian and positive semi-definite, V symmetric (Eq. (eq:QUV)); Q at t = 0 is the plain
+    sum; bins at or below f_low contribute nothing."""
+    point, aux = _fd_setup(4)
+    hf, psd, d_f, df = aux["hf"], aux["psd"], aux["d_f"], aux["df"]
+    Q, U, V = orc.quv_from_modes(hf, psd, d_f, df, -1.0, 0.0, 4096.0, 3)
+    for k in range(U.shape[0]):
+        np.testing.assert_allclose(U[k], U[k].conj().T, atol=1e-12)
+        assert np.linalg.eigvalsh(U[k]).min() > -1e-10
+        np.testing.assert_allclose(V[k], V[k].T, atol=1e-12)
+        for a in range(hf.shape[0]):
+            assert abs(Q[k, a, 0] - 2 * df * np.sum(np.conj(hf[a]) * d_f[k] / psd[k])) < 1e-10
+    f = np.fft.fftfreq(hf.shape[1], 1.0 / (hf.shape[1] * df))
+    hcut = hf.copy()
+    hcut[:, np.abs(f) <= 200.0] = 7.0  # junk below the cut must not matter
+    Q2, U2, V2 = orc.quv_from_modes(hcut, psd, d_f, df, 200.0, 0.0, 4096.0, 3)
+    Q3, U3, V3 = orc.quv_from_modes(hf, psd, d_f, df, 200.0, 0.0, 4096.0, 3)
+    np.testing.assert_allclose(U2, U3, atol=1e-12)
+    np.testing.assert_allclose(Q2, Q3, atol=1e-12)

@@ -50,11 +50,22 @@ class _Point(ctypes.Structure):
     ]
 
 
+GMM_MAX = 8
+
+
+class _Gmm1(ctypes.Structure):
+    _fields_ = [
+        ("C", ctypes.c_int), ("w", ctypes.c_double * GMM_MAX), ("mu", ctypes.c_double * GMM_MAX),
+        ("sigma", ctypes.c_double * GMM_MAX), ("n", ctypes.c_double),
+    ]
+
+
 class _Sampler(ctypes.Structure):
     _fields_ = [
         ("lo", ctypes.c_double * NDIM), ("hi", ctypes.c_double * NDIM),
         ("adaptive", ctypes.c_int * NDIM), ("cdf", ctypes.c_void_p),
         ("sky", ctypes.c_int), ("pole", ctypes.c_double * 3), ("gmst", ctypes.c_double),
+        ("gmm", ctypes.c_int * NDIM), ("model", ctypes.c_void_p),
     ]
 
 
@@ -76,7 +87,16 @@ def _load():
             lib.orc_mc_stats.argtypes = [vp, ctypes.c_long, vp]
             lib.orc_philox4x32_10.argtypes = [vp, vp, vp]
             lib.orc_sample.argtypes = [ctypes.POINTER(_Sampler), ctypes.c_uint64, ctypes.c_uint32,
-                                       ctypes.c_uint32, ctypes.c_long, ctypes.c_long, vp, vp, vp]
+                                       ctypes.c_uint32, ctypes.c_long, ctypes.c_long, vp, vp, vp, vp]
+            lib.orc_norm_ppf.argtypes = [d]
+            lib.orc_norm_ppf.restype = d
+            lib.orc_gmm_cum.argtypes = [ctypes.POINTER(_Gmm1), vp]
+            lib.orc_gmm_lnpdf.argtypes = [ctypes.POINTER(_Gmm1), d, d, d]
+            lib.orc_gmm_lnpdf.restype = d
+            lib.orc_gmm_init.argtypes = [ctypes.POINTER(_Gmm1), i, d, d]
+            lib.orc_gmm_update.argtypes = [ctypes.POINTER(_Gmm1), vp, vp, ctypes.c_long, i, d, d]
+            lib.orc_gmm_em_step.argtypes = [vp, vp, ctypes.c_long, ctypes.POINTER(_Gmm1), d, d]
+            lib.orc_gmm_merge.argtypes = [ctypes.POINTER(_Gmm1), ctypes.POINTER(_Gmm1), d, ctypes.POINTER(_Gmm1)]
             lib.orc_hist.argtypes = [vp, vp, ctypes.c_long, vp]
             lib.orc_cdf_from_hist.argtypes = [vp, d, vp]
             lib.orc_cdf_uniform.argtypes = [vp]
@@ -271,14 +291,85 @@ def philox(ctr, key):
     return out
 
 
-def make_sampler(lo, hi, adaptive, cdf, sky_pole=None, gmst=0.0):
-    """sky_pole: pole of the rotated network sky frame (variables 0, 1 in that frame), or None."""
+# ------------------------------------------------------------------------------------ mixture sampler
+def _gmm_struct(m):
+    g = _Gmm1()
+    C = len(m["w"])
+    g.C = C
+    for c in range(C):
+        g.w[c], g.mu[c], g.sigma[c] = float(m["w"][c]), float(m["mu"][c]), float(m["sigma"][c])
+    g.n = float(m.get("n", 0.0))
+    return g
+
+
+def _gmm_dict(g):
+    C = g.C
+    return dict(w=np.array(g.w[:C]), mu=np.array(g.mu[:C]), sigma=np.array(g.sigma[:C]), n=float(g.n))
+
+
+def gmm_init(C: int, lo: float, hi: float):
+    g = _Gmm1()
+    _load().orc_gmm_init(ctypes.byref(g), int(C), float(lo), float(hi))
+    return _gmm_dict(g)
+
+
+def gmm_lnpdf(m, lo: float, hi: float, u: float) -> float:
+    g = _gmm_struct(m)
+    return _load().orc_gmm_lnpdf(ctypes.byref(g), float(lo), float(hi), float(u))
+
+
+def gmm_cum(m):
+    g = _gmm_struct(m)
+    cw = np.zeros(GMM_MAX + 1, dtype=np.uint64)
+    _load().orc_gmm_cum(ctypes.byref(g), _ptr(cw))
+    return cw[: g.C + 1]
+
+
+def gmm_update(m, u, w, iters: int, lo: float, hi: float):
+    """EM on the batch (u, weights w) from the current model, then the online merge."""
+    g = _gmm_struct(m)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    _load().orc_gmm_update(ctypes.byref(g), _ptr(u), _ptr(w), u.size, int(iters), float(lo), float(hi))
+    return _gmm_dict(g)
+
+
+def gmm_em_step(m, u, w, lo: float, hi: float):
+    g = _gmm_struct(m)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    _load().orc_gmm_em_step(_ptr(u), _ptr(w), u.size, ctypes.byref(g), float(lo), float(hi))
+    return _gmm_dict(g)
+
+
+def gmm_merge(cur, bat, M: float):
+    a, b, out = _gmm_struct(cur), _gmm_struct(bat), _Gmm1()
+    _load().orc_gmm_merge(ctypes.byref(a), ctypes.byref(b), float(M), ctypes.byref(out))
+    return _gmm_dict(out)
+
+
+def norm_ppf(p: float) -> float:
+    return _load().orc_norm_ppf(float(p))
+
+
+def make_sampler(lo, hi, adaptive, cdf, sky_pole=None, gmst=0.0, gmm=None):
+    """sky_pole: pole of the rotated network sky frame (variables 0, 1 in that frame), or None.
+    gmm: None or a list of 7 entries, each None (histogram / prior) or a mixture model dict
+    (w, mu, sigma, n) for an adaptive dimension drawn from its Gaussian mixture."""
     cdf = np.ascontiguousarray(cdf, dtype=np.uint64).reshape(NDIM, NBINS + 1)
     pole = (0.0, 0.0, 0.0) if sky_pole is None else tuple(float(x) for x in sky_pole)
+    models = (_Gmm1 * NDIM)()
+    flags = [0] * NDIM
+    if gmm is not None:
+        for d in range(NDIM):
+            if gmm[d] is not None:
+                models[d] = _gmm_struct(gmm[d])
+                flags[d] = 1
     s = _Sampler((ctypes.c_double * NDIM)(*lo), (ctypes.c_double * NDIM)(*hi),
                  (ctypes.c_int * NDIM)(*[int(a) for a in adaptive]), _ptr(cdf).value, 0 if sky_pole is None else 1,
-                 (ctypes.c_double * 3)(*pole), float(gmst))
-    s._keep = cdf
+                 (ctypes.c_double * 3)(*pole), float(gmst), (ctypes.c_int * NDIM)(*flags),
+                 ctypes.cast(models, ctypes.c_void_p).value)
+    s._keep = (cdf, models)
     return s
 
 
@@ -289,13 +380,15 @@ def sky_frame(pole):
     return e1, e2, p
 
 
-def sample(sampler, seed: int, it: int, point: int, n0: int, N: int):
-    """Device-sampler definition: returns theta (7,N), ln p - ln p_s (N,), bins (7,N) uint8."""
+def sample(sampler, seed: int, it: int, point: int, n0: int, N: int, with_u: bool = False):
+    """Device-sampler definition: returns theta (7,N), ln p - ln p_s (N,), bins (7,N) uint8
+    (the mixture component for a mixture dimension), and with with_u the sampling variables u (7,N)."""
     theta = np.zeros((NDIM, N))
     lw = np.zeros(N)
     bins = np.zeros((NDIM, N), dtype=np.uint8)
-    _load().orc_sample(ctypes.byref(sampler), seed, it, point, n0, N, _ptr(theta), _ptr(lw), _ptr(bins))
-    return theta, lw, bins
+    u = np.zeros((NDIM, N))
+    _load().orc_sample(ctypes.byref(sampler), seed, it, point, n0, N, _ptr(theta), _ptr(lw), _ptr(bins), _ptr(u))
+    return (theta, lw, bins, u) if with_u else (theta, lw, bins)
 
 
 def hist(lnw, bins):
@@ -321,14 +414,21 @@ def cdf_uniform():
 
 # ------------------------------------------------------------------------------------ S0-S6 loop
 def adapt_run(point, seed: int, N: int, n_iter: int, adapt_mask: int, eps: float, lo, hi, point_id: int = 0,
-              nthreads: int = 0, cdf0=None, iter0: int = 0, sky_pole=None):
+              nthreads: int = 0, cdf0=None, iter0: int = 0, sky_pole=None, gmm_mask: int = 0,
+              gmm_components: int = 3, gmm_em_iters: int = 8, gmm0=None):
     """Adaptive-Cartesian integration in the order of Sec. "GPU-accelerated Monte Carlo integration":
     for each iteration draw N samples from the separable sampling prior, evaluate lnL_t, accumulate
     the Monte Carlo sums of Eq. (eq:lnL:MonteCarlo) (pooled over iterations, each sample weighted by
     the p_s it was drawn from) and refit each adaptive dimension's 100-bin histogram.
-    Returns the pooled estimate, the per-iteration estimates, the final tables and the last
-    iteration's samples."""
+    Adaptive dimensions in gmm_mask are drawn from a truncated Gaussian mixture instead
+    (Sec. "Adaptive sampling with gaussian mixture models"), refit each iteration by gmm_update.
+    Returns the pooled estimate, the per-iteration estimates, the final tables and mixtures, and the
+    last iteration's samples."""
     adaptive = [(adapt_mask >> d) & 1 for d in range(NDIM)]
+    gmm = [None] * NDIM
+    for d in range(NDIM):
+        if adaptive[d] and (gmm_mask >> d) & 1:
+            gmm[d] = dict(gmm0[d]) if gmm0 is not None else gmm_init(gmm_components, lo[d], hi[d])
     cdf = np.zeros((NDIM, NBINS + 1), np.uint64)
     for d in range(NDIM):
         cdf[d] = cdf_uniform() if cdf0 is None else cdf0[d]
@@ -336,18 +436,21 @@ def adapt_run(point, seed: int, N: int, n_iter: int, adapt_mask: int, eps: float
     iters = []
     last = None
     for it in range(iter0, iter0 + n_iter):
-        smp = make_sampler(lo, hi, adaptive, cdf, sky_pole, point.gmst)
-        theta, lwp, bins = sample(smp, seed, it, point_id, 0, N)
+        smp = make_sampler(lo, hi, adaptive, cdf, sky_pole, point.gmst, gmm)
+        theta, lwp, bins, u = sample(smp, seed, it, point_id, 0, N, with_u=True)
         lnl = lnL_t(point, theta, nthreads)
         lnw = lnl + lwp
         st = mc_stats(lnw)
         iters.append(st)
         lnw_all.append(lnw)
         hists = np.zeros((NDIM, NBINS))
+        gmm_before = [None if g is None else dict(g) for g in gmm]
         for d in range(NDIM):
-            if adaptive[d]:
+            if gmm[d] is not None:
+                gmm[d] = gmm_update(gmm[d], u[d], np.exp(lnw - lnw.max()), gmm_em_iters, lo[d], hi[d])
+            elif adaptive[d]:
                 hists[d] = hist(lnw, bins[d])
                 cdf[d] = cdf_from_hist(hists[d], eps)
-        last = dict(theta=theta, lnw_prior=lwp, bins=bins, lnL=lnl, hist=hists)
+        last = dict(theta=theta, lnw_prior=lwp, bins=bins, lnL=lnl, hist=hists, u=u, gmm=gmm_before)
     pooled = mc_stats(np.concatenate(lnw_all))
-    return dict(pooled=pooled, iters=iters, cdf=cdf, last=last)
+    return dict(pooled=pooled, iters=iters, cdf=cdf, last=last, gmm=gmm)

@@ -49,6 +49,12 @@
  *   R22 distance marginalisation: the distance integral sits inside the window sum, i.e. the
  *      marginal of (1/N_t) sum_j exp(a_j x - b x^2) over p(D) prop. to D^2 on [D_min, D_max],
  *      x = D_ref / D, with a_j, b the data and quadratic terms at D = D_ref.
+ *   R24 Gaussian-mixture sampler (Sec. "Adaptive sampling with gaussian mixture models" and the
+ *      appendix on its implementation), separable form: the sample weight w_n scales the
+ *      responsibility in the M-step sums, the mixture weight is divided by sum_n w_n (the
+ *      printed E-step cancels w_n), a fixed number of EM steps per iteration started from the
+ *      current model, the 1-D Mahalanobis distance |mu_i - mu_j| / sigma in the matching, and the
+ *      initial model C equal components evenly spaced over the range with sigma = range / C.
  */
 #include <math.h>
 #include <stdint.h>
@@ -360,6 +366,16 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
  * A fixed dimension is drawn from its prior; an adaptive one from a 100-bin histogram given by
  * its integer cumulative table cdf[0..100] (cdf[0] = 0, cdf[100] = 2^32).
  */
+/* One dimension's Gaussian-mixture sampling prior (App. "Gaussian mixture model
+ * implementation", separable form): C components with weights w, means mu, widths sigma, each
+ * a normal truncated to the dimension's range; n = samples the model has been trained on. */
+#define ORC_GMM_MAX 8
+typedef struct {
+    int C;
+    double w[ORC_GMM_MAX], mu[ORC_GMM_MAX], sigma[ORC_GMM_MAX];
+    double n;
+} orc_gmm1;
+
 typedef struct {
     double lo[ORC_NDIM], hi[ORC_NDIM];
     int adaptive[ORC_NDIM];
@@ -367,7 +383,65 @@ typedef struct {
     int sky;             /* 1: variables 0, 1 are (longitude, sin latitude) in the rotated frame */
     double pole[3];      /* Earth-fixed pole of the rotated frame */
     double gmst;
+    int gmm[ORC_NDIM];   /* 1: adaptive dimension drawn from its mixture instead of its histogram */
+    const orc_gmm1 *model; /* [7] */
 } orc_sampler;
+
+/* Standard normal CDF and its inverse (Newton iterations on erfc from a coarse start). */
+static double norm_cdf(double z) { return 0.5 * erfc(-z / sqrt(2.0)); }
+
+double orc_norm_ppf(double p)
+{
+    if (p <= 0.0) return -INFINITY;
+    if (p >= 1.0) return INFINITY;
+    /* start: logistic approximation, then Newton on Phi(x) - p */
+    double x = -log(1.0 / p - 1.0) / 1.702;
+    for (int it = 0; it < 100; it++) {
+        double f = norm_cdf(x) - p, d = exp(-0.5 * x * x) / sqrt(2.0 * ORC_PI);
+        double step = f / d;
+        if (step > 2.0) step = 2.0;
+        if (step < -2.0) step = -2.0;
+        x -= step;
+        if (fabs(step) < 1e-15 * (1.0 + fabs(x))) break;
+    }
+    return x;
+}
+
+/* Integer cumulative table of the component weights (2^32 scale, same rule as the histograms). */
+void orc_gmm_cum(const orc_gmm1 *g, uint64_t *cw)
+{
+    double tot = 0.0, acc = 0.0;
+    for (int c = 0; c < g->C; c++) tot += g->w[c];
+    cw[0] = 0;
+    for (int c = 0; c < g->C; c++) {
+        acc += g->w[c] / tot;
+        if (c + 1 < g->C) {
+            double v = floor(acc * 4294967296.0);
+            if (v > 4294967296.0) v = 4294967296.0;
+            cw[c + 1] = (uint64_t)v;
+        }
+    }
+    cw[g->C] = (uint64_t)1 << 32;
+    for (int c = 1; c <= g->C; c++)
+        if (cw[c] < cw[c - 1]) cw[c] = cw[c - 1];
+}
+
+/* ln of the truncated-mixture density sum_c (w_c / sum w) N(u | mu_c, sigma_c) / Z_c on [lo, hi],
+ * Z_c = Phi((hi - mu_c) / sigma_c) - Phi((lo - mu_c) / sigma_c), as a log-sum-exp over c. */
+double orc_gmm_lnpdf(const orc_gmm1 *g, double lo, double hi, double u)
+{
+    double tot = 0.0, l[ORC_GMM_MAX], m = -INFINITY;
+    for (int c = 0; c < g->C; c++) tot += g->w[c];
+    for (int c = 0; c < g->C; c++) {
+        double z = (u - g->mu[c]) / g->sigma[c];
+        double Z = norm_cdf((hi - g->mu[c]) / g->sigma[c]) - norm_cdf((lo - g->mu[c]) / g->sigma[c]);
+        l[c] = log(g->w[c] / tot) - log(sqrt(2.0 * ORC_PI) * g->sigma[c] * Z) - 0.5 * z * z;
+        if (l[c] > m) m = l[c];
+    }
+    double s = 0.0;
+    for (int c = 0; c < g->C; c++) s += exp(l[c] - m);
+    return m + log(s);
+}
 
 /* Rotated network-frame sky (R23): orthonormal (e1, e2, p) with p = pole / |pole|,
  * e1 = (z x p) / |z x p| (x when p is along z), e2 = p x e1. */
@@ -412,7 +486,7 @@ static double ln_prior(const orc_sampler *S, int d, double u)
  * and the bin of every adaptive dimension ([7][N], 255 for fixed ones).
  */
 void orc_sample(const orc_sampler *S, uint64_t seed, uint32_t iter, uint32_t point, long n0, long N,
-                double *theta, double *lnp_minus_lnps, uint8_t *bins)
+                double *theta, double *lnp_minus_lnps, uint8_t *bins, double *u_out)
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     for (long s = 0; s < N; s++) {
@@ -427,7 +501,22 @@ void orc_sample(const orc_sampler *S, uint64_t seed, uint32_t iter, uint32_t poi
             double lo = S->lo[d], hi = S->hi[d], u;
             uint32_t a = words[2 * d], b = words[2 * d + 1];
             int bin = 255;
-            if (S->adaptive[d]) {
+            if (S->adaptive[d] && S->gmm[d]) {
+                /* mixture: component = largest c with cw[c] <= a; inside it, the truncated normal
+                 * by inverting its CDF at Phi(a_c) + v (Phi(b_c) - Phi(a_c)) */
+                const orc_gmm1 *g = S->model + d;
+                uint64_t cw[ORC_GMM_MAX + 1];
+                orc_gmm_cum(g, cw);
+                bin = 0;
+                for (int c = 0; c < g->C; c++)
+                    if (cw[c] <= (uint64_t)a) bin = c;
+                double Pa = norm_cdf((lo - g->mu[bin]) / g->sigma[bin]);
+                double Pb = norm_cdf((hi - g->mu[bin]) / g->sigma[bin]);
+                u = g->mu[bin] + g->sigma[bin] * orc_norm_ppf(Pa + unit23(b) * (Pb - Pa));
+                if (u < lo) u = lo;
+                if (u > hi) u = hi;
+                lw += ln_prior(S, d, u) - orc_gmm_lnpdf(g, lo, hi, u);
+            } else if (S->adaptive[d]) {
                 const uint64_t *cdf = S->cdf + (size_t)d * (ORC_NBINS + 1);
                 bin = 0;
                 for (int q = 0; q < ORC_NBINS; q++)
@@ -458,6 +547,7 @@ void orc_sample(const orc_sampler *S, uint64_t seed, uint32_t iter, uint32_t poi
             }
             theta[(size_t)d * N + s] = phys;
             bins[(size_t)d * N + s] = (uint8_t)bin;
+            if (u_out) u_out[(size_t)d * N + s] = u;
         }
         lnp_minus_lnps[s] = lw;
     }
@@ -514,6 +604,128 @@ void orc_cdf_uniform(uint64_t *cdf)
 }
 
 int orc_version(void) { return 1; }
+
+/*
+ * One adaptive update of a dimension's mixture (App. "Gaussian mixture model implementation"):
+ * `iters` EM steps on the batch (samples u_n with weights w_n, starting from the current model),
+ * then the online merge of the batch model into the current one.
+ *   E-step: r_nc = w_c N(u_n | mu_c, sigma_c) / sum_c' (...)   (untruncated normal densities)
+ *   M-step: S0_c = sum_n w_n r_nc, mu_c = sum_n w_n r_nc u_n / S0_c,
+ *           sigma_c^2 = sum_n w_n r_nc (u_n - mu_c)^2 / S0_c, w_c = S0_c / sum_n w_n
+ *   (sigma_c >= (hi - lo) 1e-3; a component with S0_c <= 1e-12 sum w keeps its parameters, with
+ *   weight 1e-3; weights are renormalised)
+ *   merge: match each batch component i to a current component j (a permutation) minimising
+ *   sum |mu_i - mu_j| (1/sigma_i + 1/sigma_j) (the 1-D Mahalanobis distances both ways), then
+ *   combine with N = current model's sample count, M = batch size:
+ *   mu = (N w_j mu_j + M w_i mu_i) / (N w_j + M w_i),
+ *   sigma^2 = (N w_j sigma_j^2 + M w_i sigma_i^2) / (...) + (N w_j mu_j^2 + M w_i mu_i^2) / (...) - mu^2,
+ *   w = (N w_j + M w_i) / (N + M); n <- N + M.
+ */
+void orc_gmm_em_step(const double *u, const double *wn, long N, orc_gmm1 *g, double lo, double hi)
+{
+    double S0[ORC_GMM_MAX] = {0}, S1[ORC_GMM_MAX] = {0}, S2[ORC_GMM_MAX] = {0}, W = 0.0;
+    for (long n = 0; n < N; n++) {
+        /* r_c prop. to w_c N(u | mu_c, sigma_c), scaled by the largest term before exponentiating */
+        double r[ORC_GMM_MAX], l[ORC_GMM_MAX], m = -INFINITY, tot = 0.0;
+        for (int c = 0; c < g->C; c++) {
+            double z = (u[n] - g->mu[c]) / g->sigma[c];
+            l[c] = log(g->w[c] / g->sigma[c]) - 0.5 * z * z;
+            if (l[c] > m) m = l[c];
+        }
+        for (int c = 0; c < g->C; c++) {
+            r[c] = exp(l[c] - m);
+            tot += r[c];
+        }
+        W += wn[n];
+        for (int c = 0; c < g->C; c++) {
+            double q = wn[n] * r[c] / tot;
+            S0[c] += q;
+            S1[c] += q * u[n];
+            S2[c] += q * u[n] * u[n];
+        }
+    }
+    double smin = (hi - lo) * 1e-3, wsum = 0.0;
+    for (int c = 0; c < g->C; c++) {
+        if (S0[c] > 1e-12 * W) {
+            double mu = S1[c] / S0[c], var = S2[c] / S0[c] - mu * mu;
+            g->mu[c] = mu;
+            g->sigma[c] = sqrt(var > smin * smin ? var : smin * smin);
+            g->w[c] = S0[c] / W;
+        } else {
+            g->w[c] = 1e-3;
+        }
+        wsum += g->w[c];
+    }
+    for (int c = 0; c < g->C; c++) g->w[c] /= wsum;
+}
+
+void orc_gmm_merge(const orc_gmm1 *cur, const orc_gmm1 *bat, double M, orc_gmm1 *out)
+{
+    const int C = cur->C;
+    int perm[ORC_GMM_MAX], best[ORC_GMM_MAX];
+    for (int i = 0; i < C; i++) perm[i] = best[i] = i;
+    double best_cost = INFINITY;
+    /* every permutation in lexicographic order; the first one of least cost is kept */
+    for (;;) {
+        double cost = 0.0;
+        for (int a = 0; a < C; a++) {
+            int j = perm[a];
+            cost += fabs(cur->mu[j] - bat->mu[a]) / bat->sigma[a] + fabs(bat->mu[a] - cur->mu[j]) / cur->sigma[j];
+        }
+        if (cost < best_cost) {
+            best_cost = cost;
+            for (int a = 0; a < C; a++) best[a] = perm[a];
+        }
+        /* next permutation */
+        int i = C - 2;
+        while (i >= 0 && perm[i] > perm[i + 1]) i--;
+        if (i < 0) break;
+        int j = C - 1;
+        while (perm[j] < perm[i]) j--;
+        int t = perm[i];
+        perm[i] = perm[j];
+        perm[j] = t;
+        for (int x = i + 1, y = C - 1; x < y; x++, y--) {
+            t = perm[x];
+            perm[x] = perm[y];
+            perm[y] = t;
+        }
+    }
+    const double N = cur->n;
+    out->C = C;
+    for (int a = 0; a < C; a++) {
+        int j = best[a];
+        double A = N * cur->w[j], B = M * bat->w[a];
+        double mu = (A * cur->mu[j] + B * bat->mu[a]) / (A + B);
+        double var = (A * cur->sigma[j] * cur->sigma[j] + B * bat->sigma[a] * bat->sigma[a]) / (A + B) +
+                     (A * cur->mu[j] * cur->mu[j] + B * bat->mu[a] * bat->mu[a]) / (A + B) - mu * mu;
+        out->mu[a] = mu;
+        out->sigma[a] = sqrt(var > 0.0 ? var : 0.0);
+        out->w[a] = (A + B) / (N + M);
+    }
+    out->n = N + M;
+}
+
+/* Initial model: C equal components, means at the centres of C equal slices of [lo, hi],
+ * sigma = (hi - lo) / C, trained on no samples (so the first merge keeps the batch model). */
+void orc_gmm_init(orc_gmm1 *g, int C, double lo, double hi)
+{
+    g->C = C;
+    for (int c = 0; c < C; c++) {
+        g->w[c] = 1.0 / C;
+        g->mu[c] = lo + (c + 0.5) * (hi - lo) / C;
+        g->sigma[c] = (hi - lo) / C;
+    }
+    g->n = 0.0;
+}
+
+void orc_gmm_update(orc_gmm1 *g, const double *u, const double *wn, long N, int iters, double lo, double hi)
+{
+    orc_gmm1 bat = *g, out;
+    for (int it = 0; it < iters; it++) orc_gmm_em_step(u, wn, N, &bat, lo, hi);
+    orc_gmm_merge(g, &bat, (double)N, &out);
+    *g = out;
+}
 
 /* ---------------------------------------------------------------- gradients (adjoint checks) */
 

@@ -76,6 +76,7 @@ typedef enum {
 
 #define ILE_NBINS 100      /* histogram bins per adaptive dimension (Sec. GPU-accelerated MC) */
 #define ILE_NDIM 7         /* ra, dec, psi, iota, phi, D, t_c */
+#define ILE_GMM_MAX 8      /* components per Gaussian-mixture dimension */
 #define ILE_MAX_DET 4
 #define ILE_MAX_MODES 21   /* all (l, m) with 2 <= l <= 4 */
 #define ILE_MAX_WINDOW 1024
@@ -188,6 +189,30 @@ ile_status ile_integrate(ile_ctx *ctx, const double *samples, const double *ln_p
  * sin(lat') p, then dec = asin(n_z), ra = gmst - atan2(-n_y, n_x) in [0, 2 pi).  The uniform sky
  * prior is the same density in either frame; the histograms adapt in the rotated variables.
  */
+/*
+ * Gaussian-mixture sampling (Sec. "Adaptive sampling with gaussian mixture models", App.
+ * "Gaussian mixture model implementation"), separable form: an adaptive dimension d in gmm_mask
+ * is drawn from p_{s,d}(u) = sum_c w_c N(u | mu_c, sigma_c) / Z_c, each normal truncated to
+ * [lo_d, hi_d] (Z_c its mass there), instead of from a histogram.
+ *   Sampling: the component is the largest c with cw[c] <= a (cw the integer cumulative weight
+ *   table, 2^32 scale, built like the histogram tables), then u = mu_c + sigma_c Phi^-1(P1 + v
+ *   (P2 - P1)), P1, P2 = Phi((lo - mu_c) / sigma_c), Phi((hi - mu_c) / sigma_c), v from the
+ *   second word; bins[d] holds the component.
+ *   Update, every iteration: gmm_em_iters EM steps on the iteration's samples, started from the
+ *   current mixture, with responsibilities r_nc prop. to w_c N(u_n | mu_c, sigma_c) and sample
+ *   weights w_n = exp(ln w_n - max): S0_c = sum_n w_n r_nc, mu_c = sum w r u / S0_c,
+ *   sigma_c^2 = sum w r (u - mu_c)^2 / S0_c (at least (1e-3 (hi - lo))^2), w_c = S0_c / sum w_n
+ *   (a component with S0_c <= 1e-12 sum w keeps mu, sigma and gets weight 1e-3; weights are
+ *   renormalised).  Then the online merge: batch component i is paired with current component j
+ *   by the permutation of least sum |mu_i - mu_j| (1 / sigma_i + 1 / sigma_j) (the first such
+ *   permutation in lexicographic order), and each pair combined with N = samples the current
+ *   mixture was trained on, M = n_per_iter: mu = (N w_j mu_j + M w_i mu_i) / (N w_j + M w_i),
+ *   sigma^2 = (N w_j (sigma_j^2 + mu_j^2) + M w_i (sigma_i^2 + mu_i^2)) / (N w_j + M w_i) - mu^2,
+ *   w = (N w_j + M w_i) / (N + M); then N <- N + M.
+ *   Start: gmm_components equal components, means at the centres of equal slices of [lo, hi],
+ *   sigma = (hi - lo) / C, N = 0 (so the first merge keeps the batch mixture); or the mixtures of
+ *   a resumed ile_adapt_result.
+ */
 typedef struct {
     uint64_t seed;
     uint32_t point_id;
@@ -198,6 +223,9 @@ typedef struct {
     double lo[ILE_NDIM], hi[ILE_NDIM];
     int sky_frame;        /* 0: sky variables 0, 1 are (ra, sin dec); 1: rotated network frame */
     double sky_pole[3];   /* sky_frame 1: Earth-fixed vector of the frame's pole (e.g. r_L1 - r_H1) */
+    unsigned gmm_mask;    /* bits of adapt_mask drawn from a Gaussian mixture; 0: histograms only */
+    int gmm_components;   /* gmm_mask != 0: components per mixture, 1 .. ILE_GMM_MAX */
+    int gmm_em_iters;     /* gmm_mask != 0: EM steps per iteration, 1 .. 100 */
 } ile_adapt_cfg;
 
 #define ILE_ADAPT_LOG 64
@@ -209,11 +237,16 @@ typedef struct {
     double iter_n_eff[ILE_ADAPT_LOG];    /* per-iteration n_eff */
     uint64_t cdf[ILE_NDIM][ILE_NBINS + 1]; /* current integer cumulative tables (2^32 scale) */
     double hist[ILE_NDIM][ILE_NBINS];    /* last iteration's weight histograms (relative to its max) */
+    int gmm_components[ILE_NDIM];        /* mixture dimensions: components; 0 otherwise */
+    double gmm_w[ILE_NDIM][ILE_GMM_MAX], gmm_mu[ILE_NDIM][ILE_GMM_MAX], gmm_sigma[ILE_NDIM][ILE_GMM_MAX];
+    double gmm_n[ILE_NDIM];              /* samples each mixture has been trained on */
 } ile_adapt_result;
 
 /* Set up the sampler on the current point (after ile_set_data).  resume = NULL starts from uniform
- * tables and empty sums; otherwise the tables, sums and iteration counter of `resume` are loaded
- * (checkpoint/resume). */
+ * tables, the initial mixtures and empty sums; otherwise the tables, mixtures, sums and iteration
+ * counter of `resume` are loaded (checkpoint/resume).  ILE_E_ARG for a bad configuration:
+ * gmm_mask not inside adapt_mask, components or EM steps out of range, or a resumed mixture with
+ * another component count, a weight <= 0, a sigma <= 0 or a mean outside [lo, hi]. */
 ile_status ile_adapt_init(ile_ctx *ctx, const ile_adapt_cfg *cfg, const ile_adapt_result *resume);
 /* Queue n_iter iterations on the context stream (asynchronous). */
 ile_status ile_adapt_step(ile_ctx *ctx, int n_iter);

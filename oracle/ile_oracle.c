@@ -648,7 +648,7 @@ void orc_gmm_em_step(const double *u, const double *wn, long N, orc_gmm1 *g, dou
     for (int c = 0; c < g->C; c++) {
         if (S0[c] > 1e-12 * W) {
             double mu = S1[c] / S0[c], var = S2[c] / S0[c] - mu * mu;
-            g->mu[c] = mu;
+            g->mu[c] = mu < lo ? lo : (mu > hi ? hi : mu); /* a weighted mean of points in range; rounding only */
             g->sigma[c] = sqrt(var > smin * smin ? var : smin * smin);
             g->w[c] = S0[c] / W;
         } else {

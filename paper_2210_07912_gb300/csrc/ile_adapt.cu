@@ -11,6 +11,11 @@
 // keyed by the seed, counter (sample, iteration, point, block).  Because the bin choice is an
 // integer comparison, it is reproduced bit for bit by any implementation of the same definition.
 //
+// A dimension in the mixture mask is drawn from its truncated Gaussian mixture instead (tables
+// built in ile_gmm.cu): component = largest c with cw[c] <= a, u = mu_c + sigma_c Phi^-1(P1_c + v
+// Z_c) with v from the second word (evaluated from the nearer tail), ln p_s a log-sum-exp over the
+// components; the bins byte holds the component and u is kept for the EM update.
+//
 // After the likelihood, each adaptive dimension's histogram h_b = sum_{n in b} w_n / sum w
 // (w_n = exp(ln w_n - max ln w) <= 1) is accumulated as 2^-40 fixed-point integers (exact and
 // independent of the order of the atomics, so a run is reproducible bit for bit); the next table
@@ -53,21 +58,60 @@ __device__ __forceinline__ float unit23(uint32_t w) { return ((float)(w >> 9) + 
 struct SamplerTables {
     uint32_t cdf[ND][NB + 1];  // low 32 bits; cdf[100] = 2^32 is never compared against
     float lnps[ND][NB];
+    IleGmmTab gmm[ND];
 };
 
 __device__ __forceinline__ void load_tables(SamplerTables &t, const uint64_t *__restrict__ cdf,
-                                            const float *__restrict__ lnps_tab) {
+                                            const float *__restrict__ lnps_tab, const IleGmmTab *__restrict__ gmm,
+                                            unsigned gmm_mask) {
     for (int i = threadIdx.x; i < ND * (NB + 1); i += blockDim.x) {
         const int d = i / (NB + 1), b = i % (NB + 1);
         t.cdf[d][b] = (uint32_t)cdf[i];
         if (b < NB) t.lnps[d][b] = lnps_tab[d * NB + b];
     }
+    if (gmm_mask) {
+        constexpr int W = sizeof(IleGmmTab) / 4;
+        static_assert(sizeof(IleGmmTab) % 4 == 0, "table copied as words");
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(gmm);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(t.gmm);
+        for (int i = threadIdx.x; i < ND * W; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
+// One draw from dimension d's truncated mixture: returns u, sets the component and ln p_s.
+__device__ __forceinline__ float gmm_draw(const IleGmmTab &g, float lo, float hi, uint32_t a, uint32_t bw, int &comp,
+                                          float &lnps) {
+    int c = 0;
+    for (int j = 1; j < g.C; j++)
+        if (g.cw[j] <= (uint64_t)a) c = j;
+    // inverse CDF at P = Phi(z_lo) + v Z, taken from the nearer tail so that P never rounds to 1:
+    // P <= 1/2: z = Phi^-1(P); otherwise z = -Phi^-1(1 - P), 1 - P = Phi(-z_hi) + (1 - v) Z
+    // (both sums of positive terms; 1 - v is exact for the 23-bit v)
+    const float v = unit23(bw);
+    const float p = g.p1[c] + v * g.dm[c];
+    const float z = p <= 0.5f ? normcdfinvf(p) : -normcdfinvf(g.q2[c] + (1.f - v) * g.dm[c]);
+    float u = g.mu[c] + g.sig[c] * z;
+    u = fminf(fmaxf(u, lo), hi);
+    float l[ILE_GMM_MAX], m = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < ILE_GMM_MAX; j++) {
+        const float z = j < g.C ? (u - g.mu[j]) / g.sig[j] : 0.f;
+        l[j] = j < g.C ? g.coef[j] - 0.5f * z * z : -INFINITY;
+        m = fmaxf(m, l[j]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < ILE_GMM_MAX; j++) s += j < g.C ? expf(l[j] - m) : 0.f;
+    lnps = m + logf(s);
+    comp = c;
+    return u;
 }
 
 // Sample n of N (one point): theta [7][N], ln p - ln p_s, bins [7][N].
 __device__ __forceinline__ void sample_one(const IleSamplerParams &sp, const SamplerTables &tb, uint32_t iter,
                                            int64_t n, int64_t N, double *__restrict__ theta,
-                                           double *__restrict__ lnw_prior, uint8_t *__restrict__ bins) {
+                                           double *__restrict__ lnw_prior, uint8_t *__restrict__ bins,
+                                           float *__restrict__ u_gmm) {
     const uint32_t(&cdf_s)[ND][NB + 1] = tb.cdf;
     const float(&lnps_s)[ND][NB] = tb.lnps;
     uint32_t wds[16];
@@ -81,7 +125,13 @@ __device__ __forceinline__ void sample_one(const IleSamplerParams &sp, const Sam
         const uint32_t a = wds[2 * d], bw = wds[2 * d + 1];
         float u;
         int bin = 255;
-        if (sp.adapt_mask & (1u << d)) {
+        if (sp.gmm_mask & (1u << d)) {
+            float lnps;
+            u = gmm_draw(tb.gmm[d], lo, hi, a, bw, bin, lnps);
+            const float lnp = d == 5 ? logf(3.f * u * u / (hi * hi * hi - lo * lo * lo)) : -logf(hi - lo);
+            lw += lnp - lnps;
+            u_gmm[(int64_t)__popc(sp.gmm_mask & ((1u << d) - 1u)) * N + n] = u;
+        } else if (sp.adapt_mask & (1u << d)) {
             // largest b with cdf[b] <= a (cdf[0] = 0, strictly increasing until 2^32)
             int b0 = 0, b1 = NB;  // invariant: cdf[b0] <= a < cdf[b1] (cdf[100] = 2^32 > a)
             while (b1 - b0 > 1) {
@@ -123,15 +173,16 @@ __device__ __forceinline__ void sample_one(const IleSamplerParams &sp, const Sam
 
 __global__ void __launch_bounds__(256) sample_kernel(IleSamplerParams sp, const uint64_t *__restrict__ cdf,
                                                      const float *__restrict__ lnps_tab,
+                                                     const IleGmmTab *__restrict__ gmm_tab,
                                                      const int *__restrict__ iter_dev, int64_t N,
                                                      double *__restrict__ theta, double *__restrict__ lnw_prior,
-                                                     uint8_t *__restrict__ bins) {
+                                                     uint8_t *__restrict__ bins, float *__restrict__ u_gmm) {
     __shared__ SamplerTables tb;
-    load_tables(tb, cdf, lnps_tab);
+    load_tables(tb, cdf, lnps_tab, gmm_tab, sp.gmm_mask);
     __syncthreads();
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    sample_one(sp, tb, (uint32_t)(*iter_dev), n, N, theta, lnw_prior, bins);
+    sample_one(sp, tb, (uint32_t)(*iter_dev), n, N, theta, lnw_prior, bins, u_gmm);
 }
 
 // Batched: block b draws samples start .. start + 255 of point blk[b].x (blk[b].y = start).
@@ -143,11 +194,13 @@ __global__ void __launch_bounds__(256) bsample_kernel(const IleBatchPoint *__res
     __shared__ SamplerTables tb;
     const int p = blk[blockIdx.x].x;
     const IleBatchPoint &pt = bp[p];
-    load_tables(tb, cdf + (size_t)p * ND * (NB + 1), lnps_tab + (size_t)p * ND * NB);
+    load_tables(tb, cdf + (size_t)p * ND * (NB + 1), lnps_tab + (size_t)p * ND * NB, nullptr, 0u);
     __syncthreads();
     const int64_t n = (int64_t)blk[blockIdx.x].y + threadIdx.x;
     if (n >= pt.N) return;
-    sample_one(pt.sp, tb, (uint32_t)iter_dev[p], n, pt.N, theta + ND * pt.off, lnw_prior + pt.off, bins + ND * pt.off);
+    // batched points use histograms only (sp.gmm_mask = 0)
+    sample_one(pt.sp, tb, (uint32_t)iter_dev[p], n, pt.N, theta + ND * pt.off, lnw_prior + pt.off, bins + ND * pt.off,
+               nullptr);
 }
 
 // Histograms of w_n = exp(ln w_n - max) over each adaptive dimension, as 2^-40 fixed point:
@@ -354,10 +407,12 @@ cudaError_t ile_launch_lnps(const IleSamplerParams &sp, const uint64_t *cdf, flo
 }
 
 cudaError_t ile_launch_sample(const IleSamplerParams &sp, const uint64_t *cdf, const float *lnps_tab,
-                              const int *iter_dev, int64_t N, double *theta, double *lnw_prior, uint8_t *bins,
-                              cudaStream_t st) {
+                              const IleGmmTab *gmm_tab, const int *iter_dev, int64_t N, double *theta,
+                              double *lnw_prior, uint8_t *bins, float *u_gmm, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
-    sample_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(sp, cdf, lnps_tab, iter_dev, N, theta, lnw_prior, bins);
+    if (sp.gmm_mask && (!gmm_tab || !u_gmm)) return cudaErrorInvalidValue;
+    sample_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(sp, cdf, lnps_tab, gmm_tab, iter_dev, N, theta,
+                                                               lnw_prior, bins, u_gmm);
     return cudaGetLastError();
 }
 
@@ -366,8 +421,9 @@ cudaError_t ile_launch_adapt(const double *lnL, const double *lnw_prior, const u
                              unsigned long long *hist_fx, double *hist, uint64_t *cdf, float *lnps_tab, double *pooled,
                              double *iter_log, int *iter_dev, int update_tables, cudaStream_t st) {
     const int np = ile_hist_partial_count(N);
-    hist_kernel<<<np, HIST_THREADS, 0, st>>>(lnL, lnw_prior, bins, N, iter_res, sp.adapt_mask, hist_fx);
-    renorm_kernel<<<1, 1024, 0, st>>>(hist_fx, sp.adapt_mask, eps, sp, hist, cdf, lnps_tab, iter_res, N, pooled,
+    const unsigned hmask = sp.adapt_mask & ~sp.gmm_mask;  // mixture dimensions adapt in ile_gmm.cu
+    hist_kernel<<<np, HIST_THREADS, 0, st>>>(lnL, lnw_prior, bins, N, iter_res, hmask, hist_fx);
+    renorm_kernel<<<1, 1024, 0, st>>>(hist_fx, hmask, eps, sp, hist, cdf, lnps_tab, iter_res, N, pooled,
                                       iter_log, iter_dev, update_tables);
     return cudaGetLastError();
 }

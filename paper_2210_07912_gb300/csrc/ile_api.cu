@@ -50,6 +50,13 @@ struct ile_ctx {
     int *a_iter = nullptr;
     uint8_t *a_bins = nullptr;
     int64_t a_cap = 0;
+    // Gaussian-mixture dimensions (ile_gmm.cu)
+    int gmm_iters = 0;
+    IleGmm *g_cur = nullptr, *g_bat = nullptr;
+    IleGmmTab *g_tab = nullptr;
+    double *g_part = nullptr;
+    float *a_u = nullptr;  // [n mixture dims][N]
+    size_t a_u_bytes = 0;
     // adjoint scratch (ile_adjoint.cu)
     float *pig = nullptr;      // [N][N_t] g_n * pi(n, j)
     size_t pig_bytes = 0;
@@ -366,7 +373,8 @@ ile_status ile_destroy(ile_ctx *ctx) {
                     ctx->a_cdf,        ctx->a_lnps,     ctx->a_hist,    ctx->a_hist_fx, ctx->a_pooled,
                     ctx->a_iter_log,   ctx->a_iter_res, ctx->a_lnwp,    ctx->a_lnl,     ctx->a_iter,
                     ctx->a_bins,       ctx->pig,        ctx->gq_part,   ctx->guv_part,  ctx->g_in,
-                    ctx->g_out};
+                    ctx->g_out,        ctx->g_cur,      ctx->g_bat,     ctx->g_tab,     ctx->g_part,
+                    ctx->a_u};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (auto &v : ctx->ev)
@@ -414,6 +422,11 @@ bool ile_sky_frame(const double pole[3], float rot[9]) {
 // Pooled accumulators (max ln w, S1, S2, n) and the iteration log -> the summary fields of an
 // ile_adapt_result (cdf and hist are filled by the caller).
 void ile_fill_result(const double pooled[4], const double *ilog, int n_iter, ile_adapt_result *out) {
+    for (int d = 0; d < ILE_NDIM; d++) {
+        out->gmm_components[d] = 0;
+        out->gmm_n[d] = 0.0;
+        for (int c = 0; c < ILE_GMM_MAX; c++) out->gmm_w[d][c] = out->gmm_mu[d][c] = out->gmm_sigma[d][c] = 0.0;
+    }
     out->max_lnw = pooled[0];
     out->s1 = pooled[1];
     out->s2 = pooled[2];
@@ -778,6 +791,10 @@ static ile_status adapt_alloc(ile_ctx *ctx, int64_t N) {
         CK(cudaMemset(ctx->a_iter_log, 0, sizeof(double) * 2 * ILE_ADAPT_LOG));
         CK(cudaMalloc((void **)&ctx->a_iter_res, sizeof(double) * 8));
         CK(cudaMalloc((void **)&ctx->a_iter, sizeof(int)));
+        CK(cudaMalloc((void **)&ctx->g_cur, sizeof(IleGmm) * ILE_NDIM));
+        CK(cudaMalloc((void **)&ctx->g_bat, sizeof(IleGmm) * ILE_NDIM));
+        CK(cudaMalloc((void **)&ctx->g_tab, sizeof(IleGmmTab) * ILE_NDIM));
+        CK(cudaMalloc((void **)&ctx->g_part, sizeof(double) * ile_gmm_part_doubles()));
     }
     if (N > ctx->a_cap) {
         CK(grow(&ctx->a_lnwp, sizeof(double) * (size_t)N));
@@ -785,9 +802,29 @@ static ile_status adapt_alloc(ile_ctx *ctx, int64_t N) {
         CK(grow(&ctx->a_bins, (size_t)ILE_NDIM * (size_t)N));
         ctx->a_cap = N;
     }
+    const size_t ub = sizeof(float) * (size_t)__builtin_popcount(ctx->sp.gmm_mask) * (size_t)N;
+    if (ub > ctx->a_u_bytes) {
+        CK(grow(&ctx->a_u, ub));
+        ctx->a_u_bytes = ub;
+    }
     ile_status st = ensure_samples(ctx, N);
     if (st != ILE_OK) return st;
     return ILE_OK;
+}
+
+// Host form of the initial mixture (ile.h): C equal components evenly spaced over [lo, hi].
+static IleGmm gmm_initial(int C, double lo, double hi) {
+    IleGmm g{};
+    g.C = C;
+    g.lo = lo;
+    g.hi = hi;
+    for (int c = 0; c < C; c++) {
+        g.w[c] = 1.0 / C;
+        g.mu[c] = lo + (c + 0.5) * (hi - lo) / C;
+        g.sigma[c] = (hi - lo) / C;
+    }
+    g.n = 0.0;
+    return g;
 }
 
 ile_status ile_adapt_init(ile_ctx *ctx, const ile_adapt_cfg *cfg, const ile_adapt_result *resume) {
@@ -801,7 +838,30 @@ ile_status ile_adapt_init(ile_ctx *ctx, const ile_adapt_cfg *cfg, const ile_adap
         if (!(cfg->hi[d] > cfg->lo[d]) || !isfinite(cfg->lo[d]) || !isfinite(cfg->hi[d])) return ILE_E_ARG;
     if (!(cfg->lo[5] > 0.0) || cfg->lo[1] < -1.0 || cfg->hi[1] > 1.0 || cfg->lo[3] < -1.0 || cfg->hi[3] > 1.0)
         return ILE_E_ARG;
+    IleGmm gm[ILE_NDIM] = {};
+    if (cfg->gmm_mask) {
+        if (cfg->gmm_mask & ~cfg->adapt_mask) return ILE_E_ARG;
+        if (cfg->gmm_components < 1 || cfg->gmm_components > ILE_GMM_MAX) return ILE_E_ARG;
+        if (cfg->gmm_em_iters < 1 || cfg->gmm_em_iters > 100) return ILE_E_ARG;
+        for (int d = 0; d < ILE_NDIM; d++) {
+            if (!(cfg->gmm_mask & (1u << d))) continue;
+            gm[d] = gmm_initial(cfg->gmm_components, cfg->lo[d], cfg->hi[d]);
+            if (!resume) continue;
+            if (resume->gmm_components[d] != cfg->gmm_components || !(resume->gmm_n[d] >= 0.0)) return ILE_E_ARG;
+            for (int c = 0; c < cfg->gmm_components; c++) {
+                const double w = resume->gmm_w[d][c], mu = resume->gmm_mu[d][c], sg = resume->gmm_sigma[d][c];
+                if (!(w > 0.0) || !(sg > 0.0) || !isfinite(w) || !isfinite(sg) || !(mu >= cfg->lo[d]) ||
+                    !(mu <= cfg->hi[d]))
+                    return ILE_E_ARG;
+                gm[d].w[c] = w;
+                gm[d].mu[c] = mu;
+                gm[d].sigma[c] = sg;
+            }
+            gm[d].n = resume->gmm_n[d];
+        }
+    }
     DeviceGuard g(ctx->device);
+    ctx->sp.gmm_mask = cfg->gmm_mask;  // sizes the mixture buffers in adapt_alloc
     ile_status st = adapt_alloc(ctx, cfg->n_per_iter);
     if (st != ILE_OK) return st;
     IleSamplerParams sp{};
@@ -816,10 +876,18 @@ ile_status ile_adapt_init(ile_ctx *ctx, const ile_adapt_cfg *cfg, const ile_adap
     sp.gmst = ctx->pp.gmst;
     sp.sky = cfg->sky_frame;
     if (sp.sky && !ile_sky_frame(cfg->sky_pole, sp.rot)) return ILE_E_ARG;
+    sp.gmm_mask = cfg->gmm_mask;
     ctx->sp = sp;
     ctx->eps = cfg->eps;
     ctx->adapt_N = cfg->n_per_iter;
+    ctx->gmm_iters = cfg->gmm_mask ? cfg->gmm_em_iters : 0;
     CK(ile_launch_sampler_reset(sp, ctx->a_cdf, ctx->a_lnps, ctx->a_pooled, ctx->a_iter, 0, ctx->stream));
+    if (sp.gmm_mask) {
+        CK(cudaMemcpyAsync(ctx->g_cur, gm, sizeof gm, cudaMemcpyHostToDevice, ctx->stream));
+        CK(ile_launch_gmm_table(sp.gmm_mask, ctx->g_cur, ctx->g_tab, ctx->stream));
+        // gm is a stack array: the copy must finish before it goes out of scope
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     if (resume) {
         if (resume->n_iter < 0) return ILE_E_ARG;
         for (int d = 0; d < ILE_NDIM; d++) {
@@ -856,8 +924,8 @@ ile_status ile_adapt_step(ile_ctx *ctx, int n_iter) {
     for (int it = 0; it < n_iter; it++) {
         {
             StageScope t(ctx, 0);
-            CK(ile_launch_sample(ctx->sp, ctx->a_cdf, ctx->a_lnps, ctx->a_iter, N, ctx->theta, ctx->a_lnwp,
-                                 ctx->a_bins, ctx->stream));
+            CK(ile_launch_sample(ctx->sp, ctx->a_cdf, ctx->a_lnps, ctx->g_tab, ctx->a_iter, N, ctx->theta,
+                                 ctx->a_lnwp, ctx->a_bins, ctx->a_u, ctx->stream));
         }
         st = run_eval(ctx, ctx->theta, N, ctx->a_lnl, 0);
         if (st != ILE_OK) return st;
@@ -870,6 +938,11 @@ ile_status ile_adapt_step(ile_ctx *ctx, int n_iter) {
             CK(ile_launch_adapt(ctx->a_lnl, ctx->a_lnwp, ctx->a_bins, N, ctx->a_iter_res, ctx->sp, ctx->eps,
                                 ctx->a_hist_fx, ctx->a_hist, ctx->a_cdf, ctx->a_lnps, ctx->a_pooled, ctx->a_iter_log,
                                 ctx->a_iter, 1, ctx->stream));
+        }
+        if (ctx->sp.gmm_mask) {
+            StageScope t(ctx, 4, 2 * ctx->gmm_iters);
+            CK(ile_launch_gmm_update(ctx->sp.gmm_mask, ctx->a_u, ctx->a_lnl, ctx->a_lnwp, ctx->a_iter_res, N,
+                                     ctx->gmm_iters, ctx->g_cur, ctx->g_bat, ctx->g_tab, ctx->g_part, ctx->stream));
         }
     }
     return ILE_OK;
@@ -886,8 +959,20 @@ ile_status ile_adapt_get(ile_ctx *ctx, ile_adapt_result *out) {
     CK(cudaMemcpyAsync(&it, ctx->a_iter, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(out->cdf, ctx->a_cdf, sizeof(out->cdf), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(out->hist, ctx->a_hist, sizeof(out->hist), cudaMemcpyDeviceToHost, ctx->stream));
+    IleGmm gm[ILE_NDIM] = {};
+    if (ctx->sp.gmm_mask) CK(cudaMemcpyAsync(gm, ctx->g_cur, sizeof gm, cudaMemcpyDeviceToHost, ctx->stream));
     ile_status st = read_flags(ctx);
     ile_fill_result(pooled, ilog, it, out);
+    for (int d = 0; d < ILE_NDIM; d++) {
+        if (!(ctx->sp.gmm_mask & (1u << d))) continue;
+        out->gmm_components[d] = gm[d].C;
+        for (int c = 0; c < gm[d].C; c++) {
+            out->gmm_w[d][c] = gm[d].w[c];
+            out->gmm_mu[d][c] = gm[d].mu[c];
+            out->gmm_sigma[d][c] = gm[d].sigma[c];
+        }
+        out->gmm_n[d] = gm[d].n;
+    }
     return st;
 }
 

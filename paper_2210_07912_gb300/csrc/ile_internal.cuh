@@ -147,6 +147,24 @@ struct IleSamplerParams {
     int sky;                           // 1: variables 0, 1 are the rotated frame's (phi', sin lat')
     float rot[9];                      // rotated frame: columns e1, e2, p (Earth-fixed), row-major
     float gmst;
+    unsigned gmm_mask;                 // bits of adapt_mask drawn from a Gaussian mixture (ile_gmm.cu)
+};
+
+// One dimension's Gaussian mixture in FP64 (the adapted state) and its sampler form in FP32.
+struct IleGmm {
+    int C;
+    double lo, hi;
+    double w[ILE_GMM_MAX], mu[ILE_GMM_MAX], sigma[ILE_GMM_MAX];
+    double n;  // samples the mixture has been trained on
+};
+struct IleGmmTab {
+    uint64_t cw[ILE_GMM_MAX + 1];  // integer cumulative weights, 2^32 scale
+    float mu[ILE_GMM_MAX], sig[ILE_GMM_MAX];
+    float p1[ILE_GMM_MAX];    // Phi(z_lo): mass of the normal below the range
+    float q2[ILE_GMM_MAX];    // Phi(-z_hi): mass above the range
+    float dm[ILE_GMM_MAX];    // Z = Phi(z_hi) - Phi(z_lo): mass inside
+    float coef[ILE_GMM_MAX];  // ln(w_c / (sqrt(2 pi) sigma_c Z_c))
+    int C;
 };
 
 // Rotated-frame basis from a pole vector (host; see ile.h): returns false for a zero vector.
@@ -309,9 +327,19 @@ int ile_hist_partial_count(int64_t N);
 cudaError_t ile_launch_sampler_reset(const IleSamplerParams &sp, uint64_t *cdf, float *lnps_tab, double *pooled,
                                      int *iter_dev, int iter0, cudaStream_t st);
 cudaError_t ile_launch_lnps(const IleSamplerParams &sp, const uint64_t *cdf, float *lnps_tab, cudaStream_t st);
+// gmm_tab: [7] sampler tables (used for the dimensions in sp.gmm_mask; may be NULL when it is 0);
+// u_gmm: [n_gmm][N] sampling variables of the mixture dimensions, in ascending dimension order
 cudaError_t ile_launch_sample(const IleSamplerParams &sp, const uint64_t *cdf, const float *lnps_tab,
-                              const int *iter_dev, int64_t N, double *theta, double *lnw_prior, uint8_t *bins,
-                              cudaStream_t st);
+                              const IleGmmTab *gmm_tab, const int *iter_dev, int64_t N, double *theta,
+                              double *lnw_prior, uint8_t *bins, float *u_gmm, cudaStream_t st);
+// Gaussian-mixture adaptation (ile_gmm.cu).  cur, bat, tab: [7] on the device; part: scratch of
+// ile_gmm_part_doubles() doubles.  ile_launch_gmm_table rebuilds tab from cur for the dimensions
+// in mask; ile_launch_gmm_update runs em_iters EM steps and the merge (cur updated, N samples).
+size_t ile_gmm_part_doubles();
+cudaError_t ile_launch_gmm_table(unsigned mask, const IleGmm *cur, IleGmmTab *tab, cudaStream_t st);
+cudaError_t ile_launch_gmm_update(unsigned mask, const float *u_gmm, const double *lnL, const double *lnw_prior,
+                                  const double *iter_res, int64_t N, int em_iters, IleGmm *cur, IleGmm *bat,
+                                  IleGmmTab *tab, double *part, cudaStream_t st);
 cudaError_t ile_launch_adapt(const double *lnL, const double *lnw_prior, const uint8_t *bins, int64_t N,
                              const double *iter_res, const IleSamplerParams &sp, double eps,
                              unsigned long long *hist_fx, double *hist, uint64_t *cdf, float *lnps_tab, double *pooled,

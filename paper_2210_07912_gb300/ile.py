@@ -20,6 +20,7 @@ ILE_DEVICE_PTRS = 1
 ILE_NO_TMARG = 2
 NDIM = 7
 NBINS = 100
+GMM_MAX = 8
 
 _lib = None
 ADAPT_LOG = 64
@@ -29,7 +30,8 @@ class AdaptCfg(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("point_id", ctypes.c_uint32), ("n_per_iter", ctypes.c_int64),
                 ("n_iter", ctypes.c_int), ("adapt_mask", ctypes.c_uint), ("eps", ctypes.c_double),
                 ("lo", ctypes.c_double * NDIM), ("hi", ctypes.c_double * NDIM), ("sky_frame", ctypes.c_int),
-                ("sky_pole", ctypes.c_double * 3)]
+                ("sky_pole", ctypes.c_double * 3), ("gmm_mask", ctypes.c_uint), ("gmm_components", ctypes.c_int),
+                ("gmm_em_iters", ctypes.c_int)]
 
 
 class AdaptResult(ctypes.Structure):
@@ -37,7 +39,10 @@ class AdaptResult(ctypes.Structure):
                 ("ess", ctypes.c_double), ("max_lnw", ctypes.c_double), ("s1", ctypes.c_double),
                 ("s2", ctypes.c_double), ("n_total", ctypes.c_double), ("n_iter", ctypes.c_int),
                 ("iter_ln_L", ctypes.c_double * ADAPT_LOG), ("iter_n_eff", ctypes.c_double * ADAPT_LOG),
-                ("cdf", (ctypes.c_uint64 * (NBINS + 1)) * NDIM), ("hist", (ctypes.c_double * NBINS) * NDIM)]
+                ("cdf", (ctypes.c_uint64 * (NBINS + 1)) * NDIM), ("hist", (ctypes.c_double * NBINS) * NDIM),
+                ("gmm_components", ctypes.c_int * NDIM), ("gmm_w", (ctypes.c_double * GMM_MAX) * NDIM),
+                ("gmm_mu", (ctypes.c_double * GMM_MAX) * NDIM), ("gmm_sigma", (ctypes.c_double * GMM_MAX) * NDIM),
+                ("gmm_n", ctypes.c_double * NDIM)]
 
 
 class PointDesc(ctypes.Structure):
@@ -69,22 +74,30 @@ def default_ranges(fs: float = 4096.0, tc_max: float | None = None, d_min: float
 
 
 def make_adapt_cfg(seed: int, n_per_iter: int, n_iter: int = 1, adapt_mask: int = 0b11, eps: float = 0.1,
-                   point_id: int = 0, lo=None, hi=None, sky_pole=None) -> AdaptCfg:
+                   point_id: int = 0, lo=None, hi=None, sky_pole=None, gmm_mask: int = 0, gmm_components: int = 3,
+                   gmm_em_iters: int = 8) -> AdaptCfg:
     """sky_pole: Earth-fixed pole vector of the rotated network sky frame (e.g. r_L1 - r_H1); then
-    sampling variables 0, 1 are (phi', sin lat') in that frame.  None: (ra, sin dec)."""
+    sampling variables 0, 1 are (phi', sin lat') in that frame.  None: (ra, sin dec).
+    gmm_mask: adaptive dimensions drawn from a truncated Gaussian mixture of gmm_components
+    components, refit with gmm_em_iters EM steps per iteration."""
     dlo, dhi = default_ranges()
     lo = dlo if lo is None else lo
     hi = dhi if hi is None else hi
     pole = (0.0, 0.0, 0.0) if sky_pole is None else tuple(float(x) for x in sky_pole)
     return AdaptCfg(seed, point_id, n_per_iter, n_iter, adapt_mask, eps, (ctypes.c_double * NDIM)(*lo),
-                    (ctypes.c_double * NDIM)(*hi), 0 if sky_pole is None else 1, (ctypes.c_double * 3)(*pole))
+                    (ctypes.c_double * NDIM)(*hi), 0 if sky_pole is None else 1, (ctypes.c_double * 3)(*pole),
+                    gmm_mask, gmm_components if gmm_mask else 0, gmm_em_iters if gmm_mask else 0)
 
 
 def result_dict(r: AdaptResult) -> dict:
     return dict(ln_L=r.ln_L, sigma_ln=r.sigma_ln, n_eff=r.n_eff, ess=r.ess, max_lnw=r.max_lnw, s1=r.s1, s2=r.s2,
                 n_total=r.n_total, n_iter=r.n_iter, iter_ln_L=np.array(r.iter_ln_L[:max(r.n_iter, 0)]),
                 iter_n_eff=np.array(r.iter_n_eff[:max(r.n_iter, 0)]),
-                cdf=np.ctypeslib.as_array(r.cdf).copy(), hist=np.ctypeslib.as_array(r.hist).copy())
+                cdf=np.ctypeslib.as_array(r.cdf).copy(), hist=np.ctypeslib.as_array(r.hist).copy(),
+                gmm=[None if r.gmm_components[d] == 0 else
+                     dict(w=np.array(r.gmm_w[d][:r.gmm_components[d]]), mu=np.array(r.gmm_mu[d][:r.gmm_components[d]]),
+                          sigma=np.array(r.gmm_sigma[d][:r.gmm_components[d]]), n=r.gmm_n[d])
+                     for d in range(NDIM)])
 
 
 class IleError(RuntimeError):
@@ -496,6 +509,8 @@ class Batch:
     def _descs(points, cfgs):
         keep, descs = [], (PointDesc * len(points))()
         for i, (p, c) in enumerate(zip(points, cfgs)):
+            if c.gmm_mask:
+                raise ValueError("batched runs adapt histograms only; Gaussian-mixture sampling is per point")
             lm = np.ascontiguousarray(p.lm, np.int32)
             tens = np.ascontiguousarray(p.det_tensor, np.float64)
             pos = np.ascontiguousarray(p.det_pos, np.float64)

@@ -55,6 +55,7 @@ struct Sm {
     uint64_t bfull[NBMAX], bempty[NBMAX], tfull[2], tempty[2], yready, aready, s4done, tdone;
     uint32_t tmem_base;
     int wlo[4][ILE_MAX_DET], whi[4][ILE_MAX_DET];
+    int2 dkr[NMATH / 32][ILE_MAX_DET];  // per math warp and detector: (min, max) of i0 - tile lo
 };
 
 // Register-resident per-detector value (the selects avoid dynamic indexing).
@@ -115,14 +116,15 @@ struct JobIter {
         j.nwr = (nw + 15) & ~15;
         return j;
     }
-    __device__ void next() {
+    __device__ void next() { next_from(get()); }
+    // advance past job j (the job get() returned for the current position)
+    __device__ void next_from(const Job &j) {
         if (c < 0) {
             if (++k < K) return;
             k = 0;
             c = 0;
             return;
         }
-        const Job j = get();
         if (++w < j.W) return;
         w = 0;
         if (++k < K) return;
@@ -420,6 +422,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const Det4 i0d{i0[0], i0[1], i0[2], i0[3]};
             const Det4f wtd{wt[0], wt[1], wt[2], wt[3]};
             JobIter jit(Nt, K, nwcol, pt.TP - ILE_QCOLS, lo, hi);
+            // this warp's spread of window offsets per detector, for the single-window jobs (the
+            // previous tile's readers of dkr passed tdone before this tile's aready)
+#pragma unroll
+            for (int k = 0; k < ILE_MAX_DET; k++) {
+                if (k < K) {
+                    int l = i0d(k) - lo(k), h = l;
+                    for (int o = 16; o; o >>= 1) {
+                        l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
+                        h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
+                    }
+                    if (lane == 0) sm.dkr[warp][k] = make_int2(l, h);
+                }
+            }
+            __syncwarp();
 
             // ---- S4 on the tensor cores: the quadratic-term job of detector k leaves in TMEM, for
             // this sample, z = U_k c_k and w = V_k c_k as column blocks [Re z | Im z | Re w | Im w]
@@ -482,16 +498,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 fence_after();
                 const int dk = i0d(j.k) - lo(j.k);  // first column of bin 0, relative to the chunk's range
-                const int wsel = j.W == 1 ? 0 : min(dk / j.step, j.W - 1);
-                const int jbeg = g * JG;             // my first bin of the chunk
-                const bool mine = wsel == j.w && jbeg < j.Jc;
-                const int s0 = dk - j.w * j.step + jbeg + (j.wbeg - j.wbeg8);  // my first column in the window
+                const int jbeg = g * JG;             // my first bin of the chunk (warp-uniform)
+                const int shift = jbeg + (j.wbeg - j.wbeg8) - j.w * j.step;
+                const int s0 = dk + shift;           // my first column in the window
                 // my columns s0 .. s0 + 16 lie in the 16-column blocks a0 and a0 + 16 (both < NWIN)
                 const int a0 = s0 & ~15;
-                int cmin = mine ? a0 : 0x7fffffff, cmax = mine ? a0 + 16 : -1;
-                for (int o = 16; o; o >>= 1) {
-                    cmin = min(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
-                    cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+                bool mine;
+                int cmin, cmax;  // the warp's range of blocks
+                if (j.W == 1) {
+                    // one window: every sample reads it; the block range follows from the warp's
+                    // offset range ((x & ~15) is monotone)
+                    mine = jbeg < j.Jc;
+                    const int2 r = sm.dkr[warp][j.k];
+                    cmin = mine ? (r.x + shift) & ~15 : 0x7fffffff;
+                    cmax = mine ? ((r.y + shift) & ~15) + 16 : -1;
+                } else {
+                    const int wsel = min(dk / j.step, j.W - 1);
+                    mine = wsel == j.w && jbeg < j.Jc;
+                    cmin = mine ? a0 : 0x7fffffff;
+                    cmax = mine ? a0 + 16 : -1;
+                    for (int o = 16; o; o >>= 1) {
+                        cmin = min(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+                        cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+                    }
                 }
                 if (cmax >= 0) {
                     const uint32_t taddr = tmem + tb * NWIN + lane_addr;
@@ -511,17 +540,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const float w = wtd(j.k), omw = 1.f - w;
                     const float *src = my_row + (s0 & 15);
                     float vprev = src[0];
+                    if (jbeg + JG <= j.Jc) {
 #pragma unroll
-                    for (int jj = 0; jj < JG; jj++) {
-                        if (jbeg + jj < j.Jc) {
+                        for (int jj = 0; jj < JG; jj++) {
                             const float v = src[jj + 1];
-                            D[jj] += fmaf(w, v, omw * vprev);
+                            D[jj] = fmaf(omw, vprev, fmaf(w, v, D[jj]));
                             vprev = v;
+                        }
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < JG; jj++) {
+                            if (jbeg + jj < j.Jc) {
+                                const float v = src[jj + 1];
+                                D[jj] = fmaf(omw, vprev, fmaf(w, v, D[jj]));
+                                vprev = v;
+                            }
                         }
                     }
                 }
                 gjob++;
-                jit.next();
+                jit.next_from(j);
                 if (j.k == K - 1 && j.w == j.W - 1) {
                     // chunk complete: S5 log-sum-exp update (or the full grid)
                     if constexpr (DM) {

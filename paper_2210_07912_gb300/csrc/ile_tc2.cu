@@ -1,6 +1,6 @@
 // ile_tc2.cu -- fused, pipelined BF16x3 tensor-core kernel for stages S1-S5 on sm_103a.
 //
-// One persistent CTA per SM walks 128-sample tiles of the delay-sorted samples.  18 warps:
+// One persistent CTA per SM walks 128-sample tiles of the delay-sorted samples.  19 warps:
 //
 //   16 math warps: warp w serves TMEM lane quadrant q = w % 4 (samples 32q .. 32q+31 of the
 //   tile) and bin group g = w / 4, so each sample has four threads (g = 0..3):
@@ -19,11 +19,14 @@
 //   window of <= 120 columns) bulk-copy the Q window (hi and lo rows, one contiguous block each)
 //   into a ring of NB shared buffers as soon as a slot is free;
 //   warp 16, lane 0 (MMA warp): issue 3 x KP/16 tcgen05.mma (hi*hi + hi*lo + lo*hi, kind::f16,
-//   FP32 accumulation) per job into one of two TMEM accumulator buffers.
+//   FP32 accumulation) per job into one of two TMEM accumulator buffers;
+//   warp 18 (prefetch warp): gathers the next tile's sample parameters through the sort
+//   permutation into shared memory while the current tile is in flight.
 //
 // Hand-offs are mbarriers: bfull/bempty (B ring), tfull/tempty (TMEM buffers), aready (A operand
 // and the tile's column ranges written; waited on by all roles), tdone (per-thread log-sum-exp
-// partials written).  Jobs are enumerated identically by all roles.  A tile whose column spread
+// partials written), sready (sample parameters staged; the prefetch warp refills the stage once
+// yready shows that every math thread has read it).  Jobs are enumerated identically by all roles.  A tile whose column spread
 // does not fit one window is covered by overlapping windows of 128 columns, each sample reading
 // the single window that holds all the columns it needs.  Every wait is bounded; on expiry the
 // kernel raises ILE_FLAG_TIMEOUT (all CTAs then stop waiting), releases its TMEM and returns.
@@ -39,7 +42,8 @@ constexpr int NGRP = 4;                    // threads per sample
 constexpr int NMATH = TILE * NGRP;         // 512 math threads
 constexpr int MMA_WARP = NMATH / 32;        // warp 16: tcgen05.mma issue
 constexpr int COPY_WARP = MMA_WARP + 1;    // warp 17: bulk copies of the Q windows
-constexpr int NTHREADS = NMATH + 64;
+constexpr int PREF_WARP = COPY_WARP + 1;   // warp 18: gathers the next tile's sample parameters
+constexpr int NTHREADS = NMATH + 96;
 constexpr int JW = 64;                     // window bins per chunk
 constexpr int JG = JW / NGRP;              // bins per thread per chunk
 constexpr int NWIN = 128;                  // columns per TMEM accumulator buffer (= max MMA N here)
@@ -52,7 +56,7 @@ constexpr uint32_t SLEEP_NS = 10000;
 constexpr int RSTRIDE = 33;                // per-thread row: 32 staged columns + 1 (odd stride: conflict-free)
 
 struct Sm {
-    uint64_t bfull[NBMAX], bempty[NBMAX], tfull[2], tempty[2], yready, aready, s4done, tdone;
+    uint64_t bfull[NBMAX], bempty[NBMAX], tfull[2], tempty[2], yready, aready, s4done, tdone, sready;
     uint32_t tmem_base;
     int wlo[4][ILE_MAX_DET], whi[4][ILE_MAX_DET];
     int2 dkr[NMATH / 32][ILE_MAX_DET];  // per math warp and detector: (min, max) of i0 - tile lo
@@ -172,9 +176,11 @@ __device__ __forceinline__ const Tc2Point &work_item(const Tc2Point &one, const 
 // Shared-memory layout (LK detectors, LKC 16-byte K-chunks: the point's own sizes for a
 // single-point launch, the largest of the batch otherwise):
 //   A [LK][2][LKC][TILE] | B [NB][2][LKC][NWIN] | rows [NMATH][RSTRIDE] | aq_s [NMATH] | ls_s [NMATH]
+//   | stg [7][TILE] (FP64)
 // A math thread's row holds the two 16-column TMEM blocks its bins need; aq_s and ls_s its share
-// of the quadratic term and its partial log-sum-exp.  Before the job loop the rows area holds the
-// tile's harmonics table y [M][TILE] (float2).  U/V pairs are read through L1.
+// of the quadratic term and its partial log-sum-exp; stg the tile's sample parameters, gathered
+// through the sort permutation by the prefetch warp while the previous tile is in flight.  Before
+// the job loop the rows area holds the tile's harmonics table y [M][TILE] (float2).
 template <bool BATCH, bool DM>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ile_tc2_kernel(const __grid_constant__ Tc2Point one, const Tc2Point *__restrict__ pts,
@@ -188,6 +194,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float *rows = reinterpret_cast<float *>(B + (size_t)NB * 2 * LKC * NWIN);         // [NMATH][RSTRIDE]
     float *aq_s = rows + RSTRIDE * NMATH;                                             // [NMATH]
     float2 *ls_s = reinterpret_cast<float2 *>(aq_s + NMATH);                           // [NMATH]
+    double *stg = reinterpret_cast<double *>(ls_s + NMATH);                            // [7][TILE]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -205,6 +212,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_init(&sm.aready, NMATH);
         mbar_init(&sm.s4done, NMATH);
         mbar_init(&sm.tdone, NMATH);
+        mbar_init(&sm.sready, 32);
         mbar_init_fence();
     }
     fence_before();
@@ -249,6 +257,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (failed) atomicOr(flags, ILE_FLAG_TIMEOUT);
         }
         __syncwarp();
+    } else if (warp == PREF_WARP) {
+        // ------------------------------------------------------------------ prefetch warp
+        uint32_t tiles_done = 0;
+        for (int64_t it = blockIdx.x; it < nitems && !failed; it += gridDim.x, tiles_done++) {
+            // the buffer is free once every math thread has read the previous tile's values
+            // (they read them before arriving on yready)
+            if (tiles_done > 0 && !warp_wait(&sm.yready, (tiles_done - 1) & 1u, flags)) {
+                failed = true;
+                break;
+            }
+            int64_t tile;
+            const Tc2Point &pt = work_item<BATCH>(one, pts, items, it, tile);
+            const int64_t N = pt.N;
+            int64_t src[TILE / 32];
+#pragma unroll
+            for (int i = 0; i < TILE / 32; i++) {
+                const int64_t p = tile * TILE + i * 32 + lane;
+                src[i] = pt.perm[p < N ? p : tile * TILE];
+            }
+#pragma unroll
+            for (int i = 0; i < TILE / 32; i++)
+#pragma unroll
+                for (int d = 0; d < ILE_NDIM; d++) stg[d * TILE + i * 32 + lane] = pt.samples[(int64_t)d * N + src[i]];
+            mbar_arrive(&sm.sready);
+        }
+        if (failed) atomicOr(flags, ILE_FLAG_TIMEOUT);
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------------ MMA warp
         if (lane == 0) {
@@ -313,18 +347,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const PointParams &pp = pt.pp;
             const int K = pp.K, M = pp.M, Nt = pp.Nt, KC = pt.KP / 8;
             const int64_t N = pt.N;
-            const double *__restrict__ samples = pt.samples;
             const int *__restrict__ perm = pt.perm;
             double *__restrict__ out = pt.out;
             const int64_t p = tile * TILE + row;
             const bool valid = p < N;
-            const int64_t src = perm[valid ? p : tile * TILE];
-            // ---- S1/S2: geometry, harmonics, coefficients
+            // ---- S1/S2: geometry, harmonics, coefficients (parameters staged by the prefetch warp)
+            if (!warp_wait(&sm.sready, tiles_done & 1u, flags)) {
+                failed = true;
+                break;
+            }
             double th[ILE_NDIM];
             bool finite = true;
 #pragma unroll
             for (int d = 0; d < ILE_NDIM; d++) {
-                th[d] = samples[(int64_t)d * N + src];
+                th[d] = stg[d * TILE + row];
                 finite = finite && isfinite(th[d]);
             }
             if (!finite || th[5] <= 0.0) {
@@ -636,7 +672,7 @@ size_t tc2_smem(int K, int M, int KP, int NB) {
     const int KC = KP / 8;
     (void)M;  // the harmonics table (8 M TILE bytes <= 21.5 KB) fits in the rows area
     return (size_t)16 * K * 2 * KC * TILE + (size_t)16 * NB * 2 * KC * NWIN + sizeof(float) * RSTRIDE * NMATH +
-           sizeof(float) * NMATH + sizeof(float2) * NMATH;
+           sizeof(float) * NMATH + sizeof(float2) * NMATH + sizeof(double) * ILE_NDIM * TILE;
 }
 static_assert(8 * ILE_MAX_MODES * TILE <= 4 * RSTRIDE * NMATH, "y table must fit in the rows area");
 

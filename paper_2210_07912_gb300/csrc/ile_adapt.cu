@@ -21,16 +21,20 @@
 // independent of the order of the atomics, so a run is reproducible bit for bit); the next table
 // is mass_b = (1 - eps) h_b + eps / 100, accumulated left to right in FP64 (explicit
 // round-to-nearest operations, no contraction) and cut to cdf[b] = floor(2^32 sum_{b' < b} mass_b').
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
 #include <stdint.h>
 
 #include "ile_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
 constexpr int NB = ILE_NBINS;
 constexpr int ND = ILE_NDIM;
 constexpr int HIST_THREADS = 256;
-constexpr int HIST_CHUNK = 8192;
+constexpr int HIST_CHUNK = 2048;
 
 __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                                               uint32_t k1, uint32_t out[4]) {
@@ -204,7 +208,9 @@ __global__ void __launch_bounds__(256) bsample_kernel(const IleBatchPoint *__res
 }
 
 // Histograms of w_n = exp(ln w_n - max) over each adaptive dimension, as 2^-40 fixed point:
-// per-block shared-memory integer atomics, then one integer atomic per (d, b) and block.
+// the lanes of a warp that fall in the same bin are summed first (labelled partition + reduce,
+// so an adapted histogram's crowded bins cost one shared atomic per warp, not one per lane), then
+// per-block shared-memory integer atomics and one global integer atomic per (d, b) and block.
 __device__ __forceinline__ void hist_chunk(const double *__restrict__ lnL, const double *__restrict__ lnw_prior,
                                            const uint8_t *__restrict__ bins, int64_t N, int64_t beg,
                                            const double *__restrict__ iter_res, unsigned mask,
@@ -217,8 +223,14 @@ __device__ __forceinline__ void hist_chunk(const double *__restrict__ lnL, const
         const float w = __expf((float)(lnL[n] + lnw_prior[n] - m));
         const unsigned long long wf = (unsigned long long)(w * 1099511627776.0f);  // w * 2^40
 #pragma unroll
-        for (int d = 0; d < ND; d++)
-            if (mask & (1u << d)) atomicAdd(&h[d * NB + bins[(int64_t)d * N + n]], wf);
+        for (int d = 0; d < ND; d++) {
+            if (mask & (1u << d)) {
+                const unsigned b = bins[(int64_t)d * N + n];
+                const cg::coalesced_group grp = cg::labeled_partition(cg::coalesced_threads(), b);
+                const unsigned long long sum = cg::reduce(grp, wf, cg::plus<unsigned long long>());
+                if (grp.thread_rank() == 0 && sum) atomicAdd(&h[d * NB + b], sum);
+            }
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ND * NB; i += blockDim.x)
@@ -259,22 +271,37 @@ __device__ __forceinline__ void renorm_point(unsigned long long *__restrict__ hi
                                              double *__restrict__ pooled, double *__restrict__ iter_log,
                                              int *__restrict__ iter_dev, int update_tables) {
     const int i = threadIdx.x;
+    __shared__ double hs[ND][NB], tot_s[ND];
     for (int j = i; j < ND * NB; j += blockDim.x) {
-        hist[j] = (double)hist_fx[j] * (1.0 / 1099511627776.0);
+        const double v = (double)hist_fx[j] * (1.0 / 1099511627776.0);
+        hist[j] = v;
+        hs[j / NB][j % NB] = v;
         hist_fx[j] = 0ull;  // ready for the next iteration
+    }
+    __syncthreads();
+    // the bin masses in parallel (FP64 divisions are slow and independent), then the cumulative
+    // sums in bin order; the operations and their order are those of the sequential definition
+    if (update_tables && i < ND && (mask & (1u << i))) {
+        double tot = 0.0;
+        for (int b = 0; b < NB; b++) tot = __dadd_rn(tot, hs[i][b]);
+        tot_s[i] = tot;
+    }
+    __syncthreads();
+    if (update_tables) {
+        const double ome = __dsub_rn(1.0, eps), flo = __ddiv_rn(eps, (double)NB);
+        for (int j = i; j < ND * NB; j += blockDim.x) {
+            const int d = j / NB, b = j % NB;
+            if (mask & (1u << d)) hs[d][b] = __dadd_rn(__dmul_rn(ome, __ddiv_rn(hs[d][b], tot_s[d])), flo);
+        }
     }
     __syncthreads();
     if (update_tables && i < ND && (mask & (1u << i))) {
         const int d = i;
-        const double *h = hist + d * NB;
         uint64_t *c = cdf + d * (NB + 1);
-        double tot = 0.0;
-        for (int b = 0; b < NB; b++) tot = __dadd_rn(tot, h[b]);
         double acc = 0.0;
         c[0] = 0;
         for (int b = 0; b < NB; b++) {
-            const double mass =
-                __dadd_rn(__dmul_rn(__dsub_rn(1.0, eps), __ddiv_rn(h[b], tot)), __ddiv_rn(eps, (double)NB));
+            const double mass = hs[d][b];
             acc = __dadd_rn(acc, mass);
             if (b + 1 < NB) {
                 double v = floor(__dmul_rn(acc, 4294967296.0));

@@ -134,7 +134,7 @@ Layout layout() {
     L.n2t = 4096;
     L.off_t1 = 0;
     L.off_a1 = align256(L.off_t1 + sizeof(float) * (size_t)L.n1a * L.n1s);
-    L.off_t2 = align256(L.off_a1 + sizeof(float) * (size_t)L.n1a);
+    L.off_t2 = align256(L.off_a1 + sizeof(float2) * (size_t)L.n1a);
     L.off_scratch = align256(L.off_t2 + sizeof(float) * (size_t)L.n2t * L.n2s);
     L.bytes = align256(L.off_scratch + sizeof(double) * (size_t)(L.n1a > L.n2t ? L.n1a : L.n2t));
     return L;
@@ -170,20 +170,19 @@ cudaError_t ile_build_dmarg(double d_min, double d_max, double d_ref, void *buf,
     const double xc = 0.5 * (r.xmin + r.xmax), wz = 0.125 * (r.xmax - r.xmin);
     uint8_t *base = static_cast<uint8_t *>(buf);
     float *t1 = reinterpret_cast<float *>(base + L.off_t1);
-    float *a1 = reinterpret_cast<float *>(base + L.off_a1);
+    float2 *a1 = reinterpret_cast<float2 *>(base + L.off_a1);
     float *t2 = reinterpret_cast<float *>(base + L.off_t2);
     double *nodes = reinterpret_cast<double *>(base + L.off_scratch);
     const Gl8 gl = gauss_legendre8();
     // table 1 nodes
     std::vector<double> an(L.n1a);
-    std::vector<float> anf(L.n1a);
+    std::vector<float2> anf(L.n1a);  // (a_i, 1 / (a_{i+1} - a_i)) for the per-bin lerp weight
     const double dtau1 = 2.0 * L.tau1_max / (L.n1a - 1);
-    for (int i = 0; i < L.n1a; i++) {
-        an[i] = A0 * sinh(-L.tau1_max + i * dtau1);
-        anf[i] = (float)an[i];
-    }
+    for (int i = 0; i < L.n1a; i++) an[i] = A0 * sinh(-L.tau1_max + i * dtau1);
+    for (int i = 0; i < L.n1a; i++)
+        anf[i] = make_float2((float)an[i], i + 1 < L.n1a ? (float)(1.0 / (an[i + 1] - an[i])) : 0.f);
     cudaError_t e = cudaMemcpyAsync(nodes, an.data(), sizeof(double) * L.n1a, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(a1, anf.data(), sizeof(float) * L.n1a, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(a1, anf.data(), sizeof(float2) * L.n1a, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     table1_kernel<<<(L.n1a * L.n1s + 127) / 128, 128, 0, st>>>(gl, r, nodes, L.n1a, L.n1s, t1);
     e = cudaGetLastError();
@@ -217,6 +216,7 @@ cudaError_t ile_build_dmarg(double d_min, double d_max, double d_ref, void *buf,
     dm.n1a = L.n1a;
     dm.n1s = L.n1s;
     dm.A0 = (float)A0;
+    dm.inv_A0 = (float)(1.0 / A0);
     dm.tau1_max = (float)L.tau1_max;
     dm.inv_dtau1 = (float)(1.0 / dtau1);
     dm.s1_lo = (float)S1_LO;
@@ -226,6 +226,7 @@ cudaError_t ile_build_dmarg(double d_min, double d_max, double d_ref, void *buf,
     dm.n2t = L.n2t;
     dm.n2s = L.n2s;
     dm.eps = (float)EPS2;
+    dm.inv_eps = (float)(1.0 / EPS2);
     dm.tau2_lo = (float)tlo;
     dm.inv_dtau2 = (float)(1.0 / dtau2);
     dm.s2_lo = (float)L.s2_lo;

@@ -481,62 +481,116 @@ __global__ void __launch_bounds__(256, 1)
 }
 
 // ------------------------------------------------------------------ dQ: sample-reduction GEMM
-constexpr int QTB = 128;  // time columns per CTA
-constexpr int QNC = 32;   // samples per staged chunk
+// dQ_k(r, t) = sum_n C_k(r, n) P_k(n, t), P_k(n, t) = (1 - w) pi(n, t - i0) + w pi(n, t - i0 - 1).
+// One CTA per (128-column block, detector, sample split); the samples are consumed in chunks of
+// 32 whose raw pi row segments and coefficient columns are brought into shared memory with
+// cp.async (zero-filled outside the window), double-buffered: chunk c + 1 is in flight while the
+// lerp pass and the register-blocked FMA product of chunk c run.
+constexpr int QTB = 128;       // time columns per CTA
+constexpr int QNC = 32;        // samples per staged chunk
+constexpr int QRW = QTB + 4;   // staged row: pi at t0 - i0 - 1 + m, m = 0 .. QTB (stride padded)
 
-__global__ void __launch_bounds__(256)
+struct GqSmem {
+    float raw[2][QNC][QRW];
+    float Cc[2][RMAX][QNC];
+    float Pc[QNC][QTB];
+    int i0c[2][QNC];
+    float wc[2][QNC];
+};
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+__global__ void __launch_bounds__(256, 2)
     adj_gq_kernel(const __grid_constant__ PointParams pp, const float *__restrict__ pig, IleScratch s, int64_t N,
                   int nsplit, float *__restrict__ part) {
-    __shared__ __align__(16) float Cc[RMAX][QNC];
-    __shared__ __align__(16) float Pc[QNC][QTB];
-    __shared__ int i0c[QNC];
-    __shared__ float wc[QNC];
+    extern __shared__ __align__(16) uint8_t gq_raw[];
+    GqSmem &sm = *reinterpret_cast<GqSmem *>(gq_raw);
     const int Nt = pp.Nt, R = 2 * pp.M, T = pp.T_ext;
     const int t0 = blockIdx.x * QTB, k = blockIdx.y, split = blockIdx.z;
     const int64_t nb = N * split / nsplit, ne = N * (split + 1) / nsplit;
+    const int nch = (int)((ne - nb + QNC - 1) / QNC);
     const int tid = threadIdx.x, ry = tid >> 4, tx = tid & 15;
     float acc[3][8];
 #pragma unroll
     for (int m = 0; m < 3; m++)
 #pragma unroll
         for (int j = 0; j < 8; j++) acc[m][j] = 0.f;
+    // coefficient rows R .. RMAX - 1 stay zero (the copies write rows < R only)
+    for (int i = tid; i < 2 * RMAX * QNC; i += 256) (&sm.Cc[0][0][0])[i] = 0.f;
 
-    for (int64_t c0 = nb; c0 < ne; c0 += QNC) {
+    // window start and lerp weight of chunk c's sample tid (tid < QNC), 0 beyond the range
+    auto load_iw = [&](int c, int &i0v, float &wv) {
+        const int64_t n = nb + (int64_t)c * QNC + tid;
+        const bool ok = c < nch && n < ne;
+        i0v = ok ? s.I0[(int64_t)k * N + n] : 0;
+        wv = ok ? s.W[(int64_t)k * N + n] : 0.f;
+    };
+    auto issue = [&](int c, int b) {
+        const int64_t c0 = nb + (int64_t)c * QNC;
         const int nc = (int)min((int64_t)QNC, ne - c0);
-        __syncthreads();
+        for (int i = tid; i < QNC * (QTB + 1); i += 256) {
+            const int j = i / (QTB + 1), m = i - j * (QTB + 1);
+            const int idx = t0 - sm.i0c[b][j] - 1 + m;  // pi column
+            const bool ok = j < nc && idx >= 0 && idx < Nt;
+            cp_async4(&sm.raw[b][j][m], pig + (size_t)(c0 + (j < nc ? j : 0)) * Nt + (ok ? idx : 0), ok);
+        }
+        for (int i = tid; i < R * QNC; i += 256) {
+            const int r = i / QNC, j = i - r * QNC;
+            const bool ok = j < nc;
+            cp_async4(&sm.Cc[b][r][j], s.C + ((int64_t)k * R + r) * N + c0 + (ok ? j : 0), ok);
+        }
+    };
+
+    int ri0 = 0;
+    float rw = 0.f;
+    if (tid < QNC) {
+        int a;
+        float w;
+        load_iw(0, a, w);
+        sm.i0c[0][tid] = a;
+        sm.wc[0][tid] = w;
+        load_iw(1, ri0, rw);
+    }
+    __syncthreads();
+    if (nch > 0) issue(0, 0);
+    cp_async_commit();
+    for (int c = 0; c < nch; c++) {
+        const int b = c & 1;
         if (tid < QNC) {
-            i0c[tid] = tid < nc ? s.I0[(int64_t)k * N + c0 + tid] : 0;
-            wc[tid] = tid < nc ? s.W[(int64_t)k * N + c0 + tid] : 0.f;
+            sm.i0c[b ^ 1][tid] = ri0;  // chunk c + 1
+            sm.wc[b ^ 1][tid] = rw;
+            load_iw(c + 2, ri0, rw);
         }
-        for (int i = tid; i < RMAX * QNC; i += 256) {
-            int r = i / QNC, j = i - r * QNC;
-            Cc[r][j] = (r < R && j < nc) ? s.C[((int64_t)k * R + r) * N + c0 + j] : 0.f;
-        }
+        __syncthreads();  // chunk c + 1's window starts are visible; chunk c - 1's buffers are free
+        if (c + 1 < nch) issue(c + 1, b ^ 1);
+        cp_async_commit();
+        cp_async_wait1();  // this thread's copies of chunk c have landed
         __syncthreads();
         int any = 0;
         for (int i = tid; i < QNC * QTB; i += 256) {
-            int j = i / QTB, c = i - j * QTB;
-            float v = 0.f;
-            if (j < nc) {
-                int j0 = t0 + c - i0c[j];
-                const float *pr = pig + (size_t)(c0 + j) * Nt;
-                float a = (j0 >= 0 && j0 < Nt) ? pr[j0] : 0.f;
-                float b = (j0 >= 1 && j0 <= Nt) ? pr[j0 - 1] : 0.f;
-                v = (1.f - wc[j]) * a + wc[j] * b;
-                any |= (j0 >= 0 && j0 <= Nt);
-            }
-            Pc[j][c] = v;
+            const int j = i / QTB, col = i - j * QTB;
+            const float w = sm.wc[b][j];
+            const float a = sm.raw[b][j][col + 1], bb = sm.raw[b][j][col];
+            sm.Pc[j][col] = (1.f - w) * a + w * bb;
+            const int j0 = t0 + col - sm.i0c[b][j];
+            any |= (j0 >= 0 && j0 <= Nt);
         }
         if (!__syncthreads_or(any)) continue;
 #pragma unroll 4
         for (int j = 0; j < QNC; j++) {
-            const float4 p0 = *reinterpret_cast<const float4 *>(&Pc[j][tx * 4]);
-            const float4 p1 = *reinterpret_cast<const float4 *>(&Pc[j][64 + tx * 4]);
+            const float4 p0 = *reinterpret_cast<const float4 *>(&sm.Pc[j][tx * 4]);
+            const float4 p1 = *reinterpret_cast<const float4 *>(&sm.Pc[j][64 + tx * 4]);
             const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
 #pragma unroll
             for (int m = 0; m < 3; m++) {
                 const int r = ry + 16 * m;
-                const float cv = r < RMAX ? Cc[r][j] : 0.f;
+                const float cv = r < RMAX ? sm.Cc[b][r][j] : 0.f;
 #pragma unroll
                 for (int q = 0; q < 8; q++) acc[m][q] = fmaf(cv, pv[q], acc[m][q]);
             }
@@ -741,8 +795,11 @@ cudaError_t ile_launch_grad_q(const PointParams &pp, const float *pig, IleScratc
                               float *part, double *gQ, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     dim3 grid((pp.T_ext + QTB - 1) / QTB, pp.K, nsplit);
-    adj_gq_kernel<<<grid, 256, 0, st>>>(pp, pig, s, N, nsplit, part);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e =
+        cudaFuncSetAttribute(adj_gq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GqSmem));
+    if (e != cudaSuccess) return e;
+    adj_gq_kernel<<<grid, 256, sizeof(GqSmem), st>>>(pp, pig, s, N, nsplit, part);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)pp.K * pp.M * pp.T_ext;
     adj_gq_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(pp.K, pp.M, pp.T_ext, nsplit, part, gQ);

@@ -525,39 +525,44 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int jj = 0; jj < JG; jj++) D[jj] = 0.f;
             float m_run = -INFINITY, s_run = 0.f;
-            while (!jit.done) {
-                const Job j = jit.get();
-                const uint32_t tb = gjob & 1u;
-                if (!warp_wait(&sm.tfull[tb], (gjob / 2) & 1u, flags)) {
-                    failed = true;
-                    break;
+            const int jbeg = g * JG;  // my first bin of a chunk (warp-uniform)
+            // chunk [j0, j0 + Jc) complete: S5 log-sum-exp update (or the full grid)
+            auto finish_chunk = [&](int j0, int Jc) {
+                if constexpr (DM) {
+#pragma unroll
+                    for (int jj = 0; jj < JG; jj++)
+                        if (jbeg + jj < Jc) D[jj] = ile_dmarg_lnF(pp.dm, dq, D[jj]);
                 }
-                fence_after();
-                const int dk = i0d(j.k) - lo(j.k);  // first column of bin 0, relative to the chunk's range
-                const int jbeg = g * JG;             // my first bin of the chunk (warp-uniform)
-                const int shift = jbeg + (j.wbeg - j.wbeg8) - j.w * j.step;
-                const int s0 = dk + shift;           // my first column in the window
-                // my columns s0 .. s0 + 16 lie in the 16-column blocks a0 and a0 + 16 (both < NWIN)
-                const int a0 = s0 & ~15;
-                bool mine;
-                int cmin, cmax;  // the warp's range of blocks
-                if (j.W == 1) {
-                    // one window: every sample reads it; the block range follows from the warp's
-                    // offset range ((x & ~15) is monotone)
-                    mine = jbeg < j.Jc;
-                    const int2 r = sm.dkr[warp][j.k];
-                    cmin = mine ? (r.x + shift) & ~15 : 0x7fffffff;
-                    cmax = mine ? ((r.y + shift) & ~15) + 16 : -1;
-                } else {
-                    const int wsel = min(dk / j.step, j.W - 1);
-                    mine = wsel == j.w && jbeg < j.Jc;
-                    cmin = mine ? a0 : 0x7fffffff;
-                    cmax = mine ? a0 + 16 : -1;
-                    for (int o = 16; o; o >>= 1) {
-                        cmin = min(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
-                        cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+                if (full_grid) {
+                    if (valid) {
+                        const double A_n = DM ? 0.0
+                                              : (double)(aq_s[q4 * 32 + lane] + aq_s[128 + q4 * 32 + lane] +
+                                                         aq_s[256 + q4 * 32 + lane] + aq_s[384 + q4 * 32 + lane]);
+                        const int64_t o = (int64_t)perm[p] * Nt + j0 + jbeg;
+#pragma unroll
+                        for (int jj = 0; jj < JG; jj++)
+                            if (jbeg + jj < Jc) out[o + jj] = (double)D[jj] - A_n;
                     }
+                } else if (jbeg < Jc) {
+                    float mc = -INFINITY;
+#pragma unroll
+                    for (int jj = 0; jj < JG; jj++)
+                        if (jbeg + jj < Jc) mc = fmaxf(mc, D[jj]);
+                    if (mc > m_run) {
+                        s_run *= __expf(m_run - mc);
+                        m_run = mc;
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < JG; jj++)
+                        if (jbeg + jj < Jc) s_run += __expf(D[jj] - m_run);
                 }
+#pragma unroll
+                for (int jj = 0; jj < JG; jj++) D[jj] = 0.f;
+            };
+            // stage my columns s0 .. s0 + 16 of the job in TMEM buffer tb (the warp loads the 16-column
+            // blocks cmin .. cmax; mine: this thread's bins are in the job), then add the lerp
+            auto consume = [&](uint32_t tb, int s0, int cmin, int cmax, bool mine, float w, int Jc) {
+                const int a0 = s0 & ~15;
                 if (cmax >= 0) {
                     const uint32_t taddr = tmem + tb * NWIN + lane_addr;
                     for (int cb = cmin; cb <= cmax; cb += 16) {
@@ -573,10 +578,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 fence_before();
                 mbar_arrive(&sm.tempty[tb]);
                 if (mine) {
-                    const float w = wtd(j.k), omw = 1.f - w;
+                    const float omw = 1.f - w;
                     const float *src = my_row + (s0 & 15);
                     float vprev = src[0];
-                    if (jbeg + JG <= j.Jc) {
+                    if (jbeg + JG <= Jc) {
 #pragma unroll
                         for (int jj = 0; jj < JG; jj++) {
                             const float v = src[jj + 1];
@@ -586,7 +591,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     } else {
 #pragma unroll
                         for (int jj = 0; jj < JG; jj++) {
-                            if (jbeg + jj < j.Jc) {
+                            if (jbeg + jj < Jc) {
                                 const float v = src[jj + 1];
                                 D[jj] = fmaf(omw, vprev, fmaf(w, v, D[jj]));
                                 vprev = v;
@@ -594,40 +599,72 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     }
                 }
-                gjob++;
-                jit.next_from(j);
-                if (j.k == K - 1 && j.w == j.W - 1) {
-                    // chunk complete: S5 log-sum-exp update (or the full grid)
-                    if constexpr (DM) {
+            };
+            // every detector's chunk columns fit one window (the usual case for delay-sorted tiles):
+            // the jobs are (chunk c, detector k), and a thread's offsets and its warp's block range
+            // per detector are the same for every chunk
+            bool single = true;
 #pragma unroll
-                        for (int jj = 0; jj < JG; jj++)
-                            if (jbeg + jj < j.Jc) D[jj] = ile_dmarg_lnF(pp.dm, dq, D[jj]);
-                    }
-                    if (full_grid) {
-                        if (valid) {
-                            const double A_n = DM ? 0.0
-                                                        : (double)(aq_s[q4 * 32 + lane] + aq_s[128 + q4 * 32 + lane] +
-                                                                   aq_s[256 + q4 * 32 + lane] + aq_s[384 + q4 * 32 + lane]);
-                            const int64_t o = (int64_t)perm[p] * Nt + j.j0 + jbeg;
+            for (int k = 0; k < ILE_MAX_DET; k++)
+                if (k < K) single = single && hi(k) - lo(k) + JW + 1 <= nwcol;
+            if (single) {
+                for (int j0 = 0; j0 < Nt && !failed; j0 += JW) {
+                    const int Jc = min(JW, Nt - j0);
+                    const bool mine = jbeg < Jc;
 #pragma unroll
-                            for (int jj = 0; jj < JG; jj++)
-                                if (jbeg + jj < j.Jc) out[o + jj] = (double)D[jj] - A_n;
+                    for (int k = 0; k < ILE_MAX_DET; k++) {
+                        if (k >= K) break;
+                        const uint32_t tb = gjob & 1u;
+                        if (!warp_wait(&sm.tfull[tb], (gjob / 2) & 1u, flags)) {
+                            failed = true;
+                            break;
                         }
-                    } else if (jbeg < j.Jc) {
-                        float mc = -INFINITY;
-#pragma unroll
-                        for (int jj = 0; jj < JG; jj++)
-                            if (jbeg + jj < j.Jc) mc = fmaxf(mc, D[jj]);
-                        if (mc > m_run) {
-                            s_run *= __expf(m_run - mc);
-                            m_run = mc;
-                        }
-#pragma unroll
-                        for (int jj = 0; jj < JG; jj++)
-                            if (jbeg + jj < j.Jc) s_run += __expf(D[jj] - m_run);
+                        fence_after();
+                        const int shift = jbeg + (lo(k) & 7);  // window start lo_k + j0 rounded down to 8
+                        const int2 r = sm.dkr[warp][k];
+                        consume(tb, i0d(k) - lo(k) + shift, mine ? (r.x + shift) & ~15 : 0x7fffffff,
+                                mine ? ((r.y + shift) & ~15) + 16 : -1, mine, wtd(k), Jc);
+                        gjob++;
                     }
-#pragma unroll
-                    for (int jj = 0; jj < JG; jj++) D[jj] = 0.f;
+                    if (failed) break;
+                    finish_chunk(j0, Jc);
+                }
+            } else {
+                while (!jit.done) {
+                    const Job j = jit.get();
+                    const uint32_t tb = gjob & 1u;
+                    if (!warp_wait(&sm.tfull[tb], (gjob / 2) & 1u, flags)) {
+                        failed = true;
+                        break;
+                    }
+                    fence_after();
+                    const int dk = i0d(j.k) - lo(j.k);  // first column of bin 0, relative to the chunk's range
+                    const int shift = jbeg + (j.wbeg - j.wbeg8) - j.w * j.step;
+                    const int s0 = dk + shift;           // my first column in the window
+                    const int a0 = s0 & ~15;
+                    bool mine;
+                    int cmin, cmax;  // the warp's range of blocks
+                    if (j.W == 1) {
+                        // one window: every sample reads it; the block range follows from the warp's
+                        // offset range ((x & ~15) is monotone)
+                        mine = jbeg < j.Jc;
+                        const int2 r = sm.dkr[warp][j.k];
+                        cmin = mine ? (r.x + shift) & ~15 : 0x7fffffff;
+                        cmax = mine ? ((r.y + shift) & ~15) + 16 : -1;
+                    } else {
+                        const int wsel = min(dk / j.step, j.W - 1);
+                        mine = wsel == j.w && jbeg < j.Jc;
+                        cmin = mine ? a0 : 0x7fffffff;
+                        cmax = mine ? a0 + 16 : -1;
+                        for (int o = 16; o; o >>= 1) {
+                            cmin = min(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+                            cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+                        }
+                    }
+                    consume(tb, s0, cmin, cmax, mine, wtd(j.k), j.Jc);
+                    gjob++;
+                    jit.next_from(j);
+                    if (j.k == K - 1 && j.w == j.W - 1) finish_chunk(j.j0, j.Jc);
                 }
             }
             if (failed) break;

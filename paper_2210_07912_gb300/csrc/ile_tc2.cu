@@ -231,20 +231,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int K = pt.pp.K, Nt = pt.pp.Nt, KC = pt.KP / 8, TP = pt.TP;
                 const uint4 *Qhi = reinterpret_cast<const uint4 *>(pt.Qhi);
                 const uint4 *Qlo = reinterpret_cast<const uint4 *>(pt.Qlo);
-                if (!wait1(&sm.aready, tiles_done & 1u, flags)) {
-                    failed = true;
-                    break;
-                }
-                Det4 lo, hi;
-                tile_range(sm.wlo, sm.whi, K, lo, hi);
-                for (JobIter cit(Nt, K, nwcol, TP - ILE_QCOLS, lo, hi); !cit.done && !failed; cit.next(), gcopy++) {
+                auto copy_job = [&](const Job &j) {
                     const uint32_t bb = gcopy % NB;
                     // the slot is free once the MMAs of job gcopy - NB have completed
                     if (gcopy >= (uint32_t)NB && !wait1(&sm.bempty[bb], ((gcopy / NB) - 1) & 1u, flags)) {
                         failed = true;
-                        break;
+                        return;
                     }
-                    const Job j = cit.get();
                     // one contiguous block per hi/lo: [nwr/8 groups][KC][8 columns] x 16 bytes
                     const uint32_t bytes = (uint32_t)j.nwr * KC * 16u;
                     mbar_arrive_expect_tx(&sm.bfull[bb], 2u * bytes);
@@ -252,7 +245,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     uint4 *slot = B + (size_t)bb * 2 * LKC * NWIN;
                     bulk_g2s(slot, Qhi + src, bytes, &sm.bfull[bb]);
                     bulk_g2s(slot + (size_t)KC * NWIN, Qlo + src, bytes, &sm.bfull[bb]);
+                };
+                // the quadratic-term jobs come first and need no column ranges: their operands are
+                // copied before the tile's A operand and ranges are ready
+                const Det4 none{0, 0, 0, 0};
+                JobIter cit(Nt, K, nwcol, TP - ILE_QCOLS, none, none);
+                for (int q = 0; q < K && !failed; q++, cit.next(), gcopy++) copy_job(cit.get());
+                if (failed) break;
+                if (!wait1(&sm.aready, tiles_done & 1u, flags)) {
+                    failed = true;
+                    break;
                 }
+                tile_range(sm.wlo, sm.whi, K, cit.lo, cit.hi);
+                for (; !cit.done && !failed; cit.next(), gcopy++) copy_job(cit.get());
             }
             if (failed) atomicOr(flags, ILE_FLAG_TIMEOUT);
         }

@@ -53,7 +53,7 @@ constexpr uint32_t TMEM_COLS = 2 * NWIN;
 constexpr int NBMAX = 4;                   // B ring depth upper bound
 constexpr int SLEEPS = 200000;             // bounded sleeping waits: SLEEPS x SLEEP_NS at most
 constexpr uint32_t SLEEP_NS = 10000;
-constexpr int RSTRIDE = 33;                // per-thread row: 32 staged columns + 1 (odd stride: conflict-free)
+constexpr int RSTRIDE = 34;                // per-thread row: 32 staged columns + 2 (8-byte stores, half-warp conflict-free)
 
 struct Sm {
     uint64_t bfull[NBMAX], bempty[NBMAX], tfull[2], tempty[2], yready, aready, s4done, tdone, sready;
@@ -574,9 +574,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         uint32_t r[16];
                         tmem_ld16(taddr + (uint32_t)cb, r);
                         if (mine && (cb == a0 || cb == a0 + 16)) {
-                            float *dst = my_row + (cb - a0);
+                            float2 *dst = reinterpret_cast<float2 *>(my_row + (cb - a0));
 #pragma unroll
-                            for (int qq = 0; qq < 16; qq++) dst[qq] = __uint_as_float(r[qq]);
+                            for (int qq = 0; qq < 8; qq++)
+                                dst[qq] = make_float2(__uint_as_float(r[2 * qq]), __uint_as_float(r[2 * qq + 1]));
                         }
                     }
                 }

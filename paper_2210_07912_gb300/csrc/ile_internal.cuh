@@ -224,6 +224,68 @@ __device__ __forceinline__ void ile_sylm(const ModeTab &md, const float cpow[9],
     yi = amp * s;
 }
 
+// The same harmonics with every power at a compile-time index (registers, no local memory) and
+// e^{i m phi} from powers of e^{i phi}: the exponents of the terms of d^l_{m,2} that the host
+// builder (wigner_terms) lists, in its order, for the 21 modes with 2 <= l <= 4.
+struct WignerQ {
+    int n;
+    int q[4];  // power of s = sin(iota/2) of each term; the power of c is 2l - q
+};
+__host__ __device__ constexpr WignerQ ile_wigner_q(int l, int m) {
+    WignerQ w{0, {0, 0, 0, 0}};
+    for (int sp = 0; sp <= 2 * l; sp++) {
+        const int twok = sp + 2 - m;
+        if (twok < 0 || (twok & 1)) continue;
+        const int k = twok / 2;
+        if (l + 2 - k < 0 || l - m - k < 0 || k + m - 2 < 0) continue;
+        if (w.n < 4) w.q[w.n++] = sp;
+    }
+    return w;
+}
+
+template <int L, int M>
+__device__ __forceinline__ void ile_sylm_lm(const ModeTab &md, const float (&cpow)[9], const float (&spow)[9],
+                                            const float (&er)[5], const float (&ei)[5], float &yr, float &yi) {
+    constexpr WignerQ w = ile_wigner_q(L, M);
+    float amp = 0.f;
+#pragma unroll
+    for (int t = 0; t < w.n; t++) amp += md.t[t].coef * cpow[2 * L - w.q[t]] * spow[w.q[t]];
+    amp *= md.norm;
+    constexpr int AM = M < 0 ? -M : M;
+    yr = amp * er[AM];
+    yi = M < 0 ? -amp * ei[AM] : amp * ei[AM];
+}
+
+// e^{i m phi}, m = 0..4
+__device__ __forceinline__ void ile_phase_powers(float phi, float (&er)[5], float (&ei)[5]) {
+    er[0] = 1.f;
+    ei[0] = 0.f;
+    sincosf(phi, &ei[1], &er[1]);
+    er[2] = er[1] * er[1] - ei[1] * ei[1];
+    ei[2] = 2.f * er[1] * ei[1];
+    er[3] = er[2] * er[1] - ei[2] * ei[1];
+    ei[3] = er[2] * ei[1] + ei[2] * er[1];
+    er[4] = er[2] * er[2] - ei[2] * ei[2];
+    ei[4] = 2.f * er[2] * ei[2];
+}
+
+__device__ __forceinline__ void ile_sylm_fast(const ModeTab &md, const float (&cpow)[9], const float (&spow)[9],
+                                              const float (&er)[5], const float (&ei)[5], float &yr, float &yi) {
+#define ILE_LM(L, M)                                            \
+    case (L - 2) * 9 + M + 4:                                   \
+        ile_sylm_lm<L, M>(md, cpow, spow, er, ei, yr, yi);      \
+        return;
+    switch ((md.l - 2) * 9 + md.m + 4) {
+        ILE_LM(2, -2) ILE_LM(2, -1) ILE_LM(2, 0) ILE_LM(2, 1) ILE_LM(2, 2)
+        ILE_LM(3, -3) ILE_LM(3, -2) ILE_LM(3, -1) ILE_LM(3, 0) ILE_LM(3, 1) ILE_LM(3, 2) ILE_LM(3, 3)
+        ILE_LM(4, -4) ILE_LM(4, -3) ILE_LM(4, -2) ILE_LM(4, -1) ILE_LM(4, 0) ILE_LM(4, 1) ILE_LM(4, 2)
+        ILE_LM(4, 3) ILE_LM(4, 4)
+        default:
+            yr = yi = 0.f;  // 2 <= l <= 4 is checked when the point is set
+    }
+#undef ILE_LM
+}
+
 __device__ __forceinline__ void ile_half_angle_powers(float iota, float cpow[9], float spow[9]) {
     float s, c;
     sincosf(0.5f * iota, &s, &c);

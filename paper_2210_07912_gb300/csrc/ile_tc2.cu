@@ -399,12 +399,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // reuses the rows area: every thread has passed the previous tile's tdone)
             float2 *ys = reinterpret_cast<float2 *>(rows);  // [M][TILE]
             {
-                float cpow[9], spow[9];
+                float cpow[9], spow[9], er[5], ei[5];
                 ile_half_angle_powers((float)th[3], cpow, spow);
+                ile_phase_powers((float)th[4], er, ei);
 #pragma unroll 1
                 for (int a = g; a < M; a += NGRP) {
                     float yr, yi;
-                    ile_sylm(pp.mode[a], cpow, spow, (float)th[4], yr, yi);
+                    ile_sylm_fast(pp.mode[a], cpow, spow, er, ei, yr, yi);
                     ys[a * TILE + row] = make_float2(yr, yi);
                 }
             }

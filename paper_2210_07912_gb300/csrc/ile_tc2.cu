@@ -19,7 +19,7 @@
 //   window of <= 120 columns) bulk-copy the Q window (hi and lo rows, one contiguous block each)
 //   into a ring of NB shared buffers as soon as a slot is free;
 //   warp 16, lane 0 (MMA warp): issue 3 x KP/16 tcgen05.mma (hi*hi + hi*lo + lo*hi, kind::f16,
-//   FP32 accumulation) per job into one of two TMEM accumulator buffers;
+//   FP32 accumulation) per job into one of three TMEM accumulator buffers;
 //   warp 18 (prefetch warp): gathers the next tile's sample parameters through the sort
 //   permutation into shared memory while the current tile is in flight.
 //
@@ -49,14 +49,15 @@ constexpr int JG = JW / NGRP;              // bins per thread per chunk
 constexpr int NWIN = 128;                  // columns per TMEM accumulator buffer (= max MMA N here)
 constexpr int NWCOL = 120;                 // default window columns (+ up to 7 for 8-column alignment <= NWIN)
 constexpr int NWCOL_MIN = JW + 2;          // a window must hold one chunk's columns plus the lerp partner
-constexpr uint32_t TMEM_COLS = 2 * NWIN;
+constexpr int NTB = 3;                     // TMEM accumulator buffers (jobs in flight between MMA and math warps)
+constexpr uint32_t TMEM_COLS = 512;        // power of two >= NTB * NWIN
 constexpr int NBMAX = 4;                   // B ring depth upper bound
 constexpr int SLEEPS = 200000;             // bounded sleeping waits: SLEEPS x SLEEP_NS at most
 constexpr uint32_t SLEEP_NS = 10000;
 constexpr int RSTRIDE = 34;                // per-thread row: 32 staged columns + 2 (8-byte stores, half-warp conflict-free)
 
 struct Sm {
-    uint64_t bfull[NBMAX], bempty[NBMAX], tfull[2], tempty[2], yready, aready, s4done, tdone, sready;
+    uint64_t bfull[NBMAX], bempty[NBMAX], tfull[NTB], tempty[NTB], yready, aready, s4done, tdone, sready;
     uint32_t tmem_base;
     int wlo[4][ILE_MAX_DET], whi[4][ILE_MAX_DET];
     int2 dkr[NMATH / 32][ILE_MAX_DET];  // per math warp and detector: (min, max) of i0 - tile lo
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&sm.bfull[b], 1);
             mbar_init(&sm.bempty[b], 1);
         }
-        for (int b = 0; b < 2; b++) {
+        for (int b = 0; b < NTB; b++) {
             mbar_init(&sm.tfull[b], 1);
             mbar_init(&sm.tempty[b], NMATH);
         }
@@ -305,9 +306,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 fence_after();
                 for (JobIter mit(Nt, K, nwcol, TQ0, lo, hi); !mit.done && !failed; mit.next(), gjob++) {
                     const Job j = mit.get();
-                    const uint32_t bb = gjob % NB, tb = gjob & 1u;
+                    const uint32_t bb = gjob % NB, tb = gjob % NTB;
                     if (!wait1(&sm.bfull[bb], (gjob / NB) & 1u, flags) ||
-                        (gjob >= 2 && !wait1(&sm.tempty[tb], ((gjob / 2) - 1) & 1u, flags))) {
+                        (gjob >= NTB && !wait1(&sm.tempty[tb], ((gjob / NTB) - 1) & 1u, flags))) {
                         failed = true;
                         break;
                     }
@@ -336,7 +337,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             if (failed) atomicOr(flags, ILE_FLAG_TIMEOUT);
             // no MMA may still be writing TMEM when it is released (bounded)
-            if (gjob > 0) mbar_wait_sleep(&sm.tfull[(gjob - 1) & 1u], ((gjob - 1) / 2) & 1u, flags, 0u, SLEEPS, SLEEP_NS);
+            if (gjob > 0)
+                mbar_wait_sleep(&sm.tfull[(gjob - 1) % NTB], ((gjob - 1) / NTB) & 1u, flags, 0u, SLEEPS, SLEEP_NS);
         }
         __syncwarp();
     } else {
@@ -484,8 +486,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // of 32; thread g takes block g and forms its part of c^H z + Re(c^T w)
             float aq = 0.f;
             for (int kq = 0; kq < K; kq++) {
-                const uint32_t tb = gjob & 1u;
-                if (!warp_wait(&sm.tfull[tb], (gjob / 2) & 1u, flags)) {
+                const uint32_t tb = gjob % NTB;
+                if (!warp_wait(&sm.tfull[tb], (gjob / NTB) & 1u, flags)) {
                     failed = true;
                     break;
                 }
@@ -621,8 +623,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                     for (int k = 0; k < ILE_MAX_DET; k++) {
                         if (k >= K) break;
-                        const uint32_t tb = gjob & 1u;
-                        if (!warp_wait(&sm.tfull[tb], (gjob / 2) & 1u, flags)) {
+                        const uint32_t tb = gjob % NTB;
+                        if (!warp_wait(&sm.tfull[tb], (gjob / NTB) & 1u, flags)) {
                             failed = true;
                             break;
                         }
@@ -639,8 +641,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             } else {
                 while (!jit.done) {
                     const Job j = jit.get();
-                    const uint32_t tb = gjob & 1u;
-                    if (!warp_wait(&sm.tfull[tb], (gjob / 2) & 1u, flags)) {
+                    const uint32_t tb = gjob % NTB;
+                    if (!warp_wait(&sm.tfull[tb], (gjob / NTB) & 1u, flags)) {
                         failed = true;
                         break;
                     }

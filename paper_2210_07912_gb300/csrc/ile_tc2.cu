@@ -4,17 +4,19 @@
 //
 //   16 math warps: warp w serves TMEM lane quadrant q = w % 4 (samples 32q .. 32q+31 of the
 //   tile) and bin group g = w / 4, so each sample has four threads (g = 0..3):
-//     * S1/S2: every thread of a sample forms the geometry (F_k, window start i0_k + w_k) and
-//       the harmonics Y_lm; thread g < K writes detector g's coefficients
-//       c_glm = (D_ref/D) F_g Y_lm, split hi/lo (BF16), as the MMA A operand in shared memory
-//       (K index 2a + {Re, Im} of mode a, as in the split Q rows);
-//     * S4: A(n) = 1/4 (D_ref/D)^2 sum_k [|F_k|^2 y^H U_k y + Re(F_k^2 y^T V_k y)] on CUDA
-//       cores, the upper-triangle mode pairs shared round-robin among the four threads;
-//     * S3/S5 epilogue for every job: load the sample's accumulator columns from TMEM, keep the
-//       17 it needs (bins 16g .. 16g+15 and the lerp partner) in a thread-private strip of shared
-//       memory, and add (1 - w) G(i0 + j) + w G(i0 + j + 1) into its window accumulator D[16]
-//       (registers); after the last detector of a chunk, fold D into a running log-sum-exp.
-//       At the end of a tile the four threads' (max, sum) pairs are merged in FP64.
+//     * S1/S2: every thread of a sample forms the geometry (F_k, window start i0_k + w_k) and a
+//       quarter of the harmonics Y_lm (compile-time powers per (l, m)); the four threads share
+//       the K x KC chunks of the sample's coefficients c_klm = (D_ref/D) F_k Y_lm, split hi/lo
+//       (BF16), written as the MMA A operand in shared memory (K index 2a + {Re, Im} of mode a,
+//       as in the split Q rows);
+//     * S4: per detector, one MMA job against the real form of U_k and V_k leaves U_k c and
+//       V_k c in TMEM; thread g dots its 32-column block with the coefficients, and the four
+//       shares give A(n) = 1/4 sum_k [c_k^H U_k c_k + Re(c_k^T V_k c_k)];
+//     * S3/S5 epilogue for every data job: load the sample's accumulator columns from TMEM, keep
+//       the 17 it needs (bins 16g .. 16g+15 and the lerp partner) in a thread-private strip of
+//       shared memory, and add (1 - w) G(i0 + j) + w G(i0 + j + 1) into its window accumulator
+//       D[16] (registers); after the last detector of a chunk, fold D into a running
+//       log-sum-exp.  At the end of a tile the four threads' (max, sum) pairs are merged in FP64.
 //   warp 17, lane 0 (copy warp): for every job (chunk of 64 window bins x detector x column
 //   window of <= 120 columns) bulk-copy the Q window (hi and lo rows, one contiguous block each)
 //   into a ring of NB shared buffers as soon as a slot is free;
@@ -26,9 +28,11 @@
 // Hand-offs are mbarriers: bfull/bempty (B ring), tfull/tempty (TMEM buffers), aready (A operand
 // and the tile's column ranges written; waited on by all roles), tdone (per-thread log-sum-exp
 // partials written), sready (sample parameters staged; the prefetch warp refills the stage once
-// yready shows that every math thread has read it).  Jobs are enumerated identically by all roles.  A tile whose column spread
-// does not fit one window is covered by overlapping windows of 128 columns, each sample reading
-// the single window that holds all the columns it needs.  Every wait is bounded; on expiry the
+// yready shows that every math thread has read it).  Jobs are enumerated identically by all
+// roles: the quadratic-term jobs (copied before the tile is ready), then (chunk, detector,
+// window).  A tile whose column spread does not fit one window is covered by overlapping windows
+// of 128 columns, each sample reading the single window that holds all the columns it needs;
+// when every detector fits one window the math warps take a shorter job loop.  Every wait is bounded; on expiry the
 // kernel raises ILE_FLAG_TIMEOUT (all CTAs then stop waiting), releases its TMEM and returns.
 #include "ile_internal.cuh"
 #include "ile_tcgen05.cuh"
@@ -416,14 +420,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 failed = true;
                 break;
             }
-            if (g < K) {
-                // A operand of detector g: operand index r = 2a + {0: Re, 1: Im}
-                const float fr = scale * (g == 0 ? Fr[0] : g == 1 ? Fr[1] : g == 2 ? Fr[2] : Fr[3]);
-                const float fi = scale * (g == 0 ? Fi[0] : g == 1 ? Fi[1] : g == 2 ? Fi[2] : Fi[3]);
-                uint4 *Ah = A + (size_t)(g * 2) * KC * TILE + row;
-                uint4 *Al = A + (size_t)(g * 2 + 1) * KC * TILE + row;
+            {
+                // A operand: the K x KC 16-byte chunks of this sample's row (detector k, operand index
+                // r = 2a + {0: Re, 1: Im}) are shared round-robin among its four threads
+                int k = 0, kc = g;
+                while (kc >= KC) {
+                    kc -= KC;
+                    k++;
+                }
 #pragma unroll 1
-                for (int kc = 0; kc < KC; kc++) {
+                for (int t = g; t < K * KC; t += NGRP) {
+                    const float fr = scale * (k == 0 ? Fr[0] : k == 1 ? Fr[1] : k == 2 ? Fr[2] : Fr[3]);
+                    const float fi = scale * (k == 0 ? Fi[0] : k == 1 ? Fi[1] : k == 2 ? Fi[2] : Fi[3]);
                     float cv[8];
 #pragma unroll
                     for (int e = 0; e < 8; e += 2) {
@@ -434,8 +442,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                     uint4 h, l;
                     pack_chunk<true>(cv, h, l);
-                    Ah[kc * TILE] = h;
-                    Al[kc * TILE] = l;
+                    A[((size_t)(k * 2) * KC + kc) * TILE + row] = h;
+                    A[((size_t)(k * 2 + 1) * KC + kc) * TILE + row] = l;
+                    kc += NGRP;
+                    while (kc >= KC) {
+                        kc -= KC;
+                        k++;
+                    }
                 }
             }
             // ---- tile column range per detector (invalid rows repeat row 0's sample)

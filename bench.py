@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "extrinsic lnL samples/s on 1 GB300, batched split-prec vs plain, |ΔlnL|≤1e-3"
 UNIT = "samples/s"
-CONFIG = 1  # 3 detectors, 21 modes, N_t = 512, 2^20 samples
+WORKLOAD = "hlv_m21_nt512"  # 3 detectors, 21 modes, N_t = 512, 2^20 samples (synthetic.FULL)
 SEED_ADAPT = 2210079121  # Philox key of the benchmarked sampler
 
 
@@ -117,7 +117,7 @@ def oracle_step(point, N, it, seed=SEED_ADAPT, nthreads=0):
 def cpu_sample_size(point, seconds, cores):
     from paper_2210_07912_gb300 import synthetic as S
     import oracle
-    calib = S.config_samples(CONFIG, 512)
+    calib = S.workload_samples(WORKLOAD, 512)
     t = time.perf_counter()
     oracle.lnL_t(point, calib, cores)
     per = (time.perf_counter() - t) / 512
@@ -140,7 +140,7 @@ def run_reference(args, rank, world):
     import oracle
     from paper_2210_07912_gb300 import synthetic as S
     oracle.build()
-    point = S.make_point(S.SEED_BASE + CONFIG, 3, 21, 512, spectrum="decay")
+    point = S.workload_point(WORKLOAD)
     cores = os.cpu_count() or 1
     n_step = cpu_sample_size(point, 1.5, cores)
     for w in range(args.warmup):
@@ -266,9 +266,9 @@ def adjoint_bench(ile, S, local, stream, flush, steps=10):
     """Gradient of ln L_marg-style weighted sums: ile_eval_grad over 2^18 samples of the
     3-detector, 21-mode, 512-bin point, all outputs (theta, Q, U, V), FP32 with FP64 sums."""
     import torch
-    point = S.config_point(4)
-    N = S.CONFIGS[4]["n_samples"]
-    th = torch.tensor(S.config_samples(4), device="cuda")
+    point = S.workload_point(S.GRAD)
+    N = S.WORKLOADS[S.GRAD]["n_samples"]
+    th = torch.tensor(S.workload_samples(S.GRAD), device="cuda")
     g = torch.tensor(np.random.default_rng(4).normal(size=N), device="cuda")
     K, M, T = point.Q.shape
     gs = torch.empty_like(th)
@@ -336,9 +336,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    N = args.n_samples or S.CONFIGS[CONFIG]["n_samples"]
+    N = args.n_samples or S.WORKLOADS[WORKLOAD]["n_samples"]
     # replicas: every rank integrates its own intrinsic point
-    point = S.make_point(S.SEED_BASE + CONFIG + 1000 * rank, 3, 21, 512, spectrum="decay")
+    c = S.WORKLOADS[WORKLOAD]
+    point = S.make_point(S.SEED_BASE + c["seed"] + 1000 * rank, c["n_det"], c["n_modes"], c["n_window"],
+                         spectrum=c["spectrum"])
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     cfg = ile.make_adapt_cfg(seed=SEED_ADAPT + rank, n_per_iter=N, adapt_mask=0b11, point_id=rank)

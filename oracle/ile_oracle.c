@@ -27,7 +27,7 @@
  *   - gradient of lnL_t (orc_lnL_t_grad): the chain rule through the same steps; the paper
  *     states no derivative, so this is the exact derivative of the function above (R21).
  *
- * Readings of passages that are silent, garbled or ambiguous (each is listed in the design doc):
+ * Readings of passages that are silent, garbled or ambiguous:
  *   R1 ln L = Re<h|d> - <h|h>/2 (the first line of Eq. (eq:loglikelihood) is garbled; the
  *      data-only constant is dropped).
  *   R2 the data term carries Re and D_ref/D: h_k = Re[F_k sum_lm Y_lm h_lm] (D_ref/D).

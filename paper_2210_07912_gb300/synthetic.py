@@ -204,24 +204,27 @@ def prior_samples(rng, N: int, fs: float = FS, tc_max: float | None = None):
     return np.stack([ra, dec, psi, iota, phi, dist, tc])
 
 
-# Workload configurations (sizes of the paper's production ILE runs: 3 detectors, 4096 Hz,
-# modes up to l = 4).  configs 0-2 are single points; 3 is the mixed batch; 4 the adjoint.
-CONFIGS = {
-    0: dict(n_det=2, n_modes=2, n_window=256, n_samples=1 << 14, spectrum="random"),
-    1: dict(n_det=3, n_modes=21, n_window=512, n_samples=1 << 20, spectrum="decay"),
-    2: dict(n_det=3, n_modes=21, n_window=512, n_samples=1 << 20, spectrum="decay"),
-    4: dict(n_det=3, n_modes=21, n_window=512, n_samples=1 << 18, spectrum="decay"),
+# Synthetic workloads, named by their shape (the sizes of the paper's production ILE runs: 3
+# detectors at 4096 Hz, modes up to l = 4; plus a small two-detector case the oracle evaluates
+# in full).  "seed" offsets SEED_BASE for the point and its samples.
+SMALL = "hl_m2_nt256"      # H1, L1; modes (2, +-2); N_t = 256; 2^14 samples
+FULL = "hlv_m21_nt512"     # H1, L1, V1; 21 modes; N_t = 512; 2^20 samples
+GRAD = "hlv_m21_nt512_g"   # the same shape with 2^18 samples, for the adjoint
+WORKLOADS = {
+    SMALL: dict(n_det=2, n_modes=2, n_window=256, n_samples=1 << 14, spectrum="random", seed=0),
+    FULL: dict(n_det=3, n_modes=21, n_window=512, n_samples=1 << 20, spectrum="decay", seed=1),
+    GRAD: dict(n_det=3, n_modes=21, n_window=512, n_samples=1 << 18, spectrum="decay", seed=4),
 }
 
 
-def config_point(cfg: int, **kw) -> Point:
-    c = CONFIGS[cfg]
-    return make_point(SEED_BASE + cfg, c["n_det"], c["n_modes"], c["n_window"], spectrum=c["spectrum"], **kw)
+def workload_point(name: str, **kw) -> Point:
+    c = WORKLOADS[name]
+    return make_point(SEED_BASE + c["seed"], c["n_det"], c["n_modes"], c["n_window"], spectrum=c["spectrum"], **kw)
 
 
-def config_samples(cfg: int, N: int | None = None):
-    c = CONFIGS[cfg]
-    rng = np.random.default_rng([SEED_BASE + cfg, 1])
+def workload_samples(name: str, N: int | None = None):
+    c = WORKLOADS[name]
+    rng = np.random.default_rng([SEED_BASE + c["seed"], 1])
     return prior_samples(rng, c["n_samples"] if N is None else N)
 
 

@@ -32,7 +32,7 @@ def _random_tables(orc, seed):
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 def test_sampler_bits_and_values_match_oracle(ile, orc, prec):
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     ctx = ile.Context(0, None, prec)
     ctx.set_data(point)
     lo, hi = _ranges(ile)
@@ -60,7 +60,7 @@ def test_sampler_bits_and_values_match_oracle(ile, orc, prec):
 
 
 def test_histograms_and_tables_match_oracle(ile, orc):
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     ctx = ile.Context(0, None, "fp32")
     ctx.set_data(point)
     mask = 0b0101011
@@ -87,7 +87,7 @@ def test_histograms_and_tables_match_oracle(ile, orc):
 def test_first_iteration_matches_independent_oracle_run(ile, orc, prec):
     """Iteration 0 (uniform tables): the oracle draws the same samples itself (same Philox words)
     and evaluates them in FP64; ln L estimates agree within 1e-4."""
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     ctx = ile.Context(0, None, prec)
     ctx.set_data(point)
     lo, hi = _ranges(ile)
@@ -105,7 +105,7 @@ def test_adaptive_run_matches_oracle_run(ile, orc):
     weights that differ at the 1e-6 level, so the sample sets can differ in a few samples per
     iteration; the pooled estimates must agree within their Monte Carlo errors, and in practice
     agree far closer."""
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     ctx = ile.Context(0, None, "fp32")
     ctx.set_data(point)
     lo, hi = _ranges(ile)
@@ -122,7 +122,7 @@ def test_adaptive_run_matches_oracle_run(ile, orc):
 
 
 def test_resume_is_bit_reproducible(ile):
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     lo, hi = _ranges(ile)
     cfg = ile.make_adapt_cfg(seed=5, n_per_iter=4096, adapt_mask=0b1100011, point_id=2)
     a = ile.Context(0, None, "bf16x3")
@@ -146,7 +146,7 @@ def test_resume_is_bit_reproducible(ile):
 
 
 def test_adapt_argument_errors(ile):
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     ctx = ile.Context(0)
     cfg = ile.make_adapt_cfg(seed=1, n_per_iter=100)
     with pytest.raises(ile.IleError) as e:
@@ -167,7 +167,7 @@ def test_adapt_argument_errors(ile):
 def test_rotated_sky_sampler_matches_oracle(ile, orc):
     """Rotated network-frame sky variables (pole along the H1-L1 baseline): identical bins, the
     (ra, dec) the frame maps them to within FP32 rounding, ln p - ln p_s unchanged."""
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     ctx = ile.Context(0, None, "bf16x3")
     ctx.set_data(point)
     lo, hi = _ranges(ile)
@@ -193,7 +193,7 @@ def test_rotated_sky_sampler_matches_oracle(ile, orc):
 
 
 def test_rotated_sky_adaptive_run_matches_oracle_and_batch(ile, orc):
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     lo, hi = _ranges(ile)
     _, pos = S.detector_arrays(2)
     pole = pos[1] - pos[0]

@@ -45,9 +45,9 @@ def _loud_point(K=3, M=5, Nt=128, gain=25.0):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_dmarg_matches_oracle(ile, orc, prec):
-    for point, th in ((S.config_point(0), S.config_samples(0, 300)),
-                      (S.make_point(S.SEED_BASE + 81, 3, 21, 512, spectrum="decay"), S.config_samples(1, 200)),
-                      (_loud_point(), S.config_samples(0, 200))):
+    for point, th in ((S.workload_point(S.SMALL), S.workload_samples(S.SMALL, 300)),
+                      (S.make_point(S.SEED_BASE + 81, 3, 21, 512, spectrum="decay"), S.workload_samples(S.FULL, 200)),
+                      (_loud_point(), S.workload_samples(S.SMALL, 200))):
         got = _ctx(ile, point, prec).eval(th)
         ref = orc.lnL_dmarg(point, th, D_MIN, D_MAX)
         err = np.abs(got - ref).max()
@@ -59,8 +59,8 @@ def test_dmarg_per_bin_table_accuracy(ile, orc):
     exercises the tables over the (a, b) range of a normal point, a loud one and a network 30
     times louder (b up to ~350).  Bar: 1e-3 plus the FP32 precision of the inputs (the data term
     a_j is an FP32 sum, ~2e-6 relative; it only matters once |ln F| >> 100)."""
-    for point in (S.config_point(0), _loud_point(), _scaled(S.config_point(0), 30.0)):
-        th = S.config_samples(0, 40)
+    for point in (S.workload_point(S.SMALL), _loud_point(), _scaled(S.workload_point(S.SMALL), 30.0)):
+        th = S.workload_samples(S.SMALL, 40)
         grid = _ctx(ile, point, "fp32").eval(th, grid=True)
         for n in range(th.shape[1]):
             t = th[:, n].copy()
@@ -74,7 +74,7 @@ def test_dmarg_per_bin_table_accuracy(ile, orc):
 def test_dmarg_tables_over_the_ab_plane(ile, orc):
     """ln F from the tables (ile_dmarg_eval) against the oracle's quadrature on a log-spaced grid
     of b in [1e-5, 1e6] and a in a band around the peak position, both tables and their seam."""
-    c = _ctx(ile, S.config_point(0), "fp32")
+    c = _ctx(ile, S.workload_point(S.SMALL), "fp32")
     rng = np.random.default_rng(90)
     bs = 10.0 ** rng.uniform(-5, 6, 400)
     us = rng.uniform(-0.3, 1.5, 400)  # peak position a / 2b: inside, below and above [0.1, 1]
@@ -87,8 +87,8 @@ def test_dmarg_tables_over_the_ab_plane(ile, orc):
 
 
 def test_dmarg_integrate_and_adaptive_run(ile, orc):
-    point = S.config_point(0)
-    th = S.config_samples(0, 4096)
+    point = S.workload_point(S.SMALL)
+    th = S.workload_samples(S.SMALL, 4096)
     c = _ctx(ile, point, "bf16x3")
     res = c.integrate(th)
     ref = orc.mc_stats(orc.lnL_dmarg(point, th, D_MIN, D_MAX))
@@ -102,8 +102,8 @@ def test_dmarg_integrate_and_adaptive_run(ile, orc):
 
 
 def test_dmarg_switching_and_errors(ile, orc):
-    point = S.config_point(0)
-    th = S.config_samples(0, 64)
+    point = S.workload_point(S.SMALL)
+    th = S.workload_samples(S.SMALL, 64)
     c = ile.Context(0, None, "fp32")
     with pytest.raises(ile.IleError) as e:
         c.set_distance_marginalization(True, D_MIN, D_MAX)

@@ -35,8 +35,8 @@ def _ctx(ile, point, prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_single_sample(ile, orc, prec):
-    point = S.config_point(1)
-    th = S.config_samples(1, 1)
+    point = S.workload_point(S.FULL)
+    th = S.workload_samples(S.FULL, 1)
     got = _ctx(ile, point, prec).eval(th)
     assert got.shape == (1,)
     assert abs(got[0] - orc.lnL_t(point, th)[0]) < LNL_ATOL
@@ -52,7 +52,7 @@ def _toward(v, gmst):
 def test_windows_at_both_ends_of_the_series(ile, orc, prec):
     """Sky directions along and against each detector's position (largest delays) with t_c at both
     ends of its range: the windows reach the first and last columns of Q, no range error."""
-    point = S.config_point(1)
+    point = S.workload_point(S.FULL)
     rng = np.random.default_rng(11)
     cols = []
     for r in point.det_pos:
@@ -78,8 +78,8 @@ def test_windows_at_both_ends_of_the_series(ile, orc, prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_no_data_and_no_model_power(ile, orc, prec):
-    base = S.config_point(1)
-    th = S.config_samples(1, 700)
+    base = S.workload_point(S.FULL)
+    th = S.workload_samples(S.FULL, 700)
     # Q = 0: lnL(j) = -A for every window bin, so lnL_t = -A exactly
     p0 = S.Point(**{**base.__dict__, "Q": np.zeros_like(base.Q)})
     got0 = _ctx(ile, p0, prec).eval(th)
@@ -102,7 +102,7 @@ def test_no_data_and_no_model_power(ile, orc, prec):
 def test_largest_launch(ile, orc):
     """2^23 samples in one call (the largest adaptive iteration): every value finite, a random
     subset within tolerance of the oracle."""
-    point = S.config_point(1)
+    point = S.workload_point(S.FULL)
     N = 1 << 23
     th = S.prior_samples(np.random.default_rng(2026), N)
     got = _ctx(ile, point, "bf16x3").eval(th)
@@ -114,7 +114,7 @@ def test_largest_launch(ile, orc):
 def test_largest_adaptive_iteration(ile, orc):
     """n_per_iter = 2^23: the device sampler's last 4096 draws are the oracle's, bit for bit in
     the bins; the iteration's estimate is finite and its sample count exact."""
-    point = S.config_point(1)
+    point = S.workload_point(S.FULL)
     N = 1 << 23
     lo, hi = ile.default_ranges()
     cfg = ile.make_adapt_cfg(seed=0x5EED, n_per_iter=N, adapt_mask=0b11, point_id=9)

@@ -55,7 +55,7 @@ def _oracle_models(models, n):
 
 
 def test_mixture_sampler_and_update_match_oracle(ile, orc):
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     ctx = ile.Context(0, None, "fp32")
     ctx.set_data(point)
     lo, hi = ile.default_ranges()
@@ -100,7 +100,7 @@ def test_mixture_sampler_and_update_match_oracle(ile, orc):
 def test_first_iteration_matches_oracle_and_run_agrees(ile, orc):
     """Iteration 0 starts from the same initial mixtures on both sides (so the same samples);
     later iterations refit from slightly different weights, so they agree within MC errors."""
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     lo, hi = ile.default_ranges()
     N = 8192
     cfg = ile.make_adapt_cfg(seed=404, n_per_iter=N, n_iter=4, adapt_mask=0b11, point_id=2, gmm_mask=0b11,
@@ -122,7 +122,7 @@ def test_first_iteration_matches_oracle_and_run_agrees(ile, orc):
 def test_mixture_and_histogram_estimates_agree(ile):
     """Two unbiased estimators of the same integral: the Gaussian-mixture and the histogram
     sampling priors give ln L_marg within their combined Monte Carlo error."""
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     N = 1 << 15
     est = []
     for gmask in (0, 0b0101011):
@@ -137,7 +137,7 @@ def test_mixture_and_histogram_estimates_agree(ile):
 
 
 def test_mixture_resume_is_bit_reproducible(ile):
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     cfg = ile.make_adapt_cfg(seed=8, n_per_iter=4096, adapt_mask=0b0101011, point_id=1, gmm_mask=0b0001010,
                              gmm_components=2, gmm_em_iters=3)
     a = ile.Context(0, None, "bf16x3")
@@ -162,7 +162,7 @@ def test_mixture_resume_is_bit_reproducible(ile):
 
 
 def test_mixture_argument_errors(ile):
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     ctx = ile.Context(0)
     ctx.set_data(point)
     bad = [ile.make_adapt_cfg(seed=1, n_per_iter=64, adapt_mask=0b01, gmm_mask=0b10),

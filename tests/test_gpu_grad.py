@@ -82,18 +82,18 @@ def _compare_all(ile, orc, point, th, g, prec="fp32"):
     return out
 
 
-def test_grad_adjoint_config_K3_M21_Nt512(ile, orc):
+def test_grad_adjoint_K3_M21_Nt512(ile, orc):
     """Three detectors, 21 modes, 512-bin window (the adjoint workload's geometry), 2^10 samples."""
-    point = S.config_point(4)
-    th = S.config_samples(4, 1024)
+    point = S.workload_point(S.GRAD)
+    th = S.workload_samples(S.GRAD, 1024)
     g = np.random.default_rng(7).normal(size=th.shape[1])
     _compare_all(ile, orc, point, th, g)
 
 
 def test_grad_two_detectors_ragged(ile, orc):
     """K = 2, M = 2, N_t = 256; 300 samples = 4 tiles of 64 and a ragged tail."""
-    point = S.config_point(0)
-    th = S.config_samples(0, 300)
+    point = S.workload_point(S.SMALL)
+    th = S.workload_samples(S.SMALL, 300)
     g = np.random.default_rng(8).uniform(0.5, 1.5, th.shape[1])
     _compare_all(ile, orc, point, th, g)
 
@@ -108,8 +108,8 @@ def test_grad_long_window_four_detectors(ile, orc):
 
 def test_grad_matches_fp64_central_differences(ile, orc):
     """GPU gradient vs central differences (step 1e-6) of the FP64 oracle lnL_t."""
-    point = S.config_point(4)
-    th = S.config_samples(4, 48)
+    point = S.workload_point(S.GRAD)
+    th = S.workload_samples(S.GRAD, 48)
     got = _ctx(ile, point).eval_grad(th, want=("theta",))["theta"]
     kink = _near_kink(orc, point, th)
     steps = np.array([1e-6, 1e-6, 1e-6, 1e-6, 1e-6, 1e-6, 1e-6])
@@ -129,8 +129,8 @@ def test_grad_matches_fp64_central_differences(ile, orc):
 def test_grad_full_size_sampled(ile, orc):
     """2^18 samples through the full launch; the upstream weights are non-zero on 192 random
     samples only, so the oracle can check g_theta on those and the Q/U/V sums exactly."""
-    point = S.config_point(4)
-    th = S.config_samples(4)
+    point = S.workload_point(S.GRAD)
+    th = S.workload_samples(S.GRAD)
     N = th.shape[1]
     rng = np.random.default_rng(9)
     idx = np.sort(rng.choice(N, 192, replace=False))
@@ -150,8 +150,8 @@ def test_grad_full_size_sampled(ile, orc):
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 def test_integrate_grad_matches_oracle(ile, orc, prec):
     """d ln L_marg / d(theta, Q, U, V) = oracle gradient with weights w_n / sum w."""
-    point = S.config_point(4)
-    th = S.config_samples(4, 2048)
+    point = S.workload_point(S.GRAD)
+    th = S.workload_samples(S.GRAD, 2048)
     rng = np.random.default_rng(10)
     lp = rng.normal(0.0, 0.3, th.shape[1])
     lps = rng.normal(0.0, 0.3, th.shape[1])
@@ -179,8 +179,8 @@ def _torch_leaves(torch, point, dev):
 def test_autograd_lnLt(ile, orc):
     import torch
     from paper_2210_07912_gb300 import autograd as A
-    point = S.config_point(4)
-    th = S.config_samples(4, 512)
+    point = S.workload_point(S.GRAD)
+    th = S.workload_samples(S.GRAD, 512)
     ctx = _ctx(ile, point)
     dev = torch.device("cuda:0")
     x = torch.tensor(th, dtype=torch.float64, device=dev, requires_grad=True)
@@ -201,8 +201,8 @@ def test_autograd_lnLt(ile, orc):
 def test_autograd_lnLmarg(ile, orc):
     import torch
     from paper_2210_07912_gb300 import autograd as A
-    point = S.config_point(4)
-    th = S.config_samples(4, 1024)
+    point = S.workload_point(S.GRAD)
+    th = S.workload_samples(S.GRAD, 1024)
     ctx = _ctx(ile, point)
     dev = torch.device("cuda:0")
     x = torch.tensor(th, dtype=torch.float64, device=dev, requires_grad=True)
@@ -221,9 +221,9 @@ def test_autograd_lnLmarg(ile, orc):
 
 
 def test_grad_errors(ile):
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     c = ile.Context(0, None, "fp32")
-    th = S.config_samples(0, 8)
+    th = S.workload_samples(S.SMALL, 8)
     with pytest.raises(ile.IleError) as e:
         c.eval_grad(th)
     assert e.value.status == ile.ILE_E_STATE

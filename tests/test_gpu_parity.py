@@ -36,9 +36,9 @@ def _ctx(ile, point, prec="fp32"):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_grid_matches_oracle_config0(ile, orc, prec):
-    point = S.config_point(0)
-    th = S.config_samples(0, 300)  # 4 full tiles of 64 + a ragged tail
+def test_grid_matches_oracle_small_point(ile, orc, prec):
+    point = S.workload_point(S.SMALL)
+    th = S.workload_samples(S.SMALL, 300)  # 4 full tiles of 64 + a ragged tail
     ctx = _ctx(ile, point, prec)
     grid = ctx.eval(th, grid=True)
     for n in range(th.shape[1]):
@@ -48,9 +48,9 @@ def test_grid_matches_oracle_config0(ile, orc, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_lnL_t_matches_oracle_config0_all_samples(ile, orc, prec):
-    point = S.config_point(0)
-    th = S.config_samples(0)
+def test_lnL_t_matches_oracle_small_point_all_samples(ile, orc, prec):
+    point = S.workload_point(S.SMALL)
+    th = S.workload_samples(S.SMALL)
     ctx = _ctx(ile, point, prec)
     got = ctx.eval(th)
     ref = orc.lnL_t(point, th)
@@ -59,9 +59,9 @@ def test_lnL_t_matches_oracle_config0_all_samples(ile, orc, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_lnL_t_matches_oracle_config1_small(ile, orc, prec):
-    point = S.config_point(1)
-    th = S.config_samples(1, 1000)
+def test_lnL_t_matches_oracle_full_shape_1000_samples(ile, orc, prec):
+    point = S.workload_point(S.FULL)
+    th = S.workload_samples(S.FULL, 1000)
     ctx = _ctx(ile, point, prec)
     got = ctx.eval(th)
     ref = orc.lnL_t(point, th)
@@ -71,8 +71,8 @@ def test_lnL_t_matches_oracle_config1_small(ile, orc, prec):
 @pytest.mark.parametrize("prec", PRECS)
 def test_lnL_t_full_size_sampled(ile, orc, prec):
     """2^20 samples on the device (the benchmarked launch); 2048 random ones checked by the oracle."""
-    point = S.config_point(1)
-    th = S.config_samples(1)
+    point = S.workload_point(S.FULL)
+    th = S.workload_samples(S.FULL)
     ctx = _ctx(ile, point, prec)
     got = ctx.eval(th)
     idx = np.random.default_rng(3).choice(th.shape[1], 2048, replace=False)
@@ -95,8 +95,8 @@ def test_odd_shapes(ile, orc, shape, prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_integrate_matches_oracle(ile, orc, prec):
-    point = S.config_point(0)
-    th = S.config_samples(0)
+    point = S.workload_point(S.SMALL)
+    th = S.workload_samples(S.SMALL)
     rng = np.random.default_rng(4)
     lnp = rng.normal(0, 0.3, th.shape[1])
     lnps = rng.normal(0, 0.3, th.shape[1])
@@ -115,8 +115,8 @@ def test_integrate_matches_oracle(ile, orc, prec):
 def test_integrate_full_size(ile, orc, prec):
     """ln L_marg over 2^20 samples: the device reduction equals the oracle reduction of the device
     lnL_t, and the device lnL_t is within tolerance of the oracle on a random subset."""
-    point = S.config_point(1)
-    th = S.config_samples(1)
+    point = S.workload_point(S.FULL)
+    th = S.workload_samples(S.FULL)
     ctx = _ctx(ile, point, prec)
     res, lnl = ctx.integrate(th, want_lnL=True)
     st = orc.mc_stats(lnl)
@@ -129,8 +129,8 @@ def test_integrate_full_size(ile, orc, prec):
 
 def test_device_pointer_path(ile, orc):
     import torch
-    point = S.config_point(0)
-    th = S.config_samples(0, 5000)
+    point = S.workload_point(S.SMALL)
+    th = S.workload_samples(S.SMALL, 5000)
     ctx = _ctx(ile, point)
     stream = torch.cuda.Stream()
     ctx.set_stream(stream)
@@ -147,25 +147,25 @@ def test_device_pointer_path(ile, orc):
 
 
 def test_error_paths(ile):
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     c = ile.Context(0)
     with pytest.raises(ile.IleError) as e:
-        c.eval(S.config_samples(0, 4))
+        c.eval(S.workload_samples(S.SMALL, 4))
     assert e.value.status == ile.ILE_E_STATE
     c.set_data(point)
     assert c.eval(np.zeros((7, 0))).shape == (0,)
-    th = S.config_samples(0, 100)
+    th = S.workload_samples(S.SMALL, 100)
     th[6, 17] = 0.05  # coalescence time far outside the window
     with pytest.raises(ile.IleError) as e:
         c.eval(th)
     assert e.value.status == ile.ILE_E_RANGE
-    th = S.config_samples(0, 100)
+    th = S.workload_samples(S.SMALL, 100)
     th[0, 3] = np.nan
     with pytest.raises(ile.IleError) as e:
         c.eval(th)
     assert e.value.status == ile.ILE_E_NONFINITE
     # the context is still usable afterwards
-    good = S.config_samples(0, 10)
+    good = S.workload_samples(S.SMALL, 10)
     assert np.all(np.isfinite(c.eval(good)))
     bad = S.Point(**{**point.__dict__, "lm": np.array([[2, 2], [2, 2]], np.int32)})
     with pytest.raises(ile.IleError) as e:

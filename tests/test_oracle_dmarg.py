@@ -29,14 +29,15 @@ def test_lnF_normalisation_and_adaptive_quadrature(orc):
         assert abs(orc.dmarg_lnF(a, b, D_MIN, D_MAX, D_REF) - ref) < 1e-9, (a, b)
 
 
-@pytest.mark.parametrize("cfg", [0, 1])
-def test_dmarg_equals_distance_integral_of_lnL_t(orc, cfg):
+@pytest.mark.parametrize("shape", ["hl_m2", "hlv_m9"])
+def test_dmarg_equals_distance_integral_of_lnL_t(orc, shape):
     """exp(lnL_dmarg(theta)) = int p(D) exp(lnL_t(theta, D)) dD, the right side from the pinned
     time-marginalised likelihood on a 400-node Gauss-Legendre rule in D."""
-    point = S.config_point(cfg)
-    if cfg == 1:
+    if shape == "hl_m2":
+        point = S.workload_point(S.SMALL)
+    else:
         point = S.make_point(S.SEED_BASE + 70, 3, 9, 64, spectrum="decay")
-    th = S.config_samples(0, 6)
+    th = S.workload_samples(S.SMALL, 6)
     got = orc.lnL_dmarg(point, th, D_MIN, D_MAX)
     xg, wg = np.polynomial.legendre.leggauss(400)
     D = 0.5 * (D_MAX - D_MIN) * xg + 0.5 * (D_MAX + D_MIN)
@@ -51,8 +52,8 @@ def test_dmarg_equals_distance_integral_of_lnL_t(orc, cfg):
 
 
 def test_dmarg_ignores_sample_distance(orc):
-    point = S.config_point(0)
-    th = S.config_samples(0, 8)
+    point = S.workload_point(S.SMALL)
+    th = S.workload_samples(S.SMALL, 8)
     t2 = th.copy()
     t2[5] = np.linspace(150, 900, 8)
     np.testing.assert_array_equal(orc.lnL_dmarg(point, th, D_MIN, D_MAX), orc.lnL_dmarg(point, t2, D_MIN, D_MAX))

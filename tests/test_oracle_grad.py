@@ -39,11 +39,11 @@ def _bins(point, th, orc):
     return x
 
 
-@pytest.mark.parametrize("cfg,M", [(0, None), (1, 9)])
-def test_grad_theta_matches_central_differences(orc, cfg, M):
-    c = S.CONFIGS[cfg]
-    point = S.make_point(S.SEED_BASE + 40 + cfg, c["n_det"], M or c["n_modes"], 64, spectrum=c["spectrum"])
-    th = S.prior_samples(np.random.default_rng(41 + cfg), 24)
+@pytest.mark.parametrize("wl,M", [(S.SMALL, None), (S.FULL, 9)])
+def test_grad_theta_matches_central_differences(orc, wl, M):
+    c = S.WORKLOADS[wl]
+    point = S.make_point(S.SEED_BASE + 40 + c["seed"], c["n_det"], M or c["n_modes"], 64, spectrum=c["spectrum"])
+    th = S.prior_samples(np.random.default_rng(41 + c["seed"]), 24)
     lnl, g, _, _, _ = orc.lnL_t_grad(point, th)
     np.testing.assert_allclose(lnl, orc.lnL_t(point, th), rtol=1e-13, atol=1e-12)
     checked = 0
@@ -64,8 +64,8 @@ def test_grad_theta_matches_central_differences(orc, cfg, M):
 
 def test_grad_distance_closed_form(orc):
     """d lnL_t/dD = (2A - sum_j pi_j data_j)/D with pi the softmax of lnL(j)."""
-    point = S.config_point(0)
-    th = S.config_samples(0, 16)
+    point = S.workload_point(S.SMALL)
+    th = S.workload_samples(S.SMALL, 16)
     _, g, _, _, _ = orc.lnL_t_grad(point, th)
     for n in range(th.shape[1]):
         lnL, data, A = orc.lnL_grid(point, th[:, n])
@@ -101,8 +101,8 @@ def test_grad_QUV_directional_differences(orc):
 
 def test_grad_upstream_weights_are_linear(orc):
     """g_theta scales per sample with the upstream weight; g_Q, g_U, g_V are weighted sums."""
-    point = S.config_point(0)
-    th = S.config_samples(0, 6)
+    point = S.workload_point(S.SMALL)
+    th = S.workload_samples(S.SMALL, 6)
     w = np.array([0.5, -2.0, 0.0, 1.0, 3.0, -0.25])
     _, g1, _, _, _ = orc.lnL_t_grad(point, th)
     _, gw, qw, uw, vw = orc.lnL_t_grad(point, th, w)

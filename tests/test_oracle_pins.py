@@ -220,7 +220,7 @@ def test_injection_identity_and_cauchy_schwarz(orc):
 
 
 def test_symmetries_and_distance_scaling(orc):
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     rng = np.random.default_rng(9)
     th = S.prior_samples(rng, 20)
     for n in range(th.shape[1]):
@@ -242,8 +242,8 @@ def test_symmetries_and_distance_scaling(orc):
 
 def test_time_marginalisation_logsumexp(orc):
     scipy_special = pytest.importorskip("scipy.special")
-    point = S.config_point(0)
-    th = S.config_samples(0, 64)
+    point = S.workload_point(S.SMALL)
+    th = S.workload_samples(S.SMALL, 64)
     out = orc.lnL_t(point, th)
     for n in range(th.shape[1]):
         lnL, _, _ = orc.lnL_grid(point, th[:, n])
@@ -256,8 +256,8 @@ def test_time_marginalisation_logsumexp(orc):
 
 
 def test_range_error(orc):
-    point = S.config_point(0)
-    th = S.config_samples(0, 4)
+    point = S.workload_point(S.SMALL)
+    th = S.workload_samples(S.SMALL, 4)
     th[6, 1] = 0.05  # t_c far outside the window
     with pytest.raises(orc.RangeError):
         orc.lnL_t(point, th)

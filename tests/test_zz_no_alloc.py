@@ -27,7 +27,7 @@ def env():
 
 def test_noalloc_reduction_matches_integrate_twice(env):
     torch, ile = env
-    point = S.config_point(0)
+    point = S.workload_point(S.SMALL)
     ctx = ile.Context(0, None, "fp32")
     ctx.set_data(point)
     lib = ile.load()

@@ -425,6 +425,25 @@ ile_status ile_integrate_grad(ile_ctx *ctx, const double *samples, const double 
 /* Wait for the context's stream and return the first device-side error seen since the last call. */
 ile_status ile_sync(ile_ctx *ctx);
 
+/*
+ * Cap on the device memory this context allocates, in bytes (0 = no cap, the default).  A call
+ * that would allocate past the cap returns ILE_E_NOMEM before any device allocation is attempted;
+ * the memory the context already holds stays valid and the context stays usable (raise the cap
+ * and call again).  For services that must stay within a fixed budget, and for exercising the
+ * allocation-failure path.  ile_memory_used reports the bytes the context holds now.
+ */
+ile_status ile_set_memory_limit(ile_ctx *ctx, size_t bytes);
+ile_status ile_memory_used(const ile_ctx *ctx, size_t *bytes);
+
+/*
+ * Check of the bounded device-side waits: one block waits on a shared-memory mbarrier phase that
+ * nothing completes, with the same bounded sleeping wait the pipelined kernels use, limited to
+ * about timeout_s seconds (0 < timeout_s <= 10, else ILE_E_ARG).  The wait gives up, raises the
+ * context's timeout flag and the call returns ILE_E_TIMEOUT; the context remains usable.  No
+ * fault or trap is involved.
+ */
+ile_status ile_check_wait_timeout(ile_ctx *ctx, double timeout_s);
+
 /* Human-readable name of a status code (static storage). */
 const char *ile_status_string(ile_status st);
 

@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <unordered_map>
 #include <vector>
 
 #include "ile_internal.cuh"
@@ -68,6 +69,9 @@ struct ile_ctx {
     double *g_out = nullptr;   // staged g_theta [7][cap] and g_Q, g_U, g_V for host-pointer calls
     size_t g_out_bytes = 0;
     int n_sm = 0;
+    // device memory owned by the context (ctx_malloc / ctx_free) and its optional cap
+    size_t mem_limit = 0, mem_used = 0;
+    std::unordered_map<void *, size_t> allocs;
     // stage timing
     bool profiling = false;
     std::vector<cudaEvent_t> ev[ILE_NSTAGE];
@@ -100,11 +104,33 @@ ile_status cuda_fail(ile_ctx *c, cudaError_t e, const char *where) {
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
     } while (0)
 
+// Device allocations of a context go through ctx_malloc / ctx_free, which keep the bytes in use
+// so that ile_set_memory_limit can refuse an allocation (ILE_E_NOMEM) before cudaMalloc is called.
+cudaError_t ctx_malloc(ile_ctx *ctx, void **p, size_t bytes) {
+    if (ctx->mem_limit && ctx->mem_used + bytes > ctx->mem_limit) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) {
+        ctx->mem_used += bytes;
+        ctx->allocs[*p] = bytes;
+    }
+    return e;
+}
+
+void ctx_free(ile_ctx *ctx, void *p) {
+    if (!p) return;
+    const auto it = ctx->allocs.find(p);
+    if (it != ctx->allocs.end()) {
+        ctx->mem_used -= it->second;
+        ctx->allocs.erase(it);
+    }
+    cudaFree(p);
+}
+
 template <typename T>
-cudaError_t grow(T **p, size_t bytes) {
-    if (*p) cudaFree(*p);
+cudaError_t grow(ile_ctx *ctx, T **p, size_t bytes) {
+    ctx_free(ctx, *p);
     *p = nullptr;
-    return cudaMalloc((void **)p, bytes);
+    return ctx_malloc(ctx, (void **)p, bytes);
 }
 
 // Bracket one launch of stage `stage` with events on the context stream (when profiling).
@@ -132,19 +158,23 @@ ile_status ensure_samples(ile_ctx *ctx, int64_t N) {
     if (N <= ctx->cap) return ILE_OK;
     const int K = ctx->pp.K, R = 2 * ctx->pp.M;
     int64_t cap = N;
-    CK(grow(&ctx->s.C, sizeof(float) * (size_t)ILE_MAX_DET * 2 * ILE_MAX_MODES * cap));
-    CK(grow(&ctx->s.I0, sizeof(int) * (size_t)ILE_MAX_DET * cap));
-    CK(grow(&ctx->s.W, sizeof(float) * (size_t)ILE_MAX_DET * cap));
-    CK(grow(&ctx->s.A, sizeof(float) * (size_t)cap));
-    CK(grow(&ctx->theta, sizeof(double) * ILE_NDIM * (size_t)cap));
-    CK(grow(&ctx->lnp, sizeof(double) * (size_t)cap));
-    CK(grow(&ctx->lnps, sizeof(double) * (size_t)cap));
-    CK(grow(&ctx->keys, sizeof(int) * (size_t)cap));
-    CK(grow(&ctx->perm, sizeof(int) * (size_t)cap));
-    CK(grow(&ctx->g_in, sizeof(double) * (size_t)cap));
-    if (!ctx->buckets) CK(cudaMalloc((void **)&ctx->buckets, sizeof(int) * ile_sort_key_buckets()));
+    // until every buffer below is in place the scratch counts as empty (a failed growth, e.g. past
+    // the memory cap, leaves some of them released)
+    ctx->cap = 0;
+    ctx->part_cap = 0;
+    CK(grow(ctx, &ctx->s.C, sizeof(float) * (size_t)ILE_MAX_DET * 2 * ILE_MAX_MODES * cap));
+    CK(grow(ctx, &ctx->s.I0, sizeof(int) * (size_t)ILE_MAX_DET * cap));
+    CK(grow(ctx, &ctx->s.W, sizeof(float) * (size_t)ILE_MAX_DET * cap));
+    CK(grow(ctx, &ctx->s.A, sizeof(float) * (size_t)cap));
+    CK(grow(ctx, &ctx->theta, sizeof(double) * ILE_NDIM * (size_t)cap));
+    CK(grow(ctx, &ctx->lnp, sizeof(double) * (size_t)cap));
+    CK(grow(ctx, &ctx->lnps, sizeof(double) * (size_t)cap));
+    CK(grow(ctx, &ctx->keys, sizeof(int) * (size_t)cap));
+    CK(grow(ctx, &ctx->perm, sizeof(int) * (size_t)cap));
+    CK(grow(ctx, &ctx->g_in, sizeof(double) * (size_t)cap));
+    if (!ctx->buckets) CK(ctx_malloc(ctx, (void **)&ctx->buckets, sizeof(int) * ile_sort_key_buckets()));
     int np = ile_mc_partial_count(cap);
-    CK(grow(&ctx->part, sizeof(double) * 3 * (size_t)np));
+    CK(grow(ctx, &ctx->part, sizeof(double) * 3 * (size_t)np));
     ctx->part_cap = np;
     (void)K;
     (void)R;
@@ -154,7 +184,8 @@ ile_status ensure_samples(ile_ctx *ctx, int64_t N) {
 
 ile_status ensure_out(ile_ctx *ctx, size_t bytes) {
     if (bytes <= ctx->out_bytes) return ILE_OK;
-    CK(grow(&ctx->out, bytes));
+    ctx->out_bytes = 0;
+    CK(grow(ctx, &ctx->out, bytes));
     ctx->out_bytes = bytes;
     return ILE_OK;
 }
@@ -210,8 +241,9 @@ ile_status ensure_tc_operands(ile_ctx *ctx, int prec) {
     if (ctx->Qtc_ready[prec]) return ILE_OK;
     const size_t bytes = ile_tc_q_bytes(prec, ctx->pp.K, ctx->pp.M, ctx->pp.T_ext);
     if (bytes > ctx->Qtc_bytes[prec]) {
-        CK(grow(&ctx->Qtc[prec][0], bytes));
-        CK(grow(&ctx->Qtc[prec][1], bytes));
+        ctx->Qtc_bytes[prec] = 0;
+        CK(grow(ctx, &ctx->Qtc[prec][0], bytes));
+        CK(grow(ctx, &ctx->Qtc[prec][1], bytes));
         ctx->Qtc_bytes[prec] = bytes;
     }
     CK(ile_launch_tc_split(prec, ctx->pp, ctx->Qp, ctx->Qquad, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ctx->stream));
@@ -259,9 +291,9 @@ ile_status run_eval(ile_ctx *ctx, const double *dsamples, int64_t N, double *dou
 }
 
 template <typename T>
-cudaError_t ensure_bytes(T **p, size_t *have, size_t bytes) {
+cudaError_t ensure_bytes(ile_ctx *ctx, T **p, size_t *have, size_t bytes) {
     if (bytes <= *have && *p) return cudaSuccess;
-    cudaError_t e = grow(p, bytes);
+    cudaError_t e = grow(ctx, p, bytes);
     *have = e == cudaSuccess ? bytes : 0;
     return e;
 }
@@ -276,14 +308,14 @@ ile_status run_grad(ile_ctx *ctx, const double *dsamples, const double *dg, int6
     if (!ctx->n_sm) CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
     float *pig = nullptr;
     if (gQ) {
-        CK(ensure_bytes(&ctx->pig, &ctx->pig_bytes, sizeof(float) * (size_t)N * pp.Nt));
+        CK(ensure_bytes(ctx, &ctx->pig, &ctx->pig_bytes, sizeof(float) * (size_t)N * pp.Nt));
         pig = ctx->pig;
     }
     const int nsplit = ile_grad_q_splits(pp, N, ctx->n_sm);
     const int nblk = ile_grad_uv_blocks(N, ctx->n_sm);
-    if (gQ) CK(ensure_bytes(&ctx->gq_part, &ctx->gq_bytes, sizeof(float) * (size_t)nsplit * pp.K * 2 * pp.M * pp.T_ext));
+    if (gQ) CK(ensure_bytes(ctx, &ctx->gq_part, &ctx->gq_bytes, sizeof(float) * (size_t)nsplit * pp.K * 2 * pp.M * pp.T_ext));
     if (gU || gV)
-        CK(ensure_bytes(&ctx->guv_part, &ctx->guv_bytes,
+        CK(ensure_bytes(ctx, &ctx->guv_part, &ctx->guv_bytes,
                         sizeof(float) * (size_t)nblk * pp.K * (pp.M * (pp.M + 1) / 2) * 4));
     {
         StageScope t(ctx, 1, 4);
@@ -305,7 +337,7 @@ ile_status run_grad_host(ile_ctx *ctx, const double *samples, const double *g, i
     const PointParams &pp = ctx->pp;
     const size_t nth = (size_t)ILE_NDIM * N, nq = 2 * (size_t)pp.K * pp.M * pp.T_ext,
                  nuv = 2 * (size_t)pp.K * pp.M * pp.M;
-    CK(ensure_bytes(&ctx->g_out, &ctx->g_out_bytes, sizeof(double) * (nth + nq + 2 * nuv + (size_t)N)));
+    CK(ensure_bytes(ctx, &ctx->g_out, &ctx->g_out_bytes, sizeof(double) * (nth + nq + 2 * nuv + (size_t)N)));
     double *d_th = ctx->g_out, *d_q = d_th + nth, *d_u = d_q + nq, *d_v = d_u + nuv, *d_l = d_v + nuv;
     CK(cudaMemcpyAsync(ctx->theta, samples, sizeof(double) * nth, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->g_in, g, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
@@ -381,6 +413,25 @@ ile_status ile_destroy(ile_ctx *ctx) {
         for (cudaEvent_t e : v) cudaEventDestroy(e);
     delete ctx;
     return ILE_OK;
+}
+
+ile_status ile_set_memory_limit(ile_ctx *ctx, size_t bytes) {
+    if (!ctx) return ILE_E_ARG;
+    ctx->mem_limit = bytes;
+    return ILE_OK;
+}
+
+ile_status ile_memory_used(const ile_ctx *ctx, size_t *bytes) {
+    if (!ctx || !bytes) return ILE_E_ARG;
+    *bytes = ctx->mem_used;
+    return ILE_OK;
+}
+
+ile_status ile_check_wait_timeout(ile_ctx *ctx, double timeout_s) {
+    if (!ctx || !(timeout_s > 0.0) || !(timeout_s <= 10.0)) return ILE_E_ARG;
+    DeviceGuard g(ctx->device);
+    CK(ile_launch_wait_check(ctx->flags, timeout_s, ctx->stream));
+    return read_flags(ctx);
 }
 
 ile_status ile_set_stream(ile_ctx *ctx, void *cuda_stream) {
@@ -550,9 +601,12 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
                                       n_window, gmst_rad, d_ref_mpc, pp, qp, uv, quad);
     if (st != ILE_OK) return st;
     DeviceGuard g(ctx->device);
-    CK(grow(&ctx->Qp, sizeof(float) * qp.size()));
-    CK(grow(&ctx->UV, sizeof(float) * uv.size()));
-    CK(grow(&ctx->Qquad, sizeof(float) * quad.size()));
+    // the previous point's arrays are released by the growth below: no data until it completes
+    ctx->has_data = false;
+    ctx->Qtc_ready[1] = ctx->Qtc_ready[2] = false;
+    CK(grow(ctx, &ctx->Qp, sizeof(float) * qp.size()));
+    CK(grow(ctx, &ctx->UV, sizeof(float) * uv.size()));
+    CK(grow(ctx, &ctx->Qquad, sizeof(float) * quad.size()));
     CK(cudaMemcpyAsync(ctx->Qp, qp.data(), sizeof(float) * qp.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->UV, uv.data(), sizeof(float) * uv.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->Qquad, quad.data(), sizeof(float) * quad.size(), cudaMemcpyHostToDevice, ctx->stream));
@@ -573,7 +627,7 @@ ile_status ile_set_distance_marginalization(ile_ctx *ctx, int enable, double d_m
     }
     if (!(d_min_mpc > 0.0) || !(d_max_mpc > d_min_mpc) || !isfinite(d_max_mpc)) return ILE_E_ARG;
     DeviceGuard g(ctx->device);
-    if (!ctx->dm_table) CK(cudaMalloc(&ctx->dm_table, ile_dmarg_buffer_bytes()));
+    if (!ctx->dm_table) CK(ctx_malloc(ctx, &ctx->dm_table, ile_dmarg_buffer_bytes()));
     DmargParams dm{};
     CK(ile_build_dmarg(d_min_mpc, d_max_mpc, (double)ctx->pp.d_ref, ctx->dm_table, dm, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -595,7 +649,7 @@ ile_status ile_build_quv(ile_ctx *ctx, int n_det, int n_modes, int64_t L, const 
     double *buf = nullptr;
     const bool dev = (flags & ILE_DEVICE_PTRS) != 0;
     const size_t n_all = nz + (dev ? 0 : nh + nd + ns + nq + 2 * nuv);
-    CK(cudaMalloc((void **)&buf, sizeof(double) * n_all));
+    CK(ctx_malloc(ctx, (void **)&buf, sizeof(double) * n_all));
     double *z = buf, *dh = (double *)h, *dp = (double *)psd, *dd = (double *)d, *dQ = Q, *dU = U, *dV = V;
     cudaError_t e = cudaSuccess;
     if (!dev) {
@@ -618,7 +672,7 @@ ile_status ile_build_quv(ile_ctx *ctx, int n_det, int n_modes, int64_t L, const 
     }
     // the scratch is released after the work that uses it (stream-ordered wait)
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    cudaFree(buf);
+    ctx_free(ctx, buf);
     CK(e);
     return ILE_OK;
 }
@@ -634,14 +688,14 @@ ile_status ile_dmarg_eval(ile_ctx *ctx, const double *a, const double *b, int64_
         return ILE_OK;
     }
     double *d = nullptr;
-    CK(cudaMalloc((void **)&d, sizeof(double) * 3 * (size_t)n));
+    CK(ctx_malloc(ctx, (void **)&d, sizeof(double) * 3 * (size_t)n));
     cudaError_t e = cudaMemcpyAsync(d, a, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d + n, b, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = ile_launch_dmarg_eval(ctx->pp.dm, d, d + n, n, d + 2 * n, ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, d + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    cudaFree(d);
+    ctx_free(ctx, d);
     CK(e);
     return ILE_OK;
 }
@@ -765,7 +819,7 @@ ile_status ile_integrate_grad(ile_ctx *ctx, const double *samples, const double 
     const PointParams &pp = ctx->pp;
     const size_t nth = (size_t)ILE_NDIM * N, nq = 2 * (size_t)pp.K * pp.M * pp.T_ext,
                  nuv = 2 * (size_t)pp.K * pp.M * pp.M;
-    CK(ensure_bytes(&ctx->g_out, &ctx->g_out_bytes, sizeof(double) * (nth + nq + 2 * nuv)));
+    CK(ensure_bytes(ctx, &ctx->g_out, &ctx->g_out_bytes, sizeof(double) * (nth + nq + 2 * nuv)));
     double *d_th = ctx->g_out, *d_q = d_th + nth, *d_u = d_q + nq, *d_v = d_u + nuv;
     st = run_grad(ctx, ds, ctx->g_in, N, g_samples ? d_th : nullptr, g_Q ? d_q : nullptr, g_U ? d_u : nullptr,
                   g_V ? d_v : nullptr, nullptr);
@@ -779,32 +833,39 @@ ile_status ile_integrate_grad(ile_ctx *ctx, const double *samples, const double 
 }
 
 static ile_status adapt_alloc(ile_ctx *ctx, int64_t N) {
-    if (!ctx->a_cdf) {
-        CK(cudaMalloc((void **)&ctx->a_cdf, sizeof(uint64_t) * ILE_NDIM * (ILE_NBINS + 1)));
-        CK(cudaMalloc((void **)&ctx->a_lnps, sizeof(float) * ILE_NDIM * ILE_NBINS));
-        CK(cudaMalloc((void **)&ctx->a_hist, sizeof(double) * ILE_NDIM * ILE_NBINS));
-        CK(cudaMalloc((void **)&ctx->a_hist_fx, sizeof(unsigned long long) * ILE_NDIM * ILE_NBINS));
-        CK(cudaMemset(ctx->a_hist_fx, 0, sizeof(unsigned long long) * ILE_NDIM * ILE_NBINS));
+    // each fixed-size buffer is allocated once (a failed call leaves the rest for the next one)
+    if (!ctx->a_cdf) CK(ctx_malloc(ctx, (void **)&ctx->a_cdf, sizeof(uint64_t) * ILE_NDIM * (ILE_NBINS + 1)));
+    if (!ctx->a_lnps) CK(ctx_malloc(ctx, (void **)&ctx->a_lnps, sizeof(float) * ILE_NDIM * ILE_NBINS));
+    if (!ctx->a_hist) {
+        CK(ctx_malloc(ctx, (void **)&ctx->a_hist, sizeof(double) * ILE_NDIM * ILE_NBINS));
         CK(cudaMemset(ctx->a_hist, 0, sizeof(double) * ILE_NDIM * ILE_NBINS));
-        CK(cudaMalloc((void **)&ctx->a_pooled, sizeof(double) * 4));
-        CK(cudaMalloc((void **)&ctx->a_iter_log, sizeof(double) * 2 * ILE_ADAPT_LOG));
-        CK(cudaMemset(ctx->a_iter_log, 0, sizeof(double) * 2 * ILE_ADAPT_LOG));
-        CK(cudaMalloc((void **)&ctx->a_iter_res, sizeof(double) * 8));
-        CK(cudaMalloc((void **)&ctx->a_iter, sizeof(int)));
-        CK(cudaMalloc((void **)&ctx->g_cur, sizeof(IleGmm) * ILE_NDIM));
-        CK(cudaMalloc((void **)&ctx->g_bat, sizeof(IleGmm) * ILE_NDIM));
-        CK(cudaMalloc((void **)&ctx->g_tab, sizeof(IleGmmTab) * ILE_NDIM));
-        CK(cudaMalloc((void **)&ctx->g_part, sizeof(double) * ile_gmm_part_doubles()));
     }
+    if (!ctx->a_hist_fx) {
+        CK(ctx_malloc(ctx, (void **)&ctx->a_hist_fx, sizeof(unsigned long long) * ILE_NDIM * ILE_NBINS));
+        CK(cudaMemset(ctx->a_hist_fx, 0, sizeof(unsigned long long) * ILE_NDIM * ILE_NBINS));
+    }
+    if (!ctx->a_pooled) CK(ctx_malloc(ctx, (void **)&ctx->a_pooled, sizeof(double) * 4));
+    if (!ctx->a_iter_log) {
+        CK(ctx_malloc(ctx, (void **)&ctx->a_iter_log, sizeof(double) * 2 * ILE_ADAPT_LOG));
+        CK(cudaMemset(ctx->a_iter_log, 0, sizeof(double) * 2 * ILE_ADAPT_LOG));
+    }
+    if (!ctx->a_iter_res) CK(ctx_malloc(ctx, (void **)&ctx->a_iter_res, sizeof(double) * 8));
+    if (!ctx->a_iter) CK(ctx_malloc(ctx, (void **)&ctx->a_iter, sizeof(int)));
+    if (!ctx->g_cur) CK(ctx_malloc(ctx, (void **)&ctx->g_cur, sizeof(IleGmm) * ILE_NDIM));
+    if (!ctx->g_bat) CK(ctx_malloc(ctx, (void **)&ctx->g_bat, sizeof(IleGmm) * ILE_NDIM));
+    if (!ctx->g_tab) CK(ctx_malloc(ctx, (void **)&ctx->g_tab, sizeof(IleGmmTab) * ILE_NDIM));
+    if (!ctx->g_part) CK(ctx_malloc(ctx, (void **)&ctx->g_part, sizeof(double) * ile_gmm_part_doubles()));
     if (N > ctx->a_cap) {
-        CK(grow(&ctx->a_lnwp, sizeof(double) * (size_t)N));
-        CK(grow(&ctx->a_lnl, sizeof(double) * (size_t)N));
-        CK(grow(&ctx->a_bins, (size_t)ILE_NDIM * (size_t)N));
+        ctx->a_cap = 0;
+        CK(grow(ctx, &ctx->a_lnwp, sizeof(double) * (size_t)N));
+        CK(grow(ctx, &ctx->a_lnl, sizeof(double) * (size_t)N));
+        CK(grow(ctx, &ctx->a_bins, (size_t)ILE_NDIM * (size_t)N));
         ctx->a_cap = N;
     }
     const size_t ub = sizeof(float) * (size_t)__builtin_popcount(ctx->sp.gmm_mask) * (size_t)N;
     if (ub > ctx->a_u_bytes) {
-        CK(grow(&ctx->a_u, ub));
+        ctx->a_u_bytes = 0;
+        CK(grow(ctx, &ctx->a_u, ub));
         ctx->a_u_bytes = ub;
     }
     ile_status st = ensure_samples(ctx, N);

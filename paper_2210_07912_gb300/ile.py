@@ -174,6 +174,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ile_eval_grad.restype = i32
     lib.ile_integrate_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, u]
     lib.ile_integrate_grad.restype = i32
+    lib.ile_set_memory_limit.argtypes = [vp, ctypes.c_size_t]
+    lib.ile_set_memory_limit.restype = i32
+    lib.ile_memory_used.argtypes = [vp, P(ctypes.c_size_t)]
+    lib.ile_memory_used.restype = i32
+    lib.ile_check_wait_timeout.argtypes = [vp, d]
+    lib.ile_check_wait_timeout.restype = i32
     for name in ("ile_create", "ile_destroy", "ile_set_stream", "ile_set_precision", "ile_set_data", "ile_eval",
                  "ile_integrate", "ile_sync", "ile_profile", "ile_profile_read", "ile_adapt_init", "ile_adapt_step",
                  "ile_adapt_get", "ile_adapt_run", "ile_adapt_last"):
@@ -270,6 +276,19 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_memory_limit(self, nbytes: int):
+        """Cap the device memory this context may hold (0: no cap); past it calls raise ILE_E_NOMEM."""
+        self._check(self._lib.ile_set_memory_limit(self._h, int(nbytes)), "ile_set_memory_limit")
+
+    def memory_used(self) -> int:
+        v = ctypes.c_size_t(0)
+        self._check(self._lib.ile_memory_used(self._h, ctypes.byref(v)), "ile_memory_used")
+        return v.value
+
+    def check_wait_timeout(self, timeout_s: float = 0.05):
+        """Run the bounded-wait check; raises IleError with ILE_E_TIMEOUT when the wait gives up."""
+        self._check(self._lib.ile_check_wait_timeout(self._h, float(timeout_s)), "ile_check_wait_timeout")
 
     def set_stream(self, stream):
         self._check(self._lib.ile_set_stream(self._h, _stream_handle(stream)), "ile_set_stream")

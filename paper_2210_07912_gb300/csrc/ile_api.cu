@@ -4,6 +4,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <unordered_map>
 #include <vector>
 
@@ -133,15 +135,22 @@ cudaError_t grow(ile_ctx *ctx, T **p, size_t bytes) {
     return ctx_malloc(ctx, (void **)p, bytes);
 }
 
-// Bracket one launch of stage `stage` with events on the context stream (when profiling).
+// Bracket one launch of stage `stage` with events on the context stream (when profiling) and
+// with an NVTX range on the host timeline (a no-op unless a tool such as Nsight is attached).
+const char *const kStageName[ILE_NSTAGE] = {"ile:sample", "ile:coefficients", "ile:contraction",
+                                            "ile:mc_reduce", "ile:adapt",  "ile:adjoint"};
 struct StageScope {
     ile_ctx *c;
     int stage;
     StageScope(ile_ctx *ctx, int s, int n_kernels = 1) : c(ctx), stage(s) {
+        nvtxRangePushA(kStageName[s]);
         if (c->profiling) c->kernels[s] += n_kernels;
         mark();
     }
-    ~StageScope() { mark(); }
+    ~StageScope() {
+        mark();
+        nvtxRangePop();
+    }
     void mark() {
         if (!c->profiling) return;
         auto &v = c->ev[stage];

@@ -124,6 +124,20 @@ def cpu_sample_size(point, seconds, cores):
     return int(max(512, min(1 << 20, seconds / per)))
 
 
+def oracle_error(ctx, point, n=2048):
+    """lnL_t of a random subset of the context's last iteration (device samples, device values)
+    against the FP64 oracle evaluated on the same samples."""
+    import numpy as np
+    import oracle
+    theta, _, _, lnl = ctx.adapt_last()
+    idx = np.random.default_rng(11).choice(theta.shape[1], min(n, theta.shape[1]), replace=False)
+    ref = oracle.lnL_t(point, np.ascontiguousarray(theta[:, idx]))
+    d = np.abs(lnl[idx] - ref)
+    return {"max_abs_dlnL_t": float(d.max()), "rms_dlnL_t": float(np.sqrt(np.mean(d * d))),
+            "samples_checked": int(idx.size), "bar": 1e-3,
+            "what": "lnL_t of random samples of the last device iteration vs the FP64 oracle on the same samples"}
+
+
 def cpu_baseline(point, seconds=12.0):
     cores = os.cpu_count() or 1
     n = cpu_sample_size(point, seconds, cores)
@@ -179,6 +193,22 @@ def profile_traffic(kernel_file, prec):
         return float(vals["dram_bytes_per_launch_full"]), digest
     except (KeyError, ValueError):
         return None, digest
+
+
+def profile_tensor_active(kernel_file, prec):
+    """Tensor-pipe activity (fraction) of the committed ncu capture of the contraction kernel, if it
+    was taken on the current source (else None)."""
+    traffic, digest = profile_traffic(kernel_file, prec)
+    if traffic is None:
+        return None
+    summ = os.path.join(ROOT, "profiles", f"contract_{prec}_c1.md")
+    for line in open(summ):
+        if "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active" in line:
+            try:
+                return float(line.split(":", 1)[1].split()[0]) / 100.0
+            except (IndexError, ValueError):
+                return None
+    return None
 
 
 def batch_bench(ile, S, local, flush, iters=5, n_points=512, plain_iters=1):
@@ -435,7 +465,8 @@ def main():
         traffic, _ = profile_traffic(kfile, args.prec)
         achieved = alg_flops / per_launch_s / 1e12
         roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": traffic, "algorithmic_flops_per_launch": alg_flops,
+                     "traffic": traffic, "tensor_pipe_active_ncu": profile_tensor_active(kfile, args.prec),
+                     "algorithmic_flops_per_launch": alg_flops,
                      "launch_ms": per_launch_s * 1e3, "peak_source": pk_kind})
         launches = sum(c for (_, c) in prof.values())  # kernels launched by the library in the timed steps
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -454,6 +485,7 @@ def main():
                            "iterations": res["n_iter"]}}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(point)
+            line["error_vs_oracle"] = oracle_error(ctx, point)
         if not args.no_adjoint:
             line["adjoint"] = adjoint_bench(ile, S, local, stream, flush)
         if not args.no_dmarg:

@@ -398,7 +398,7 @@ cudaError_t ile_launch_lnps(const IleSamplerParams &sp, const uint64_t *cdf, flo
 cudaError_t ile_launch_sample(const IleSamplerParams &sp, const uint64_t *cdf, const float *lnps_tab,
                               const IleGmmTab *gmm_tab, const int *iter_dev, int64_t N, double *theta,
                               double *lnw_prior, uint8_t *bins, float *u_gmm, cudaStream_t st);
-// Bounded-wait check (ile_tc2.cu): one block waits on an mbarrier phase nothing completes, for
+// Bounded-wait check (ile_selftest.cu): one block waits on an mbarrier phase nothing completes, for
 // about timeout_s, with the kernels' bounded sleeping wait; it then sets ILE_FLAG_TIMEOUT.
 cudaError_t ile_launch_wait_check(unsigned *flags, double timeout_s, cudaStream_t st);
 // Gaussian-mixture adaptation (ile_gmm.cu).  cur, bat, tab: [7] on the device; part: scratch of

@@ -781,29 +781,6 @@ cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo
     return cudaGetLastError();
 }
 
-namespace {
-
-// Nothing arrives on `bar`, so the bounded wait must give up: tries x SLEEP_NS of suspended
-// try_wait at most (each try returns no later than its suspend-time hint).
-__global__ void wait_check_kernel(unsigned *flags, int tries) {
-    __shared__ uint64_t bar;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && !mbar_wait_sleep(&bar, 0u, flags, 0u, tries, SLEEP_NS)) atomicOr(flags, ILE_FLAG_TIMEOUT);
-}
-
-}  // namespace
-
-cudaError_t ile_launch_wait_check(unsigned *flags, double timeout_s, cudaStream_t st) {
-    const double t = timeout_s * 1e9 / SLEEP_NS;
-    const int tries = t < 1.0 ? 1 : t > 1e6 ? 1000000 : (int)t;
-    wait_check_kernel<<<1, 32, 0, st>>>(flags, tries);
-    return cudaGetLastError();
-}
-
 int ile_tc2_tile() { return TILE; }
 
 size_t ile_tc2_batch_smem(int LK, int LM, int LKP, int NB) { return tc2_smem(LK, LM, LKP, NB); }

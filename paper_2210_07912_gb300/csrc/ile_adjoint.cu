@@ -90,7 +90,7 @@ struct MainSmem {
 };
 
 template <int NS>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     adj_main_kernel(const __grid_constant__ PointParams pp, const float *__restrict__ Qp, const float4 *__restrict__ UV,
                     IleScratch s, const int *__restrict__ perm, const double *__restrict__ samples,
                     const double *__restrict__ g_lnL, int64_t N, float *__restrict__ pig,
@@ -787,7 +787,7 @@ cudaError_t ile_launch_grad_main(const PointParams &pp, const float *Qp, const f
                                  const int *perm, const double *samples, const double *g_lnL, int64_t N, float *pig,
                                  double *g_samples, double *lnl_out, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
-    if (pp.Nt <= 512) return launch_main<64>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, g_samples, lnl_out, st);
+    if (pp.Nt <= 256) return launch_main<64>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, g_samples, lnl_out, st);
     return launch_main<32>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, g_samples, lnl_out, st);
 }
 

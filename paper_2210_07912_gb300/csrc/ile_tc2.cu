@@ -4,8 +4,9 @@
 //
 //   16 math warps: warp w serves TMEM lane quadrant q = w % 4 (samples 32q .. 32q+31 of the
 //   tile) and bin group g = w / 4, so each sample has four threads (g = 0..3):
-//     * S1/S2: every thread of a sample forms the geometry (F_k, window start i0_k + w_k) and a
-//       quarter of the harmonics Y_lm (compile-time powers per (l, m)); the four threads share
+//     * S1/S2: the four threads of a sample read its geometry (F_k, window start i0_k + w_k,
+//       staged by the prefetch warp) and form a quarter of the harmonics Y_lm each (compile-time
+//       powers per (l, m)); the four threads share
 //       the K x KC chunks of the sample's coefficients c_klm = (D_ref/D) F_k Y_lm, split hi/lo
 //       (BF16), written as the MMA A operand in shared memory (K index 2a + {Re, Im} of mode a,
 //       as in the split Q rows);
@@ -23,12 +24,13 @@
 //   warp 16, lane 0 (MMA warp): issue 3 x KP/16 tcgen05.mma (hi*hi + hi*lo + lo*hi, kind::f16,
 //   FP32 accumulation) per job into one of three TMEM accumulator buffers;
 //   warp 18 (prefetch warp): gathers the next tile's sample parameters through the sort
-//   permutation into shared memory while the current tile is in flight.
+//   permutation and computes their geometry (S1) into shared memory while the current tile is in
+//   flight.
 //
 // Hand-offs are mbarriers: bfull/bempty (B ring), tfull/tempty (TMEM buffers), aready (A operand
 // and the tile's column ranges written; waited on by all roles), tdone (per-thread log-sum-exp
-// partials written), sready (sample parameters staged; the prefetch warp refills the stage once
-// yready shows that every math thread has read it).  Jobs are enumerated identically by all
+// partials written), sready (geometry staged; the prefetch warp refills the stage once yready
+// shows that every math thread has read it).  Jobs are enumerated identically by all
 // roles: the quadratic-term jobs (copied before the tile is ready), then (chunk, detector,
 // window).  A tile whose column spread does not fit one window is covered by overlapping windows
 // of 128 columns, each sample reading the single window that holds all the columns it needs;
@@ -181,10 +183,11 @@ __device__ __forceinline__ const Tc2Point &work_item(const Tc2Point &one, const 
 // Shared-memory layout (LK detectors, LKC 16-byte K-chunks: the point's own sizes for a
 // single-point launch, the largest of the batch otherwise):
 //   A [LK][2][LKC][TILE] | B [NB][2][LKC][NWIN] | rows [NMATH][RSTRIDE] | aq_s [NMATH] | ls_s [NMATH]
-//   | stg [7][TILE] (FP64)
+//   | geo [14][TILE]
 // A math thread's row holds the two 16-column TMEM blocks its bins need; aq_s and ls_s its share
-// of the quadratic term and its partial log-sum-exp; stg the tile's sample parameters, gathered
-// through the sort permutation by the prefetch warp while the previous tile is in flight.  Before
+// of the quadratic term and its partial log-sum-exp; geo the tile's per-sample geometry (antenna
+// factors, window starts, iota, phi), computed by the prefetch warp from the parameters it gathers
+// through the sort permutation while the previous tile is in flight.  Before
 // the job loop the rows area holds the tile's harmonics table y [M][TILE] (float2).
 template <bool BATCH, bool DM>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float *rows = reinterpret_cast<float *>(B + (size_t)NB * 2 * LKC * NWIN);         // [NMATH][RSTRIDE]
     float *aq_s = rows + RSTRIDE * NMATH;                                             // [NMATH]
     float2 *ls_s = reinterpret_cast<float2 *>(aq_s + NMATH);                           // [NMATH]
-    double *stg = reinterpret_cast<double *>(ls_s + NMATH);                            // [7][TILE]
+    float *geo = reinterpret_cast<float *>(ls_s + NMATH);                              // [14][TILE]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -279,17 +282,50 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             int64_t tile;
             const Tc2Point &pt = work_item<BATCH>(one, pts, items, it, tile);
+            const PointParams &pp = pt.pp;
             const int64_t N = pt.N;
-            int64_t src[TILE / 32];
-#pragma unroll
+            // S1 for the tile's samples (rows i * 32 + lane): antenna factors times D_ref / D (1 in the
+            // distance-marginalised mode) and fractional window starts, staged as geo[14][TILE]:
+            // F_r (4), F_i (4), x0 (4), iota, phi.  Invalid rows repeat the tile's first sample.
+#pragma unroll 1
             for (int i = 0; i < TILE / 32; i++) {
-                const int64_t p = tile * TILE + i * 32 + lane;
-                src[i] = pt.perm[p < N ? p : tile * TILE];
+                const int r = i * 32 + lane;
+                const int64_t p = tile * TILE + r;
+                const bool valid = p < N;
+                const int64_t src = pt.perm[valid ? p : tile * TILE];
+                double th[ILE_NDIM];
+                bool finite = true;
+#pragma unroll
+                for (int d = 0; d < ILE_NDIM; d++) {
+                    th[d] = pt.samples[(int64_t)d * N + src];
+                    finite = finite && isfinite(th[d]);
+                }
+                if (!finite || th[5] <= 0.0) {
+                    if (valid) atomicOr(flags, ILE_FLAG_NONFINITE);
+                    th[0] = th[1] = th[2] = th[3] = th[4] = th[6] = 0.0;
+                    th[5] = 1.0;
+                }
+                const float scale = DM ? 1.f : pp.d_ref / (float)th[5];
+                float Fr[ILE_MAX_DET], Fi[ILE_MAX_DET], x0[ILE_MAX_DET];
+                ile_sample_geometry(pp, (float)th[0], (float)th[1], (float)th[2], (float)th[6], Fr, Fi, x0);
+                bool in_range = true;
+#pragma unroll
+                for (int k = 0; k < ILE_MAX_DET; k++) {
+                    const float fl = floorf(x0[k]);
+                    in_range = in_range && (k >= pp.K || (fl >= 0.f && fl + (float)pp.Nt <= (float)(pp.T_ext - 1)));
+                }
+                if (!in_range && valid) atomicOr(flags, ILE_FLAG_RANGE);
+#pragma unroll
+                for (int k = 0; k < ILE_MAX_DET; k++) {
+                    const bool on = k < pp.K;
+                    geo[k * TILE + r] = on ? scale * Fr[k] : 0.f;
+                    geo[(4 + k) * TILE + r] = on ? scale * Fi[k] : 0.f;
+                    // a sample outside the series gets a harmless placement; the call reports ILE_E_RANGE
+                    geo[(8 + k) * TILE + r] = on && in_range ? x0[k] : 0.f;
+                }
+                geo[12 * TILE + r] = (float)th[3];
+                geo[13 * TILE + r] = (float)th[4];
             }
-#pragma unroll
-            for (int i = 0; i < TILE / 32; i++)
-#pragma unroll
-                for (int d = 0; d < ILE_NDIM; d++) stg[d * TILE + i * 32 + lane] = pt.samples[(int64_t)d * N + src[i]];
             mbar_arrive(&sm.sready);
         }
         if (failed) atomicOr(flags, ILE_FLAG_TIMEOUT);
@@ -362,52 +398,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             double *__restrict__ out = pt.out;
             const int64_t p = tile * TILE + row;
             const bool valid = p < N;
-            // ---- S1/S2: geometry, harmonics, coefficients (parameters staged by the prefetch warp)
+            // ---- S1/S2: geometry (staged by the prefetch warp), harmonics, coefficients
             if (!warp_wait(&sm.sready, tiles_done & 1u, flags)) {
                 failed = true;
                 break;
             }
-            double th[ILE_NDIM];
-            bool finite = true;
-#pragma unroll
-            for (int d = 0; d < ILE_NDIM; d++) {
-                th[d] = stg[d * TILE + row];
-                finite = finite && isfinite(th[d]);
-            }
-            if (!finite || th[5] <= 0.0) {
-                if (valid && g == 0) atomicOr(flags, ILE_FLAG_NONFINITE);
-                th[0] = th[1] = th[2] = th[3] = th[4] = th[6] = 0.0;
-                th[5] = 1.0;
-            }
-            // distance-marginalised mode: coefficients and quadratic term at D = D_ref
-            const float scale = DM ? 1.f : pp.d_ref / (float)th[5];
-            float Fr[ILE_MAX_DET], Fi[ILE_MAX_DET], x0[ILE_MAX_DET];
-            ile_sample_geometry(pp, (float)th[0], (float)th[1], (float)th[2], (float)th[6], Fr, Fi, x0);
+            float Fr[ILE_MAX_DET], Fi[ILE_MAX_DET];  // antenna factors times D_ref / D
             int i0[ILE_MAX_DET];
             float wt[ILE_MAX_DET];
-            bool in_range = true;
 #pragma unroll
             for (int k = 0; k < ILE_MAX_DET; k++) {
-                const float fl = floorf(x0[k]);
-                in_range = in_range && (k >= K || (fl >= 0.f && fl + (float)Nt <= (float)(pp.T_ext - 1)));
+                Fr[k] = geo[k * TILE + row];
+                Fi[k] = geo[(4 + k) * TILE + row];
+                const float x0 = geo[(8 + k) * TILE + row];
+                const float fl = floorf(x0);
                 i0[k] = (int)fl;
-                wt[k] = x0[k] - fl;
+                wt[k] = x0 - fl;
             }
-            if (!in_range) {
-                if (valid && g == 0) atomicOr(flags, ILE_FLAG_RANGE);
-#pragma unroll
-                for (int k = 0; k < ILE_MAX_DET; k++) {
-                    i0[k] = 0;
-                    wt[k] = 0.f;
-                }
-            }
+            const float iota = geo[12 * TILE + row], phi = geo[13 * TILE + row];
             // harmonics: thread g forms modes a = g, g + 4, ... into the shared y table (which
             // reuses the rows area: every thread has passed the previous tile's tdone)
             float2 *ys = reinterpret_cast<float2 *>(rows);  // [M][TILE]
             {
                 float cpow[9], spow[9], er[5], ei[5];
-                ile_half_angle_powers((float)th[3], cpow, spow);
-                ile_phase_powers((float)th[4], er, ei);
+                ile_half_angle_powers(iota, cpow, spow);
+                ile_phase_powers(phi, er, ei);
 #pragma unroll 1
                 for (int a = g; a < M; a += NGRP) {
                     float yr, yi;
@@ -430,8 +445,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
 #pragma unroll 1
                 for (int t = g; t < K * KC; t += NGRP) {
-                    const float fr = scale * (k == 0 ? Fr[0] : k == 1 ? Fr[1] : k == 2 ? Fr[2] : Fr[3]);
-                    const float fi = scale * (k == 0 ? Fi[0] : k == 1 ? Fi[1] : k == 2 ? Fi[2] : Fi[3]);
+                    const float fr = k == 0 ? Fr[0] : k == 1 ? Fr[1] : k == 2 ? Fr[2] : Fr[3];
+                    const float fi = k == 0 ? Fi[0] : k == 1 ? Fi[1] : k == 2 ? Fi[2] : Fi[3];
                     float cv[8];
 #pragma unroll
                     for (int e = 0; e < 8; e += 2) {
@@ -509,8 +524,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tmem_ld32(tmem + tb * NWIN + lane_addr + (uint32_t)(32 * g), r);
                 fence_before();
                 mbar_arrive(&sm.tempty[tb]);
-                const float fr = scale * (kq == 0 ? Fr[0] : kq == 1 ? Fr[1] : kq == 2 ? Fr[2] : Fr[3]);
-                const float fi = scale * (kq == 0 ? Fi[0] : kq == 1 ? Fi[1] : kq == 2 ? Fi[2] : Fi[3]);
+                const float fr = kq == 0 ? Fr[0] : kq == 1 ? Fr[1] : kq == 2 ? Fr[2] : Fr[3];
+                const float fi = kq == 0 ? Fi[0] : kq == 1 ? Fi[1] : kq == 2 ? Fi[2] : Fi[3];
                 // component of c_b this block pairs with: Re c_b = fr yr - fi yi, Im c_b = fr yi + fi yr
                 // (block 3 enters with a minus sign: Re(c^T w) = Re c . Re w - Im c . Im w)
                 const float ca = g == 1 ? fi : g == 3 ? -fi : fr;
@@ -731,7 +746,7 @@ size_t tc2_smem(int K, int M, int KP, int NB) {
     const int KC = KP / 8;
     (void)M;  // the harmonics table (8 M TILE bytes <= 21.5 KB) fits in the rows area
     return (size_t)16 * K * 2 * KC * TILE + (size_t)16 * NB * 2 * KC * NWIN + sizeof(float) * RSTRIDE * NMATH +
-           sizeof(float) * NMATH + sizeof(float2) * NMATH + sizeof(double) * ILE_NDIM * TILE;
+           sizeof(float) * NMATH + sizeof(float2) * NMATH + sizeof(float) * 14 * TILE;
 }
 static_assert(8 * ILE_MAX_MODES * TILE <= 4 * RSTRIDE * NMATH, "y table must fit in the rows area");
 

@@ -292,9 +292,10 @@ def dmarg_bench(ile, point, cfg, N, local, stream, flush, prec, steps=20):
             "table_build_s": t_tables, "ln_L_marg": res["ln_L"], "sigma_ln": res["sigma_ln"]}
 
 
-def adjoint_bench(ile, S, local, stream, flush, steps=10):
+def adjoint_bench(ile, S, local, stream, flush, steps=10, prec="bf16x3"):
     """Gradient of ln L_marg-style weighted sums: ile_eval_grad over 2^18 samples of the
-    3-detector, 21-mode, 512-bin point, all outputs (theta, Q, U, V), FP32 with FP64 sums."""
+    3-detector, 21-mode, 512-bin point, all outputs (theta, Q, U, V), FP64 sums.  prec bf16x3: the
+    data term comes from the fused tensor-core forward kernel; fp32: recomputed on CUDA cores."""
     import torch
     point = S.workload_point(S.GRAD)
     N = S.WORKLOADS[S.GRAD]["n_samples"]
@@ -305,7 +306,7 @@ def adjoint_bench(ile, S, local, stream, flush, steps=10):
     gQ = torch.empty((K, M, T, 2), dtype=torch.float64, device="cuda")
     gU = torch.empty((K, M, M, 2), dtype=torch.float64, device="cuda")
     gV = torch.empty_like(gU)
-    ctx = ile.Context(local, stream, "fp32")
+    ctx = ile.Context(local, stream, prec)
     ctx.set_data(point)
     for _ in range(3):
         ctx.eval_grad_device(th, g, gs, gQ, gU, gV)
@@ -330,7 +331,9 @@ def adjoint_bench(ile, S, local, stream, flush, steps=10):
     return {"workload": "gradient of sum_n g_n lnL_t(n) w.r.t. theta (7 x 2^18), Q, U, V: H1/L1/V1, 21 modes, "
                         "N_t=512, 2^18 samples", "value": N * steps / (ms / 1e3), "unit": UNIT,
             "ms_per_call": ms / steps, "stage_ms_per_call": {k: v[0] / steps for k, v in prof.items() if v[1]},
-            "algorithmic_tflops": flops / (ms / steps / 1e3) / 1e12, "arithmetic": "fp32 CUDA cores, fp64 sums"}
+            "algorithmic_tflops": flops / (ms / steps / 1e3) / 1e12,
+            "arithmetic": ("data term from the fused BF16x3 tensor-core kernel, " if prec == "bf16x3" else "") +
+                          "fp32 CUDA cores, fp64 sums", "precision": prec}
 
 
 def main():
@@ -487,7 +490,7 @@ def main():
             line["cpu_baseline"] = cpu_baseline(point)
             line["error_vs_oracle"] = oracle_error(ctx, point)
         if not args.no_adjoint:
-            line["adjoint"] = adjoint_bench(ile, S, local, stream, flush)
+            line["adjoint"] = adjoint_bench(ile, S, local, stream, flush, prec=args.prec)
         if not args.no_dmarg:
             line["distance_marginalised"] = dmarg_bench(ile, point, cfg, N, local, stream, flush, args.prec)
         if not args.no_batch:

@@ -18,8 +18,9 @@
 // delays dt_k(ra, dec).  The coefficient stage is recomputed, never stored across calls.
 //
 // Kernels (one call):
-//   adj_main   one CTA per tile of NS samples (in delay-sorted order): recomputes D(n, j) with an
-//              FP32 register-blocked GEMM per 64-column chunk (as the plain forward), takes the
+//   adj_main   one CTA per tile of NS samples (in delay-sorted order): takes D(n, j) from the
+//              fused BF16x3 forward kernel (BF16x3 contexts) or recomputes it with an FP32
+//              register-blocked GEMM per 64-column chunk (as the plain forward), takes the
 //              window softmax, then per detector a second chunked GEMM
 //              [2 NS x 64] x [64 x 2M] gives E and the slope sums; a thread per sample finishes
 //              the chain rule and writes g_theta.  pi * g_n goes to HBM for dQ.
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     adj_main_kernel(const __grid_constant__ PointParams pp, const float *__restrict__ Qp, const float4 *__restrict__ UV,
                     IleScratch s, const int *__restrict__ perm, const double *__restrict__ samples,
                     const double *__restrict__ g_lnL, int64_t N, float *__restrict__ pig,
-                    double *__restrict__ g_samples, double *__restrict__ lnl_out) {
+                    const float *__restrict__ Din, double *__restrict__ g_samples, double *__restrict__ lnl_out) {
     constexpr int RS = NS / 16;  // samples per thread in both GEMM micro-tiles
     constexpr int PLD = NS + 4;
     constexpr int YLD = 4 * ILE_MAX_MODES + 1;
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     const int64_t n0 = (int64_t)blockIdx.x * NS;
     const int ns = (int)min((int64_t)NS, N - n0);
 
-    for (int i = tid; i < NS * Nt; i += 256) Ds[i] = 0.f;
+    for (int i = tid; i < NS * Nt; i += 256) Ds[i] = (Din && i < ns * Nt) ? Din[n0 * Nt + i] : 0.f;
 
     auto load_detector = [&](int k) {
         if (tid < NS) {
@@ -166,6 +167,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
             lo_s[k] = lo;
             hi_s[k] = hi;
         }
+        if (Din) continue;  // D(n, j) came from the tensor-core forward kernel
         const int cend = hi + Nt;
         for (int c0 = lo; c0 <= cend; c0 += TCOL) {
             __syncthreads();
@@ -754,14 +756,14 @@ __global__ void adj_guv_reduce_kernel(int K, int M, int nblk, const float *__res
 
 template <int NS>
 cudaError_t launch_main(const PointParams &pp, const float *Qp, const float *UV, IleScratch s, const int *perm,
-                        const double *samples, const double *g, int64_t N, float *pig, double *g_samples,
-                        double *lnl, cudaStream_t st) {
+                        const double *samples, const double *g, int64_t N, float *pig, const float *Din,
+                        double *g_samples, double *lnl, cudaStream_t st) {
     const size_t smem = sizeof(float) * MainSmem<NS>::floats(pp.Nt) + 16;
     cudaError_t e = cudaFuncSetAttribute(adj_main_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (N + NS - 1) / NS;
     adj_main_kernel<NS><<<(unsigned)blocks, 256, smem, st>>>(pp, Qp, (const float4 *)UV, s, perm, samples, g, N, pig,
-                                                             g_samples, lnl);
+                                                             Din, g_samples, lnl);
     return cudaGetLastError();
 }
 
@@ -785,10 +787,11 @@ int ile_grad_uv_blocks(int64_t N, int n_sm) {
 
 cudaError_t ile_launch_grad_main(const PointParams &pp, const float *Qp, const float *UV, IleScratch s,
                                  const int *perm, const double *samples, const double *g_lnL, int64_t N, float *pig,
-                                 double *g_samples, double *lnl_out, cudaStream_t st) {
+                                 const float *Din, double *g_samples, double *lnl_out, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
-    if (pp.Nt <= 256) return launch_main<64>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, g_samples, lnl_out, st);
-    return launch_main<32>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, g_samples, lnl_out, st);
+    if (pp.Nt <= 256)
+        return launch_main<64>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, Din, g_samples, lnl_out, st);
+    return launch_main<32>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, Din, g_samples, lnl_out, st);
 }
 
 cudaError_t ile_launch_grad_q(const PointParams &pp, const float *pig, IleScratch s, int64_t N, int nsplit,

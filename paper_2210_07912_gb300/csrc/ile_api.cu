@@ -279,8 +279,8 @@ ile_status run_eval(ile_ctx *ctx, const double *dsamples, int64_t N, double *dou
         }
         StageScope t(ctx, 2);
         CK(ile_launch_tc2(ctx->pp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ile_tc_tpad(ctx->pp.T_ext),
-                          ile_tc_kpad(prec, ctx->pp.M), ctx->UV, dsamples, ctx->perm, N, dout, full_grid, ctx->flags,
-                          ctx->stream));
+                          ile_tc_kpad(prec, ctx->pp.M), ctx->UV, dsamples, ctx->perm, N, dout, nullptr, full_grid,
+                          ctx->flags, ctx->stream));
         return ILE_OK;
     }
     {
@@ -315,10 +315,17 @@ ile_status run_grad(ile_ctx *ctx, const double *dsamples, const double *dg, int6
     if (st != ILE_OK) return st;
     const PointParams &pp = ctx->pp;
     if (!ctx->n_sm) CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
+    // BF16x3 contexts take the data term D(n, j) from the fused tensor-core kernel (written into
+    // the pi buffer, which the adjoint then overwrites with g * pi) instead of recomputing it
+    const bool tc2_fwd = ctx->prec == ILE_PREC_BF16X3 && (g_theta || gQ || lnl);
     float *pig = nullptr;
-    if (gQ) {
+    if (gQ || tc2_fwd) {
         CK(ensure_bytes(ctx, &ctx->pig, &ctx->pig_bytes, sizeof(float) * (size_t)N * pp.Nt));
         pig = ctx->pig;
+    }
+    if (tc2_fwd) {
+        st = ensure_tc_operands(ctx, ILE_PREC_BF16X3);
+        if (st != ILE_OK) return st;
     }
     const int nsplit = ile_grad_q_splits(pp, N, ctx->n_sm);
     const int nblk = ile_grad_uv_blocks(N, ctx->n_sm);
@@ -331,10 +338,14 @@ ile_status run_grad(ile_ctx *ctx, const double *dsamples, const double *dg, int6
         CK(ile_launch_sort(pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));
         CK(ile_launch_prep(pp, ctx->UV, dsamples, ctx->perm, N, ctx->s, ctx->flags, ctx->stream));
     }
-    StageScope t(ctx, 5, 1 + (gQ ? 2 : 0) + ((gU || gV) ? 2 : 0));
+    StageScope t(ctx, 5, 1 + (tc2_fwd ? 1 : 0) + (gQ ? 2 : 0) + ((gU || gV) ? 2 : 0));
+    if (tc2_fwd)
+        CK(ile_launch_tc2(pp, ctx->Qtc[ILE_PREC_BF16X3][0], ctx->Qtc[ILE_PREC_BF16X3][1], ile_tc_tpad(pp.T_ext),
+                          ile_tc_kpad(ILE_PREC_BF16X3, pp.M), ctx->UV, dsamples, ctx->perm, N, nullptr, pig, 2,
+                          ctx->flags, ctx->stream));
     if (g_theta || gQ || lnl)
-        CK(ile_launch_grad_main(pp, ctx->Qp, ctx->UV, ctx->s, ctx->perm, dsamples, dg, N, pig, g_theta, lnl,
-                                ctx->stream));
+        CK(ile_launch_grad_main(pp, ctx->Qp, ctx->UV, ctx->s, ctx->perm, dsamples, dg, N, pig,
+                                tc2_fwd ? pig : nullptr, g_theta, lnl, ctx->stream));
     if (gQ) CK(ile_launch_grad_q(pp, pig, ctx->s, N, nsplit, ctx->gq_part, gQ, ctx->stream));
     if (gU || gV) CK(ile_launch_grad_uv(pp, dsamples, dg, N, nblk, ctx->guv_part, gU, gV, ctx->stream));
     return ILE_OK;

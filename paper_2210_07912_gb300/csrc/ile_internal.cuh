@@ -306,6 +306,7 @@ struct Tc2Point {
     const double *samples;  // SoA [7][N]
     const int *perm;        // [N] processing order -> caller index
     double *out;            // [N]
+    float *grid_f;          // grid mode 2: data term D(n, j) in processing order [N][N_t]
     int64_t N;
     int TP, KP;
 };
@@ -339,15 +340,19 @@ cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp
                                 void *lo, cudaStream_t st);
 cudaError_t ile_launch_tc(int prec, const PointParams &pp, const void *hi, const void *lo, IleScratch s,
                           const int *perm, int64_t N, double *out, int full_grid, unsigned *flags, cudaStream_t st);
+// full_grid 0: lnL_t into out (caller order); 1: the grid lnL(n, j) into out (caller order);
+// 2: the data term D(n, j) in FP32 into grid_f, rows in processing (sorted) order
 cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo, int TP, int KP, const float *UV,
-                           const double *samples, const int *perm, int64_t N, double *out, int full_grid,
-                           unsigned *flags, cudaStream_t st);
+                           const double *samples, const int *perm, int64_t N, double *out, float *grid_f,
+                           int full_grid, unsigned *flags, cudaStream_t st);
 // adjoint (ile_adjoint.cu)
 int ile_grad_q_splits(const PointParams &pp, int64_t N, int n_sm);
 int ile_grad_uv_blocks(int64_t N, int n_sm);
+// Din: the data term D(n, j) in processing order (from ile_launch_tc2, grid mode 2), or NULL to
+// recompute it on CUDA cores
 cudaError_t ile_launch_grad_main(const PointParams &pp, const float *Qp, const float *UV, IleScratch s,
                                  const int *perm, const double *samples, const double *g_lnL, int64_t N, float *pig,
-                                 double *g_samples, double *lnl_out, cudaStream_t st);
+                                 const float *Din, double *g_samples, double *lnl_out, cudaStream_t st);
 cudaError_t ile_launch_grad_q(const PointParams &pp, const float *pig, IleScratch s, int64_t N, int nsplit,
                               float *part, double *gQ, cudaStream_t st);
 cudaError_t ile_launch_grad_uv(const PointParams &pp, const double *samples, const double *g_lnL, int64_t N, int nblk,

@@ -569,7 +569,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     for (int jj = 0; jj < JG; jj++)
                         if (jbeg + jj < Jc) D[jj] = ile_dmarg_lnF(pp.dm, dq, D[jj]);
                 }
-                if (full_grid) {
+                if (full_grid == 2) {
+                    if (valid) {
+                        float *o = pt.grid_f + p * Nt + j0 + jbeg;
+#pragma unroll
+                        for (int jj = 0; jj < JG; jj++)
+                            if (jbeg + jj < Jc) o[jj] = D[jj];
+                    }
+                } else if (full_grid) {
                     if (valid) {
                         const double A_n = DM ? 0.0
                                               : (double)(aq_s[q4 * 32 + lane] + aq_s[128 + q4 * 32 + lane] +
@@ -762,8 +769,8 @@ int sm_count() {
 }  // namespace
 
 cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo, int TP, int KP, const float *UV,
-                           const double *samples, const int *perm, int64_t N, double *out, int full_grid,
-                           unsigned *flags, cudaStream_t st) {
+                           const double *samples, const int *perm, int64_t N, double *out, float *grid_f,
+                           int full_grid, unsigned *flags, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     int NB = NBMAX;
     while (NB > 2 && tc2_smem(pp.K, pp.M, KP, NB) > SMEM_LIMIT) NB--;
@@ -784,6 +791,7 @@ cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo
     one.samples = samples;
     one.perm = perm;
     one.out = out;
+    one.grid_f = grid_f;
     one.N = N;
     one.TP = TP;
     one.KP = KP;

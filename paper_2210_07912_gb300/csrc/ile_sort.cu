@@ -55,40 +55,47 @@ __global__ void __launch_bounds__(256) key_count_kernel(const __grid_constant__ 
     atomicAdd(&count[key], 1);
 }
 
-// Exclusive scan of NKEY counts in one block of 1024 threads (NKEY / 1024 entries per thread).
+// Exclusive scan of NKEY counts in one block of 1024 threads: warp w scans the contiguous segment
+// [w * SEG, (w + 1) * SEG) in 32-element rows read and written coalesced (lane l holds element
+// i * 32 + l of its segment), after a scan of the 32 segment totals.
+constexpr int SEG = NKEY / 32;
 static_assert(NKEY % 1024 == 0, "scan layout");
 // (one block per point in the batched form: block b scans count + b * NKEY)
 __global__ void __launch_bounds__(1024) scan_kernel(int *__restrict__ count) {
-    constexpr int PER = NKEY / 1024;
+    constexpr int ROWS = SEG / 32;
     __shared__ int warp_tot[32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    int *c = count + (size_t)blockIdx.x * NKEY + t * PER;
-    int local = 0;
-#pragma unroll 4
-    for (int i = 0; i < PER; i++) local += c[i];
-    int incl = local;
-    for (int o = 1; o < 32; o <<= 1) {
-        int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
+    int *c = count + (size_t)blockIdx.x * NKEY + (size_t)warp * SEG;
+    int v[ROWS];
+    int tot = 0;
+#pragma unroll
+    for (int i = 0; i < ROWS; i++) {
+        v[i] = c[i * 32 + lane];
+        tot += v[i];
     }
-    if (lane == 31) warp_tot[warp] = incl;
+    for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) warp_tot[warp] = tot;
     __syncthreads();
     if (warp == 0) {
-        int v = warp_tot[lane];
-        int vi = v;
+        const int x = warp_tot[lane];
+        int incl = x;
         for (int o = 1; o < 32; o <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, vi, o);
-            if (lane >= o) vi += u;
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
         }
-        warp_tot[lane] = vi - v;
+        warp_tot[lane] = incl - x;  // exclusive: counts before segment `lane`
     }
     __syncthreads();
-    int run = warp_tot[warp] + incl - local;
-#pragma unroll 4
-    for (int i = 0; i < PER; i++) {
-        int v = c[i];
-        c[i] = run;
-        run += v;
+    int carry = warp_tot[warp];
+#pragma unroll
+    for (int i = 0; i < ROWS; i++) {
+        int incl = v[i];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        c[i * 32 + lane] = carry + incl - v[i];
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
 }
 

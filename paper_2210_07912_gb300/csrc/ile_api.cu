@@ -586,7 +586,9 @@ ile_status ile_prepare_point(int n_det, int n_modes, const int *lm, const double
             }
     }
     // real form of U_k and V_k for the quadratic-term MMA: operand row r = 2a + {0: Re c_a, 1: Im c_a};
-    // column blocks of 32: Re z_b, Im z_b (z = U c), Re w_b, Im w_b (w = V c)
+    // output column 32 (b % 4) + 4 (b / 4) + p holds, for mode b, p = 0: Re z_b, 1: Im z_b
+    // (z = U c), 2: Re w_b, 3: Im w_b (w = V c), so that the 32-column block g has everything of
+    // the modes b = g, g + 4, ... (the modes math thread g of a sample forms the harmonics of)
     const int KPq = (R + 15) & ~15;
     quad.assign((size_t)K * KPq * ILE_QCOLS, 0.f);
     for (int k = 0; k < K; k++)
@@ -596,14 +598,15 @@ ile_status ile_prepare_point(int n_det, int n_modes, const int *lm, const double
                 const double *v = V + 2 * (((size_t)k * M + b) * M + a);  // V_ba
                 float *re = &quad[((size_t)k * KPq + 2 * a) * ILE_QCOLS];
                 float *im = &quad[((size_t)k * KPq + 2 * a + 1) * ILE_QCOLS];
-                re[b] = (float)u[0];
-                im[b] = (float)-u[1];
-                re[32 + b] = (float)u[1];
-                im[32 + b] = (float)u[0];
-                re[64 + b] = (float)v[0];
-                im[64 + b] = (float)-v[1];
-                re[96 + b] = (float)v[1];
-                im[96 + b] = (float)v[0];
+                const int c0 = 32 * (b % 4) + 4 * (b / 4);
+                re[c0] = (float)u[0];
+                im[c0] = (float)-u[1];
+                re[c0 + 1] = (float)u[1];
+                im[c0 + 1] = (float)u[0];
+                re[c0 + 2] = (float)v[0];
+                im[c0 + 2] = (float)-v[1];
+                re[c0 + 3] = (float)v[1];
+                im[c0 + 3] = (float)v[0];
             }
     pp_out = pp;
     return ILE_OK;

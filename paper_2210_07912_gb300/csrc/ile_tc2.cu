@@ -510,8 +510,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             __syncwarp();
 
             // ---- S4 on the tensor cores: the quadratic-term job of detector k leaves in TMEM, for
-            // this sample, z = U_k c_k and w = V_k c_k as column blocks [Re z | Im z | Re w | Im w]
-            // of 32; thread g takes block g and forms its part of c^H z + Re(c^T w)
+            // this sample, z = U_k c_k and w = V_k c_k; column 32 (b % 4) + 4 (b / 4) + {0, 1, 2, 3}
+            // holds Re z_b, Im z_b, Re w_b, Im w_b, so thread g's block covers its own modes
+            // b = g, g + 4, ... and it forms their part of c^H z + Re(c^T w)
             float aq = 0.f;
             for (int kq = 0; kq < K; kq++) {
                 const uint32_t tb = gjob % NTB;
@@ -526,16 +527,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 mbar_arrive(&sm.tempty[tb]);
                 const float fr = kq == 0 ? Fr[0] : kq == 1 ? Fr[1] : kq == 2 ? Fr[2] : Fr[3];
                 const float fi = kq == 0 ? Fi[0] : kq == 1 ? Fi[1] : kq == 2 ? Fi[2] : Fi[3];
-                // component of c_b this block pairs with: Re c_b = fr yr - fi yi, Im c_b = fr yi + fi yr
-                // (block 3 enters with a minus sign: Re(c^T w) = Re c . Re w - Im c . Im w)
-                const float ca = g == 1 ? fi : g == 3 ? -fi : fr;
-                const float cb = g == 1 ? fr : g == 3 ? -fr : -fi;
+                // Re c_b = fr yr - fi yi, Im c_b = fr yi + fi yr;
+                // Re(conj(c_b) z_b) + Re(c_b w_b) = Re c_b (Re z_b + Re w_b) + Im c_b (Im z_b - Im w_b)
                 float part = 0.f;
 #pragma unroll
-                for (int b = 0; b < 32; b++) {
+                for (int i = 0; i < 8; i++) {
+                    const int b = g + 4 * i;
                     if (b < M) {
                         const float2 y = ys[b * TILE + row];
-                        part = fmaf(fmaf(ca, y.x, cb * y.y), __uint_as_float(r[b]), part);
+                        const float rc = fmaf(fr, y.x, -fi * y.y), ic = fmaf(fr, y.y, fi * y.x);
+                        const float zr = __uint_as_float(r[4 * i]) + __uint_as_float(r[4 * i + 2]);
+                        const float zi = __uint_as_float(r[4 * i + 1]) - __uint_as_float(r[4 * i + 3]);
+                        part = fmaf(rc, zr, fmaf(ic, zi, part));
                     }
                 }
                 aq += part;

@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------------------------ copy warp
         if (lane == 0) {
             uint32_t gcopy = 0, tiles_done = 0;
+            uint32_t bb = 0, bpar = 0;  // ring slot and phase parity of copy gcopy
             for (int64_t it = blockIdx.x; it < nitems && !failed; it += gridDim.x, tiles_done++) {
                 int64_t tile;
                 const Tc2Point &pt = work_item<BATCH>(one, pts, items, it, tile);
@@ -240,9 +241,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint4 *Qhi = reinterpret_cast<const uint4 *>(pt.Qhi);
                 const uint4 *Qlo = reinterpret_cast<const uint4 *>(pt.Qlo);
                 auto copy_job = [&](const Job &j) {
-                    const uint32_t bb = gcopy % NB;
                     // the slot is free once the MMAs of job gcopy - NB have completed
-                    if (gcopy >= (uint32_t)NB && !wait1(&sm.bempty[bb], ((gcopy / NB) - 1) & 1u, flags)) {
+                    if (gcopy >= (uint32_t)NB && !wait1(&sm.bempty[bb], bpar ^ 1u, flags)) {
                         failed = true;
                         return;
                     }
@@ -253,6 +253,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     uint4 *slot = B + (size_t)bb * 2 * LKC * NWIN;
                     bulk_g2s(slot, Qhi + src, bytes, &sm.bfull[bb]);
                     bulk_g2s(slot + (size_t)KC * NWIN, Qlo + src, bytes, &sm.bfull[bb]);
+                    if (++bb == (uint32_t)NB) {
+                        bb = 0;
+                        bpar ^= 1u;
+                    }
                 };
                 // the quadratic-term jobs come first and need no column ranges: their operands are
                 // copied before the tile's A operand and ranges are ready
@@ -333,6 +337,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------------------------ MMA warp
         if (lane == 0) {
             uint32_t gjob = 0, tiles_done = 0;
+            // ring positions and phase parities of job gjob (running, no division per job)
+            uint32_t bb = 0, bpar = 0, tb = 0, tpar = 0;
             for (int64_t it = blockIdx.x; it < nitems && !failed; it += gridDim.x, tiles_done++) {
                 int64_t tile;
                 const Tc2Point &pt = work_item<BATCH>(one, pts, items, it, tile);
@@ -344,35 +350,45 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 Det4 lo, hi;
                 tile_range(sm.wlo, sm.whi, K, lo, hi);
                 fence_after();
+                // shared-memory descriptors: A [KC][TILE rows] chunks (LBO = TILE*16, SBO = 128),
+                // B [nwr/8][KC][8] chunks (LBO = 128, SBO = KC*128); a K step of 16 advances the
+                // start address (descriptor bits 0-13, address >> 4) by 2 chunks
+                const uint64_t a0 = sdesc(smem_u32(A), TILE * 16, 128);
+                const uint64_t b0 = sdesc(smem_u32(B), 128, KC * 128);
+                const uint64_t a_det = (uint64_t)(2 * KC * TILE * 16) >> 4, a_lo = (uint64_t)(KC * TILE * 16) >> 4;
+                const uint64_t b_slot = (uint64_t)(2 * LKC * NWIN * 16) >> 4, b_lo = (uint64_t)(KC * NWIN * 16) >> 4;
+                const uint64_t a_ks = (uint64_t)(2 * TILE * 16) >> 4, b_ks = (uint64_t)(2 * 128) >> 4;
                 for (JobIter mit(Nt, K, nwcol, TQ0, lo, hi); !mit.done && !failed; mit.next(), gjob++) {
                     const Job j = mit.get();
-                    const uint32_t bb = gjob % NB, tb = gjob % NTB;
-                    if (!wait1(&sm.bfull[bb], (gjob / NB) & 1u, flags) ||
-                        (gjob >= NTB && !wait1(&sm.tempty[tb], ((gjob / NTB) - 1) & 1u, flags))) {
+                    if (!wait1(&sm.bfull[bb], bpar, flags) || (gjob >= NTB && !wait1(&sm.tempty[tb], tpar ^ 1u, flags))) {
                         failed = true;
                         break;
                     }
                     fence_after();
                     const uint32_t id = idesc(1, TILE, j.nwr);
-                    const uint32_t a_hi = smem_u32(A + (size_t)(j.k * 2 + 0) * KC * TILE);
-                    const uint32_t a_lo = smem_u32(A + (size_t)(j.k * 2 + 1) * KC * TILE);
-                    const uint32_t b_hi = smem_u32(B + (size_t)bb * 2 * LKC * NWIN);
-                    const uint32_t b_lo = smem_u32(B + (size_t)bb * 2 * LKC * NWIN + (size_t)KC * NWIN);
+                    const uint64_t ah = a0 + (uint64_t)j.k * a_det, al = ah + a_lo;
+                    const uint64_t bh = b0 + (uint64_t)bb * b_slot, bl = bh + b_lo;
                     const uint32_t d = tmem + tb * NWIN;
+                    const int nks = KP / 16;
                     uint32_t acc = 0;
                     for (int pass = 0; pass < 3; pass++) {
-                        const uint32_t ab = pass == 2 ? a_lo : a_hi;
-                        const uint32_t bs = pass == 1 ? b_lo : b_hi;
-                        for (int ks = 0; ks < KP / 16; ks++) {
-                            // A: [KC][TILE rows] chunks (LBO = TILE*16, SBO = 128);
-                            // B: [nwr/8][KC][8] chunks (LBO = 128, SBO = KC*128)
-                            mma_bf16(d, sdesc(ab + ks * 2 * TILE * 16, TILE * 16, 128),
-                                     sdesc(bs + ks * 2 * 128, 128, KC * 128), id, acc);
+                        const uint64_t ad = pass == 2 ? al : ah;
+                        const uint64_t bd = pass == 1 ? bl : bh;
+                        for (int ks = 0; ks < nks; ks++) {
+                            mma_bf16(d, ad + (uint64_t)ks * a_ks, bd + (uint64_t)ks * b_ks, id, acc);
                             acc = 1;
                         }
                     }
                     mma_commit(&sm.bempty[bb]);
                     mma_commit(&sm.tfull[tb]);
+                    if (++bb == (uint32_t)NB) {
+                        bb = 0;
+                        bpar ^= 1u;
+                    }
+                    if (++tb == (uint32_t)NTB) {
+                        tb = 0;
+                        tpar ^= 1u;
+                    }
                 }
             }
             if (failed) atomicOr(flags, ILE_FLAG_TIMEOUT);

@@ -30,12 +30,14 @@
 // Hand-offs are mbarriers: bfull/bempty (B ring), tfull/tempty (TMEM buffers), aready (A operand
 // and the tile's column ranges written; waited on by all roles), tdone (per-thread log-sum-exp
 // partials written), sready (geometry staged; the prefetch warp refills the stage once yready
-// shows that every math thread has read it).  Jobs are enumerated identically by all
-// roles: the quadratic-term jobs (copied before the tile is ready), then (chunk, detector,
-// window).  A tile whose column spread does not fit one window is covered by overlapping windows
-// of 128 columns, each sample reading the single window that holds all the columns it needs;
-// when every detector fits one window the math warps take a shorter job loop.  Every wait is bounded; on expiry the
-// kernel raises ILE_FLAG_TIMEOUT (all CTAs then stop waiting), releases its TMEM and returns.
+// shows that every math thread has read it).  The copy and math warps enumerate the jobs
+// identically (the quadratic-term jobs, copied before the tile is ready, then (chunk, detector,
+// window)); the copy warp publishes each job's detector and width with its B slot and the MMA
+// warp follows that sequence.  A tile whose column spread does not fit one window is covered by
+// overlapping windows of 128 columns, each sample reading the single window that holds all the
+// columns it needs; when every detector fits one window the math warps take a shorter job loop.
+// Every wait is bounded; on expiry the kernel raises ILE_FLAG_TIMEOUT (all CTAs then stop
+// waiting), releases its TMEM and returns.
 #include "ile_internal.cuh"
 #include "ile_tcgen05.cuh"
 
@@ -67,6 +69,7 @@ struct Sm {
     uint32_t tmem_base;
     int wlo[4][ILE_MAX_DET], whi[4][ILE_MAX_DET];
     int2 dkr[NMATH / 32][ILE_MAX_DET];  // per math warp and detector: (min, max) of i0 - tile lo
+    uint32_t jinfo[NBMAX];  // job of each B slot for the MMA warp: detector | nwr << 4 | last-of-tile << 16
 };
 
 // Register-resident per-detector value (the selects avoid dynamic indexing).
@@ -240,12 +243,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int K = pt.pp.K, Nt = pt.pp.Nt, KC = pt.KP / 8, TP = pt.TP;
                 const uint4 *Qhi = reinterpret_cast<const uint4 *>(pt.Qhi);
                 const uint4 *Qlo = reinterpret_cast<const uint4 *>(pt.Qlo);
-                auto copy_job = [&](const Job &j) {
+                auto copy_job = [&](const Job &j, bool last) {
                     // the slot is free once the MMAs of job gcopy - NB have completed
                     if (gcopy >= (uint32_t)NB && !wait1(&sm.bempty[bb], bpar ^ 1u, flags)) {
                         failed = true;
                         return;
                     }
+                    // the job as the MMA warp needs it (visible to it through bfull: the arrive
+                    // below releases this store)
+                    sm.jinfo[bb] = (uint32_t)j.k | ((uint32_t)j.nwr << 4) | (last ? 1u << 16 : 0u);
                     // one contiguous block per hi/lo: [nwr/8 groups][KC][8 columns] x 16 bytes
                     const uint32_t bytes = (uint32_t)j.nwr * KC * 16u;
                     mbar_arrive_expect_tx(&sm.bfull[bb], 2u * bytes);
@@ -262,14 +268,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 // copied before the tile's A operand and ranges are ready
                 const Det4 none{0, 0, 0, 0};
                 JobIter cit(Nt, K, nwcol, TP - ILE_QCOLS, none, none);
-                for (int q = 0; q < K && !failed; q++, cit.next(), gcopy++) copy_job(cit.get());
+                for (int q = 0; q < K && !failed; q++, cit.next(), gcopy++) copy_job(cit.get(), false);
                 if (failed) break;
                 if (!wait1(&sm.aready, tiles_done & 1u, flags)) {
                     failed = true;
                     break;
                 }
                 tile_range(sm.wlo, sm.whi, K, cit.lo, cit.hi);
-                for (; !cit.done && !failed; cit.next(), gcopy++) copy_job(cit.get());
+                while (!cit.done && !failed) {
+                    const Job j = cit.get();
+                    cit.next_from(j);
+                    copy_job(j, cit.done);
+                    gcopy++;
+                }
             }
             if (failed) atomicOr(flags, ILE_FLAG_TIMEOUT);
         }
@@ -342,13 +353,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int64_t it = blockIdx.x; it < nitems && !failed; it += gridDim.x, tiles_done++) {
                 int64_t tile;
                 const Tc2Point &pt = work_item<BATCH>(one, pts, items, it, tile);
-                const int K = pt.pp.K, Nt = pt.pp.Nt, KP = pt.KP, KC = KP / 8, TQ0 = pt.TP - ILE_QCOLS;
+                const int KP = pt.KP, KC = KP / 8;
                 if (!wait1(&sm.aready, tiles_done & 1u, flags)) {
                     failed = true;
                     break;
                 }
-                Det4 lo, hi;
-                tile_range(sm.wlo, sm.whi, K, lo, hi);
                 fence_after();
                 // shared-memory descriptors: A [KC][TILE rows] chunks (LBO = TILE*16, SBO = 128),
                 // B [nwr/8][KC][8] chunks (LBO = 128, SBO = KC*128); a K step of 16 advances the
@@ -358,15 +367,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint64_t a_det = (uint64_t)(2 * KC * TILE * 16) >> 4, a_lo = (uint64_t)(KC * TILE * 16) >> 4;
                 const uint64_t b_slot = (uint64_t)(2 * LKC * NWIN * 16) >> 4, b_lo = (uint64_t)(KC * NWIN * 16) >> 4;
                 const uint64_t a_ks = (uint64_t)(2 * TILE * 16) >> 4, b_ks = (uint64_t)(2 * 128) >> 4;
-                for (JobIter mit(Nt, K, nwcol, TQ0, lo, hi); !mit.done && !failed; mit.next(), gjob++) {
-                    const Job j = mit.get();
+                // the tile's jobs, in the order the copy warp published them (it enumerates them)
+                for (bool last = false; !last && !failed; gjob++) {
                     if (!wait1(&sm.bfull[bb], bpar, flags) || (gjob >= NTB && !wait1(&sm.tempty[tb], tpar ^ 1u, flags))) {
                         failed = true;
                         break;
                     }
                     fence_after();
-                    const uint32_t id = idesc(1, TILE, j.nwr);
-                    const uint64_t ah = a0 + (uint64_t)j.k * a_det, al = ah + a_lo;
+                    const uint32_t info = sm.jinfo[bb];
+                    const int jk = (int)(info & 15u), nwr = (int)((info >> 4) & 0xFFFu);
+                    last = (info >> 16) != 0u;
+                    const uint32_t id = idesc(1, TILE, nwr);
+                    const uint64_t ah = a0 + (uint64_t)jk * a_det, al = ah + a_lo;
                     const uint64_t bh = b0 + (uint64_t)bb * b_slot, bl = bh + b_lo;
                     const uint32_t d = tmem + tb * NWIN;
                     const int nks = KP / 16;

@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
                     const double *__restrict__ g_lnL, int64_t N, float *__restrict__ pig,
                     const float *__restrict__ Din, double *__restrict__ g_samples, double *__restrict__ lnl_out) {
     constexpr int RS = NS / 16;  // samples per thread in both GEMM micro-tiles
+    constexpr int SUB = 256 / NS;  // threads per sample in the per-sample stages (mode or pair splits)
     constexpr int PLD = NS + 4;
     constexpr int YLD = 4 * ILE_MAX_MODES + 1;
     extern __shared__ __align__(16) float smem[];
@@ -119,6 +120,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     __shared__ float Ss[ILE_MAX_DET][NS];
     __shared__ float proj[ILE_MAX_DET][6][NS];
     __shared__ int red[2][8];
+    __shared__ uint16_t pab[ILE_MAX_MODES * (ILE_MAX_MODES + 1) / 2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n0 = (int64_t)blockIdx.x * NS;
@@ -321,32 +323,47 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
                 if (tx == 0) Ss[k][nn] = sp;
             }
             __syncthreads();
-            // projections of E on the harmonics: e = sum_a conj(E_a) y_a, with y -> dy/diota, i m y
-            if (tid < ns) {
-                const int64_t src = perm ? (int64_t)perm[n0 + tid] : n0 + tid;
-                const float iota = (float)samples[3 * N + src], phi = (float)samples[4 * N + src];
-                float cpow[10], spow[10];
-                half_angle_powers10(iota, cpow, spow);
+            // projections of E on the harmonics: e = sum_a conj(E_a) y_a, with y -> dy/diota, i m y;
+            // SUB threads per sample, thread sub taking the modes a = sub, sub + SUB, ...
+            {
+                const int nn = tid / SUB, sub = tid % SUB;
                 float er = 0.f, ei = 0.f, gr = 0.f, gi = 0.f, fr = 0.f, fi = 0.f;
-                const float *E = Es + tid * (RMAX + 1);
-                for (int a = 0; a < M; a++) {
-                    float yr, yi, dr, di;
-                    sylm_and_diota(pp.mode[a], cpow, spow, phi, yr, yi, dr, di);
-                    const float Er = E[a], Ei = E[M + a], mm = (float)pp.mode[a].m;
-                    er += Er * yr + Ei * yi;
-                    ei += Er * yi - Ei * yr;
-                    gr += Er * dr + Ei * di;
-                    gi += Er * di - Ei * dr;
-                    // i m y = (-m yi, m yr)
-                    fr += mm * (-Er * yi + Ei * yr);
-                    fi += mm * (Er * yr + Ei * yi);
+                if (nn < ns) {
+                    const int64_t src = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
+                    const float iota = (float)samples[3 * N + src], phi = (float)samples[4 * N + src];
+                    float cpow[10], spow[10];
+                    half_angle_powers10(iota, cpow, spow);
+                    const float *E = Es + nn * (RMAX + 1);
+                    for (int a = sub; a < M; a += SUB) {
+                        float yr, yi, dr, di;
+                        sylm_and_diota(pp.mode[a], cpow, spow, phi, yr, yi, dr, di);
+                        const float Er = E[a], Ei = E[M + a], mm = (float)pp.mode[a].m;
+                        er += Er * yr + Ei * yi;
+                        ei += Er * yi - Ei * yr;
+                        gr += Er * dr + Ei * di;
+                        gi += Er * di - Ei * dr;
+                        // i m y = (-m yi, m yr)
+                        fr += mm * (-Er * yi + Ei * yr);
+                        fi += mm * (Er * yr + Ei * yi);
+                    }
                 }
-                proj[k][0][tid] = er;
-                proj[k][1][tid] = ei;
-                proj[k][2][tid] = gr;
-                proj[k][3][tid] = gi;
-                proj[k][4][tid] = fr;
-                proj[k][5][tid] = fi;
+#pragma unroll
+                for (int o = SUB / 2; o; o >>= 1) {
+                    er += __shfl_xor_sync(0xffffffffu, er, o);
+                    ei += __shfl_xor_sync(0xffffffffu, ei, o);
+                    gr += __shfl_xor_sync(0xffffffffu, gr, o);
+                    gi += __shfl_xor_sync(0xffffffffu, gi, o);
+                    fr += __shfl_xor_sync(0xffffffffu, fr, o);
+                    fi += __shfl_xor_sync(0xffffffffu, fi, o);
+                }
+                if (nn < ns && sub == 0) {
+                    proj[k][0][nn] = er;
+                    proj[k][1][nn] = ei;
+                    proj[k][2][nn] = gr;
+                    proj[k][3][nn] = gi;
+                    proj[k][4][nn] = fr;
+                    proj[k][5][nn] = fi;
+                }
             }
         }
     }
@@ -355,20 +372,28 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     // ---------------------------------------------------------------- epilogue: chain rule to theta
     const int P = M * (M + 1) / 2;
     for (int i = tid; i < K * P; i += 256) UVs[i] = UV[i];
-    if (tid < ns) {
-        const int64_t src = perm ? (int64_t)perm[n0 + tid] : n0 + tid;
-        float th[ILE_NDIM];
-#pragma unroll
-        for (int d = 0; d < ILE_NDIM; d++) th[d] = (float)samples[(int64_t)d * N + src];
+    // mode pairs (a <= b) in the order of the UV table
+    for (int i = tid; i < P; i += 256) {
+        int a = 0, rest = i;
+        while (rest >= M - a) rest -= M - a++;
+        pab[i] = (uint16_t)(a | ((a + rest) << 8));
+    }
+    const int nn = tid / SUB, sub = tid % SUB;  // SUB threads per sample from here on
+    if (nn < ns) {
+        const int64_t src = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
+        const float iota = (float)samples[3 * N + src], phi = (float)samples[4 * N + src];
         float cpow[10], spow[10];
-        half_angle_powers10(th[3], cpow, spow);
-        float *y = Ys + tid * YLD;
-        for (int a = 0; a < M; a++)
-            sylm_and_diota(pp.mode[a], cpow, spow, th[4], y[4 * a], y[4 * a + 1], y[4 * a + 2], y[4 * a + 3]);
+        half_angle_powers10(iota, cpow, spow);
+        float *y = Ys + nn * YLD;
+        for (int a = sub; a < M; a += SUB)
+            sylm_and_diota(pp.mode[a], cpow, spow, phi, y[4 * a], y[4 * a + 1], y[4 * a + 2], y[4 * a + 3]);
     }
     __syncthreads();
-    if (tid < ns) {
-        const int64_t src = perm ? (int64_t)perm[n0 + tid] : n0 + tid;
+    {
+        // every thread of a sample runs the preamble; the invalid rows of a ragged tile take
+        // sample 0's values and write nothing
+        const int nv = nn < ns ? nn : 0;
+        const int64_t src = perm ? (int64_t)perm[n0 + nv] : n0 + nv;
         const double gn = g_lnL[src];
         const float ra = (float)samples[src], dec = (float)samples[N + src], psi = (float)samples[2 * N + src];
         const float dist = (float)samples[5 * N + src];
@@ -399,12 +424,13 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
             vfi[ILE_MAX_DET];
 #pragma unroll
         for (int k = 0; k < ILE_MAX_DET; k++) u[k] = ui[k] = uf[k] = vr[k] = vi[k] = vir[k] = vii[k] = vfr[k] = vfi[k] = 0.f;
-        const float *y = Ys + tid * YLD;
-        int p = 0;
-        for (int a = 0; a < M; a++) {
-            const float yar = y[4 * a], yai = y[4 * a + 1], dar = y[4 * a + 2], dai = y[4 * a + 3];
-            const float ma = (float)pp.mode[a].m;
-            for (int b = a; b < M; b++, p++) {
+        const float *y = Ys + nv * YLD;
+        // thread sub takes the pairs p = sub, sub + SUB, ...
+        for (int p = sub; p < P; p += SUB) {
+            const int a = pab[p] & 0xff, b = pab[p] >> 8;
+            {
+                const float yar = y[4 * a], yai = y[4 * a + 1], dar = y[4 * a + 2], dai = y[4 * a + 3];
+                const float ma = (float)pp.mode[a].m;
                 const float ybr = y[4 * b], ybi = y[4 * b + 1], dbr = y[4 * b + 2], dbi = y[4 * b + 3];
                 const float mb = (float)pp.mode[b].m;
                 // q = conj(y_a) y_b, its iota derivative; pp = y_a y_b, its iota derivative
@@ -433,6 +459,24 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
                 }
             }
         }
+        // sums over the sample's SUB threads
+#pragma unroll
+        for (int k = 0; k < ILE_MAX_DET; k++) {
+            if (k < K) {
+#pragma unroll
+                for (int o = SUB / 2; o; o >>= 1) {
+                    u[k] += __shfl_xor_sync(0xffffffffu, u[k], o);
+                    ui[k] += __shfl_xor_sync(0xffffffffu, ui[k], o);
+                    uf[k] += __shfl_xor_sync(0xffffffffu, uf[k], o);
+                    vr[k] += __shfl_xor_sync(0xffffffffu, vr[k], o);
+                    vi[k] += __shfl_xor_sync(0xffffffffu, vi[k], o);
+                    vir[k] += __shfl_xor_sync(0xffffffffu, vir[k], o);
+                    vii[k] += __shfl_xor_sync(0xffffffffu, vii[k], o);
+                    vfr[k] += __shfl_xor_sync(0xffffffffu, vfr[k], o);
+                    vfi[k] += __shfl_xor_sync(0xffffffffu, vfi[k], o);
+                }
+            }
+        }
 
         float g_ra = 0.f, g_dec = 0.f, g_psi = 0.f, g_iota = 0.f, g_phi = 0.f, g_tc = 0.f, data = 0.f, A = 0.f;
 #pragma unroll
@@ -452,10 +496,10 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
             const float Fr_de = dot3(Xd, DX) + dot3(X, DXd) - dot3(Yd, DY) - dot3(Y, DYd);
             const float Fi_de = dot3(Xd, DY) + dot3(X, DYd) + dot3(Yd, DX) + dot3(Y, DXd);
             const float dt_ra = -dot3(pp.det_pos_c[k], n_ra), dt_de = -dot3(pp.det_pos_c[k], n_de);
-            const float er = proj[k][0][tid], ei = proj[k][1][tid];
-            const float gr = proj[k][2][tid], gi = proj[k][3][tid];
-            const float fr = proj[k][4][tid], fi = proj[k][5][tid];
-            const float S = Ss[k][tid] * pp.fs;
+            const float er = proj[k][0][nv], ei = proj[k][1][nv];
+            const float gr = proj[k][2][nv], gi = proj[k][3][nv];
+            const float fr = proj[k][4][nv], fi = proj[k][5][nv];
+            const float S = Ss[k][nv] * pp.fs;
             const float F2 = Fr * Fr + Fi * Fi, Gr = Fr * Fr - Fi * Fi, Gi = 2.f * Fr * Fi;  // |F|^2, F^2
             const float Fvr = Fr * vr[k] - Fi * vi[k], Fvi = Fr * vi[k] + Fi * vr[k];      // F v
             const float gFr = sc * er - 0.5f * sc2 * (Fr * u[k] + Fvr);
@@ -470,7 +514,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
             A += 0.25f * sc2 * (F2 * u[k] + Gr * vr[k] - Gi * vi[k]);
         }
         const float g_D = (2.f * A - data) / dist;
-        if (g_samples) {
+        if (g_samples && nn < ns && sub == 0) {
             g_samples[src] = gn * (double)g_ra;
             g_samples[N + src] = gn * (double)g_dec;
             g_samples[2 * N + src] = gn * (double)g_psi;

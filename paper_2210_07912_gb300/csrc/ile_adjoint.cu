@@ -28,6 +28,9 @@
 //   adj_guv    grid of sample splits; a thread per (a <= b) mode pair: dU, dV partials.
 //   *_reduce   FP64 sums of the partials into the caller's layouts.
 #include "ile_internal.cuh"
+#include "ile_tcgen05.cuh"
+
+using namespace ile_tc;
 
 namespace {
 
@@ -35,6 +38,24 @@ constexpr int TCOL = 64;                 // columns per chunk in adj_main
 constexpr int RMAX = 2 * ILE_MAX_MODES;  // real rows of the contraction (Re rows, then Im rows)
 constexpr int RP = 48;                   // rows padded to 3 x 16 for the backward GEMM
 constexpr int QT_LD = RP + 1;            // transposed Q chunk row stride (odd: conflict-free)
+
+// Tensor-core form of the E / slope contraction (BF16x3 contexts): per detector and 32-column
+// chunk, A = [P_E; P_D] (128 rows: the pi-weighted interpolation weights and their differences of
+// 64 samples, K = 32 columns) times B = Qp^T (N = RP rows, K-major), accumulated in TMEM over the
+// chunks; the hi/lo operands are double-buffered so that one chunk's MMAs run while the next is
+// built.
+constexpr int TC_NS = 64;                            // samples per CTA
+constexpr int TC_COLS = 32;                          // columns per chunk (two K steps of 16)
+constexpr int TC_KC = TC_COLS / 8;                   // 16-byte K chunks per chunk
+constexpr int TC_A_BYTES = TC_KC * 128 * 16;         // one of A hi / A lo
+constexpr int TC_B_BYTES = TC_KC * RP * 16;          // one of B hi / B lo
+constexpr int TC_BUF = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
+constexpr uint32_t TC_TMEM_COLS = 64;                // >= RP, power of two
+constexpr int TC_SLEEPS = 200000;                    // bounded sleeping waits (x 10 us at most)
+constexpr uint32_t TC_SLEEP_NS = 10000;
+// columns of the transposed split operand: T_ext + one chunk of zeros, so that every chunk that
+// starts at or before the last column stays inside the array
+__host__ __device__ constexpr int adj_qt_cols(int T) { return T + TC_COLS; }
 
 // d^l_{m,2}(iota) and its derivative d/diota, from the Wigner polynomial in c = cos(iota/2),
 // s = sin(iota/2): d/diota c^p s^q = (q c^(p+1) s^(q-1) - p c^(p-1) s^(q+1)) / 2.
@@ -78,32 +99,38 @@ __device__ __forceinline__ void matvec3(const float *D, const float *x, float *y
     y[2] = D[6] * x[0] + D[7] * x[1] + D[8] * x[2];
 }
 
-template <int NS>
+template <int NS, bool TC>
 struct MainSmem {
+    // row stride of the D / pi rows: odd in the tensor-core form, whose operand build reads them
+    // at per-sample offsets
+    __host__ __device__ static int ldd(int Nt) { return TC ? Nt + 1 : Nt; }
     static size_t floats(int Nt) {
-        const size_t p1 = (size_t)RMAX * TCOL + (size_t)NS * (TCOL + 1);
-        const size_t p3 = (size_t)TCOL * QT_LD + 2 * (size_t)TCOL * (NS + 4);
-        const size_t ep = (size_t)NS * (4 * ILE_MAX_MODES + 1) + (size_t)ILE_MAX_DET * (ILE_MAX_MODES * (ILE_MAX_MODES + 1) / 2) * 4;
+        const size_t p1 = TC ? 0 : (size_t)RMAX * TCOL + (size_t)NS * (TCOL + 1);
+        const size_t p3 = TC ? 2 * (size_t)TC_BUF / 4 : (size_t)TCOL * QT_LD + 2 * (size_t)TCOL * (NS + 4);
+        const size_t ep = (size_t)NS * (4 * ILE_MAX_MODES + 1) + 4 + (size_t)ILE_MAX_DET * (ILE_MAX_MODES * (ILE_MAX_MODES + 1) / 2) * 4;
         size_t u = p1 > p3 ? p1 : p3;
         u = u > ep ? u : ep;
-        return (size_t)NS * Nt + (size_t)RMAX * NS + (size_t)NS * (RMAX + 1) + u;
+        return (size_t)NS * ldd(Nt) + (size_t)RMAX * NS + (size_t)NS * (RMAX + 1) + u;
     }
 };
 
-template <int NS>
+template <int NS, bool TC>
 __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     adj_main_kernel(const __grid_constant__ PointParams pp, const float *__restrict__ Qp, const float4 *__restrict__ UV,
                     IleScratch s, const int *__restrict__ perm, const double *__restrict__ samples,
                     const double *__restrict__ g_lnL, int64_t N, float *__restrict__ pig,
-                    const float *__restrict__ Din, double *__restrict__ g_samples, double *__restrict__ lnl_out) {
+                    const float *__restrict__ Din, const uint4 *__restrict__ QThi, const uint4 *__restrict__ QTlo,
+                    unsigned *flags, double *__restrict__ g_samples, double *__restrict__ lnl_out) {
+    static_assert(!TC || NS == TC_NS, "tensor-core form: 64 samples per CTA");
     constexpr int RS = NS / 16;  // samples per thread in both GEMM micro-tiles
     constexpr int SUB = 256 / NS;  // threads per sample in the per-sample stages (mode or pair splits)
     constexpr int PLD = NS + 4;
     constexpr int YLD = 4 * ILE_MAX_MODES + 1;
     extern __shared__ __align__(16) float smem[];
     const int Nt = pp.Nt, M = pp.M, R = 2 * M, T = pp.T_ext, K = pp.K;
-    float *Ds = smem;                     // [NS][Nt]: D(n, j), then pi(n, j)
-    float *Cs = Ds + (size_t)NS * Nt;     // [RMAX][NS]
+    const int LDD = MainSmem<NS, TC>::ldd(Nt);
+    float *Ds = smem;                     // [NS][LDD]: D(n, j), then pi(n, j)
+    float *Cs = Ds + (size_t)NS * LDD;    // [RMAX][NS]
     float *Es = Cs + RMAX * NS;           // [NS][RMAX + 1]
     float *U1 = Es + NS * (RMAX + 1);     // phase-dependent region
     float *Qs = U1;                       // phase 1: [RMAX][TCOL]
@@ -121,12 +148,39 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     __shared__ float proj[ILE_MAX_DET][6][NS];
     __shared__ int red[2][8];
     __shared__ uint16_t pab[ILE_MAX_MODES * (ILE_MAX_MODES + 1) / 2];
+    __shared__ uint64_t tc_bfull[2], tc_mma[2];
+    __shared__ uint32_t tc_tmem;
+    __shared__ int tc_abort;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n0 = (int64_t)blockIdx.x * NS;
     const int ns = (int)min((int64_t)NS, N - n0);
 
-    for (int i = tid; i < NS * Nt; i += 256) Ds[i] = (Din && i < ns * Nt) ? Din[n0 * Nt + i] : 0.f;
+    uint32_t tmem = 0;
+    if constexpr (TC) {
+        if (warp == 0) tmem_alloc(&tc_tmem, TC_TMEM_COLS);
+        if (tid == 0) {
+            for (int b = 0; b < 2; b++) {
+                mbar_init(&tc_bfull[b], 1);
+                mbar_init(&tc_mma[b], 1);
+            }
+            tc_abort = 0;
+            mbar_init_fence();
+        }
+        fence_before();
+        __syncthreads();
+        fence_after();
+        tmem = tc_tmem;
+    }
+
+    if (LDD == Nt) {
+        for (int i = tid; i < NS * Nt; i += 256) Ds[i] = (Din && i < ns * Nt) ? Din[n0 * Nt + i] : 0.f;
+    } else {
+        for (int i = tid; i < NS * Nt; i += 256) {
+            const int nn = i / Nt, j = i - nn * Nt;
+            Ds[nn * LDD + j] = (Din && i < ns * Nt) ? Din[n0 * Nt + i] : 0.f;
+        }
+    }
 
     auto load_detector = [&](int k) {
         if (tid < NS) {
@@ -210,7 +264,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
                 const float wt = ws[nn];
                 const int jlo = max(0, c0 - 1 - i0), jhi = min(Nt - 1, c0 + TCOL - 1 - i0);
                 const float *g = Gs + nn * (TCOL + 1);
-                float *d = Ds + (size_t)nn * Nt;
+                float *d = Ds + (size_t)nn * LDD;
                 for (int j = jlo + lane; j <= jhi; j += 32) {
                     int c = i0 + j - c0;
                     float v = 0.f;
@@ -226,7 +280,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     // ---------------------------------------------------------------- phase 2: window softmax
     const double log_nt = log((double)Nt);
     for (int nn = warp; nn < ns; nn += 8) {
-        float *d = Ds + (size_t)nn * Nt;
+        float *d = Ds + (size_t)nn * LDD;
         const int64_t src = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
         float m = -INFINITY;
         for (int j = lane; j < Nt; j += 32) m = fmaxf(m, d[j]);
@@ -245,8 +299,180 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
         if (lnl_out && lane == 0) lnl_out[src] = (double)m + (double)logf(sum) - (double)s.A[n0 + nn] - log_nt;
     }
 
+    // projections of detector k's E on the harmonics: e = sum_a conj(E_a) y_a, with y -> dy/diota,
+    // i m y; SUB threads per sample, thread sub taking the modes a = sub, sub + SUB, ...
+    auto project = [&](int k) {
+        const int nn = tid / SUB, sub = tid % SUB;
+        float er = 0.f, ei = 0.f, gr = 0.f, gi = 0.f, fr = 0.f, fi = 0.f;
+        if (nn < ns) {
+            const int64_t src = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
+            const float iota = (float)samples[3 * N + src], phi = (float)samples[4 * N + src];
+            float cpow[10], spow[10];
+            half_angle_powers10(iota, cpow, spow);
+            const float *E = Es + nn * (RMAX + 1);
+            for (int a = sub; a < M; a += SUB) {
+                float yr, yi, dr, di;
+                sylm_and_diota(pp.mode[a], cpow, spow, phi, yr, yi, dr, di);
+                const float Er = E[a], Ei = E[M + a], mm = (float)pp.mode[a].m;
+                er += Er * yr + Ei * yi;
+                ei += Er * yi - Ei * yr;
+                gr += Er * dr + Ei * di;
+                gi += Er * di - Ei * dr;
+                // i m y = (-m yi, m yr)
+                fr += mm * (-Er * yi + Ei * yr);
+                fi += mm * (Er * yr + Ei * yi);
+            }
+        }
+#pragma unroll
+        for (int o = SUB / 2; o; o >>= 1) {
+            er += __shfl_xor_sync(0xffffffffu, er, o);
+            ei += __shfl_xor_sync(0xffffffffu, ei, o);
+            gr += __shfl_xor_sync(0xffffffffu, gr, o);
+            gi += __shfl_xor_sync(0xffffffffu, gi, o);
+            fr += __shfl_xor_sync(0xffffffffu, fr, o);
+            fi += __shfl_xor_sync(0xffffffffu, fi, o);
+        }
+        if (nn < ns && sub == 0) {
+            proj[k][0][nn] = er;
+            proj[k][1][nn] = ei;
+            proj[k][2][nn] = gr;
+            proj[k][3][nn] = gi;
+            proj[k][4][nn] = fr;
+            proj[k][5][nn] = fi;
+        }
+    };
+
     // ---------------------------------------------------------------- phase 3: E and slope sums
-    {
+    if constexpr (TC) {
+        // tensor-core form.  Thread (nn, q) builds the rows nn (P_E) and 64 + nn (P_D) of its 16-byte
+        // K chunk q (8 columns) of A; thread 0 copies the chunk's B (hi, lo) with bulk copies and
+        // issues 2 K steps x 3 products (hi.hi, hi.lo, lo.hi) into the detector's accumulator.
+        // Waits are bounded: a wait that runs out sets the timeout flag and tc_abort, after which no
+        // more MMAs are issued (every thread still passes every barrier).
+        const int nn = tid & (TC_NS - 1), q = tid >> 6;
+        uint8_t *tcb = reinterpret_cast<uint8_t *>(U1);
+        const uint32_t id = idesc(1, 128, RP);
+        const uint64_t a_ks = (uint64_t)(2 * 128 * 16) >> 4, b_ks = (uint64_t)(2 * RP * 16) >> 4;
+        const int TQ8 = adj_qt_cols(T) / 8;
+        auto aborted = [&]() { return *(volatile int *)&tc_abort != 0; };
+        auto wait = [&](uint64_t *bar, uint32_t parity) {
+            if (aborted()) return;
+            if (!mbar_wait_sleep(bar, parity, flags, ILE_FLAG_TIMEOUT, TC_SLEEPS, TC_SLEEP_NS)) {
+                atomicOr(flags, ILE_FLAG_TIMEOUT);
+                tc_abort = 1;
+            }
+        };
+        uint32_t gch = 0;        // chunks issued so far, over all detectors
+        int64_t last_commit = -1;  // (thread 0) the last chunk whose MMAs were committed
+        for (int k = 0; k < K; k++) {
+            __syncthreads();
+            load_detector(k);
+            __syncthreads();
+            // chunks of 32 columns from the tile's first window column (rounded down to 8) to its
+            // last lerp partner, inside [0, T_ext)
+            const int lo8 = max(lo_s[k], 0) & ~7;
+            const int cend = min(hi_s[k] + Nt, T - 1);
+            const int nch = cend >= lo8 ? (cend - lo8) / TC_COLS + 1 : 0;
+            for (int ci = 0; ci < nch; ci++, gch++) {
+                const int b = (int)(gch & 1u);
+                const int c0 = lo8 + ci * TC_COLS;
+                uint4 *Ah = reinterpret_cast<uint4 *>(tcb + b * TC_BUF), *Al = Ah + TC_A_BYTES / 16;
+                uint4 *Bh = Al + TC_A_BYTES / 16, *Bl = Bh + TC_B_BYTES / 16;
+                // buffer b is free once the MMAs of chunk gch - 2 have completed
+                if (gch >= 2) wait(&tc_mma[b], ((gch - 2) >> 1) & 1u);
+                if (tid == 0 && !aborted()) {
+                    mbar_arrive_expect_tx(&tc_bfull[b], 2u * TC_B_BYTES);
+                    const size_t off = ((size_t)k * TQ8 + (size_t)(c0 / 8)) * RP;
+                    bulk_g2s(Bh, QThi + off, TC_B_BYTES, &tc_bfull[b]);
+                    bulk_g2s(Bl, QTlo + off, TC_B_BYTES, &tc_bfull[b]);
+                }
+                {
+                    const int j0 = c0 + 8 * q - i0s[nn];  // window bin of the chunk's column 8 q
+                    const float wt = ws[nn];
+                    const float *pr = Ds + (size_t)nn * LDD;
+                    float pe[8], pd[8];
+                    float prev = (j0 >= 1 && j0 <= Nt) ? pr[j0 - 1] : 0.f;
+#pragma unroll
+                    for (int e = 0; e < 8; e++) {
+                        const int j = j0 + e;
+                        const float cur = (j >= 0 && j < Nt) ? pr[j] : 0.f;
+                        pe[e] = (1.f - wt) * cur + wt * prev;
+                        pd[e] = prev - cur;
+                        prev = cur;
+                    }
+                    uint4 h, l;
+                    pack_chunk<true>(pe, h, l);
+                    Ah[q * 128 + nn] = h;
+                    Al[q * 128 + nn] = l;
+                    pack_chunk<true>(pd, h, l);
+                    Ah[q * 128 + TC_NS + nn] = h;
+                    Al[q * 128 + TC_NS + nn] = l;
+                }
+                fence_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    wait(&tc_bfull[b], (gch >> 1) & 1u);
+                    if (!aborted()) {
+                        fence_after();
+                        const uint64_t ah = sdesc(smem_u32(Ah), 128 * 16, 128), al = sdesc(smem_u32(Al), 128 * 16, 128);
+                        const uint64_t bh = sdesc(smem_u32(Bh), RP * 16, 128), bl = sdesc(smem_u32(Bl), RP * 16, 128);
+                        uint32_t acc = ci > 0 ? 1u : 0u;
+                        for (int pass = 0; pass < 3; pass++) {
+                            const uint64_t ad = pass == 2 ? al : ah;
+                            const uint64_t bd = pass == 1 ? bl : bh;
+                            for (int ks = 0; ks < TC_COLS / 16; ks++) {
+                                mma_bf16(tmem, ad + (uint64_t)ks * a_ks, bd + (uint64_t)ks * b_ks, id, acc);
+                                acc = 1u;
+                            }
+                        }
+                        mma_commit(&tc_mma[b]);
+                        last_commit = gch;
+                    }
+                }
+            }
+            // the detector's sums: rows 0-63 E(r), rows 64-127 the slope terms dE(r)
+            if (nch > 0) wait(&tc_mma[(gch - 1) & 1u], ((gch - 1) >> 1) & 1u);
+            __syncthreads();  // tc_abort is final for this detector: the branch below is uniform
+            const bool have = nch > 0 && !aborted();
+            fence_after();
+            if (warp < 4) {
+                const int row = warp * 32 + lane;
+                const int sm_ = row & (TC_NS - 1);
+                float v[RP];
+                if (have) {
+                    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+                    for (int cb = 0; cb < RP / 16; cb++) {
+                        uint32_t r16[16];
+                        tmem_ld16(ta + (uint32_t)(cb * 16), r16);
+#pragma unroll
+                        for (int i = 0; i < 16; i++) v[cb * 16 + i] = __uint_as_float(r16[i]);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < RP; i++) v[i] = 0.f;
+                }
+                if (row < TC_NS) {
+#pragma unroll
+                    for (int r = 0; r < RP; r++)
+                        if (r < R) Es[sm_ * (RMAX + 1) + r] = v[r];
+                } else {
+                    float sp = 0.f;
+#pragma unroll
+                    for (int r = 0; r < RP; r++)
+                        if (r < R) sp = fmaf(Cs[r * NS + sm_], v[r], sp);
+                    Ss[k][sm_] = sp;
+                }
+            }
+            fence_before();
+            __syncthreads();
+            project(k);
+        }
+        // no MMA may still be writing TMEM when it is released (bounded)
+        if (tid == 0 && aborted() && last_commit >= 0)
+            mbar_wait_sleep(&tc_mma[last_commit & 1], (uint32_t)(last_commit >> 1) & 1u, flags, 0u, TC_SLEEPS,
+                            TC_SLEEP_NS);
+    } else {
         const int ty = tid >> 4, tx = tid & 15;
         for (int k = 0; k < K; k++) {
             __syncthreads();
@@ -271,7 +497,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
                 for (int i = tid; i < NS * TCOL; i += 256) {
                     int c = i / NS, nn = i - c * NS;
                     int j0 = c0 + c - i0s[nn];
-                    const float *pr = Ds + (size_t)nn * Nt;
+                    const float *pr = Ds + (size_t)nn * LDD;
                     float a = (j0 >= 0 && j0 < Nt) ? pr[j0] : 0.f;
                     float b = (j0 >= 1 && j0 <= Nt) ? pr[j0 - 1] : 0.f;
                     float wt = ws[nn];
@@ -323,48 +549,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
                 if (tx == 0) Ss[k][nn] = sp;
             }
             __syncthreads();
-            // projections of E on the harmonics: e = sum_a conj(E_a) y_a, with y -> dy/diota, i m y;
-            // SUB threads per sample, thread sub taking the modes a = sub, sub + SUB, ...
-            {
-                const int nn = tid / SUB, sub = tid % SUB;
-                float er = 0.f, ei = 0.f, gr = 0.f, gi = 0.f, fr = 0.f, fi = 0.f;
-                if (nn < ns) {
-                    const int64_t src = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
-                    const float iota = (float)samples[3 * N + src], phi = (float)samples[4 * N + src];
-                    float cpow[10], spow[10];
-                    half_angle_powers10(iota, cpow, spow);
-                    const float *E = Es + nn * (RMAX + 1);
-                    for (int a = sub; a < M; a += SUB) {
-                        float yr, yi, dr, di;
-                        sylm_and_diota(pp.mode[a], cpow, spow, phi, yr, yi, dr, di);
-                        const float Er = E[a], Ei = E[M + a], mm = (float)pp.mode[a].m;
-                        er += Er * yr + Ei * yi;
-                        ei += Er * yi - Ei * yr;
-                        gr += Er * dr + Ei * di;
-                        gi += Er * di - Ei * dr;
-                        // i m y = (-m yi, m yr)
-                        fr += mm * (-Er * yi + Ei * yr);
-                        fi += mm * (Er * yr + Ei * yi);
-                    }
-                }
-#pragma unroll
-                for (int o = SUB / 2; o; o >>= 1) {
-                    er += __shfl_xor_sync(0xffffffffu, er, o);
-                    ei += __shfl_xor_sync(0xffffffffu, ei, o);
-                    gr += __shfl_xor_sync(0xffffffffu, gr, o);
-                    gi += __shfl_xor_sync(0xffffffffu, gi, o);
-                    fr += __shfl_xor_sync(0xffffffffu, fr, o);
-                    fi += __shfl_xor_sync(0xffffffffu, fi, o);
-                }
-                if (nn < ns && sub == 0) {
-                    proj[k][0][nn] = er;
-                    proj[k][1][nn] = ei;
-                    proj[k][2][nn] = gr;
-                    proj[k][3][nn] = gi;
-                    proj[k][4][nn] = fr;
-                    proj[k][5][nn] = fi;
-                }
-            }
+            project(k);
         }
     }
     __syncthreads();
@@ -522,6 +707,14 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
             g_samples[4 * N + src] = gn * (double)g_phi;
             g_samples[5 * N + src] = gn * (double)g_D;
             g_samples[6 * N + src] = gn * (double)g_tc;
+        }
+    }
+    if constexpr (TC) {
+        fence_before();
+        __syncthreads();
+        if (warp == 0) {
+            fence_after();
+            tmem_dealloc(tmem, TC_TMEM_COLS);
         }
     }
 }
@@ -798,16 +991,36 @@ __global__ void adj_guv_reduce_kernel(int K, int M, int nblk, const float *__res
     }
 }
 
-template <int NS>
+// Transposed split operand of the tensor-core E contraction: QT[k][c / 8][r][c % 8] (BF16 hi and
+// lo of Qp[k][r][c]; zero for r >= 2M and c >= T_ext), one thread per (k, column group, row).
+__global__ void adj_qt_kernel(const __grid_constant__ PointParams pp, const float *__restrict__ Qp,
+                              uint4 *__restrict__ hi, uint4 *__restrict__ lo) {
+    const int T = pp.T_ext, R = 2 * pp.M, TQ8 = adj_qt_cols(T) / 8;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)pp.K * TQ8 * RP) return;
+    const int r = (int)(i % RP), cg = (int)((i / RP) % TQ8), k = (int)(i / ((int64_t)RP * TQ8));
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        const int c = cg * 8 + e;
+        v[e] = (r < R && c < T) ? Qp[((int64_t)k * R + r) * T + c] : 0.f;
+    }
+    pack_chunk<true>(v, hi[i], lo[i]);
+}
+
+template <int NS, bool TC>
 cudaError_t launch_main(const PointParams &pp, const float *Qp, const float *UV, IleScratch s, const int *perm,
                         const double *samples, const double *g, int64_t N, float *pig, const float *Din,
-                        double *g_samples, double *lnl, cudaStream_t st) {
-    const size_t smem = sizeof(float) * MainSmem<NS>::floats(pp.Nt) + 16;
-    cudaError_t e = cudaFuncSetAttribute(adj_main_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                        const void *QThi, const void *QTlo, unsigned *flags, double *g_samples, double *lnl,
+                        cudaStream_t st) {
+    const size_t smem = sizeof(float) * MainSmem<NS, TC>::floats(pp.Nt) + 16;
+    cudaError_t e =
+        cudaFuncSetAttribute(adj_main_kernel<NS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (N + NS - 1) / NS;
-    adj_main_kernel<NS><<<(unsigned)blocks, 256, smem, st>>>(pp, Qp, (const float4 *)UV, s, perm, samples, g, N, pig,
-                                                             Din, g_samples, lnl);
+    adj_main_kernel<NS, TC><<<(unsigned)blocks, 256, smem, st>>>(pp, Qp, (const float4 *)UV, s, perm, samples, g, N,
+                                                                 pig, Din, (const uint4 *)QThi, (const uint4 *)QTlo,
+                                                                 flags, g_samples, lnl);
     return cudaGetLastError();
 }
 
@@ -829,13 +1042,32 @@ int ile_grad_uv_blocks(int64_t N, int n_sm) {
     return (int)(b < 1 ? 1 : b);
 }
 
+bool ile_grad_tc_ok(const PointParams &pp) {
+    // the tensor-core form holds 64 samples' D rows in shared memory and at most RP real rows
+    return 2 * pp.M <= RP && sizeof(float) * MainSmem<TC_NS, true>::floats(pp.Nt) + 16 + 12 * 1024 <= 227 * 1024;
+}
+
+size_t ile_grad_qt_bytes(const PointParams &pp) { return (size_t)pp.K * (adj_qt_cols(pp.T_ext) / 8) * RP * 16; }
+
+cudaError_t ile_launch_grad_qt(const PointParams &pp, const float *Qp, void *hi, void *lo, cudaStream_t st) {
+    const int64_t n = (int64_t)pp.K * (adj_qt_cols(pp.T_ext) / 8) * RP;
+    adj_qt_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pp, Qp, (uint4 *)hi, (uint4 *)lo);
+    return cudaGetLastError();
+}
+
 cudaError_t ile_launch_grad_main(const PointParams &pp, const float *Qp, const float *UV, IleScratch s,
                                  const int *perm, const double *samples, const double *g_lnL, int64_t N, float *pig,
-                                 const float *Din, double *g_samples, double *lnl_out, cudaStream_t st) {
+                                 const float *Din, const void *QThi, const void *QTlo, unsigned *flags,
+                                 double *g_samples, double *lnl_out, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
+    if (Din && QThi && QTlo && ile_grad_tc_ok(pp))
+        return launch_main<TC_NS, true>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, Din, QThi, QTlo, flags,
+                                        g_samples, lnl_out, st);
     if (pp.Nt <= 256)
-        return launch_main<64>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, Din, g_samples, lnl_out, st);
-    return launch_main<32>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, Din, g_samples, lnl_out, st);
+        return launch_main<64, false>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, Din, nullptr, nullptr, flags,
+                                      g_samples, lnl_out, st);
+    return launch_main<32, false>(pp, Qp, UV, s, perm, samples, g_lnL, N, pig, Din, nullptr, nullptr, flags,
+                                  g_samples, lnl_out, st);
 }
 
 cudaError_t ile_launch_grad_q(const PointParams &pp, const float *pig, IleScratch s, int64_t N, int nsplit,

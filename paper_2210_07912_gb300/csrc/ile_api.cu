@@ -26,6 +26,10 @@ struct ile_ctx {
     void *Qtc[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     bool Qtc_ready[3] = {false, false, false};
     size_t Qtc_bytes[3] = {0, 0, 0};
+    // transposed split operand (hi, lo) of the adjoint's tensor-core E contraction (ile_adjoint.cu)
+    void *Qadj[2] = {nullptr, nullptr};
+    bool Qadj_ready = false;
+    size_t Qadj_bytes = 0;
     // delay-sort scratch
     int *keys = nullptr, *buckets = nullptr, *perm = nullptr;
     // per-sample scratch
@@ -260,6 +264,21 @@ ile_status ensure_tc_operands(ile_ctx *ctx, int prec) {
     return ILE_OK;
 }
 
+// The adjoint's transposed split operand of the current point (built once per point).
+ile_status ensure_adj_operands(ile_ctx *ctx) {
+    if (ctx->Qadj_ready) return ILE_OK;
+    const size_t bytes = ile_grad_qt_bytes(ctx->pp);
+    if (bytes > ctx->Qadj_bytes) {
+        ctx->Qadj_bytes = 0;
+        CK(grow(ctx, &ctx->Qadj[0], bytes));
+        CK(grow(ctx, &ctx->Qadj[1], bytes));
+        ctx->Qadj_bytes = bytes;
+    }
+    CK(ile_launch_grad_qt(ctx->pp, ctx->Qp, ctx->Qadj[0], ctx->Qadj[1], ctx->stream));
+    ctx->Qadj_ready = true;
+    return ILE_OK;
+}
+
 // S1-S5 on device-resident samples; writes lnL_t (or the grid) to dout in the caller's order.
 // Samples are first ordered by quantised detector delays (ile_sort.cu) so that a tile of the
 // contraction spans few time columns; the per-sample results do not depend on that order.
@@ -323,8 +342,14 @@ ile_status run_grad(ile_ctx *ctx, const double *dsamples, const double *dg, int6
         CK(ensure_bytes(ctx, &ctx->pig, &ctx->pig_bytes, sizeof(float) * (size_t)N * pp.Nt));
         pig = ctx->pig;
     }
+    // ... and run the E / slope contraction on the tensor cores when it fits shared memory
+    const bool tc_adj = tc2_fwd && ile_grad_tc_ok(pp);
     if (tc2_fwd) {
         st = ensure_tc_operands(ctx, ILE_PREC_BF16X3);
+        if (st != ILE_OK) return st;
+    }
+    if (tc_adj) {
+        st = ensure_adj_operands(ctx);
         if (st != ILE_OK) return st;
     }
     const int nsplit = ile_grad_q_splits(pp, N, ctx->n_sm);
@@ -345,7 +370,8 @@ ile_status run_grad(ile_ctx *ctx, const double *dsamples, const double *dg, int6
                           ctx->flags, ctx->stream));
     if (g_theta || gQ || lnl)
         CK(ile_launch_grad_main(pp, ctx->Qp, ctx->UV, ctx->s, ctx->perm, dsamples, dg, N, pig,
-                                tc2_fwd ? pig : nullptr, g_theta, lnl, ctx->stream));
+                                tc2_fwd ? pig : nullptr, tc_adj ? ctx->Qadj[0] : nullptr,
+                                tc_adj ? ctx->Qadj[1] : nullptr, ctx->flags, g_theta, lnl, ctx->stream));
     if (gQ) CK(ile_launch_grad_q(pp, pig, ctx->s, N, nsplit, ctx->gq_part, gQ, ctx->stream));
     if (gU || gV) CK(ile_launch_grad_uv(pp, dsamples, dg, N, nblk, ctx->guv_part, gU, gV, ctx->stream));
     return ILE_OK;
@@ -426,7 +452,7 @@ ile_status ile_destroy(ile_ctx *ctx) {
                     ctx->a_iter_log,   ctx->a_iter_res, ctx->a_lnwp,    ctx->a_lnl,     ctx->a_iter,
                     ctx->a_bins,       ctx->pig,        ctx->gq_part,   ctx->guv_part,  ctx->g_in,
                     ctx->g_out,        ctx->g_cur,      ctx->g_bat,     ctx->g_tab,     ctx->g_part,
-                    ctx->a_u};
+                    ctx->a_u,          ctx->Qadj[0],    ctx->Qadj[1]};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (auto &v : ctx->ev)
@@ -626,7 +652,7 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
     DeviceGuard g(ctx->device);
     // the previous point's arrays are released by the growth below: no data until it completes
     ctx->has_data = false;
-    ctx->Qtc_ready[1] = ctx->Qtc_ready[2] = false;
+    ctx->Qtc_ready[1] = ctx->Qtc_ready[2] = ctx->Qadj_ready = false;
     CK(grow(ctx, &ctx->Qp, sizeof(float) * qp.size()));
     CK(grow(ctx, &ctx->UV, sizeof(float) * uv.size()));
     CK(grow(ctx, &ctx->Qquad, sizeof(float) * quad.size()));
@@ -636,7 +662,7 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->pp = pp;
     ctx->has_data = true;
-    ctx->Qtc_ready[1] = ctx->Qtc_ready[2] = false;
+    ctx->Qtc_ready[1] = ctx->Qtc_ready[2] = ctx->Qadj_ready = false;
     ctx->cap = ctx->cap;  // scratch is sized for ILE_MAX_DET x ILE_MAX_MODES, so it stays valid
     return ILE_OK;
 }

@@ -349,10 +349,16 @@ cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo
 int ile_grad_q_splits(const PointParams &pp, int64_t N, int n_sm);
 int ile_grad_uv_blocks(int64_t N, int n_sm);
 // Din: the data term D(n, j) in processing order (from ile_launch_tc2, grid mode 2), or NULL to
-// recompute it on CUDA cores
+// recompute it on CUDA cores.  With Din and the transposed split operand QThi / QTlo (from
+// ile_launch_grad_qt) and ile_grad_tc_ok(pp), the E and slope contraction runs on the tensor
+// cores; a bounded wait that runs out sets ILE_FLAG_TIMEOUT in *flags.
+bool ile_grad_tc_ok(const PointParams &pp);
+size_t ile_grad_qt_bytes(const PointParams &pp);
+cudaError_t ile_launch_grad_qt(const PointParams &pp, const float *Qp, void *hi, void *lo, cudaStream_t st);
 cudaError_t ile_launch_grad_main(const PointParams &pp, const float *Qp, const float *UV, IleScratch s,
                                  const int *perm, const double *samples, const double *g_lnL, int64_t N, float *pig,
-                                 const float *Din, double *g_samples, double *lnl_out, cudaStream_t st);
+                                 const float *Din, const void *QThi, const void *QTlo, unsigned *flags,
+                                 double *g_samples, double *lnl_out, cudaStream_t st);
 cudaError_t ile_launch_grad_q(const PointParams &pp, const float *pig, IleScratch s, int64_t N, int nsplit,
                               float *part, double *gQ, cudaStream_t st);
 cudaError_t ile_launch_grad_uv(const PointParams &pp, const double *samples, const double *g_lnL, int64_t N, int nblk,

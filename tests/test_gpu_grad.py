@@ -82,28 +82,37 @@ def _compare_all(ile, orc, point, th, g, prec="fp32"):
     return out
 
 
-def test_grad_adjoint_K3_M21_Nt512(ile, orc):
+# fp32 contexts recompute D(n, j) and contract on CUDA cores; bf16x3 contexts take D(n, j) from the
+# fused tensor-core forward kernel and, where 64 samples' rows fit shared memory (N_t <= 512), run
+# the E / slope contraction on the tensor cores as well
+PRECS = ["fp32", "bf16x3"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_grad_adjoint_K3_M21_Nt512(ile, orc, prec):
     """Three detectors, 21 modes, 512-bin window (the adjoint workload's geometry), 2^10 samples."""
     point = S.workload_point(S.GRAD)
     th = S.workload_samples(S.GRAD, 1024)
     g = np.random.default_rng(7).normal(size=th.shape[1])
-    _compare_all(ile, orc, point, th, g)
+    _compare_all(ile, orc, point, th, g, prec)
 
 
-def test_grad_two_detectors_ragged(ile, orc):
+@pytest.mark.parametrize("prec", PRECS)
+def test_grad_two_detectors_ragged(ile, orc, prec):
     """K = 2, M = 2, N_t = 256; 300 samples = 4 tiles of 64 and a ragged tail."""
     point = S.workload_point(S.SMALL)
     th = S.workload_samples(S.SMALL, 300)
     g = np.random.default_rng(8).uniform(0.5, 1.5, th.shape[1])
-    _compare_all(ile, orc, point, th, g)
+    _compare_all(ile, orc, point, th, g, prec)
 
 
-def test_grad_long_window_four_detectors(ile, orc):
-    """N_t = 1024 (32-sample tiles), K = 4, M = 9."""
+@pytest.mark.parametrize("prec", PRECS)
+def test_grad_long_window_four_detectors(ile, orc, prec):
+    """N_t = 1024 (32-sample tiles; the bf16x3 context keeps the CUDA-core contraction), K = 4, M = 9."""
     point = S.make_point(S.SEED_BASE + 60, 4, 9, 1024, spectrum="decay")
     th = S.prior_samples(np.random.default_rng(61), 200)
     g = np.random.default_rng(62).normal(size=th.shape[1])
-    _compare_all(ile, orc, point, th, g)
+    _compare_all(ile, orc, point, th, g, prec)
 
 
 def test_grad_matches_fp64_central_differences(ile, orc):
@@ -126,7 +135,8 @@ def test_grad_matches_fp64_central_differences(ile, orc):
     _check_theta(orc, point, th[:, ~kink], got[:, ~kink], fd[:, ~kink])
 
 
-def test_grad_full_size_sampled(ile, orc):
+@pytest.mark.parametrize("prec", PRECS)
+def test_grad_full_size_sampled(ile, orc, prec):
     """2^18 samples through the full launch; the upstream weights are non-zero on 192 random
     samples only, so the oracle can check g_theta on those and the Q/U/V sums exactly."""
     point = S.workload_point(S.GRAD)
@@ -136,7 +146,7 @@ def test_grad_full_size_sampled(ile, orc):
     idx = np.sort(rng.choice(N, 192, replace=False))
     g = np.zeros(N)
     g[idx] = rng.normal(size=idx.size)
-    out = _ctx(ile, point).eval_grad(th, g)
+    out = _ctx(ile, point, prec).eval_grad(th, g)
     rest = np.ones(N, bool)
     rest[idx] = False
     assert np.all(out["theta"][:, rest] == 0.0)

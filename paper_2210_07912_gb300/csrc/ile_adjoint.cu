@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     __shared__ float proj[ILE_MAX_DET][6][NS];
     __shared__ int red[2][8];
     __shared__ uint16_t pab[ILE_MAX_MODES * (ILE_MAX_MODES + 1) / 2];
-    __shared__ uint64_t tc_bfull[2], tc_mma[2];
+    __shared__ uint64_t tc_bfull[2], tc_mma[2], tc_aready[2];
     __shared__ uint32_t tc_tmem;
     __shared__ int tc_abort;
 
@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
             for (int b = 0; b < 2; b++) {
                 mbar_init(&tc_bfull[b], 1);
                 mbar_init(&tc_mma[b], 1);
+                mbar_init(&tc_aready[b], 256);
             }
             tc_abort = 0;
             mbar_init_fence();
@@ -176,9 +177,19 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     if (LDD == Nt) {
         for (int i = tid; i < NS * Nt; i += 256) Ds[i] = (Din && i < ns * Nt) ? Din[n0 * Nt + i] : 0.f;
     } else {
-        for (int i = tid; i < NS * Nt; i += 256) {
-            const int nn = i / Nt, j = i - nn * Nt;
-            Ds[nn * LDD + j] = (Din && i < ns * Nt) ? Din[n0 * Nt + i] : 0.f;
+        // odd row stride: a warp moves 4 rows x 8 float4 (whole 128-byte lines, one per row); lane l
+        // stores to row 4 i + l / 8 at column 4 (l % 8) + e, i.e. 32 distinct banks per store
+        const int NT4 = Nt / 4, rr = lane >> 3, cc = lane & 7;
+        const float4 *src4 = reinterpret_cast<const float4 *>(Din + n0 * Nt);
+#pragma unroll 4
+        for (int it = warp; it < (NS / 4) * (NT4 / 8); it += 8) {
+            const int rg = it / (NT4 / 8), c4 = (it - rg * (NT4 / 8)) * 8 + cc, nn = rg * 4 + rr;
+            const float4 v = nn < ns ? src4[(size_t)nn * NT4 + c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float *d = Ds + nn * LDD + 4 * c4;
+            d[0] = v.x;
+            d[1] = v.y;
+            d[2] = v.z;
+            d[3] = v.w;
         }
     }
 
@@ -345,8 +356,9 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     // ---------------------------------------------------------------- phase 3: E and slope sums
     if constexpr (TC) {
         // tensor-core form.  Thread (nn, q) builds the rows nn (P_E) and 64 + nn (P_D) of its 16-byte
-        // K chunk q (8 columns) of A; thread 0 copies the chunk's B (hi, lo) with bulk copies and
-        // issues 2 K steps x 3 products (hi.hi, hi.lo, lo.hi) into the detector's accumulator.
+        // K chunk q (8 columns) of A; thread 0 issues 2 K steps x 3 products (hi.hi, hi.lo, lo.hi)
+        // into the detector's accumulator and then starts the bulk copies of the next chunk's B
+        // (hi, lo) into the other buffer, so that they land while that chunk's A is built.
         // Waits are bounded: a wait that runs out sets the timeout flag and tc_abort, after which no
         // more MMAs are issued (every thread still passes every barrier).
         const int nn = tid & (TC_NS - 1), q = tid >> 6;
@@ -361,6 +373,13 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
                 atomicOr(flags, ILE_FLAG_TIMEOUT);
                 tc_abort = 1;
             }
+        };
+        auto copy_b = [&](int b, int k, int c0) {
+            uint4 *Bh = reinterpret_cast<uint4 *>(tcb + b * TC_BUF + 2 * TC_A_BYTES), *Bl = Bh + TC_B_BYTES / 16;
+            mbar_arrive_expect_tx(&tc_bfull[b], 2u * TC_B_BYTES);
+            const size_t off = ((size_t)k * TQ8 + (size_t)(c0 / 8)) * RP;
+            bulk_g2s(Bh, QThi + off, TC_B_BYTES, &tc_bfull[b]);
+            bulk_g2s(Bl, QTlo + off, TC_B_BYTES, &tc_bfull[b]);
         };
         uint32_t gch = 0;        // chunks issued so far, over all detectors
         int64_t last_commit = -1;  // (thread 0) the last chunk whose MMAs were committed
@@ -380,12 +399,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
                 uint4 *Bh = Al + TC_A_BYTES / 16, *Bl = Bh + TC_B_BYTES / 16;
                 // buffer b is free once the MMAs of chunk gch - 2 have completed
                 if (gch >= 2) wait(&tc_mma[b], ((gch - 2) >> 1) & 1u);
-                if (tid == 0 && !aborted()) {
-                    mbar_arrive_expect_tx(&tc_bfull[b], 2u * TC_B_BYTES);
-                    const size_t off = ((size_t)k * TQ8 + (size_t)(c0 / 8)) * RP;
-                    bulk_g2s(Bh, QThi + off, TC_B_BYTES, &tc_bfull[b]);
-                    bulk_g2s(Bl, QTlo + off, TC_B_BYTES, &tc_bfull[b]);
-                }
+                if (tid == 0 && ci == 0 && !aborted()) copy_b(b, k, c0);  // a detector's first chunk
                 {
                     const int j0 = c0 + 8 * q - i0s[nn];  // window bin of the chunk's column 8 q
                     const float wt = ws[nn];
@@ -408,9 +422,12 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
                     Ah[q * 128 + TC_NS + nn] = h;
                     Al[q * 128 + TC_NS + nn] = l;
                 }
+                // A written: arrive instead of a block barrier, so that the other warps go on to the
+                // next chunk while thread 0 issues this one
                 fence_async_smem();
-                __syncthreads();
+                mbar_arrive(&tc_aready[b]);
                 if (tid == 0) {
+                    wait(&tc_aready[b], (gch >> 1) & 1u);
                     wait(&tc_bfull[b], (gch >> 1) & 1u);
                     if (!aborted()) {
                         fence_after();
@@ -427,6 +444,11 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
                         }
                         mma_commit(&tc_mma[b]);
                         last_commit = gch;
+                    }
+                    // the next chunk's B goes to the other buffer once chunk gch - 1's MMAs are done
+                    if (ci + 1 < nch) {
+                        if (gch >= 1) wait(&tc_mma[b ^ 1], ((gch - 1) >> 1) & 1u);
+                        if (!aborted()) copy_b(b ^ 1, k, c0 + TC_COLS);
                     }
                 }
             }
@@ -1044,7 +1066,9 @@ int ile_grad_uv_blocks(int64_t N, int n_sm) {
 
 bool ile_grad_tc_ok(const PointParams &pp) {
     // the tensor-core form holds 64 samples' D rows in shared memory and at most RP real rows
-    return 2 * pp.M <= RP && sizeof(float) * MainSmem<TC_NS, true>::floats(pp.Nt) + 16 + 12 * 1024 <= 227 * 1024;
+    // (and reads them as whole 32-column groups)
+    return 2 * pp.M <= RP && pp.Nt % 32 == 0 &&
+           sizeof(float) * MainSmem<TC_NS, true>::floats(pp.Nt) + 16 + 12 * 1024 <= 227 * 1024;
 }
 
 size_t ile_grad_qt_bytes(const PointParams &pp) { return (size_t)pp.K * (adj_qt_cols(pp.T_ext) / 8) * RP * 16; }

@@ -869,6 +869,199 @@ __global__ void __launch_bounds__(256, 2)
     }
 }
 
+// Tensor-core form (BF16x3 contexts): the same chunks of 32 samples, staged the same way; per
+// chunk the operands A = P^T (128 columns t x 32 samples, K-major: 8 samples per 16 bytes) and
+// B = C (RP rows r x 32 samples) are split into BF16 hi / lo and thread 0 issues 2 K steps x 3
+// products (hi.hi, hi.lo, lo.hi) into a [128 t x RP r] TMEM accumulator that lives for the whole
+// sample split; operand buffers alternate between chunks.  Waits are bounded (a wait that runs
+// out sets ILE_FLAG_TIMEOUT and stops further MMAs; every thread still passes every barrier).
+struct GqTcSmem {
+    uint8_t ops[2][TC_BUF];  // A hi | A lo | B hi | B lo
+    float raw[2][QNC][QRW];
+    float Cc[2][RMAX][QNC];
+    int i0c[2][QNC];
+    float wc[2][QNC];
+    uint64_t mma[2];
+    uint32_t tmem;
+    int abort;
+};
+
+__global__ void __launch_bounds__(256, 2)
+    adj_gq_tc_kernel(const __grid_constant__ PointParams pp, const float *__restrict__ pig, IleScratch s, int64_t N,
+                     int nsplit, float *__restrict__ part, unsigned *flags) {
+    extern __shared__ __align__(16) uint8_t gq_raw[];
+    GqTcSmem &sm = *reinterpret_cast<GqTcSmem *>(gq_raw);
+    const int Nt = pp.Nt, R = 2 * pp.M, T = pp.T_ext;
+    const int t0 = blockIdx.x * QTB, k = blockIdx.y, split = blockIdx.z;
+    const int64_t nb = N * split / nsplit, ne = N * (split + 1) / nsplit;
+    const int nch = (int)((ne - nb + QNC - 1) / QNC);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) tmem_alloc(&sm.tmem, TC_TMEM_COLS);
+    if (tid == 0) {
+        mbar_init(&sm.mma[0], 1);
+        mbar_init(&sm.mma[1], 1);
+        sm.abort = 0;
+        mbar_init_fence();
+    }
+    // coefficient rows R .. RMAX - 1 stay zero (the copies write rows < R only)
+    for (int i = tid; i < 2 * RMAX * QNC; i += 256) (&sm.Cc[0][0][0])[i] = 0.f;
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = sm.tmem;
+    auto aborted = [&]() { return *(volatile int *)&sm.abort != 0; };
+    auto wait = [&](uint64_t *bar, uint32_t parity) {
+        if (aborted()) return;
+        if (!mbar_wait_sleep(bar, parity, flags, ILE_FLAG_TIMEOUT, TC_SLEEPS, TC_SLEEP_NS)) {
+            atomicOr(flags, ILE_FLAG_TIMEOUT);
+            sm.abort = 1;
+        }
+    };
+
+    auto load_iw = [&](int c, int &i0v, float &wv) {
+        const int64_t n = nb + (int64_t)c * QNC + tid;
+        const bool ok = c < nch && n < ne;
+        i0v = ok ? s.I0[(int64_t)k * N + n] : 0;
+        wv = ok ? s.W[(int64_t)k * N + n] : 0.f;
+    };
+    auto issue = [&](int c, int b) {
+        const int64_t c0 = nb + (int64_t)c * QNC;
+        const int nc = (int)min((int64_t)QNC, ne - c0);
+        for (int i = tid; i < QNC * (QTB + 1); i += 256) {
+            const int j = i / (QTB + 1), m = i - j * (QTB + 1);
+            const int idx = t0 - sm.i0c[b][j] - 1 + m;  // pi column
+            const bool ok = j < nc && idx >= 0 && idx < Nt;
+            cp_async4(&sm.raw[b][j][m], pig + (size_t)(c0 + (j < nc ? j : 0)) * Nt + (ok ? idx : 0), ok);
+        }
+        for (int i = tid; i < R * QNC; i += 256) {
+            const int r = i / QNC, j = i - r * QNC;
+            const bool ok = j < nc;
+            cp_async4(&sm.Cc[b][r][j], s.C + ((int64_t)k * R + r) * N + c0 + (ok ? j : 0), ok);
+        }
+    };
+
+    int ri0 = 0;
+    float rw = 0.f;
+    if (tid < QNC) {
+        int a;
+        float w;
+        load_iw(0, a, w);
+        sm.i0c[0][tid] = a;
+        sm.wc[0][tid] = w;
+        load_iw(1, ri0, rw);
+    }
+    __syncthreads();
+    if (nch > 0) issue(0, 0);
+    cp_async_commit();
+    const uint32_t id = idesc(1, 128, RP);
+    const uint64_t a_ks = (uint64_t)(2 * 128 * 16) >> 4, b_ks = (uint64_t)(2 * RP * 16) >> 4;
+    uint32_t issued = 0;  // chunks whose MMAs were issued (uniform over the block)
+    for (int c = 0; c < nch; c++) {
+        const int b = c & 1;
+        if (tid < QNC) {
+            sm.i0c[b ^ 1][tid] = ri0;  // chunk c + 1
+            sm.wc[b ^ 1][tid] = rw;
+            load_iw(c + 2, ri0, rw);
+        }
+        __syncthreads();  // chunk c + 1's window starts are visible; chunk c - 1's buffers are free
+        if (c + 1 < nch) issue(c + 1, b ^ 1);
+        cp_async_commit();
+        cp_async_wait1();  // this thread's copies of chunk c have landed
+        __syncthreads();
+        // chunks whose windows miss the column block contribute nothing
+        int any = 0;
+        if (tid < QNC) {
+            const int lo = t0 - sm.i0c[b][tid], hi = lo + QTB - 1;  // window bins of the block's columns
+            any = hi >= 0 && lo <= Nt;
+        }
+        if (!__syncthreads_or(any)) continue;
+        const int ob = (int)(issued & 1u);
+        // operand buffer ob is free once the MMAs of the chunk issued two before have completed
+        if (issued >= 2) wait(&sm.mma[ob], ((issued - 2) >> 1) & 1u);
+        uint4 *Ah = reinterpret_cast<uint4 *>(sm.ops[ob]), *Al = Ah + TC_A_BYTES / 16;
+        uint4 *Bh = Al + TC_A_BYTES / 16, *Bl = Bh + TC_B_BYTES / 16;
+        // A: thread (t, g) packs P(8 g .. 8 g + 7, t), P(j, t) = (1 - w) pi(t - i0) + w pi(t - i0 - 1)
+#pragma unroll
+        for (int it = 0; it < 2; it++) {
+            const int t = tid & (QTB - 1), g = (tid >> 7) + 2 * it;
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const int j = 8 * g + e;
+                const float w = sm.wc[b][j];
+                v[e] = (1.f - w) * sm.raw[b][j][t + 1] + w * sm.raw[b][j][t];
+            }
+            uint4 h, l;
+            pack_chunk<true>(v, h, l);
+            Ah[g * 128 + t] = h;
+            Al[g * 128 + t] = l;
+        }
+        // B: thread (r, g) packs C(r, 8 g .. 8 g + 7); rows RMAX .. RP - 1 are zero
+        if (tid < RP * (QNC / 8)) {
+            const int r = tid % RP, g = tid / RP;
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; e++) v[e] = r < RMAX ? sm.Cc[b][r][8 * g + e] : 0.f;
+            uint4 h, l;
+            pack_chunk<true>(v, h, l);
+            Bh[g * RP + r] = h;
+            Bl[g * RP + r] = l;
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0 && !aborted()) {
+            fence_after();
+            const uint64_t ah = sdesc(smem_u32(Ah), 128 * 16, 128), al = sdesc(smem_u32(Al), 128 * 16, 128);
+            const uint64_t bh = sdesc(smem_u32(Bh), RP * 16, 128), bl = sdesc(smem_u32(Bl), RP * 16, 128);
+            uint32_t acc = issued > 0 ? 1u : 0u;
+            for (int pass = 0; pass < 3; pass++) {
+                const uint64_t ad = pass == 2 ? al : ah;
+                const uint64_t bd = pass == 1 ? bl : bh;
+                for (int ks = 0; ks < QNC / 16; ks++) {
+                    mma_bf16(tmem, ad + (uint64_t)ks * a_ks, bd + (uint64_t)ks * b_ks, id, acc);
+                    acc = 1u;
+                }
+            }
+            mma_commit(&sm.mma[ob]);
+        }
+        issued++;
+    }
+    // the split's partial dQ(t, r): wait for the last chunk's MMAs, then one TMEM row per column
+    if (issued > 0) wait(&sm.mma[(issued - 1) & 1u], ((issued - 1) >> 1) & 1u);
+    __syncthreads();  // the abort flag is final: the branch below is uniform
+    const bool have = issued > 0 && !aborted();
+    fence_after();
+    if (warp < 4) {
+        const int t = t0 + warp * 32 + lane;
+        float v[RP];
+        if (have) {
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+            for (int cb = 0; cb < RP / 16; cb++) {
+                uint32_t r16[16];
+                tmem_ld16(ta + (uint32_t)(cb * 16), r16);
+#pragma unroll
+                for (int i = 0; i < 16; i++) v[cb * 16 + i] = __uint_as_float(r16[i]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < RP; i++) v[i] = 0.f;
+        }
+        if (t < T) {
+#pragma unroll
+            for (int r = 0; r < RP; r++)
+                if (r < R) part[(((int64_t)split * pp.K + k) * R + r) * T + t] = v[r];
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        tmem_dealloc(tmem, TC_TMEM_COLS);
+    }
+}
+
 __global__ void adj_gq_reduce_kernel(int K, int M, int T, int nsplit, const float *__restrict__ part,
                                      double *__restrict__ gQ) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1095,13 +1288,19 @@ cudaError_t ile_launch_grad_main(const PointParams &pp, const float *Qp, const f
 }
 
 cudaError_t ile_launch_grad_q(const PointParams &pp, const float *pig, IleScratch s, int64_t N, int nsplit,
-                              float *part, double *gQ, cudaStream_t st) {
+                              float *part, double *gQ, bool tc, unsigned *flags, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     dim3 grid((pp.T_ext + QTB - 1) / QTB, pp.K, nsplit);
-    cudaError_t e =
-        cudaFuncSetAttribute(adj_gq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GqSmem));
-    if (e != cudaSuccess) return e;
-    adj_gq_kernel<<<grid, 256, sizeof(GqSmem), st>>>(pp, pig, s, N, nsplit, part);
+    cudaError_t e;
+    if (tc && 2 * pp.M <= RP) {
+        e = cudaFuncSetAttribute(adj_gq_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GqTcSmem));
+        if (e != cudaSuccess) return e;
+        adj_gq_tc_kernel<<<grid, 256, sizeof(GqTcSmem), st>>>(pp, pig, s, N, nsplit, part, flags);
+    } else {
+        e = cudaFuncSetAttribute(adj_gq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GqSmem));
+        if (e != cudaSuccess) return e;
+        adj_gq_kernel<<<grid, 256, sizeof(GqSmem), st>>>(pp, pig, s, N, nsplit, part);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)pp.K * pp.M * pp.T_ext;

@@ -372,7 +372,9 @@ ile_status run_grad(ile_ctx *ctx, const double *dsamples, const double *dg, int6
         CK(ile_launch_grad_main(pp, ctx->Qp, ctx->UV, ctx->s, ctx->perm, dsamples, dg, N, pig,
                                 tc2_fwd ? pig : nullptr, tc_adj ? ctx->Qadj[0] : nullptr,
                                 tc_adj ? ctx->Qadj[1] : nullptr, ctx->flags, g_theta, lnl, ctx->stream));
-    if (gQ) CK(ile_launch_grad_q(pp, pig, ctx->s, N, nsplit, ctx->gq_part, gQ, ctx->stream));
+    if (gQ)
+        CK(ile_launch_grad_q(pp, pig, ctx->s, N, nsplit, ctx->gq_part, gQ, ctx->prec == ILE_PREC_BF16X3, ctx->flags,
+                             ctx->stream));
     if (gU || gV) CK(ile_launch_grad_uv(pp, dsamples, dg, N, nblk, ctx->guv_part, gU, gV, ctx->stream));
     return ILE_OK;
 }

@@ -359,8 +359,10 @@ cudaError_t ile_launch_grad_main(const PointParams &pp, const float *Qp, const f
                                  const int *perm, const double *samples, const double *g_lnL, int64_t N, float *pig,
                                  const float *Din, const void *QThi, const void *QTlo, unsigned *flags,
                                  double *g_samples, double *lnl_out, cudaStream_t st);
+// tc: the sample-reduction GEMM on the tensor cores (BF16x3 split operands; bounded waits report
+// through ILE_FLAG_TIMEOUT in *flags), else FP32 on CUDA cores
 cudaError_t ile_launch_grad_q(const PointParams &pp, const float *pig, IleScratch s, int64_t N, int nsplit,
-                              float *part, double *gQ, cudaStream_t st);
+                              float *part, double *gQ, bool tc, unsigned *flags, cudaStream_t st);
 cudaError_t ile_launch_grad_uv(const PointParams &pp, const double *samples, const double *g_lnL, int64_t N, int nblk,
                                float *part, double *gU, double *gV, cudaStream_t st);
 // g_n = scale * d ln L_marg / d lnL_t(n) = scale * exp(ln w_n - max) / S1, from the result of

@@ -332,8 +332,8 @@ def adjoint_bench(ile, S, local, stream, flush, steps=10, prec="bf16x3"):
                         "N_t=512, 2^18 samples", "value": N * steps / (ms / 1e3), "unit": UNIT,
             "ms_per_call": ms / steps, "stage_ms_per_call": {k: v[0] / steps for k, v in prof.items() if v[1]},
             "algorithmic_tflops": flops / (ms / steps / 1e3) / 1e12,
-            "arithmetic": ("data term from the fused BF16x3 tensor-core kernel, E and slope contraction as a "
-                           "BF16x3 tcgen05 GEMM, dQ and the chain rule on fp32 CUDA cores, fp64 sums"
+            "arithmetic": ("data term from the fused BF16x3 tensor-core kernel, E / slope and dQ contractions as "
+                           "BF16x3 tcgen05 GEMMs, chain rule on fp32 CUDA cores, fp64 sums"
                            if prec == "bf16x3" else "fp32 CUDA cores, fp64 sums"), "precision": prec}
 
 

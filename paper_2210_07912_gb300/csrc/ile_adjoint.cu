@@ -875,10 +875,11 @@ __global__ void __launch_bounds__(256, 2)
 // products (hi.hi, hi.lo, lo.hi) into a [128 t x RP r] TMEM accumulator that lives for the whole
 // sample split; operand buffers alternate between chunks.  Waits are bounded (a wait that runs
 // out sets ILE_FLAG_TIMEOUT and stops further MMAs; every thread still passes every barrier).
+static_assert(QNC == 32, "the staging maps one lane to one sample of a chunk");
 struct GqTcSmem {
     uint8_t ops[2][TC_BUF];  // A hi | A lo | B hi | B lo
     float raw[2][QNC][QRW];
-    float Cc[2][RMAX][QNC];
+    float Cc[2][RMAX][QNC + 1];  // odd row stride: the B packing reads one row per lane
     int i0c[2][QNC];
     float wc[2][QNC];
     uint64_t mma[2];
@@ -905,7 +906,7 @@ __global__ void __launch_bounds__(256, 2)
         mbar_init_fence();
     }
     // coefficient rows R .. RMAX - 1 stay zero (the copies write rows < R only)
-    for (int i = tid; i < 2 * RMAX * QNC; i += 256) (&sm.Cc[0][0][0])[i] = 0.f;
+    for (int i = tid; i < 2 * RMAX * (QNC + 1); i += 256) (&sm.Cc[0][0][0])[i] = 0.f;
     fence_before();
     __syncthreads();
     fence_after();
@@ -925,20 +926,23 @@ __global__ void __launch_bounds__(256, 2)
         i0v = ok ? s.I0[(int64_t)k * N + n] : 0;
         wv = ok ? s.W[(int64_t)k * N + n] : 0.f;
     };
+    // warp w stages the pi row segments of samples w, w + 8, ... (lanes along the row) and the
+    // coefficient rows w, w + 8, ... (lanes along the samples)
     auto issue = [&](int c, int b) {
         const int64_t c0 = nb + (int64_t)c * QNC;
         const int nc = (int)min((int64_t)QNC, ne - c0);
-        for (int i = tid; i < QNC * (QTB + 1); i += 256) {
-            const int j = i / (QTB + 1), m = i - j * (QTB + 1);
-            const int idx = t0 - sm.i0c[b][j] - 1 + m;  // pi column
-            const bool ok = j < nc && idx >= 0 && idx < Nt;
-            cp_async4(&sm.raw[b][j][m], pig + (size_t)(c0 + (j < nc ? j : 0)) * Nt + (ok ? idx : 0), ok);
+        for (int j = warp; j < QNC; j += 8) {
+            const int base = t0 - sm.i0c[b][j] - 1;  // pi column of staged element 0
+            const float *row = pig + (size_t)(c0 + (j < nc ? j : 0)) * Nt;
+            for (int m = lane; m < QTB + 1; m += 32) {
+                const int idx = base + m;
+                const bool ok = j < nc && idx >= 0 && idx < Nt;
+                cp_async4(&sm.raw[b][j][m], row + (ok ? idx : 0), ok);
+            }
         }
-        for (int i = tid; i < R * QNC; i += 256) {
-            const int r = i / QNC, j = i - r * QNC;
-            const bool ok = j < nc;
-            cp_async4(&sm.Cc[b][r][j], s.C + ((int64_t)k * R + r) * N + c0 + (ok ? j : 0), ok);
-        }
+        const bool okj = lane < nc;
+        for (int r = warp; r < R; r += 8)
+            cp_async4(&sm.Cc[b][r][lane], s.C + ((int64_t)k * R + r) * N + c0 + (okj ? lane : 0), okj);
     };
 
     int ri0 = 0;

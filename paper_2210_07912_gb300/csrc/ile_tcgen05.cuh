@@ -176,17 +176,18 @@ __device__ __forceinline__ void split(float x, uint32_t &hi, uint32_t &lo) {
 }
 
 // Split and pack one 16-byte K-chunk (8 BF16 or 4 TF32 elements, element 0 at the lowest address).
+// BF16 pairs are rounded two at a time (the same round-to-nearest-even of each element as split).
 template <bool BF16>
 __device__ __forceinline__ void pack_chunk(const float *v, uint4 &hi, uint4 &lo) {
     uint32_t h[4], l[4];
     if constexpr (BF16) {
 #pragma unroll
         for (int w = 0; w < 4; w++) {
-            uint32_t h0, l0, h1, l1;
-            split<true>(v[2 * w], h0, l0);
-            split<true>(v[2 * w + 1], h1, l1);
-            h[w] = h0 | (h1 << 16);
-            l[w] = l0 | (l1 << 16);
+            const __nv_bfloat162 hp = __floats2bfloat162_rn(v[2 * w], v[2 * w + 1]);
+            const float2 hf = __bfloat1622float2(hp);
+            const __nv_bfloat162 lp = __floats2bfloat162_rn(v[2 * w] - hf.x, v[2 * w + 1] - hf.y);
+            h[w] = *reinterpret_cast<const uint32_t *>(&hp);
+            l[w] = *reinterpret_cast<const uint32_t *>(&lp);
         }
     } else {
 #pragma unroll

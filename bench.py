@@ -177,11 +177,16 @@ def profile_traffic(kernel_file, prec):
     """DRAM bytes per launch of the contraction kernel from the committed ncu summary, if it was
     taken on the current source of that kernel (else None)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2210_07912_gb300", "csrc", kernel_file)
+    csrc = os.path.join(ROOT, "paper_2210_07912_gb300", "csrc")
+    # the kernel's source and the headers it is compiled with
+    srcs = [os.path.join(csrc, f) for f in (kernel_file, "ile_tcgen05.cuh", "ile_internal.cuh")]
     summ = os.path.join(ROOT, "profiles", f"contract_{prec}_c1.md")
-    if not (os.path.exists(src) and os.path.exists(summ)):
+    if not (all(os.path.exists(f) for f in srcs) and os.path.exists(summ)):
         return None, None
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in srcs:
+        h.update(open(f, "rb").read())
+    digest = h.hexdigest()[:16]
     vals = {}
     for line in open(summ):
         if ":" in line and line.strip().startswith("- "):

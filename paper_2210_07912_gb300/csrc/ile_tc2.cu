@@ -415,7 +415,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int row = q4 * 32 + lane;            // sample row in the tile = TMEM lane
         const uint32_t lane_addr = (uint32_t)(q4 * 32) << 16;
         float *my_row = rows + tid * RSTRIDE;
-        uint32_t gjob = 0, tiles_done = 0;
+        uint32_t tiles_done = 0;
+        uint32_t jtb = 0, jtpar = 0;  // TMEM buffer and phase parity of the next job (running)
+        auto next_job = [&]() {
+            if (++jtb == (uint32_t)NTB) {
+                jtb = 0;
+                jtpar ^= 1u;
+            }
+        };
         for (int64_t it = blockIdx.x; it < nitems && !failed; it += gridDim.x, tiles_done++) {
             int64_t tile;
             const Tc2Point &pt = work_item<BATCH>(one, pts, items, it, tile);
@@ -543,8 +550,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // b = g, g + 4, ... and it forms their part of c^H z + Re(c^T w)
             float aq = 0.f;
             for (int kq = 0; kq < K; kq++) {
-                const uint32_t tb = gjob % NTB;
-                if (!warp_wait(&sm.tfull[tb], (gjob / NTB) & 1u, flags)) {
+                const uint32_t tb = jtb;
+                if (!warp_wait(&sm.tfull[tb], jtpar, flags)) {
                     failed = true;
                     break;
                 }
@@ -570,7 +577,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
                 aq += part;
-                gjob++;
+                next_job();
                 jit.next();
             }
             if (failed) break;
@@ -689,8 +696,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                     for (int k = 0; k < ILE_MAX_DET; k++) {
                         if (k >= K) break;
-                        const uint32_t tb = gjob % NTB;
-                        if (!warp_wait(&sm.tfull[tb], (gjob / NTB) & 1u, flags)) {
+                        const uint32_t tb = jtb;
+                        if (!warp_wait(&sm.tfull[tb], jtpar, flags)) {
                             failed = true;
                             break;
                         }
@@ -699,7 +706,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         const int2 r = sm.dkr[warp][k];
                         consume(tb, i0d(k) - lo(k) + shift, mine ? (r.x + shift) & ~15 : 0x7fffffff,
                                 mine ? ((r.y + shift) & ~15) + 16 : -1, mine, wtd(k), Jc);
-                        gjob++;
+                        next_job();
                     }
                     if (failed) break;
                     finish_chunk(j0, Jc);
@@ -707,8 +714,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             } else {
                 while (!jit.done) {
                     const Job j = jit.get();
-                    const uint32_t tb = gjob % NTB;
-                    if (!warp_wait(&sm.tfull[tb], (gjob / NTB) & 1u, flags)) {
+                    const uint32_t tb = jtb;
+                    if (!warp_wait(&sm.tfull[tb], jtpar, flags)) {
                         failed = true;
                         break;
                     }
@@ -737,7 +744,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     }
                     consume(tb, s0, cmin, cmax, mine, wtd(j.k), j.Jc);
-                    gjob++;
+                    next_job();
                     jit.next_from(j);
                     if (j.k == K - 1 && j.w == j.W - 1) finish_chunk(j.j0, j.Jc);
                 }

@@ -63,6 +63,14 @@ constexpr int NBMAX = 4;                   // B ring depth upper bound
 constexpr int SLEEPS = 200000;             // bounded sleeping waits: SLEEPS x SLEEP_NS at most
 constexpr uint32_t SLEEP_NS = 10000;
 constexpr int RSTRIDE = 34;                // per-thread row: 32 staged columns + 2 (8-byte stores, half-warp conflict-free)
+constexpr float ILE_LOG2E_F = 1.4426950408889634f;  // log2(e)
+
+// 2^x with the SFU's base-2 exponential (approximate; flushes subnormal results to zero)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 struct Sm {
     uint64_t bfull[NBMAX], bempty[NBMAX], tfull[NTB], tempty[NTB], yready, aready, s4done, tdone, sready;
@@ -633,9 +641,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         s_run *= __expf(m_run - mc);
                         m_run = mc;
                     }
+                    // e^(D - m) = 2^(D log2(e) - m log2(e)): one FMA and one ex2 per bin
+                    const float ml2 = m_run * ILE_LOG2E_F;
 #pragma unroll
                     for (int jj = 0; jj < JG; jj++)
-                        if (jbeg + jj < Jc) s_run += __expf(D[jj] - m_run);
+                        if (jbeg + jj < Jc) s_run += ex2_approx(fmaf(D[jj], ILE_LOG2E_F, -ml2));
                 }
 #pragma unroll
                 for (int jj = 0; jj < JG; jj++) D[jj] = 0.f;

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         for (int b = 0; b < NTB; b++) {
             mbar_init(&sm.tfull[b], 1);
-            mbar_init(&sm.tempty[b], NMATH);
+            mbar_init(&sm.tempty[b], NMATH / 32);  // one arrival per math warp
         }
         mbar_init(&sm.yready, NMATH);
         mbar_init(&sm.aready, NMATH);
@@ -567,7 +567,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 uint32_t r[32];
                 tmem_ld32(tmem + tb * NWIN + lane_addr + (uint32_t)(32 * g), r);
                 fence_before();
-                mbar_arrive(&sm.tempty[tb]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.tempty[tb]);
                 const float fr = kq == 0 ? Fr[0] : kq == 1 ? Fr[1] : kq == 2 ? Fr[2] : Fr[3];
                 const float fi = kq == 0 ? Fi[0] : kq == 1 ? Fi[1] : kq == 2 ? Fi[2] : Fi[3];
                 // Re c_b = fr yr - fi yi, Im c_b = fr yi + fi yr;
@@ -668,7 +669,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
                 fence_before();
-                mbar_arrive(&sm.tempty[tb]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.tempty[tb]);
                 if (mine) {
                     const float omw = 1.f - w;
                     const float *src = my_row + (s0 & 15);

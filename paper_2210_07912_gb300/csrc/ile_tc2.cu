@@ -634,19 +634,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             if (jbeg + jj < Jc) out[o + jj] = (double)D[jj] - A_n;
                     }
                 } else if (jbeg < Jc) {
+                    // all JG bins in the chunk (the usual case), or the first Jc - jbeg of them
+                    const bool full = jbeg + JG <= Jc;
                     float mc = -INFINITY;
+                    if (full) {
 #pragma unroll
-                    for (int jj = 0; jj < JG; jj++)
-                        if (jbeg + jj < Jc) mc = fmaxf(mc, D[jj]);
+                        for (int jj = 0; jj < JG; jj++) mc = fmaxf(mc, D[jj]);
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < JG; jj++)
+                            if (jbeg + jj < Jc) mc = fmaxf(mc, D[jj]);
+                    }
                     if (mc > m_run) {
                         s_run *= __expf(m_run - mc);
                         m_run = mc;
                     }
                     // e^(D - m) = 2^(D log2(e) - m log2(e)): one FMA and one ex2 per bin
                     const float ml2 = m_run * ILE_LOG2E_F;
+                    if (full) {
 #pragma unroll
-                    for (int jj = 0; jj < JG; jj++)
-                        if (jbeg + jj < Jc) s_run += ex2_approx(fmaf(D[jj], ILE_LOG2E_F, -ml2));
+                        for (int jj = 0; jj < JG; jj++) s_run += ex2_approx(fmaf(D[jj], ILE_LOG2E_F, -ml2));
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < JG; jj++)
+                            if (jbeg + jj < Jc) s_run += ex2_approx(fmaf(D[jj], ILE_LOG2E_F, -ml2));
+                    }
                 }
 #pragma unroll
                 for (int jj = 0; jj < JG; jj++) D[jj] = 0.f;

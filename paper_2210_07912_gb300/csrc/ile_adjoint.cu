@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
         // stores to row 4 i + l / 8 at column 4 (l % 8) + e, i.e. 32 distinct banks per store
         const int NT4 = Nt / 4, rr = lane >> 3, cc = lane & 7;
         const float4 *src4 = reinterpret_cast<const float4 *>(Din + n0 * Nt);
-#pragma unroll 4
+#pragma unroll 8
         for (int it = warp; it < (NS / 4) * (NT4 / 8); it += 8) {
             const int rg = it / (NT4 / 8), c4 = (it - rg * (NT4 / 8)) * 8 + cc, nn = rg * 4 + rr;
             const float4 v = nn < ns ? src4[(size_t)nn * NT4 + c4] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -297,13 +297,17 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
         for (int j = lane; j < Nt; j += 32) m = fmaxf(m, d[j]);
         for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         float sum = 0.f;
-        for (int j = lane; j < Nt; j += 32) sum += expf(d[j] - m);
+        for (int j = lane; j < Nt; j += 32) {
+            const float e = expf(d[j] - m);
+            d[j] = e;  // kept for the normalisation pass
+            sum += e;
+        }
         for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         const float inv = 1.f / sum;
         const float gn = (float)g_lnL[src];
         float *pg = pig ? pig + (size_t)(n0 + nn) * Nt : nullptr;
         for (int j = lane; j < Nt; j += 32) {
-            float p = expf(d[j] - m) * inv;
+            const float p = d[j] * inv;
             d[j] = p;
             if (pg) pg[j] = gn * p;
         }

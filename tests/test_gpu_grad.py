@@ -107,6 +107,16 @@ def test_grad_two_detectors_ragged(ile, orc, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_grad_four_detectors_nt512(ile, orc, prec):
+    """K = 4 (H1/L1/V1/K1), M = 9, N_t = 512: four detectors through the 64-sample tensor-core
+    contraction of bf16x3 contexts; 333 samples (a ragged last CTA)."""
+    point = S.make_point(S.SEED_BASE + 63, 4, 9, 512, spectrum="decay")
+    th = S.prior_samples(np.random.default_rng(64), 333)
+    g = np.random.default_rng(65).normal(size=th.shape[1])
+    _compare_all(ile, orc, point, th, g, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_grad_long_window_four_detectors(ile, orc, prec):
     """N_t = 1024 (32-sample tiles; the bf16x3 context keeps the CUDA-core contraction), K = 4, M = 9."""
     point = S.make_point(S.SEED_BASE + 60, 4, 9, 1024, spectrum="decay")

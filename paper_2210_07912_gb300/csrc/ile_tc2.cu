@@ -227,10 +227,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&sm.tfull[b], 1);
             mbar_init(&sm.tempty[b], NMATH / 32);  // one arrival per math warp
         }
-        mbar_init(&sm.yready, NMATH);
-        mbar_init(&sm.aready, NMATH);
-        mbar_init(&sm.s4done, NMATH);
-        mbar_init(&sm.tdone, NMATH);
+        // the math-warp barriers count one arrival per warp (lane 0, after the warp synchronises)
+        mbar_init(&sm.yready, NMATH / 32);
+        mbar_init(&sm.aready, NMATH / 32);
+        mbar_init(&sm.s4done, NMATH / 32);
+        mbar_init(&sm.tdone, NMATH / 32);
         mbar_init(&sm.sready, 32);
         mbar_init_fence();
     }
@@ -473,7 +474,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     ys[a * TILE + row] = make_float2(yr, yi);
                 }
             }
-            mbar_arrive(&sm.yready);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.yready);
             if (!warp_wait(&sm.yready, tiles_done & 1u, flags)) {
                 failed = true;
                 break;
@@ -527,7 +529,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
             fence_async_smem();
-            mbar_arrive(&sm.aready);  // A operand and column ranges are written: the MMAs may start
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.aready);  // A operand and column ranges written: the MMAs may start
             if (!warp_wait(&sm.aready, tiles_done & 1u, flags)) {
                 failed = true;
                 break;
@@ -592,7 +595,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (failed) break;
             aq_s[tid] = 0.25f * aq;
             // everyone is done with the y table before the rows take the TMEM blocks
-            mbar_arrive(&sm.s4done);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.s4done);
             if (!warp_wait(&sm.s4done, tiles_done & 1u, flags)) {
                 failed = true;
                 break;
@@ -776,7 +780,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (failed) break;
             // ---- merge the four threads' partial log-sum-exps
             ls_s[tid] = make_float2(m_run, s_run);
-            mbar_arrive(&sm.tdone);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.tdone);
             if (!warp_wait(&sm.tdone, tiles_done & 1u, flags)) {
                 failed = true;
                 break;

@@ -200,20 +200,25 @@ def profile_traffic(kernel_file, prec):
         return None, digest
 
 
-def profile_tensor_active(kernel_file, prec):
-    """Tensor-pipe activity (fraction) of the committed ncu capture of the contraction kernel, if it
-    was taken on the current source (else None)."""
+def profile_fraction(kernel_file, prec, metric):
+    """A percentage metric (as a fraction) of the committed ncu capture of the contraction kernel,
+    if it was taken on the current source (else None)."""
     traffic, digest = profile_traffic(kernel_file, prec)
     if traffic is None:
         return None
     summ = os.path.join(ROOT, "profiles", f"contract_{prec}_c1.md")
     for line in open(summ):
-        if "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active" in line:
+        if line.strip().startswith(f"- {metric}:"):
             try:
                 return float(line.split(":", 1)[1].split()[0]) / 100.0
             except (IndexError, ValueError):
                 return None
     return None
+
+
+def profile_tensor_active(kernel_file, prec):
+    """Tensor-pipe activity (fraction) of the committed capture of the contraction kernel."""
+    return profile_fraction(kernel_file, prec, "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active")
 
 
 def batch_bench(ile, S, local, flush, iters=5, n_points=512, plain_iters=1):
@@ -475,6 +480,9 @@ def main():
         achieved = alg_flops / per_launch_s / 1e12
         roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": traffic, "tensor_pipe_active_ncu": profile_tensor_active(kfile, args.prec),
+                     # the kernel's actual limiter: instruction issue of its math warps
+                     "issue_active_ncu": profile_fraction(
+                         kfile, args.prec, "smsp__issue_active.avg.pct_of_peak_sustained_active"),
                      "algorithmic_flops_per_launch": alg_flops,
                      "launch_ms": per_launch_s * 1e3, "peak_source": pk_kind})
         launches = sum(c for (_, c) in prof.values())  # kernels launched by the library in the timed steps

@@ -117,7 +117,7 @@ __global__ void table2_kernel(Gl8 gl, Range r, const double *__restrict__ u_node
 struct Layout {
     int n1a, n1s, n2t, n2s;
     double tau1_max, tau2_lo, tau2_hi, s2_lo;
-    size_t off_t1, off_a1, off_t2, off_scratch, bytes;
+    size_t off_t1, off_a1, off_t2, off_t1p, off_t2p, off_scratch, bytes;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -135,12 +135,24 @@ Layout layout() {
     L.off_t1 = 0;
     L.off_a1 = align256(L.off_t1 + sizeof(float) * (size_t)L.n1a * L.n1s);
     L.off_t2 = align256(L.off_a1 + sizeof(float2) * (size_t)L.n1a);
-    L.off_scratch = align256(L.off_t2 + sizeof(float) * (size_t)L.n2t * L.n2s);
+    L.off_t1p = align256(L.off_t2 + sizeof(float) * (size_t)L.n2t * L.n2s);
+    L.off_t2p = align256(L.off_t1p + sizeof(float2) * (size_t)L.n1a * L.n1s);
+    L.off_scratch = align256(L.off_t2p + sizeof(float2) * (size_t)L.n2t * L.n2s);
     L.bytes = align256(L.off_scratch + sizeof(double) * (size_t)(L.n1a > L.n2t ? L.n1a : L.n2t));
     return L;
 }
 
 double tau2_of(double u, double xmin, double xmax) { return asinh((u - xmin) / EPS2) + asinh((u - xmax) / EPS2); }
+
+// Node pairs (t[i], t[i + 1]) of a row-major table with ncol columns, so that one 8-byte load
+// gives both ends of an interpolation interval (the last column pairs with itself; the lookups
+// never start an interval there).
+__global__ void pair_kernel(const float *__restrict__ t, int ncol, int64_t n, float2 *__restrict__ tp) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % ncol);
+    tp[i] = make_float2(t[i], c + 1 < ncol ? t[i + 1] : t[i]);
+}
 
 __global__ void dmarg_eval_kernel(const DmargParams dm, const double *__restrict__ a, const double *__restrict__ b,
                                   int64_t n, double *__restrict__ out) {
@@ -172,6 +184,8 @@ cudaError_t ile_build_dmarg(double d_min, double d_max, double d_ref, void *buf,
     float *t1 = reinterpret_cast<float *>(base + L.off_t1);
     float2 *a1 = reinterpret_cast<float2 *>(base + L.off_a1);
     float *t2 = reinterpret_cast<float *>(base + L.off_t2);
+    float2 *t1p = reinterpret_cast<float2 *>(base + L.off_t1p);
+    float2 *t2p = reinterpret_cast<float2 *>(base + L.off_t2p);
     double *nodes = reinterpret_cast<double *>(base + L.off_scratch);
     const Gl8 gl = gauss_legendre8();
     // table 1 nodes
@@ -206,6 +220,13 @@ cudaError_t ile_build_dmarg(double d_min, double d_max, double d_ref, void *buf,
     if (e != cudaSuccess) return e;
     table2_kernel<<<(L.n2t * L.n2s + 127) / 128, 128, 0, st>>>(gl, r, nodes, L.n2t, L.n2s, L.s2_lo, t2);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    {
+        const int64_t n1 = (int64_t)L.n1a * L.n1s, n2 = (int64_t)L.n2t * L.n2s;
+        pair_kernel<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(t1, L.n1a, n1, t1p);
+        pair_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(t2, L.n2t, n2, t2p);
+    }
+    e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
     dm = DmargParams{};
@@ -232,5 +253,7 @@ cudaError_t ile_build_dmarg(double d_min, double d_max, double d_ref, void *buf,
     dm.s2_lo = (float)L.s2_lo;
     dm.inv_ds2 = (float)(1.0 / DS2);
     dm.t2 = t2;
+    dm.t1p = t1p;
+    dm.t2p = t2p;
     return cudaSuccess;
 }

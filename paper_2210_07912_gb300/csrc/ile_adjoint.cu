@@ -39,23 +39,30 @@ constexpr int RMAX = 2 * ILE_MAX_MODES;  // real rows of the contraction (Re row
 constexpr int RP = 48;                   // rows padded to 3 x 16 for the backward GEMM
 constexpr int QT_LD = RP + 1;            // transposed Q chunk row stride (odd: conflict-free)
 
-// Tensor-core form of the E / slope contraction (BF16x3 contexts): per detector and 32-column
-// chunk, A = [P_E; P_D] (128 rows: the pi-weighted interpolation weights and their differences of
-// 64 samples, K = 32 columns) times B = Qp^T (N = RP rows, K-major), accumulated in TMEM over the
-// chunks; the hi/lo operands are double-buffered so that one chunk's MMAs run while the next is
-// built.
-constexpr int TC_NS = 64;                            // samples per CTA
-constexpr int TC_COLS = 32;                          // columns per chunk (two K steps of 16)
-constexpr int TC_KC = TC_COLS / 8;                   // 16-byte K chunks per chunk
-constexpr int TC_A_BYTES = TC_KC * 128 * 16;         // one of A hi / A lo
-constexpr int TC_B_BYTES = TC_KC * RP * 16;          // one of B hi / B lo
-constexpr int TC_BUF = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
+// Tensor-core forms (BF16x3 contexts).  Shared: 64 samples per adj_main CTA, the TMEM
+// accumulator width and the bounded waits.
+constexpr int TC_NS = 64;                            // samples per CTA of the main kernel
 constexpr uint32_t TC_TMEM_COLS = 64;                // >= RP, power of two
 constexpr int TC_SLEEPS = 200000;                    // bounded sleeping waits (x 10 us at most)
 constexpr uint32_t TC_SLEEP_NS = 10000;
+// E / slope contraction in adj_main: per detector and 64-column chunk, A = [P_E; P_D] (128 rows:
+// the pi-weighted interpolation weights of 64 samples and their differences, K = 64 columns, four
+// K steps) times B = Qp^T (N = RP rows, K-major), accumulated in TMEM over the chunks.  A is
+// single-buffered (every thread packs two of its 16-byte K chunks per chunk), B double-buffered.
+constexpr int AM_COLS = 64;
+constexpr int AM_KC = AM_COLS / 8;
+constexpr int AM_A_BYTES = AM_KC * 128 * 16;  // one of A hi / A lo
+constexpr int AM_B_BYTES = AM_KC * RP * 16;   // one of B hi / B lo
+constexpr int AM_SMEM = 2 * AM_A_BYTES + 4 * AM_B_BYTES;
+// dQ contraction in adj_gq_tc: per chunk of 32 samples (two K steps), A = P^T (128 columns) and
+// B = C (RP rows), both operand sets double-buffered.
+constexpr int TC_KC = 32 / 8;                        // 16-byte K chunks per chunk
+constexpr int TC_A_BYTES = TC_KC * 128 * 16;         // one of A hi / A lo
+constexpr int TC_B_BYTES = TC_KC * RP * 16;          // one of B hi / B lo
+constexpr int TC_BUF = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
 // columns of the transposed split operand: T_ext + one chunk of zeros, so that every chunk that
 // starts at or before the last column stays inside the array
-__host__ __device__ constexpr int adj_qt_cols(int T) { return T + TC_COLS; }
+__host__ __device__ constexpr int adj_qt_cols(int T) { return T + AM_COLS; }
 
 // d^l_{m,2}(iota) and its derivative d/diota, from the Wigner polynomial in c = cos(iota/2),
 // s = sin(iota/2): d/diota c^p s^q = (q c^(p+1) s^(q-1) - p c^(p-1) s^(q+1)) / 2.
@@ -106,7 +113,7 @@ struct MainSmem {
     __host__ __device__ static int ldd(int Nt) { return TC ? Nt + 1 : Nt; }
     static size_t floats(int Nt) {
         const size_t p1 = TC ? 0 : (size_t)RMAX * TCOL + (size_t)NS * (TCOL + 1);
-        const size_t p3 = TC ? 2 * (size_t)TC_BUF / 4 : (size_t)TCOL * QT_LD + 2 * (size_t)TCOL * (NS + 4);
+        const size_t p3 = TC ? (size_t)AM_SMEM / 4 : (size_t)TCOL * QT_LD + 2 * (size_t)TCOL * (NS + 4);
         const size_t ep = (size_t)NS * (4 * ILE_MAX_MODES + 1) + 4 + (size_t)ILE_MAX_DET * (ILE_MAX_MODES * (ILE_MAX_MODES + 1) / 2) * 4;
         size_t u = p1 > p3 ? p1 : p3;
         u = u > ep ? u : ep;
@@ -359,14 +366,16 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
 
     // ---------------------------------------------------------------- phase 3: E and slope sums
     if constexpr (TC) {
-        // tensor-core form.  Thread (nn, q) builds the rows nn (P_E) and 64 + nn (P_D) of its 16-byte
-        // K chunk q (8 columns) of A; thread 0 issues 2 K steps x 3 products (hi.hi, hi.lo, lo.hi)
-        // into the detector's accumulator and then starts the bulk copies of the next chunk's B
-        // (hi, lo) into the other buffer, so that they land while that chunk's A is built.
-        // Waits are bounded: a wait that runs out sets the timeout flag and tc_abort, after which no
-        // more MMAs are issued (every thread still passes every barrier).
-        const int nn = tid & (TC_NS - 1), q = tid >> 6;
+        // tensor-core form.  Per 64-column chunk, thread (nn, q0) builds the rows nn (P_E) and
+        // 64 + nn (P_D) of the 16-byte K chunks q0 and q0 + 4 (8 columns each) of A; thread 0
+        // issues 4 K steps x 3 products (hi.hi, hi.lo, lo.hi) into the detector's accumulator and
+        // then starts the bulk copies of the next chunk's B (hi, lo) into the other B buffer, so
+        // that they land while that chunk's A is built.  A is reused once the chunk's MMAs have
+        // completed.  Waits are bounded: a wait that runs out sets the timeout flag and tc_abort,
+        // after which no more MMAs are issued (every thread still passes every barrier).
+        const int nn = tid & (TC_NS - 1), q0 = tid >> 6;
         uint8_t *tcb = reinterpret_cast<uint8_t *>(U1);
+        uint4 *Ah = reinterpret_cast<uint4 *>(tcb), *Al = Ah + AM_A_BYTES / 16;
         const uint32_t id = idesc(1, 128, RP);
         const uint64_t a_ks = (uint64_t)(2 * 128 * 16) >> 4, b_ks = (uint64_t)(2 * RP * 16) >> 4;
         const int TQ8 = adj_qt_cols(T) / 8;
@@ -378,86 +387,88 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
                 tc_abort = 1;
             }
         };
+        auto b_hi = [&](int b) { return reinterpret_cast<uint4 *>(tcb + 2 * AM_A_BYTES + b * 2 * AM_B_BYTES); };
         auto copy_b = [&](int b, int k, int c0) {
-            uint4 *Bh = reinterpret_cast<uint4 *>(tcb + b * TC_BUF + 2 * TC_A_BYTES), *Bl = Bh + TC_B_BYTES / 16;
-            mbar_arrive_expect_tx(&tc_bfull[b], 2u * TC_B_BYTES);
+            uint4 *Bh = b_hi(b), *Bl = Bh + AM_B_BYTES / 16;
+            mbar_arrive_expect_tx(&tc_bfull[b], 2u * AM_B_BYTES);
             const size_t off = ((size_t)k * TQ8 + (size_t)(c0 / 8)) * RP;
-            bulk_g2s(Bh, QThi + off, TC_B_BYTES, &tc_bfull[b]);
-            bulk_g2s(Bl, QTlo + off, TC_B_BYTES, &tc_bfull[b]);
+            bulk_g2s(Bh, QThi + off, AM_B_BYTES, &tc_bfull[b]);
+            bulk_g2s(Bl, QTlo + off, AM_B_BYTES, &tc_bfull[b]);
         };
-        uint32_t gch = 0;        // chunks issued so far, over all detectors
+        uint32_t gch = 0;          // chunks issued so far, over all detectors
         int64_t last_commit = -1;  // (thread 0) the last chunk whose MMAs were committed
         for (int k = 0; k < K; k++) {
             __syncthreads();
             load_detector(k);
             __syncthreads();
-            // chunks of 32 columns from the tile's first window column (rounded down to 8) to its
+            // chunks of 64 columns from the tile's first window column (rounded down to 8) to its
             // last lerp partner, inside [0, T_ext)
             const int lo8 = max(lo_s[k], 0) & ~7;
             const int cend = min(hi_s[k] + Nt, T - 1);
-            const int nch = cend >= lo8 ? (cend - lo8) / TC_COLS + 1 : 0;
+            const int nch = cend >= lo8 ? (cend - lo8) / AM_COLS + 1 : 0;
             for (int ci = 0; ci < nch; ci++, gch++) {
-                const int b = (int)(gch & 1u);
-                const int c0 = lo8 + ci * TC_COLS;
-                uint4 *Ah = reinterpret_cast<uint4 *>(tcb + b * TC_BUF), *Al = Ah + TC_A_BYTES / 16;
-                uint4 *Bh = Al + TC_A_BYTES / 16, *Bl = Bh + TC_B_BYTES / 16;
-                // buffer b is free once the MMAs of chunk gch - 2 have completed
-                if (gch >= 2) wait(&tc_mma[b], ((gch - 2) >> 1) & 1u);
-                if (tid == 0 && ci == 0 && !aborted()) copy_b(b, k, c0);  // a detector's first chunk
+                const int bb = (int)(gch & 1u);  // B buffer of this chunk
+                const int c0 = lo8 + ci * AM_COLS;
+                // A (and the other B buffer) are free once the previous chunk's MMAs have completed
+                if (gch >= 1) wait(&tc_mma[0], (gch - 1) & 1u);
+                if (tid == 0 && ci == 0 && !aborted()) copy_b(bb, k, c0);  // a detector's first chunk
                 {
-                    const int j0 = c0 + 8 * q - i0s[nn];  // window bin of the chunk's column 8 q
                     const float wt = ws[nn];
                     const float *pr = Ds + (size_t)nn * LDD;
-                    float pe[8], pd[8];
-                    float prev = (j0 >= 1 && j0 <= Nt) ? pr[j0 - 1] : 0.f;
 #pragma unroll
-                    for (int e = 0; e < 8; e++) {
-                        const int j = j0 + e;
-                        const float cur = (j >= 0 && j < Nt) ? pr[j] : 0.f;
-                        pe[e] = (1.f - wt) * cur + wt * prev;
-                        pd[e] = prev - cur;
-                        prev = cur;
+                    for (int it = 0; it < 2; it++) {
+                        const int q = q0 + 4 * it;
+                        const int j0 = c0 + 8 * q - i0s[nn];  // window bin of the chunk's column 8 q
+                        float pe[8], pd[8];
+                        float prev = (j0 >= 1 && j0 <= Nt) ? pr[j0 - 1] : 0.f;
+#pragma unroll
+                        for (int e = 0; e < 8; e++) {
+                            const int j = j0 + e;
+                            const float cur = (j >= 0 && j < Nt) ? pr[j] : 0.f;
+                            pe[e] = (1.f - wt) * cur + wt * prev;
+                            pd[e] = prev - cur;
+                            prev = cur;
+                        }
+                        uint4 h, l;
+                        pack_chunk<true>(pe, h, l);
+                        Ah[q * 128 + nn] = h;
+                        Al[q * 128 + nn] = l;
+                        pack_chunk<true>(pd, h, l);
+                        Ah[q * 128 + TC_NS + nn] = h;
+                        Al[q * 128 + TC_NS + nn] = l;
                     }
-                    uint4 h, l;
-                    pack_chunk<true>(pe, h, l);
-                    Ah[q * 128 + nn] = h;
-                    Al[q * 128 + nn] = l;
-                    pack_chunk<true>(pd, h, l);
-                    Ah[q * 128 + TC_NS + nn] = h;
-                    Al[q * 128 + TC_NS + nn] = l;
                 }
-                // A written: arrive instead of a block barrier, so that the other warps go on to the
-                // next chunk while thread 0 issues this one
+                // A written: arrive instead of a block barrier, so that thread 0 issues the chunk as
+                // soon as the last warp is done
                 fence_async_smem();
-                mbar_arrive(&tc_aready[b]);
+                mbar_arrive(&tc_aready[0]);
                 if (tid == 0) {
-                    wait(&tc_aready[b], (gch >> 1) & 1u);
-                    wait(&tc_bfull[b], (gch >> 1) & 1u);
+                    wait(&tc_aready[0], gch & 1u);
+                    wait(&tc_bfull[bb], (gch >> 1) & 1u);
                     if (!aborted()) {
                         fence_after();
+                        uint4 *Bh = b_hi(bb), *Bl = Bh + AM_B_BYTES / 16;
                         const uint64_t ah = sdesc(smem_u32(Ah), 128 * 16, 128), al = sdesc(smem_u32(Al), 128 * 16, 128);
                         const uint64_t bh = sdesc(smem_u32(Bh), RP * 16, 128), bl = sdesc(smem_u32(Bl), RP * 16, 128);
                         uint32_t acc = ci > 0 ? 1u : 0u;
                         for (int pass = 0; pass < 3; pass++) {
                             const uint64_t ad = pass == 2 ? al : ah;
                             const uint64_t bd = pass == 1 ? bl : bh;
-                            for (int ks = 0; ks < TC_COLS / 16; ks++) {
+                            for (int ks = 0; ks < AM_COLS / 16; ks++) {
                                 mma_bf16(tmem, ad + (uint64_t)ks * a_ks, bd + (uint64_t)ks * b_ks, id, acc);
                                 acc = 1u;
                             }
                         }
-                        mma_commit(&tc_mma[b]);
+                        mma_commit(&tc_mma[0]);
                         last_commit = gch;
                     }
-                    // the next chunk's B goes to the other buffer once chunk gch - 1's MMAs are done
-                    if (ci + 1 < nch) {
-                        if (gch >= 1) wait(&tc_mma[b ^ 1], ((gch - 1) >> 1) & 1u);
-                        if (!aborted()) copy_b(b ^ 1, k, c0 + TC_COLS);
-                    }
+                    // the next chunk's B goes to the other buffer (its previous chunk, gch - 1, has
+                    // completed: every thread waited for it at the top of this chunk)
+                    if (ci + 1 < nch && !aborted()) copy_b(bb ^ 1, k, c0 + AM_COLS);
                 }
             }
             // the detector's sums: rows 0-63 E(r), rows 64-127 the slope terms dE(r)
-            if (nch > 0) wait(&tc_mma[(gch - 1) & 1u], ((gch - 1) >> 1) & 1u);
+            if (nch > 0) wait(&tc_mma[0], (gch - 1) & 1u);
             __syncthreads();  // tc_abort is final for this detector: the branch below is uniform
             const bool have = nch > 0 && !aborted();
             fence_after();
@@ -496,8 +507,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
         }
         // no MMA may still be writing TMEM when it is released (bounded)
         if (tid == 0 && aborted() && last_commit >= 0)
-            mbar_wait_sleep(&tc_mma[last_commit & 1], (uint32_t)(last_commit >> 1) & 1u, flags, 0u, TC_SLEEPS,
-                            TC_SLEEP_NS);
+            mbar_wait_sleep(&tc_mma[0], (uint32_t)last_commit & 1u, flags, 0u, TC_SLEEPS, TC_SLEEP_NS);
     } else {
         const int ty = tid >> 4, tx = tid & 15;
         for (int k = 0; k < K; k++) {
@@ -880,6 +890,7 @@ __global__ void __launch_bounds__(256, 2)
 // sample split; operand buffers alternate between chunks.  Waits are bounded (a wait that runs
 // out sets ILE_FLAG_TIMEOUT and stops further MMAs; every thread still passes every barrier).
 static_assert(QNC == 32, "the staging maps one lane to one sample of a chunk");
+static_assert(TC_KC * 8 == QNC, "one dQ chunk is TC_KC 16-byte K chunks of samples");
 struct GqTcSmem {
     uint8_t ops[2][TC_BUF];  // A hi | A lo | B hi | B lo
     float raw[2][QNC][QRW];

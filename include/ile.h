@@ -397,16 +397,21 @@ const char *ile_batch_last_error(const ile_batch *b);
  * adjoint kernels.  The paper gives no derivative: this is the exact derivative of the
  * time-marginalised likelihood of Eq. (eq:loglikelihood) as computed (linear interpolation of Q
  * differentiated inside the bin the window start falls in), in FP32 per sample with FP64 sums
- * over samples; the coefficient stage is recomputed from the samples.
+ * over samples; the coefficient stage is recomputed from the samples.  The context's precision
+ * selects the contractions: FP32 contexts recompute the data term and contract on CUDA cores;
+ * BF16x3 contexts take the data term from the fused tensor-core forward kernel and run the
+ * E / interpolation-slope and dQ contractions as BF16x3 tensor-core GEMMs (FP32 accumulation).
  *   samples: SoA [7][N] FP64 as in ile_eval; g_lnL: [N] upstream weights.
  *   g_samples: [7][N] d/d(ra, dec, psi, iota, phi, D_Mpc, tc_s) of each sample, times g_lnL[n].
  *   g_Q: [n_det][n_modes][T_ext][2]; g_U, g_V: [n_det][n_modes][n_modes][2]: derivatives with
  *   respect to the real and imaginary part of every entry, the entries taken as independent
  *   (no Hermitian or symmetric tying), summed over the samples.  U and V themselves must be
  *   Hermitian / symmetric as ile_set_data requires.
- *   lnL_t_out: [N] lnL_t recomputed by the adjoint's FP32 forward pass.
+ *   lnL_t_out: [N] lnL_t recomputed by the adjoint's forward pass.
  * Any output may be NULL (at least one is required); 1 <= N <= ILE_GRAD_MAX_SAMPLES.  Device
- * memory: N * n_window * 4 bytes of scratch when g_Q is requested.  flags: ILE_DEVICE_PTRS.
+ * memory: N * n_window * 4 bytes of scratch when g_Q is requested, and in BF16x3 contexts
+ * whenever g_samples, g_Q or lnL_t_out is; a timed-out device wait returns ILE_E_TIMEOUT.
+ * flags: ILE_DEVICE_PTRS.
  */
 ile_status ile_eval_grad(ile_ctx *ctx, const double *samples, int64_t N, const double *g_lnL, double *g_samples,
                          double *g_Q, double *g_U, double *g_V, double *lnL_t_out, unsigned flags);

@@ -29,7 +29,8 @@
  *
  * Ownership: the caller owns every buffer it passes.  ile_set_data copies its inputs into
  * context-owned device memory, so the caller may free them on return.  Outputs are written in
- * full, or left untouched when the call fails before launching work.
+ * full, or not at all: a host-pointer call that fails (including a range, non-finite or timeout
+ * error raised on the device) leaves the caller's output buffers untouched.
  *
  * Pointers: without ILE_DEVICE_PTRS every array argument is a host pointer and the call is
  * synchronous (it returns after the results are in host memory).  With ILE_DEVICE_PTRS they are
@@ -283,10 +284,12 @@ ile_status ile_profile_read(ile_ctx *ctx, double *out_ms, int64_t *out_count, in
  * current CUDA device; the work is queued on cuda_stream (a cudaStream_t; NULL = legacy default
  * stream) and the call returns without waiting.  It needs no context and allocates nothing: its
  * scratch (the per-block partial sums) is a fixed array inside the library, 24 KB on every
- * device that loads the library, kept until the process exits.
+ * device that loads the library, kept as long as the CUDA context that loaded it (normally until
+ * the process exits).
  *   N must be in [1, ILE_NOALLOC_MAX_SAMPLES]; larger N returns ILE_E_ARG (use ile_integrate).
- *   The first call on each device looks up the array's device address (cudaGetSymbolAddress);
- *   make that first call before capturing a stream into a CUDA graph.
+ *   Every call looks up the array's device address (cudaGetSymbolAddress), so the entry point
+ *   keeps working after cudaDeviceReset; the first call on a device may load the library's device
+ *   code into the context, so make that first call before capturing a stream into a CUDA graph.
  *   Every call shares the one array: calls whose work overlaps on the GPU (on different streams,
  *   or from different host threads without ordering) race and may return wrong results.
  *   Returns ILE_E_CUDA if the device address cannot be obtained or a launch fails.
@@ -426,6 +429,16 @@ ile_status ile_eval_grad(ile_ctx *ctx, const double *samples, int64_t N, const d
 ile_status ile_integrate_grad(ile_ctx *ctx, const double *samples, const double *ln_prior, const double *ln_ps,
                               int64_t N, const double *g_scale, double *result, double *g_samples, double *g_Q,
                               double *g_U, double *g_V, unsigned flags);
+
+/*
+ * The sampler's random-number generator, exposed for known-answer tests: Philox4x32-10 (Salmon,
+ * Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11), the generator the
+ * device sampler draws its words from (Sec. "GPU-accelerated Monte Carlo integration" draws the
+ * samples on the GPU).  ctr_key: [n][6] device array, counter words 0..3 then key words 0..1;
+ * out: [n][4] device array of output words.  Queued on cuda_stream (a cudaStream_t; NULL = legacy
+ * default stream) without waiting; 1 <= n <= 2^24, else ILE_E_ARG.  Allocates nothing.
+ */
+ile_status ile_philox4x32_10(const uint32_t *ctr_key, int64_t n, uint32_t *out, void *cuda_stream);
 
 /* Wait for the context's stream and return the first device-side error seen since the last call. */
 ile_status ile_sync(ile_ctx *ctx);

@@ -454,3 +454,46 @@ def adapt_run(point, seed: int, N: int, n_iter: int, adapt_mask: int, eps: float
         last = dict(theta=theta, lnw_prior=lwp, bins=bins, lnL=lnl, hist=hists, u=u, gmm=gmm_before)
     pooled = mc_stats(np.concatenate(lnw_all))
     return dict(pooled=pooled, iters=iters, cdf=cdf, last=last, gmm=gmm)
+
+
+# ------------------------------------------------------------------------------------ loud injections
+def injection_coeffs(point, theta0):
+    """True coefficients c0_k,lm = (D_ref/D) F_k Y_lm and arrival times t0_k = t_c + dt_k of the
+    extrinsic sample theta0 (7,) for the detectors and modes of `point` (Eq. (eq:loglikelihood):
+    the coefficients of the likelihood's h_k at theta0)."""
+    K, M = point.n_det, point.n_modes
+    ra, dec, psi, iota, phi, dist, tc = (float(x) for x in theta0)
+    c0 = np.array([[(point.d_ref / dist) * antenna(point.det_tensor[k], ra, dec, psi, point.gmst) *
+                    sylm(int(l), int(m), iota, phi) for (l, m) in point.lm] for k in range(K)])
+    t0 = np.array([tc + delay(point.det_pos[k], ra, dec, point.gmst) for k in range(K)])
+    return c0, t0
+
+
+def loud_point(S, seed: int, rho2: float, n_det: int = 3, n_modes: int = 21, n_window: int = 512,
+               spectrum: str = "decay", theta0=None):
+    """A loud intrinsic point: a pulse injected at theta0 with <h0|h0> = rho2 (so the data term of
+    samples near theta0 is about rho2 and lnL_t about rho2/2), the U and V of the synthetic
+    recipe scaled up until the injection has that strength (App. "Choices for finite-precision
+    floating point arithmetic and overflow" discusses SNRs rho ~ 35 and beyond).  S is the
+    synthetic-input module.  Returns (point, theta0)."""
+    if theta0 is None:
+        theta0 = np.array([1.3, 0.35, 0.8, 0.6, 2.2, 400.0, 0.5 / S.FS])
+    theta0 = np.asarray(theta0, float)
+    probe = S.make_point(seed, n_det, n_modes, n_window, spectrum=spectrum, noise=0.0, pulse_sigma=None)
+    c0, t0 = injection_coeffs(probe, theta0)
+    _, _, A0 = lnL_grid(probe, theta0)          # A = <h|h>/2 of theta0 at unit scale
+    scale = rho2 / (2.0 * A0)
+    point = S.make_point(seed, n_det, n_modes, n_window, spectrum=spectrum, c_true=c0, t_true=t0, uv_scale=scale)
+    return point, theta0
+
+
+def loud_samples(S, rng, theta0, n_near: int, n_prior: int, spread: float = 1.0):
+    """Samples for a loud point: n_near Gaussian perturbations of theta0 (the region that holds the
+    posterior mass and the largest |lnL_t|) followed by n_prior draws from the extrinsic prior."""
+    sd = spread * np.array([0.02, 0.02, 0.05, 0.05, 0.05, 0.0, 0.2 / S.FS])
+    near = theta0[:, None] + sd[:, None] * rng.normal(size=(7, n_near))
+    near[5] = theta0[5] * np.exp(0.05 * spread * rng.normal(size=n_near))
+    near[0] = np.mod(near[0], 2 * np.pi)
+    near[1] = np.clip(near[1], -1.5, 1.5)
+    near[6] = np.clip(near[6], -3.5 / S.FS, 3.5 / S.FS)
+    return np.concatenate([near, S.prior_samples(rng, n_prior)], axis=1)

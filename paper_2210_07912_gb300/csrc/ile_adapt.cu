@@ -56,6 +56,16 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
     out[3] = c3;
 }
 
+// Known-answer check of the generator: out[i] = Philox4x32-10(counter ck[6i .. 6i+3], key ck[6i+4 .. 6i+5]).
+__global__ void philox_kat_kernel(const uint32_t *__restrict__ ck, int64_t n, uint32_t *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t *c = ck + 6 * i;
+    uint32_t w[4];
+    philox4x32_10(c[0], c[1], c[2], c[3], c[4], c[5], w);
+    for (int q = 0; q < 4; q++) out[4 * i + q] = w[q];
+}
+
 // Uniform in (0, 1) from the top 23 bits of a word (exact in FP32).
 __device__ __forceinline__ float unit23(uint32_t w) { return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f); }
 
@@ -482,4 +492,10 @@ cudaError_t ile_launch_batch_adapt(int n_points, const IleBatchPoint *bp, const 
         bhist_kernel<<<n_hblk, HIST_THREADS, 0, st>>>(bp, hblk, lnL, lnw_prior, bins, iter_res, hist_fx);
     brenorm_kernel<<<n_points, 1024, 0, st>>>(bp, hist_fx, hist, cdf, lnps_tab, iter_res, pooled, iter_log, iter_dev);
     return cudaGetLastError();
+}
+
+extern "C" ile_status ile_philox4x32_10(const uint32_t *ctr_key, int64_t n, uint32_t *out, void *cuda_stream) {
+    if (!ctr_key || !out || n < 1 || n > (1ll << 24)) return ILE_E_ARG;
+    philox_kat_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)cuda_stream>>>(ctr_key, n, out);
+    return cudaGetLastError() == cudaSuccess ? ILE_OK : ILE_E_CUDA;
 }

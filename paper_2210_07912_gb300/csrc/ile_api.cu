@@ -249,6 +249,13 @@ ile_status read_flags(ile_ctx *ctx) {
     return ILE_OK;
 }
 
+// Host-pointer calls: the device-side flags are read (and the stream synchronised) before any
+// output is copied back, so a call that fails leaves the caller's buffers untouched.
+ile_status finish_host_copies(ile_ctx *ctx) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ILE_OK;
+}
+
 // Operand rows of the split-precision contraction for the current point (built once per point).
 ile_status ensure_tc_operands(ile_ctx *ctx, int prec) {
     if (ctx->Qtc_ready[prec]) return ILE_OK;
@@ -392,12 +399,14 @@ ile_status run_grad_host(ile_ctx *ctx, const double *samples, const double *g, i
     ile_status st = run_grad(ctx, ctx->theta, ctx->g_in, N, g_theta ? d_th : nullptr, gQ ? d_q : nullptr,
                              gU ? d_u : nullptr, gV ? d_v : nullptr, lnl ? d_l : nullptr);
     if (st != ILE_OK) return st;
+    st = read_flags(ctx);
+    if (st != ILE_OK) return st;
     if (g_theta) CK(cudaMemcpyAsync(g_theta, d_th, sizeof(double) * nth, cudaMemcpyDeviceToHost, ctx->stream));
     if (gQ) CK(cudaMemcpyAsync(gQ, d_q, sizeof(double) * nq, cudaMemcpyDeviceToHost, ctx->stream));
     if (gU) CK(cudaMemcpyAsync(gU, d_u, sizeof(double) * nuv, cudaMemcpyDeviceToHost, ctx->stream));
     if (gV) CK(cudaMemcpyAsync(gV, d_v, sizeof(double) * nuv, cudaMemcpyDeviceToHost, ctx->stream));
     if (lnl) CK(cudaMemcpyAsync(lnl, d_l, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
-    return read_flags(ctx);
+    return finish_host_copies(ctx);
 }
 
 }  // namespace
@@ -770,8 +779,10 @@ ile_status ile_eval(ile_ctx *ctx, const double *samples, int64_t N, double *out,
                        ctx->stream));
     st = run_eval(ctx, ctx->theta, N, ctx->out, full);
     if (st != ILE_OK) return st;
+    st = read_flags(ctx);
+    if (st != ILE_OK) return st;
     CK(cudaMemcpyAsync(out, ctx->out, sizeof(double) * out_elems, cudaMemcpyDeviceToHost, ctx->stream));
-    return read_flags(ctx);
+    return finish_host_copies(ctx);
 }
 
 ile_status ile_integrate(ile_ctx *ctx, const double *samples, const double *ln_prior, const double *ln_ps,
@@ -810,9 +821,11 @@ ile_status ile_integrate(ile_ctx *ctx, const double *samples, const double *ln_p
         CK(ile_launch_mc(ctx->out, ln_prior ? ctx->lnp : nullptr, ln_ps ? ctx->lnps : nullptr, N, ctx->part, np,
                          ctx->result, ctx->stream));
     }
+    st = read_flags(ctx);
+    if (st != ILE_OK) return st;
     CK(cudaMemcpyAsync(result, ctx->result, 7 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if (lnL_t_out) CK(cudaMemcpyAsync(lnL_t_out, ctx->out, sizeof(double) * N, cudaMemcpyDeviceToHost, ctx->stream));
-    return read_flags(ctx);
+    return finish_host_copies(ctx);
 }
 
 ile_status ile_eval_grad(ile_ctx *ctx, const double *samples, int64_t N, const double *g_lnL, double *g_samples,
@@ -875,12 +888,14 @@ ile_status ile_integrate_grad(ile_ctx *ctx, const double *samples, const double 
     st = run_grad(ctx, ds, ctx->g_in, N, g_samples ? d_th : nullptr, g_Q ? d_q : nullptr, g_U ? d_u : nullptr,
                   g_V ? d_v : nullptr, nullptr);
     if (st != ILE_OK) return st;
+    st = read_flags(ctx);
+    if (st != ILE_OK) return st;
     CK(cudaMemcpyAsync(result, ctx->result, 7 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if (g_samples) CK(cudaMemcpyAsync(g_samples, d_th, sizeof(double) * nth, cudaMemcpyDeviceToHost, ctx->stream));
     if (g_Q) CK(cudaMemcpyAsync(g_Q, d_q, sizeof(double) * nq, cudaMemcpyDeviceToHost, ctx->stream));
     if (g_U) CK(cudaMemcpyAsync(g_U, d_u, sizeof(double) * nuv, cudaMemcpyDeviceToHost, ctx->stream));
     if (g_V) CK(cudaMemcpyAsync(g_V, d_v, sizeof(double) * nuv, cudaMemcpyDeviceToHost, ctx->stream));
-    return read_flags(ctx);
+    return finish_host_copies(ctx);
 }
 
 static ile_status adapt_alloc(ile_ctx *ctx, int64_t N) {

@@ -1,8 +1,8 @@
 // ile_mc.cu -- stage S6: Monte Carlo marginal likelihood of Eq. (eq:lnL:MonteCarlo) in log space.
 //
 // ln w_n = lnL_t(n) + ln p(theta_n) - ln p_s(theta_n).  Each block reduces one contiguous chunk to
-// a partial (max ln w, S1 = sum e^{ln w - max}, S2 = sum e^{2(ln w - max)}) -- the exponentials in
-// FP32 relative to the block maximum, the sums in FP64 -- and a one-block merge combines the
+// a partial (max ln w, S1 = sum e^{ln w - max}, S2 = sum e^{2(ln w - max)}) -- exponentials and
+// sums in FP64, relative to the block maximum -- and a one-block merge combines the
 // partials in a fixed tree order, so the result does not depend on scheduling.  The merge gives
 //   ln I = max + ln(S1/N),  sigma_ln = sigma_I / I = sqrt((N S2/S1^2 - 1)/(N - 1)),
 //   n_eff = S1 (= sum w / max w, Eq. (eq:neff)),  ess = S1^2 / S2 (Eq. (eq:neff_ESS)).
@@ -42,9 +42,9 @@ __device__ __forceinline__ void mc_partial_chunk(const double *__restrict__ lnL,
     m = block_reduce(m, [](double a, double b) { return fmax(a, b); }, sh);
     double s1 = 0.0, s2 = 0.0;
     for (int64_t n = beg + threadIdx.x; n < end; n += MC_THREADS) {
-        float e = expf((float)(lnw_at(lnL, lp, lps, n) - m));
-        s1 += (double)e;
-        s2 += (double)e * (double)e;
+        const double e = exp(lnw_at(lnL, lp, lps, n) - m);
+        s1 += e;
+        s2 += e * e;
     }
     s1 = block_reduce(s1, [](double a, double b) { return a + b; }, sh);
     s2 = block_reduce(s2, [](double a, double b) { return a + b; }, sh);
@@ -160,10 +160,11 @@ cudaError_t ile_launch_mc(const double *lnL_t, const double *ln_prior, const dou
 //
 // ile_mc_reduce_noalloc runs the same two kernels with their per-block partial sums in a
 // file-scope device array instead of context-owned memory, for callers that may not allocate
-// device memory (see include/ile.h).  The array lives as long as the library is loaded, on every
-// device that loads it.  Host code must not pass the symbol itself to a kernel (on the host it is
-// only a stand-in); its device address is looked up once per device with cudaGetSymbolAddress.
-#include <mutex>
+// device memory (see include/ile.h).  The array exists on every device that loads the library,
+// for as long as the CUDA context that loaded it (normally until the process exits).  Host code
+// must not pass the symbol itself to a kernel (on the host it is only a stand-in); its device
+// address is looked up with cudaGetSymbolAddress on every call, so a context rebuilt by
+// cudaDeviceReset gets the new array's address rather than a stale one.
 
 namespace {
 
@@ -172,28 +173,15 @@ static_assert(ILE_NOALLOC_MAX_SAMPLES % MC_CHUNK == 0, "scratch sizing");
 
 static __device__ __align__(256) double g_noalloc_partials[3 * NOALLOC_MAX_PART];
 
-constexpr int NOALLOC_MAX_DEVICES = 64;
-std::mutex g_noalloc_mutex;
-double *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
-
 }  // namespace
 
 extern "C" ile_status ile_mc_reduce_noalloc(const double *lnL_t, const double *ln_prior, const double *ln_ps,
                                             int64_t N, double *result, void *cuda_stream) {
     if (!lnL_t || !result || N < 1) return ILE_E_ARG;
     if (N > ILE_NOALLOC_MAX_SAMPLES) return ILE_E_ARG;  // the fixed scratch holds this many samples' partials
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return ILE_E_CUDA;
-    double *part = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[dev]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return ILE_E_CUDA;
-            g_noalloc_ptr[dev] = static_cast<double *>(p);
-        }
-        part = g_noalloc_ptr[dev];
-    }
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return ILE_E_CUDA;
+    double *part = static_cast<double *>(p);
     // every partial the merge reads is written by the partial kernel of the same call, so the
     // shared array needs no clearing between calls
     const int np = ile_mc_partial_count(N);

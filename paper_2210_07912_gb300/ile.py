@@ -149,6 +149,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ile_merge_partials.restype = i32
     lib.ile_mc_reduce_noalloc.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ile_mc_reduce_noalloc.restype = i32
+    lib.ile_philox4x32_10.argtypes = [vp, i64, vp, vp]
+    lib.ile_philox4x32_10.restype = i32
     lib.ile_batch_create.argtypes = [P(vp), i32, vp, i32]
     lib.ile_batch_destroy.argtypes = [vp]
     lib.ile_batch_set_points.argtypes = [vp, i32, P(PointDesc)]
@@ -238,14 +240,41 @@ def mc_reduce_noalloc(lnL_t, result, ln_prior=None, ln_ps=None, stream=None):
     float64 on the current device; N = lnL_t.numel() must not exceed NOALLOC_MAX_SAMPLES.
     Queued on `stream` (torch stream or raw handle; None = legacy default stream)."""
     lib = load()
+    import torch
     N = lnL_t.numel()
     if N > NOALLOC_MAX_SAMPLES:
         raise IleError(ILE_E_ARG, "ile_mc_reduce_noalloc",
                        f"N = {N} exceeds the fixed scratch of {NOALLOC_MAX_SAMPLES} samples")
+    # the kernels read N doubles of every input and write 7 of result on the current device: refuse
+    # anything else before it reaches them
+    cur = torch.cuda.current_device()
+    for name, t, need in (("lnL_t", lnL_t, N), ("ln_prior", ln_prior, N), ("ln_ps", ln_ps, N), ("result", result, 7)):
+        if t is None:
+            if name in ("lnL_t", "result"):
+                raise IleError(ILE_E_ARG, "ile_mc_reduce_noalloc", f"{name} is required")
+            continue
+        if not t.is_cuda or t.device.index != cur or t.dtype != torch.float64 or not t.is_contiguous() \
+                or t.numel() < need:
+            raise IleError(ILE_E_ARG, "ile_mc_reduce_noalloc",
+                           f"{name} must be a contiguous float64 CUDA tensor on device {cur} with >= {need} elements")
     st = lib.ile_mc_reduce_noalloc(_dev_ptr(lnL_t), _dev_ptr(ln_prior), _dev_ptr(ln_ps), N, _dev_ptr(result),
                                    _stream_handle(stream))
     if st != ILE_OK:
         raise IleError(st, "ile_mc_reduce_noalloc")
+
+
+def philox4x32_10(ctr_key, out, stream=None):
+    """Philox4x32-10 words of the device sampler's generator: ctr_key is a CUDA int32/uint32
+    tensor [n][6] (counter words 0..3, key words 0..1), out a CUDA tensor [n][4] of the same
+    dtype.  Queued on `stream` (None = legacy default stream)."""
+    lib = load()
+    n = ctr_key.shape[0]
+    if ctr_key.shape != (n, 6) or out.shape != (n, 4) or not (ctr_key.is_cuda and out.is_cuda) \
+            or ctr_key.element_size() != 4 or out.element_size() != 4:
+        raise IleError(ILE_E_ARG, "ile_philox4x32_10", "ctr_key [n][6] and out [n][4] 32-bit CUDA tensors")
+    st = lib.ile_philox4x32_10(_dev_ptr(ctr_key.contiguous()), n, _dev_ptr(out), _stream_handle(stream))
+    if st != ILE_OK:
+        raise IleError(st, "ile_philox4x32_10")
 
 
 class Context:

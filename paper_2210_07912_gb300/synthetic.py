@@ -130,7 +130,7 @@ def _sqrt_psd(U):
     return (W * np.sqrt(np.clip(w, 0.0, None))) @ W.conj().T
 
 
-def draw_UV(rng, n_det, n_modes, spectrum="random"):
+def draw_UV(rng, n_det, n_modes, spectrum="random", scale=1.0):
     U = np.zeros((n_det, n_modes, n_modes), complex)
     V = np.zeros_like(U)
     for k in range(n_det):
@@ -150,24 +150,25 @@ def draw_UV(rng, n_det, n_modes, spectrum="random"):
         R = _sqrt_psd(U[k])
         V[k] = R.T @ Km @ R
         V[k] = 0.5 * (V[k] + V[k].T)
-    return U, V
+    return scale * U, scale * V
 
 
 def make_point(seed: int, n_det: int, n_modes: int, n_window: int, *, fs: float = FS,
                spectrum: str = "random", c_true=None, t_true=None, noise: float = 1.0,
-               pulse_sigma: float | None = 2e-3, gmst: float = 0.0) -> Point:
+               pulse_sigma: float | None = 2e-3, gmst: float = 0.0, uv_scale: float = 1.0) -> Point:
     """One synthetic intrinsic point.
 
     c_true: (K, M) complex true coefficients (F_k Y_lm D_ref/D at the injected sample), or None
     to draw them; t_true: (K,) true arrival times at each detector (s), or None to draw them.
-    pulse_sigma=None gives a flat profile (g = 1).
+    pulse_sigma=None gives a flat profile (g = 1).  uv_scale multiplies U and V (and with them
+    the signal part of Q): a louder detector network, <h|h> and the data term grow in proportion.
     """
     rng = np.random.default_rng(seed)
     tens, pos = detector_arrays(n_det)
     lm = mode_list(n_modes)
     T_ext = t_ext_for(n_window, pos, fs)
     t_start = -(T_ext // 2) / fs
-    U, V = draw_UV(rng, n_det, n_modes, spectrum)
+    U, V = draw_UV(rng, n_det, n_modes, spectrum, uv_scale)
     if c_true is None:
         amp = rng.normal(0.0, 0.5, n_det) + 1j * rng.normal(0.0, 0.5, n_det)
         y = _cgauss(rng, n_modes, 0.3)

@@ -108,6 +108,27 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
                         const double *U, const double *V, int n_window, double gmst_rad, double d_ref_mpc);
 
 /*
+ * Refinement of loud samples (the subsection "Choices for finite-precision floating point
+ * arithmetic and overflow" keeps the likelihood in log space so that loud signals, SNR rho ~ 35 and
+ * beyond, do not overflow; this keeps them accurate too).  Every fast path computes geometry,
+ * coefficients and the data and quadratic terms in single precision (or split precision on the
+ * tensor cores), whose absolute error grows with |D| + A: measured against the FP64 oracle, below
+ * 1e-6 (FP32, TF32X3) and 5e-6 (BF16X3) of |max_j D| + A.  With refinement on (the default), a
+ * sample with |max_j D| + A above 300 (FP32, TF32X3) or 50 (BF16X3) is recomputed on the device:
+ * geometry, harmonics, coefficients and A in FP64 from FP64 copies of the point, every window bin's
+ * data term in FP32, and in FP64 every bin with D_j >= max_j D - 30 and |D_j| above the same
+ * threshold; its lnL_t is then the FP64 log-sum-exp of those bins.  Applies to ile_eval (lnL_t),
+ * ile_integrate, the adaptive integrator and the batched run, not to the lnL(n, j) grid, the
+ * adjoint or the distance-marginalised likelihood.  Costs one small launch per evaluation when no
+ * sample is loud; the FP64 work of a loud sample is a few ten thousand FP64 operations.
+ *   ile_set_refine: enable (1, default) or disable (0) it for the context.
+ *   ile_refine_count: waits for the context's stream; *n = the number of samples the last
+ *   evaluation refined (the last iteration's, after ile_adapt_step).
+ */
+ile_status ile_set_refine(ile_ctx *ctx, int enable);
+ile_status ile_refine_count(ile_ctx *ctx, int64_t *n);
+
+/*
  * Distance marginalisation (App. "Distance marginalization"; the paper gives no formula, the
  * integral is written out here).  When enabled, every likelihood the context returns (ile_eval,
  * ile_integrate, the adaptive integrator) is marginalised over the luminosity distance:

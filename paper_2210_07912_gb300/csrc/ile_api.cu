@@ -18,6 +18,10 @@ struct ile_ctx {
     bool has_data = false;
     PointParams pp{};
     // point data
+    double2 *Q64 = nullptr, *U64 = nullptr, *V64 = nullptr;  // FP64 copies for the refinement (ile_refine.cu)
+    Refine64 r64{};
+    int *loud = nullptr;   // [2 cap + 1] loud samples of the last evaluation (count, then (0, index) pairs)
+    bool refine = true;    // refine loud samples in FP64 (ile_set_refine)
     float *Qp = nullptr;   // [K][2M][T_ext]
     float *UV = nullptr;   // [K][P][4]
     float *Qquad = nullptr;  // [K][KP][ILE_QCOLS] real form of U, V (quadratic-term MMA operand)
@@ -185,6 +189,7 @@ ile_status ensure_samples(ile_ctx *ctx, int64_t N) {
     CK(grow(ctx, &ctx->keys, sizeof(int) * (size_t)cap));
     CK(grow(ctx, &ctx->perm, sizeof(int) * (size_t)cap));
     CK(grow(ctx, &ctx->g_in, sizeof(double) * (size_t)cap));
+    CK(grow(ctx, &ctx->loud, sizeof(int) * (size_t)(2 * cap + 1)));
     if (!ctx->buckets) CK(ctx_malloc(ctx, (void **)&ctx->buckets, sizeof(int) * ile_sort_key_buckets()));
     int np = ile_mc_partial_count(cap);
     CK(grow(ctx, &ctx->part, sizeof(double) * 3 * (size_t)np));
@@ -210,10 +215,12 @@ double factorial(int n) {
 }
 
 // Polynomial form of d^l_{m,2}(iota) in c = cos(iota/2), s = sin(iota/2) (Wigner's formula).
-bool wigner_terms(int l, int m, ModeTab &md) {
+// Terms of d^l_{m,2}(iota) = sum_t coef_t cos(iota/2)^p_t sin(iota/2)^q_t (the explicit Wigner
+// small-d sum) and the normalisation sqrt((2l+1)/4pi) of _{-2}Y_lm, in FP64.
+bool wigner_terms64(int l, int m, Mode64 &md) {
     md.l = l;
     md.m = m;
-    md.norm = (float)sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
+    md.norm = sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
     md.nterms = 0;
     const double root = sqrt(factorial(l + m) * factorial(l - m) * factorial(l + 2) * factorial(l - 2));
     for (int sp = 0; sp <= 2 * l; sp++) {  // sp = power of s = 2k - 2 + m
@@ -224,10 +231,25 @@ bool wigner_terms(int l, int m, ModeTab &md) {
         if (f1 < 0 || f2 < 0 || f3 < 0) continue;
         if (md.nterms >= 4) return false;
         double sign = (f3 % 2 == 0) ? 1.0 : -1.0;
-        WignerTerm &t = md.t[md.nterms++];
-        t.coef = (float)(sign * root / (factorial(f1) * factorial(k) * factorial(f2) * factorial(f3)));
-        t.p = 2 * l - sp;
-        t.q = sp;
+        md.coef[md.nterms] = sign * root / (factorial(f1) * factorial(k) * factorial(f2) * factorial(f3));
+        md.p[md.nterms] = 2 * l - sp;
+        md.q[md.nterms] = sp;
+        md.nterms++;
+    }
+    return true;
+}
+
+bool wigner_terms(int l, int m, ModeTab &md) {
+    Mode64 d;
+    if (!wigner_terms64(l, m, d)) return false;
+    md.l = l;
+    md.m = m;
+    md.norm = (float)d.norm;
+    md.nterms = d.nterms;
+    for (int t = 0; t < d.nterms; t++) {
+        md.t[t].coef = (float)d.coef[t];
+        md.t[t].p = d.p[t];
+        md.t[t].q = d.q[t];
     }
     return true;
 }
@@ -289,6 +311,44 @@ ile_status ensure_adj_operands(ile_ctx *ctx) {
 // S1-S5 on device-resident samples; writes lnL_t (or the grid) to dout in the caller's order.
 // Samples are first ordered by quantised detector delays (ile_sort.cu) so that a tile of the
 // contraction spans few time columns; the per-sample results do not depend on that order.
+}  // namespace
+
+// Samples with |max_j D| + A above this go to the FP64 refinement (ile_refine.cu).  The fast paths'
+// absolute errors measured against the FP64 oracle on injections of <h0|h0> = 1e2 .. 1e4 stay
+// below 1e-6 (FP32, TF32X3) and 5e-6 (BF16X3) of |max_j D| + A, so the samples left to them stay
+// below 3e-4.
+float ile_refine_threshold(int prec) { return prec == ILE_PREC_BF16X3 ? 50.f : 300.f; }
+
+// FP64 description of a point for the refinement (the arguments have been validated by
+// ile_prepare_point).
+bool ile_refine_params(int n_det, int n_modes, const int *lm, const double *det_tensor, const double *det_pos_m,
+                       int T_ext, double t_start_s, double fs_hz, int n_window, double gmst_rad, double d_ref_mpc,
+                       Refine64 &r) {
+    r = Refine64{};
+    r.K = n_det;
+    r.M = n_modes;
+    r.Nt = n_window;
+    r.T_ext = T_ext;
+    r.fs = fs_hz;
+    r.t_start = t_start_s;
+    r.gmst = gmst_rad;
+    r.d_ref = d_ref_mpc;
+    r.log_nt = log((double)n_window);
+    for (int k = 0; k < n_det; k++) {
+        for (int i = 0; i < 9; i++) r.det_tensor[k][i] = det_tensor[9 * k + i];
+        for (int i = 0; i < 3; i++) r.det_pos[k][i] = det_pos_m[3 * k + i];
+    }
+    for (int a = 0; a < n_modes; a++)
+        if (!wigner_terms64(lm[2 * a], lm[2 * a + 1], r.mode[a])) return false;
+    return true;
+}
+
+namespace {
+
+// S1-S5 on device-resident samples; writes lnL_t (or the grid) to dout in the caller's order.
+// Samples are first ordered by quantised detector delays (ile_sort.cu) so that a tile of the
+// contraction spans few time columns; the per-sample results do not depend on that order.
+// lnL_t of loud samples is then recomputed in FP64 (unless the context's refinement is off).
 ile_status run_eval(ile_ctx *ctx, const double *dsamples, int64_t N, double *dout, int full_grid) {
     ile_status st = ensure_samples(ctx, N);
     if (st != ILE_OK) return st;
@@ -296,6 +356,11 @@ ile_status run_eval(ile_ctx *ctx, const double *dsamples, int64_t N, double *dou
     if (prec != ILE_PREC_FP32) {
         st = ensure_tc_operands(ctx, prec);
         if (st != ILE_OK) return st;
+    }
+    LoudList loud{nullptr, 0.f};
+    if (full_grid == 0 && ctx->refine && !ctx->pp.dm.on) {
+        loud = LoudList{ctx->loud, ile_refine_threshold(prec), 0, ctx->cap};
+        CK(cudaMemsetAsync(ctx->loud, 0, sizeof(int), ctx->stream));
     }
     if (prec == ILE_PREC_BF16X3) {
         // fused kernel: S1, S2, S4 are computed inside the tensor-core kernel
@@ -306,21 +371,27 @@ ile_status run_eval(ile_ctx *ctx, const double *dsamples, int64_t N, double *dou
         StageScope t(ctx, 2);
         CK(ile_launch_tc2(ctx->pp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ile_tc_tpad(ctx->pp.T_ext),
                           ile_tc_kpad(prec, ctx->pp.M), ctx->UV, dsamples, ctx->perm, N, dout, nullptr, full_grid,
-                          ctx->flags, ctx->stream));
-        return ILE_OK;
-    }
-    {
-        StageScope t(ctx, 1, 4);
-        CK(ile_launch_sort(ctx->pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));
-        CK(ile_launch_prep(ctx->pp, ctx->UV, dsamples, ctx->perm, N, ctx->s, ctx->flags, ctx->stream));
-    }
-    {
+                          loud, ctx->flags, ctx->stream));
+    } else {
+        {
+            StageScope t(ctx, 1, 4);
+            CK(ile_launch_sort(ctx->pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));
+            CK(ile_launch_prep(ctx->pp, ctx->UV, dsamples, ctx->perm, N, ctx->s, ctx->flags, ctx->stream));
+        }
         StageScope t(ctx, 2);
         if (prec == ILE_PREC_FP32)
-            CK(ile_launch_plain(ctx->pp, ctx->Qp, ctx->s, ctx->perm, N, dout, full_grid, ctx->flags, ctx->stream));
+            CK(ile_launch_plain(ctx->pp, ctx->Qp, ctx->s, ctx->perm, N, dout, full_grid, loud, ctx->flags,
+                                ctx->stream));
         else
             CK(ile_launch_tc(prec, ctx->pp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ctx->s, ctx->perm, N, dout,
-                             full_grid, ctx->flags, ctx->stream));
+                             full_grid, loud, ctx->flags, ctx->stream));
+    }
+    if (loud.list) {
+        StageScope t(ctx, 2);
+        Refine64 r = ctx->r64;
+        r.thr = loud.thr;
+        CK(ile_launch_refine(r, ctx->Q64, ctx->U64, ctx->V64, ctx->Qp, dsamples, N, ctx->loud, ctx->cap, dout,
+                             ctx->flags, ctx->n_sm, ctx->stream));
     }
     return ILE_OK;
 }
@@ -374,7 +445,7 @@ ile_status run_grad(ile_ctx *ctx, const double *dsamples, const double *dg, int6
     if (tc2_fwd)
         CK(ile_launch_tc2(pp, ctx->Qtc[ILE_PREC_BF16X3][0], ctx->Qtc[ILE_PREC_BF16X3][1], ile_tc_tpad(pp.T_ext),
                           ile_tc_kpad(ILE_PREC_BF16X3, pp.M), ctx->UV, dsamples, ctx->perm, N, nullptr, pig, 2,
-                          ctx->flags, ctx->stream));
+                          LoudList{nullptr, 0.f, 0, 0}, ctx->flags, ctx->stream));
     if (g_theta || gQ || lnl)
         CK(ile_launch_grad_main(pp, ctx->Qp, ctx->UV, ctx->s, ctx->perm, dsamples, dg, N, pig,
                                 tc2_fwd ? pig : nullptr, tc_adj ? ctx->Qadj[0] : nullptr,
@@ -443,6 +514,7 @@ ile_status ile_create(ile_ctx **out, int device, void *cuda_stream, ile_prec pre
     cudaError_t e = cudaMalloc((void **)&ctx->flags, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(ctx->flags, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->result, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) {
         ile_status st = cuda_fail(ctx, e, "ile_create");
         ile_destroy(ctx);
@@ -463,7 +535,8 @@ ile_status ile_destroy(ile_ctx *ctx) {
                     ctx->a_iter_log,   ctx->a_iter_res, ctx->a_lnwp,    ctx->a_lnl,     ctx->a_iter,
                     ctx->a_bins,       ctx->pig,        ctx->gq_part,   ctx->guv_part,  ctx->g_in,
                     ctx->g_out,        ctx->g_cur,      ctx->g_bat,     ctx->g_tab,     ctx->g_part,
-                    ctx->a_u,          ctx->Qadj[0],    ctx->Qadj[1]};
+                    ctx->a_u,          ctx->Qadj[0],    ctx->Qadj[1],   ctx->Q64,       ctx->U64,
+                    ctx->V64,          ctx->loud};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (auto &v : ctx->ev)
@@ -494,6 +567,24 @@ ile_status ile_check_wait_timeout(ile_ctx *ctx, double timeout_s) {
 ile_status ile_set_stream(ile_ctx *ctx, void *cuda_stream) {
     if (!ctx) return ILE_E_ARG;
     ctx->stream = (cudaStream_t)cuda_stream;
+    return ILE_OK;
+}
+
+ile_status ile_set_refine(ile_ctx *ctx, int enable) {
+    if (!ctx) return ILE_E_ARG;
+    ctx->refine = enable != 0;
+    return ILE_OK;
+}
+
+ile_status ile_refine_count(ile_ctx *ctx, int64_t *n) {
+    if (!ctx || !n) return ILE_E_ARG;
+    *n = 0;
+    if (!ctx->loud) return ILE_OK;
+    DeviceGuard g(ctx->device);
+    int c = 0;
+    CK(cudaMemcpyAsync(&c, ctx->loud, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *n = c;
     return ILE_OK;
 }
 
@@ -667,11 +758,20 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
     CK(grow(ctx, &ctx->Qp, sizeof(float) * qp.size()));
     CK(grow(ctx, &ctx->UV, sizeof(float) * uv.size()));
     CK(grow(ctx, &ctx->Qquad, sizeof(float) * quad.size()));
+    const size_t nq = (size_t)n_det * n_modes * T_ext, nuv = (size_t)n_det * n_modes * n_modes;
+    CK(grow(ctx, &ctx->Q64, sizeof(double2) * nq));
+    CK(grow(ctx, &ctx->U64, sizeof(double2) * nuv));
+    CK(grow(ctx, &ctx->V64, sizeof(double2) * nuv));
+    CK(cudaMemcpyAsync(ctx->Q64, Q, sizeof(double2) * nq, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->U64, U, sizeof(double2) * nuv, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->V64, V, sizeof(double2) * nuv, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->Qp, qp.data(), sizeof(float) * qp.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->UV, uv.data(), sizeof(float) * uv.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->Qquad, quad.data(), sizeof(float) * quad.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->pp = pp;
+    ile_refine_params(n_det, n_modes, lm, det_tensor, det_pos_m, T_ext, t_start_s, fs_hz, n_window, gmst_rad,
+                      d_ref_mpc, ctx->r64);  // validated above
     ctx->has_data = true;
     ctx->Qtc_ready[1] = ctx->Qtc_ready[2] = ctx->Qadj_ready = false;
     ctx->cap = ctx->cap;  // scratch is sized for ILE_MAX_DET x ILE_MAX_MODES, so it stays valid

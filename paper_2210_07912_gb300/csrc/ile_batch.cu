@@ -27,6 +27,7 @@ struct ile_batch {
     ile_prec prec = ILE_PREC_BF16X3;
     int n_points = 0;
     int64_t n_total = 0;
+    int n_sm = 0;
     std::vector<PointParams> pps;
     std::vector<int64_t> N, off;
     std::vector<double> eps;
@@ -34,6 +35,9 @@ struct ile_batch {
     float *Qp = nullptr, *UV = nullptr, *Qquad = nullptr;
     std::vector<size_t> qp_off, uv_off, tc_off, quad_off;
     uint8_t *Qtc_hi = nullptr, *Qtc_lo = nullptr;
+    double2 *Q64 = nullptr, *UV64 = nullptr;  // FP64 copies for the refinement of loud samples
+    RefinePoint *rpts = nullptr;              // [n_points] (ile_refine.cu)
+    int *loud = nullptr;                      // [2 n_total + 1] loud samples of the last iteration
     Tc2Point *pts = nullptr;
     IleBatchPoint *bp = nullptr;
     std::vector<IleBatchPoint> bp_host;
@@ -102,6 +106,10 @@ void free_points(ile_batch *b) {
     release(b->Qquad);
     release(b->Qtc_hi);
     release(b->Qtc_lo);
+    release(b->Q64);
+    release(b->UV64);
+    release(b->rpts);
+    release(b->loud);
     release(b->pts);
     release(b->bp);
     release(b->items);
@@ -171,6 +179,10 @@ ile_status enqueue_iteration(ile_batch *b) {
                                b->stream));
     BK(ile_launch_batch_sort(b->n_points, b->bp, b->blk256, b->n_blk256, b->theta, b->keys, b->buckets, b->perm,
                              b->stream));
+    // loud samples of every point are refined in FP64 after the contraction, exactly as in a
+    // single-point run (so that each point's result equals that run bit for bit)
+    BK(cudaMemsetAsync(b->loud, 0, sizeof(int), b->stream));
+    const float thr = ile_refine_threshold((int)b->prec);
     if (b->prec == ILE_PREC_BF16X3) {
         BK(ile_launch_tc2_batch(b->pts, b->items, b->n_items, b->LK, b->LM, b->LKP, b->NB, b->nwcol, b->grid,
                                 b->flags, b->stream));
@@ -182,12 +194,14 @@ ile_status enqueue_iteration(ile_batch *b) {
             double *out = b->lnl + b->off[p];
             BK(ile_launch_prep(pp, b->UV + b->uv_off[p], smp, prm, b->N[p], b->s, b->flags, b->stream));
             if (b->prec == ILE_PREC_FP32)
-                BK(ile_launch_plain(pp, b->Qp + b->qp_off[p], b->s, prm, b->N[p], out, 0, b->flags, b->stream));
+                BK(ile_launch_plain(pp, b->Qp + b->qp_off[p], b->s, prm, b->N[p], out, 0, LoudList{b->loud, thr, p, b->n_total},
+                                    b->flags, b->stream));
             else
                 BK(ile_launch_tc(b->prec, pp, b->Qtc_hi + b->tc_off[p], b->Qtc_lo + b->tc_off[p], b->s, prm, b->N[p],
-                                 out, 0, b->flags, b->stream));
+                                 out, 0, LoudList{b->loud, thr, p, b->n_total}, b->flags, b->stream));
         }
     }
+    BK(ile_launch_batch_refine(b->rpts, b->n_total, b->loud, b->n_total, b->flags, b->n_sm, b->stream));
     BK(ile_launch_batch_mc(b->n_points, b->bp, b->mblk, b->n_mblk, b->mfirst, b->lnl, b->lnwp, b->mc_part,
                            b->iter_res, b->stream));
     BK(ile_launch_batch_adapt(b->n_points, b->bp, b->hblk, b->n_hblk, b->lnl, b->lnwp, b->bins, b->iter_res,
@@ -247,6 +261,7 @@ ile_status ile_batch_create(ile_batch **out, int device, void *cuda_stream, ile_
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->flags, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(b->flags, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->grid, cudaDevAttrMultiProcessorCount, device);
+    b->n_sm = b->grid;
     if (e != cudaSuccess) {
         ile_status st = fail(b, e, "ile_batch_create");
         ile_batch_destroy(b);
@@ -332,6 +347,27 @@ ile_status ile_batch_set_points(ile_batch *b, int n_points, const ile_point_desc
     for (int p = 0; p < n_points; p++)
         BK(ile_launch_tc_split(split, pps[p], b->Qp + b->qp_off[p], b->Qquad + b->quad_off[p],
                                b->Qtc_hi + b->tc_off[p], b->Qtc_lo + b->tc_off[p], b->stream));
+    // FP64 copies of Q, U, V for the refinement of loud samples: Q64 [sum K M T_ext], UV64 = U then V
+    // of each point [2 sum K M^2]
+    std::vector<size_t> q64_off(n_points), uv64_off(n_points);
+    size_t q64_tot = 0, uv64_tot = 0;
+    for (int p = 0; p < n_points; p++) {
+        q64_off[p] = q64_tot;
+        q64_tot += (size_t)pts[p].n_det * pts[p].n_modes * pts[p].T_ext;
+        uv64_off[p] = uv64_tot;
+        uv64_tot += 2 * (size_t)pts[p].n_det * pts[p].n_modes * pts[p].n_modes;
+    }
+    BK(cudaMalloc((void **)&b->Q64, sizeof(double2) * q64_tot));
+    BK(cudaMalloc((void **)&b->UV64, sizeof(double2) * uv64_tot));
+    for (int p = 0; p < n_points; p++) {
+        const size_t nq = (size_t)pts[p].n_det * pts[p].n_modes * pts[p].T_ext,
+                     nuv = (size_t)pts[p].n_det * pts[p].n_modes * pts[p].n_modes;
+        BK(cudaMemcpyAsync(b->Q64 + q64_off[p], pts[p].Q, sizeof(double2) * nq, cudaMemcpyHostToDevice, b->stream));
+        BK(cudaMemcpyAsync(b->UV64 + uv64_off[p], pts[p].U, sizeof(double2) * nuv, cudaMemcpyHostToDevice, b->stream));
+        BK(cudaMemcpyAsync(b->UV64 + uv64_off[p] + nuv, pts[p].V, sizeof(double2) * nuv, cudaMemcpyHostToDevice,
+                           b->stream));
+    }
+    BK(cudaMalloc((void **)&b->loud, sizeof(int) * (2 * (size_t)ntot + 1)));
     // per-sample arrays
     BK(cudaMalloc((void **)&b->theta, sizeof(double) * ILE_NDIM * ntot));
     BK(cudaMalloc((void **)&b->lnwp, sizeof(double) * ntot));
@@ -351,6 +387,8 @@ ile_status ile_batch_set_points(ile_batch *b, int n_points, const ile_point_desc
     BK(cudaMalloc((void **)&b->iter, sizeof(int) * n_points));
     // descriptors and work lists
     std::vector<Tc2Point> tp(n_points);
+    std::vector<RefinePoint> rp(n_points);
+    const float thr = ile_refine_threshold((int)b->prec);
     std::vector<IleBatchPoint> bph(n_points);
     std::vector<int2> items, blk256, hblk, mblk;
     std::vector<int> mfirst(n_points + 1, 0);
@@ -370,6 +408,19 @@ ile_status ile_batch_set_points(ile_batch *b, int n_points, const ile_point_desc
         t.N = b->N[p];
         t.TP = ile_tc_tpad(pp.T_ext);
         t.KP = ile_tc_kpad(ILE_PREC_BF16X3, pp.M);
+        t.loud = LoudList{b->loud, thr, p, b->n_total};
+        RefinePoint &r = rp[p];
+        ile_refine_params(d.n_det, d.n_modes, d.lm, d.det_tensor, d.det_pos_m, d.T_ext, d.t_start_s, d.fs_hz,
+                          d.n_window, d.gmst_rad, d.d_ref_mpc, r.r);
+        r.r.thr = thr;
+        const size_t nuv = (size_t)d.n_det * d.n_modes * d.n_modes;
+        r.Q64 = b->Q64 + q64_off[p];
+        r.U64 = b->UV64 + uv64_off[p];
+        r.V64 = b->UV64 + uv64_off[p] + nuv;
+        r.Qp = b->Qp + b->qp_off[p];
+        r.samples = b->theta + ILE_NDIM * b->off[p];
+        r.N = b->N[p];
+        r.out = b->lnl + b->off[p];
         IleBatchPoint &q = bph[p];
         for (int k = 0; k < ILE_NDIM; k++) {
             q.sp.lo[k] = (float)d.lo[k];
@@ -404,6 +455,7 @@ ile_status ile_batch_set_points(ile_batch *b, int n_points, const ile_point_desc
     std::vector<int2> sorted(items.size());
     for (size_t i = 0; i < order.size(); i++) sorted[i] = items[order[i]];
     BK(upload(&b->pts, tp, b->stream));
+    BK(upload(&b->rpts, rp, b->stream));
     BK(upload(&b->bp, bph, b->stream));
     BK(upload(&b->items, sorted, b->stream));
     BK(upload(&b->blk256, blk256, b->stream));
@@ -544,13 +596,19 @@ ile_status ile_batch_tune(ile_batch *b, int reps, ile_batch_tuning *out) {
         for (int wi = 0; wi < 3; wi++) {
             const int W = widths[wi];
             if (wi > 0 && W == widths[wi - 1]) continue;
-            // warm-up launch, then `reps` timed launches
-            cudaError_t e = ile_launch_tc2_batch(b->pts, b->items, b->n_items, b->LK, b->LM, b->LKP, NB, W, sms,
-                                                 b->flags, b->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-            for (int r = 0; r < reps && e == cudaSuccess; r++)
+            // warm-up launch, then `reps` timed launches (each refills the loud-sample list: its count
+            // is reset first)
+            cudaError_t e = cudaMemsetAsync(b->loud, 0, sizeof(int), b->stream);
+            if (e == cudaSuccess)
                 e = ile_launch_tc2_batch(b->pts, b->items, b->n_items, b->LK, b->LM, b->LKP, NB, W, sms, b->flags,
                                          b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            for (int r = 0; r < reps && e == cudaSuccess; r++) {
+                e = cudaMemsetAsync(b->loud, 0, sizeof(int), b->stream);
+                if (e == cudaSuccess)
+                    e = ile_launch_tc2_batch(b->pts, b->items, b->n_items, b->LK, b->LM, b->LKP, NB, W, sms,
+                                             b->flags, b->stream);
+            }
             if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;

@@ -301,6 +301,51 @@ __device__ __forceinline__ void ile_half_angle_powers(float iota, float cpow[9],
     }
 }
 
+// FP64 description of a point for the refinement of loud samples (ile_refine.cu).
+struct Mode64 {
+    int l, m, nterms;
+    double norm;     // sqrt((2l+1)/4pi)
+    double coef[4];  // d^l_{m,2}(iota) = sum_t coef_t cos(iota/2)^p_t sin(iota/2)^q_t
+    int p[4], q[4];
+};
+struct Refine64 {
+    int K, M, Nt, T_ext;
+    double fs, t_start, gmst, d_ref, log_nt;
+    float thr;  // a window bin's data term is recomputed in FP64 when |D_j| exceeds this
+    double det_tensor[ILE_MAX_DET][9];
+    double det_pos[ILE_MAX_DET][3];  // metres
+    Mode64 mode[ILE_MAX_MODES];
+};
+
+// Device list of loud samples: list[0] = count, then (point, caller index) pairs at list[1 + 2 i],
+// list[2 + 2 i], i < cap (the list holds 2 cap + 1 ints).  A fast kernel appends a sample when
+// |max_j D(n, j)| + A(n) > thr (list == nullptr: no list); point identifies the intrinsic point in a
+// batched run (0 otherwise).  The count is reset before every launch that fills the list; appends
+// past cap are dropped.
+struct LoudList {
+    int *list;
+    float thr;
+    int point;
+    int64_t cap;
+};
+__device__ __forceinline__ void ile_loud_append(const LoudList &l, int n) {
+    const int i = atomicAdd(l.list, 1);
+    if (i < l.cap) {
+        l.list[1 + 2 * i] = l.point;
+        l.list[2 + 2 * i] = n;
+    }
+}
+// One point of a batched refinement (ile_refine.cu): its FP64 description and arrays, its samples
+// [7][N] and its lnL_t [N].
+struct RefinePoint {
+    Refine64 r;
+    const double2 *Q64, *U64, *V64;
+    const float *Qp;
+    const double *samples;
+    int64_t N;
+    double *out;
+};
+
 // One intrinsic point as seen by the fused tensor-core kernel (ile_tc2.cu).
 struct Tc2Point {
     PointParams pp;
@@ -312,6 +357,7 @@ struct Tc2Point {
     float *grid_f;          // grid mode 2: data term D(n, j) in processing order [N][N_t]
     int64_t N;
     int TP, KP;
+    LoudList loud;          // loud samples for the FP64 refinement (single-point launches)
 };
 
 // ------------------------------------------------------------------ host-side launch wrappers
@@ -326,7 +372,18 @@ struct IleScratch {
 cudaError_t ile_launch_prep(const PointParams &pp, const float *UV, const double *samples, const int *perm, int64_t N,
                             IleScratch s, unsigned *flags, cudaStream_t st);
 cudaError_t ile_launch_plain(const PointParams &pp, const float *Qp, IleScratch s, const int *perm, int64_t N,
-                             double *out, int full_grid, unsigned *flags, cudaStream_t st);
+                             double *out, int full_grid, LoudList loud, unsigned *flags, cudaStream_t st);
+// FP64 refinement of the samples in list (ile_refine.cu): lnL_t recomputed into out (caller order)
+cudaError_t ile_launch_refine(const Refine64 &P, const double2 *Q64, const double2 *U64, const double2 *V64,
+                              const float *Qp, const double *samples, int64_t N, const int *list, int64_t cap,
+                              double *out, unsigned *flags, int n_sm, cudaStream_t st);
+cudaError_t ile_launch_batch_refine(const RefinePoint *pts, int64_t n_total, const int *list, int64_t cap,
+                                    unsigned *flags, int n_sm, cudaStream_t st);
+// FP64 description of a point (ile_api.cu) and the refinement threshold of a precision
+bool ile_refine_params(int n_det, int n_modes, const int *lm, const double *det_tensor, const double *det_pos_m,
+                       int T_ext, double t_start_s, double fs_hz, int n_window, double gmst_rad, double d_ref_mpc,
+                       Refine64 &r);
+float ile_refine_threshold(int prec);
 // delay-bucket sort (ile_sort.cu): keys [N], buckets [ile_sort_key_buckets()], perm [N]
 size_t ile_sort_key_buckets();
 cudaError_t ile_launch_sort(const PointParams &pp, const double *samples, int64_t N, int *keys, int *buckets,
@@ -342,12 +399,13 @@ size_t ile_tc_q_bytes(int prec, int K, int M, int T_ext);
 cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp, const float *quad, void *hi,
                                 void *lo, cudaStream_t st);
 cudaError_t ile_launch_tc(int prec, const PointParams &pp, const void *hi, const void *lo, IleScratch s,
-                          const int *perm, int64_t N, double *out, int full_grid, unsigned *flags, cudaStream_t st);
+                          const int *perm, int64_t N, double *out, int full_grid, LoudList loud, unsigned *flags,
+                          cudaStream_t st);
 // full_grid 0: lnL_t into out (caller order); 1: the grid lnL(n, j) into out (caller order);
 // 2: the data term D(n, j) in FP32 into grid_f, rows in processing (sorted) order
 cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo, int TP, int KP, const float *UV,
                            const double *samples, const int *perm, int64_t N, double *out, float *grid_f,
-                           int full_grid, unsigned *flags, cudaStream_t st);
+                           int full_grid, LoudList loud, unsigned *flags, cudaStream_t st);
 // adjoint (ile_adjoint.cu)
 int ile_grad_q_splits(const PointParams &pp, int64_t N, int n_sm);
 int ile_grad_uv_blocks(int64_t N, int n_sm);

@@ -23,7 +23,7 @@ template <int NS>
 __global__ void __launch_bounds__(256) ile_plain_kernel(const __grid_constant__ PointParams pp,
                                                         const float *__restrict__ Qp, IleScratch s,
                                                         const int *__restrict__ perm, int64_t N,
-                                                        double *__restrict__ out, int full_grid) {
+                                                        double *__restrict__ out, int full_grid, LoudList loud) {
     constexpr int RS = NS / 16;  // samples per thread in the micro-tile
     extern __shared__ float smem[];
     const int Nt = pp.Nt, R = 2 * pp.M, T = pp.T_ext;
@@ -150,7 +150,11 @@ __global__ void __launch_bounds__(256) ile_plain_kernel(const __grid_constant__ 
         float sum = 0.f;
         for (int j = lane; j < Nt; j += 32) sum += expf(d[j] - m);
         for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) out[dst] = (double)m + (double)logf(sum) - A - log_nt;
+        if (lane == 0) {
+            out[dst] = (double)m + (double)logf(sum) - A - log_nt;
+            // a sample too loud for FP32 goes to the FP64 refinement (ile_refine.cu)
+            if (loud.list && fabsf(m) + (float)A > loud.thr) ile_loud_append(loud, (int)dst);
+        }
     }
 }
 
@@ -161,21 +165,22 @@ size_t plain_smem(const PointParams &pp) {
 
 template <int NS>
 cudaError_t launch(const PointParams &pp, const float *Qp, IleScratch s, const int *perm, int64_t N, double *out,
-                   int full_grid, cudaStream_t st) {
+                   int full_grid, LoudList loud, cudaStream_t st) {
     size_t smem = plain_smem<NS>(pp);
     cudaError_t e = cudaFuncSetAttribute(ile_plain_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int64_t blocks = (N + NS - 1) / NS;
-    ile_plain_kernel<NS><<<(unsigned)blocks, 256, smem, st>>>(pp, Qp, s, perm, N, out, full_grid);
+    ile_plain_kernel<NS><<<(unsigned)blocks, 256, smem, st>>>(pp, Qp, s, perm, N, out, full_grid, loud);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t ile_launch_plain(const PointParams &pp, const float *Qp, IleScratch s, const int *perm, int64_t N,
-                             double *out, int full_grid, unsigned *flags, cudaStream_t st) {
+                             double *out, int full_grid, LoudList loud, unsigned *flags, cudaStream_t st) {
     (void)flags;
     if (N <= 0) return cudaSuccess;
-    if (pp.Nt <= 512) return launch<64>(pp, Qp, s, perm, N, out, full_grid, st);
-    return launch<32>(pp, Qp, s, perm, N, out, full_grid, st);
+    if (full_grid || pp.dm.on) loud.list = nullptr;
+    if (pp.Nt <= 512) return launch<64>(pp, Qp, s, perm, N, out, full_grid, loud, st);
+    return launch<32>(pp, Qp, s, perm, N, out, full_grid, loud, st);
 }

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
                                                         const uint4 *__restrict__ Qhi, const uint4 *__restrict__ Qlo,
                                                         int TP, int KP, IleScratch s, const int *__restrict__ perm,
                                                         int64_t N, double *__restrict__ out, int full_grid,
-                                                        unsigned *flags) {
+                                                        LoudList loud, unsigned *flags) {
     constexpr int EPC = Tc<BF16>::EPC, KS = Tc<BF16>::KS;
     extern __shared__ __align__(1024) uint8_t dsm[];
     __shared__ TcSmem sm;
@@ -221,8 +221,12 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
         }
         for (int jj = 0; jj < Jc; jj++) s_run += expf(Dt[jj * TILE + t] - m_run);
     }
-    if (valid && !full_grid && !timed_out)
-        out[perm ? perm[p] : p] = (double)m_run + (double)logf(s_run) - (double)A - (double)pp.log_nt;
+    if (valid && !full_grid && !timed_out) {
+        const int64_t dst = perm ? perm[p] : p;
+        out[dst] = (double)m_run + (double)logf(s_run) - (double)A - (double)pp.log_nt;
+        // a sample too loud for single precision goes to the FP64 refinement (ile_refine.cu)
+        if (loud.list && fabsf(m_run) + A > loud.thr) ile_loud_append(loud, (int)dst);
+    }
 
     fence_before();
     __syncthreads();
@@ -327,8 +331,10 @@ cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp
 }
 
 cudaError_t ile_launch_tc(int prec, const PointParams &pp, const void *hi, const void *lo, IleScratch s,
-                          const int *perm, int64_t N, double *out, int full_grid, unsigned *flags, cudaStream_t st) {
+                          const int *perm, int64_t N, double *out, int full_grid, LoudList loud, unsigned *flags,
+                          cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
+    if (full_grid || pp.dm.on) loud.list = nullptr;
     const int KP = ile_tc_kpad(prec, pp.M), TP = ile_tc_tpad(pp.T_ext);
     const unsigned blocks = (unsigned)((N + TILE - 1) / TILE);
     if (prec == ILE_PREC_BF16X3) {
@@ -336,13 +342,13 @@ cudaError_t ile_launch_tc(int prec, const PointParams &pp, const void *hi, const
         cudaError_t e = cudaFuncSetAttribute(ile_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         ile_tc_kernel<true><<<blocks, TILE, sm, st>>>(pp, (const uint4 *)hi, (const uint4 *)lo, TP, KP, s, perm, N, out,
-                                                     full_grid, flags);
+                                                     full_grid, loud, flags);
     } else {
         const size_t sm = tc_smem_bytes<false>(KP);
         cudaError_t e = cudaFuncSetAttribute(ile_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         ile_tc_kernel<false><<<blocks, TILE, sm, st>>>(pp, (const uint4 *)hi, (const uint4 *)lo, TP, KP, s, perm, N,
-                                                      out, full_grid, flags);
+                                                      out, full_grid, loud, flags);
     }
     return cudaGetLastError();
 }

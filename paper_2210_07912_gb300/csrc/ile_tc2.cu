@@ -802,7 +802,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     if (v.y > 0.f) ssum += v.y * __expf(v.x - m);
                 }
                 const double A_n = DM ? 0.0 : (double)aqs;
-                out[perm[p]] = (double)m + (double)logf(ssum) - A_n - (double)pp.log_nt;
+                const int dst = perm[p];
+                out[dst] = (double)m + (double)logf(ssum) - A_n - (double)pp.log_nt;
+                // a sample too loud for single precision goes to the FP64 refinement (ile_refine.cu)
+                if (!DM && pt.loud.list && fabsf(m) + aqs > pt.loud.thr) ile_loud_append(pt.loud, dst);
             }
         }
         if (failed) atomicOr(flags, ILE_FLAG_TIMEOUT);
@@ -837,7 +840,7 @@ int sm_count() {
 
 cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo, int TP, int KP, const float *UV,
                            const double *samples, const int *perm, int64_t N, double *out, float *grid_f,
-                           int full_grid, unsigned *flags, cudaStream_t st) {
+                           int full_grid, LoudList loud, unsigned *flags, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     int NB = NBMAX;
     while (NB > 2 && tc2_smem(pp.K, pp.M, KP, NB) > SMEM_LIMIT) NB--;
@@ -862,6 +865,7 @@ cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo
     one.N = N;
     one.TP = TP;
     one.KP = KP;
+    one.loud = (full_grid || pp.dm.on) ? LoudList{nullptr, 0.f, 0, 0} : loud;
     if (dm)
         ile_tc2_kernel<false, true><<<grid, NTHREADS, smem, st>>>(one, nullptr, nullptr, ntiles, pp.K, KP / 8,
                                                                   pp.M * (pp.M + 1) / 2, NB, NWCOL, full_grid, flags);

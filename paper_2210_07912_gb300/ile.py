@@ -149,6 +149,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ile_merge_partials.restype = i32
     lib.ile_mc_reduce_noalloc.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ile_mc_reduce_noalloc.restype = i32
+    lib.ile_set_refine.argtypes = [vp, i32]
+    lib.ile_set_refine.restype = i32
+    lib.ile_refine_count.argtypes = [vp, P(i64)]
+    lib.ile_refine_count.restype = i32
     lib.ile_philox4x32_10.argtypes = [vp, i64, vp, vp]
     lib.ile_philox4x32_10.restype = i32
     lib.ile_batch_create.argtypes = [P(vp), i32, vp, i32]
@@ -321,6 +325,16 @@ class Context:
 
     def set_stream(self, stream):
         self._check(self._lib.ile_set_stream(self._h, _stream_handle(stream)), "ile_set_stream")
+
+    def set_refine(self, enable: bool = True):
+        """FP64 refinement of loud samples (on by default; see ile_set_refine in include/ile.h)."""
+        self._check(self._lib.ile_set_refine(self._h, 1 if enable else 0), "ile_set_refine")
+
+    def refine_count(self) -> int:
+        """Samples the last evaluation refined in FP64."""
+        n = ctypes.c_int64()
+        self._check(self._lib.ile_refine_count(self._h, ctypes.byref(n)), "ile_refine_count")
+        return int(n.value)
 
     def set_precision(self, prec: str):
         self._check(self._lib.ile_set_precision(self._h, PREC[prec]), "ile_set_precision")

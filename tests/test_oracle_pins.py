@@ -494,3 +494,16 @@ def test_quv_structure_and_frequency_cut(orc):
     Q3, U3, V3 = orc.quv_from_modes(hf, psd, d_f, df, 200.0, 0.0, 4096.0, 3)
     np.testing.assert_allclose(U2, U3, atol=1e-12)
     np.testing.assert_allclose(Q2, Q3, atol=1e-12)
+
+
+def test_loud_injection_has_the_requested_strength(orc):
+    """The loud points of the GPU tests: the injected template's <h0|h0>/2 (the oracle's quadratic
+    term at theta0) equals rho2/2, and the window bin of the true arrival time recovers about that
+    (the injection identity, up to the noise and the pulse's interpolation error)."""
+    for rho2 in (1e2, 1e4):
+        point, theta0 = orc.loud_point(S, S.SEED_BASE + 90, rho2)
+        lnl, data, A = orc.lnL_grid(point, theta0)
+        assert abs(A - rho2 / 2) < 1e-9 * rho2
+        j0 = point.n_window // 2  # bin j is at t_c + (j - N_t/2)/f_s: theta0's own t_c is the true time
+        assert abs(lnl.max() - rho2 / 2) < 0.05 * rho2 / 2 + 5.0
+        assert abs(int(np.argmax(lnl)) - j0) <= 2

@@ -138,6 +138,26 @@ def oracle_error(ctx, point, n=2048):
             "what": "lnL_t of random samples of the last device iteration vs the FP64 oracle on the same samples"}
 
 
+def loud_error(ile, S, local, prec, rho2s=(1e3, 1e4)):
+    """lnL_t of injections of <h0|h0> = rho2 (2048 samples near the injection, 2048 from the prior)
+    against the FP64 oracle: the loud regime of App. "Choices for finite-precision floating point
+    arithmetic and overflow", through the default path (loud samples refined in FP64)."""
+    import oracle
+    out = []
+    for rho2 in rho2s:
+        point, theta0 = oracle.loud_point(S, S.SEED_BASE + 90, rho2)
+        th = oracle.loud_samples(S, np.random.default_rng(int(rho2) + 5), theta0, 2048, 2048)
+        ref = oracle.lnL_t(point, th)
+        ctx = ile.Context(local, None, prec)
+        ctx.set_data(point)
+        d = np.abs(ctx.eval(th) - ref)
+        out.append({"rho2": rho2, "max_abs_dlnL_t": float(d.max()), "rms_dlnL_t": float(np.sqrt(np.mean(d * d))),
+                    "max_abs_lnL_t": float(np.abs(ref).max()), "samples_checked": int(d.size),
+                    "samples_refined": ctx.refine_count(), "bar": 1e-3})
+        ctx.close()
+    return out
+
+
 def cpu_baseline(point, seconds=12.0):
     cores = os.cpu_count() or 1
     n = cpu_sample_size(point, seconds, cores)
@@ -221,7 +241,7 @@ def profile_tensor_active(kernel_file, prec):
     return profile_fraction(kernel_file, prec, "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active")
 
 
-def batch_bench(ile, S, local, flush, iters=5, n_points=512, plain_iters=1):
+def batch_bench(ile, S, local, flush, iters=5, n_points=512, plain_iters=5):
     """The mixed batch: n_points intrinsic points (M in {2,5,9,21}, K in {3,4}, N_t in
     {256,512,1024}, 2^U(14,20) samples each), `iters` adaptive iterations, tiles chosen by the
     autotuner, every iteration one CUDA-graph launch; the same batch with the plain FP32
@@ -233,32 +253,45 @@ def batch_bench(ile, S, local, flush, iters=5, n_points=512, plain_iters=1):
             for i, d in enumerate(descs)]
     n_iter_samples = sum(d["n_samples"] for d in descs)
 
+    # algorithmic data-term flops of one iteration (4 M N_t K per sample, every point)
+    alg_flops = sum(4.0 * d["n_modes"] * d["n_window"] * d["n_det"] * d["n_samples"] for d in descs)
+
     def timed(prec, n_it, tune):
-        b = ile.Batch(local, None, prec)
+        st = torch.cuda.Stream()
+        b = ile.Batch(local, st, prec)
         b.set_points(points, cfgs)
-        t = b.tune(reps=1) if tune else None
+        t = b.tune(reps=3) if tune else None
         b.reset()
         b.step(1)  # warm-up iteration (graph instantiation), then restart the run
         b.get()
         b.reset()
         torch.cuda.synchronize()
-        flush.fill_(1)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        with torch.cuda.stream(st):
+            flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
         b.step(n_it)
+        e1.record(st)
         res = b.get()
-        dt = time.perf_counter() - t0
+        e1.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3
         b.close()
         return dt, res, t
 
     dt, res, tuning = timed("bf16x3", iters, True)
+    peak = peaks()[0]["bf16_tflops"]
+    achieved = alg_flops * iters / dt / 1e12
     line = {"workload": f"{n_points} intrinsic points (M in {{2,5,9,21}}, K in {{3,4}}, N_t in {{256,512,1024}}, "
                         f"2^U(14,20) samples per point per iteration), {iters} adaptive iterations",
             "n_points": n_points, "samples_per_iteration": n_iter_samples, "iterations": iters,
             "value": n_iter_samples * iters / dt, "unit": UNIT, "s_per_iteration": dt / iters,
             "contraction": "bf16x3, one persistent launch per iteration", "tuning": tuning,
             "ln_L_marg_first_points": [r["ln_L"] for r in res[:4]],
-            "timing": "host clock around step(iterations) + get (graph launches, stream synchronised)"}
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "what": "algorithmic data-term flops of every point / whole iteration time (sampling, "
+                                 "sort, MC sums and histograms included), against the measured dense bf16 peak"},
+            "timing": "CUDA events on the batch's stream around step(iterations) (graph launches)"}
     if plain_iters:
         pdt, _, _ = timed("fp32", plain_iters, False)
         line["plain_fp32"] = {"value": n_iter_samples * plain_iters / pdt, "s_per_iteration": pdt / plain_iters,
@@ -435,6 +468,22 @@ def main():
         psteps = max(3, min(args.steps, 10))
         plain = {"value": N * psteps * world / (pms / 1e3), "ms_per_step": pms / psteps, "contraction": "fp32"}
         pctx.close()
+    # the other split-precision variant of the same workload (config c2 asks for both)
+    variants = {}
+    if not args.no_plain:  # every rank times it (the timing takes a barrier); rank 0 reports
+        for vp in ("bf16x3", "tf32x3"):
+            if vp == args.prec:
+                vctx, vms, vprof, vsteps = ctx, ms, prof, args.steps
+            else:
+                vsteps = max(3, min(args.steps, 10))
+                vms, vprof, _, _, vctx = timed(vp, vsteps, True)
+            cm, cn = vprof["contract"]
+            variants[vp] = {"value": N * vsteps / (vms / 1e3), "ms_per_step": vms / vsteps,
+                            "contract_ms_per_step": cm / vsteps,
+                            "error_vs_oracle": None if (args.no_cpu_baseline or rank != 0)
+                            else oracle_error(vctx, point)}
+            if vctx is not ctx:
+                vctx.close()
 
     # e2e: a user's full evaluation of one intrinsic point through the public API every step --
     # upload the point (host arrays), set up the sampler, one iteration, read the result back
@@ -500,9 +549,12 @@ def main():
                 "gpu_launches": launches, "clocks": clk,
                 "result": {"ln_L_marg": res["ln_L"], "sigma_ln": res["sigma_ln"], "n_eff": res["n_eff"],
                            "iterations": res["n_iter"]}}
+        if variants:
+            line["split_variants"] = variants
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(point)
             line["error_vs_oracle"] = oracle_error(ctx, point)
+            line["error_vs_oracle_loud"] = loud_error(ile, S, local, args.prec)
         if not args.no_adjoint:
             line["adjoint"] = adjoint_bench(ile, S, local, stream, flush, prec=args.prec)
         if not args.no_dmarg:

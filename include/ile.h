@@ -74,6 +74,9 @@ typedef enum {
 /* flags */
 #define ILE_DEVICE_PTRS 1u /* array arguments are device pointers; call is asynchronous */
 #define ILE_NO_TMARG 2u    /* ile_eval writes lnL(n, j) for every window bin: out is [N][N_t] */
+#define ILE_NEAREST 4u     /* ile_eval / ile_integrate: Q_k(t) at the nearest sample (ties to even)
+                              instead of the linear interpolation between samples, for brute-force
+                              cross-checks against a plain sum over the Q series */
 
 #define ILE_NBINS 100      /* histogram bins per adaptive dimension (Sec. GPU-accelerated MC) */
 #define ILE_NDIM 7         /* ra, dec, psi, iota, phi, D, t_c */
@@ -287,9 +290,9 @@ ile_status ile_adapt_last(ile_ctx *ctx, double *theta, double *lnw_prior, uint8_
  * of kernel launches (out_count[s], may be NULL) since the previous read, then resets them.
  * Stages: 0 sampler (S0), 1 geometry/coefficients/quadratic (S1, S2, S4), 2 shifted contraction
  * and time log-sum-exp (S3, S5), 3 Monte Carlo reduction (S6), 4 histogram adaptation (S6),
- * 5 adjoint (ile_eval_grad / ile_integrate_grad).
+ * 5 adjoint (ile_eval_grad / ile_integrate_grad), 6 FP64 refinement of loud samples.
  */
-#define ILE_NSTAGE 6
+#define ILE_NSTAGE 7
 ile_status ile_profile(ile_ctx *ctx, int enable);
 ile_status ile_profile_read(ile_ctx *ctx, double *out_ms, int64_t *out_count, int n_stages);
 

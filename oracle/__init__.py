@@ -47,6 +47,7 @@ class _Point(ctypes.Structure):
         ("Q", ctypes.c_void_p), ("T_ext", ctypes.c_int), ("t_start", ctypes.c_double),
         ("fs", ctypes.c_double), ("U", ctypes.c_void_p), ("V", ctypes.c_void_p),
         ("n_window", ctypes.c_int), ("gmst", ctypes.c_double), ("d_ref", ctypes.c_double),
+        ("nearest", ctypes.c_int),
     ]
 
 
@@ -118,7 +119,7 @@ def _ptr(a: np.ndarray):
 class _PointView:
     """Keeps the contiguous FP64 copies of a point alive while C reads them."""
 
-    def __init__(self, p):
+    def __init__(self, p, nearest: bool = False):
         self.lm = np.ascontiguousarray(p.lm, dtype=np.int32)
         self.det_tensor = np.ascontiguousarray(p.det_tensor, dtype=np.float64)
         self.det_pos = np.ascontiguousarray(p.det_pos, dtype=np.float64)
@@ -128,7 +129,7 @@ class _PointView:
         K, M, T = p.Q.shape
         self.s = _Point(K, M, _ptr(self.lm).value, _ptr(self.det_tensor).value, _ptr(self.det_pos).value,
                         _ptr(self.Q).value, T, float(p.t_start), float(p.fs), _ptr(self.U).value,
-                        _ptr(self.V).value, int(p.n_window), float(p.gmst), float(p.d_ref))
+                        _ptr(self.V).value, int(p.n_window), float(p.gmst), float(p.d_ref), int(bool(nearest)))
 
 
 # ------------------------------------------------------------------------------------ S1 / S2
@@ -170,9 +171,10 @@ class RangeError(ValueError):
     pass
 
 
-def lnL_grid(point, theta):
-    """lnL(j) for j < N_t of one sample theta (7,), plus the data term and A = <h|h>/2."""
-    pv = _PointView(point)
+def lnL_grid(point, theta, nearest: bool = False):
+    """lnL(j) for j < N_t of one sample theta (7,), plus the data term and A = <h|h>/2.
+    nearest: Q at the nearest sample instead of the linear interpolation."""
+    pv = _PointView(point, nearest)
     th = np.ascontiguousarray(theta, dtype=np.float64)
     lnL = np.zeros(point.n_window)
     data = np.zeros(point.n_window)
@@ -185,9 +187,10 @@ def lnL_grid(point, theta):
     return lnL, data, float(A[0])
 
 
-def lnL_t(point, samples, nthreads: int = 0):
-    """Time-marginalised lnL of every sample; samples is SoA (7, N)."""
-    pv = _PointView(point)
+def lnL_t(point, samples, nthreads: int = 0, nearest: bool = False):
+    """Time-marginalised lnL of every sample; samples is SoA (7, N).  nearest: Q at the nearest
+    sample instead of the linear interpolation."""
+    pv = _PointView(point, nearest)
     s = np.ascontiguousarray(samples, dtype=np.float64)
     N = s.shape[1]
     out = np.zeros(N)

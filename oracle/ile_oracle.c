@@ -35,7 +35,8 @@
  *   R4 _{-2}Y_lm(iota,phi) = sqrt((2l+1)/4pi) d^l_{m,2}(iota) e^{i m phi} with the explicit
  *      Wigner-d sum d^l_{m'm}; this gives the closed forms common in GW data analysis
  *      (e.g. _{-2}Y_21 = +sqrt(5/16pi) sin(iota)(1+cos(iota)) e^{i phi}).
- *   R5 geocentric reference time, dt_k = -(r_k . n)/c, linear interpolation of Q between bins.
+ *   R5 geocentric reference time, dt_k = -(r_k . n)/c, linear interpolation of Q between bins;
+ *      a nearest-sample mode (the sample rint(x), ties to even) serves brute-force cross-checks.
  *   R6 time marginalisation with a uniform prior over the N_t-bin window: LSE_j - ln N_t;
  *      bin j sits at t_c + (j - N_t/2)/f_s.
  *   R7 MC error sigma_I / I with the sample variance s^2/N.
@@ -55,6 +56,10 @@
  *      printed E-step cancels w_n), a fixed number of EM steps per iteration started from the
  *      current model, the 1-D Mahalanobis distance |mu_i - mu_j| / sigma in the matching, and the
  *      initial model C equal components evenly spaced over the range with sigma = range / C.
+ *   R25 the M-step mean is clamped into [lo, hi]: a weighted mean of points inside the range lies
+ *      inside it, so the clamp changes nothing but rounding excursions at the range ends (the
+ *      truncated normals of Sec. "Adaptive sampling with gaussian mixture models" need mu there
+ *      for the sampler's tail-safe inverse CDF).
  */
 #include <math.h>
 #include <stdint.h>
@@ -86,6 +91,7 @@ typedef struct {
     int n_window;              /* N_t */
     double gmst;               /* radians */
     double d_ref;              /* Mpc */
+    int nearest;               /* 1: Q at the nearest sample instead of linear interpolation (R5) */
 } orc_point;
 
 /* ---------------------------------------------------------------- S1: geometry (R3, R5) */
@@ -236,8 +242,11 @@ int orc_lnL_grid(const orc_point *P, const double th[7], double *lnL, double *da
         for (int k = 0; k < K; k++) {
             double tau = th[6] + ((double)j - 0.5 * Nt) / P->fs + dt[k];
             double x = (tau - P->t_start) * P->fs;
-            double fl = floor(x);
-            double w = x - fl;
+            /* linear interpolation between samples floor(x) and floor(x) + 1 (reading R5); in the
+             * nearest-sample mode the sample closest to x (ties to even), i.e. the interpolation
+             * with its weight set to zero at the rounded position */
+            double fl = P->nearest ? rint(x) : floor(x);
+            double w = P->nearest ? 0.0 : x - fl;
             if (fl < 0.0 || fl + 1.0 > (double)(T - 1)) { status = ORC_E_RANGE; continue; }
             long i = (long)fl;
             for (int a = 0; a < M; a++) {
@@ -648,7 +657,7 @@ void orc_gmm_em_step(const double *u, const double *wn, long N, orc_gmm1 *g, dou
     for (int c = 0; c < g->C; c++) {
         if (S0[c] > 1e-12 * W) {
             double mu = S1[c] / S0[c], var = S2[c] / S0[c] - mu * mu;
-            g->mu[c] = mu < lo ? lo : (mu > hi ? hi : mu); /* a weighted mean of points in range; rounding only */
+            g->mu[c] = mu < lo ? lo : (mu > hi ? hi : mu); /* R25: a weighted mean of points in range */
             g->sigma[c] = sqrt(var > smin * smin ? var : smin * smin);
             g->w[c] = S0[c] / W;
         } else {

@@ -146,7 +146,7 @@ cudaError_t grow(ile_ctx *ctx, T **p, size_t bytes) {
 // Bracket one launch of stage `stage` with events on the context stream (when profiling) and
 // with an NVTX range on the host timeline (a no-op unless a tool such as Nsight is attached).
 const char *const kStageName[ILE_NSTAGE] = {"ile:sample", "ile:coefficients", "ile:contraction",
-                                            "ile:mc_reduce", "ile:adapt",  "ile:adjoint"};
+                                            "ile:mc_reduce", "ile:adapt",  "ile:adjoint", "ile:refine"};
 struct StageScope {
     ile_ctx *c;
     int stage;
@@ -349,16 +349,19 @@ namespace {
 // Samples are first ordered by quantised detector delays (ile_sort.cu) so that a tile of the
 // contraction spans few time columns; the per-sample results do not depend on that order.
 // lnL_t of loud samples is then recomputed in FP64 (unless the context's refinement is off).
-ile_status run_eval(ile_ctx *ctx, const double *dsamples, int64_t N, double *dout, int full_grid) {
+ile_status run_eval(ile_ctx *ctx, const double *dsamples, int64_t N, double *dout, int full_grid,
+                    bool nearest = false) {
     ile_status st = ensure_samples(ctx, N);
     if (st != ILE_OK) return st;
     const int prec = (int)ctx->prec;
+    PointParams pp = ctx->pp;
+    pp.nearest = nearest ? 1 : 0;
     if (prec != ILE_PREC_FP32) {
         st = ensure_tc_operands(ctx, prec);
         if (st != ILE_OK) return st;
     }
     LoudList loud{nullptr, 0.f};
-    if (full_grid == 0 && ctx->refine && !ctx->pp.dm.on) {
+    if (full_grid == 0 && ctx->refine && !pp.dm.on) {
         loud = LoudList{ctx->loud, ile_refine_threshold(prec), 0, ctx->cap};
         CK(cudaMemsetAsync(ctx->loud, 0, sizeof(int), ctx->stream));
     }
@@ -366,30 +369,31 @@ ile_status run_eval(ile_ctx *ctx, const double *dsamples, int64_t N, double *dou
         // fused kernel: S1, S2, S4 are computed inside the tensor-core kernel
         {
             StageScope t(ctx, 1, 3);
-            CK(ile_launch_sort(ctx->pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));
+            CK(ile_launch_sort(pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));
         }
         StageScope t(ctx, 2);
-        CK(ile_launch_tc2(ctx->pp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ile_tc_tpad(ctx->pp.T_ext),
-                          ile_tc_kpad(prec, ctx->pp.M), ctx->UV, dsamples, ctx->perm, N, dout, nullptr, full_grid,
+        CK(ile_launch_tc2(pp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ile_tc_tpad(pp.T_ext),
+                          ile_tc_kpad(prec, pp.M), ctx->UV, dsamples, ctx->perm, N, dout, nullptr, full_grid,
                           loud, ctx->flags, ctx->stream));
     } else {
         {
             StageScope t(ctx, 1, 4);
-            CK(ile_launch_sort(ctx->pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));
-            CK(ile_launch_prep(ctx->pp, ctx->UV, dsamples, ctx->perm, N, ctx->s, ctx->flags, ctx->stream));
+            CK(ile_launch_sort(pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));
+            CK(ile_launch_prep(pp, ctx->UV, dsamples, ctx->perm, N, ctx->s, ctx->flags, ctx->stream));
         }
         StageScope t(ctx, 2);
         if (prec == ILE_PREC_FP32)
-            CK(ile_launch_plain(ctx->pp, ctx->Qp, ctx->s, ctx->perm, N, dout, full_grid, loud, ctx->flags,
+            CK(ile_launch_plain(pp, ctx->Qp, ctx->s, ctx->perm, N, dout, full_grid, loud, ctx->flags,
                                 ctx->stream));
         else
-            CK(ile_launch_tc(prec, ctx->pp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ctx->s, ctx->perm, N, dout,
+            CK(ile_launch_tc(prec, pp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ctx->s, ctx->perm, N, dout,
                              full_grid, loud, ctx->flags, ctx->stream));
     }
     if (loud.list) {
-        StageScope t(ctx, 2);
+        StageScope t(ctx, 6);
         Refine64 r = ctx->r64;
         r.thr = loud.thr;
+        r.nearest = pp.nearest;
         CK(ile_launch_refine(r, ctx->Q64, ctx->U64, ctx->V64, ctx->Qp, dsamples, N, ctx->loud, ctx->cap, dout,
                              ctx->flags, ctx->n_sm, ctx->stream));
     }
@@ -872,12 +876,13 @@ ile_status ile_eval(ile_ctx *ctx, const double *samples, int64_t N, double *out,
     DeviceGuard g(ctx->device);
     ile_status st = ensure_samples(ctx, N);
     if (st != ILE_OK) return st;
-    if (flags & ILE_DEVICE_PTRS) return run_eval(ctx, samples, N, out, full);
+    const bool nearest = (flags & ILE_NEAREST) != 0;
+    if (flags & ILE_DEVICE_PTRS) return run_eval(ctx, samples, N, out, full, nearest);
     st = ensure_out(ctx, sizeof(double) * out_elems);
     if (st != ILE_OK) return st;
     CK(cudaMemcpyAsync(ctx->theta, samples, sizeof(double) * ILE_NDIM * (size_t)N, cudaMemcpyHostToDevice,
                        ctx->stream));
-    st = run_eval(ctx, ctx->theta, N, ctx->out, full);
+    st = run_eval(ctx, ctx->theta, N, ctx->out, full, nearest);
     if (st != ILE_OK) return st;
     st = read_flags(ctx);
     if (st != ILE_OK) return st;
@@ -901,7 +906,7 @@ ile_status ile_integrate(ile_ctx *ctx, const double *samples, const double *ln_p
             if (st != ILE_OK) return st;
             lnl = ctx->out;
         }
-        st = run_eval(ctx, samples, N, lnl, 0);
+        st = run_eval(ctx, samples, N, lnl, 0, (flags & ILE_NEAREST) != 0);
         if (st != ILE_OK) return st;
         StageScope t(ctx, 3, 2);
         CK(ile_launch_mc(lnl, ln_prior, ln_ps, N, ctx->part, np, result, ctx->stream));
@@ -914,7 +919,7 @@ ile_status ile_integrate(ile_ctx *ctx, const double *samples, const double *ln_p
     if (ln_prior)
         CK(cudaMemcpyAsync(ctx->lnp, ln_prior, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
     if (ln_ps) CK(cudaMemcpyAsync(ctx->lnps, ln_ps, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
-    st = run_eval(ctx, ctx->theta, N, ctx->out, 0);
+    st = run_eval(ctx, ctx->theta, N, ctx->out, 0, (flags & ILE_NEAREST) != 0);
     if (st != ILE_OK) return st;
     {
         StageScope t(ctx, 3, 2);

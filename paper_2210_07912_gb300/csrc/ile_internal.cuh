@@ -72,6 +72,7 @@ struct PointParams {
     float gmst;
     float d_ref;
     float log_nt;     // ln N_t
+    int nearest;      // 1: Q at the nearest sample (window start rounded, interpolation weight 0)
     float det_tensor[ILE_MAX_DET][9];
     float det_pos_c[ILE_MAX_DET][3];  // r_k / c in seconds
     ModeTab mode[ILE_MAX_MODES];
@@ -212,6 +213,8 @@ __device__ __forceinline__ void ile_sample_geometry(const PointParams &pp, float
         Fi[k] = (X0 * DY0 + X1 * DY1 + X2 * DY2) + (Y0 * DX0 + Y1 * DX1 + Y2 * DX2);
         float dt = -(pp.det_pos_c[k][0] * n0 + pp.det_pos_c[k][1] * n1 + pp.det_pos_c[k][2] * n2);
         x0[k] = (tc + dt) * pp.fs + pp.x_offset;
+        // nearest-sample mode: bin j reads sample rint(x0 + j) = rint(x0) + j with weight 0
+        if (pp.nearest) x0[k] = rintf(x0[k]);
     }
 }
 
@@ -311,7 +314,8 @@ struct Mode64 {
 struct Refine64 {
     int K, M, Nt, T_ext;
     double fs, t_start, gmst, d_ref, log_nt;
-    float thr;  // a window bin's data term is recomputed in FP64 when |D_j| exceeds this
+    float thr;    // a window bin's data term is recomputed in FP64 when |D_j| exceeds this
+    int nearest;  // 1: Q at the nearest sample
     double det_tensor[ILE_MAX_DET][9];
     double det_pos[ILE_MAX_DET][3];  // metres
     Mode64 mode[ILE_MAX_MODES];

@@ -75,7 +75,8 @@ __device__ void refine_one(const Refine64 &P, const double2 *__restrict__ Q64, c
     for (int k = 0; k < ILE_MAX_DET; k++) {
         Frk[k] = __shfl_sync(0xffffffffu, Fr, k);
         Fik[k] = __shfl_sync(0xffffffffu, Fi, k);
-        const double xk = __shfl_sync(0xffffffffu, x0, k);
+        const double xs = __shfl_sync(0xffffffffu, x0, k);
+        const double xk = P.nearest ? rint(xs) : xs;  // nearest-sample mode: weight 0 at the rounded start
         const double fl = floor(xk);
         ik[k] = k < K ? (int)fl : 0;
         wk[k] = xk - fl;

@@ -18,6 +18,7 @@ ILE_OK, ILE_E_ARG, ILE_E_STATE, ILE_E_RANGE, ILE_E_NONFINITE, ILE_E_CUDA, ILE_E_
 PREC = {"fp32": 0, "tf32x3": 1, "bf16x3": 2}
 ILE_DEVICE_PTRS = 1
 ILE_NO_TMARG = 2
+ILE_NEAREST = 4
 NDIM = 7
 NBINS = 100
 GMM_MAX = 8
@@ -387,24 +388,27 @@ class Context:
         return out
 
     # ---------------------------------------------------------------- host-pointer calls
-    def eval(self, samples: np.ndarray, grid: bool = False) -> np.ndarray:
+    def eval(self, samples: np.ndarray, grid: bool = False, nearest: bool = False) -> np.ndarray:
+        """lnL_t (or with grid=True the lnL(n, j) grid) of samples (7, N); nearest: Q at the nearest
+        sample instead of the linear interpolation (ILE_NEAREST)."""
         s = np.ascontiguousarray(samples, np.float64)
         if s.ndim != 2 or s.shape[0] != NDIM:
             raise ValueError("samples must be (7, N)")
         N = s.shape[1]
         out = np.zeros((N, self.n_window) if grid else N, np.float64)
-        self._check(self._lib.ile_eval(self._h, _np_ptr(s), N, _np_ptr(out), ILE_NO_TMARG if grid else 0),
-                    "ile_eval")
+        flags = (ILE_NO_TMARG if grid else 0) | (ILE_NEAREST if nearest else 0)
+        self._check(self._lib.ile_eval(self._h, _np_ptr(s), N, _np_ptr(out), flags), "ile_eval")
         return out
 
-    def integrate(self, samples, ln_prior=None, ln_ps=None, want_lnL=False):
+    def integrate(self, samples, ln_prior=None, ln_ps=None, want_lnL=False, nearest: bool = False):
         s = np.ascontiguousarray(samples, np.float64)
         N = s.shape[1]
         lp = None if ln_prior is None else np.ascontiguousarray(ln_prior, np.float64)
         lps = None if ln_ps is None else np.ascontiguousarray(ln_ps, np.float64)
         res = np.zeros(7)
         lnl = np.zeros(N) if want_lnL else None
-        st = self._lib.ile_integrate(self._h, _np_ptr(s), _np_ptr(lp), _np_ptr(lps), N, _np_ptr(res), _np_ptr(lnl), 0)
+        st = self._lib.ile_integrate(self._h, _np_ptr(s), _np_ptr(lp), _np_ptr(lps), N, _np_ptr(res), _np_ptr(lnl),
+                                     ILE_NEAREST if nearest else 0)
         self._check(st, "ile_integrate")
         d = dict(ln_L=res[0], sigma_ln=res[1], n_eff=res[2], ess=res[3], m=res[4], s1=res[5], s2=res[6])
         return (d, lnl) if want_lnL else d
@@ -524,7 +528,7 @@ class Context:
         return theta, lw, bins, lnl
 
     # ---------------------------------------------------------------- stage timing
-    STAGES = ("sample", "prep", "contract", "mc", "adapt", "grad")
+    STAGES = ("sample", "prep", "contract", "mc", "adapt", "grad", "refine")
 
     def profile(self, enable: bool = True):
         self._check(self._lib.ile_profile(self._h, 1 if enable else 0), "ile_profile")

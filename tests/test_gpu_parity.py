@@ -171,3 +171,32 @@ def test_error_paths(ile):
     with pytest.raises(ile.IleError) as e:
         c.set_data(bad)
     assert e.value.status == ile.ILE_E_ARG
+
+
+def _half_integer_clear(orc, point, th, margin=1e-3):
+    """Samples whose window starts are at least `margin` samples away from a half-integer in
+    every detector: there the nearest-sample choice does not depend on FP32 vs FP64 rounding."""
+    keep = np.ones(th.shape[1], bool)
+    for n in range(th.shape[1]):
+        for k in range(point.n_det):
+            dt = orc.delay(point.det_pos[k], th[0, n], th[1, n], point.gmst)
+            x = (th[6, n] - point.n_window / 2 / point.fs + dt - point.t_start) * point.fs
+            if abs((x - np.floor(x)) - 0.5) < margin:
+                keep[n] = False
+    return th[:, keep]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_nearest_sample_mode_matches_oracle(ile, orc, prec):
+    """ILE_NEAREST (Q at the nearest sample) against the oracle's brute-force-pinned nearest mode,
+    every sample of the small point and 2000 of the full-shape point."""
+    for name, N in ((S.SMALL, 2000), (S.FULL, 2000)):
+        point = S.workload_point(name)
+        th = _half_integer_clear(orc, point, S.workload_samples(name, N))
+        ctx = ile.Context(0, None, prec)
+        ctx.set_data(point)
+        got = ctx.eval(th, nearest=True)
+        ref = orc.lnL_t(point, th, nearest=True)
+        assert np.abs(got - ref).max() < 1e-3, (name, prec)
+        # and the nearest mode is a different function from the interpolated one
+        assert np.abs(ctx.eval(th) - ref).max() > 1e-6

@@ -63,7 +63,10 @@ def test_point_from_built_quv_likelihood(ile, orc):
     th = S.prior_samples(np.random.default_rng(6), 500)
     got = ctx.eval(th)
     ref = orc.lnL_t(mk(Qr, Ur, Vr), th)
-    assert np.abs(got - ref).max() < 1e-3 * max(1.0, np.abs(ref).max() / 100.0)
+    # |lnL_t| reaches ~750 here: the loud samples go through the FP64 refinement, so the absolute
+    # bar of the path applies as it stands
+    assert np.abs(ref).max() > 100.0
+    assert np.abs(got - ref).max() < 1e-3
 
 
 def test_build_quv_errors(ile):

@@ -507,3 +507,33 @@ def test_loud_injection_has_the_requested_strength(orc):
         j0 = point.n_window // 2  # bin j is at t_c + (j - N_t/2)/f_s: theta0's own t_c is the true time
         assert abs(lnl.max() - rho2 / 2) < 0.05 * rho2 / 2 + 5.0
         assert abs(int(np.argmax(lnl)) - j0) <= 2
+
+
+def test_nearest_sample_mode_brute_force(orc):
+    """The oracle's nearest-sample mode (reading of the delay interpolation, exported as
+    ILE_NEAREST) against a plain Python sum over the Q series with Python's own round-half-even,
+    on a tiny point; where every detector's window start is an integer the nearest and linear
+    modes agree."""
+    point = S.make_point(S.SEED_BASE + 70, 2, 2, 8, spectrum="random")
+    rng = np.random.default_rng(71)
+    th = S.prior_samples(rng, 6)
+    for n in range(th.shape[1]):
+        t = th[:, n]
+        lnl, data, A = orc.lnL_grid(point, t, nearest=True)
+        ra, dec, psi, iota, phi, dist, tc = t
+        y = np.array([orc.sylm(int(l), int(m), iota, phi) for l, m in point.lm])
+        for j in range(point.n_window):
+            want = 0.0
+            for k in range(point.n_det):
+                c = (point.d_ref / dist) * orc.antenna(point.det_tensor[k], ra, dec, psi) * y
+                tau = tc + (j - point.n_window / 2) / point.fs + orc.delay(point.det_pos[k], ra, dec)
+                i = round((tau - point.t_start) * point.fs)  # Python rounds half to even
+                want += np.sum((np.conj(c) * point.Q[k, :, i]).real)
+            assert abs(data[j] - want) < 1e-10 * max(1.0, abs(want)), (n, j)
+            assert abs(lnl[j] - (want - A)) < 1e-10 * max(1.0, abs(want - A))
+    # with a flat (time-independent) Q the choice of sample does not matter: the two modes agree
+    flat = S.make_point(S.SEED_BASE + 72, 2, 2, 8, spectrum="random", pulse_sigma=None, noise=0.0)
+    for n in range(th.shape[1]):
+        a = orc.lnL_grid(flat, th[:, n], nearest=True)[0]
+        b = orc.lnL_grid(flat, th[:, n])[0]
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)

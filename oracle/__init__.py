@@ -61,12 +61,20 @@ class _Gmm1(ctypes.Structure):
     ]
 
 
+class _Gmm2(ctypes.Structure):
+    _fields_ = [
+        ("C", ctypes.c_int), ("w", ctypes.c_double * GMM_MAX), ("mu", (ctypes.c_double * 2) * GMM_MAX),
+        ("cov", (ctypes.c_double * 3) * GMM_MAX), ("n", ctypes.c_double),
+    ]
+
+
 class _Sampler(ctypes.Structure):
     _fields_ = [
         ("lo", ctypes.c_double * NDIM), ("hi", ctypes.c_double * NDIM),
         ("adaptive", ctypes.c_int * NDIM), ("cdf", ctypes.c_void_p),
         ("sky", ctypes.c_int), ("pole", ctypes.c_double * 3), ("gmst", ctypes.c_double),
         ("gmm", ctypes.c_int * NDIM), ("model", ctypes.c_void_p),
+        ("pair", ctypes.c_int), ("pair_model", ctypes.c_void_p),
     ]
 
 
@@ -102,6 +110,20 @@ def _load():
             lib.orc_cdf_from_hist.argtypes = [vp, d, vp]
             lib.orc_cdf_uniform.argtypes = [vp]
             lib.orc_sky_frame.argtypes = [vp, vp, vp, vp]
+            G2 = ctypes.POINTER(_Gmm2)
+            lib.orc_bvn_rect.argtypes = [vp, vp, vp, vp]
+            lib.orc_bvn_rect.restype = d
+            lib.orc_gmm2_lnpdf.argtypes = [G2, vp, vp, vp]
+            lib.orc_gmm2_lnpdf.restype = d
+            lib.orc_gmm2_lnpdf_z.argtypes = [G2, vp, vp]
+            lib.orc_gmm2_lnpdf_z.restype = d
+            lib.orc_gmm2_masses.argtypes = [G2, vp, vp, vp]
+            lib.orc_gmm2_em_step.argtypes = [vp, vp, vp, ctypes.c_long, G2, vp, vp]
+            lib.orc_gmm2_merge.argtypes = [G2, G2, d, vp, vp, G2]
+            lib.orc_gmm2_init.argtypes = [G2, i, vp, vp]
+            lib.orc_gmm2_update.argtypes = [G2, vp, vp, vp, ctypes.c_long, i, vp, vp]
+            lib.orc_pair_draw.argtypes = [G2, vp, vp, ctypes.c_uint32, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
+            lib.orc_pair_draw.restype = i
             lib.orc_dmarg_lnF.argtypes = [d, d, d, d, d]
             lib.orc_dmarg_lnF.restype = d
             lib.orc_lnL_dmarg.argtypes = [ctypes.POINTER(_Point), vp, ctypes.c_long, d, d, vp]
@@ -351,14 +373,110 @@ def gmm_merge(cur, bat, M: float):
     return _gmm_dict(out)
 
 
+# ------------------------------------------------------------------------------------ correlated sky pair
+def _gmm2_struct(m):
+    g = _Gmm2()
+    C = len(m["w"])
+    g.C = C
+    for c in range(C):
+        g.w[c] = float(m["w"][c])
+        for j in range(2):
+            g.mu[c][j] = float(m["mu"][c][j])
+        for j in range(3):
+            g.cov[c][j] = float(m["cov"][c][j])
+    g.n = float(m.get("n", 0.0))
+    return g
+
+
+def _gmm2_dict(g):
+    C = g.C
+    return dict(w=np.array(g.w[:C]), mu=np.array([[g.mu[c][0], g.mu[c][1]] for c in range(C)]),
+                cov=np.array([[g.cov[c][0], g.cov[c][1], g.cov[c][2]] for c in range(C)]), n=float(g.n))
+
+
+def _v2(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def bvn_rect(mu, cov, lo, hi) -> float:
+    """Mass of the rectangle [lo0, hi0] x [lo1, hi1] under N(mu, [[cov0, cov1], [cov1, cov2]])."""
+    a, b, c, e = _v2(mu), _v2(cov), _v2(lo), _v2(hi)
+    return _load().orc_bvn_rect(_ptr(a), _ptr(b), _ptr(c), _ptr(e))
+
+
+def gmm2_init(C: int, lo, hi):
+    g = _Gmm2()
+    a, b = _v2(lo), _v2(hi)
+    _load().orc_gmm2_init(ctypes.byref(g), int(C), _ptr(a), _ptr(b))
+    return _gmm2_dict(g)
+
+
+def gmm2_masses(m, lo, hi):
+    """Each component's mass inside the rectangle."""
+    g = _gmm2_struct(m)
+    a, b = _v2(lo), _v2(hi)
+    Z = np.zeros(GMM_MAX)
+    _load().orc_gmm2_masses(ctypes.byref(g), _ptr(a), _ptr(b), _ptr(Z))
+    return Z[: g.C]
+
+
+def gmm2_lnpdf(m, lo, hi, x, Z=None) -> float:
+    """ln of the truncated pair density at x (Z: the masses from gmm2_masses, else computed)."""
+    g = _gmm2_struct(m)
+    if Z is None:
+        a, b, c = _v2(lo), _v2(hi), _v2(x)
+        return _load().orc_gmm2_lnpdf(ctypes.byref(g), _ptr(a), _ptr(b), _ptr(c))
+    z = np.zeros(GMM_MAX)
+    z[: len(Z)] = Z
+    c = _v2(x)
+    return _load().orc_gmm2_lnpdf_z(ctypes.byref(g), _ptr(z), _ptr(c))
+
+
+def gmm2_em_step(m, u0, u1, w, lo, hi):
+    g = _gmm2_struct(m)
+    x0, x1, ww, a, b = _v2(u0), _v2(u1), _v2(w), _v2(lo), _v2(hi)
+    _load().orc_gmm2_em_step(_ptr(x0), _ptr(x1), _ptr(ww), x0.size, ctypes.byref(g), _ptr(a), _ptr(b))
+    return _gmm2_dict(g)
+
+
+def gmm2_merge(cur, bat, M: float, lo, hi):
+    a, b, out = _gmm2_struct(cur), _gmm2_struct(bat), _Gmm2()
+    l, h = _v2(lo), _v2(hi)
+    _load().orc_gmm2_merge(ctypes.byref(a), ctypes.byref(b), float(M), _ptr(l), _ptr(h), ctypes.byref(out))
+    return _gmm2_dict(out)
+
+
+def gmm2_update(m, u0, u1, w, iters: int, lo, hi):
+    """EM on the batch (points (u0, u1), weights w) from the current pair model, then the merge."""
+    g = _gmm2_struct(m)
+    x0, x1, ww, a, b = _v2(u0), _v2(u1), _v2(w), _v2(lo), _v2(hi)
+    _load().orc_gmm2_update(ctypes.byref(g), _ptr(x0), _ptr(x1), _ptr(ww), x0.size, int(iters), _ptr(a), _ptr(b))
+    return _gmm2_dict(g)
+
+
+def pair_draw(m, lo, hi, a_word: int, ctr0, key):
+    """One draw of the pair (see orc_pair_draw): returns (x (2,), component, attempts)."""
+    g = _gmm2_struct(m)
+    l, h = _v2(lo), _v2(hi)
+    c0 = np.ascontiguousarray(ctr0, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    x = np.zeros(2)
+    comp = ctypes.c_int()
+    t = _load().orc_pair_draw(ctypes.byref(g), _ptr(l), _ptr(h), int(a_word), _ptr(c0), _ptr(k), _ptr(x),
+                              ctypes.byref(comp))
+    return x, comp.value, t
+
+
 def norm_ppf(p: float) -> float:
     return _load().orc_norm_ppf(float(p))
 
 
-def make_sampler(lo, hi, adaptive, cdf, sky_pole=None, gmst=0.0, gmm=None):
+def make_sampler(lo, hi, adaptive, cdf, sky_pole=None, gmst=0.0, gmm=None, pair=None):
     """sky_pole: pole of the rotated network sky frame (variables 0, 1 in that frame), or None.
     gmm: None or a list of 7 entries, each None (histogram / prior) or a mixture model dict
-    (w, mu, sigma, n) for an adaptive dimension drawn from its Gaussian mixture."""
+    (w, mu, sigma, n) for an adaptive dimension drawn from its Gaussian mixture.
+    pair: None or a pair model dict (w, mu (C,2), cov (C,3), n): variables 0 and 1 drawn together
+    from the correlated mixture."""
     cdf = np.ascontiguousarray(cdf, dtype=np.uint64).reshape(NDIM, NBINS + 1)
     pole = (0.0, 0.0, 0.0) if sky_pole is None else tuple(float(x) for x in sky_pole)
     models = (_Gmm1 * NDIM)()
@@ -372,7 +490,12 @@ def make_sampler(lo, hi, adaptive, cdf, sky_pole=None, gmst=0.0, gmm=None):
                  (ctypes.c_int * NDIM)(*[int(a) for a in adaptive]), _ptr(cdf).value, 0 if sky_pole is None else 1,
                  (ctypes.c_double * 3)(*pole), float(gmst), (ctypes.c_int * NDIM)(*flags),
                  ctypes.cast(models, ctypes.c_void_p).value)
-    s._keep = (cdf, models)
+    pm = None
+    if pair is not None:
+        pm = _gmm2_struct(pair)
+        s.pair = 1
+        s.pair_model = ctypes.cast(ctypes.pointer(pm), ctypes.c_void_p).value
+    s._keep = (cdf, models, pm)
     return s
 
 
@@ -418,13 +541,15 @@ def cdf_uniform():
 # ------------------------------------------------------------------------------------ S0-S6 loop
 def adapt_run(point, seed: int, N: int, n_iter: int, adapt_mask: int, eps: float, lo, hi, point_id: int = 0,
               nthreads: int = 0, cdf0=None, iter0: int = 0, sky_pole=None, gmm_mask: int = 0,
-              gmm_components: int = 3, gmm_em_iters: int = 8, gmm0=None):
+              gmm_components: int = 3, gmm_em_iters: int = 8, gmm0=None, gmm_pair: bool = False, pair0=None):
     """Adaptive-Cartesian integration in the order of Sec. "GPU-accelerated Monte Carlo integration":
     for each iteration draw N samples from the separable sampling prior, evaluate lnL_t, accumulate
     the Monte Carlo sums of Eq. (eq:lnL:MonteCarlo) (pooled over iterations, each sample weighted by
     the p_s it was drawn from) and refit each adaptive dimension's 100-bin histogram.
     Adaptive dimensions in gmm_mask are drawn from a truncated Gaussian mixture instead
-    (Sec. "Adaptive sampling with gaussian mixture models"), refit each iteration by gmm_update.
+    (Sec. "Adaptive sampling with gaussian mixture models"), refit each iteration by gmm_update;
+    with gmm_pair the sky pair (variables 0 and 1) is drawn from one correlated mixture, refit by
+    gmm2_update.
     Returns the pooled estimate, the per-iteration estimates, the final tables and mixtures, and the
     last iteration's samples."""
     adaptive = [(adapt_mask >> d) & 1 for d in range(NDIM)]
@@ -432,6 +557,10 @@ def adapt_run(point, seed: int, N: int, n_iter: int, adapt_mask: int, eps: float
     for d in range(NDIM):
         if adaptive[d] and (gmm_mask >> d) & 1:
             gmm[d] = dict(gmm0[d]) if gmm0 is not None else gmm_init(gmm_components, lo[d], hi[d])
+    plo, phi_ = [lo[0], lo[1]], [hi[0], hi[1]]
+    pair = None
+    if gmm_pair:
+        pair = dict(pair0) if pair0 is not None else gmm2_init(gmm_components, plo, phi_)
     cdf = np.zeros((NDIM, NBINS + 1), np.uint64)
     for d in range(NDIM):
         cdf[d] = cdf_uniform() if cdf0 is None else cdf0[d]
@@ -439,7 +568,7 @@ def adapt_run(point, seed: int, N: int, n_iter: int, adapt_mask: int, eps: float
     iters = []
     last = None
     for it in range(iter0, iter0 + n_iter):
-        smp = make_sampler(lo, hi, adaptive, cdf, sky_pole, point.gmst, gmm)
+        smp = make_sampler(lo, hi, adaptive, cdf, sky_pole, point.gmst, gmm, pair)
         theta, lwp, bins, u = sample(smp, seed, it, point_id, 0, N, with_u=True)
         lnl = lnL_t(point, theta, nthreads)
         lnw = lnl + lwp
@@ -448,15 +577,21 @@ def adapt_run(point, seed: int, N: int, n_iter: int, adapt_mask: int, eps: float
         lnw_all.append(lnw)
         hists = np.zeros((NDIM, NBINS))
         gmm_before = [None if g is None else dict(g) for g in gmm]
+        pair_before = None if pair is None else dict(pair)
+        if pair is not None:
+            pair = gmm2_update(pair, u[0], u[1], np.exp(lnw - lnw.max()), gmm_em_iters, plo, phi_)
         for d in range(NDIM):
+            if pair is not None and d < 2:
+                continue
             if gmm[d] is not None:
                 gmm[d] = gmm_update(gmm[d], u[d], np.exp(lnw - lnw.max()), gmm_em_iters, lo[d], hi[d])
             elif adaptive[d]:
                 hists[d] = hist(lnw, bins[d])
                 cdf[d] = cdf_from_hist(hists[d], eps)
-        last = dict(theta=theta, lnw_prior=lwp, bins=bins, lnL=lnl, hist=hists, u=u, gmm=gmm_before)
+        last = dict(theta=theta, lnw_prior=lwp, bins=bins, lnL=lnl, hist=hists, u=u, gmm=gmm_before,
+                    pair=pair_before)
     pooled = mc_stats(np.concatenate(lnw_all))
-    return dict(pooled=pooled, iters=iters, cdf=cdf, last=last, gmm=gmm)
+    return dict(pooled=pooled, iters=iters, cdf=cdf, last=last, gmm=gmm, pair=pair)
 
 
 # ------------------------------------------------------------------------------------ loud injections

@@ -56,6 +56,18 @@
  *      printed E-step cancels w_n), a fixed number of EM steps per iteration started from the
  *      current model, the 1-D Mahalanobis distance |mu_i - mu_j| / sigma in the matching, and the
  *      initial model C equal components evenly spaced over the range with sigma = range / C.
+ *   R26 correlated sampling of the sky pair (sampling variables 0 and 1; Sec. "Adaptive sampling
+ *      with gaussian mixture models" samples subsets of dimensions jointly, App. "Gaussian mixture
+ *      model implementation" gives the multivariate EM, merge and the truncation by rejection):
+ *      each component is a bivariate normal truncated to the rectangle, its mass Z_c inside
+ *      computed exactly (so ln p_s is the normalised density and the integral stays unbiased);
+ *      the component is drawn once per sample and only the whitened pair is redrawn on
+ *      rejection (so the accepted density of component c is its truncated normal); the whitening
+ *      uses the Cholesky factor of the covariance (any square root gives the same draws' law;
+ *      the paper writes the eigen form); floors sigma_j >= 1e-3 of the range, |rho| <= 0.9, the
+ *      mean inside the rectangle (after every M-step and merge); the initial model places C
+ *      components on the rectangle's diagonal; the cost of a matching is the paper's sum of the
+ *      two one-sided Mahalanobis distances of every matched pair.
  *   R25 the M-step mean is clamped into [lo, hi]: a weighted mean of points inside the range lies
  *      inside it, so the clamp changes nothing but rounding excursions at the range ends (the
  *      truncated normals of Sec. "Adaptive sampling with gaussian mixture models" need mu there
@@ -385,6 +397,17 @@ typedef struct {
     double n;
 } orc_gmm1;
 
+/* The correlated mixture of the sky pair (sampling variables 0 and 1 together; Sec. "Adaptive
+ * sampling with gaussian mixture models": correlated sampling in a subset of dimensions; App.
+ * "Gaussian mixture model implementation"): C components with weights w, means mu[c] and
+ * covariances cov[c] = {S00, S01, S11}, each a bivariate normal truncated to the rectangle
+ * [lo0, hi0] x [lo1, hi1]; n = samples the model has been trained on. */
+typedef struct {
+    int C;
+    double w[ORC_GMM_MAX], mu[ORC_GMM_MAX][2], cov[ORC_GMM_MAX][3];
+    double n;
+} orc_gmm2;
+
 typedef struct {
     double lo[ORC_NDIM], hi[ORC_NDIM];
     int adaptive[ORC_NDIM];
@@ -394,6 +417,8 @@ typedef struct {
     double gmst;
     int gmm[ORC_NDIM];   /* 1: adaptive dimension drawn from its mixture instead of its histogram */
     const orc_gmm1 *model; /* [7] */
+    int pair;            /* 1: variables 0 and 1 drawn together from pair_model */
+    const orc_gmm2 *pair_model;
 } orc_sampler;
 
 /* Standard normal CDF and its inverse (Newton iterations on erfc from a coarse start). */
@@ -452,6 +477,305 @@ double orc_gmm_lnpdf(const orc_gmm1 *g, double lo, double hi, double u)
     return m + log(s);
 }
 
+/* Uniform in (0, 1) from the top 23 bits of one 32-bit word. */
+static double unit23(uint32_t w)
+{
+    return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
+}
+
+/* ---- correlated sky-pair mixture (R26) */
+
+/* Mass of the rectangle [lo0, hi0] x [lo1, hi1] under N(mu, cov): in standardised coordinates
+ * u_j = (x_j - mu_j) / sigma_j with correlation rho it is the integral over u_0 in [a_0, b_0] of
+ * phi(u_0) [Phi((b_1 - rho u_0) / s) - Phi((a_1 - rho u_0) / s)], s = sqrt(1 - rho^2) (the
+ * conditional law of u_1 given u_0), evaluated by composite Simpson over [a_0, b_0] cut to
+ * [-12, 12] (4096 panels). */
+double orc_bvn_rect(const double mu[2], const double cov[3], const double lo[2], const double hi[2])
+{
+    double s0 = sqrt(cov[0]), s1 = sqrt(cov[2]);
+    double rho = cov[1] / (s0 * s1), s = sqrt(1.0 - rho * rho);
+    double a0 = (lo[0] - mu[0]) / s0, b0 = (hi[0] - mu[0]) / s0;
+    double a1 = (lo[1] - mu[1]) / s1, b1 = (hi[1] - mu[1]) / s1;
+    if (a0 < -12.0) a0 = -12.0;
+    if (b0 > 12.0) b0 = 12.0;
+    if (!(b0 > a0)) return 0.0;
+    const int P = 4096;
+    double h = (b0 - a0) / P, sum = 0.0;
+    for (int i = 0; i <= P; i++) {
+        double u = a0 + i * h;
+        double f = exp(-0.5 * u * u) / sqrt(2.0 * ORC_PI) * (norm_cdf((b1 - rho * u) / s) - norm_cdf((a1 - rho * u) / s));
+        double wgt = (i == 0 || i == P) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+        sum += wgt * f;
+    }
+    return sum * h / 3.0;
+}
+
+/* Every component's mass Z_c inside the rectangle (orc_bvn_rect). */
+void orc_gmm2_masses(const orc_gmm2 *g, const double lo[2], const double hi[2], double *Z)
+{
+    for (int c = 0; c < g->C; c++) Z[c] = orc_bvn_rect(g->mu[c], g->cov[c], lo, hi);
+}
+
+/* ln of the truncated pair density sum_c (w_c / sum w) N(x | mu_c, cov_c) / Z_c on the rectangle,
+ * Z_c the components' masses (orc_gmm2_masses), as a log-sum-exp over c. */
+double orc_gmm2_lnpdf_z(const orc_gmm2 *g, const double *Z, const double x[2])
+{
+    double tot = 0.0, l[ORC_GMM_MAX], m = -INFINITY;
+    for (int c = 0; c < g->C; c++) tot += g->w[c];
+    for (int c = 0; c < g->C; c++) {
+        const double *S = g->cov[c];
+        double det = S[0] * S[2] - S[1] * S[1];
+        double d0 = x[0] - g->mu[c][0], d1 = x[1] - g->mu[c][1];
+        double q = (S[2] * d0 * d0 - 2.0 * S[1] * d0 * d1 + S[0] * d1 * d1) / det;
+        l[c] = log(g->w[c] / tot) - log(2.0 * ORC_PI * sqrt(det) * Z[c]) - 0.5 * q;
+        if (l[c] > m) m = l[c];
+    }
+    double sum = 0.0;
+    for (int c = 0; c < g->C; c++) sum += exp(l[c] - m);
+    return m + log(sum);
+}
+
+double orc_gmm2_lnpdf(const orc_gmm2 *g, const double lo[2], const double hi[2], const double x[2])
+{
+    double Z[ORC_GMM_MAX];
+    orc_gmm2_masses(g, lo, hi, Z);
+    return orc_gmm2_lnpdf_z(g, Z, x);
+}
+
+/* Integer cumulative table of mixture weights w[0..C-1] (2^32 scale, same rule as the histograms). */
+static void weights_cum(const double *w, int C, uint64_t *cw)
+{
+    double tot = 0.0, acc = 0.0;
+    for (int c = 0; c < C; c++) tot += w[c];
+    cw[0] = 0;
+    for (int c = 0; c < C; c++) {
+        acc += w[c] / tot;
+        if (c + 1 < C) {
+            double v = floor(acc * 4294967296.0);
+            if (v > 4294967296.0) v = 4294967296.0;
+            cw[c + 1] = (uint64_t)v;
+        }
+    }
+    cw[C] = (uint64_t)1 << 32;
+    for (int c = 1; c <= C; c++)
+        if (cw[c] < cw[c - 1]) cw[c] = cw[c - 1];
+}
+
+/* Square root L (lower triangular, L L^T = cov) of component c and the box [blo, bhi] of whitened
+ * coordinates y = L^-1 (x - mu) that contains the image of the rectangle (its corners' extent). */
+static void pair_whiten(const orc_gmm2 *g, int c, const double lo[2], const double hi[2], double L[3],
+                        double blo[2], double bhi[2])
+{
+    const double *S = g->cov[c];
+    L[0] = sqrt(S[0]);
+    L[1] = S[1] / L[0];
+    L[2] = sqrt(S[2] - L[1] * L[1]);
+    blo[0] = blo[1] = INFINITY;
+    bhi[0] = bhi[1] = -INFINITY;
+    for (int k = 0; k < 4; k++) {
+        double x0 = (k & 1) ? hi[0] : lo[0], x1 = (k & 2) ? hi[1] : lo[1];
+        double y0 = (x0 - g->mu[c][0]) / L[0];
+        double y1 = (x1 - g->mu[c][1] - L[1] * y0) / L[2];
+        if (y0 < blo[0]) blo[0] = y0;
+        if (y0 > bhi[0]) bhi[0] = y0;
+        if (y1 < blo[1]) blo[1] = y1;
+        if (y1 > bhi[1]) bhi[1] = y1;
+    }
+}
+
+/* One draw of the pair for sample n: the component is the largest c with cw[c] <= a; then, for
+ * attempt t = 0, 1, ..., the Philox block 4 + t gives two words v_0, v_1, the whitened pair is
+ * y_j = Phi^-1(Phi(blo_j) + v_j (Phi(bhi_j) - Phi(blo_j))) (standard normals truncated to the box)
+ * and x = mu_c + L_c y; the first x inside the rectangle is kept (at most 1024 attempts; returns
+ * the attempt count, or -1).  The accepted x has density N(x | mu_c, cov_c) / Z_c on the rectangle. */
+int orc_pair_draw(const orc_gmm2 *g, const double lo[2], const double hi[2], uint32_t a, const uint32_t ctr0[3],
+                  const uint32_t key[2], double x[2], int *comp)
+{
+    uint64_t cw[ORC_GMM_MAX + 1];
+    weights_cum(g->w, g->C, cw);
+    int c = 0;
+    for (int j = 1; j < g->C; j++)
+        if (cw[j] <= (uint64_t)a) c = j;
+    *comp = c;
+    double L[3], blo[2], bhi[2];
+    pair_whiten(g, c, lo, hi, L, blo, bhi);
+    for (int t = 0; t < 1024; t++) {
+        uint32_t ctr[4] = {ctr0[0], ctr0[1], ctr0[2], 4u + (uint32_t)t}, w[4];
+        orc_philox4x32_10(ctr, key, w);
+        double y[2];
+        for (int j = 0; j < 2; j++) {
+            double P1 = norm_cdf(blo[j]), P2 = norm_cdf(bhi[j]);
+            y[j] = orc_norm_ppf(P1 + unit23(w[j]) * (P2 - P1));
+        }
+        x[0] = g->mu[c][0] + L[0] * y[0];
+        x[1] = g->mu[c][1] + L[1] * y[0] + L[2] * y[1];
+        if (x[0] >= lo[0] && x[0] <= hi[0] && x[1] >= lo[1] && x[1] <= hi[1]) return t + 1;
+    }
+    return -1;
+}
+
+/* Floors that keep every pair component usable by the sampler: sigma_j >= 1e-3 (hi_j - lo_j),
+ * |rho| <= 0.9, the mean inside the rectangle. */
+static void pair_floor(orc_gmm2 *g, int c, const double lo[2], const double hi[2])
+{
+    double *S = g->cov[c];
+    for (int j = 0; j < 2; j++) {
+        double smin = 1e-3 * (hi[j] - lo[j]);
+        if (S[2 * j] < smin * smin) S[2 * j] = smin * smin;
+        if (g->mu[c][j] < lo[j]) g->mu[c][j] = lo[j];
+        if (g->mu[c][j] > hi[j]) g->mu[c][j] = hi[j];
+    }
+    double lim = 0.9 * sqrt(S[0] * S[2]);
+    if (S[1] > lim) S[1] = lim;
+    if (S[1] < -lim) S[1] = -lim;
+}
+
+/*
+ * One EM step of the pair on the batch (points x_n = (u0_n, u1_n), sample weights w_n), the
+ * multivariate form of App. "Gaussian mixture model implementation" with the sample weight in the
+ * sums (R24): r_nc prop. to w_c N(x_n | mu_c, cov_c) (untruncated), S0_c = sum w_n r_nc,
+ * mu_c = sum w_n r_nc x_n / S0_c, cov_c = sum w_n r_nc (x_n - mu_c)(x_n - mu_c)^T / S0_c,
+ * w_c = S0_c / sum w_n; then the floors; a component with S0_c <= 1e-12 sum w keeps its
+ * parameters with weight 1e-3; weights renormalised.
+ */
+void orc_gmm2_em_step(const double *u0, const double *u1, const double *wn, long N, orc_gmm2 *g, const double lo[2],
+                      const double hi[2])
+{
+    double S0[ORC_GMM_MAX] = {0}, S1[ORC_GMM_MAX][2] = {{0}}, S2[ORC_GMM_MAX][3] = {{0}}, W = 0.0;
+    for (long n = 0; n < N; n++) {
+        double l[ORC_GMM_MAX], m = -INFINITY, tot = 0.0;
+        for (int c = 0; c < g->C; c++) {
+            const double *S = g->cov[c];
+            double det = S[0] * S[2] - S[1] * S[1];
+            double d0 = u0[n] - g->mu[c][0], d1 = u1[n] - g->mu[c][1];
+            double q = (S[2] * d0 * d0 - 2.0 * S[1] * d0 * d1 + S[0] * d1 * d1) / det;
+            l[c] = log(g->w[c]) - 0.5 * log(det) - 0.5 * q;
+            if (l[c] > m) m = l[c];
+        }
+        for (int c = 0; c < g->C; c++) {
+            l[c] = exp(l[c] - m);
+            tot += l[c];
+        }
+        W += wn[n];
+        for (int c = 0; c < g->C; c++) {
+            double q = wn[n] * l[c] / tot;
+            S0[c] += q;
+            S1[c][0] += q * u0[n];
+            S1[c][1] += q * u1[n];
+            S2[c][0] += q * u0[n] * u0[n];
+            S2[c][1] += q * u0[n] * u1[n];
+            S2[c][2] += q * u1[n] * u1[n];
+        }
+    }
+    double wsum = 0.0;
+    for (int c = 0; c < g->C; c++) {
+        if (S0[c] > 1e-12 * W) {
+            double m0 = S1[c][0] / S0[c], m1 = S1[c][1] / S0[c];
+            g->mu[c][0] = m0;
+            g->mu[c][1] = m1;
+            g->cov[c][0] = S2[c][0] / S0[c] - m0 * m0;
+            g->cov[c][1] = S2[c][1] / S0[c] - m0 * m1;
+            g->cov[c][2] = S2[c][2] / S0[c] - m1 * m1;
+            pair_floor(g, c, lo, hi);
+            g->w[c] = S0[c] / W;
+        } else {
+            g->w[c] = 1e-3;
+        }
+        wsum += g->w[c];
+    }
+    for (int c = 0; c < g->C; c++) g->w[c] /= wsum;
+}
+
+/* Mahalanobis distance of d under covariance S: sqrt(d^T S^-1 d). */
+static double mahalanobis(const double d[2], const double S[3])
+{
+    double det = S[0] * S[2] - S[1] * S[1];
+    return sqrt((S[2] * d[0] * d[0] - 2.0 * S[1] * d[0] * d[1] + S[0] * d[1] * d[1]) / det);
+}
+
+/* Online merge of the batch pair model into the current one (App. "Gaussian mixture model
+ * implementation"): the permutation matching batch component i to current component j with the
+ * least sum of sqrt((mu_j - mu_i)^T S_i^-1 (mu_j - mu_i)) + sqrt((mu_i - mu_j)^T S_j^-1 (mu_i - mu_j))
+ * (first such in lexicographic order), then mu = (N w_j mu_j + M w_i mu_i) / (N w_j + M w_i),
+ * S = (N w_j S_j + M w_i S_i) / (...) + (N w_j mu_j mu_j^T + M w_i mu_i mu_i^T) / (...) - mu mu^T,
+ * w = (N w_j + M w_i) / (N + M), then the floors; n <- N + M. */
+void orc_gmm2_merge(const orc_gmm2 *cur, const orc_gmm2 *bat, double M, const double lo[2], const double hi[2],
+                    orc_gmm2 *out)
+{
+    const int C = cur->C;
+    int perm[ORC_GMM_MAX], best[ORC_GMM_MAX];
+    for (int i = 0; i < C; i++) perm[i] = best[i] = i;
+    double best_cost = INFINITY;
+    for (;;) {
+        double cost = 0.0;
+        for (int a = 0; a < C; a++) {
+            int j = perm[a];
+            double d[2] = {cur->mu[j][0] - bat->mu[a][0], cur->mu[j][1] - bat->mu[a][1]};
+            cost += mahalanobis(d, bat->cov[a]) + mahalanobis(d, cur->cov[j]);
+        }
+        if (cost < best_cost) {
+            best_cost = cost;
+            for (int a = 0; a < C; a++) best[a] = perm[a];
+        }
+        int i = C - 2;
+        while (i >= 0 && perm[i] > perm[i + 1]) i--;
+        if (i < 0) break;
+        int j = C - 1;
+        while (perm[j] < perm[i]) j--;
+        int t = perm[i];
+        perm[i] = perm[j];
+        perm[j] = t;
+        for (int x = i + 1, y = C - 1; x < y; x++, y--) {
+            t = perm[x];
+            perm[x] = perm[y];
+            perm[y] = t;
+        }
+    }
+    const double N = cur->n;
+    out->C = C;
+    for (int a = 0; a < C; a++) {
+        int j = best[a];
+        double A = N * cur->w[j], B = M * bat->w[a];
+        double m0 = (A * cur->mu[j][0] + B * bat->mu[a][0]) / (A + B);
+        double m1 = (A * cur->mu[j][1] + B * bat->mu[a][1]) / (A + B);
+        out->mu[a][0] = m0;
+        out->mu[a][1] = m1;
+        out->cov[a][0] = (A * cur->cov[j][0] + B * bat->cov[a][0]) / (A + B) +
+                         (A * cur->mu[j][0] * cur->mu[j][0] + B * bat->mu[a][0] * bat->mu[a][0]) / (A + B) - m0 * m0;
+        out->cov[a][1] = (A * cur->cov[j][1] + B * bat->cov[a][1]) / (A + B) +
+                         (A * cur->mu[j][0] * cur->mu[j][1] + B * bat->mu[a][0] * bat->mu[a][1]) / (A + B) - m0 * m1;
+        out->cov[a][2] = (A * cur->cov[j][2] + B * bat->cov[a][2]) / (A + B) +
+                         (A * cur->mu[j][1] * cur->mu[j][1] + B * bat->mu[a][1] * bat->mu[a][1]) / (A + B) - m1 * m1;
+        out->w[a] = (A + B) / (N + M);
+        pair_floor(out, a, lo, hi);
+    }
+    out->n = N + M;
+}
+
+/* Initial pair model: C equal components with means on the rectangle's diagonal at the centres
+ * of C equal slices, standard deviations (hi_j - lo_j) / C, no correlation, trained on no samples. */
+void orc_gmm2_init(orc_gmm2 *g, int C, const double lo[2], const double hi[2])
+{
+    g->C = C;
+    for (int c = 0; c < C; c++) {
+        g->w[c] = 1.0 / C;
+        for (int j = 0; j < 2; j++) g->mu[c][j] = lo[j] + (c + 0.5) * (hi[j] - lo[j]) / C;
+        g->cov[c][0] = ((hi[0] - lo[0]) / C) * ((hi[0] - lo[0]) / C);
+        g->cov[c][1] = 0.0;
+        g->cov[c][2] = ((hi[1] - lo[1]) / C) * ((hi[1] - lo[1]) / C);
+    }
+    g->n = 0.0;
+}
+
+void orc_gmm2_update(orc_gmm2 *g, const double *u0, const double *u1, const double *wn, long N, int iters,
+                     const double lo[2], const double hi[2])
+{
+    orc_gmm2 bat = *g, out;
+    for (int it = 0; it < iters; it++) orc_gmm2_em_step(u0, u1, wn, N, &bat, lo, hi);
+    orc_gmm2_merge(g, &bat, (double)N, lo, hi, &out);
+    *g = out;
+}
+
 /* Rotated network-frame sky (R23): orthonormal (e1, e2, p) with p = pole / |pole|,
  * e1 = (z x p) / |z x p| (x when p is along z), e2 = p x e1. */
 void orc_sky_frame(const double pole[3], double e1[3], double e2[3], double p[3])
@@ -474,12 +798,6 @@ void orc_sky_frame(const double pole[3], double e1[3], double e2[3], double p[3]
     e2[2] = p[0] * e1[1] - p[1] * e1[0];
 }
 
-/* Uniform in (0, 1) from the top 23 bits of one 32-bit word. */
-static double unit23(uint32_t w)
-{
-    return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
-}
-
 /* Prior density of sampling variable d at u. */
 static double ln_prior(const orc_sampler *S, int d, double u)
 {
@@ -498,6 +816,8 @@ void orc_sample(const orc_sampler *S, uint64_t seed, uint32_t iter, uint32_t poi
                 double *theta, double *lnp_minus_lnps, uint8_t *bins, double *u_out)
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    double pair_lo[2] = {S->lo[0], S->lo[1]}, pair_hi[2] = {S->hi[0], S->hi[1]}, pair_Z[ORC_GMM_MAX];
+    if (S->pair) orc_gmm2_masses(S->pair_model, pair_lo, pair_hi, pair_Z);
     for (long s = 0; s < N; s++) {
         uint32_t n = (uint32_t)(n0 + s);
         uint32_t words[16];
@@ -506,11 +826,25 @@ void orc_sample(const orc_sampler *S, uint64_t seed, uint32_t iter, uint32_t poi
             orc_philox4x32_10(ctr, key, words + 4 * blk);
         }
         double lw = 0.0;
+        double pair_x[2] = {0.0, 0.0};
+        int pair_c = 0;
+        if (S->pair) {
+            /* the sky pair together (R26); its component uses word 0, its attempts Philox blocks 4.. */
+            uint32_t ctr0[3] = {n, iter, point};
+            if (orc_pair_draw(S->pair_model, pair_lo, pair_hi, words[0], ctr0, key, pair_x, &pair_c) < 0) {
+                pair_x[0] = 0.5 * (pair_lo[0] + pair_hi[0]);
+                pair_x[1] = 0.5 * (pair_lo[1] + pair_hi[1]);
+            }
+            lw += ln_prior(S, 0, pair_x[0]) + ln_prior(S, 1, pair_x[1]) - orc_gmm2_lnpdf_z(S->pair_model, pair_Z, pair_x);
+        }
         for (int d = 0; d < ORC_NDIM; d++) {
             double lo = S->lo[d], hi = S->hi[d], u;
             uint32_t a = words[2 * d], b = words[2 * d + 1];
             int bin = 255;
-            if (S->adaptive[d] && S->gmm[d]) {
+            if (S->pair && d < 2) {
+                u = pair_x[d];
+                bin = pair_c;
+            } else if (S->adaptive[d] && S->gmm[d]) {
                 /* mixture: component = largest c with cw[c] <= a; inside it, the truncated normal
                  * by inverting its CDF at Phi(a_c) + v (Phi(b_c) - Phi(a_c)) */
                 const orc_gmm1 *g = S->model + d;

@@ -238,6 +238,30 @@ ile_status ile_integrate(ile_ctx *ctx, const double *samples, const double *ln_p
  *   sigma = (hi - lo) / C, N = 0 (so the first merge keeps the batch mixture); or the mixtures of
  *   a resumed ile_adapt_result.
  */
+/*
+ * Correlated sampling of the sky pair (the same section: correlated sampling in a chosen subset of
+ * dimensions, with the multivariate EM, merge and rejection to the finite domain of App. "Gaussian
+ * mixture model implementation"): with gmm_pair = 1, sampling variables 0 and 1 (ra and sin dec,
+ * or the rotated frame's longitude and sin latitude) are drawn together from
+ *   p_s(x) = sum_c w_c N(x | mu_c, S_c) / Z_c  on the rectangle R = [lo0, hi0] x [lo1, hi1],
+ * each component a bivariate normal truncated to R, Z_c its mass in R (computed by quadrature of
+ * the conditional normal, so ln p_s is exact and the integral unbiased).
+ *   Sampling: the component is the largest c with cw[c] <= a (a = word 0 of the sample); then
+ *   attempt t = 0, 1, ... takes Philox block 4 + t of the sample's counter, two standard normals
+ *   y truncated to the box that holds L_c^-1 (R - mu_c) (L_c the Cholesky factor of S_c, inverse
+ *   CDF from the nearer tail) and x = mu_c + L_c y; the first x inside R is kept (1024 attempts at
+ *   most, else ILE_E_RANGE).  bins[0] = bins[1] = c.
+ *   Update, every iteration: gmm_em_iters EM steps on the iteration's pairs with r_nc prop. to
+ *   w_c N(x_n | mu_c, S_c) and weights w_n = exp(ln w_n - max): S0_c = sum w_n r_nc, mu_c, S_c
+ *   the weighted mean and covariance, w_c = S0_c / sum w_n; then sigma_j >= 1e-3 (hi_j - lo_j),
+ *   |rho| <= 0.9 and mu_c inside R.  The merge pairs batch and current components by the least
+ *   sum of sqrt(d^T S_i^-1 d) + sqrt(d^T S_j^-1 d) (d = mu_j - mu_i; first least permutation) and
+ *   combines them with N and M as for one dimension, S = (N w_j S_j + M w_i S_i) / (...) +
+ *   (N w_j mu_j mu_j^T + M w_i mu_i mu_i^T) / (...) - mu mu^T, followed by the same limits.
+ *   Start: C components with means on R's diagonal at the centres of C equal slices, standard
+ *   deviations (hi_j - lo_j) / C, no correlation, N = 0; or gmm_pair_* of a resumed result.
+ *   Requires bits 0 and 1 of adapt_mask and not of gmm_mask.
+ */
 typedef struct {
     uint64_t seed;
     uint32_t point_id;
@@ -249,8 +273,9 @@ typedef struct {
     int sky_frame;        /* 0: sky variables 0, 1 are (ra, sin dec); 1: rotated network frame */
     double sky_pole[3];   /* sky_frame 1: Earth-fixed vector of the frame's pole (e.g. r_L1 - r_H1) */
     unsigned gmm_mask;    /* bits of adapt_mask drawn from a Gaussian mixture; 0: histograms only */
-    int gmm_components;   /* gmm_mask != 0: components per mixture, 1 .. ILE_GMM_MAX */
-    int gmm_em_iters;     /* gmm_mask != 0: EM steps per iteration, 1 .. 100 */
+    int gmm_components;   /* gmm_mask != 0 or gmm_pair: components per mixture, 1 .. ILE_GMM_MAX */
+    int gmm_em_iters;     /* gmm_mask != 0 or gmm_pair: EM steps per iteration, 1 .. 100 */
+    int gmm_pair;         /* 1: sampling variables 0 and 1 (the sky pair) from one correlated mixture */
 } ile_adapt_cfg;
 
 #define ILE_ADAPT_LOG 64
@@ -265,6 +290,10 @@ typedef struct {
     int gmm_components[ILE_NDIM];        /* mixture dimensions: components; 0 otherwise */
     double gmm_w[ILE_NDIM][ILE_GMM_MAX], gmm_mu[ILE_NDIM][ILE_GMM_MAX], gmm_sigma[ILE_NDIM][ILE_GMM_MAX];
     double gmm_n[ILE_NDIM];              /* samples each mixture has been trained on */
+    int gmm_pair_components;             /* the sky pair's correlated mixture (gmm_pair): components */
+    double gmm_pair_w[ILE_GMM_MAX], gmm_pair_mu[ILE_GMM_MAX][2];
+    double gmm_pair_cov[ILE_GMM_MAX][3]; /* {S00, S01, S11} of each component */
+    double gmm_pair_n;
 } ile_adapt_result;
 
 /* Set up the sampler on the current point (after ile_set_data).  resume = NULL starts from uniform

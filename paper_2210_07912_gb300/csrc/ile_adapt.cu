@@ -73,11 +73,19 @@ struct SamplerTables {
     uint32_t cdf[ND][NB + 1];  // low 32 bits; cdf[100] = 2^32 is never compared against
     float lnps[ND][NB];
     IleGmmTab gmm[ND];
+    IleGmm2Tab pair;
 };
 
 __device__ __forceinline__ void load_tables(SamplerTables &t, const uint64_t *__restrict__ cdf,
                                             const float *__restrict__ lnps_tab, const IleGmmTab *__restrict__ gmm,
-                                            unsigned gmm_mask) {
+                                            unsigned gmm_mask, const IleGmm2Tab *__restrict__ pair = nullptr) {
+    if (pair) {
+        constexpr int W2 = sizeof(IleGmm2Tab) / 4;
+        static_assert(sizeof(IleGmm2Tab) % 4 == 0, "table copied as words");
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(pair);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&t.pair);
+        for (int i = threadIdx.x; i < W2; i += blockDim.x) dst[i] = src[i];
+    }
     for (int i = threadIdx.x; i < ND * (NB + 1); i += blockDim.x) {
         const int d = i / (NB + 1), b = i % (NB + 1);
         t.cdf[d][b] = (uint32_t)cdf[i];
@@ -121,11 +129,61 @@ __device__ __forceinline__ float gmm_draw(const IleGmmTab &g, float lo, float hi
     return u;
 }
 
+// z from a standard normal truncated to the box axis with Phi(lo) = p1, Phi(-hi) = q2, mass dm, by
+// inverting its CDF at p1 + v dm from the nearer tail (as gmm_draw).
+__device__ __forceinline__ float trunc_normal(float p1, float q2, float dm, float v) {
+    const float p = p1 + v * dm;
+    return p <= 0.5f ? normcdfinvf(p) : -normcdfinvf(q2 + (1.f - v) * dm);
+}
+
+// One draw of the sky pair (variables 0, 1) from its correlated mixture: the component is the
+// largest c with cw[c] <= a; then attempt t = 0, 1, ... takes Philox block 4 + t of the sample's
+// counter, two truncated standard normals y on the component's whitened box and x = mu + L y, and
+// keeps the first x inside the rectangle (so the kept x follows the component's normal truncated
+// to it).  Returns false after 1024 attempts without one.  ln p_s of the kept x: log-sum-exp of
+// coef_c - (x - mu_c)^T cov_c^-1 (x - mu_c) / 2.
+__device__ bool pair_draw(const IleSamplerParams &sp, const IleGmm2Tab &g, uint32_t a, uint32_t n, uint32_t iter,
+                          float &x0, float &x1, int &comp, float &lnps) {
+    int c = 0;
+    for (int j = 1; j < g.C; j++)
+        if (g.cw[j] <= (uint64_t)a) c = j;
+    comp = c;
+    const float lo0 = sp.lo[0], hi0 = sp.hi[0], lo1 = sp.lo[1], hi1 = sp.hi[1];
+    bool ok = false;
+    for (uint32_t t = 0; t < 1024u && !ok; t++) {
+        uint32_t w[4];
+        philox4x32_10(n, iter, sp.point, 4u + t, sp.key0, sp.key1, w);
+        const float y0 = trunc_normal(g.p1[c][0], g.q2[c][0], g.dm[c][0], unit23(w[0]));
+        const float y1 = trunc_normal(g.p1[c][1], g.q2[c][1], g.dm[c][1], unit23(w[1]));
+        x0 = g.mu[c][0] + g.L[c][0] * y0;
+        x1 = g.mu[c][1] + g.L[c][1] * y0 + g.L[c][2] * y1;
+        ok = x0 >= lo0 && x0 <= hi0 && x1 >= lo1 && x1 <= hi1;
+    }
+    if (!ok) {
+        x0 = fminf(fmaxf(x0, lo0), hi0);
+        x1 = fminf(fmaxf(x1, lo1), hi1);
+    }
+    float l[ILE_GMM_MAX], m = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < ILE_GMM_MAX; j++) {
+        const float d0 = x0 - g.mu[j][0], d1 = x1 - g.mu[j][1];
+        const float q = g.icov[j][0] * d0 * d0 + 2.f * g.icov[j][1] * d0 * d1 + g.icov[j][2] * d1 * d1;
+        l[j] = j < g.C ? g.coef[j] - 0.5f * q : -INFINITY;
+        m = fmaxf(m, l[j]);
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int j = 0; j < ILE_GMM_MAX; j++) sum += j < g.C ? expf(l[j] - m) : 0.f;
+    lnps = m + logf(sum);
+    return ok;
+}
+
 // Sample n of N (one point): theta [7][N], ln p - ln p_s, bins [7][N].
 __device__ __forceinline__ void sample_one(const IleSamplerParams &sp, const SamplerTables &tb, uint32_t iter,
                                            int64_t n, int64_t N, double *__restrict__ theta,
                                            double *__restrict__ lnw_prior, uint8_t *__restrict__ bins,
-                                           float *__restrict__ u_gmm) {
+                                           float *__restrict__ u_gmm, float *__restrict__ u_pair = nullptr,
+                                           unsigned *flags = nullptr) {
     const uint32_t(&cdf_s)[ND][NB + 1] = tb.cdf;
     const float(&lnps_s)[ND][NB] = tb.lnps;
     uint32_t wds[16];
@@ -133,13 +191,27 @@ __device__ __forceinline__ void sample_one(const IleSamplerParams &sp, const Sam
     for (uint32_t blk = 0; blk < 4; blk++)
         philox4x32_10((uint32_t)n, iter, sp.point, blk, sp.key0, sp.key1, wds + 4 * blk);
     float lw = 0.f;
+    float px0 = 0.f, px1 = 0.f;
+    int pc = 0;
+    if (sp.gmm_pair) {
+        // the sky pair together from its correlated mixture; its component uses word 0
+        float lnps;
+        if (!pair_draw(sp, tb.pair, wds[0], (uint32_t)n, iter, px0, px1, pc, lnps) && flags)
+            atomicOr(flags, ILE_FLAG_RANGE);
+        lw += -logf(sp.hi[0] - sp.lo[0]) - logf(sp.hi[1] - sp.lo[1]) - lnps;
+        u_pair[n] = px0;
+        u_pair[N + n] = px1;
+    }
 #pragma unroll
     for (int d = 0; d < ND; d++) {
         const float lo = sp.lo[d], hi = sp.hi[d];
         const uint32_t a = wds[2 * d], bw = wds[2 * d + 1];
         float u;
         int bin = 255;
-        if (sp.gmm_mask & (1u << d)) {
+        if (sp.gmm_pair && d < 2) {
+            u = d == 0 ? px0 : px1;
+            bin = pc;
+        } else if (sp.gmm_mask & (1u << d)) {
             float lnps;
             u = gmm_draw(tb.gmm[d], lo, hi, a, bw, bin, lnps);
             const float lnp = d == 5 ? logf(3.f * u * u / (hi * hi * hi - lo * lo * lo)) : -logf(hi - lo);
@@ -188,15 +260,17 @@ __device__ __forceinline__ void sample_one(const IleSamplerParams &sp, const Sam
 __global__ void __launch_bounds__(256) sample_kernel(IleSamplerParams sp, const uint64_t *__restrict__ cdf,
                                                      const float *__restrict__ lnps_tab,
                                                      const IleGmmTab *__restrict__ gmm_tab,
+                                                     const IleGmm2Tab *__restrict__ pair_tab,
                                                      const int *__restrict__ iter_dev, int64_t N,
                                                      double *__restrict__ theta, double *__restrict__ lnw_prior,
-                                                     uint8_t *__restrict__ bins, float *__restrict__ u_gmm) {
+                                                     uint8_t *__restrict__ bins, float *__restrict__ u_gmm,
+                                                     float *__restrict__ u_pair, unsigned *flags) {
     __shared__ SamplerTables tb;
-    load_tables(tb, cdf, lnps_tab, gmm_tab, sp.gmm_mask);
+    load_tables(tb, cdf, lnps_tab, gmm_tab, sp.gmm_mask, sp.gmm_pair ? pair_tab : nullptr);
     __syncthreads();
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    sample_one(sp, tb, (uint32_t)(*iter_dev), n, N, theta, lnw_prior, bins, u_gmm);
+    sample_one(sp, tb, (uint32_t)(*iter_dev), n, N, theta, lnw_prior, bins, u_gmm, u_pair, flags);
 }
 
 // Batched: block b draws samples start .. start + 255 of point blk[b].x (blk[b].y = start).
@@ -444,12 +518,14 @@ cudaError_t ile_launch_lnps(const IleSamplerParams &sp, const uint64_t *cdf, flo
 }
 
 cudaError_t ile_launch_sample(const IleSamplerParams &sp, const uint64_t *cdf, const float *lnps_tab,
-                              const IleGmmTab *gmm_tab, const int *iter_dev, int64_t N, double *theta,
-                              double *lnw_prior, uint8_t *bins, float *u_gmm, cudaStream_t st) {
+                              const IleGmmTab *gmm_tab, const IleGmm2Tab *pair_tab, const int *iter_dev, int64_t N,
+                              double *theta, double *lnw_prior, uint8_t *bins, float *u_gmm, float *u_pair,
+                              unsigned *flags, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     if (sp.gmm_mask && (!gmm_tab || !u_gmm)) return cudaErrorInvalidValue;
-    sample_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(sp, cdf, lnps_tab, gmm_tab, iter_dev, N, theta,
-                                                               lnw_prior, bins, u_gmm);
+    if (sp.gmm_pair && (!pair_tab || !u_pair)) return cudaErrorInvalidValue;
+    sample_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(sp, cdf, lnps_tab, gmm_tab, pair_tab, iter_dev, N,
+                                                               theta, lnw_prior, bins, u_gmm, u_pair, flags);
     return cudaGetLastError();
 }
 

@@ -67,6 +67,12 @@ struct ile_ctx {
     IleGmmTab *g_tab = nullptr;
     double *g_part = nullptr;
     float *a_u = nullptr;  // [n mixture dims][N]
+    // the sky pair's correlated mixture (ile_gmm.cu)
+    IleGmm2 *g2_cur = nullptr, *g2_bat = nullptr;
+    IleGmm2Tab *g2_tab = nullptr;
+    double *g2_part = nullptr;
+    float *a_upair = nullptr;  // [2][N]
+    int64_t a_upair_cap = 0;
     size_t a_u_bytes = 0;
     // adjoint scratch (ile_adjoint.cu)
     float *pig = nullptr;      // [N][N_t] g_n * pi(n, j)
@@ -540,7 +546,8 @@ ile_status ile_destroy(ile_ctx *ctx) {
                     ctx->a_bins,       ctx->pig,        ctx->gq_part,   ctx->guv_part,  ctx->g_in,
                     ctx->g_out,        ctx->g_cur,      ctx->g_bat,     ctx->g_tab,     ctx->g_part,
                     ctx->a_u,          ctx->Qadj[0],    ctx->Qadj[1],   ctx->Q64,       ctx->U64,
-                    ctx->V64,          ctx->loud};
+                    ctx->V64,          ctx->loud,       ctx->g2_cur,    ctx->g2_bat,    ctx->g2_tab,
+                    ctx->g2_part,      ctx->a_upair};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (auto &v : ctx->ev)
@@ -629,6 +636,13 @@ void ile_fill_result(const double pooled[4], const double *ilog, int n_iter, ile
         out->gmm_components[d] = 0;
         out->gmm_n[d] = 0.0;
         for (int c = 0; c < ILE_GMM_MAX; c++) out->gmm_w[d][c] = out->gmm_mu[d][c] = out->gmm_sigma[d][c] = 0.0;
+    }
+    out->gmm_pair_components = 0;
+    out->gmm_pair_n = 0.0;
+    for (int c = 0; c < ILE_GMM_MAX; c++) {
+        out->gmm_pair_w[c] = 0.0;
+        for (int j = 0; j < 2; j++) out->gmm_pair_mu[c][j] = 0.0;
+        for (int j = 0; j < 3; j++) out->gmm_pair_cov[c][j] = 0.0;
     }
     out->max_lnw = pooled[0];
     out->s1 = pooled[1];
@@ -1026,6 +1040,17 @@ static ile_status adapt_alloc(ile_ctx *ctx, int64_t N) {
     if (!ctx->g_bat) CK(ctx_malloc(ctx, (void **)&ctx->g_bat, sizeof(IleGmm) * ILE_NDIM));
     if (!ctx->g_tab) CK(ctx_malloc(ctx, (void **)&ctx->g_tab, sizeof(IleGmmTab) * ILE_NDIM));
     if (!ctx->g_part) CK(ctx_malloc(ctx, (void **)&ctx->g_part, sizeof(double) * ile_gmm_part_doubles()));
+    if (ctx->sp.gmm_pair) {
+        if (!ctx->g2_cur) CK(ctx_malloc(ctx, (void **)&ctx->g2_cur, sizeof(IleGmm2)));
+        if (!ctx->g2_bat) CK(ctx_malloc(ctx, (void **)&ctx->g2_bat, sizeof(IleGmm2)));
+        if (!ctx->g2_tab) CK(ctx_malloc(ctx, (void **)&ctx->g2_tab, sizeof(IleGmm2Tab)));
+        if (!ctx->g2_part) CK(ctx_malloc(ctx, (void **)&ctx->g2_part, sizeof(double) * ile_gmm2_part_doubles()));
+        if (N > ctx->a_upair_cap) {
+            ctx->a_upair_cap = 0;
+            CK(grow(ctx, &ctx->a_upair, sizeof(float) * 2 * (size_t)N));
+            ctx->a_upair_cap = N;
+        }
+    }
     if (N > ctx->a_cap) {
         ctx->a_cap = 0;
         CK(grow(ctx, &ctx->a_lnwp, sizeof(double) * (size_t)N));
@@ -1092,8 +1117,36 @@ ile_status ile_adapt_init(ile_ctx *ctx, const ile_adapt_cfg *cfg, const ile_adap
             gm[d].n = resume->gmm_n[d];
         }
     }
+    IleGmm2 g2{};
+    if (cfg->gmm_pair) {
+        // the sky pair drawn together: both variables adaptive and not in the separable mixtures
+        if (cfg->gmm_pair != 1 || (cfg->adapt_mask & 3u) != 3u || (cfg->gmm_mask & 3u)) return ILE_E_ARG;
+        if (cfg->gmm_components < 1 || cfg->gmm_components > ILE_GMM_MAX) return ILE_E_ARG;
+        if (cfg->gmm_em_iters < 1 || cfg->gmm_em_iters > 100) return ILE_E_ARG;
+        const double plo[2] = {cfg->lo[0], cfg->lo[1]}, phi[2] = {cfg->hi[0], cfg->hi[1]};
+        ile_gmm2_init(g2, cfg->gmm_components, plo, phi);
+        if (resume) {
+            if (resume->gmm_pair_components != cfg->gmm_components || !(resume->gmm_pair_n >= 0.0)) return ILE_E_ARG;
+            for (int c = 0; c < cfg->gmm_components; c++) {
+                const double w = resume->gmm_pair_w[c], *mu = resume->gmm_pair_mu[c], *cv = resume->gmm_pair_cov[c];
+                const double det = cv[0] * cv[2] - cv[1] * cv[1];
+                if (!(w > 0.0) || !isfinite(w) || !(cv[0] > 0.0) || !(cv[2] > 0.0) || !(det > 0.0) ||
+                    !isfinite(det))
+                    return ILE_E_ARG;
+                for (int j = 0; j < 2; j++)
+                    if (!(mu[j] >= plo[j]) || !(mu[j] <= phi[j])) return ILE_E_ARG;
+                g2.w[c] = w;
+                for (int j = 0; j < 2; j++) g2.mu[c][j] = mu[j];
+                for (int j = 0; j < 3; j++) g2.cov[c][j] = cv[j];
+            }
+            g2.n = resume->gmm_pair_n;
+        }
+    } else if (cfg->gmm_pair != 0) {
+        return ILE_E_ARG;
+    }
     DeviceGuard g(ctx->device);
     ctx->sp.gmm_mask = cfg->gmm_mask;  // sizes the mixture buffers in adapt_alloc
+    ctx->sp.gmm_pair = cfg->gmm_pair;
     ile_status st = adapt_alloc(ctx, cfg->n_per_iter);
     if (st != ILE_OK) return st;
     IleSamplerParams sp{};
@@ -1109,16 +1162,22 @@ ile_status ile_adapt_init(ile_ctx *ctx, const ile_adapt_cfg *cfg, const ile_adap
     sp.sky = cfg->sky_frame;
     if (sp.sky && !ile_sky_frame(cfg->sky_pole, sp.rot)) return ILE_E_ARG;
     sp.gmm_mask = cfg->gmm_mask;
+    sp.gmm_pair = cfg->gmm_pair;
     ctx->sp = sp;
     ctx->eps = cfg->eps;
     ctx->adapt_N = cfg->n_per_iter;
-    ctx->gmm_iters = cfg->gmm_mask ? cfg->gmm_em_iters : 0;
+    ctx->gmm_iters = (cfg->gmm_mask || cfg->gmm_pair) ? cfg->gmm_em_iters : 0;
     CK(ile_launch_sampler_reset(sp, ctx->a_cdf, ctx->a_lnps, ctx->a_pooled, ctx->a_iter, 0, ctx->stream));
     if (sp.gmm_mask) {
         CK(cudaMemcpyAsync(ctx->g_cur, gm, sizeof gm, cudaMemcpyHostToDevice, ctx->stream));
         CK(ile_launch_gmm_table(sp.gmm_mask, ctx->g_cur, ctx->g_tab, ctx->stream));
         // gm is a stack array: the copy must finish before it goes out of scope
         CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (sp.gmm_pair) {
+        CK(cudaMemcpyAsync(ctx->g2_cur, &g2, sizeof g2, cudaMemcpyHostToDevice, ctx->stream));
+        CK(ile_launch_gmm2_table(ctx->g2_cur, ctx->g2_tab, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));  // g2 is a stack object
     }
     if (resume) {
         if (resume->n_iter < 0) return ILE_E_ARG;
@@ -1156,8 +1215,9 @@ ile_status ile_adapt_step(ile_ctx *ctx, int n_iter) {
     for (int it = 0; it < n_iter; it++) {
         {
             StageScope t(ctx, 0);
-            CK(ile_launch_sample(ctx->sp, ctx->a_cdf, ctx->a_lnps, ctx->g_tab, ctx->a_iter, N, ctx->theta,
-                                 ctx->a_lnwp, ctx->a_bins, ctx->a_u, ctx->stream));
+            CK(ile_launch_sample(ctx->sp, ctx->a_cdf, ctx->a_lnps, ctx->g_tab, ctx->g2_tab, ctx->a_iter, N,
+                                 ctx->theta, ctx->a_lnwp, ctx->a_bins, ctx->a_u, ctx->a_upair, ctx->flags,
+                                 ctx->stream));
         }
         st = run_eval(ctx, ctx->theta, N, ctx->a_lnl, 0);
         if (st != ILE_OK) return st;
@@ -1176,6 +1236,11 @@ ile_status ile_adapt_step(ile_ctx *ctx, int n_iter) {
             CK(ile_launch_gmm_update(ctx->sp.gmm_mask, ctx->a_u, ctx->a_lnl, ctx->a_lnwp, ctx->a_iter_res, N,
                                      ctx->gmm_iters, ctx->g_cur, ctx->g_bat, ctx->g_tab, ctx->g_part, ctx->stream));
         }
+        if (ctx->sp.gmm_pair) {
+            StageScope t(ctx, 4, 2 * ctx->gmm_iters);
+            CK(ile_launch_gmm2_update(ctx->a_upair, ctx->a_lnl, ctx->a_lnwp, ctx->a_iter_res, N, ctx->gmm_iters,
+                                      ctx->g2_cur, ctx->g2_bat, ctx->g2_tab, ctx->g2_part, ctx->stream));
+        }
     }
     return ILE_OK;
 }
@@ -1193,8 +1258,19 @@ ile_status ile_adapt_get(ile_ctx *ctx, ile_adapt_result *out) {
     CK(cudaMemcpyAsync(out->hist, ctx->a_hist, sizeof(out->hist), cudaMemcpyDeviceToHost, ctx->stream));
     IleGmm gm[ILE_NDIM] = {};
     if (ctx->sp.gmm_mask) CK(cudaMemcpyAsync(gm, ctx->g_cur, sizeof gm, cudaMemcpyDeviceToHost, ctx->stream));
+    IleGmm2 g2{};
+    if (ctx->sp.gmm_pair) CK(cudaMemcpyAsync(&g2, ctx->g2_cur, sizeof g2, cudaMemcpyDeviceToHost, ctx->stream));
     ile_status st = read_flags(ctx);
     ile_fill_result(pooled, ilog, it, out);
+    if (ctx->sp.gmm_pair) {
+        out->gmm_pair_components = g2.C;
+        for (int c = 0; c < g2.C; c++) {
+            out->gmm_pair_w[c] = g2.w[c];
+            for (int j = 0; j < 2; j++) out->gmm_pair_mu[c][j] = g2.mu[c][j];
+            for (int j = 0; j < 3; j++) out->gmm_pair_cov[c][j] = g2.cov[c][j];
+        }
+        out->gmm_pair_n = g2.n;
+    }
     for (int d = 0; d < ILE_NDIM; d++) {
         if (!(ctx->sp.gmm_mask & (1u << d))) continue;
         out->gmm_components[d] = gm[d].C;

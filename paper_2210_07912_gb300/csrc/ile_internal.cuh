@@ -156,6 +156,7 @@ struct IleSamplerParams {
     float rot[9];                      // rotated frame: columns e1, e2, p (Earth-fixed), row-major
     float gmst;
     unsigned gmm_mask;                 // bits of adapt_mask drawn from a Gaussian mixture (ile_gmm.cu)
+    int gmm_pair;                      // 1: variables 0 and 1 drawn together from the correlated pair mixture
 };
 
 // One dimension's Gaussian mixture in FP64 (the adapted state) and its sampler form in FP32.
@@ -172,6 +173,28 @@ struct IleGmmTab {
     float q2[ILE_GMM_MAX];    // Phi(-z_hi): mass above the range
     float dm[ILE_GMM_MAX];    // Z = Phi(z_hi) - Phi(z_lo): mass inside
     float coef[ILE_GMM_MAX];  // ln(w_c / (sqrt(2 pi) sigma_c Z_c))
+    int C;
+};
+
+// The sky pair's correlated mixture in FP64 (the adapted state): component c has weight w[c], mean
+// mu[c] and covariance cov[c] = {S00, S01, S11}, a bivariate normal truncated to the rectangle
+// [lo0, hi0] x [lo1, hi1] of sampling variables 0 and 1.
+struct IleGmm2 {
+    int C;
+    double lo[2], hi[2];
+    double w[ILE_GMM_MAX], mu[ILE_GMM_MAX][2], cov[ILE_GMM_MAX][3];
+    double n;
+};
+// Its sampler form in FP32: integer weight table; per component the mean, the Cholesky factor
+// L = {l00, l10, l11} of the covariance, per whitened axis j the box [blo, bhi] that holds the
+// image of the rectangle as Phi(blo) (p1), Phi(-bhi) (q2) and Phi(bhi) - Phi(blo) (dm), the inverse
+// covariance {i00, i01, i11} and ln(w_c / (2 pi sqrt(det) Z_c)) with Z_c the component's mass in
+// the rectangle.
+struct IleGmm2Tab {
+    uint64_t cw[ILE_GMM_MAX + 1];
+    float mu[ILE_GMM_MAX][2], L[ILE_GMM_MAX][3], icov[ILE_GMM_MAX][3];
+    float p1[ILE_GMM_MAX][2], q2[ILE_GMM_MAX][2], dm[ILE_GMM_MAX][2];
+    float coef[ILE_GMM_MAX];
     int C;
 };
 
@@ -473,9 +496,22 @@ cudaError_t ile_launch_sampler_reset(const IleSamplerParams &sp, uint64_t *cdf, 
 cudaError_t ile_launch_lnps(const IleSamplerParams &sp, const uint64_t *cdf, float *lnps_tab, cudaStream_t st);
 // gmm_tab: [7] sampler tables (used for the dimensions in sp.gmm_mask; may be NULL when it is 0);
 // u_gmm: [n_gmm][N] sampling variables of the mixture dimensions, in ascending dimension order
+// pair_tab / u_pair: the sky pair's table and the sampling variables of the pair [2][N] (used when
+// sp.gmm_pair; may be NULL otherwise); a pair draw that finds no point of the rectangle in 1024
+// attempts sets ILE_FLAG_RANGE in *flags
 cudaError_t ile_launch_sample(const IleSamplerParams &sp, const uint64_t *cdf, const float *lnps_tab,
-                              const IleGmmTab *gmm_tab, const int *iter_dev, int64_t N, double *theta,
-                              double *lnw_prior, uint8_t *bins, float *u_gmm, cudaStream_t st);
+                              const IleGmmTab *gmm_tab, const IleGmm2Tab *pair_tab, const int *iter_dev, int64_t N,
+                              double *theta, double *lnw_prior, uint8_t *bins, float *u_gmm, float *u_pair,
+                              unsigned *flags, cudaStream_t st);
+// the sky pair's mixture (ile_gmm.cu): table from cur; em_iters EM steps and the merge of the
+// iteration's pair samples u_pair [2][N] (part: ile_gmm2_part_doubles() doubles)
+size_t ile_gmm2_part_doubles();
+cudaError_t ile_launch_gmm2_table(const IleGmm2 *cur, IleGmm2Tab *tab, cudaStream_t st);
+cudaError_t ile_launch_gmm2_update(const float *u_pair, const double *lnL, const double *lnw_prior,
+                                   const double *iter_res, int64_t N, int em_iters, IleGmm2 *cur, IleGmm2 *bat,
+                                   IleGmm2Tab *tab, double *part, cudaStream_t st);
+// the initial pair model (host; ile_gmm.cu): C components on the rectangle's diagonal
+void ile_gmm2_init(IleGmm2 &g, int C, const double lo[2], const double hi[2]);
 // Bounded-wait check (ile_selftest.cu): one block waits on an mbarrier phase nothing completes, for
 // about timeout_s, with the kernels' bounded sleeping wait; it then sets ILE_FLAG_TIMEOUT.
 cudaError_t ile_launch_wait_check(unsigned *flags, double timeout_s, cudaStream_t st);

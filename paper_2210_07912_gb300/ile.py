@@ -32,7 +32,7 @@ class AdaptCfg(ctypes.Structure):
                 ("n_iter", ctypes.c_int), ("adapt_mask", ctypes.c_uint), ("eps", ctypes.c_double),
                 ("lo", ctypes.c_double * NDIM), ("hi", ctypes.c_double * NDIM), ("sky_frame", ctypes.c_int),
                 ("sky_pole", ctypes.c_double * 3), ("gmm_mask", ctypes.c_uint), ("gmm_components", ctypes.c_int),
-                ("gmm_em_iters", ctypes.c_int)]
+                ("gmm_em_iters", ctypes.c_int), ("gmm_pair", ctypes.c_int)]
 
 
 class AdaptResult(ctypes.Structure):
@@ -43,7 +43,9 @@ class AdaptResult(ctypes.Structure):
                 ("cdf", (ctypes.c_uint64 * (NBINS + 1)) * NDIM), ("hist", (ctypes.c_double * NBINS) * NDIM),
                 ("gmm_components", ctypes.c_int * NDIM), ("gmm_w", (ctypes.c_double * GMM_MAX) * NDIM),
                 ("gmm_mu", (ctypes.c_double * GMM_MAX) * NDIM), ("gmm_sigma", (ctypes.c_double * GMM_MAX) * NDIM),
-                ("gmm_n", ctypes.c_double * NDIM)]
+                ("gmm_n", ctypes.c_double * NDIM), ("gmm_pair_components", ctypes.c_int),
+                ("gmm_pair_w", ctypes.c_double * GMM_MAX), ("gmm_pair_mu", (ctypes.c_double * 2) * GMM_MAX),
+                ("gmm_pair_cov", (ctypes.c_double * 3) * GMM_MAX), ("gmm_pair_n", ctypes.c_double)]
 
 
 class PointDesc(ctypes.Structure):
@@ -76,18 +78,20 @@ def default_ranges(fs: float = 4096.0, tc_max: float | None = None, d_min: float
 
 def make_adapt_cfg(seed: int, n_per_iter: int, n_iter: int = 1, adapt_mask: int = 0b11, eps: float = 0.1,
                    point_id: int = 0, lo=None, hi=None, sky_pole=None, gmm_mask: int = 0, gmm_components: int = 3,
-                   gmm_em_iters: int = 8) -> AdaptCfg:
+                   gmm_em_iters: int = 8, gmm_pair: bool = False) -> AdaptCfg:
     """sky_pole: Earth-fixed pole vector of the rotated network sky frame (e.g. r_L1 - r_H1); then
     sampling variables 0, 1 are (phi', sin lat') in that frame.  None: (ra, sin dec).
     gmm_mask: adaptive dimensions drawn from a truncated Gaussian mixture of gmm_components
-    components, refit with gmm_em_iters EM steps per iteration."""
+    components, refit with gmm_em_iters EM steps per iteration.
+    gmm_pair: sampling variables 0 and 1 drawn together from one correlated (bivariate) mixture."""
     dlo, dhi = default_ranges()
     lo = dlo if lo is None else lo
     hi = dhi if hi is None else hi
     pole = (0.0, 0.0, 0.0) if sky_pole is None else tuple(float(x) for x in sky_pole)
     return AdaptCfg(seed, point_id, n_per_iter, n_iter, adapt_mask, eps, (ctypes.c_double * NDIM)(*lo),
                     (ctypes.c_double * NDIM)(*hi), 0 if sky_pole is None else 1, (ctypes.c_double * 3)(*pole),
-                    gmm_mask, gmm_components if gmm_mask else 0, gmm_em_iters if gmm_mask else 0)
+                    gmm_mask, gmm_components if (gmm_mask or gmm_pair) else 0,
+                    gmm_em_iters if (gmm_mask or gmm_pair) else 0, 1 if gmm_pair else 0)
 
 
 def result_dict(r: AdaptResult) -> dict:
@@ -98,7 +102,12 @@ def result_dict(r: AdaptResult) -> dict:
                 gmm=[None if r.gmm_components[d] == 0 else
                      dict(w=np.array(r.gmm_w[d][:r.gmm_components[d]]), mu=np.array(r.gmm_mu[d][:r.gmm_components[d]]),
                           sigma=np.array(r.gmm_sigma[d][:r.gmm_components[d]]), n=r.gmm_n[d])
-                     for d in range(NDIM)])
+                     for d in range(NDIM)],
+                pair=None if r.gmm_pair_components == 0 else
+                dict(w=np.array(r.gmm_pair_w[:r.gmm_pair_components]),
+                     mu=np.array([[r.gmm_pair_mu[c][0], r.gmm_pair_mu[c][1]] for c in range(r.gmm_pair_components)]),
+                     cov=np.array([[r.gmm_pair_cov[c][j] for j in range(3)] for c in range(r.gmm_pair_components)]),
+                     n=r.gmm_pair_n))
 
 
 class IleError(RuntimeError):

@@ -4,175 +4,207 @@
 // The data term of Eq. (eq:loglikelihood) at window bin j is
 //   D(n, j) = sum_k [ (1 - w_k) G_k(n, i_k + j) + w_k G_k(n, i_k + j + 1) ],
 //   G_k(n, t) = sum_r C_k(r, n) Qp_k(r, t)      (r over Re and Im rows: Re(conj(c) Q)),
-// where i_k(n) + w_k(n) is the sample's fractional window start in detector k.  One CTA takes a
-// tile of NS samples; for every detector it sweeps the columns the tile needs in chunks of 64:
-// an FP32 register-blocked GEMM (each thread a (NS/16) x 4 micro-tile) forms G for the chunk in
-// shared memory, and a gather adds each sample's interpolated, shifted row into its window
-// accumulator D (shared memory, one row of N_t per sample).  After the last detector one warp
-// per sample takes the log-sum-exp over the window (S5) and assembles
+// where i_k(n) + w_k(n) is the sample's fractional window start in detector k.  One CTA of 256
+// threads takes 64 delay-sorted samples, four threads per sample, each thread 16 bins of every
+// 64-bin chunk of the window held in registers.  Per (chunk, detector) the tile's columns are
+// covered by blocks of 80 (overlapping by the lerp partner): an FP32 register-blocked GEMM (a
+// 4-sample x 5-column micro-tile per thread, K = 2M) forms G for the block in shared memory and
+// every thread adds the interpolation of its own shifted columns.  After the last detector of a
+// chunk each thread folds its bins into a running log-sum-exp; the four threads of a sample merge
+// theirs and assemble
 //   lnL_t = max_j D + ln sum_j exp(D - max) - A - ln N_t
-// in FP64.
+// in FP64.  ~77 KB of shared memory per CTA: two CTAs (16 warps) per SM.
 #include "ile_internal.cuh"
 
 namespace {
 
-constexpr int TCOL = 64;                   // columns per chunk
+constexpr int NS = 64;                     // samples per CTA (4 threads each)
+constexpr int NT = 256;
+constexpr int JW = 64;                     // window bins per chunk
+constexpr int JG = 16;                     // bins per thread per chunk
+constexpr int WC = 80;                     // columns of one GEMM block (16 column groups x 5)
+constexpr int WSTEP = WC - 1;              // blocks overlap by one column: the lerp partner
 constexpr int RMAX = 2 * ILE_MAX_MODES;    // real rows of the contraction
+constexpr int GROW = WC + 4;               // G row: WC columns, each 32-column segment skewed by one bank
 
-template <int NS>
-__global__ void __launch_bounds__(256) ile_plain_kernel(const __grid_constant__ PointParams pp,
-                                                        const float *__restrict__ Qp, IleScratch s,
-                                                        const int *__restrict__ perm, int64_t N,
-                                                        double *__restrict__ out, int full_grid, LoudList loud) {
-    constexpr int RS = NS / 16;  // samples per thread in the micro-tile
-    extern __shared__ float smem[];
-    const int Nt = pp.Nt, R = 2 * pp.M, T = pp.T_ext;
-    float *Ds = smem;                   // [NS][Nt]
-    float *Cs = Ds + NS * Nt;           // [RMAX][NS]
-    float *Qs = Cs + RMAX * NS;         // [RMAX][TCOL]
-    float *Gs = Qs + RMAX * TCOL;       // [NS][TCOL + 1]
-    __shared__ int i0s[NS];
-    __shared__ float ws[NS];
-    __shared__ int red[2][8];
+// Column c of a G row sits at c + c / 32: the four threads of a sample read columns 16 apart, and
+// the skew keeps the two that are 32 apart off the same bank.
+__device__ __forceinline__ int gcol(int c) { return c + (c >> 5); }
+
+// One CTA: NS samples (processing order n0 .. n0 + NS - 1).  Thread t serves sample t / 4 and the
+// bins 16 (t % 4) .. 16 (t % 4) + 15 of every 64-bin chunk, accumulating D in registers.  Per
+// (chunk, detector) the tile's column range [min i0 + j0, max i0 + j0 + Jc] is covered by blocks of
+// WC columns: a register-blocked FP32 GEMM G = C^T Qp (each thread a 4-sample x 5-column
+// micro-tile, K = 2M) into shared memory, then each thread adds the lerp of its own shifted
+// columns.  After the last detector of a chunk the thread folds its bins into a running
+// log-sum-exp; the four threads of a sample merge theirs at the end and lnL_t is assembled in FP64.
+__global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant__ PointParams pp,
+                                                          const float *__restrict__ Qp, IleScratch s,
+                                                          const int *__restrict__ perm, int64_t N,
+                                                          double *__restrict__ out, int full_grid, LoudList loud) {
+    extern __shared__ __align__(16) float smem[];
+    const int K = pp.K, Nt = pp.Nt, R = 2 * pp.M, T = pp.T_ext;
+    float *Cs = smem;                          // [K][RMAX][NS]
+    float *Qs = Cs + ILE_MAX_DET * RMAX * NS;  // [RMAX][WC]
+    float *Gs = Qs + RMAX * WC;                // [NS][GROW]
+    __shared__ int rng[2][8][ILE_MAX_DET];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = tid >> 2, g = tid & 3, jbeg = g * JG;
     const int64_t n0 = (int64_t)blockIdx.x * NS;
     const int ns = (int)min((int64_t)NS, N - n0);
+    const bool valid = n < ns;
+    const int64_t p = n0 + (valid ? n : 0);  // invalid rows repeat the tile's first sample
 
-    for (int i = tid; i < NS * Nt; i += 256) Ds[i] = 0.f;
-
-    for (int k = 0; k < pp.K; k++) {
-        __syncthreads();
-        if (tid < NS) {
-            int nn = tid < ns ? tid : 0;
-            i0s[tid] = s.I0[(int64_t)k * N + n0 + nn];
-            ws[tid] = s.W[(int64_t)k * N + n0 + nn];
-        }
-        for (int i = tid; i < R * NS; i += 256) {
-            int r = i / NS, nn = i - r * NS;
-            Cs[r * NS + nn] = nn < ns ? s.C[((int64_t)k * R + r) * N + n0 + nn] : 0.f;
-        }
-        __syncthreads();
-        // column range needed by the tile: [min i0, max i0 + Nt]
-        int lo = 0x7fffffff, hi = -0x7fffffff;
-        for (int i = tid; i < ns; i += 256) {
-            lo = min(lo, i0s[i]);
-            hi = max(hi, i0s[i]);
-        }
+    // the tile's coefficients, and this sample's window placement per detector
+    for (int i = tid; i < K * R * NS; i += NT) {
+        const int nn = i % NS, kr = i / NS;
+        Cs[kr / R * RMAX * NS + (kr % R) * NS + nn] = nn < ns ? s.C[(int64_t)kr * N + n0 + nn] : 0.f;
+    }
+    int i0[ILE_MAX_DET];
+    float wt[ILE_MAX_DET];
+#pragma unroll
+    for (int k = 0; k < ILE_MAX_DET; k++) {
+        i0[k] = k < K ? s.I0[(int64_t)k * N + p] : 0;
+        wt[k] = k < K ? s.W[(int64_t)k * N + p] : 0.f;
+    }
+    // per-detector range of window starts over the tile
+#pragma unroll
+    for (int k = 0; k < ILE_MAX_DET; k++) {
+        int lo = i0[k], hi = i0[k];
         for (int o = 16; o; o >>= 1) {
             lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
             hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         }
         if (lane == 0) {
-            red[0][warp] = lo;
-            red[1][warp] = hi;
-        }
-        __syncthreads();
-        lo = red[0][0];
-        hi = red[1][0];
-        for (int w = 1; w < 8; w++) {
-            lo = min(lo, red[0][w]);
-            hi = max(hi, red[1][w]);
-        }
-        const int cend = hi + Nt;  // last column used (inclusive)
-
-        for (int c0 = lo; c0 <= cend; c0 += TCOL) {
-            __syncthreads();
-            for (int i = tid; i < R * TCOL; i += 256) {
-                int r = i / TCOL, c = i - r * TCOL;
-                int col = c0 + c;
-                Qs[r * TCOL + c] = (col >= 0 && col < T) ? Qp[((int64_t)k * R + r) * T + col] : 0.f;
-            }
-            __syncthreads();
-            {
-                const int ty = tid >> 4, tx = tid & 15;
-                float acc[RS][4];
-#pragma unroll
-                for (int i = 0; i < RS; i++)
-#pragma unroll
-                    for (int j = 0; j < 4; j++) acc[i][j] = 0.f;
-                for (int r = 0; r < R; r++) {
-                    float a[RS];
-#pragma unroll
-                    for (int i = 0; i < RS; i++) a[i] = Cs[r * NS + ty * RS + i];
-                    float4 b = *reinterpret_cast<const float4 *>(&Qs[r * TCOL + tx * 4]);
-#pragma unroll
-                    for (int i = 0; i < RS; i++) {
-                        acc[i][0] = fmaf(a[i], b.x, acc[i][0]);
-                        acc[i][1] = fmaf(a[i], b.y, acc[i][1]);
-                        acc[i][2] = fmaf(a[i], b.z, acc[i][2]);
-                        acc[i][3] = fmaf(a[i], b.w, acc[i][3]);
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < RS; i++)
-#pragma unroll
-                    for (int j = 0; j < 4; j++) Gs[(ty * RS + i) * (TCOL + 1) + tx * 4 + j] = acc[i][j];
-            }
-            __syncthreads();
-            // gather: window bin j of sample n takes columns i0 + j (weight 1 - w) and i0 + j + 1 (weight w)
-            for (int nn = warp; nn < ns; nn += 8) {
-                const int i0 = i0s[nn];
-                const float wt = ws[nn];
-                const int jlo = max(0, c0 - 1 - i0), jhi = min(Nt - 1, c0 + TCOL - 1 - i0);
-                const float *g = Gs + nn * (TCOL + 1);
-                float *d = Ds + nn * Nt;
-                for (int j = jlo + lane; j <= jhi; j += 32) {
-                    int c = i0 + j - c0;
-                    float v = 0.f;
-                    if (c >= 0) v = (1.f - wt) * g[c];
-                    if (c + 1 < TCOL) v = fmaf(wt, g[c + 1], v);
-                    d[j] += v;
-                }
-            }
+            rng[0][warp][k] = lo;
+            rng[1][warp][k] = hi;
         }
     }
     __syncthreads();
+    int tlo[ILE_MAX_DET], thi[ILE_MAX_DET];
+#pragma unroll
+    for (int k = 0; k < ILE_MAX_DET; k++) {
+        tlo[k] = rng[0][0][k];
+        thi[k] = rng[1][0][k];
+        for (int w = 1; w < NT / 32; w++) {
+            tlo[k] = min(tlo[k], rng[0][w][k]);
+            thi[k] = max(thi[k], rng[1][w][k]);
+        }
+    }
+    const float A = s.A[p];
+    DmargSample dq{};
+    if (pp.dm.on) dq = ile_dmarg_sample(pp.dm, A);
 
-    // S5: log-sum-exp over the window, FP64 assembly (distance-marginalised: ln F(D_j, A) per bin)
-    const double log_nt = log((double)Nt);
-    for (int nn = warp; nn < ns; nn += 8) {
-        float *d = Ds + nn * Nt;
-        double A = (double)s.A[n0 + nn];
-        const int64_t dst = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
+    float D[JG];
+#pragma unroll
+    for (int jj = 0; jj < JG; jj++) D[jj] = 0.f;
+    float m_run = -INFINITY, s_run = 0.f;
+    const int ty = tid >> 4, tx = tid & 15;  // GEMM micro-tile: samples 4 ty .. 4 ty + 3, columns 5 tx .. 5 tx + 4
+
+    for (int j0 = 0; j0 < Nt; j0 += JW) {
+        const int Jc = min(JW, Nt - j0);
+        for (int k = 0; k < K; k++) {
+            const float *Ck = Cs + k * RMAX * NS;
+            const float *Qk = Qp + (int64_t)k * R * T;
+            const float omw = 1.f - wt[k], w = wt[k];
+            const int clast = thi[k] + j0 + Jc - 1;  // last column whose lerp pair starts in the chunk
+            for (int cb = tlo[k] + j0; cb <= clast; cb += WSTEP) {
+                __syncthreads();
+                for (int i = tid; i < R * WC; i += NT) {
+                    const int r = i / WC, c = i - r * WC, col = cb + c;
+                    Qs[r * WC + c] = (col >= 0 && col < T) ? __ldg(Qk + (int64_t)r * T + col) : 0.f;
+                }
+                __syncthreads();
+                {
+                    float acc[4][5];
+#pragma unroll
+                    for (int a = 0; a < 4; a++)
+#pragma unroll
+                        for (int b = 0; b < 5; b++) acc[a][b] = 0.f;
+#pragma unroll 6
+                    for (int r = 0; r < R; r++) {
+                        const float4 av = *reinterpret_cast<const float4 *>(Ck + r * NS + 4 * ty);
+                        const float *qr = Qs + r * WC + 5 * tx;
+                        float bv[5];
+#pragma unroll
+                        for (int b = 0; b < 5; b++) bv[b] = qr[b];
+#pragma unroll
+                        for (int b = 0; b < 5; b++) {
+                            acc[0][b] = fmaf(av.x, bv[b], acc[0][b]);
+                            acc[1][b] = fmaf(av.y, bv[b], acc[1][b]);
+                            acc[2][b] = fmaf(av.z, bv[b], acc[2][b]);
+                            acc[3][b] = fmaf(av.w, bv[b], acc[3][b]);
+                        }
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; a++)
+#pragma unroll
+                        for (int b = 0; b < 5; b++) Gs[(4 * ty + a) * GROW + gcol(5 * tx + b)] = acc[a][b];
+                }
+                __syncthreads();
+                // my bins j0 + jbeg + jj read columns c = i0 + j0 + jbeg + jj and c + 1 of the block
+                // (each column read once: the partner of bin jj is the first column of bin jj + 1)
+                const float *gr = Gs + n * GROW;
+                const int c0 = i0[k] + j0 + jbeg - cb;
+                float vprev = (c0 >= 0 && c0 < WC) ? gr[gcol(c0)] : 0.f;
+#pragma unroll
+                for (int jj = 0; jj < JG; jj++) {
+                    const int c = c0 + jj;
+                    const float v = (c + 1 >= 0 && c + 1 < WC) ? gr[gcol(c + 1)] : 0.f;
+                    if (jbeg + jj < Jc && c >= 0 && c < WSTEP) D[jj] = fmaf(omw, vprev, fmaf(w, v, D[jj]));
+                    vprev = v;
+                }
+            }
+        }
+        // chunk complete
         if (pp.dm.on) {
-            const DmargSample q = ile_dmarg_sample(pp.dm, (float)A);
-            for (int j = lane; j < Nt; j += 32) d[j] = ile_dmarg_lnF(pp.dm, q, d[j]);
-            A = 0.0;
+#pragma unroll
+            for (int jj = 0; jj < JG; jj++)
+                if (jbeg + jj < Jc) D[jj] = ile_dmarg_lnF(pp.dm, dq, D[jj]);
         }
         if (full_grid) {
-            for (int j = lane; j < Nt; j += 32) out[dst * Nt + j] = (double)d[j] - A;
-            continue;
+            if (valid) {
+                const double An = pp.dm.on ? 0.0 : (double)A;
+                const int64_t o = (int64_t)(perm ? perm[p] : p) * Nt + j0 + jbeg;
+#pragma unroll
+                for (int jj = 0; jj < JG; jj++)
+                    if (jbeg + jj < Jc) out[o + jj] = (double)D[jj] - An;
+            }
+        } else if (jbeg < Jc) {
+            float mc = -INFINITY;
+#pragma unroll
+            for (int jj = 0; jj < JG; jj++)
+                if (jbeg + jj < Jc) mc = fmaxf(mc, D[jj]);
+            if (mc > m_run) {
+                s_run *= expf(m_run - mc);
+                m_run = mc;
+            }
+#pragma unroll
+            for (int jj = 0; jj < JG; jj++)
+                if (jbeg + jj < Jc) s_run += expf(D[jj] - m_run);
         }
-        float m = -INFINITY;
-        for (int j = lane; j < Nt; j += 32) m = fmaxf(m, d[j]);
-        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        float sum = 0.f;
-        for (int j = lane; j < Nt; j += 32) sum += expf(d[j] - m);
-        for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) {
-            out[dst] = (double)m + (double)logf(sum) - A - log_nt;
-            // a sample too loud for FP32 goes to the FP64 refinement (ile_refine.cu)
-            if (loud.list && fabsf(m) + (float)A > loud.thr) ile_loud_append(loud, (int)dst);
-        }
+#pragma unroll
+        for (int jj = 0; jj < JG; jj++) D[jj] = 0.f;
+    }
+    if (full_grid) return;
+    // S5: merge the four threads of the sample (consecutive lanes), FP64 assembly
+    float m = m_run;
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    float sm = s_run > 0.f ? s_run * expf(m_run - m) : 0.f;
+    sm += __shfl_xor_sync(0xffffffffu, sm, 1);
+    sm += __shfl_xor_sync(0xffffffffu, sm, 2);
+    if (g == 0 && valid) {
+        const double An = pp.dm.on ? 0.0 : (double)A;
+        const int64_t dst = perm ? perm[p] : p;
+        out[dst] = (double)m + (double)logf(sm) - An - (double)pp.log_nt;
+        // a sample too loud for FP32 goes to the FP64 refinement (ile_refine.cu)
+        if (loud.list && fabsf(m) + A > loud.thr) ile_loud_append(loud, (int)dst);
     }
 }
 
-template <int NS>
-size_t plain_smem(const PointParams &pp) {
-    return sizeof(float) * ((size_t)NS * pp.Nt + RMAX * NS + RMAX * TCOL + (size_t)NS * (TCOL + 1));
-}
-
-template <int NS>
-cudaError_t launch(const PointParams &pp, const float *Qp, IleScratch s, const int *perm, int64_t N, double *out,
-                   int full_grid, LoudList loud, cudaStream_t st) {
-    size_t smem = plain_smem<NS>(pp);
-    cudaError_t e = cudaFuncSetAttribute(ile_plain_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int64_t blocks = (N + NS - 1) / NS;
-    ile_plain_kernel<NS><<<(unsigned)blocks, 256, smem, st>>>(pp, Qp, s, perm, N, out, full_grid, loud);
-    return cudaGetLastError();
-}
+size_t plain_smem() { return sizeof(float) * ((size_t)ILE_MAX_DET * RMAX * NS + RMAX * WC + (size_t)NS * GROW); }
 
 }  // namespace
 
@@ -181,6 +213,10 @@ cudaError_t ile_launch_plain(const PointParams &pp, const float *Qp, IleScratch 
     (void)flags;
     if (N <= 0) return cudaSuccess;
     if (full_grid || pp.dm.on) loud.list = nullptr;
-    if (pp.Nt <= 512) return launch<64>(pp, Qp, s, perm, N, out, full_grid, loud, st);
-    return launch<32>(pp, Qp, s, perm, N, out, full_grid, loud, st);
+    const size_t smem = plain_smem();
+    cudaError_t e = cudaFuncSetAttribute(ile_plain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (N + NS - 1) / NS;
+    ile_plain_kernel<<<(unsigned)blocks, NT, smem, st>>>(pp, Qp, s, perm, N, out, full_grid, loud);
+    return cudaGetLastError();
 }

@@ -159,9 +159,38 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
         }
         // chunk complete
         if (pp.dm.on) {
+            // ln F(D_j, A) of the chunk's bins: one Chebyshev interpolant per sample through 12 table
+            // values (3 per thread; the sample's four threads are consecutive lanes), or per-bin
+            // table reads where the sample's data terms span more than ILE_DM_WMAX
+            float lo = INFINITY, hi = -INFINITY;
 #pragma unroll
             for (int jj = 0; jj < JG; jj++)
-                if (jbeg + jj < Jc) D[jj] = ile_dmarg_lnF(pp.dm, dq, D[jj]);
+                if (jbeg + jj < Jc) {
+                    lo = fminf(lo, D[jj]);
+                    hi = fmaxf(hi, D[jj]);
+                }
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, 1));
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, 2));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, 1));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, 2));
+            const DmRange rg = ile_dm_range(lo, hi);
+            float fv[3];
+#pragma unroll
+            for (int i = 0; i < 3; i++) fv[i] = rg.fit ? ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, 3 * g + i)) : 0.f;
+            float f[ILE_DM_NODES];
+#pragma unroll
+            for (int k = 0; k < ILE_DM_NODES; k++) f[k] = __shfl_sync(0xffffffffu, fv[k % 3], (lane & ~3) | (k / 3));
+            if (rg.fit) {
+                float c[ILE_DM_NODES];
+                ile_dm_coeffs(f, c);
+#pragma unroll
+                for (int jj = 0; jj < JG; jj++)
+                    if (jbeg + jj < Jc) D[jj] = ile_dm_eval(c, rg, D[jj]);
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < JG; jj++)
+                    if (jbeg + jj < Jc) D[jj] = ile_dmarg_lnF(pp.dm, dq, D[jj]);
+            }
         }
         if (full_grid) {
             if (valid) {

@@ -7,18 +7,21 @@
 // (Eq. (eq:loglikelihood), first line).  The quadratic term
 //   A = 1/4 (D_ref/D)^2 sum_k [ |F_k|^2 y^H U_k y + Re(F_k^2 y^T V_k y) ]      (second line)
 // uses the pair products conj(y_a) y_b and y_a y_b once for all detectors, with U and V staged
-// in shared memory as upper-triangle pairs.  Everything is FP32; the result feeds the FP64
+// in shared memory as upper-triangle pairs and the harmonics in a per-thread column of a shared
+// table.  Everything is FP32; the result feeds the FP64
 // per-sample assembly of the contraction kernels.
 #include "ile_internal.cuh"
 
 namespace {
 
-__global__ void __launch_bounds__(256) ile_prep_kernel(const __grid_constant__ PointParams pp,
+constexpr int PREP_NT = 256;
+
+__global__ void __launch_bounds__(PREP_NT) ile_prep_kernel(const __grid_constant__ PointParams pp,
                                                        const float4 *__restrict__ UV,
                                                        const double *__restrict__ samples,
                                                        const int *__restrict__ perm, int64_t N, IleScratch s,
                                                        unsigned *flags) {
-    extern __shared__ float4 uv_s[];  // [K][P]
+    extern __shared__ float4 uv_s[];  // [K][P], then the y table
     const int M = pp.M, K = pp.K, P = M * (M + 1) / 2;
     for (int i = threadIdx.x; i < K * P; i += blockDim.x) uv_s[i] = UV[i];
     __syncthreads();
@@ -65,53 +68,54 @@ __global__ void __launch_bounds__(256) ile_prep_kernel(const __grid_constant__ P
         s.W[(int64_t)k * N + n] = in_range ? x0[k] - fl : 0.f;
     }
 
-    float cpow[9], spow[9];
-    ile_half_angle_powers(iota, cpow, spow);
-    float yr[ILE_MAX_MODES], yi[ILE_MAX_MODES];
-#pragma unroll
-    for (int a = 0; a < ILE_MAX_MODES; a++) {
-        if (a < M) {
-            ile_sylm(pp.mode[a], cpow, spow, phi, yr[a], yi[a]);
-        } else {
-            yr[a] = 0.f;
-            yi[a] = 0.f;
+    // harmonics with every power at a compile-time index (registers) and e^{i m phi} from powers of
+    // e^{i phi}, into this thread's column of the shared y table: the mode and pair loops below stay
+    // rolled (fully unrolled, they overflow the instruction cache)
+    float2 *ys = reinterpret_cast<float2 *>(uv_s + K * P);  // [M][PREP_NT]
+    {
+        float cpow[9], spow[9], er[5], ei[5];
+        ile_half_angle_powers(iota, cpow, spow);
+        ile_phase_powers(phi, er, ei);
+#pragma unroll 1
+        for (int a = 0; a < M; a++) {
+            float yr, yi;
+            ile_sylm_fast(pp.mode[a], cpow, spow, er, ei, yr, yi);
+            ys[a * PREP_NT + threadIdx.x] = make_float2(yr, yi);
         }
     }
     const int R = 2 * M;
 #pragma unroll
     for (int k = 0; k < ILE_MAX_DET; k++) {
         if (k >= K) break;
-        float fr = scale * Fr[k], fi = scale * Fi[k];
+        const float fr = scale * Fr[k], fi = scale * Fi[k];
         float *Ck = s.C + (int64_t)k * R * N + n;
-#pragma unroll
-        for (int a = 0; a < ILE_MAX_MODES; a++) {
-            if (a < M) {
-                Ck[(int64_t)a * N] = fr * yr[a] - fi * yi[a];
-                Ck[(int64_t)(M + a) * N] = fr * yi[a] + fi * yr[a];
-            }
+#pragma unroll 1
+        for (int a = 0; a < M; a++) {
+            const float2 y = ys[a * PREP_NT + threadIdx.x];
+            Ck[(int64_t)a * N] = fr * y.x - fi * y.y;
+            Ck[(int64_t)(M + a) * N] = fr * y.y + fi * y.x;
         }
     }
 
     float au[ILE_MAX_DET] = {0.f, 0.f, 0.f, 0.f}, avr[ILE_MAX_DET] = {0.f, 0.f, 0.f, 0.f},
           avi[ILE_MAX_DET] = {0.f, 0.f, 0.f, 0.f};
     int p = 0;
+#pragma unroll 1
+    for (int a = 0; a < M; a++) {
+        const float2 ya = ys[a * PREP_NT + threadIdx.x];
+#pragma unroll 1
+        for (int b = a; b < M; b++, p++) {
+            const float2 yb = ys[b * PREP_NT + threadIdx.x];
+            const float qr = ya.x * yb.x + ya.y * yb.y, qi = ya.x * yb.y - ya.y * yb.x;  // conj(y_a) y_b
+            const float pr = ya.x * yb.x - ya.y * yb.y, pi = ya.x * yb.y + ya.y * yb.x;  // y_a y_b
 #pragma unroll
-    for (int a = 0; a < ILE_MAX_MODES; a++) {
-#pragma unroll
-        for (int b = a; b < ILE_MAX_MODES; b++) {
-            if (b < M) {
-                float qr = yr[a] * yr[b] + yi[a] * yi[b], qi = yr[a] * yi[b] - yi[a] * yr[b];  // conj(y_a) y_b
-                float pr = yr[a] * yr[b] - yi[a] * yi[b], pi = yr[a] * yi[b] + yi[a] * yr[b];  // y_a y_b
-#pragma unroll
-                for (int k = 0; k < ILE_MAX_DET; k++) {
-                    if (k < K) {
-                        float4 u = uv_s[k * P + p];
-                        au[k] += u.x * qr - u.y * qi;
-                        avr[k] += u.z * pr - u.w * pi;
-                        avi[k] += u.z * pi + u.w * pr;
-                    }
+            for (int k = 0; k < ILE_MAX_DET; k++) {
+                if (k < K) {
+                    const float4 u = uv_s[k * P + p];
+                    au[k] += u.x * qr - u.y * qi;
+                    avr[k] += u.z * pr - u.w * pi;
+                    avi[k] += u.z * pi + u.w * pr;
                 }
-                p++;
             }
         }
     }
@@ -132,8 +136,12 @@ cudaError_t ile_launch_prep(const PointParams &pp, const float *UV, const double
                             IleScratch s, unsigned *flags, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     const int P = pp.M * (pp.M + 1) / 2;
-    size_t smem = sizeof(float4) * pp.K * P;
-    int64_t blocks = (N + 255) / 256;
-    ile_prep_kernel<<<(unsigned)blocks, 256, smem, st>>>(pp, (const float4 *)UV, samples, perm, N, s, flags);
+    const size_t smem = sizeof(float4) * pp.K * P + sizeof(float2) * pp.M * PREP_NT;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(ile_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t blocks = (N + PREP_NT - 1) / PREP_NT;
+    ile_prep_kernel<<<(unsigned)blocks, PREP_NT, smem, st>>>(pp, (const float4 *)UV, samples, perm, N, s, flags);
     return cudaGetLastError();
 }

@@ -204,8 +204,25 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
             }
         }
         if (timed_out) break;
-        if (pp.dm.on)
-            for (int jj = 0; jj < Jc; jj++) Dt[jj * TILE + t] = ile_dmarg_lnF(pp.dm, dq, Dt[jj * TILE + t]);
+        if (pp.dm.on) {
+            // ln F(D_j, A) of the chunk's bins: a Chebyshev interpolant through 12 table values, or
+            // per-bin table reads where the data terms span more than ILE_DM_WMAX
+            float lo = INFINITY, hi = -INFINITY;
+            for (int jj = 0; jj < Jc; jj++) {
+                lo = fminf(lo, Dt[jj * TILE + t]);
+                hi = fmaxf(hi, Dt[jj * TILE + t]);
+            }
+            const DmRange rg = ile_dm_range(lo, hi);
+            if (rg.fit) {
+                float f[ILE_DM_NODES], c[ILE_DM_NODES];
+#pragma unroll
+                for (int k = 0; k < ILE_DM_NODES; k++) f[k] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, k));
+                ile_dm_coeffs(f, c);
+                for (int jj = 0; jj < Jc; jj++) Dt[jj * TILE + t] = ile_dm_eval(c, rg, Dt[jj * TILE + t]);
+            } else {
+                for (int jj = 0; jj < Jc; jj++) Dt[jj * TILE + t] = ile_dmarg_lnF(pp.dm, dq, Dt[jj * TILE + t]);
+            }
+        }
         if (full_grid) {
             if (valid) {
                 const int64_t o = (int64_t)(perm ? perm[p] : p) * Nt + j0;

@@ -74,6 +74,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 struct Sm {
     uint64_t bfull[NBMAX], bempty[NBMAX], tfull[NTB], tempty[NTB], yready, aready, s4done, tdone, sready;
+    uint64_t dmx[4];  // distance-marginalised chunks: the four warps of a TMEM lane quarter exchange values
     uint32_t tmem_base;
     int wlo[4][ILE_MAX_DET], whi[4][ILE_MAX_DET];
     int2 dkr[NMATH / 32][ILE_MAX_DET];  // per math warp and detector: (min, max) of i0 - tile lo
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_init(&sm.s4done, NMATH / 32);
         mbar_init(&sm.tdone, NMATH / 32);
         mbar_init(&sm.sready, 32);
+        for (int q = 0; q < 4; q++) mbar_init(&sm.dmx[q], NGRP);
         mbar_init_fence();
     }
     fence_before();
@@ -426,6 +428,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         float *my_row = rows + tid * RSTRIDE;
         uint32_t tiles_done = 0;
         uint32_t jtb = 0, jtpar = 0;  // TMEM buffer and phase parity of the next job (running)
+        uint32_t dmph = 0;            // phases of this quarter's dmx barrier passed (distance marginalisation)
         auto next_job = [&]() {
             if (++jtb == (uint32_t)NTB) {
                 jtb = 0;
@@ -614,11 +617,67 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             float m_run = -INFINITY, s_run = 0.f;
             const int jbeg = g * JG;  // my first bin of a chunk (warp-uniform)
             // chunk [j0, j0 + Jc) complete: S5 log-sum-exp update (or the full grid)
+            // (sets failed if a distance-marginalised exchange times out)
             auto finish_chunk = [&](int j0, int Jc) {
                 if constexpr (DM) {
+                    // ln F(D_j, A) of the chunk's bins: one Chebyshev interpolant per sample through 12
+                    // table values, or per-bin table reads where the sample's data terms span more than
+                    // ILE_DM_WMAX.  The sample's four threads sit in the four warps of this TMEM lane
+                    // quarter: each publishes its bins' range (ls_s, free until the tile's end), then
+                    // three node values (the two spare words of its staging row and aq_s, free once
+                    // the quarter's warps have formed dq), with a barrier of the quarter after each.
+                    float lo = INFINITY, hi = -INFINITY;
 #pragma unroll
                     for (int jj = 0; jj < JG; jj++)
-                        if (jbeg + jj < Jc) D[jj] = ile_dmarg_lnF(pp.dm, dq, D[jj]);
+                        if (jbeg + jj < Jc) {
+                            lo = fminf(lo, D[jj]);
+                            hi = fmaxf(hi, D[jj]);
+                        }
+                    ls_s[tid] = make_float2(lo, hi);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm.dmx[q4]);
+                    if (!warp_wait(&sm.dmx[q4], dmph & 1u, flags)) {
+                        failed = true;
+                        return;
+                    }
+                    dmph++;
+#pragma unroll
+                    for (int h = 0; h < NGRP; h++) {
+                        const float2 v = ls_s[(4 * h + q4) * 32 + lane];
+                        lo = fminf(lo, v.x);
+                        hi = fmaxf(hi, v.y);
+                    }
+                    const DmRange rg = ile_dm_range(lo, hi);
+                    if (rg.fit) {
+                        my_row[32] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, 3 * g));
+                        my_row[33] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, 3 * g + 1));
+                        aq_s[tid] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, 3 * g + 2));
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm.dmx[q4]);
+                    if (!warp_wait(&sm.dmx[q4], dmph & 1u, flags)) {
+                        failed = true;
+                        return;
+                    }
+                    dmph++;
+                    if (rg.fit) {
+                        float f[ILE_DM_NODES], c[ILE_DM_NODES];
+#pragma unroll
+                        for (int h = 0; h < NGRP; h++) {
+                            const int t = (4 * h + q4) * 32 + lane;
+                            f[3 * h] = rows[t * RSTRIDE + 32];
+                            f[3 * h + 1] = rows[t * RSTRIDE + 33];
+                            f[3 * h + 2] = aq_s[t];
+                        }
+                        ile_dm_coeffs(f, c);
+#pragma unroll
+                        for (int jj = 0; jj < JG; jj++)
+                            if (jbeg + jj < Jc) D[jj] = ile_dm_eval(c, rg, D[jj]);
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < JG; jj++)
+                            if (jbeg + jj < Jc) D[jj] = ile_dmarg_lnF(pp.dm, dq, D[jj]);
+                    }
                 }
                 if (full_grid == 2) {
                     if (valid) {
@@ -774,7 +833,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     consume(tb, s0, cmin, cmax, mine, wtd(j.k), j.Jc);
                     next_job();
                     jit.next_from(j);
-                    if (j.k == K - 1 && j.w == j.W - 1) finish_chunk(j.j0, j.Jc);
+                    if (j.k == K - 1 && j.w == j.W - 1) {
+                        finish_chunk(j.j0, j.Jc);
+                        if (failed) break;
+                    }
                 }
             }
             if (failed) break;
@@ -793,7 +855,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int h = 0; h < NGRP; h++) {
                     const int t = (4 * h + q4) * 32 + lane;
                     m = fmaxf(m, ls_s[t].x);
-                    aqs += aq_s[t];
+                    if constexpr (!DM) aqs += aq_s[t];
                 }
                 float ssum = 0.f;
 #pragma unroll
@@ -826,6 +888,7 @@ size_t tc2_smem(int K, int M, int KP, int NB) {
            sizeof(float) * NMATH + sizeof(float2) * NMATH + sizeof(float) * 14 * TILE;
 }
 static_assert(8 * ILE_MAX_MODES * TILE <= 4 * RSTRIDE * NMATH, "y table must fit in the rows area");
+static_assert(RSTRIDE >= 34, "words 32 and 33 of a staging row carry distance-marginalisation node values");
 
 constexpr size_t SMEM_LIMIT = 227 * 1024 - sizeof(Sm) - 64;
 

@@ -427,9 +427,12 @@ typedef struct {
  *   ile_batch_config: set the fused kernel's B-ring depth (2..4, if it fits in shared memory),
  *     window width and CTA count by hand.
  *   ile_batch_tune: autotuner -- runs one iteration to have samples, then times the fused
- *     kernel over that iteration's work items for every admissible (nb, nwcol), reps launches
- *     each, and keeps the fastest (BF16X3 only; else ILE_E_STATE).  The sampler advances by one
- *     iteration: call ile_batch_reset before the run that counts.
+ *     kernel over that iteration's work items (a warm-up launch and reps timed launches per
+ *     candidate; reps >= 3 recommended): every window width nwcol on an 8-column grid over the
+ *     admissible range (its two ends included) at the deepest B ring that fits, then each
+ *     shallower ring at the best width; keeps the fastest (BF16X3 only; else ILE_E_STATE).  The
+ *     grid stays one persistent CTA per SM (the kernel holds a whole SM).  The sampler advances
+ *     by one iteration: call ile_batch_reset before the run that counts.
  */
 ile_status ile_batch_create(ile_batch **out, int device, void *cuda_stream, ile_prec prec);
 ile_status ile_batch_destroy(ile_batch *b);

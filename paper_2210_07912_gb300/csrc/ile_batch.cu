@@ -585,52 +585,61 @@ ile_status ile_batch_tune(ile_batch *b, int reps, ile_batch_tuning *out) {
     ile_tc2_nwcol_range(&lo, &hi);
     int sms = 0;
     BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
-    const int widths[3] = {std::max(lo, 72), std::max(lo, 96), hi};
+    // the deepest B ring that fits; every window width on an 8-column grid over the admissible
+    // range [lo, hi] (both ends included) at that depth, then the shallower rings at the best width
+    int nb_max = 2;
+    for (int NB = 3; NB <= 4; NB++)
+        if (ile_tc2_batch_fits(b->LK, b->LM, b->LKP, NB)) nb_max = NB;
     cudaEvent_t e0, e1;
     BK(cudaEventCreate(&e0));
     BK(cudaEventCreate(&e1));
     float best = 1e30f;
     int bNB = b->NB, bW = b->nwcol, n_tried = 0;
-    for (int NB = 2; NB <= 4; NB++) {
-        if (!ile_tc2_batch_fits(b->LK, b->LM, b->LKP, NB)) continue;
-        for (int wi = 0; wi < 3; wi++) {
-            const int W = widths[wi];
-            if (wi > 0 && W == widths[wi - 1]) continue;
-            // warm-up launch, then `reps` timed launches (each refills the loud-sample list: its count
-            // is reset first)
-            cudaError_t e = cudaMemsetAsync(b->loud, 0, sizeof(int), b->stream);
+    auto time_one = [&](int NB, int W) -> cudaError_t {
+        // warm-up launch, then `reps` timed launches (each refills the loud-sample list: its count is
+        // reset first)
+        cudaError_t e = cudaMemsetAsync(b->loud, 0, sizeof(int), b->stream);
+        if (e == cudaSuccess)
+            e = ile_launch_tc2_batch(b->pts, b->items, b->n_items, b->LK, b->LM, b->LKP, NB, W, sms, b->flags,
+                                     b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; r++) {
+            e = cudaMemsetAsync(b->loud, 0, sizeof(int), b->stream);
             if (e == cudaSuccess)
                 e = ile_launch_tc2_batch(b->pts, b->items, b->n_items, b->LK, b->LM, b->LKP, NB, W, sms, b->flags,
                                          b->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-            for (int r = 0; r < reps && e == cudaSuccess; r++) {
-                e = cudaMemsetAsync(b->loud, 0, sizeof(int), b->stream);
-                if (e == cudaSuccess)
-                    e = ile_launch_tc2_batch(b->pts, b->items, b->n_items, b->LK, b->LM, b->LKP, NB, W, sms,
-                                             b->flags, b->stream);
-            }
-            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return fail(b, e, "ile_batch_tune");
-            }
-            ms /= reps;
-            if (out && n_tried < ILE_TUNE_MAX) {
-                out->tried_nb[n_tried] = NB;
-                out->tried_nwcol[n_tried] = W;
-                out->tried_ms[n_tried] = ms;
-            }
-            n_tried++;
-            if (ms < best) {
-                best = ms;
-                bNB = NB;
-                bW = W;
-            }
         }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) return e;
+        ms /= reps;
+        if (out && n_tried < ILE_TUNE_MAX) {
+            out->tried_nb[n_tried] = NB;
+            out->tried_nwcol[n_tried] = W;
+            out->tried_ms[n_tried] = ms;
+        }
+        n_tried++;
+        if (ms < best) {
+            best = ms;
+            bNB = NB;
+            bW = W;
+        }
+        return cudaSuccess;
+    };
+    cudaError_t e = cudaSuccess;
+    for (int W = lo; e == cudaSuccess; W += 8) {
+        W = std::min(W, hi);
+        e = time_one(nb_max, W);
+        if (W == hi) break;
+    }
+    const int wbest = bW;
+    for (int NB = 2; NB < nb_max && e == cudaSuccess; NB++) e = time_one(NB, wbest);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(b, e, "ile_batch_tune");
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -647,7 +647,7 @@ class Batch:
     def config(self, nb: int, nwcol: int, grid: int):
         self._check(self._lib.ile_batch_config(self._h, nb, nwcol, grid), "ile_batch_config")
 
-    def tune(self, reps: int = 2) -> dict:
+    def tune(self, reps: int = 3) -> dict:
         t = BatchTuning()
         self._check(self._lib.ile_batch_tune(self._h, reps, ctypes.byref(t)), "ile_batch_tune")
         tried = [(t.tried_nb[i], t.tried_nwcol[i], float(t.tried_ms[i])) for i in range(t.n_tried)]

@@ -108,6 +108,10 @@ def test_batch_tune_keeps_results(ile):
     before = b.get()
     t = b.tune(reps=1)
     assert t["nb"] in (2, 3, 4) and 66 <= t["nwcol"] <= 121 and t["ms"] > 0 and len(t["tried"]) >= 2
+    # the widths tried span the admissible range, both ends included, and the choice is the fastest
+    widths = sorted({w for _, w, _ in t["tried"]})
+    assert widths[0] == 66 and widths[-1] == 121 and len(widths) >= 8
+    assert min(t["tried"], key=lambda c: c[2])[:2] == (t["nb"], t["nwcol"])
     b.reset()
     b.step(2)
     after = b.get()

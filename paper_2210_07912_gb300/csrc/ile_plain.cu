@@ -25,11 +25,18 @@ constexpr int JG = 16;                     // bins per thread per chunk
 constexpr int WC = 80;                     // columns of one GEMM block (16 column groups x 5)
 constexpr int WSTEP = WC - 1;              // blocks overlap by one column: the lerp partner
 constexpr int RMAX = 2 * ILE_MAX_MODES;    // real rows of the contraction
-constexpr int GROW = WC + 4;               // G row: WC columns, each 32-column segment skewed by one bank
+constexpr int GROW = WC + 4;               // G row stride (floats)
+constexpr int NFILL = (NT / WC) * WC;      // threads that stage the Q block: 240, column tid % WC
 
-// Column c of a G row sits at c + c / 32: the four threads of a sample read columns 16 apart, and
-// the skew keeps the two that are 32 apart off the same bank.
-__device__ __forceinline__ int gcol(int c) { return c + (c >> 5); }
+// Per-detector value held in registers (selects instead of a dynamically indexed local array).
+struct PerDet {
+    float v0, v1, v2, v3;
+    __device__ float operator()(int k) const { return k == 0 ? v0 : k == 1 ? v1 : k == 2 ? v2 : v3; }
+};
+struct PerDetI {
+    int v0, v1, v2, v3;
+    __device__ int operator()(int k) const { return k == 0 ? v0 : k == 1 ? v1 : k == 2 ? v2 : v3; }
+};
 
 // One CTA: NS samples (processing order n0 .. n0 + NS - 1).  Thread t serves sample t / 4 and the
 // bins 16 (t % 4) .. 16 (t % 4) + 15 of every 64-bin chunk, accumulating D in registers.  Per
@@ -68,6 +75,8 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
         i0[k] = k < K ? s.I0[(int64_t)k * N + p] : 0;
         wt[k] = k < K ? s.W[(int64_t)k * N + p] : 0.f;
     }
+    const PerDetI i0d{i0[0], i0[1], i0[2], i0[3]};
+    const PerDet wtd{wt[0], wt[1], wt[2], wt[3]};
     // per-detector range of window starts over the tile
 #pragma unroll
     for (int k = 0; k < ILE_MAX_DET; k++) {
@@ -87,11 +96,13 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
     for (int k = 0; k < ILE_MAX_DET; k++) {
         tlo[k] = rng[0][0][k];
         thi[k] = rng[1][0][k];
+#pragma unroll
         for (int w = 1; w < NT / 32; w++) {
             tlo[k] = min(tlo[k], rng[0][w][k]);
             thi[k] = max(thi[k], rng[1][w][k]);
         }
     }
+    const PerDetI tlod{tlo[0], tlo[1], tlo[2], tlo[3]}, thid{thi[0], thi[1], thi[2], thi[3]};
     const float A = s.A[p];
     DmargSample dq{};
     if (pp.dm.on) dq = ile_dmarg_sample(pp.dm, A);
@@ -100,20 +111,31 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
 #pragma unroll
     for (int jj = 0; jj < JG; jj++) D[jj] = 0.f;
     float m_run = -INFINITY, s_run = 0.f;
-    const int ty = tid >> 4, tx = tid & 15;  // GEMM micro-tile: samples 4 ty .. 4 ty + 3, columns 5 tx .. 5 tx + 4
+    // GEMM micro-tile: samples 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3 and 64 + tx
+    const int ty = tid >> 4, tx = tid & 15;
+    const int fc = tid % WC, fr0 = tid / WC;  // Q staging: column fc, rows fr0, fr0 + NT / WC, ...
 
     for (int j0 = 0; j0 < Nt; j0 += JW) {
         const int Jc = min(JW, Nt - j0);
         for (int k = 0; k < K; k++) {
             const float *Ck = Cs + k * RMAX * NS;
             const float *Qk = Qp + (int64_t)k * R * T;
-            const float omw = 1.f - wt[k], w = wt[k];
-            const int clast = thi[k] + j0 + Jc - 1;  // last column whose lerp pair starts in the chunk
-            for (int cb = tlo[k] + j0; cb <= clast; cb += WSTEP) {
+            const float w = wtd(k), omw = 1.f - w;
+            const int ik = i0d(k);
+            const int clast = thid(k) + j0 + Jc - 1;  // last column whose lerp pair starts in the chunk
+            for (int cb = tlod(k) + j0; cb <= clast; cb += WSTEP) {
                 __syncthreads();
-                for (int i = tid; i < R * WC; i += NT) {
-                    const int r = i / WC, c = i - r * WC, col = cb + c;
-                    Qs[r * WC + c] = (col >= 0 && col < T) ? __ldg(Qk + (int64_t)r * T + col) : 0.f;
+                if (tid < NFILL) {
+                    const int col = cb + fc;
+                    const bool in = col >= 0 && col < T;
+                    const float *src = Qk + (int64_t)fr0 * T + (in ? col : 0);
+                    float *dst = Qs + fr0 * WC + fc;
+#pragma unroll 2
+                    for (int r = fr0; r < R; r += NT / WC) {
+                        *dst = in ? __ldg(src) : 0.f;
+                        src += (NT / WC) * (int64_t)T;
+                        dst += (NT / WC) * WC;
+                    }
                 }
                 __syncthreads();
                 {
@@ -125,10 +147,8 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
 #pragma unroll 6
                     for (int r = 0; r < R; r++) {
                         const float4 av = *reinterpret_cast<const float4 *>(Ck + r * NS + 4 * ty);
-                        const float *qr = Qs + r * WC + 5 * tx;
-                        float bv[5];
-#pragma unroll
-                        for (int b = 0; b < 5; b++) bv[b] = qr[b];
+                        const float4 b4 = *reinterpret_cast<const float4 *>(Qs + r * WC + 4 * tx);
+                        const float bv[5] = {b4.x, b4.y, b4.z, b4.w, Qs[r * WC + 64 + tx]};
 #pragma unroll
                         for (int b = 0; b < 5; b++) {
                             acc[0][b] = fmaf(av.x, bv[b], acc[0][b]);
@@ -138,22 +158,36 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
                         }
                     }
 #pragma unroll
-                    for (int a = 0; a < 4; a++)
-#pragma unroll
-                        for (int b = 0; b < 5; b++) Gs[(4 * ty + a) * GROW + gcol(5 * tx + b)] = acc[a][b];
+                    for (int a = 0; a < 4; a++) {
+                        float *g = Gs + (4 * ty + a) * GROW;
+                        *reinterpret_cast<float4 *>(g + 4 * tx) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+                        g[64 + tx] = acc[a][4];
+                    }
                 }
                 __syncthreads();
                 // my bins j0 + jbeg + jj read columns c = i0 + j0 + jbeg + jj and c + 1 of the block
                 // (each column read once: the partner of bin jj is the first column of bin jj + 1)
                 const float *gr = Gs + n * GROW;
-                const int c0 = i0[k] + j0 + jbeg - cb;
-                float vprev = (c0 >= 0 && c0 < WC) ? gr[gcol(c0)] : 0.f;
+                const int c0 = ik + j0 + jbeg - cb;
+                if (c0 >= 0 && c0 + JG <= WSTEP && jbeg + JG <= Jc) {
+                    // the usual case: all my bins and their partners lie in this block
+                    const float *src = gr + c0;
+                    float vprev = src[0];
 #pragma unroll
-                for (int jj = 0; jj < JG; jj++) {
-                    const int c = c0 + jj;
-                    const float v = (c + 1 >= 0 && c + 1 < WC) ? gr[gcol(c + 1)] : 0.f;
-                    if (jbeg + jj < Jc && c >= 0 && c < WSTEP) D[jj] = fmaf(omw, vprev, fmaf(w, v, D[jj]));
-                    vprev = v;
+                    for (int jj = 0; jj < JG; jj++) {
+                        const float v = src[jj + 1];
+                        D[jj] = fmaf(omw, vprev, fmaf(w, v, D[jj]));
+                        vprev = v;
+                    }
+                } else {
+                    float vprev = (c0 >= 0 && c0 < WC) ? gr[c0] : 0.f;
+#pragma unroll
+                    for (int jj = 0; jj < JG; jj++) {
+                        const int c = c0 + jj;
+                        const float v = (c + 1 >= 0 && c + 1 < WC) ? gr[c + 1] : 0.f;
+                        if (jbeg + jj < Jc && c >= 0 && c < WSTEP) D[jj] = fmaf(omw, vprev, fmaf(w, v, D[jj]));
+                        vprev = v;
+                    }
                 }
             }
         }

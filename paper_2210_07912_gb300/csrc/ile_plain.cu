@@ -13,7 +13,8 @@
 // chunk each thread folds its bins into a running log-sum-exp; the four threads of a sample merge
 // theirs and assemble
 //   lnL_t = max_j D + ln sum_j exp(D - max) - A - ln N_t
-// in FP64.  ~77 KB of shared memory per CTA: two CTAs (16 warps) per SM.
+// in FP64.  The Q columns of the next block are copied asynchronously while the current one is
+// contracted.  ~91 KB of shared memory per CTA: two CTAs (16 warps) per SM.
 #include "ile_internal.cuh"
 
 namespace {
@@ -38,6 +39,16 @@ struct PerDetI {
     __device__ int operator()(int k) const { return k == 0 ? v0 : k == 1 ? v1 : k == 2 ? v2 : v3; }
 };
 
+// Asynchronous 4-byte global -> shared copy (zero-filled when `in` is false; src stays a valid
+// address either way), and its group commit / wait.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool in) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(in ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // One CTA: NS samples (processing order n0 .. n0 + NS - 1).  Thread t serves sample t / 4 and the
 // bins 16 (t % 4) .. 16 (t % 4) + 15 of every 64-bin chunk, accumulating D in registers.  Per
 // (chunk, detector) the tile's column range [min i0 + j0, max i0 + j0 + Jc] is covered by blocks of
@@ -52,8 +63,8 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
     extern __shared__ __align__(16) float smem[];
     const int K = pp.K, Nt = pp.Nt, R = 2 * pp.M, T = pp.T_ext;
     float *Cs = smem;                          // [K][RMAX][NS]
-    float *Qs = Cs + ILE_MAX_DET * RMAX * NS;  // [RMAX][WC]
-    float *Gs = Qs + RMAX * WC;                // [NS][GROW]
+    float *Qs = Cs + ILE_MAX_DET * RMAX * NS;  // [2][RMAX][WC]: the block in use and the next one
+    float *Gs = Qs + 2 * RMAX * WC;            // [NS][GROW]
     __shared__ int rng[2][8][ILE_MAX_DET];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -115,83 +126,108 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
     const int ty = tid >> 4, tx = tid & 15;
     const int fc = tid % WC, fr0 = tid / WC;  // Q staging: column fc, rows fr0, fr0 + NT / WC, ...
 
-    for (int j0 = 0; j0 < Nt; j0 += JW) {
+    // The blocks in order: chunk j0, detector k, first column cb (steps of WSTEP up to the last column
+    // whose lerp pair starts in the chunk).  Block b's Q columns are copied asynchronously into
+    // buffer b & 1 while block b - 1 is contracted.
+    auto next_block = [&](int &j0, int &k, int &cb) {
+        cb += WSTEP;
+        if (cb > thid(k) + j0 + min(JW, Nt - j0) - 1) {
+            if (++k == K) {
+                k = 0;
+                j0 += JW;
+            }
+            cb = tlod(k) + j0;
+        }
+    };
+    auto stage = [&](int buf, int k, int cb) {
+        if (tid < NFILL) {
+            const int col = cb + fc;
+            const bool in = col >= 0 && col < T;
+            const float *src = Qp + ((int64_t)k * R + fr0) * T + (in ? col : 0);
+            float *dst = Qs + buf * RMAX * WC + fr0 * WC + fc;
+            for (int r = fr0; r < R; r += NT / WC) {
+                cp_async4(dst, src, in);
+                src += (NT / WC) * (int64_t)T;
+                dst += (NT / WC) * WC;
+            }
+        }
+        cp_async_commit();
+    };
+    int j0 = 0, k = 0, cb = tlod(0), buf = 0;
+    stage(0, 0, cb);
+    while (j0 < Nt) {
+        int nj0 = j0, nk = k, ncb = cb;
+        next_block(nj0, nk, ncb);
+        if (nj0 < Nt)
+            stage(buf ^ 1, nk, ncb);  // buffer buf ^ 1 was last read by block b - 1's GEMM, before its G barrier
+        else
+            cp_async_commit();  // an empty group keeps "all but the newest group" meaning block b
+        cp_async_wait_prev();
+        __syncthreads();  // block b's columns are in; every thread is done with block b - 1's G
         const int Jc = min(JW, Nt - j0);
-        for (int k = 0; k < K; k++) {
+        {
             const float *Ck = Cs + k * RMAX * NS;
-            const float *Qk = Qp + (int64_t)k * R * T;
-            const float w = wtd(k), omw = 1.f - w;
-            const int ik = i0d(k);
-            const int clast = thid(k) + j0 + Jc - 1;  // last column whose lerp pair starts in the chunk
-            for (int cb = tlod(k) + j0; cb <= clast; cb += WSTEP) {
-                __syncthreads();
-                if (tid < NFILL) {
-                    const int col = cb + fc;
-                    const bool in = col >= 0 && col < T;
-                    const float *src = Qk + (int64_t)fr0 * T + (in ? col : 0);
-                    float *dst = Qs + fr0 * WC + fc;
-#pragma unroll 2
-                    for (int r = fr0; r < R; r += NT / WC) {
-                        *dst = in ? __ldg(src) : 0.f;
-                        src += (NT / WC) * (int64_t)T;
-                        dst += (NT / WC) * WC;
-                    }
-                }
-                __syncthreads();
-                {
-                    float acc[4][5];
+            const float *Qb = Qs + buf * RMAX * WC;
+            float acc[4][5];
 #pragma unroll
-                    for (int a = 0; a < 4; a++)
+            for (int a = 0; a < 4; a++)
 #pragma unroll
-                        for (int b = 0; b < 5; b++) acc[a][b] = 0.f;
+                for (int b = 0; b < 5; b++) acc[a][b] = 0.f;
 #pragma unroll 6
-                    for (int r = 0; r < R; r++) {
-                        const float4 av = *reinterpret_cast<const float4 *>(Ck + r * NS + 4 * ty);
-                        const float4 b4 = *reinterpret_cast<const float4 *>(Qs + r * WC + 4 * tx);
-                        const float bv[5] = {b4.x, b4.y, b4.z, b4.w, Qs[r * WC + 64 + tx]};
+            for (int r = 0; r < R; r++) {
+                const float4 av = *reinterpret_cast<const float4 *>(Ck + r * NS + 4 * ty);
+                const float4 b4 = *reinterpret_cast<const float4 *>(Qb + r * WC + 4 * tx);
+                const float bv[5] = {b4.x, b4.y, b4.z, b4.w, Qb[r * WC + 64 + tx]};
 #pragma unroll
-                        for (int b = 0; b < 5; b++) {
-                            acc[0][b] = fmaf(av.x, bv[b], acc[0][b]);
-                            acc[1][b] = fmaf(av.y, bv[b], acc[1][b]);
-                            acc[2][b] = fmaf(av.z, bv[b], acc[2][b]);
-                            acc[3][b] = fmaf(av.w, bv[b], acc[3][b]);
-                        }
-                    }
-#pragma unroll
-                    for (int a = 0; a < 4; a++) {
-                        float *g = Gs + (4 * ty + a) * GROW;
-                        *reinterpret_cast<float4 *>(g + 4 * tx) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
-                        g[64 + tx] = acc[a][4];
-                    }
+                for (int b = 0; b < 5; b++) {
+                    acc[0][b] = fmaf(av.x, bv[b], acc[0][b]);
+                    acc[1][b] = fmaf(av.y, bv[b], acc[1][b]);
+                    acc[2][b] = fmaf(av.z, bv[b], acc[2][b]);
+                    acc[3][b] = fmaf(av.w, bv[b], acc[3][b]);
                 }
-                __syncthreads();
-                // my bins j0 + jbeg + jj read columns c = i0 + j0 + jbeg + jj and c + 1 of the block
-                // (each column read once: the partner of bin jj is the first column of bin jj + 1)
-                const float *gr = Gs + n * GROW;
-                const int c0 = ik + j0 + jbeg - cb;
-                if (c0 >= 0 && c0 + JG <= WSTEP && jbeg + JG <= Jc) {
-                    // the usual case: all my bins and their partners lie in this block
-                    const float *src = gr + c0;
-                    float vprev = src[0];
+            }
 #pragma unroll
-                    for (int jj = 0; jj < JG; jj++) {
-                        const float v = src[jj + 1];
-                        D[jj] = fmaf(omw, vprev, fmaf(w, v, D[jj]));
-                        vprev = v;
-                    }
-                } else {
-                    float vprev = (c0 >= 0 && c0 < WC) ? gr[c0] : 0.f;
+            for (int a = 0; a < 4; a++) {
+                float *gw = Gs + (4 * ty + a) * GROW;
+                *reinterpret_cast<float4 *>(gw + 4 * tx) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+                gw[64 + tx] = acc[a][4];
+            }
+        }
+        __syncthreads();
+        {
+            // my bins j0 + jbeg + jj read columns c = i0 + j0 + jbeg + jj and c + 1 of the block
+            // (each column read once: the partner of bin jj is the first column of bin jj + 1)
+            const float w = wtd(k), omw = 1.f - w;
+            const float *gr = Gs + n * GROW;
+            const int c0 = i0d(k) + j0 + jbeg - cb;
+            if (c0 >= 0 && c0 + JG <= WSTEP && jbeg + JG <= Jc) {
+                // the usual case: all my bins and their partners lie in this block
+                const float *src = gr + c0;
+                float vprev = src[0];
 #pragma unroll
-                    for (int jj = 0; jj < JG; jj++) {
-                        const int c = c0 + jj;
-                        const float v = (c + 1 >= 0 && c + 1 < WC) ? gr[c + 1] : 0.f;
-                        if (jbeg + jj < Jc && c >= 0 && c < WSTEP) D[jj] = fmaf(omw, vprev, fmaf(w, v, D[jj]));
-                        vprev = v;
-                    }
+                for (int jj = 0; jj < JG; jj++) {
+                    const float v = src[jj + 1];
+                    D[jj] = fmaf(omw, vprev, fmaf(w, v, D[jj]));
+                    vprev = v;
+                }
+            } else {
+                float vprev = (c0 >= 0 && c0 < WC) ? gr[c0] : 0.f;
+#pragma unroll
+                for (int jj = 0; jj < JG; jj++) {
+                    const int c = c0 + jj;
+                    const float v = (c + 1 >= 0 && c + 1 < WC) ? gr[c + 1] : 0.f;
+                    if (jbeg + jj < Jc && c >= 0 && c < WSTEP) D[jj] = fmaf(omw, vprev, fmaf(w, v, D[jj]));
+                    vprev = v;
                 }
             }
         }
-        // chunk complete
+        const int bj0 = j0;  // this block's chunk
+        j0 = nj0;
+        k = nk;
+        cb = ncb;
+        buf ^= 1;
+        if (j0 == bj0) continue;
+        // chunk bj0 complete
         if (pp.dm.on) {
             // ln F(D_j, A) of the chunk's bins: one Chebyshev interpolant per sample through 12 table
             // values (3 per thread; the sample's four threads are consecutive lanes), or per-bin
@@ -213,7 +249,7 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
             for (int i = 0; i < 3; i++) fv[i] = rg.fit ? ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, 3 * g + i)) : 0.f;
             float f[ILE_DM_NODES];
 #pragma unroll
-            for (int k = 0; k < ILE_DM_NODES; k++) f[k] = __shfl_sync(0xffffffffu, fv[k % 3], (lane & ~3) | (k / 3));
+            for (int q = 0; q < ILE_DM_NODES; q++) f[q] = __shfl_sync(0xffffffffu, fv[q % 3], (lane & ~3) | (q / 3));
             if (rg.fit) {
                 float c[ILE_DM_NODES];
                 ile_dm_coeffs(f, c);
@@ -229,7 +265,7 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
         if (full_grid) {
             if (valid) {
                 const double An = pp.dm.on ? 0.0 : (double)A;
-                const int64_t o = (int64_t)(perm ? perm[p] : p) * Nt + j0 + jbeg;
+                const int64_t o = (int64_t)(perm ? perm[p] : p) * Nt + bj0 + jbeg;
 #pragma unroll
                 for (int jj = 0; jj < JG; jj++)
                     if (jbeg + jj < Jc) out[o + jj] = (double)D[jj] - An;
@@ -267,7 +303,7 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
     }
 }
 
-size_t plain_smem() { return sizeof(float) * ((size_t)ILE_MAX_DET * RMAX * NS + RMAX * WC + (size_t)NS * GROW); }
+size_t plain_smem() { return sizeof(float) * ((size_t)ILE_MAX_DET * RMAX * NS + 2 * RMAX * WC + (size_t)NS * GROW); }
 
 }  // namespace
 

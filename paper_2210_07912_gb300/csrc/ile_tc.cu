@@ -29,9 +29,10 @@ using namespace ile_tc;
 namespace {
 
 constexpr int TILE = 128;     // samples per CTA = MMA M = TMEM lanes
-constexpr int NWMAX = 256;    // max MMA N (columns per window)
-constexpr int JCH = 128;      // window bins per chunk
-constexpr uint32_t TMEM_COLS = 256;
+constexpr int NWMAX = 80;     // max MMA N (columns per window)
+constexpr int JCH = 64;       // window bins per chunk
+constexpr uint32_t TMEM_COLS = 128;  // power of two >= NWMAX rounded up to the 32-column loads
+constexpr int TPAD = 256;     // columns of the tiled operand past T_ext (room for any window)
 constexpr int WAIT_SPINS = 1 << 20;
 
 template <bool BF16>
@@ -55,12 +56,17 @@ struct TcSmem {
     uint64_t bar;
     uint32_t tmem_base;
     int lohi[2][ILE_MAX_DET];
-    int i0[ILE_MAX_DET][TILE];
-    float w[ILE_MAX_DET][TILE];
+};
+
+// Per-detector value held in registers (selects instead of a dynamically indexed local array).
+template <typename T>
+struct Det {
+    T v0, v1, v2, v3;
+    __device__ T operator()(int k) const { return k == 0 ? v0 : k == 1 ? v1 : k == 2 ? v2 : v3; }
 };
 
 template <bool BF16>
-__global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__ PointParams pp,
+__global__ void __launch_bounds__(TILE, 2) ile_tc_kernel(const __grid_constant__ PointParams pp,
                                                         const uint4 *__restrict__ Qhi, const uint4 *__restrict__ Qlo,
                                                         int TP, int KP, IleScratch s, const int *__restrict__ perm,
                                                         int64_t N, double *__restrict__ out, int full_grid,
@@ -86,19 +92,25 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
         mbar_init(&sm.bar, 1);
         mbar_init_fence();
     }
-    for (int k = 0; k < K; k++) {
+    int i0v[ILE_MAX_DET];
+    float wv[ILE_MAX_DET];
+#pragma unroll
+    for (int k = 0; k < ILE_MAX_DET; k++) {
         const int64_t q = valid ? p : p0;
-        sm.i0[k][t] = s.I0[(int64_t)k * N + q];
-        sm.w[k][t] = valid ? s.W[(int64_t)k * N + q] : 0.f;
+        i0v[k] = k < K ? s.I0[(int64_t)k * N + q] : 0;
+        wv[k] = (k < K && valid) ? s.W[(int64_t)k * N + q] : 0.f;
     }
+    const Det<int> i0d{i0v[0], i0v[1], i0v[2], i0v[3]};
+    const Det<float> wd{wv[0], wv[1], wv[2], wv[3]};
     if (t < 2 * ILE_MAX_DET) sm.lohi[t / ILE_MAX_DET][t % ILE_MAX_DET] = (t < ILE_MAX_DET) ? 0x7fffffff : -0x7fffffff;
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = sm.tmem_base;
-    for (int k = 0; k < K; k++) {
-        int v = sm.i0[k][t];
-        int lo = v, hi = v;
+#pragma unroll
+    for (int k = 0; k < ILE_MAX_DET; k++) {
+        if (k >= K) break;
+        int lo = i0v[k], hi = i0v[k];
         for (int o = 16; o; o >>= 1) {
             lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
             hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
@@ -139,8 +151,8 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
                 Ahi[kc * TILE + t] = h;
                 Alo[kc * TILE + t] = l;
             }
-            const int i0 = sm.i0[k][t];
-            const float w = sm.w[k][t];
+            const int i0 = i0d(k);
+            const float w = wd(k);
             const int col_lo = sm.lohi[0][k] + j0;
             const int col_hi = sm.lohi[1][k] + j0 + Jc;  // last column used (inclusive)
             for (int wbeg = col_lo; wbeg <= col_hi && !timed_out; wbeg += NWMAX) {
@@ -196,8 +208,10 @@ __global__ void __launch_bounds__(TILE, 1) ile_tc_kernel(const __grid_constant__
                     for (int q = 0; q < 32; q++) {
                         const float g = __uint_as_float(r[q]);
                         const int jq = jbase + q;
-                        if (jq >= 0 && jq < Jc) Dt[jq * TILE + t] += (1.f - w) * g;
-                        if (jq >= 1 && jq <= Jc) Dt[(jq - 1) * TILE + t] += w * g;
+                        // columns at or past nw belong to the next window (or lie past the last one)
+                        const bool col = cb + q < nw;
+                        if (col && jq >= 0 && jq < Jc) Dt[jq * TILE + t] += (1.f - w) * g;
+                        if (col && jq >= 1 && jq <= Jc) Dt[(jq - 1) * TILE + t] += w * g;
                     }
                 }
                 fence_before();
@@ -328,7 +342,7 @@ int ile_tc_kpad(int prec, int M) {
 
 // Time columns of the tiled operand: T_ext plus room for a full window past the end, then the
 // ILE_QCOLS quadratic-term columns (used by the BF16X3 fused kernel) at column tpad - ILE_QCOLS.
-int ile_tc_tpad(int T_ext) { return ((T_ext + NWMAX + 16 + 7) & ~7) + ILE_QCOLS; }
+int ile_tc_tpad(int T_ext) { return ((T_ext + TPAD + 16 + 7) & ~7) + ILE_QCOLS; }
 
 size_t ile_tc_q_bytes(int prec, int K, int M, int T_ext) {
     const int KP = ile_tc_kpad(prec, M);

@@ -427,10 +427,11 @@ typedef struct {
  *   ile_batch_config: set the fused kernel's B-ring depth (2..4, if it fits in shared memory),
  *     window width and CTA count by hand.
  *   ile_batch_tune: autotuner -- runs one iteration to have samples, then times the fused
- *     kernel over that iteration's work items (a warm-up launch and reps timed launches per
- *     candidate; reps >= 3 recommended): every window width nwcol on an 8-column grid over the
- *     admissible range (its two ends included) at the deepest B ring that fits, then each
- *     shallower ring at the best width; keeps the fastest (BF16X3 only; else ILE_E_STATE).  The
+ *     kernel over that iteration's work items (a timed warm-up launch per candidate, then reps
+ *     timed launches unless the warm-up already took more than twice the best time; reps >= 3
+ *     recommended): every window width nwcol on an 8-column grid over the admissible range (its
+ *     two ends included, widest first) at the deepest B ring that fits, then each shallower ring
+ *     at the best width; keeps the fastest (BF16X3 only; else ILE_E_STATE).  The
  *     grid stays one persistent CTA per SM (the kernel holds a whole SM).  The sampler advances
  *     by one iteration: call ile_batch_reset before the run that counts.
  */

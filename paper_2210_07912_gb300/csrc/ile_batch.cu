@@ -596,25 +596,32 @@ ile_status ile_batch_tune(ile_batch *b, int reps, ile_batch_tuning *out) {
     float best = 1e30f;
     int bNB = b->NB, bW = b->nwcol, n_tried = 0;
     auto time_one = [&](int NB, int W) -> cudaError_t {
-        // warm-up launch, then `reps` timed launches (each refills the loud-sample list: its count is
-        // reset first)
-        cudaError_t e = cudaMemsetAsync(b->loud, 0, sizeof(int), b->stream);
-        if (e == cudaSuccess)
-            e = ile_launch_tc2_batch(b->pts, b->items, b->n_items, b->LK, b->LM, b->LKP, NB, W, sms, b->flags,
-                                     b->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-        for (int r = 0; r < reps && e == cudaSuccess; r++) {
-            e = cudaMemsetAsync(b->loud, 0, sizeof(int), b->stream);
+        // a timed warm-up launch; a candidate already slower than twice the best is recorded at that
+        // time, the others by `reps` more timed launches (each launch refills the loud-sample list:
+        // its count is reset first)
+        auto launch = [&]() {
+            cudaError_t e = cudaMemsetAsync(b->loud, 0, sizeof(int), b->stream);
             if (e == cudaSuccess)
                 e = ile_launch_tc2_batch(b->pts, b->items, b->n_items, b->LK, b->LM, b->LKP, NB, W, sms, b->flags,
                                          b->stream);
-        }
+            return e;
+        };
+        float ms = 0.f;
+        cudaError_t e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) e = launch();
         if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         if (e != cudaSuccess) return e;
-        ms /= reps;
+        if (ms <= 2.f * best) {
+            e = cudaEventRecord(e0, b->stream);
+            for (int r = 0; r < reps && e == cudaSuccess; r++) e = launch();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) return e;
+            ms /= reps;
+        }
         if (out && n_tried < ILE_TUNE_MAX) {
             out->tried_nb[n_tried] = NB;
             out->tried_nwcol[n_tried] = W;
@@ -628,11 +635,13 @@ ile_status ile_batch_tune(ile_batch *b, int reps, ile_batch_tuning *out) {
         }
         return cudaSuccess;
     };
+    // widest first (the usual optimum), so that narrow windows, whose multi-window jobs cost several
+    // times more, are usually dismissed after their warm-up launch
     cudaError_t e = cudaSuccess;
-    for (int W = lo; e == cudaSuccess; W += 8) {
-        W = std::min(W, hi);
+    for (int W = hi; e == cudaSuccess; W -= 8) {
+        W = std::max(W, lo);
         e = time_one(nb_max, W);
-        if (W == hi) break;
+        if (W == lo) break;
     }
     const int wbest = bW;
     for (int NB = 2; NB < nb_max && e == cudaSuccess; NB++) e = time_one(NB, wbest);

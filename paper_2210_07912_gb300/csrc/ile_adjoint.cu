@@ -372,7 +372,11 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
         // then starts the bulk copies of the next chunk's B (hi, lo) into the other B buffer, so
         // that they land while that chunk's A is built.  A is reused once the chunk's MMAs have
         // completed.  Waits are bounded: a wait that runs out sets the timeout flag and tc_abort,
-        // after which no more MMAs are issued (every thread still passes every barrier).
+        // after which no more MMAs are issued (every thread still passes every barrier).  After an
+        // abort the other threads skip the MMA waits and may rewrite A while the last committed MMA
+        // still reads it: from then on A, B and TMEM hold garbage by design, the call's outputs are
+        // discarded and only ILE_E_TIMEOUT is returned; the drain wait on the last commit before
+        // TMEM is released stays.
         const int nn = tid & (TC_NS - 1), q0 = tid >> 6;
         uint8_t *tcb = reinterpret_cast<uint8_t *>(U1);
         uint4 *Ah = reinterpret_cast<uint4 *>(tcb), *Al = Ah + AM_A_BYTES / 16;

@@ -39,6 +39,16 @@ struct PerDetI {
     __device__ int operator()(int k) const { return k == 0 ? v0 : k == 1 ? v1 : k == 2 ? v2 : v3; }
 };
 
+// Packed FP32 fma of two lanes (fma.rn.f32x2: each lane an IEEE round-to-nearest fma).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
 // Asynchronous 4-byte global -> shared copy (zero-filled when `in` is false; src stays a valid
 // address either way), and its group commit / wait.
 __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool in) {
@@ -168,29 +178,33 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
         {
             const float *Ck = Cs + k * RMAX * NS;
             const float *Qb = Qs + buf * RMAX * WC;
-            float acc[4][5];
+            // accumulators in sample pairs (4 ty, 4 ty + 1) and (4 ty + 2, 4 ty + 3): one packed FP32
+            // FMA (two IEEE fmas, the same results as two fmaf) per pair and column
+            float2 acc[2][5];
 #pragma unroll
-            for (int a = 0; a < 4; a++)
+            for (int h = 0; h < 2; h++)
 #pragma unroll
-                for (int b = 0; b < 5; b++) acc[a][b] = 0.f;
+                for (int b = 0; b < 5; b++) acc[h][b] = make_float2(0.f, 0.f);
 #pragma unroll 6
             for (int r = 0; r < R; r++) {
                 const float4 av = *reinterpret_cast<const float4 *>(Ck + r * NS + 4 * ty);
                 const float4 b4 = *reinterpret_cast<const float4 *>(Qb + r * WC + 4 * tx);
                 const float bv[5] = {b4.x, b4.y, b4.z, b4.w, Qb[r * WC + 64 + tx]};
+                const float2 a01 = make_float2(av.x, av.y), a23 = make_float2(av.z, av.w);
 #pragma unroll
                 for (int b = 0; b < 5; b++) {
-                    acc[0][b] = fmaf(av.x, bv[b], acc[0][b]);
-                    acc[1][b] = fmaf(av.y, bv[b], acc[1][b]);
-                    acc[2][b] = fmaf(av.z, bv[b], acc[2][b]);
-                    acc[3][b] = fmaf(av.w, bv[b], acc[3][b]);
+                    const float2 bb = make_float2(bv[b], bv[b]);
+                    acc[0][b] = ffma2(a01, bb, acc[0][b]);
+                    acc[1][b] = ffma2(a23, bb, acc[1][b]);
                 }
             }
 #pragma unroll
-            for (int a = 0; a < 4; a++) {
-                float *gw = Gs + (4 * ty + a) * GROW;
-                *reinterpret_cast<float4 *>(gw + 4 * tx) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
-                gw[64 + tx] = acc[a][4];
+            for (int h = 0; h < 2; h++) {
+                float *g0 = Gs + (4 * ty + 2 * h) * GROW, *g1 = g0 + GROW;
+                *reinterpret_cast<float4 *>(g0 + 4 * tx) = make_float4(acc[h][0].x, acc[h][1].x, acc[h][2].x, acc[h][3].x);
+                *reinterpret_cast<float4 *>(g1 + 4 * tx) = make_float4(acc[h][0].y, acc[h][1].y, acc[h][2].y, acc[h][3].y);
+                g0[64 + tx] = acc[h][4].x;
+                g1[64 + tx] = acc[h][4].y;
             }
         }
         __syncthreads();

@@ -143,6 +143,33 @@ __device__ __forceinline__ float ile_dmarg_lnF(const DmargParams &dm, const Dmar
     return big ? fmaf(a, xs, -q.b * xs * xs) + h : h;  // table 2 holds ln F - E*
 }
 
+// Packed FP32 arithmetic on two lanes (add/mul/fma .rn.f32x2: each lane rounds as its scalar
+// IEEE round-to-nearest counterpart, so results equal two scalar operations).
+__device__ __forceinline__ float2 ile_f2op_fma(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 ile_f2op_add(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " add.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 ile_f2op_mul(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " mul.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
 // ---- Distance-marginalised window bins without per-bin table reads.  For one sample (b fixed)
 // and one chunk of window bins, ln F(., b) over the chunk's data-term range [a_min, a_max] is its
 // degree-11 Chebyshev interpolant through the table values at the 12 Chebyshev points of that
@@ -242,6 +269,15 @@ __device__ __forceinline__ float ile_dm_eval(const float (&m)[ILE_DM_NODES], con
     float v = m[ILE_DM_NODES - 1];
 #pragma unroll
     for (int i = ILE_DM_NODES - 2; i >= 0; i--) v = fmaf(v, t, m[i]);
+    return v;
+}
+
+// the same for two bins at once (packed FP32: the results equal two ile_dm_eval calls)
+__device__ __forceinline__ float2 ile_dm_eval2(const float (&m)[ILE_DM_NODES], const DmRange &r, float2 a) {
+    const float2 t = ile_f2op_mul(ile_f2op_add(a, make_float2(-r.mid, -r.mid)), make_float2(r.inv_half, r.inv_half));
+    float2 v = make_float2(m[ILE_DM_NODES - 1], m[ILE_DM_NODES - 1]);
+#pragma unroll
+    for (int i = ILE_DM_NODES - 2; i >= 0; i--) v = ile_f2op_fma(v, t, make_float2(m[i], m[i]));
     return v;
 }
 

@@ -39,16 +39,6 @@ struct PerDetI {
     __device__ int operator()(int k) const { return k == 0 ? v0 : k == 1 ? v1 : k == 2 ? v2 : v3; }
 };
 
-// Packed FP32 fma of two lanes (fma.rn.f32x2: each lane an IEEE round-to-nearest fma).
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-    float2 d;
-    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
-        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
-
 // Asynchronous 4-byte global -> shared copy (zero-filled when `in` is false; src stays a valid
 // address either way), and its group commit / wait.
 __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool in) {
@@ -194,8 +184,8 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
 #pragma unroll
                 for (int b = 0; b < 5; b++) {
                     const float2 bb = make_float2(bv[b], bv[b]);
-                    acc[0][b] = ffma2(a01, bb, acc[0][b]);
-                    acc[1][b] = ffma2(a23, bb, acc[1][b]);
+                    acc[0][b] = ile_f2op_fma(a01, bb, acc[0][b]);
+                    acc[1][b] = ile_f2op_fma(a23, bb, acc[1][b]);
                 }
             }
 #pragma unroll
@@ -267,9 +257,18 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
             if (rg.fit) {
                 float c[ILE_DM_NODES];
                 ile_dm_coeffs(f, c);
+                if (jbeg + JG <= Jc) {
 #pragma unroll
-                for (int jj = 0; jj < JG; jj++)
-                    if (jbeg + jj < Jc) D[jj] = ile_dm_eval(c, rg, D[jj]);
+                    for (int jj = 0; jj < JG; jj += 2) {
+                        const float2 v = ile_dm_eval2(c, rg, make_float2(D[jj], D[jj + 1]));
+                        D[jj] = v.x;
+                        D[jj + 1] = v.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < JG; jj++)
+                        if (jbeg + jj < Jc) D[jj] = ile_dm_eval(c, rg, D[jj]);
+                }
             } else {
 #pragma unroll
                 for (int jj = 0; jj < JG; jj++)

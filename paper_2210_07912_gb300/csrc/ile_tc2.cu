@@ -670,9 +670,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             f[3 * h + 2] = aq_s[t];
                         }
                         ile_dm_coeffs(f, c);
+                        if (jbeg + JG <= Jc) {
 #pragma unroll
-                        for (int jj = 0; jj < JG; jj++)
-                            if (jbeg + jj < Jc) D[jj] = ile_dm_eval(c, rg, D[jj]);
+                            for (int jj = 0; jj < JG; jj += 2) {
+                                const float2 v = ile_dm_eval2(c, rg, make_float2(D[jj], D[jj + 1]));
+                                D[jj] = v.x;
+                                D[jj + 1] = v.y;
+                            }
+                        } else {
+#pragma unroll
+                            for (int jj = 0; jj < JG; jj++)
+                                if (jbeg + jj < Jc) D[jj] = ile_dm_eval(c, rg, D[jj]);
+                        }
                     } else {
 #pragma unroll
                         for (int jj = 0; jj < JG; jj++)

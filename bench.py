@@ -158,6 +158,49 @@ def loud_error(ile, S, local, prec, rho2s=(1e3, 1e4)):
     return out
 
 
+def error_vs_data_term(ile, S, local, precs=("bf16x3", "tf32x3", "fp32"), n=1024):
+    """|lnL_t - oracle| of each precision binned by the sample's largest |data term|
+    max_j |Re sum_k (D_ref/D) conj(F_k Y) Q_k(j)|: the benchmarked point's prior samples plus
+    injections of <h0|h0> = 1e2, 1e3, 1e4 (n samples near each injection, n from the prior).  For
+    every bin: the raw single-precision path (FP64 refinement of loud samples off) and the shipped
+    path (refinement on)."""
+    import oracle
+    cases = [(S.workload_point(WORKLOAD), S.workload_samples(WORKLOAD, 2 * n))]
+    for rho2 in (1e2, 1e3, 1e4):
+        point, theta0 = oracle.loud_point(S, S.SEED_BASE + 90, rho2)
+        cases.append((point, oracle.loud_samples(S, np.random.default_rng(int(rho2) + 5), theta0, n, n)))
+    edges = [0.0, 1.0, 10.0, 100.0, 1e3, 1e4, 1e5]
+    mags, refs = [], []
+    for point, th in cases:
+        mag = np.empty(th.shape[1])
+        for i in range(th.shape[1]):
+            _, data, _ = oracle.lnL_grid(point, th[:, i])
+            mag[i] = np.abs(data).max()
+        mags.append(mag)
+        refs.append(oracle.lnL_t(point, th))
+    mag = np.concatenate(mags)
+    bins = np.digitize(mag, edges[1:-1])
+    out = {"bin_edges_abs_data_term": edges, "samples_per_bin": np.bincount(bins, minlength=len(edges) - 1).tolist()}
+    for prec in precs:
+        res = {}
+        for refine in (False, True):
+            errs = []
+            for (point, th), ref in zip(cases, refs):
+                ctx = ile.Context(local, None, prec)
+                ctx.set_data(point)
+                ctx.set_refine(refine)
+                errs.append(np.abs(ctx.eval(th) - ref))
+                ctx.close()
+            err = np.concatenate(errs)
+            res["refined" if refine else "raw"] = {
+                "max_abs_dlnL_t": [float(err[bins == b].max()) if np.any(bins == b) else None
+                                   for b in range(len(edges) - 1)],
+                "rms_dlnL_t": [float(np.sqrt(np.mean(err[bins == b] ** 2))) if np.any(bins == b) else None
+                               for b in range(len(edges) - 1)]}
+        out[prec] = res
+    return out
+
+
 def cpu_baseline(point, seconds=12.0):
     cores = os.cpu_count() or 1
     n = cpu_sample_size(point, seconds, cores)
@@ -555,6 +598,7 @@ def main():
             line["cpu_baseline"] = cpu_baseline(point)
             line["error_vs_oracle"] = oracle_error(ctx, point)
             line["error_vs_oracle_loud"] = loud_error(ile, S, local, args.prec)
+            line["split_error_vs_data_term"] = error_vs_data_term(ile, S, local)
         if not args.no_adjoint:
             line["adjoint"] = adjoint_bench(ile, S, local, stream, flush, prec=args.prec)
         if not args.no_dmarg:

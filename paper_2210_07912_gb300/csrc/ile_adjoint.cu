@@ -1130,36 +1130,42 @@ __global__ void __launch_bounds__(256)
     for (int64_t c0 = nb; c0 < ne; c0 += UVC) {
         const int nc = (int)min((int64_t)UVC, ne - c0);
         __syncthreads();
-        if (tid < UVC) {
-            const int64_t n = c0 + tid;
-            float cpow[9], spow[9];
-            float Fr[ILE_MAX_DET], Fi[ILE_MAX_DET], x0[ILE_MAX_DET];
-            float g = 0.f, sc2 = 0.f;
-            float ra = 0.f, dec = 0.f, psi = 0.f, iota = 0.f, phi = 0.f;
-            if (tid < nc) {
-                ra = (float)samples[n];
-                dec = (float)samples[N + n];
-                psi = (float)samples[2 * N + n];
-                iota = (float)samples[3 * N + n];
-                phi = (float)samples[4 * N + n];
-                const float sc = pp.d_ref / (float)samples[5 * N + n];
-                sc2 = sc * sc;
-                g = (float)g_lnL[n];
-            }
-            ile_sample_geometry(pp, ra, dec, psi, 0.f, Fr, Fi, x0);
+        {
+            // four threads per sample of the chunk: each forms the harmonics of modes q, q + 4, ...;
+            // the first also the sample's detector weights
+            const int j = tid >> 2, q = tid & 3;
+            const int64_t n = c0 + j;
+            const bool ok = j < nc;
+            const float iota = ok ? (float)samples[3 * N + n] : 0.f, phi = ok ? (float)samples[4 * N + n] : 0.f;
+            float cpow[9], spow[9], er[5], ei[5];
             ile_half_angle_powers(iota, cpow, spow);
-            for (int a = 0; a < M; a++) {
+            ile_phase_powers(phi, er, ei);
+#pragma unroll 1
+            for (int a = q; a < M; a += 4) {
                 float yr, yi;
-                ile_sylm(pp.mode[a], cpow, spow, phi, yr, yi);
-                Yc[tid][a] = make_float2(yr, yi);
+                ile_sylm_fast(pp.mode[a], cpow, spow, er, ei, yr, yi);
+                Yc[j][a] = make_float2(yr, yi);
             }
-            const float wgt = g * sc2;
+            if (q == 0) {
+                float Fr[ILE_MAX_DET], Fi[ILE_MAX_DET], x0[ILE_MAX_DET];
+                float g = 0.f, sc2 = 0.f, ra = 0.f, dec = 0.f, psi = 0.f;
+                if (ok) {
+                    ra = (float)samples[n];
+                    dec = (float)samples[N + n];
+                    psi = (float)samples[2 * N + n];
+                    const float sc = pp.d_ref / (float)samples[5 * N + n];
+                    sc2 = sc * sc;
+                    g = (float)g_lnL[n];
+                }
+                ile_sample_geometry(pp, ra, dec, psi, 0.f, Fr, Fi, x0);
+                const float wgt = g * sc2;
 #pragma unroll
-            for (int k = 0; k < ILE_MAX_DET; k++) {
-                if (k < K) {
-                    Wc[tid][3 * k] = wgt * (Fr[k] * Fr[k] + Fi[k] * Fi[k]);
-                    Wc[tid][3 * k + 1] = wgt * (Fr[k] * Fr[k] - Fi[k] * Fi[k]);
-                    Wc[tid][3 * k + 2] = wgt * 2.f * Fr[k] * Fi[k];
+                for (int k = 0; k < ILE_MAX_DET; k++) {
+                    if (k < K) {
+                        Wc[j][3 * k] = wgt * (Fr[k] * Fr[k] + Fi[k] * Fi[k]);
+                        Wc[j][3 * k + 1] = wgt * (Fr[k] * Fr[k] - Fi[k] * Fi[k]);
+                        Wc[j][3 * k + 2] = wgt * 2.f * Fr[k] * Fi[k];
+                    }
                 }
             }
         }
@@ -1197,8 +1203,10 @@ __global__ void __launch_bounds__(256)
 // independent (Re, Im) pair: d/dRe = -1/4 Re(sum), d/dIm = +1/4 Im(sum).
 __global__ void adj_guv_reduce_kernel(int K, int M, int nblk, const float *__restrict__ part, double *__restrict__ gU,
                                       double *__restrict__ gV) {
+    // one warp per entry (k, p): lane-strided FP64 sums over the blocks, then a fixed xor tree
+    // (deterministic; every lane ends with the same sums)
     const int P = M * (M + 1) / 2;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (i >= K * P) return;
     const int k = i / P, p = i - k * P;
     int a = 0, q = p;
@@ -1208,8 +1216,18 @@ __global__ void adj_guv_reduce_kernel(int K, int M, int nblk, const float *__res
     }
     const int b = a + q;
     double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int blk = 0; blk < nblk; blk++)
-        for (int c = 0; c < 4; c++) s[c] += (double)part[(((int64_t)blk * K + k) * P + p) * 4 + c];
+    for (int blk = lane; blk < nblk; blk += 32) {
+        const float4 v = *reinterpret_cast<const float4 *>(part + (((int64_t)blk * K + k) * P + p) * 4);
+        s[0] += (double)v.x;
+        s[1] += (double)v.y;
+        s[2] += (double)v.z;
+        s[3] += (double)v.w;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 4; c++) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+    if (lane != 0) return;
     const size_t ab = 2 * (((size_t)k * M + a) * M + b), ba = 2 * (((size_t)k * M + b) * M + a);
     if (gU) {
         gU[ab] = -0.25 * s[0];
@@ -1338,6 +1356,6 @@ cudaError_t ile_launch_grad_uv(const PointParams &pp, const double *samples, con
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int P = pp.M * (pp.M + 1) / 2;
-    adj_guv_reduce_kernel<<<(pp.K * P + 255) / 256, 256, 0, st>>>(pp.K, pp.M, nblk, part, gU, gV);
+    adj_guv_reduce_kernel<<<(pp.K * P * 32 + 255) / 256, 256, 0, st>>>(pp.K, pp.M, nblk, part, gU, gV);
     return cudaGetLastError();
 }

@@ -123,3 +123,25 @@ def test_dmarg_switching_and_errors(ile, orc):
     c.set_distance_marginalization(True, D_MIN, D_MAX)
     c.set_data(point)  # a new point turns it off
     np.testing.assert_allclose(c.eval(th), plain, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_dmarg_ragged_window_and_both_epilogue_paths(ile, orc, prec):
+    """A window of 200 bins (three full 64-bin chunks and a ragged chunk of 8), on a quiet point
+    (every chunk's data terms within the interpolated range) and on a 25x louder one (most chunks
+    wider: per-bin table reads), per sample and per bin against the oracle's quadrature."""
+    for gain in (1.0, 25.0):
+        point = _scaled(S.make_point(S.SEED_BASE + 83, 3, 9, 200, spectrum="decay"), gain)
+        th = S.workload_samples(S.SMALL, 256)
+        c = _ctx(ile, point, prec)
+        got = c.eval(th)
+        ref = orc.lnL_dmarg(point, th, D_MIN, D_MAX)
+        assert np.abs(got - ref).max() < 1e-3, (prec, gain, np.abs(got - ref).max())
+        grid = c.eval(th[:, :12], grid=True)
+        for n in range(12):
+            t = th[:, n].copy()
+            t[5] = point.d_ref
+            _, data, A = orc.lnL_grid(point, t)
+            for j in list(range(0, 200, 9)) + [192, 195, 199]:
+                want = orc.dmarg_lnF(data[j], A, D_MIN, D_MAX, point.d_ref)
+                assert abs(grid[n, j] - want) < 1e-3 + 2e-6 * abs(want), (prec, gain, n, j)

@@ -65,12 +65,19 @@ constexpr int TC_BUF = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
 __host__ __device__ constexpr int adj_qt_cols(int T) { return T + AM_COLS; }
 
 // d^l_{m,2}(iota) and its derivative d/diota, from the Wigner polynomial in c = cos(iota/2),
-// s = sin(iota/2): d/diota c^p s^q = (q c^(p+1) s^(q-1) - p c^(p-1) s^(q+1)) / 2.
-__device__ __forceinline__ void sylm_and_diota(const ModeTab &md, const float *cpow, const float *spow, float phi,
-                                               float &yr, float &yi, float &dr, float &di) {
+// s = sin(iota/2): d/diota c^p s^q = (q c^(p+1) s^(q-1) - p c^(p-1) s^(q+1)) / 2.  Every power is
+// at a compile-time index (registers, no local memory): the exponents of mode (l, m) are those the
+// host builder lists (ile_wigner_q, q the power of s, p = 2l - q), e^{i m phi} comes from powers
+// of e^{i phi}.
+template <int L, int MM>
+__device__ __forceinline__ void sylm_diota_lm(const ModeTab &md, const float (&cpow)[10], const float (&spow)[10],
+                                              const float (&er)[5], const float (&ei)[5], float &yr, float &yi,
+                                              float &dr, float &di) {
+    constexpr WignerQ w = ile_wigner_q(L, MM);
     float amp = 0.f, damp = 0.f;
-    for (int t = 0; t < md.nterms; t++) {
-        const int p = md.t[t].p, q = md.t[t].q;
+#pragma unroll
+    for (int t = 0; t < w.n; t++) {
+        const int q = w.q[t], p = 2 * L - q;
         const float cf = md.t[t].coef;
         amp += cf * cpow[p] * spow[q];
         float d = 0.f;
@@ -78,15 +85,33 @@ __device__ __forceinline__ void sylm_and_diota(const ModeTab &md, const float *c
         if (p > 0) d -= (float)p * cpow[p - 1] * spow[q + 1];
         damp += 0.5f * cf * d;
     }
-    float sn, cs;
-    sincosf((float)md.m * phi, &sn, &cs);
+    constexpr int AM = MM < 0 ? -MM : MM;
+    const float cs = er[AM], sn = MM < 0 ? -ei[AM] : ei[AM];
     yr = md.norm * amp * cs;
     yi = md.norm * amp * sn;
     dr = md.norm * damp * cs;
     di = md.norm * damp * sn;
 }
 
-__device__ __forceinline__ void half_angle_powers10(float iota, float *cpow, float *spow) {
+__device__ __forceinline__ void sylm_and_diota(const ModeTab &md, const float (&cpow)[10], const float (&spow)[10],
+                                               const float (&er)[5], const float (&ei)[5], float &yr, float &yi,
+                                               float &dr, float &di) {
+#define ADJ_LM(L, M)                                                     \
+    case (L - 2) * 9 + M + 4:                                            \
+        sylm_diota_lm<L, M>(md, cpow, spow, er, ei, yr, yi, dr, di);     \
+        return;
+    switch ((md.l - 2) * 9 + md.m + 4) {
+        ADJ_LM(2, -2) ADJ_LM(2, -1) ADJ_LM(2, 0) ADJ_LM(2, 1) ADJ_LM(2, 2)
+        ADJ_LM(3, -3) ADJ_LM(3, -2) ADJ_LM(3, -1) ADJ_LM(3, 0) ADJ_LM(3, 1) ADJ_LM(3, 2) ADJ_LM(3, 3)
+        ADJ_LM(4, -4) ADJ_LM(4, -3) ADJ_LM(4, -2) ADJ_LM(4, -1) ADJ_LM(4, 0) ADJ_LM(4, 1) ADJ_LM(4, 2)
+        ADJ_LM(4, 3) ADJ_LM(4, 4)
+        default:
+            yr = yi = dr = di = 0.f;  // 2 <= l <= 4 is checked when the point is set
+    }
+#undef ADJ_LM
+}
+
+__device__ __forceinline__ void half_angle_powers10(float iota, float (&cpow)[10], float (&spow)[10]) {
     float s, c;
     sincosf(0.5f * iota, &s, &c);
     cpow[0] = 1.f;
@@ -329,12 +354,13 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
         if (nn < ns) {
             const int64_t src = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
             const float iota = (float)samples[3 * N + src], phi = (float)samples[4 * N + src];
-            float cpow[10], spow[10];
+            float cpow[10], spow[10], er5[5], ei5[5];
             half_angle_powers10(iota, cpow, spow);
+            ile_phase_powers(phi, er5, ei5);
             const float *E = Es + nn * (RMAX + 1);
             for (int a = sub; a < M; a += SUB) {
                 float yr, yi, dr, di;
-                sylm_and_diota(pp.mode[a], cpow, spow, phi, yr, yi, dr, di);
+                sylm_and_diota(pp.mode[a], cpow, spow, er5, ei5, yr, yi, dr, di);
                 const float Er = E[a], Ei = E[M + a], mm = (float)pp.mode[a].m;
                 er += Er * yr + Ei * yi;
                 ei += Er * yi - Ei * yr;
@@ -607,11 +633,12 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     if (nn < ns) {
         const int64_t src = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
         const float iota = (float)samples[3 * N + src], phi = (float)samples[4 * N + src];
-        float cpow[10], spow[10];
+        float cpow[10], spow[10], er5[5], ei5[5];
         half_angle_powers10(iota, cpow, spow);
+        ile_phase_powers(phi, er5, ei5);
         float *y = Ys + nn * YLD;
         for (int a = sub; a < M; a += SUB)
-            sylm_and_diota(pp.mode[a], cpow, spow, phi, y[4 * a], y[4 * a + 1], y[4 * a + 2], y[4 * a + 3]);
+            sylm_and_diota(pp.mode[a], cpow, spow, er5, ei5, y[4 * a], y[4 * a + 1], y[4 * a + 2], y[4 * a + 3]);
     }
     __syncthreads();
     {

@@ -371,16 +371,23 @@ ile_status run_eval(ile_ctx *ctx, const double *dsamples, int64_t N, double *dou
         loud = LoudList{ctx->loud, ile_refine_threshold(prec), 0, ctx->cap};
         CK(cudaMemsetAsync(ctx->loud, 0, sizeof(int), ctx->stream));
     }
-    if (prec == ILE_PREC_BF16X3) {
+    const bool fused = prec == ILE_PREC_BF16X3 ||
+                       (prec == ILE_PREC_TF32X3 && ile_tc3_fits(pp.K, ile_tc_kpad(prec, pp.M)));
+    if (fused) {
         // fused kernel: S1, S2, S4 are computed inside the tensor-core kernel
         {
             StageScope t(ctx, 1, 3);
             CK(ile_launch_sort(pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));
         }
         StageScope t(ctx, 2);
-        CK(ile_launch_tc2(pp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ile_tc_tpad(pp.T_ext),
-                          ile_tc_kpad(prec, pp.M), ctx->UV, dsamples, ctx->perm, N, dout, nullptr, full_grid,
-                          loud, ctx->flags, ctx->stream));
+        if (prec == ILE_PREC_BF16X3)
+            CK(ile_launch_tc2(pp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ile_tc_tpad(pp.T_ext),
+                              ile_tc_kpad(prec, pp.M), ctx->UV, dsamples, ctx->perm, N, dout, nullptr, full_grid,
+                              loud, ctx->flags, ctx->stream));
+        else
+            CK(ile_launch_tc3(pp, ctx->Qtc[prec][0], ctx->Qtc[prec][1], ile_tc_tpad(pp.T_ext),
+                              ile_tc_kpad(prec, pp.M), dsamples, ctx->perm, N, dout, full_grid, loud, ctx->flags,
+                              ctx->stream));
     } else {
         {
             StageScope t(ctx, 1, 4);

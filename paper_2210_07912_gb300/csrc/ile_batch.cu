@@ -192,6 +192,14 @@ ile_status enqueue_iteration(ile_batch *b) {
             const double *smp = b->theta + ILE_NDIM * b->off[p];
             const int *prm = b->perm + b->off[p];
             double *out = b->lnl + b->off[p];
+            const int kp = ile_tc_kpad((int)b->prec, pp.M);
+            if (b->prec == ILE_PREC_TF32X3 && ile_tc3_fits(pp.K, kp)) {
+                // the fused TF32x3 kernel, as in a single-point run of this point
+                BK(ile_launch_tc3(pp, b->Qtc_hi + b->tc_off[p], b->Qtc_lo + b->tc_off[p], ile_tc_tpad(pp.T_ext), kp,
+                                  smp, prm, b->N[p], out, 0, LoudList{b->loud, thr, p, b->n_total}, b->flags,
+                                  b->stream));
+                continue;
+            }
             BK(ile_launch_prep(pp, b->UV + b->uv_off[p], smp, prm, b->N[p], b->s, b->flags, b->stream));
             if (b->prec == ILE_PREC_FP32)
                 BK(ile_launch_plain(pp, b->Qp + b->qp_off[p], b->s, prm, b->N[p], out, 0, LoudList{b->loud, thr, p, b->n_total},

@@ -509,7 +509,7 @@ struct RefinePoint {
     double *out;
 };
 
-// One intrinsic point as seen by the fused tensor-core kernel (ile_tc2.cu).
+// One intrinsic point as seen by the fused tensor-core kernel (ile_tc2_kernel.cuh).
 struct Tc2Point {
     PointParams pp;
     const void *Qhi, *Qlo;  // split operand tiles of Q (ile_tc.cu layout)
@@ -558,7 +558,11 @@ size_t ile_tc_q_bytes(int prec, int K, int M, int T_ext);
 // Columns appended to every detector's operand rows for the quadratic term (ile_tc.cu): the real
 // form of U_k and V_k, so that one extra MMA per detector gives U_k c and V_k c.
 #define ILE_QCOLS 128
-// quad: [K][KP][ILE_QCOLS] FP32 real-form block (BF16X3 layout only; may be null)
+// The TF32x3 fused kernel takes the same block in its first TF32_QCOLS columns, four blocks of 24
+// (column 24 (b % 4) + 4 (b / 4) + p; 24 = 4 ceil(ILE_MAX_MODES / 4)) instead of 32.
+#define TF32_QCOLS 96
+static_assert(4 * ((ILE_MAX_MODES + 3) / 4) <= TF32_QCOLS / 4, "TF32 quadratic-term blocks");
+// quad: [K][KPq][ILE_QCOLS] FP32 real-form block, KPq the BF16X3 operand rows (may be null)
 cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp, const float *quad, void *hi,
                                 void *lo, cudaStream_t st);
 cudaError_t ile_launch_tc(int prec, const PointParams &pp, const void *hi, const void *lo, IleScratch s,
@@ -569,6 +573,12 @@ cudaError_t ile_launch_tc(int prec, const PointParams &pp, const void *hi, const
 cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo, int TP, int KP, const float *UV,
                            const double *samples, const int *perm, int64_t N, double *out, float *grid_f,
                            int full_grid, LoudList loud, unsigned *flags, cudaStream_t st);
+// the same kernel in TF32x3 with its A operand in TMEM (ile_tc3.cu), for points with
+// ile_tc3_fits(K, KP) (KP the TF32 operand rows); full_grid 0 or 1
+bool ile_tc3_fits(int K, int KP);
+cudaError_t ile_launch_tc3(const PointParams &pp, const void *hi, const void *lo, int TP, int KP,
+                           const double *samples, const int *perm, int64_t N, double *out, int full_grid,
+                           LoudList loud, unsigned *flags, cudaStream_t st);
 // adjoint (ile_adjoint.cu)
 int ile_grad_q_splits(const PointParams &pp, int64_t N, int n_sm);
 int ile_grad_uv_blocks(int64_t N, int n_sm);

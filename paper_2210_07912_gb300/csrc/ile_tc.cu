@@ -300,21 +300,29 @@ __global__ void split_q_kernel(const float *__restrict__ Qp, int K, int R, int T
     }
 }
 
-// The quadratic-term block (real form of U_k, V_k; rows r = 2a + {Re, Im}) into columns
-// TP - ILE_QCOLS .. TP - 1 of the BF16 tiled layout.
-__global__ void split_quad_kernel(const float *__restrict__ quad, int K, int KP, int TP, uint4 *__restrict__ hi,
-                                  uint4 *__restrict__ lo) {
-    const int KC = KP / 8;
-    const int64_t total = (int64_t)K * KC * ILE_QCOLS;
+// The quadratic-term block (real form of U_k, V_k; rows r = 2a + {Re, Im}, row stride KPq of the
+// host array, four 32-column blocks) into columns TP - ILE_QCOLS .. of the tiled split layout: as
+// it is for BF16, and with the blocks packed to 24 columns (the first TF32_QCOLS columns) for TF32.
+template <bool BF16>
+__global__ void split_quad_kernel(const float *__restrict__ quad, int K, int KPq, int KP, int TP,
+                                  uint4 *__restrict__ hi, uint4 *__restrict__ lo) {
+    constexpr int EPC = Tc<BF16>::EPC;
+    constexpr int NCOL = BF16 ? ILE_QCOLS : TF32_QCOLS, BLK = NCOL / 4;
+    const int KC = KP / EPC;
+    const int64_t total = (int64_t)K * KC * NCOL;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int col = (int)(i % ILE_QCOLS);
-        const int kc = (int)((i / ILE_QCOLS) % KC);
-        const int k = (int)(i / ((int64_t)ILE_QCOLS * KC));
-        float v[8];
+        const int col = (int)(i % NCOL);
+        const int kc = (int)((i / NCOL) % KC);
+        const int k = (int)(i / ((int64_t)NCOL * KC));
+        const int src = (col / BLK) * (ILE_QCOLS / 4) + col % BLK;
+        float v[EPC];
 #pragma unroll
-        for (int e = 0; e < 8; e++) v[e] = quad[((int64_t)k * KP + kc * 8 + e) * ILE_QCOLS + col];
+        for (int e = 0; e < EPC; e++) {
+            const int r = kc * EPC + e;
+            v[e] = r < KPq ? quad[((int64_t)k * KPq + r) * ILE_QCOLS + src] : 0.f;
+        }
         uint4 h, l;
-        pack_chunk<true>(v, h, l);
+        pack_chunk<BF16>(v, h, l);
         const int t = TP - ILE_QCOLS + col;
         const int64_t o = (((int64_t)k * (TP / 8) + t / 8) * KC + kc) * 8 + (t & 7);
         hi[o] = h;
@@ -353,11 +361,15 @@ size_t ile_tc_q_bytes(int prec, int K, int M, int T_ext) {
 cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp, const float *quad, void *hi,
                                 void *lo, cudaStream_t st) {
     const int KP = ile_tc_kpad(prec, pp.M), TP = ile_tc_tpad(pp.T_ext);
+    // the host's real-form array has BF16 operand rows (KP rounded up to 16)
+    const int KPq = ile_tc_kpad(ILE_PREC_BF16X3, pp.M);
     if (prec == ILE_PREC_BF16X3) {
         split_q_kernel<true><<<256, 256, 0, st>>>(Qp, pp.K, 2 * pp.M, pp.T_ext, KP, TP, (uint4 *)hi, (uint4 *)lo);
-        if (quad) split_quad_kernel<<<64, 256, 0, st>>>(quad, pp.K, KP, TP, (uint4 *)hi, (uint4 *)lo);
-    } else
+        if (quad) split_quad_kernel<true><<<64, 256, 0, st>>>(quad, pp.K, KPq, KP, TP, (uint4 *)hi, (uint4 *)lo);
+    } else {
         split_q_kernel<false><<<256, 256, 0, st>>>(Qp, pp.K, 2 * pp.M, pp.T_ext, KP, TP, (uint4 *)hi, (uint4 *)lo);
+        if (quad) split_quad_kernel<false><<<64, 256, 0, st>>>(quad, pp.K, KPq, KP, TP, (uint4 *)hi, (uint4 *)lo);
+    }
     return cudaGetLastError();
 }
 

@@ -558,10 +558,10 @@ size_t ile_tc_q_bytes(int prec, int K, int M, int T_ext);
 // Columns appended to every detector's operand rows for the quadratic term (ile_tc.cu): the real
 // form of U_k and V_k, so that one extra MMA per detector gives U_k c and V_k c.
 #define ILE_QCOLS 128
-// The TF32x3 fused kernel takes the same block in its first TF32_QCOLS columns, four blocks of 24
-// (column 24 (b % 4) + 4 (b / 4) + p; 24 = 4 ceil(ILE_MAX_MODES / 4)) instead of 32.
-#define TF32_QCOLS 96
-static_assert(4 * ((ILE_MAX_MODES + 3) / 4) <= TF32_QCOLS / 4, "TF32 quadratic-term blocks");
+// The fused kernel's quadratic-term job reads the block packed into the first ILE_QUAD_NCOL of
+// those columns: four blocks of 24 (column 24 (b % 4) + 4 (b / 4) + p; 24 = 4 ceil(ILE_MAX_MODES / 4)).
+#define ILE_QUAD_NCOL 96
+static_assert(4 * ((ILE_MAX_MODES + 3) / 4) <= ILE_QUAD_NCOL / 4, "quadratic-term blocks");
 // quad: [K][KPq][ILE_QCOLS] FP32 real-form block, KPq the BF16X3 operand rows (may be null)
 cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp, const float *quad, void *hi,
                                 void *lo, cudaStream_t st);

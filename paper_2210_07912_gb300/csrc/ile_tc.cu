@@ -301,13 +301,13 @@ __global__ void split_q_kernel(const float *__restrict__ Qp, int K, int R, int T
 }
 
 // The quadratic-term block (real form of U_k, V_k; rows r = 2a + {Re, Im}, row stride KPq of the
-// host array, four 32-column blocks) into columns TP - ILE_QCOLS .. of the tiled split layout: as
-// it is for BF16, and with the blocks packed to 24 columns (the first TF32_QCOLS columns) for TF32.
+// host array, four 32-column blocks) into columns TP - ILE_QCOLS .. TP - ILE_QCOLS + ILE_QUAD_NCOL
+// of the tiled split layout, its blocks packed to ILE_QUAD_NCOL / 4 columns.
 template <bool BF16>
 __global__ void split_quad_kernel(const float *__restrict__ quad, int K, int KPq, int KP, int TP,
                                   uint4 *__restrict__ hi, uint4 *__restrict__ lo) {
     constexpr int EPC = Tc<BF16>::EPC;
-    constexpr int NCOL = BF16 ? ILE_QCOLS : TF32_QCOLS, BLK = NCOL / 4;
+    constexpr int NCOL = ILE_QUAD_NCOL, BLK = NCOL / 4;
     const int KC = KP / EPC;
     const int64_t total = (int64_t)K * KC * NCOL;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {

@@ -73,13 +73,22 @@ constexpr uint32_t SLEEP_NS = 10000;
 constexpr int RSTRIDE = 34;                // per-thread row: 32 staged columns + 2 (8-byte stores, half-warp conflict-free)
 constexpr float ILE_LOG2E_F = 1.4426950408889634f;  // log2(e)
 
-// TF32x3 keeps the A operand in TMEM: detector k's hi rows in columns [2 k KP, 2 k KP + KP), its lo
-// rows in the next KP columns (one TF32 element per column, row n in lane n), at most TF32_ACOL
-// columns; the two accumulator buffers of TF32_BW columns follow.
-constexpr int TF32_ACOL = 320;
-static_assert(TF32_QCOLS <= ((int)TMEM_COLS - TF32_ACOL) / NTB_TF32, "the quadratic-term job fits one buffer");
-constexpr int TF32_BW = ((int)TMEM_COLS - TF32_ACOL) / NTB_TF32;
-static_assert(TF32_BW % 16 == 0 && TF32_BW - 7 >= NWCOL_MIN && TF32_BW >= ILE_QCOLS / 2, "TF32x3 accumulator buffers");
+// Operand variants of the kernel: BF16x3 with the A operand in shared memory (the batched launch),
+// BF16x3 with A in TMEM, TF32x3 with A in TMEM.  A in TMEM: row n of the tile in lane n, detector
+// k's hi values then its lo values, KP values each, in consecutive 32-bit columns (two BF16 or one
+// TF32 value per column), at most acol_of columns; the accumulator buffers follow.
+enum : int { OP_BF16_SMEM = 0, OP_BF16_TMEM = 1, OP_TF32_TMEM = 2 };
+__host__ __device__ constexpr int acol_of(int op) { return op == OP_TF32_TMEM ? 320 : op == OP_BF16_TMEM ? 176 : 0; }
+__host__ __device__ constexpr int ntb_of(int op) { return op == OP_TF32_TMEM ? NTB_TF32 : NTB; }
+__host__ __device__ constexpr int bw_of(int op) {
+    return op == OP_BF16_SMEM ? NWIN : ((int)TMEM_COLS - acol_of(op)) / ntb_of(op) / 16 * 16;
+}
+// TMEM columns of a point's A operand (K detectors, KP values per row and part)
+__host__ __device__ constexpr int acols_needed(int op, int K, int KP) { return op == OP_TF32_TMEM ? 2 * K * KP : K * KP; }
+static_assert(bw_of(OP_TF32_TMEM) == 96 && bw_of(OP_BF16_TMEM) == 112, "accumulator buffers");
+static_assert(acol_of(OP_BF16_TMEM) + NTB * bw_of(OP_BF16_TMEM) <= (int)TMEM_COLS, "BF16x3 TMEM layout");
+static_assert(acol_of(OP_TF32_TMEM) + NTB_TF32 * bw_of(OP_TF32_TMEM) <= (int)TMEM_COLS, "TF32x3 TMEM layout");
+static_assert(ILE_QUAD_NCOL <= 96 && 96 - 7 >= NWCOL_MIN, "a quadratic-term job and a window fit every buffer");
 
 // 2^x with the SFU's base-2 exponential (approximate; flushes subnormal results to zero)
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -199,7 +208,7 @@ __device__ __forceinline__ const Tc2Point &work_item(const Tc2Point &one, const 
 // factors, window starts, iota, phi), computed by the prefetch warp from the parameters it gathers
 // through the sort permutation while the previous tile is in flight.  Before
 // the job loop the rows area holds the tile's harmonics table y [M][TILE] (float2).
-template <bool BATCH, bool DM, bool TF32>
+template <bool BATCH, bool DM, int OP>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ile_tc2_kernel(const __grid_constant__ Tc2Point one, const Tc2Point *__restrict__ pts,
                    const int2 *__restrict__ items, int64_t nitems, int LK, int LKC, int LNP, int NB, int nwcol,
@@ -207,16 +216,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     extern __shared__ __align__(1024) uint8_t dsm[];
     __shared__ Sm sm;
     (void)LNP;
-    // operand element layout: 16-byte chunks of 8 BF16 or 4 TF32 values; TF32x3 A operand in TMEM
+    // operand element layout: 16-byte chunks of 8 BF16 or 4 TF32 values; A in TMEM or shared memory
+    constexpr bool TF32 = OP == OP_TF32_TMEM, ATM = OP != OP_BF16_SMEM;
     constexpr int EPC = TF32 ? 4 : 8;
-    constexpr int NTBv = TF32 ? NTB_TF32 : NTB;
-    // quadratic-term job width: the real form of U_k, V_k in four 32-column blocks (BF16x3) or four
-    // 24-column blocks (TF32x3, whose accumulator buffers are 96 columns; 24 = 4 ceil(ILE_MAX_MODES / 4))
-    constexpr int QN = TF32 ? TF32_QCOLS : ILE_QCOLS;
-    constexpr int acol = TF32 ? TF32_ACOL : 0;  // first accumulator column
-    constexpr int bw = TF32 ? TF32_BW : NWIN;   // accumulator buffer and B slot width
+    constexpr int NTBv = ntb_of(OP);
+    // quadratic-term job width: the real form of U_k, V_k in four blocks of QN / 4 columns
+    constexpr int QN = ILE_QUAD_NCOL;
+    constexpr int acol = acol_of(OP);  // first accumulator column
+    constexpr int bw = bw_of(OP);      // accumulator buffer and B slot width
     uint4 *A = reinterpret_cast<uint4 *>(dsm);                                        // [K][2][KC][TILE]
-    uint4 *B = A + (TF32 ? 0 : (size_t)LK * 2 * LKC * TILE);                          // [NB][2][LKC][BW]
+    uint4 *B = A + (ATM ? 0 : (size_t)LK * 2 * LKC * TILE);                           // [NB][2][LKC][BW]
     float *rows = reinterpret_cast<float *>(B + (size_t)NB * 2 * LKC * bw);           // [NMATH][RSTRIDE]
     float *aq_s = rows + RSTRIDE * NMATH;                                             // [NMATH]
     float2 *ls_s = reinterpret_cast<float2 *>(aq_s + NMATH);                           // [NMATH]
@@ -406,14 +415,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const uint64_t bh = b0 + (uint64_t)bb * b_slot, bl = bh + b_lo;
                     const uint32_t d = tmem + (uint32_t)acol + tb * (uint32_t)bw;
                     uint32_t acc = 0;
-                    if constexpr (TF32) {
-                        const uint32_t ah = tmem + (uint32_t)(2 * jk * KP), al = ah + (uint32_t)KP;
-                        const int nks = KP / 8;
+                    if constexpr (ATM) {
+                        // A in TMEM: hi then lo, KP values each; a K step (8 TF32 or 16 BF16) is 8 columns
+                        const int acols = TF32 ? KP : KP / 2;
+                        const uint32_t ah = tmem + (uint32_t)(2 * jk * acols), al = ah + (uint32_t)acols;
+                        const int nks = acols / 8;
                         for (int pass = 0; pass < 3; pass++) {
                             const uint32_t ad = pass == 2 ? al : ah;
                             const uint64_t bd = pass == 1 ? bl : bh;
                             for (int ks = 0; ks < nks; ks++) {
-                                mma_tf32_ts(d, ad + (uint32_t)(8 * ks), bd + (uint64_t)ks * b_ks, id, acc);
+                                if constexpr (TF32)
+                                    mma_tf32_ts(d, ad + (uint32_t)(8 * ks), bd + (uint64_t)ks * b_ks, id, acc);
+                                else
+                                    mma_bf16_ts(d, ad + (uint32_t)(8 * ks), bd + (uint64_t)ks * b_ks, id, acc);
                                 acc = 1;
                             }
                         }
@@ -538,6 +552,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         const uint32_t ta = tmem + lane_addr + (uint32_t)(2 * k * pt.KP + 8 * kc);
                         tmem_st8(ta, h);
                         tmem_st8(ta + (uint32_t)pt.KP, l);
+                    } else if constexpr (ATM) {
+                        // TMEM lane `row`: BF16 pairs, hi values at columns k KP + r / 2, lo KP / 2 further
+                        uint4 h, l;
+                        pack_chunk<true>(cv, h, l);
+                        const uint32_t ta = tmem + lane_addr + (uint32_t)(k * pt.KP + 4 * kc);
+                        tmem_st4(ta, h);
+                        tmem_st4(ta + (uint32_t)(pt.KP / 2), l);
                     } else {
                         uint4 h, l;
                         pack_chunk<true>(cv, h, l);
@@ -568,7 +589,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
             }
-            if constexpr (TF32) {
+            if constexpr (ATM) {
                 tmem_wait_st();  // this warp's A-operand stores have reached TMEM
                 fence_before();
             }
@@ -613,13 +634,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 fence_after();
                 uint32_t r[32];
                 const uint32_t qa = tmem + (uint32_t)acol + tb * (uint32_t)bw + lane_addr + (uint32_t)(QN / 4 * g);
-                if constexpr (TF32) {
-                    // the 24 columns of the block (modes b = g + 4 i, i < 6)
-                    tmem_ld16(qa, *reinterpret_cast<uint32_t(*)[16]>(r));
-                    tmem_ld8(qa + 16u, *reinterpret_cast<uint32_t(*)[8]>(r + 16));
-                } else {
-                    tmem_ld32(qa, r);
-                }
+                // the 24 columns of the block (modes b = g + 4 i, i < 6)
+                tmem_ld16(qa, *reinterpret_cast<uint32_t(*)[16]>(r));
+                tmem_ld8(qa + 16u, *reinterpret_cast<uint32_t(*)[8]>(r + 16));
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.tempty[tb]);
@@ -941,11 +958,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-template <bool TF32>
+template <int OP>
 size_t tc2_smem(int K, int M, int KP, int NB) {
-    const int KC = KP / (TF32 ? 4 : 8), bw = TF32 ? TF32_BW : NWIN;
+    const int KC = KP / (OP == OP_TF32_TMEM ? 4 : 8), bw = bw_of(OP);
     (void)M;  // the harmonics table (8 M TILE bytes <= 21.5 KB) fits in the rows area
-    return (TF32 ? (size_t)0 : (size_t)16 * K * 2 * KC * TILE) + (size_t)16 * NB * 2 * KC * bw +
+    return (OP != OP_BF16_SMEM ? (size_t)0 : (size_t)16 * K * 2 * KC * TILE) + (size_t)16 * NB * 2 * KC * bw +
            sizeof(float) * RSTRIDE * NMATH + sizeof(float) * NMATH + sizeof(float2) * NMATH +
            sizeof(float) * 14 * TILE;
 }

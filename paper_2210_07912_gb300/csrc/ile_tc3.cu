@@ -12,8 +12,8 @@
 #include "ile_tc2_kernel.cuh"
 
 bool ile_tc3_fits(int K, int KP) {
-    return K >= 1 && K <= ILE_MAX_DET && KP % 8 == 0 && 2 * K * KP <= TF32_ACOL &&
-           tc2_smem<true>(K, 0, KP, 2) <= SMEM_LIMIT;
+    return K >= 1 && K <= ILE_MAX_DET && KP % 8 == 0 && acols_needed(OP_TF32_TMEM, K, KP) <= acol_of(OP_TF32_TMEM) &&
+           tc2_smem<OP_TF32_TMEM>(K, 0, KP, 2) <= SMEM_LIMIT;
 }
 
 cudaError_t ile_launch_tc3(const PointParams &pp, const void *hi, const void *lo, int TP, int KP,
@@ -22,14 +22,14 @@ cudaError_t ile_launch_tc3(const PointParams &pp, const void *hi, const void *lo
     if (N <= 0) return cudaSuccess;
     if (!ile_tc3_fits(pp.K, KP) || full_grid == 2) return cudaErrorInvalidConfiguration;
     int NB = NBMAX;
-    while (NB > 2 && tc2_smem<true>(pp.K, pp.M, KP, NB) > SMEM_LIMIT) NB--;
-    const size_t smem = tc2_smem<true>(pp.K, pp.M, KP, NB);
+    while (NB > 2 && tc2_smem<OP_TF32_TMEM>(pp.K, pp.M, KP, NB) > SMEM_LIMIT) NB--;
+    const size_t smem = tc2_smem<OP_TF32_TMEM>(pp.K, pp.M, KP, NB);
     const bool dm = pp.dm.on != 0;
-    cudaError_t e = cudaFuncSetAttribute(dm ? ile_tc2_kernel<false, true, true> : ile_tc2_kernel<false, false, true>,
+    cudaError_t e = cudaFuncSetAttribute(dm ? ile_tc2_kernel<false, true, OP_TF32_TMEM> : ile_tc2_kernel<false, false, OP_TF32_TMEM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // a window (plus up to 7 columns of 8-column alignment) must fit one accumulator buffer
-    const int nwcol = TF32_BW - 7;
+    const int nwcol = bw_of(OP_TF32_TMEM) - 7;
     const int sms = sm_count();
     const int64_t ntiles = (N + TILE - 1) / TILE;
     const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
@@ -45,10 +45,10 @@ cudaError_t ile_launch_tc3(const PointParams &pp, const void *hi, const void *lo
     one.KP = KP;
     one.loud = (full_grid || pp.dm.on) ? LoudList{nullptr, 0.f, 0, 0} : loud;
     if (dm)
-        ile_tc2_kernel<false, true, true><<<grid, NTHREADS, smem, st>>>(one, nullptr, nullptr, ntiles, pp.K, KP / 4,
+        ile_tc2_kernel<false, true, OP_TF32_TMEM><<<grid, NTHREADS, smem, st>>>(one, nullptr, nullptr, ntiles, pp.K, KP / 4,
                                                                         0, NB, nwcol, full_grid, flags);
     else
-        ile_tc2_kernel<false, false, true><<<grid, NTHREADS, smem, st>>>(one, nullptr, nullptr, ntiles, pp.K, KP / 4,
+        ile_tc2_kernel<false, false, OP_TF32_TMEM><<<grid, NTHREADS, smem, st>>>(one, nullptr, nullptr, ntiles, pp.K, KP / 4,
                                                                          0, NB, nwcol, full_grid, flags);
     return cudaGetLastError();
 }

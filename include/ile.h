@@ -367,7 +367,7 @@ ile_status ile_merge_partials(int n_shards, const double *max_lnw, const double 
 /* ------------------------------------------------------------------ batched adaptive run */
 
 #define ILE_BATCH_MAX_POINTS 4096
-#define ILE_TUNE_MAX 16
+#define ILE_TUNE_MAX 32
 
 /* One intrinsic point of a batch: the ile_set_data arguments plus its sampler (as in
  * ile_adapt_cfg; n_iter is given to ile_batch_step instead).  Host pointers, copied by
@@ -393,14 +393,14 @@ typedef struct {
 
 typedef struct ile_batch ile_batch; /* opaque; owns the device copies of all points */
 
-/* Result of ile_batch_tune: the chosen configuration of the fused kernel (B-ring depth nb, job
- * window width nwcol in time columns, persistent CTAs grid), its time per launch, and every
- * combination tried. */
+/* Result of ile_batch_tune: the chosen configuration of the fused kernel (placement of the MMA A
+ * operand a_tmem: 0 shared memory, 1 tensor memory; B-ring depth nb; job window width nwcol in
+ * time columns; persistent CTAs grid), its time per launch, and every combination tried. */
 typedef struct {
-    int nb, nwcol, grid;
+    int a_tmem, nb, nwcol, grid;
     float ms;
     int n_tried;
-    int tried_nb[ILE_TUNE_MAX], tried_nwcol[ILE_TUNE_MAX];
+    int tried_a_tmem[ILE_TUNE_MAX], tried_nb[ILE_TUNE_MAX], tried_nwcol[ILE_TUNE_MAX];
     float tried_ms[ILE_TUNE_MAX];
 } ile_batch_tuning;
 
@@ -424,16 +424,21 @@ typedef struct {
  *     the first device-side error, as ile_sync).
  *   ile_batch_run: set_points + step(n_iter) + get of all points; out has n_points entries.
  *   ile_batch_last_samples: the last iteration's samples [7][N] and lnL_t [N] of one point (host).
- *   ile_batch_config: set the fused kernel's B-ring depth (2..4, if it fits in shared memory),
- *     window width and CTA count by hand.
+ *   ile_batch_config: set the fused kernel's configuration by hand: a_tmem 0 keeps the MMA A
+ *     operand (the tile's coefficients) in shared memory with three 128-column TMEM accumulator
+ *     buffers (window widths 66 .. 121), a_tmem 1 puts it in tensor memory with two 160-column
+ *     buffers (widths 66 .. 153; every point needs n_det x (2 n_modes rounded up to 16) <= 192),
+ *     the B-ring depth (2..4, if it fits in shared memory), the window width and the CTA count;
+ *     ILE_E_ARG otherwise.  Every configuration gives the same results bit for bit.
  *   ile_batch_tune: autotuner -- runs one iteration to have samples, then times the fused
  *     kernel over that iteration's work items (a timed warm-up launch per candidate, then reps
  *     timed launches unless the warm-up already took more than twice the best time; reps >= 3
- *     recommended): every window width nwcol on an 8-column grid over the admissible range (its
- *     two ends included, widest first) at the deepest B ring that fits, then each shallower ring
- *     at the best width; keeps the fastest (BF16X3 only; else ILE_E_STATE).  The
- *     grid stays one persistent CTA per SM (the kernel holds a whole SM).  The sampler advances
- *     by one iteration: call ile_batch_reset before the run that counts.
+ *     recommended): for each A placement that fits, every window width nwcol on an 8-column grid
+ *     over its admissible range (both ends included, widest first) at the deepest B ring that
+ *     fits, then each shallower ring at that placement's best width; keeps the fastest (BF16X3
+ *     only; else ILE_E_STATE).  The grid stays one persistent CTA per SM (the kernel holds a
+ *     whole SM).  The sampler advances by one iteration: call ile_batch_reset before the run that
+ *     counts.
  */
 ile_status ile_batch_create(ile_batch **out, int device, void *cuda_stream, ile_prec prec);
 ile_status ile_batch_destroy(ile_batch *b);
@@ -444,7 +449,7 @@ ile_status ile_batch_get(ile_batch *b, int first, int count, ile_adapt_result *o
 ile_status ile_batch_run(ile_batch *b, int n_points, const ile_point_desc *points, int n_iter,
                          ile_adapt_result *out);
 ile_status ile_batch_last_samples(ile_batch *b, int point, double *theta, double *lnL_t);
-ile_status ile_batch_config(ile_batch *b, int nb, int nwcol, int grid);
+ile_status ile_batch_config(ile_batch *b, int a_tmem, int nb, int nwcol, int grid);
 ile_status ile_batch_tune(ile_batch *b, int reps, ile_batch_tuning *out);
 const char *ile_batch_last_error(const ile_batch *b);
 

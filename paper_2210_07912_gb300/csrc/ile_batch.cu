@@ -62,7 +62,7 @@ struct ile_batch {
     unsigned *flags = nullptr;
     // fused-kernel configuration
     int LK = 0, LM = 0, LKP = 0;
-    int NB = 2, nwcol = 120, grid = 0;
+    int a_tmem = 0, NB = 2, nwcol = 120, grid = 0;  // fused-kernel configuration (A placement, B ring, window)
     // graph of one iteration
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -184,7 +184,7 @@ ile_status enqueue_iteration(ile_batch *b) {
     BK(cudaMemsetAsync(b->loud, 0, sizeof(int), b->stream));
     const float thr = ile_refine_threshold((int)b->prec);
     if (b->prec == ILE_PREC_BF16X3) {
-        BK(ile_launch_tc2_batch(b->pts, b->items, b->n_items, b->LK, b->LM, b->LKP, b->NB, b->nwcol, b->grid,
+        BK(ile_launch_tc2_batch(b->pts, b->items, b->n_items, b->LK, b->LM, b->LKP, b->a_tmem, b->NB, b->nwcol, b->grid,
                                 b->flags, b->stream));
     } else {
         for (int p = 0; p < b->n_points; p++) {
@@ -484,11 +484,12 @@ ile_status ile_batch_set_points(ile_batch *b, int n_points, const ile_point_desc
         BK(cudaMalloc((void **)&b->s.A, sizeof(float) * (size_t)cap));
         b->s_cap = cap;
     }
-    // fused-kernel defaults: deepest B ring that fits, the widest window
+    // fused-kernel defaults: A operand in shared memory, deepest B ring that fits, the widest window
     int lo = 0, hi = 0;
-    b->nwcol = ile_tc2_nwcol_range(&lo, &hi);
+    b->a_tmem = 0;
+    b->nwcol = ile_tc2_nwcol_range(0, &lo, &hi);
     b->NB = 4;
-    while (b->NB > 2 && !ile_tc2_batch_fits(b->LK, b->LM, b->LKP, b->NB)) b->NB--;
+    while (b->NB > 2 && !ile_tc2_batch_fits(0, b->LK, b->LM, b->LKP, b->NB)) b->NB--;
     BK(ile_launch_batch_reset(n_points, b->bp, b->cdf, b->lnps, b->pooled, b->iter, b->hist_fx, b->hist, b->iter_log,
                               b->stream));
     BK(cudaStreamSynchronize(b->stream));
@@ -567,13 +568,15 @@ ile_status ile_batch_last_samples(ile_batch *b, int point, double *theta, double
     return read_flags(b);
 }
 
-ile_status ile_batch_config(ile_batch *b, int NB, int nwcol, int grid) {
+ile_status ile_batch_config(ile_batch *b, int a_tmem, int NB, int nwcol, int grid) {
     if (!b) return ILE_E_ARG;
     if (!b->n_points) return ILE_E_STATE;
+    if (a_tmem != 0 && a_tmem != 1) return ILE_E_ARG;
     int lo = 0, hi = 0;
-    ile_tc2_nwcol_range(&lo, &hi);
+    ile_tc2_nwcol_range(a_tmem, &lo, &hi);
     if (NB < 2 || NB > 4 || nwcol < lo || nwcol > hi || grid < 1) return ILE_E_ARG;
-    if (!ile_tc2_batch_fits(b->LK, b->LM, b->LKP, NB)) return ILE_E_ARG;
+    if (!ile_tc2_batch_fits(a_tmem, b->LK, b->LM, b->LKP, NB)) return ILE_E_ARG;
+    b->a_tmem = a_tmem;
     b->NB = NB;
     b->nwcol = nwcol;
     b->grid = grid;
@@ -589,32 +592,25 @@ ile_status ile_batch_tune(ile_batch *b, int reps, ile_batch_tuning *out) {
     // samples to time on: one iteration (advances the samplers by one iteration)
     ile_status st = ile_batch_step(b, 1);
     if (st != ILE_OK) return st;
-    int lo = 0, hi = 0;
-    ile_tc2_nwcol_range(&lo, &hi);
     int sms = 0;
     BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
-    // the deepest B ring that fits; every window width on an 8-column grid over the admissible
-    // range [lo, hi] (both ends included) at that depth, then the shallower rings at the best width
-    int nb_max = 2;
-    for (int NB = 3; NB <= 4; NB++)
-        if (ile_tc2_batch_fits(b->LK, b->LM, b->LKP, NB)) nb_max = NB;
     cudaEvent_t e0, e1;
     BK(cudaEventCreate(&e0));
     BK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bNB = b->NB, bW = b->nwcol, n_tried = 0;
-    auto time_one = [&](int NB, int W) -> cudaError_t {
+    int bA = b->a_tmem, bNB = b->NB, bW = b->nwcol, n_tried = 0;
+    auto time_one = [&](int A, int NB, int W, float &ms) -> cudaError_t {
         // a timed warm-up launch; a candidate already slower than twice the best is recorded at that
         // time, the others by `reps` more timed launches (each launch refills the loud-sample list:
         // its count is reset first)
         auto launch = [&]() {
             cudaError_t e = cudaMemsetAsync(b->loud, 0, sizeof(int), b->stream);
             if (e == cudaSuccess)
-                e = ile_launch_tc2_batch(b->pts, b->items, b->n_items, b->LK, b->LM, b->LKP, NB, W, sms, b->flags,
+                e = ile_launch_tc2_batch(b->pts, b->items, b->n_items, b->LK, b->LM, b->LKP, A, NB, W, sms, b->flags,
                                          b->stream);
             return e;
         };
-        float ms = 0.f;
+        ms = 0.f;
         cudaError_t e = cudaEventRecord(e0, b->stream);
         if (e == cudaSuccess) e = launch();
         if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
@@ -631,6 +627,7 @@ ile_status ile_batch_tune(ile_batch *b, int reps, ile_batch_tuning *out) {
             ms /= reps;
         }
         if (out && n_tried < ILE_TUNE_MAX) {
+            out->tried_a_tmem[n_tried] = A;
             out->tried_nb[n_tried] = NB;
             out->tried_nwcol[n_tried] = W;
             out->tried_ms[n_tried] = ms;
@@ -638,21 +635,42 @@ ile_status ile_batch_tune(ile_batch *b, int reps, ile_batch_tuning *out) {
         n_tried++;
         if (ms < best) {
             best = ms;
+            bA = A;
             bNB = NB;
             bW = W;
         }
         return cudaSuccess;
     };
-    // widest first (the usual optimum), so that narrow windows, whose multi-window jobs cost several
-    // times more, are usually dismissed after their warm-up launch
+    // per A placement (shared memory, then TMEM when every point's operand fits): every window width
+    // on an 8-column grid over the placement's admissible range (both ends included, widest first,
+    // so that narrow windows, whose multi-window jobs cost several times more, are usually dismissed
+    // after their warm-up launch) at the deepest B ring that fits, then the shallower rings at the
+    // placement's best width
     cudaError_t e = cudaSuccess;
-    for (int W = hi; e == cudaSuccess; W -= 8) {
-        W = std::max(W, lo);
-        e = time_one(nb_max, W);
-        if (W == lo) break;
+    for (int A = 0; A <= 1 && e == cudaSuccess; A++) {
+        if (!ile_tc2_batch_fits(A, b->LK, b->LM, b->LKP, 2)) continue;
+        int lo = 0, hi = 0;
+        ile_tc2_nwcol_range(A, &lo, &hi);
+        int nb_max = 2;
+        for (int NB = 3; NB <= 4; NB++)
+            if (ile_tc2_batch_fits(A, b->LK, b->LM, b->LKP, NB)) nb_max = NB;
+        float abest = 1e30f;
+        int aW = hi;
+        for (int W = hi; e == cudaSuccess; W -= 8) {
+            W = std::max(W, lo);
+            float ms = 0.f;
+            e = time_one(A, nb_max, W, ms);
+            if (e == cudaSuccess && ms < abest) {
+                abest = ms;
+                aW = W;
+            }
+            if (W == lo) break;
+        }
+        for (int NB = 2; NB < nb_max && e == cudaSuccess; NB++) {
+            float ms = 0.f;
+            e = time_one(A, NB, aW, ms);
+        }
     }
-    const int wbest = bW;
-    for (int NB = 2; NB < nb_max && e == cudaSuccess; NB++) e = time_one(NB, wbest);
     if (e != cudaSuccess) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -662,11 +680,13 @@ ile_status ile_batch_tune(ile_batch *b, int reps, ile_batch_tuning *out) {
     cudaEventDestroy(e1);
     st = read_flags(b);
     if (st != ILE_OK) return st;
+    b->a_tmem = bA;
     b->NB = bNB;
     b->nwcol = bW;
     b->grid = sms;
     invalidate_graph(b);
     if (out) {
+        out->a_tmem = bA;
         out->nb = bNB;
         out->nwcol = bW;
         out->grid = sms;

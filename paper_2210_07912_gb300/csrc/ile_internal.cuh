@@ -627,12 +627,13 @@ cudaError_t ile_launch_batch_mc(int n_points, const IleBatchPoint *bp, const int
                                 double *iter_res, cudaStream_t st);
 // batched fused kernel: items are (point, tile) pairs; LK, LM, LKP the largest sizes of the batch
 int ile_tc2_tile();
-size_t ile_tc2_batch_smem(int LK, int LM, int LKP, int NB);
-bool ile_tc2_batch_fits(int LK, int LM, int LKP, int NB);
-// window width (MMA N per job before alignment): default returned, admissible range in lo, hi
-int ile_tc2_nwcol_range(int *lo, int *hi);
+// a_tmem: 0 = A operand in shared memory, 1 = in TMEM (wider windows; see ile_tc2.cu)
+size_t ile_tc2_batch_smem(int a_tmem, int LK, int LM, int LKP, int NB);
+bool ile_tc2_batch_fits(int a_tmem, int LK, int LM, int LKP, int NB);
+// admissible window widths [lo, hi] of a placement; returns the default width
+int ile_tc2_nwcol_range(int a_tmem, int *lo, int *hi);
 cudaError_t ile_launch_tc2_batch(const Tc2Point *pts_dev, const int2 *items_dev, int64_t nitems, int LK, int LM,
-                                 int LKP, int NB, int nwcol, int grid, unsigned *flags, cudaStream_t st);
+                                 int LKP, int a_tmem, int NB, int nwcol, int grid, unsigned *flags, cudaStream_t st);
 cudaError_t ile_launch_mc(const double *lnL_t, const double *ln_prior, const double *ln_ps, int64_t N,
                           double *partials, int n_part, double *result, cudaStream_t st);
 int ile_mc_partial_count(int64_t N);

@@ -58,29 +58,40 @@ cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo
 
 int ile_tc2_tile() { return TILE; }
 
-size_t ile_tc2_batch_smem(int LK, int LM, int LKP, int NB) { return tc2_smem<OP_BF16_SMEM>(LK, LM, LKP, NB); }
+// Batched launches: a_tmem 0 keeps the A operand in shared memory (three 128-column accumulator
+// buffers), 1 puts it in TMEM (two 160-column buffers; needs K KP <= 192 for every point).
+static int batch_op(int a_tmem) { return a_tmem ? OP_BF16_TMEM_W : OP_BF16_SMEM; }
 
-bool ile_tc2_batch_fits(int LK, int LM, int LKP, int NB) { return tc2_smem<OP_BF16_SMEM>(LK, LM, LKP, NB) <= SMEM_LIMIT; }
+size_t ile_tc2_batch_smem(int a_tmem, int LK, int LM, int LKP, int NB) {
+    return a_tmem ? tc2_smem<OP_BF16_TMEM_W>(LK, LM, LKP, NB) : tc2_smem<OP_BF16_SMEM>(LK, LM, LKP, NB);
+}
 
-int ile_tc2_nwcol_range(int *lo, int *hi) {
+bool ile_tc2_batch_fits(int a_tmem, int LK, int LM, int LKP, int NB) {
+    if (a_tmem && acols_needed(OP_BF16_TMEM_W, LK, LKP) > acol_of(OP_BF16_TMEM_W)) return false;
+    return ile_tc2_batch_smem(a_tmem, LK, LM, LKP, NB) <= SMEM_LIMIT;
+}
+
+int ile_tc2_nwcol_range(int a_tmem, int *lo, int *hi) {
     *lo = NWCOL_MIN;
-    *hi = NWIN - 7;
-    return NWCOL;
+    *hi = bw_of(batch_op(a_tmem)) - 7;
+    return *hi < NWCOL ? *hi : NWCOL;
 }
 
 cudaError_t ile_launch_tc2_batch(const Tc2Point *pts_dev, const int2 *items_dev, int64_t nitems, int LK, int LM,
-                                 int LKP, int NB, int nwcol, int grid, unsigned *flags, cudaStream_t st) {
+                                 int LKP, int a_tmem, int NB, int nwcol, int grid, unsigned *flags, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
-    if (NB < 2 || NB > NBMAX || nwcol < NWCOL_MIN || nwcol > NWIN - 7) return cudaErrorInvalidValue;
-    const size_t smem = tc2_smem<OP_BF16_SMEM>(LK, LM, LKP, NB);
-    if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
-    cudaError_t e =
-        cudaFuncSetAttribute(ile_tc2_kernel<true, false, OP_BF16_SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int lo = 0, hi = 0;
+    ile_tc2_nwcol_range(a_tmem, &lo, &hi);
+    if (NB < 2 || NB > NBMAX || nwcol < lo || nwcol > hi) return cudaErrorInvalidValue;
+    if (!ile_tc2_batch_fits(a_tmem, LK, LM, LKP, NB)) return cudaErrorInvalidConfiguration;
+    const size_t smem = ile_tc2_batch_smem(a_tmem, LK, LM, LKP, NB);
+    auto kern = a_tmem ? ile_tc2_kernel<true, false, OP_BF16_TMEM_W> : ile_tc2_kernel<true, false, OP_BF16_SMEM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (grid <= 0) grid = sm_count();
     if (grid > nitems) grid = (int)nitems;
     Tc2Point none{};
-    ile_tc2_kernel<true, false, OP_BF16_SMEM><<<grid, NTHREADS, smem, st>>>(none, pts_dev, items_dev, nitems, LK, LKP / 8,
-                                                       LM * (LM + 1) / 2, NB, nwcol, 0, flags);
+    kern<<<grid, NTHREADS, smem, st>>>(none, pts_dev, items_dev, nitems, LK, LKP / 8, LM * (LM + 1) / 2, NB, nwcol, 0,
+                                        flags);
     return cudaGetLastError();
 }

@@ -73,19 +73,26 @@ constexpr uint32_t SLEEP_NS = 10000;
 constexpr int RSTRIDE = 34;                // per-thread row: 32 staged columns + 2 (8-byte stores, half-warp conflict-free)
 constexpr float ILE_LOG2E_F = 1.4426950408889634f;  // log2(e)
 
-// Operand variants of the kernel: BF16x3 with the A operand in shared memory (the batched launch),
-// BF16x3 with A in TMEM, TF32x3 with A in TMEM.  A in TMEM: row n of the tile in lane n, detector
-// k's hi values then its lo values, KP values each, in consecutive 32-bit columns (two BF16 or one
-// TF32 value per column), at most acol_of columns; the accumulator buffers follow.
-enum : int { OP_BF16_SMEM = 0, OP_BF16_TMEM = 1, OP_TF32_TMEM = 2 };
-__host__ __device__ constexpr int acol_of(int op) { return op == OP_TF32_TMEM ? 320 : op == OP_BF16_TMEM ? 176 : 0; }
-__host__ __device__ constexpr int ntb_of(int op) { return op == OP_TF32_TMEM ? NTB_TF32 : NTB; }
+// Operand variants of the kernel: BF16x3 with the A operand in shared memory and three 128-column
+// accumulator buffers; BF16x3 with A in TMEM and three 112-column buffers; BF16x3 with A in TMEM
+// and two 160-column buffers (wider windows, more shared memory for the B ring: a choice of the
+// batch autotuner); TF32x3 with A in TMEM and two 96-column buffers.  A in TMEM: row n of the tile
+// in lane n, detector k's hi values then its lo values, KP values each, in consecutive 32-bit
+// columns (two BF16 or one TF32 value per column), at most acol_of columns; the accumulator
+// buffers follow.
+enum : int { OP_BF16_SMEM = 0, OP_BF16_TMEM = 1, OP_TF32_TMEM = 2, OP_BF16_TMEM_W = 3 };
+__host__ __device__ constexpr int acol_of(int op) {
+    return op == OP_TF32_TMEM ? 320 : op == OP_BF16_TMEM ? 176 : op == OP_BF16_TMEM_W ? 192 : 0;
+}
+__host__ __device__ constexpr int ntb_of(int op) { return op == OP_TF32_TMEM || op == OP_BF16_TMEM_W ? 2 : NTB; }
 __host__ __device__ constexpr int bw_of(int op) {
     return op == OP_BF16_SMEM ? NWIN : ((int)TMEM_COLS - acol_of(op)) / ntb_of(op) / 16 * 16;
 }
 // TMEM columns of a point's A operand (K detectors, KP values per row and part)
 __host__ __device__ constexpr int acols_needed(int op, int K, int KP) { return op == OP_TF32_TMEM ? 2 * K * KP : K * KP; }
-static_assert(bw_of(OP_TF32_TMEM) == 96 && bw_of(OP_BF16_TMEM) == 112, "accumulator buffers");
+static_assert(bw_of(OP_TF32_TMEM) == 96 && bw_of(OP_BF16_TMEM) == 112 && bw_of(OP_BF16_TMEM_W) == 160,
+              "accumulator buffers");
+static_assert(acol_of(OP_BF16_TMEM_W) + 2 * bw_of(OP_BF16_TMEM_W) <= (int)TMEM_COLS, "wide BF16x3 TMEM layout");
 static_assert(acol_of(OP_BF16_TMEM) + NTB * bw_of(OP_BF16_TMEM) <= (int)TMEM_COLS, "BF16x3 TMEM layout");
 static_assert(acol_of(OP_TF32_TMEM) + NTB_TF32 * bw_of(OP_TF32_TMEM) <= (int)TMEM_COLS, "TF32x3 TMEM layout");
 static_assert(ILE_QUAD_NCOL <= 96 && 96 - 7 >= NWCOL_MIN, "a quadratic-term job and a window fit every buffer");
@@ -220,6 +227,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     constexpr bool TF32 = OP == OP_TF32_TMEM, ATM = OP != OP_BF16_SMEM;
     constexpr int EPC = TF32 ? 4 : 8;
     constexpr int NTBv = ntb_of(OP);
+    static_assert(NTBv <= NTB, "barrier arrays");
     // quadratic-term job width: the real form of U_k, V_k in four blocks of QN / 4 columns
     constexpr int QN = ILE_QUAD_NCOL;
     constexpr int acol = acol_of(OP);  // first accumulator column
@@ -755,9 +763,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (full_grid == 2) {
                     if (valid) {
                         float *o = pt.grid_f + p * Nt + j0 + jbeg;
+                        if (jbeg + JG <= Jc && (Nt & 3) == 0) {
+                            // 16 whole bins at a 16-byte boundary (the buffer is 256-byte aligned)
 #pragma unroll
-                        for (int jj = 0; jj < JG; jj++)
-                            if (jbeg + jj < Jc) o[jj] = D[jj];
+                            for (int q = 0; q < JG / 4; q++)
+                                reinterpret_cast<float4 *>(o)[q] =
+                                    make_float4(D[4 * q], D[4 * q + 1], D[4 * q + 2], D[4 * q + 3]);
+                        } else {
+#pragma unroll
+                            for (int jj = 0; jj < JG; jj++)
+                                if (jbeg + jj < Jc) o[jj] = D[jj];
+                        }
                     }
                 } else if (full_grid) {
                     if (valid) {

@@ -59,13 +59,14 @@ class PointDesc(ctypes.Structure):
                 ("sky_frame", ctypes.c_int), ("sky_pole", ctypes.c_double * 3)]
 
 
-TUNE_MAX = 16
+TUNE_MAX = 32
 
 
 class BatchTuning(ctypes.Structure):
-    _fields_ = [("nb", ctypes.c_int), ("nwcol", ctypes.c_int), ("grid", ctypes.c_int), ("ms", ctypes.c_float),
-                ("n_tried", ctypes.c_int), ("tried_nb", ctypes.c_int * TUNE_MAX),
-                ("tried_nwcol", ctypes.c_int * TUNE_MAX), ("tried_ms", ctypes.c_float * TUNE_MAX)]
+    _fields_ = [("a_tmem", ctypes.c_int), ("nb", ctypes.c_int), ("nwcol", ctypes.c_int), ("grid", ctypes.c_int),
+                ("ms", ctypes.c_float), ("n_tried", ctypes.c_int), ("tried_a_tmem", ctypes.c_int * TUNE_MAX),
+                ("tried_nb", ctypes.c_int * TUNE_MAX), ("tried_nwcol", ctypes.c_int * TUNE_MAX),
+                ("tried_ms", ctypes.c_float * TUNE_MAX)]
 
 
 def default_ranges(fs: float = 4096.0, tc_max: float | None = None, d_min: float = 100.0, d_max: float = 1000.0):
@@ -173,7 +174,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ile_batch_get.argtypes = [vp, i32, i32, P(AdaptResult)]
     lib.ile_batch_run.argtypes = [vp, i32, P(PointDesc), i32, P(AdaptResult)]
     lib.ile_batch_last_samples.argtypes = [vp, i32, vp, vp]
-    lib.ile_batch_config.argtypes = [vp, i32, i32, i32]
+    lib.ile_batch_config.argtypes = [vp, i32, i32, i32, i32]
     lib.ile_batch_tune.argtypes = [vp, i32, P(BatchTuning)]
     lib.ile_batch_last_error.argtypes = [vp]
     lib.ile_batch_last_error.restype = ctypes.c_char_p
@@ -644,11 +645,11 @@ class Batch:
                     "ile_batch_last_samples")
         return theta, lnl
 
-    def config(self, nb: int, nwcol: int, grid: int):
-        self._check(self._lib.ile_batch_config(self._h, nb, nwcol, grid), "ile_batch_config")
+    def config(self, nb: int, nwcol: int, grid: int, a_tmem: int = 0):
+        self._check(self._lib.ile_batch_config(self._h, a_tmem, nb, nwcol, grid), "ile_batch_config")
 
     def tune(self, reps: int = 3) -> dict:
         t = BatchTuning()
         self._check(self._lib.ile_batch_tune(self._h, reps, ctypes.byref(t)), "ile_batch_tune")
-        tried = [(t.tried_nb[i], t.tried_nwcol[i], float(t.tried_ms[i])) for i in range(t.n_tried)]
-        return {"nb": t.nb, "nwcol": t.nwcol, "grid": t.grid, "ms": float(t.ms), "tried": tried}
+        tried = [(t.tried_a_tmem[i], t.tried_nb[i], t.tried_nwcol[i], float(t.tried_ms[i])) for i in range(t.n_tried)]
+        return {"a_tmem": t.a_tmem, "nb": t.nb, "nwcol": t.nwcol, "grid": t.grid, "ms": float(t.ms), "tried": tried}

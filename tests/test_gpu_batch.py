@@ -107,22 +107,26 @@ def test_batch_tune_keeps_results(ile):
     b.step(2)
     before = b.get()
     t = b.tune(reps=1)
-    assert t["nb"] in (2, 3, 4) and 66 <= t["nwcol"] <= 121 and t["ms"] > 0 and len(t["tried"]) >= 2
-    # the widths tried span the admissible range, both ends included, and the choice is the fastest
-    widths = sorted({w for _, w, _ in t["tried"]})
-    assert widths[0] == 66 and widths[-1] == 121 and len(widths) >= 8
-    assert min(t["tried"], key=lambda c: c[2])[:2] == (t["nb"], t["nwcol"])
+    assert t["a_tmem"] in (0, 1) and t["nb"] in (2, 3, 4) and t["ms"] > 0 and len(t["tried"]) >= 2
+    assert 66 <= t["nwcol"] <= (121 if t["a_tmem"] == 0 else 153)
+    # per A placement, the widths tried span its admissible range (both ends included), and the
+    # choice is the fastest of everything tried
+    for a, hi in ((0, 121), (1, 153)):
+        widths = sorted({w for aa, _, w, _ in t["tried"] if aa == a})
+        assert widths[0] == 66 and widths[-1] == hi and len(widths) >= 8, (a, widths)
+    assert min(t["tried"], key=lambda c: c[3])[:3] == (t["a_tmem"], t["nb"], t["nwcol"])
     b.reset()
     b.step(2)
     after = b.get()
     for i in range(len(points)):
         _assert_same(before[i], after[i], f"point {i}")
     # every admissible hand-set configuration gives the same results
-    b.config(2, 72, 40)
-    b.reset()
-    b.step(2)
-    for i, r in enumerate(b.get()):
-        _assert_same(before[i], r, f"point {i} (nb 2, nwcol 72, 40 CTAs)")
+    for a_tmem, nb, nwcol, grid in ((0, 2, 72, 40), (1, 4, 153, 152), (1, 2, 80, 37)):
+        b.config(nb, nwcol, grid, a_tmem)
+        b.reset()
+        b.step(2)
+        for i, r in enumerate(b.get()):
+            _assert_same(before[i], r, f"point {i} (a_tmem {a_tmem}, nb {nb}, nwcol {nwcol}, {grid} CTAs)")
 
 
 def test_batch_errors(ile):
@@ -141,6 +145,12 @@ def test_batch_errors(ile):
     assert e.value.status == ile.ILE_E_ARG
     with pytest.raises(ile.IleError) as e:
         b.config(2, 10, 152)  # window narrower than one chunk
+    assert e.value.status == ile.ILE_E_ARG
+    with pytest.raises(ile.IleError) as e:
+        b.config(2, 129, 152, 0)  # wider than the shared-memory placement's 128-column buffers allow
+    assert e.value.status == ile.ILE_E_ARG
+    with pytest.raises(ile.IleError) as e:
+        b.config(2, 100, 152, 2)  # no such placement
     assert e.value.status == ile.ILE_E_ARG
     f = ile.Batch(0, None, "fp32")
     f.set_points(points[:2], cfgs[:2])

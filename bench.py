@@ -236,13 +236,13 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------------------------ our arm
-def profile_traffic(kernel_file, prec):
+def profile_traffic(kernel_files, prec):
     """DRAM bytes per launch of the contraction kernel from the committed ncu summary, if it was
-    taken on the current source of that kernel (else None)."""
+    taken on the current source of that kernel (else None).  kernel_files: the kernel's source
+    files; the two headers every kernel is compiled with are added."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2210_07912_gb300", "csrc")
-    # the kernel's source and the headers it is compiled with
-    srcs = [os.path.join(csrc, f) for f in (kernel_file, "ile_tcgen05.cuh", "ile_internal.cuh")]
+    srcs = [os.path.join(csrc, f) for f in (*kernel_files, "ile_tcgen05.cuh", "ile_internal.cuh")]
     summ = os.path.join(ROOT, "profiles", f"contract_{prec}_c1.md")
     if not (all(os.path.exists(f) for f in srcs) and os.path.exists(summ)):
         return None, None
@@ -561,13 +561,14 @@ def main():
             peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
             roof = {"bound": "alu", "kernel": "ile_plain_kernel (S3+S5)",
                     "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % sm_mhz}
-            kfile = "ile_plain.cu"
+            kfile = ("ile_plain.cu",)
         else:
             peak = pk["bf16_tflops"] * (0.5 if args.prec == "tf32x3" else 1.0)
             roof = {"bound": "tensor",
-                    "kernel": "ile_tc2_kernel (S1-S5 fused)" if args.prec == "bf16x3" else "ile_tc_kernel (S3+S5)",
+                    "kernel": "ile_tc2_kernel (S1-S5 fused, BF16x3, A operand in shared memory)"
+                    if args.prec == "bf16x3" else "ile_tc2_kernel (S1-S5 fused, TF32x3, A operand in TMEM)",
                     "peak_kind": "measured dense bf16 (burst)" + (" x 1/2 for tf32" if args.prec == "tf32x3" else "")}
-            kfile = "ile_tc2.cu" if args.prec == "bf16x3" else "ile_tc.cu"
+            kfile = ("ile_tc2_kernel.cuh", "ile_tc2.cu" if args.prec == "bf16x3" else "ile_tc3.cu")
         traffic, _ = profile_traffic(kfile, args.prec)
         achieved = alg_flops / per_launch_s / 1e12
         roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,

@@ -104,7 +104,10 @@ ile_status ile_set_precision(ile_ctx *ctx, ile_prec prec);
  *   Q: [n_det][n_modes][T_ext][2] (re, im) = <h_lm(t_i) | d>_k at t_i = t_start_s + i / fs_hz.
  *   U, V: [n_det][n_modes][n_modes][2], U_k Hermitian, V_k symmetric (Eq. (eq:QUV)).
  *   n_window = N_t in [1, 1024]; T_ext in [2, 4096]; fs_hz > 0; d_ref_mpc > 0.
- * May be called again to replace the point.  Returns ILE_E_NONFINITE for a non-finite input.
+ * May be called again to replace the point.  Returns ILE_E_ARG or ILE_E_NONFINITE for a bad
+ * argument; the previous point is kept after an ILE_E_ARG and after a non-finite detector
+ * description, U or V, but a non-finite Q (checked on the device while it is converted) leaves
+ * the context without data (ILE_E_STATE until the next successful call).
  */
 ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, const double *det_tensor,
                         const double *det_pos_m, const double *Q, int T_ext, double t_start_s, double fs_hz,

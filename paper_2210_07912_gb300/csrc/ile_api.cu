@@ -528,8 +528,9 @@ ile_status ile_create(ile_ctx **out, int device, void *cuda_stream, ile_prec pre
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->prec = prec;
     DeviceGuard g(device);
-    cudaError_t e = cudaMalloc((void **)&ctx->flags, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(ctx->flags, 0, sizeof(unsigned));
+    // flags[0]: the kernels' status bits; flags[1]: the check of the last ile_set_data's Q
+    cudaError_t e = cudaMalloc((void **)&ctx->flags, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(ctx->flags, 0, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->result, 8 * sizeof(double));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) {
@@ -683,7 +684,7 @@ ile_status ile_prepare_point(int n_det, int n_modes, const int *lm, const double
                              const double *det_pos_m, const double *Q, int T_ext, double t_start_s, double fs_hz,
                              const double *U, const double *V, int n_window, double gmst_rad, double d_ref_mpc,
                              PointParams &pp_out, std::vector<float> &qp, std::vector<float> &uv,
-                             std::vector<float> &quad) {
+                             std::vector<float> &quad, bool host_q) {
     if (!lm || !det_tensor || !det_pos_m || !Q || !U || !V) return ILE_E_ARG;
     if (n_det < 1 || n_det > ILE_MAX_DET || n_modes < 1 || n_modes > ILE_MAX_MODES) return ILE_E_ARG;
     if (n_window < 1 || n_window > ILE_MAX_WINDOW || T_ext < 2 || T_ext > ILE_MAX_TEXT) return ILE_E_ARG;
@@ -707,16 +708,17 @@ ile_status ile_prepare_point(int n_det, int n_modes, const int *lm, const double
             if (lm[2 * b] == l && lm[2 * b + 1] == m) return ILE_E_ARG;
         if (!wigner_terms(l, m, pp.mode[a])) return ILE_E_ARG;
     }
+    // (with host_q false, Q is converted and checked on the device by the caller)
     if (!finite_array(det_tensor, 9 * (size_t)K) || !finite_array(det_pos_m, 3 * (size_t)K) ||
-        !finite_array(Q, 2 * (size_t)K * M * T) || !finite_array(U, 2 * (size_t)K * M * M) ||
+        (host_q && !finite_array(Q, 2 * (size_t)K * M * T)) || !finite_array(U, 2 * (size_t)K * M * M) ||
         !finite_array(V, 2 * (size_t)K * M * M))
         return ILE_E_NONFINITE;
     for (int k = 0; k < K; k++) {
         for (int i = 0; i < 9; i++) pp.det_tensor[k][i] = (float)det_tensor[9 * k + i];
         for (int i = 0; i < 3; i++) pp.det_pos_c[k][i] = (float)(det_pos_m[3 * k + i] / ILE_C_SI);
     }
-    qp.assign((size_t)K * R * T, 0.f);
-    for (int k = 0; k < K; k++)
+    qp.assign(host_q ? (size_t)K * R * T : 0, 0.f);
+    for (int k = 0; k < K && host_q; k++)
         for (int a = 0; a < M; a++)
             for (int t = 0; t < T; t++) {
                 const double *q = Q + 2 * (((size_t)k * M + a) * T + t);
@@ -773,14 +775,17 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
     if (!ctx) return ILE_E_ARG;
     PointParams pp{};
     std::vector<float> qp, uv, quad;
+    // Q is converted to its FP32 rows (and checked) on the device, from the FP64 copy the
+    // refinement keeps anyway
     ile_status st = ile_prepare_point(n_det, n_modes, lm, det_tensor, det_pos_m, Q, T_ext, t_start_s, fs_hz, U, V,
-                                      n_window, gmst_rad, d_ref_mpc, pp, qp, uv, quad);
+                                      n_window, gmst_rad, d_ref_mpc, pp, qp, uv, quad, false);
     if (st != ILE_OK) return st;
     DeviceGuard g(ctx->device);
     // the previous point's arrays are released by the growth below: no data until it completes
     ctx->has_data = false;
     ctx->Qtc_ready[1] = ctx->Qtc_ready[2] = ctx->Qadj_ready = false;
-    CK(grow(ctx, &ctx->Qp, sizeof(float) * qp.size()));
+    const size_t nqp = (size_t)n_det * 2 * n_modes * T_ext;
+    CK(grow(ctx, &ctx->Qp, sizeof(float) * nqp));
     CK(grow(ctx, &ctx->UV, sizeof(float) * uv.size()));
     CK(grow(ctx, &ctx->Qquad, sizeof(float) * quad.size()));
     const size_t nq = (size_t)n_det * n_modes * T_ext, nuv = (size_t)n_det * n_modes * n_modes;
@@ -790,10 +795,15 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
     CK(cudaMemcpyAsync(ctx->Q64, Q, sizeof(double2) * nq, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->U64, U, sizeof(double2) * nuv, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->V64, V, sizeof(double2) * nuv, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->Qp, qp.data(), sizeof(float) * qp.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->UV, uv.data(), sizeof(float) * uv.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->Qquad, quad.data(), sizeof(float) * quad.size(), cudaMemcpyHostToDevice, ctx->stream));
+    unsigned *qchk = ctx->flags + 1, qbad = 0;
+    CK(cudaMemsetAsync(qchk, 0, sizeof(unsigned), ctx->stream));
+    CK(ile_launch_q_convert(reinterpret_cast<const double2 *>(ctx->Q64), n_det, n_modes, T_ext, ctx->Qp, qchk,
+                            ctx->stream));
+    CK(cudaMemcpyAsync(&qbad, qchk, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (qbad) return ILE_E_NONFINITE;  // the context stays without data
     ctx->pp = pp;
     ile_refine_params(n_det, n_modes, lm, det_tensor, det_pos_m, T_ext, t_start_s, fs_hz, n_window, gmst_rad,
                       d_ref_mpc, ctx->r64);  // validated above

@@ -563,6 +563,9 @@ size_t ile_tc_q_bytes(int prec, int K, int M, int T_ext);
 #define ILE_QUAD_NCOL 96
 static_assert(4 * ((ILE_MAX_MODES + 3) / 4) <= ILE_QUAD_NCOL / 4, "quadratic-term blocks");
 // quad: [K][KPq][ILE_QCOLS] FP32 real-form block, KPq the BF16X3 operand rows (may be null)
+// Qp (FP32 [K][2M][T]) from the device copy of the caller's Q (FP64 complex [K][M][T]); ILE_FLAG_NONFINITE in
+// *chk for a non-finite entry
+cudaError_t ile_launch_q_convert(const double2 *Q64, int K, int M, int T, float *Qp, unsigned *chk, cudaStream_t st);
 cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp, const float *quad, void *hi,
                                 void *lo, cudaStream_t st);
 cudaError_t ile_launch_tc(int prec, const PointParams &pp, const void *hi, const void *lo, IleScratch s,
@@ -693,5 +696,5 @@ ile_status ile_prepare_point(int n_det, int n_modes, const int *lm, const double
                              const double *det_pos_m, const double *Q, int T_ext, double t_start_s, double fs_hz,
                              const double *U, const double *V, int n_window, double gmst_rad, double d_ref_mpc,
                              PointParams &pp_out, std::vector<float> &qp, std::vector<float> &uv,
-                             std::vector<float> &quad);
+                             std::vector<float> &quad, bool host_q = true);
 void ile_fill_result(const double pooled[4], const double *ilog, int n_iter, ile_adapt_result *out);

@@ -358,6 +358,30 @@ size_t ile_tc_q_bytes(int prec, int K, int M, int T_ext) {
     return (size_t)K * KC * ile_tc_tpad(T_ext) * 16;
 }
 
+namespace {
+// FP32 operand rows of Q from its FP64 copy: Qp[k][a][t] = Re Q, Qp[k][M + a][t] = Im Q; a
+// non-finite entry raises ILE_FLAG_NONFINITE in *chk.
+__global__ void q_convert_kernel(const double2 *__restrict__ Q64, int K, int M, int T, float *__restrict__ Qp,
+                                 unsigned *__restrict__ chk) {
+    const int64_t total = (int64_t)K * M * T;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 q = Q64[i];
+        const int64_t ka = i / T;
+        const int t = (int)(i - ka * T), k = (int)(ka / M), a = (int)(ka - (int64_t)k * M);
+        Qp[((int64_t)k * 2 * M + a) * T + t] = (float)q.x;
+        Qp[((int64_t)k * 2 * M + M + a) * T + t] = (float)q.y;
+        bad = bad || !isfinite(q.x) || !isfinite(q.y);
+    }
+    if (bad) atomicOr(chk, ILE_FLAG_NONFINITE);
+}
+}  // namespace
+
+cudaError_t ile_launch_q_convert(const double2 *Q64, int K, int M, int T, float *Qp, unsigned *chk, cudaStream_t st) {
+    q_convert_kernel<<<256, 256, 0, st>>>(Q64, K, M, T, Qp, chk);
+    return cudaGetLastError();
+}
+
 cudaError_t ile_launch_tc_split(int prec, const PointParams &pp, const float *Qp, const float *quad, void *hi,
                                 void *lo, cudaStream_t st) {
     const int KP = ile_tc_kpad(prec, pp.M), TP = ile_tc_tpad(pp.T_ext);

@@ -50,7 +50,7 @@ cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo
     one.TP = TP;
     one.KP = KP;
     one.loud = (full_grid || pp.dm.on) ? LoudList{nullptr, 0.f, 0, 0} : loud;
-    if (!pp.dm.on) return launch_one<OP_BF16_SMEM, false>(pp, one, ntiles, KP, full_grid, flags, st);
+    if (!pp.dm.on) return launch_one<OP_BF16_SMEM_N, false>(pp, one, ntiles, KP, full_grid, flags, st);
     if (acols_needed(OP_BF16_TMEM, pp.K, KP) <= acol_of(OP_BF16_TMEM))
         return launch_one<OP_BF16_TMEM, true>(pp, one, ntiles, KP, full_grid, flags, st);
     return launch_one<OP_BF16_SMEM, true>(pp, one, ntiles, KP, full_grid, flags, st);

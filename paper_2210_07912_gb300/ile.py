@@ -355,9 +355,8 @@ class Context:
         lm = np.ascontiguousarray(p.lm, np.int32)
         tens = np.ascontiguousarray(p.det_tensor, np.float64)
         pos = np.ascontiguousarray(p.det_pos, np.float64)
-        Q = np.ascontiguousarray(np.stack([p.Q.real, p.Q.imag], -1), np.float64)
-        U = np.ascontiguousarray(np.stack([p.U.real, p.U.imag], -1), np.float64)
-        V = np.ascontiguousarray(np.stack([p.V.real, p.V.imag], -1), np.float64)
+        # complex128 arrays already hold (re, im) pairs in the [..][2] layout the library takes
+        Q, U, V = (np.ascontiguousarray(x, np.complex128).view(np.float64) for x in (p.Q, p.U, p.V))
         K, M, T = p.Q.shape
         st = self._lib.ile_set_data(self._h, K, M, _np_ptr(lm), _np_ptr(tens), _np_ptr(pos), _np_ptr(Q), T,
                                     float(p.t_start), float(p.fs), _np_ptr(U), _np_ptr(V), int(p.n_window),

@@ -200,3 +200,21 @@ def test_nearest_sample_mode_matches_oracle(ile, orc, prec):
         assert np.abs(got - ref).max() < 1e-3, (name, prec)
         # and the nearest mode is a different function from the interpolated one
         assert np.abs(ctx.eval(th) - ref).max() > 1e-6
+
+
+def test_set_data_nonfinite_q(ile, orc):
+    """A non-finite Q is found on the device while Q is converted: ILE_E_NONFINITE, and the
+    context then has no point until the next successful ile_set_data (which evaluates as usual)."""
+    point = S.workload_point(S.SMALL)
+    c = ile.Context(0)
+    q = point.Q.copy()
+    q[1, 0, 7] = complex(np.inf, 0.0)
+    with pytest.raises(ile.IleError) as e:
+        c.set_data(S.Point(**{**point.__dict__, "Q": q}))
+    assert e.value.status == ile.ILE_E_NONFINITE
+    th = S.workload_samples(S.SMALL, 64)
+    with pytest.raises(ile.IleError) as e:
+        c.eval(th)
+    assert e.value.status == ile.ILE_E_STATE
+    c.set_data(point)
+    assert np.abs(c.eval(th) - orc.lnL_t(point, th)).max() < 1e-3

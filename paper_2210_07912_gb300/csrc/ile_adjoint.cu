@@ -809,6 +809,12 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid
                  "l"(src), "r"(valid ? 4 : 0)
                  : "memory");
 }
+// 16 bytes, or 16 zero bytes when !valid (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
@@ -927,11 +933,14 @@ struct GqTcSmem {
     float raw[2][QNC][QRW];
     float Cc[2][RMAX][QNC + 1];  // odd row stride: the B packing reads one row per lane
     int i0c[2][QNC];
+    int oc[2][QNC];  // offset of pi column t0 - i0 - 1 in its staged row (16-byte staging)
     float wc[2][QNC];
     uint64_t mma[2];
     uint32_t tmem;
     int abort;
 };
+// 16-byte staging: rows start 16-byte aligned and hold the QTB + 1 values at offsets up to 3
+static_assert(QRW % 4 == 0 && QRW >= QTB + 4 && TC_BUF % 16 == 0, "16-byte pi staging");
 
 __global__ void __launch_bounds__(256, 2)
     adj_gq_tc_kernel(const __grid_constant__ PointParams pp, const float *__restrict__ pig, IleScratch s, int64_t N,
@@ -974,16 +983,30 @@ __global__ void __launch_bounds__(256, 2)
     };
     // warp w stages the pi row segments of samples w, w + 8, ... (lanes along the row) and the
     // coefficient rows w, w + 8, ... (lanes along the samples)
+    // (with N_t a multiple of 4, pi rows are 16-byte aligned: a row segment moves in 16-byte pieces
+    // from the 4-aligned column at or below t0 - i0 - 1; every piece lies wholly inside the window
+    // [0, N_t) or wholly outside it (zero-filled), and the segment starts oc = (t0 - i0 - 1) mod 4
+    // floats into its staged row)
+    const bool v16 = (Nt & 3) == 0;
     auto issue = [&](int c, int b) {
         const int64_t c0 = nb + (int64_t)c * QNC;
         const int nc = (int)min((int64_t)QNC, ne - c0);
         for (int j = warp; j < QNC; j += 8) {
             const int base = t0 - sm.i0c[b][j] - 1;  // pi column of staged element 0
             const float *row = pig + (size_t)(c0 + (j < nc ? j : 0)) * Nt;
-            for (int m = lane; m < QTB + 1; m += 32) {
-                const int idx = base + m;
-                const bool ok = j < nc && idx >= 0 && idx < Nt;
-                cp_async4(&sm.raw[b][j][m], row + (ok ? idx : 0), ok);
+            if (v16) {
+                const int sb = base & ~3;  // rounded down to a multiple of 4
+                for (int q = lane; q < QRW / 4; q += 32) {
+                    const int idx = sb + 4 * q;
+                    const bool ok = j < nc && idx >= 0 && idx < Nt;
+                    cp_async16(&sm.raw[b][j][4 * q], row + (ok ? idx : 0), ok);
+                }
+            } else {
+                for (int m = lane; m < QTB + 1; m += 32) {
+                    const int idx = base + m;
+                    const bool ok = j < nc && idx >= 0 && idx < Nt;
+                    cp_async4(&sm.raw[b][j][m], row + (ok ? idx : 0), ok);
+                }
             }
         }
         const bool okj = lane < nc;
@@ -998,6 +1021,7 @@ __global__ void __launch_bounds__(256, 2)
         float w;
         load_iw(0, a, w);
         sm.i0c[0][tid] = a;
+        sm.oc[0][tid] = v16 ? ((t0 - a - 1) & 3) : 0;
         sm.wc[0][tid] = w;
         load_iw(1, ri0, rw);
     }
@@ -1011,6 +1035,7 @@ __global__ void __launch_bounds__(256, 2)
         const int b = c & 1;
         if (tid < QNC) {
             sm.i0c[b ^ 1][tid] = ri0;  // chunk c + 1
+            sm.oc[b ^ 1][tid] = v16 ? ((t0 - ri0 - 1) & 3) : 0;
             sm.wc[b ^ 1][tid] = rw;
             load_iw(c + 2, ri0, rw);
         }
@@ -1040,7 +1065,8 @@ __global__ void __launch_bounds__(256, 2)
             for (int e = 0; e < 8; e++) {
                 const int j = 8 * g + e;
                 const float w = sm.wc[b][j];
-                v[e] = (1.f - w) * sm.raw[b][j][t + 1] + w * sm.raw[b][j][t];
+                const float *rr = sm.raw[b][j] + sm.oc[b][j];
+                v[e] = (1.f - w) * rr[t + 1] + w * rr[t];
             }
             uint4 h, l;
             pack_chunk<true>(v, h, l);

@@ -147,15 +147,18 @@ struct MainSmem {
 };
 
 template <int NS, bool TC>
-__global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
+__global__ void __launch_bounds__(TC ? 512 : 256, NS == 32 ? 2 : 1)
     adj_main_kernel(const __grid_constant__ PointParams pp, const float *__restrict__ Qp, const float4 *__restrict__ UV,
                     IleScratch s, const int *__restrict__ perm, const double *__restrict__ samples,
                     const double *__restrict__ g_lnL, int64_t N, float *__restrict__ pig,
                     const float *__restrict__ Din, const uint4 *__restrict__ QThi, const uint4 *__restrict__ QTlo,
                     unsigned *flags, double *__restrict__ g_samples, double *__restrict__ lnl_out) {
     static_assert(!TC || NS == TC_NS, "tensor-core form: 64 samples per CTA");
-    constexpr int RS = NS / 16;  // samples per thread in both GEMM micro-tiles
-    constexpr int SUB = 256 / NS;  // threads per sample in the per-sample stages (mode or pair splits)
+    // threads per CTA: 16 warps in the tensor-core form (one 219 KB CTA per SM; more warps hide
+    // the latency of its D loads, softmax and operand builds), 8 in the CUDA-core form
+    constexpr int NT = TC ? 512 : 256, NW = NT / 32;
+    constexpr int RS = NS / 16;  // samples per thread in both GEMM micro-tiles (CUDA-core form)
+    constexpr int SUB = NT / NS;  // threads per sample in the per-sample stages (mode or pair splits)
     constexpr int PLD = NS + 4;
     constexpr int YLD = 4 * ILE_MAX_MODES + 1;
     extern __shared__ __align__(16) float smem[];
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     __shared__ int lo_s[ILE_MAX_DET], hi_s[ILE_MAX_DET];
     __shared__ float Ss[ILE_MAX_DET][NS];
     __shared__ float proj[ILE_MAX_DET][6][NS];
-    __shared__ int red[2][8];
+    __shared__ int red[2][NW];
     __shared__ uint16_t pab[ILE_MAX_MODES * (ILE_MAX_MODES + 1) / 2];
     __shared__ uint64_t tc_bfull[2], tc_mma[2], tc_aready[2];
     __shared__ uint32_t tc_tmem;
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
             for (int b = 0; b < 2; b++) {
                 mbar_init(&tc_bfull[b], 1);
                 mbar_init(&tc_mma[b], 1);
-                mbar_init(&tc_aready[b], 256);
+                mbar_init(&tc_aready[b], NT);
             }
             tc_abort = 0;
             mbar_init_fence();
@@ -207,14 +210,14 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
     }
 
     if (LDD == Nt) {
-        for (int i = tid; i < NS * Nt; i += 256) Ds[i] = (Din && i < ns * Nt) ? Din[n0 * Nt + i] : 0.f;
+        for (int i = tid; i < NS * Nt; i += NT) Ds[i] = (Din && i < ns * Nt) ? Din[n0 * Nt + i] : 0.f;
     } else {
         // odd row stride: a warp moves 4 rows x 8 float4 (whole 128-byte lines, one per row); lane l
         // stores to row 4 i + l / 8 at column 4 (l % 8) + e, i.e. 32 distinct banks per store
         const int NT4 = Nt / 4, rr = lane >> 3, cc = lane & 7;
         const float4 *src4 = reinterpret_cast<const float4 *>(Din + n0 * Nt);
 #pragma unroll 8
-        for (int it = warp; it < (NS / 4) * (NT4 / 8); it += 8) {
+        for (int it = warp; it < (NS / 4) * (NT4 / 8); it += NW) {
             const int rg = it / (NT4 / 8), c4 = (it - rg * (NT4 / 8)) * 8 + cc, nn = rg * 4 + rr;
             const float4 v = nn < ns ? src4[(size_t)nn * NT4 + c4] : make_float4(0.f, 0.f, 0.f, 0.f);
             float *d = Ds + nn * LDD + 4 * c4;
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
             i0s[tid] = s.I0[(int64_t)k * N + n0 + nn];
             ws[tid] = s.W[(int64_t)k * N + n0 + nn];
         }
-        for (int i = tid; i < R * NS; i += 256) {
+        for (int i = tid; i < R * NS; i += NT) {
             int r = i / NS, nn = i - r * NS;
             Cs[r * NS + nn] = nn < ns ? s.C[((int64_t)k * R + r) * N + n0 + nn] : 0.f;
         }
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
         load_detector(k);
         __syncthreads();
         int lo = 0x7fffffff, hi = -0x7fffffff;
-        for (int i = tid; i < ns; i += 256) {
+        for (int i = tid; i < ns; i += NT) {
             lo = min(lo, i0s[i]);
             hi = max(hi, i0s[i]);
         }
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
         __syncthreads();
         lo = red[0][0];
         hi = red[1][0];
-        for (int w = 1; w < 8; w++) {
+        for (int w = 1; w < NW; w++) {
             lo = min(lo, red[0][w]);
             hi = max(hi, red[1][w]);
         }
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
             lo_s[k] = lo;
             hi_s[k] = hi;
         }
-        if (Din) continue;  // D(n, j) came from the tensor-core forward kernel
+        if (TC || Din) continue;  // D(n, j) came from the tensor-core forward kernel (always, in that form)
         const int cend = hi + Nt;
         for (int c0 = lo; c0 <= cend; c0 += TCOL) {
             __syncthreads();
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
                     for (int j = 0; j < 4; j++) Gs[(ty * RS + i) * (TCOL + 1) + tx * 4 + j] = acc[i][j];
             }
             __syncthreads();
-            for (int nn = warp; nn < ns; nn += 8) {
+            for (int nn = warp; nn < ns; nn += NW) {
                 const int i0 = i0s[nn];
                 const float wt = ws[nn];
                 const int jlo = max(0, c0 - 1 - i0), jhi = min(Nt - 1, c0 + TCOL - 1 - i0);
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
 
     // ---------------------------------------------------------------- phase 2: window softmax
     const double log_nt = log((double)Nt);
-    for (int nn = warp; nn < ns; nn += 8) {
+    for (int nn = warp; nn < ns; nn += NW) {
         float *d = Ds + (size_t)nn * LDD;
         const int64_t src = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
         float m = -INFINITY;
@@ -403,6 +406,9 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
         // still reads it: from then on A, B and TMEM hold garbage by design, the call's outputs are
         // discarded and only ILE_E_TIMEOUT is returned; the drain wait on the last commit before
         // TMEM is released stays.
+        // thread (nn, q0) builds the K chunks q0, q0 + NT / 64, ... of rows nn and 64 + nn
+        constexpr int QSTEP = NT / TC_NS, QPT = (AM_COLS / 8) / QSTEP;
+        static_assert(QPT * QSTEP == AM_COLS / 8, "K chunks per thread");
         const int nn = tid & (TC_NS - 1), q0 = tid >> 6;
         uint8_t *tcb = reinterpret_cast<uint8_t *>(U1);
         uint4 *Ah = reinterpret_cast<uint4 *>(tcb), *Al = Ah + AM_A_BYTES / 16;
@@ -446,8 +452,8 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
                     const float wt = ws[nn];
                     const float *pr = Ds + (size_t)nn * LDD;
 #pragma unroll
-                    for (int it = 0; it < 2; it++) {
-                        const int q = q0 + 4 * it;
+                    for (int it = 0; it < QPT; it++) {
+                        const int q = q0 + QSTEP * it;
                         const int j0 = c0 + 8 * q - i0s[nn];  // window bin of the chunk's column 8 q
                         float pe[8], pd[8];
                         float prev = (j0 >= 1 && j0 <= Nt) ? pr[j0 - 1] : 0.f;
@@ -622,9 +628,9 @@ __global__ void __launch_bounds__(256, NS == 32 ? 2 : 1)
 
     // ---------------------------------------------------------------- epilogue: chain rule to theta
     const int P = M * (M + 1) / 2;
-    for (int i = tid; i < K * P; i += 256) UVs[i] = UV[i];
+    for (int i = tid; i < K * P; i += NT) UVs[i] = UV[i];
     // mode pairs (a <= b) in the order of the UV table
-    for (int i = tid; i < P; i += 256) {
+    for (int i = tid; i < P; i += NT) {
         int a = 0, rest = i;
         while (rest >= M - a) rest -= M - a++;
         pab[i] = (uint16_t)(a | ((a + rest) << 8));
@@ -1327,7 +1333,8 @@ cudaError_t launch_main(const PointParams &pp, const float *Qp, const float *UV,
         cudaFuncSetAttribute(adj_main_kernel<NS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (N + NS - 1) / NS;
-    adj_main_kernel<NS, TC><<<(unsigned)blocks, 256, smem, st>>>(pp, Qp, (const float4 *)UV, s, perm, samples, g, N,
+    if (TC && !Din) return cudaErrorInvalidValue;  // the tensor-core form takes D(n, j) from the forward kernel
+    adj_main_kernel<NS, TC><<<(unsigned)blocks, TC ? 512 : 256, smem, st>>>(pp, Qp, (const float4 *)UV, s, perm, samples, g, N,
                                                                  pig, Din, (const uint4 *)QThi, (const uint4 *)QTlo,
                                                                  flags, g_samples, lnl);
     return cudaGetLastError();

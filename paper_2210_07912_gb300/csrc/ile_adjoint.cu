@@ -351,19 +351,34 @@ __global__ void __launch_bounds__(TC ? 512 : 256, NS == 32 ? 2 : 1)
 
     // projections of detector k's E on the harmonics: e = sum_a conj(E_a) y_a, with y -> dy/diota,
     // i m y; SUB threads per sample, thread sub taking the modes a = sub, sub + SUB, ...
+    // the sample's harmonics and their iota derivatives for this thread's modes a = sub + SUB i,
+    // formed once: they serve every detector's projection and the chain rule
+    constexpr int YPT = (ILE_MAX_MODES + SUB - 1) / SUB;
+    float yh[YPT][4];
+    {
+        const int nn = tid / SUB, sub = tid % SUB, nv = nn < ns ? nn : 0;
+        const int64_t src = perm ? (int64_t)perm[n0 + nv] : n0 + nv;
+        const float iota = (float)samples[3 * N + src], phi = (float)samples[4 * N + src];
+        float cpow[10], spow[10], er5[5], ei5[5];
+        half_angle_powers10(iota, cpow, spow);
+        ile_phase_powers(phi, er5, ei5);
+#pragma unroll
+        for (int i = 0; i < YPT; i++) {
+            const int a = sub + SUB * i;
+            yh[i][0] = yh[i][1] = yh[i][2] = yh[i][3] = 0.f;
+            if (a < M) sylm_and_diota(pp.mode[a], cpow, spow, er5, ei5, yh[i][0], yh[i][1], yh[i][2], yh[i][3]);
+        }
+    }
     auto project = [&](int k) {
         const int nn = tid / SUB, sub = tid % SUB;
         float er = 0.f, ei = 0.f, gr = 0.f, gi = 0.f, fr = 0.f, fi = 0.f;
         if (nn < ns) {
-            const int64_t src = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
-            const float iota = (float)samples[3 * N + src], phi = (float)samples[4 * N + src];
-            float cpow[10], spow[10], er5[5], ei5[5];
-            half_angle_powers10(iota, cpow, spow);
-            ile_phase_powers(phi, er5, ei5);
             const float *E = Es + nn * (RMAX + 1);
-            for (int a = sub; a < M; a += SUB) {
-                float yr, yi, dr, di;
-                sylm_and_diota(pp.mode[a], cpow, spow, er5, ei5, yr, yi, dr, di);
+#pragma unroll
+            for (int i = 0; i < YPT; i++) {
+                const int a = sub + SUB * i;
+                if (a >= M) break;
+                const float yr = yh[i][0], yi = yh[i][1], dr = yh[i][2], di = yh[i][3];
                 const float Er = E[a], Ei = E[M + a], mm = (float)pp.mode[a].m;
                 er += Er * yr + Ei * yi;
                 ei += Er * yi - Ei * yr;
@@ -637,14 +652,17 @@ __global__ void __launch_bounds__(TC ? 512 : 256, NS == 32 ? 2 : 1)
     }
     const int nn = tid / SUB, sub = tid % SUB;  // SUB threads per sample from here on
     if (nn < ns) {
-        const int64_t src = perm ? (int64_t)perm[n0 + nn] : n0 + nn;
-        const float iota = (float)samples[3 * N + src], phi = (float)samples[4 * N + src];
-        float cpow[10], spow[10], er5[5], ei5[5];
-        half_angle_powers10(iota, cpow, spow);
-        ile_phase_powers(phi, er5, ei5);
         float *y = Ys + nn * YLD;
-        for (int a = sub; a < M; a += SUB)
-            sylm_and_diota(pp.mode[a], cpow, spow, er5, ei5, y[4 * a], y[4 * a + 1], y[4 * a + 2], y[4 * a + 3]);
+#pragma unroll
+        for (int i = 0; i < YPT; i++) {
+            const int a = sub + SUB * i;
+            if (a < M) {
+                y[4 * a] = yh[i][0];
+                y[4 * a + 1] = yh[i][1];
+                y[4 * a + 2] = yh[i][2];
+                y[4 * a + 3] = yh[i][3];
+            }
+        }
     }
     __syncthreads();
     {

@@ -64,7 +64,11 @@ typedef enum {
     ILE_E_TIMEOUT = 7    /* a bounded device-side wait gave up */
 } ile_status;
 
-/* Arithmetic of the shifted contraction (S3); every other stage is the same in all modes. */
+/* Arithmetic of the shifted contraction (S3); every other stage is the same in all modes.  Both
+ * split precisions run the fused S1-S5 kernel (the quadratic term S4 as one more product per
+ * detector in the same precision); TF32X3 keeps the coefficient operand in tensor memory and falls
+ * back to an unfused kernel (S1, S2, S4 in FP32 on CUDA cores) for points with
+ * n_det x (2 n_modes rounded up to 8) > 160. */
 typedef enum {
     ILE_PREC_FP32 = 0,   /* FP32 CUDA-core GEMM ("plain") */
     ILE_PREC_TF32X3 = 1, /* tcgen05 kind::tf32, hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM */

@@ -60,6 +60,16 @@ def test_batch_equals_single_point_runs(ile):
         _assert_same(res[i], _single(ile, p, c, "bf16x3", 3), f"point {i}")
 
 
+def test_batch_tf32_equals_single_point_runs(ile):
+    """TF32x3 batches run the fused TF32x3 kernel point by point (A operand in TMEM), as a
+    single-point run of each point does: the results agree bit for bit."""
+    points, cfgs = _batch_inputs(ile, seed=550)
+    b = ile.Batch(0, None, "tf32x3")
+    res = b.run(points, cfgs, 2)
+    for i, (p, c) in enumerate(zip(points, cfgs)):
+        _assert_same(res[i], _single(ile, p, c, "tf32x3", 2), f"point {i}")
+
+
 def test_batch_fp32_path_matches_single_point_runs(ile):
     """The plain FP32 path adds a window bin's two interpolation terms in the order of the
     64-column chunks, whose boundaries follow the tile's first column, i.e. the (atomic) sort

@@ -955,7 +955,7 @@ static_assert(TC_KC * 8 == QNC, "one dQ chunk is TC_KC 16-byte K chunks of sampl
 struct GqTcSmem {
     uint8_t ops[2][TC_BUF];  // A hi | A lo | B hi | B lo
     float raw[2][QNC][QRW];
-    float Cc[2][RMAX][QNC + 1];  // odd row stride: the B packing reads one row per lane
+    float Cc[2][RMAX][QNC + 4];  // 16-byte rows: 16-byte staging copies and packing loads
     int i0c[2][QNC];
     int oc[2][QNC];  // offset of pi column t0 - i0 - 1 in its staged row (16-byte staging)
     float wc[2][QNC];
@@ -965,6 +965,7 @@ struct GqTcSmem {
 };
 // 16-byte staging: rows start 16-byte aligned and hold the QTB + 1 values at offsets up to 3
 static_assert(QRW % 4 == 0 && QRW >= QTB + 4 && TC_BUF % 16 == 0, "16-byte pi staging");
+static_assert((QNC + 4) % 4 == 0 && QNC % 32 == 0, "16-byte coefficient staging");
 
 __global__ void __launch_bounds__(256, 2)
     adj_gq_tc_kernel(const __grid_constant__ PointParams pp, const float *__restrict__ pig, IleScratch s, int64_t N,
@@ -973,7 +974,10 @@ __global__ void __launch_bounds__(256, 2)
     GqTcSmem &sm = *reinterpret_cast<GqTcSmem *>(gq_raw);
     const int Nt = pp.Nt, R = 2 * pp.M, T = pp.T_ext;
     const int t0 = blockIdx.x * QTB, k = blockIdx.y, split = blockIdx.z;
-    const int64_t nb = N * split / nsplit, ne = N * (split + 1) / nsplit;
+    // sample splits start on 32-sample boundaries, so that with N a multiple of 4 every chunk's
+    // coefficient columns start 16-byte aligned
+    auto bound = [&](int sp) { return sp >= nsplit ? N : (N * sp / nsplit) & ~(int64_t)31; };
+    const int64_t nb = bound(split), ne = bound(split + 1);
     const int nch = (int)((ne - nb + QNC - 1) / QNC);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -985,7 +989,7 @@ __global__ void __launch_bounds__(256, 2)
         mbar_init_fence();
     }
     // coefficient rows R .. RMAX - 1 stay zero (the copies write rows < R only)
-    for (int i = tid; i < 2 * RMAX * (QNC + 1); i += 256) (&sm.Cc[0][0][0])[i] = 0.f;
+    for (int i = tid; i < 2 * RMAX * (QNC + 4); i += 256) (&sm.Cc[0][0][0])[i] = 0.f;
     fence_before();
     __syncthreads();
     fence_after();
@@ -1011,7 +1015,7 @@ __global__ void __launch_bounds__(256, 2)
     // from the 4-aligned column at or below t0 - i0 - 1; every piece lies wholly inside the window
     // [0, N_t) or wholly outside it (zero-filled), and the segment starts oc = (t0 - i0 - 1) mod 4
     // floats into its staged row)
-    const bool v16 = (Nt & 3) == 0;
+    const bool v16 = (Nt & 3) == 0, c16 = (N & 3) == 0;
     auto issue = [&](int c, int b) {
         const int64_t c0 = nb + (int64_t)c * QNC;
         const int nc = (int)min((int64_t)QNC, ne - c0);
@@ -1033,9 +1037,19 @@ __global__ void __launch_bounds__(256, 2)
                 }
             }
         }
-        const bool okj = lane < nc;
-        for (int r = warp; r < R; r += 8)
-            cp_async4(&sm.Cc[b][r][lane], s.C + ((int64_t)k * R + r) * N + c0 + (okj ? lane : 0), okj);
+        if (c16) {
+            // coefficient rows in 16-byte pieces of 4 samples (N a multiple of 4, c0 of 32; ne is
+            // a multiple of 4 too, so every piece is wholly inside the split or outside it)
+            for (int i = tid; i < R * (QNC / 4); i += 256) {
+                const int r = i / (QNC / 4), q = i % (QNC / 4);
+                const bool ok = 4 * q < nc;
+                cp_async16(&sm.Cc[b][r][4 * q], s.C + ((int64_t)k * R + r) * N + c0 + (ok ? 4 * q : 0), ok);
+            }
+        } else {
+            const bool okj = lane < nc;
+            for (int r = warp; r < R; r += 8)
+                cp_async4(&sm.Cc[b][r][lane], s.C + ((int64_t)k * R + r) * N + c0 + (okj ? lane : 0), okj);
+        }
     };
 
     int ri0 = 0;
@@ -1100,9 +1114,13 @@ __global__ void __launch_bounds__(256, 2)
         // B: thread (r, g) packs C(r, 8 g .. 8 g + 7); rows RMAX .. RP - 1 are zero
         if (tid < RP * (QNC / 8)) {
             const int r = tid % RP, g = tid / RP;
-            float v[8];
-#pragma unroll
-            for (int e = 0; e < 8; e++) v[e] = r < RMAX ? sm.Cc[b][r][8 * g + e] : 0.f;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
+            if (r < RMAX) {
+                const float4 *cr = reinterpret_cast<const float4 *>(&sm.Cc[b][r][8 * g]);
+                x = cr[0];
+                y = cr[1];
+            }
+            const float v[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
             uint4 h, l;
             pack_chunk<true>(v, h, l);
             Bh[g * RP + r] = h;

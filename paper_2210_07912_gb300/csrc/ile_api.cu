@@ -454,15 +454,17 @@ ile_status run_grad(ile_ctx *ctx, const double *dsamples, const double *dg, int6
         CK(ensure_bytes(ctx, &ctx->guv_part, &ctx->guv_bytes,
                         sizeof(float) * (size_t)nblk * pp.K * (pp.M * (pp.M + 1) / 2) * 4));
     {
-        StageScope t(ctx, 1, 4);
+        // (the BF16x3 D(n, j) pass below writes the per-sample coefficients, window placements and
+        // quadratic term itself; other contexts form them with the coefficient kernel)
+        StageScope t(ctx, 1, tc2_fwd ? 3 : 4);
         CK(ile_launch_sort(pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));
-        CK(ile_launch_prep(pp, ctx->UV, dsamples, ctx->perm, N, ctx->s, ctx->flags, ctx->stream));
+        if (!tc2_fwd) CK(ile_launch_prep(pp, ctx->UV, dsamples, ctx->perm, N, ctx->s, ctx->flags, ctx->stream));
     }
     StageScope t(ctx, 5, 1 + (tc2_fwd ? 1 : 0) + (gQ ? 2 : 0) + ((gU || gV) ? 2 : 0));
     if (tc2_fwd)
         CK(ile_launch_tc2(pp, ctx->Qtc[ILE_PREC_BF16X3][0], ctx->Qtc[ILE_PREC_BF16X3][1], ile_tc_tpad(pp.T_ext),
                           ile_tc_kpad(ILE_PREC_BF16X3, pp.M), ctx->UV, dsamples, ctx->perm, N, nullptr, pig, 2,
-                          LoudList{nullptr, 0.f, 0, 0}, ctx->flags, ctx->stream));
+                          LoudList{nullptr, 0.f, 0, 0}, ctx->flags, ctx->stream, &ctx->s));
     if (g_theta || gQ || lnl)
         CK(ile_launch_grad_main(pp, ctx->Qp, ctx->UV, ctx->s, ctx->perm, dsamples, dg, N, pig,
                                 tc2_fwd ? pig : nullptr, tc_adj ? ctx->Qadj[0] : nullptr,

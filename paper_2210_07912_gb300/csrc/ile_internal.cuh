@@ -518,6 +518,11 @@ struct Tc2Point {
     const int *perm;        // [N] processing order -> caller index
     double *out;            // [N]
     float *grid_f;          // grid mode 2: data term D(n, j) in processing order [N][N_t]
+    // grid mode 2 (may be null): the per-sample coefficients C [K][2M][N], window starts I0 [K][N],
+    // lerp weights W [K][N] and quadratic term A [N] in processing order, as ile_prep_kernel writes them
+    float *sC;
+    int *sI0;
+    float *sW, *sA;
     int64_t N;
     int TP, KP;
     LoudList loud;          // loud samples for the FP64 refinement (single-point launches)
@@ -573,9 +578,11 @@ cudaError_t ile_launch_tc(int prec, const PointParams &pp, const void *hi, const
                           cudaStream_t st);
 // full_grid 0: lnL_t into out (caller order); 1: the grid lnL(n, j) into out (caller order);
 // 2: the data term D(n, j) in FP32 into grid_f, rows in processing (sorted) order
+// (scr, grid mode 2 only, may be null: the per-sample C, I0, W, A are written there too)
 cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo, int TP, int KP, const float *UV,
                            const double *samples, const int *perm, int64_t N, double *out, float *grid_f,
-                           int full_grid, LoudList loud, unsigned *flags, cudaStream_t st);
+                           int full_grid, LoudList loud, unsigned *flags, cudaStream_t st,
+                           const IleScratch *scr = nullptr);
 // the same kernel in TF32x3 with its A operand in TMEM (ile_tc3.cu), for points with
 // ile_tc3_fits(K, KP) (KP the TF32 operand rows); full_grid 0 or 1
 bool ile_tc3_fits(int K, int KP);

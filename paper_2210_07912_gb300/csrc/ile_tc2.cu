@@ -4,22 +4,23 @@
 
 namespace {
 
-// One single-point launch of operand variant OP (DM: distance-marginalised epilogue).
-template <int OP, bool DM>
+// One single-point launch of operand variant OP (DM: distance-marginalised epilogue; ADJ: the
+// adjoint's D(n, j) pass with its per-sample outputs).
+template <int OP, bool DM, bool ADJ = false>
 cudaError_t launch_one(const PointParams &pp, const Tc2Point &one, int64_t ntiles, int KP, int full_grid,
                        unsigned *flags, cudaStream_t st) {
     int NB = NBMAX;
     while (NB > 2 && tc2_smem<OP>(pp.K, pp.M, KP, NB) > SMEM_LIMIT) NB--;
     const size_t smem = tc2_smem<OP>(pp.K, pp.M, KP, NB);
     if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(ile_tc2_kernel<false, DM, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(ile_tc2_kernel<false, DM, OP, ADJ>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // a window (plus up to 7 columns of 8-column alignment) fits one accumulator buffer
     const int nwcol = bw_of(OP) - 7 < NWCOL ? bw_of(OP) - 7 : NWCOL;
     const int sms = sm_count();
     const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-    ile_tc2_kernel<false, DM, OP><<<grid, NTHREADS, smem, st>>>(one, nullptr, nullptr, ntiles, pp.K, KP / 8,
+    ile_tc2_kernel<false, DM, OP, ADJ><<<grid, NTHREADS, smem, st>>>(one, nullptr, nullptr, ntiles, pp.K, KP / 8,
                                                                 pp.M * (pp.M + 1) / 2, NB, nwcol, full_grid, flags);
     return cudaGetLastError();
 }
@@ -34,7 +35,7 @@ cudaError_t launch_one(const PointParams &pp, const Tc2Point &one, int64_t ntile
 // there (1.633 against 1.670 ms per 2^20 samples).  Both give identical results.
 cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo, int TP, int KP, const float *UV,
                            const double *samples, const int *perm, int64_t N, double *out, float *grid_f,
-                           int full_grid, LoudList loud, unsigned *flags, cudaStream_t st) {
+                           int full_grid, LoudList loud, unsigned *flags, cudaStream_t st, const IleScratch *scr) {
     if (N <= 0) return cudaSuccess;
     const int64_t ntiles = (N + TILE - 1) / TILE;
     Tc2Point one{};
@@ -46,10 +47,17 @@ cudaError_t ile_launch_tc2(const PointParams &pp, const void *hi, const void *lo
     one.perm = perm;
     one.out = out;
     one.grid_f = grid_f;
+    if (full_grid == 2 && scr) {
+        one.sC = scr->C;
+        one.sI0 = scr->I0;
+        one.sW = scr->W;
+        one.sA = scr->A;
+    }
     one.N = N;
     one.TP = TP;
     one.KP = KP;
     one.loud = (full_grid || pp.dm.on) ? LoudList{nullptr, 0.f, 0, 0} : loud;
+    if (!pp.dm.on && full_grid == 2 && scr) return launch_one<OP_BF16_SMEM_N, false, true>(pp, one, ntiles, KP, 2, flags, st);
     if (!pp.dm.on) return launch_one<OP_BF16_SMEM_N, false>(pp, one, ntiles, KP, full_grid, flags, st);
     if (acols_needed(OP_BF16_TMEM, pp.K, KP) <= acol_of(OP_BF16_TMEM))
         return launch_one<OP_BF16_TMEM, true>(pp, one, ntiles, KP, full_grid, flags, st);

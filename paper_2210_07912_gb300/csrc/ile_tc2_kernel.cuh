@@ -224,7 +224,9 @@ __device__ __forceinline__ const Tc2Point &work_item(const Tc2Point &one, const 
 // factors, window starts, iota, phi), computed by the prefetch warp from the parameters it gathers
 // through the sort permutation while the previous tile is in flight.  Before
 // the job loop the rows area holds the tile's harmonics table y [M][TILE] (float2).
-template <bool BATCH, bool DM, int OP>
+// ADJ: the adjoint's D(n, j) pass (grid mode 2), which also writes each sample's coefficients,
+// window placements and quadratic term (Tc2Point::sC, sI0, sW, sA)
+template <bool BATCH, bool DM, int OP, bool ADJ = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ile_tc2_kernel(const __grid_constant__ Tc2Point one, const Tc2Point *__restrict__ pts,
                    const int2 *__restrict__ items, int64_t nitems, int LK, int LKC, int LNP, int NB, int nwcol,
@@ -522,6 +524,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 wt[k] = x0 - fl;
             }
             const float iota = geo[12 * TILE + row], phi = geo[13 * TILE + row];
+            // grid mode 2 for the adjoint: this sample's window starts and lerp weights
+            if (ADJ && g == 0 && valid) {
+#pragma unroll
+                for (int k = 0; k < ILE_MAX_DET; k++)
+                    if (k < K) {
+                        pt.sI0[(int64_t)k * N + p] = i0[k];
+                        pt.sW[(int64_t)k * N + p] = wt[k];
+                    }
+            }
             // harmonics: thread g forms modes a = g, g + 4, ... into the shared y table (which
             // reuses the rows area: every thread has passed the previous tile's tdone)
             float2 *ys = reinterpret_cast<float2 *>(rows);  // [M][TILE]
@@ -561,6 +572,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         const float2 y = a < M ? ys[a * TILE + row] : make_float2(0.f, 0.f);
                         cv[e] = fr * y.x - fi * y.y;
                         cv[e + 1] = fr * y.y + fi * y.x;
+                    }
+                    // grid mode 2 for the adjoint: the coefficients, rows Re c_a at a, Im c_a at M + a
+                    if (ADJ && valid) {
+#pragma unroll
+                        for (int e = 0; e < 8; e++) {
+                            const int a = 4 * kc + e / 2;
+                            if (a < M) pt.sC[((int64_t)k * 2 * M + ((e & 1) ? M + a : a)) * N + p] = cv[e];
+                        }
                     }
                     if constexpr (TF32) {
                         // TMEM lane `row`: hi values at columns 2 k KP + r, lo values KP further
@@ -686,6 +705,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 failed = true;
                 break;
             }
+            // grid mode 2 for the adjoint: this sample's quadratic term
+            if (ADJ && g == 0 && valid)
+                pt.sA[p] = aq_s[q4 * 32 + lane] + aq_s[128 + q4 * 32 + lane] + aq_s[256 + q4 * 32 + lane] +
+                           aq_s[384 + q4 * 32 + lane];
             // distance-marginalised mode: per-bin terms ln F(D_j, A) with A this sample's quadratic term
             DmargSample dq{};
             if constexpr (DM)

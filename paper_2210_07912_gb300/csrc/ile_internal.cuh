@@ -172,16 +172,16 @@ __device__ __forceinline__ float2 ile_f2op_mul(float2 a, float2 b) {
 
 // ---- Distance-marginalised window bins without per-bin table reads.  For one sample (b fixed)
 // and one chunk of window bins, ln F(., b) over the chunk's data-term range [a_min, a_max] is its
-// degree-11 Chebyshev interpolant through the table values at the 12 Chebyshev points of that
-// range (Horner evaluation per bin): 12 table reads per sample and chunk instead of one per bin.
+// degree-9 Chebyshev interpolant through the table values at the 10 Chebyshev points of that
+// range (Horner evaluation per bin): 10 table reads per sample and chunk instead of one per bin.
 // Where a_max - a_min > ILE_DM_WMAX the bins keep their own table reads.  ln F is analytic in a
 // (a cumulant-generating function of x = D_ref / D on [x_min, x_max]).  Against FP64 quadrature of
-// ln F for b from 1e-4 to 1e4, the interpolant of the exact function is within 2.4e-5 of it on
-// ranges up to 12 wide; with node values carrying the tables' bilinear-interpolation error (an
-// emulation of the tables on the CPU) it stayed within that error (3.8e-4 against 4.1e-4 at the
-// worst ranges found): Chebyshev points amplify node errors by at most ~2.5, and the tables'
-// errors vary smoothly along a.
-constexpr int ILE_DM_NODES = 12;
+// ln F for b from 1e-4 to 1e4, the interpolant of the exact function is within 1e-4 of it on
+// ranges up to 12 wide (within 5.1e-5 where the data terms of real chunks lie: around 0, b and
+// 2b); node values carry the tables' bilinear-interpolation error, which Chebyshev points amplify
+// by at most ~2.4 and which varies smoothly along a.  (Degree 11 through 12 points was within
+// 2.4e-5; it cost a third more table reads and coefficient arithmetic per chunk.)
+constexpr int ILE_DM_NODES = 10;
 constexpr float ILE_DM_WMAX = 12.f;
 
 struct DmRange {
@@ -199,10 +199,10 @@ __device__ __forceinline__ DmRange ile_dm_range(float lo, float hi) {
     return r;
 }
 
-// x_k = cos(pi (k + 1/2) / 12), k = 0 .. 11
+// x_k = cos(pi (k + 1/2) / 10), k = 0 .. 9
 static __constant__ float ile_dm_xk[ILE_DM_NODES] = {
-    9.914448614e-01f,  9.238795325e-01f,  7.933533403e-01f,  6.087614290e-01f,  3.826834324e-01f,  1.305261922e-01f,
-    -1.305261922e-01f, -3.826834324e-01f, -6.087614290e-01f, -7.933533403e-01f, -9.238795325e-01f, -9.914448614e-01f};
+    9.876883406e-01f,  8.910065242e-01f,  7.071067812e-01f,  4.539904997e-01f,  1.564344650e-01f,
+    -1.564344650e-01f, -4.539904997e-01f, -7.071067812e-01f, -8.910065242e-01f, -9.876883406e-01f};
 
 // Chebyshev point k of the range: mid + half x_k
 __device__ __forceinline__ float ile_dm_node(const DmRange &r, int k) { return fmaf(r.half, ile_dm_xk[k], r.mid); }
@@ -222,36 +222,35 @@ __host__ __device__ constexpr IleChebMono ile_cheb_mono() {
 }
 
 // The interpolant as a polynomial in t = (a - mid) / half: Chebyshev coefficients
-// c_j = (2 - [j = 0]) / 12 sum_k f_k T_j(x_k) (using x_{11-k} = -x_k: T_j(x_{11-k}) = (-1)^j T_j(x_k)),
+// c_j = (2 - [j = 0]) / 10 sum_k f_k T_j(x_k) (using x_{9-k} = -x_k: T_j(x_{9-k}) = (-1)^j T_j(x_k)),
 // then m_i = sum_j a[i][j] c_j.  Rounding in c_j stays bounded by the size of T_j on [-1, 1] whatever
 // the monomial coefficients; in FP32 the result is within ~1e-5 of the FP64 Clenshaw sum on ranges
 // up to ILE_DM_WMAX with |a| < 2000 (above that the FP32 resolution of a itself dominates).
 __device__ __forceinline__ void ile_dm_coeffs(const float (&f)[ILE_DM_NODES], float (&m)[ILE_DM_NODES]) {
-    constexpr float T[ILE_DM_NODES][6] = {
-        {8.333333333e-02f, 8.333333333e-02f, 8.333333333e-02f, 8.333333333e-02f, 8.333333333e-02f, 8.333333333e-02f},
-        {1.652408102e-01f, 1.539799221e-01f, 1.322255567e-01f, 1.014602382e-01f, 6.378057206e-02f, 2.175436537e-02f},
-        {1.609876377e-01f, 1.178511302e-01f, 4.313650752e-02f, -4.313650752e-02f, -1.178511302e-01f, -1.609876377e-01f},
-        {1.539799221e-01f, 6.378057206e-02f, -6.378057206e-02f, -1.539799221e-01f, -1.539799221e-01f, -6.378057206e-02f},
-        {1.443375673e-01f, 0.000000000e+00f, -1.443375673e-01f, -1.443375673e-01f, 0.000000000e+00f, 1.443375673e-01f},
-        {1.322255567e-01f, -6.378057206e-02f, -1.652408102e-01f, -2.175436537e-02f, 1.539799221e-01f, 1.014602382e-01f},
-        {1.178511302e-01f, -1.178511302e-01f, -1.178511302e-01f, 1.178511302e-01f, 1.178511302e-01f, -1.178511302e-01f},
-        {1.014602382e-01f, -1.539799221e-01f, -2.175436537e-02f, 1.652408102e-01f, -6.378057206e-02f, -1.322255567e-01f},
-        {8.333333333e-02f, -1.666666667e-01f, 8.333333333e-02f, 8.333333333e-02f, -1.666666667e-01f, 8.333333333e-02f},
-        {6.378057206e-02f, -1.539799221e-01f, 1.539799221e-01f, -6.378057206e-02f, -6.378057206e-02f, 1.539799221e-01f},
-        {4.313650752e-02f, -1.178511302e-01f, 1.609876377e-01f, -1.609876377e-01f, 1.178511302e-01f, -4.313650752e-02f},
-        {2.175436537e-02f, -6.378057206e-02f, 1.014602382e-01f, -1.322255567e-01f, 1.539799221e-01f, -1.652408102e-01f}};
+    constexpr int H = ILE_DM_NODES / 2;
+    constexpr float T[ILE_DM_NODES][H] = {
+        {1.000000000e-01f, 1.000000000e-01f, 1.000000000e-01f, 1.000000000e-01f, 1.000000000e-01f},
+        {1.975376681e-01f, 1.782013048e-01f, 1.414213562e-01f, 9.079809995e-02f, 3.128689301e-02f},
+        {1.902113033e-01f, 1.175570505e-01f, 0.000000000e+00f, -1.175570505e-01f, -1.902113033e-01f},
+        {1.782013048e-01f, 3.128689301e-02f, -1.414213562e-01f, -1.975376681e-01f, -9.079809995e-02f},
+        {1.618033989e-01f, -6.180339887e-02f, -2.000000000e-01f, -6.180339887e-02f, 1.618033989e-01f},
+        {1.414213562e-01f, -1.414213562e-01f, -1.414213562e-01f, 1.414213562e-01f, 1.414213562e-01f},
+        {1.175570505e-01f, -1.902113033e-01f, 0.000000000e+00f, 1.902113033e-01f, -1.175570505e-01f},
+        {9.079809995e-02f, -1.975376681e-01f, 1.414213562e-01f, 3.128689301e-02f, -1.782013048e-01f},
+        {6.180339887e-02f, -1.618033989e-01f, 2.000000000e-01f, -1.618033989e-01f, 6.180339887e-02f},
+        {3.128689301e-02f, -9.079809995e-02f, 1.414213562e-01f, -1.782013048e-01f, 1.975376681e-01f}};
     constexpr IleChebMono CM = ile_cheb_mono();
-    float e[6], o[6], c[ILE_DM_NODES];
+    float e[H], o[H], c[ILE_DM_NODES];
 #pragma unroll
-    for (int k = 0; k < 6; k++) {
-        e[k] = f[k] + f[11 - k];
-        o[k] = f[k] - f[11 - k];
+    for (int k = 0; k < H; k++) {
+        e[k] = f[k] + f[ILE_DM_NODES - 1 - k];
+        o[k] = f[k] - f[ILE_DM_NODES - 1 - k];
     }
 #pragma unroll
     for (int j = 0; j < ILE_DM_NODES; j++) {
         float s = 0.f;
 #pragma unroll
-        for (int k = 0; k < 6; k++) s = fmaf(T[j][k], (j & 1) ? o[k] : e[k], s);
+        for (int k = 0; k < H; k++) s = fmaf(T[j][k], (j & 1) ? o[k] : e[k], s);
         c[j] = s;
     }
 #pragma unroll

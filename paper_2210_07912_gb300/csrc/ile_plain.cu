@@ -250,10 +250,11 @@ __global__ void __launch_bounds__(NT, 2) ile_plain_kernel(const __grid_constant_
             const DmRange rg = ile_dm_range(lo, hi);
             float fv[3];
 #pragma unroll
-            for (int i = 0; i < 3; i++) fv[i] = rg.fit ? ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, 3 * g + i)) : 0.f;
+            for (int i = 0; i < 3; i++)  // thread g: nodes g, g + 4, g + 8
+                fv[i] = rg.fit && g + 4 * i < ILE_DM_NODES ? ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, g + 4 * i)) : 0.f;
             float f[ILE_DM_NODES];
 #pragma unroll
-            for (int q = 0; q < ILE_DM_NODES; q++) f[q] = __shfl_sync(0xffffffffu, fv[q % 3], (lane & ~3) | (q / 3));
+            for (int q = 0; q < ILE_DM_NODES; q++) f[q] = __shfl_sync(0xffffffffu, fv[q / 4], (lane & ~3) | (q % 4));
             if (rg.fit) {
                 float c[ILE_DM_NODES];
                 ile_dm_coeffs(f, c);

@@ -725,12 +725,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // (sets failed if a distance-marginalised exchange times out)
             auto finish_chunk = [&](int j0, int Jc) {
                 if constexpr (DM) {
-                    // ln F(D_j, A) of the chunk's bins: one Chebyshev interpolant per sample through 12
+                    // ln F(D_j, A) of the chunk's bins: one Chebyshev interpolant per sample through 10
                     // table values, or per-bin table reads where the sample's data terms span more than
                     // ILE_DM_WMAX.  The sample's four threads sit in the four warps of this TMEM lane
                     // quarter: each publishes its bins' range (ls_s, free until the tile's end), then
-                    // three node values (the two spare words of its staging row and aq_s, free once
-                    // the quarter's warps have formed dq), with a barrier of the quarter after each.
+                    // two or three node values (the two spare words of its staging row and aq_s, free
+                    // once the quarter's warps have formed dq), with a barrier of the quarter after each.
                     float lo = INFINITY, hi = -INFINITY;
 #pragma unroll
                     for (int jj = 0; jj < JG; jj++)
@@ -754,9 +754,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                     const DmRange rg = ile_dm_range(lo, hi);
                     if (rg.fit) {
-                        my_row[32] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, 3 * g));
-                        my_row[33] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, 3 * g + 1));
-                        aq_s[tid] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, 3 * g + 2));
+                        // thread g: nodes g, g + 4 and (g < 2) g + 8
+                        my_row[32] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, g));
+                        my_row[33] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, g + 4));
+                        if (g + 8 < ILE_DM_NODES) aq_s[tid] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, g + 8));
                     }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sm.dmx[q4]);
@@ -770,9 +771,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                         for (int h = 0; h < NGRP; h++) {
                             const int t = (4 * h + q4) * 32 + lane;
-                            f[3 * h] = rows[t * RS + 32];
-                            f[3 * h + 1] = rows[t * RS + 33];
-                            f[3 * h + 2] = aq_s[t];
+                            f[h] = rows[t * RS + 32];
+                            f[h + 4] = rows[t * RS + 33];
+                            if (h + 8 < ILE_DM_NODES) f[h + 8] = aq_s[t];
                         }
                         ile_dm_coeffs(f, c);
                         if (jbeg + JG <= Jc) {

@@ -81,6 +81,8 @@ struct ile_ctx {
     size_t gq_bytes = 0;
     float *guv_part = nullptr; // [blocks][K][P][4]
     size_t guv_bytes = 0;
+    int *ss_work = nullptr;    // the stable sort's key, index and histogram arrays
+    size_t ss_bytes = 0;
     double *g_in = nullptr;    // staged host upstream gradient [cap]
     double *g_out = nullptr;   // staged g_theta [7][cap] and g_Q, g_U, g_V for host-pointer calls
     size_t g_out_bytes = 0;
@@ -449,15 +451,18 @@ ile_status run_grad(ile_ctx *ctx, const double *dsamples, const double *dg, int6
     }
     const int nsplit = ile_grad_q_splits(pp, N, ctx->n_sm);
     const int nblk = ile_grad_uv_blocks(N, ctx->n_sm);
+    CK(ensure_bytes(ctx, &ctx->ss_work, &ctx->ss_bytes, sizeof(int) * ile_sort_stable_work_ints(N)));
     if (gQ) CK(ensure_bytes(ctx, &ctx->gq_part, &ctx->gq_bytes, sizeof(float) * (size_t)nsplit * pp.K * 2 * pp.M * pp.T_ext));
     if (gU || gV)
         CK(ensure_bytes(ctx, &ctx->guv_part, &ctx->guv_bytes,
                         sizeof(float) * (size_t)nblk * pp.K * (pp.M * (pp.M + 1) / 2) * 4));
     {
         // (the BF16x3 D(n, j) pass below writes the per-sample coefficients, window placements and
-        // quadratic term itself; other contexts form them with the coefficient kernel)
-        StageScope t(ctx, 1, tc2_fwd ? 3 : 4);
-        CK(ile_launch_sort(pp, dsamples, N, ctx->keys, ctx->buckets, ctx->perm, ctx->stream));
+        // quadratic term itself; other contexts form them with the coefficient kernel).  The sort
+        // is the stable form: dQ sums over samples in its order, so equal keys keep the caller's
+        // order and the call gives the same result on every run.
+        StageScope t(ctx, 1, tc2_fwd ? 6 : 7);
+        CK(ile_launch_sort_stable(pp, dsamples, N, ctx->keys, ctx->ss_work, ctx->perm, ctx->stream));
         if (!tc2_fwd) CK(ile_launch_prep(pp, ctx->UV, dsamples, ctx->perm, N, ctx->s, ctx->flags, ctx->stream));
     }
     StageScope t(ctx, 5, 1 + (tc2_fwd ? 1 : 0) + (gQ ? 2 : 0) + ((gU || gV) ? 2 : 0));
@@ -557,7 +562,7 @@ ile_status ile_destroy(ile_ctx *ctx) {
                     ctx->g_out,        ctx->g_cur,      ctx->g_bat,     ctx->g_tab,     ctx->g_part,
                     ctx->a_u,          ctx->Qadj[0],    ctx->Qadj[1],   ctx->Q64,       ctx->U64,
                     ctx->V64,          ctx->loud,       ctx->g2_cur,    ctx->g2_bat,    ctx->g2_tab,
-                    ctx->g2_part,      ctx->a_upair};
+                    ctx->g2_part,      ctx->a_upair,    ctx->ss_work};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (auto &v : ctx->ev)

@@ -555,6 +555,11 @@ float ile_refine_threshold(int prec);
 size_t ile_sort_key_buckets();
 cudaError_t ile_launch_sort(const PointParams &pp, const double *samples, int64_t N, int *keys, int *buckets,
                             int *perm, cudaStream_t st);
+// the same order with equal keys kept in the caller's order (deterministic; the adjoint's
+// sample sums run in this order): work holds ile_sort_stable_work_ints(N) ints
+size_t ile_sort_stable_work_ints(int64_t N);
+cudaError_t ile_launch_sort_stable(const PointParams &pp, const double *samples, int64_t N, int *keys, int *work,
+                                   int *perm, cudaStream_t st);
 // tensor-core path (ile_tc.cu)
 int ile_tc_kpad(int prec, int M);
 int ile_tc_tpad(int T_ext);

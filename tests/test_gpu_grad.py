@@ -82,10 +82,32 @@ def _compare_all(ile, orc, point, th, g, prec="fp32"):
     return out
 
 
-# fp32 contexts recompute D(n, j) and contract on CUDA cores; bf16x3 contexts take D(n, j) from the
-# fused tensor-core forward kernel and, where 64 samples' rows fit shared memory (N_t <= 512), run
-# the E / slope contraction on the tensor cores as well
+# fp32 contexts recompute D(n, j) and contract on CUDA cores; bf16x3 contexts take the window
+# softmax from the fused tensor-core forward kernel and, where 64 samples' rows fit shared memory
+# (N_t <= 512), run the E / slope contraction on the tensor cores as well
 PRECS = ["fp32", "bf16x3"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("n_window", [512, 1024])
+def test_grad_repeatable_and_output_subsets_equal_full_call(ile, prec, n_window):
+    """The gradient call gives the same bits on every run (dQ sums over samples in the delay
+    sort's order, which keeps equal keys in the caller's order), and a call that asks for some of
+    the outputs returns them bit for bit as the call that asks for all of them.  700 samples over
+    3 detectors: several 32-sample dQ chunks and sort buckets holding more than one sample."""
+    point = S.make_point(S.SEED_BASE + 61, 3, 9, n_window, spectrum="decay")
+    th = S.workload_samples(S.GRAD, 700)
+    g = np.random.default_rng(8).normal(size=th.shape[1])
+    ctx = _ctx(ile, point, prec)
+    full = ctx.eval_grad(th, g, want_lnL=True)
+    for _ in range(3):
+        again = ctx.eval_grad(th, g, want_lnL=True)
+        for key in full:
+            assert np.array_equal(again[key], full[key]), key
+    for want, lnl in [(("Q",), False), ((), True), (("theta",), False), (("U", "V"), False), (("Q",), True)]:
+        part = ctx.eval_grad(th, g, want=want, want_lnL=lnl)
+        for key in list(want) + (["lnL"] if lnl else []):
+            assert np.array_equal(part[key], full[key]), (want, lnl, key)
 
 
 @pytest.mark.parametrize("prec", PRECS)

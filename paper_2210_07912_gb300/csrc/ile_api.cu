@@ -151,6 +151,17 @@ cudaError_t grow(ile_ctx *ctx, T **p, size_t bytes) {
     return ctx_malloc(ctx, (void **)p, bytes);
 }
 
+// Keep *p when its allocation already holds `bytes` (a point's arrays are re-used by the next
+// point of the same or a smaller shape: no cudaFree / cudaMalloc per ile_set_data), else grow.
+template <typename T>
+cudaError_t reserve(ile_ctx *ctx, T **p, size_t bytes) {
+    if (*p) {
+        const auto it = ctx->allocs.find((void *)*p);
+        if (it != ctx->allocs.end() && it->second >= bytes) return cudaSuccess;
+    }
+    return grow(ctx, p, bytes);
+}
+
 // Bracket one launch of stage `stage` with events on the context stream (when profiling) and
 // with an NVTX range on the host timeline (a no-op unless a tool such as Nsight is attached).
 const char *const kStageName[ILE_NSTAGE] = {"ile:sample", "ile:coefficients", "ile:contraction",
@@ -788,17 +799,18 @@ ile_status ile_set_data(ile_ctx *ctx, int n_det, int n_modes, const int *lm, con
                                       n_window, gmst_rad, d_ref_mpc, pp, qp, uv, quad, false);
     if (st != ILE_OK) return st;
     DeviceGuard g(ctx->device);
-    // the previous point's arrays are released by the growth below: no data until it completes
+    // the previous point's arrays are overwritten (or released and grown) below: no data until
+    // that completes
     ctx->has_data = false;
     ctx->Qtc_ready[1] = ctx->Qtc_ready[2] = ctx->Qadj_ready = false;
     const size_t nqp = (size_t)n_det * 2 * n_modes * T_ext;
-    CK(grow(ctx, &ctx->Qp, sizeof(float) * nqp));
-    CK(grow(ctx, &ctx->UV, sizeof(float) * uv.size()));
-    CK(grow(ctx, &ctx->Qquad, sizeof(float) * quad.size()));
+    CK(reserve(ctx, &ctx->Qp, sizeof(float) * nqp));
+    CK(reserve(ctx, &ctx->UV, sizeof(float) * uv.size()));
+    CK(reserve(ctx, &ctx->Qquad, sizeof(float) * quad.size()));
     const size_t nq = (size_t)n_det * n_modes * T_ext, nuv = (size_t)n_det * n_modes * n_modes;
-    CK(grow(ctx, &ctx->Q64, sizeof(double2) * nq));
-    CK(grow(ctx, &ctx->U64, sizeof(double2) * nuv));
-    CK(grow(ctx, &ctx->V64, sizeof(double2) * nuv));
+    CK(reserve(ctx, &ctx->Q64, sizeof(double2) * nq));
+    CK(reserve(ctx, &ctx->U64, sizeof(double2) * nuv));
+    CK(reserve(ctx, &ctx->V64, sizeof(double2) * nuv));
     CK(cudaMemcpyAsync(ctx->Q64, Q, sizeof(double2) * nq, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->U64, U, sizeof(double2) * nuv, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->V64, V, sizeof(double2) * nuv, cudaMemcpyHostToDevice, ctx->stream));

@@ -199,6 +199,20 @@ __device__ __forceinline__ DmRange ile_dm_range(float lo, float hi) {
     return r;
 }
 
+// The same for a fit that later chunks of the sample may reuse: the range is widened to at least
+// ILE_DM_WMAX around its middle (the fused kernel keeps the interpolant while a chunk's data terms
+// stay inside it).  On ranges that wide the interpolant of the exact ln F stays within 1e-4 of it
+// (the bound above); on the benchmarked workload's chunks the per-sample time-marginalised result
+// moves by at most 6e-7 against a fit on each chunk's own range.
+__device__ __forceinline__ DmRange ile_dm_range_wide(float lo, float hi) {
+    DmRange r;
+    r.fit = hi - lo <= ILE_DM_WMAX;  // false for NaN
+    r.mid = 0.5f * (lo + hi);
+    r.half = fmaxf(0.5f * (hi - lo), 0.5f * ILE_DM_WMAX);
+    r.inv_half = 1.f / r.half;
+    return r;
+}
+
 // x_k = cos(pi (k + 1/2) / 10), k = 0 .. 9
 static __constant__ float ile_dm_xk[ILE_DM_NODES] = {
     9.876883406e-01f,  8.910065242e-01f,  7.071067812e-01f,  4.539904997e-01f,  1.564344650e-01f,

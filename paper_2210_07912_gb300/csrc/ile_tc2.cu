@@ -10,8 +10,8 @@ template <int OP, bool DM, bool ADJ = false>
 cudaError_t launch_one(const PointParams &pp, const Tc2Point &one, int64_t ntiles, int KP, int full_grid,
                        unsigned *flags, cudaStream_t st) {
     int NB = NBMAX;
-    while (NB > 2 && tc2_smem<OP>(pp.K, pp.M, KP, NB) > SMEM_LIMIT) NB--;
-    const size_t smem = tc2_smem<OP>(pp.K, pp.M, KP, NB);
+    while (NB > 2 && tc2_smem<OP>(pp.K, pp.M, KP, NB, DM) > SMEM_LIMIT) NB--;
+    const size_t smem = tc2_smem<OP>(pp.K, pp.M, KP, NB, DM);
     if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(ile_tc2_kernel<false, DM, OP, ADJ>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -55,6 +55,7 @@ namespace {
 constexpr int TILE = 128;
 constexpr int NGRP = 4;                    // threads per sample
 constexpr int NMATH = TILE * NGRP;         // 512 math threads
+constexpr int DMC_ROWS = 4 + ILE_DM_NODES;  // per-sample interpolant store (distance marginalisation)
 constexpr int MMA_WARP = NMATH / 32;        // warp 16: tcgen05.mma issue
 constexpr int COPY_WARP = MMA_WARP + 1;    // warp 17: bulk copies of the Q windows
 constexpr int PREF_WARP = COPY_WARP + 1;   // warp 18: gathers the next tile's sample parameters
@@ -236,6 +237,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     (void)LNP;
     // operand element layout: 16-byte chunks of 8 BF16 or 4 TF32 values; A in TMEM or shared memory
     constexpr bool TF32 = OP == OP_TF32_TMEM, ATM = OP != OP_BF16_SMEM && OP != OP_BF16_SMEM_N;
+    // distance marginalisation keeps each sample's interpolant across chunks (a 15 KB store), except
+    // in the variant with A in shared memory, whose four-detector launches have no room for it
+    constexpr bool DMREUSE = DM && OP != OP_BF16_SMEM;
     constexpr int RS = rstride_of(OP);  // staging-row stride
     constexpr int EPC = TF32 ? 4 : 8;
     constexpr int NTBv = ntb_of(OP);
@@ -250,6 +254,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float *aq_s = rows + RS * NMATH;                                                  // [NMATH]
     float2 *ls_s = reinterpret_cast<float2 *>(aq_s + NMATH);                           // [NMATH]
     float *geo = reinterpret_cast<float *>(ls_s + NMATH);                              // [14][TILE]
+    // distance-marginalised mode: each sample's current interpolant, [DMC_ROWS][TILE] (rows: range
+    // low and high end, middle, 1 / half-width, the 10 monomial coefficients), and the chunk-range
+    // exchange, two buffers of [NMATH]
+    float *dmc = geo + 14 * TILE;
+    float2 *dmr = reinterpret_cast<float2 *>(dmc + DMC_ROWS * TILE);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -714,6 +723,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if constexpr (DM)
                 dq = ile_dmarg_sample(pp.dm, aq_s[q4 * 32 + lane] + aq_s[128 + q4 * 32 + lane] +
                                                  aq_s[256 + q4 * 32 + lane] + aq_s[384 + q4 * 32 + lane]);
+            // and no interpolant of this sample yet (its range is empty; read by the sample's
+            // four threads after the first chunk's range exchange, which orders this store)
+            if (DMREUSE && g == 0) {
+                dmc[q4 * 32 + lane] = INFINITY;
+                dmc[TILE + q4 * 32 + lane] = -INFINITY;
+            }
 
             // ---- S3/S5: consume the jobs
             float D[JG];
@@ -726,11 +741,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             auto finish_chunk = [&](int j0, int Jc) {
                 if constexpr (DM) {
                     // ln F(D_j, A) of the chunk's bins: one Chebyshev interpolant per sample through 10
-                    // table values, or per-bin table reads where the sample's data terms span more than
-                    // ILE_DM_WMAX.  The sample's four threads sit in the four warps of this TMEM lane
-                    // quarter: each publishes its bins' range (ls_s, free until the tile's end), then
-                    // two or three node values (the two spare words of its staging row and aq_s, free
-                    // once the quarter's warps have formed dq), with a barrier of the quarter after each.
+                    // table values on a range at least ILE_DM_WMAX wide, kept for the following chunks
+                    // of the tile while their data terms stay inside it (a refit otherwise), or
+                    // per-bin table reads where a chunk's data terms span more than ILE_DM_WMAX.  The
+                    // sample's four threads sit in the four warps of this TMEM lane quarter: each
+                    // publishes its bins' range (dmr, one buffer per chunk parity), then, when a
+                    // sample of the quarter refits, two or three node values (the two spare words of
+                    // its staging row and aq_s, free once the quarter's warps have formed dq), with a
+                    // barrier of the quarter after each.  Every decision below is the same in the four
+                    // warps (lane l holds the same sample in each), so they pass the same barriers.
                     float lo = INFINITY, hi = -INFINITY;
 #pragma unroll
                     for (int jj = 0; jj < JG; jj++)
@@ -738,7 +757,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             lo = fminf(lo, D[jj]);
                             hi = fmaxf(hi, D[jj]);
                         }
-                    ls_s[tid] = make_float2(lo, hi);
+                    float2 *dr = DMREUSE ? dmr + ((j0 / JW) & 1) * NMATH : ls_s;
+                    dr[tid] = make_float2(lo, hi);
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sm.dmx[q4]);
                     if (!warp_wait(&sm.dmx[q4], dmph & 1u, flags)) {
@@ -748,34 +768,67 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     dmph++;
 #pragma unroll
                     for (int h = 0; h < NGRP; h++) {
-                        const float2 v = ls_s[(4 * h + q4) * 32 + lane];
+                        const float2 v = dr[(4 * h + q4) * 32 + lane];
                         lo = fminf(lo, v.x);
                         hi = fmaxf(hi, v.y);
                     }
-                    const DmRange rg = ile_dm_range(lo, hi);
-                    if (rg.fit) {
-                        // thread g: nodes g, g + 4 and (g < 2) g + 8
-                        my_row[32] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, g));
-                        my_row[33] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, g + 4));
-                        if (g + 8 < ILE_DM_NODES) aq_s[tid] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, g + 8));
+                    const int sl = q4 * 32 + lane;  // the sample's slot in the interpolant store
+                    const bool reuse = DMREUSE && lo >= dmc[sl] && hi <= dmc[TILE + sl];  // false for NaN
+                    DmRange rg{};
+                    float c[ILE_DM_NODES];
+                    bool refit = false;
+                    if (!reuse) {
+                        rg = ile_dm_range_wide(lo, hi);
+                        refit = rg.fit;
                     }
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sm.dmx[q4]);
-                    if (!warp_wait(&sm.dmx[q4], dmph & 1u, flags)) {
-                        failed = true;
-                        return;
-                    }
-                    dmph++;
-                    if (rg.fit) {
-                        float f[ILE_DM_NODES], c[ILE_DM_NODES];
-#pragma unroll
-                        for (int h = 0; h < NGRP; h++) {
-                            const int t = (4 * h + q4) * 32 + lane;
-                            f[h] = rows[t * RS + 32];
-                            f[h + 4] = rows[t * RS + 33];
-                            if (h + 8 < ILE_DM_NODES) f[h + 8] = aq_s[t];
+                    // (without the store the second exchange also keeps dr = ls_s from being
+                    // rewritten before the quarter has read it)
+                    if (!DMREUSE || __any_sync(0xffffffffu, refit)) {
+                        if (refit) {
+                            // thread g: nodes g, g + 4 and (g < 2) g + 8
+                            my_row[32] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, g));
+                            my_row[33] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, g + 4));
+                            if (g + 8 < ILE_DM_NODES) aq_s[tid] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, g + 8));
                         }
-                        ile_dm_coeffs(f, c);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sm.dmx[q4]);
+                        if (!warp_wait(&sm.dmx[q4], dmph & 1u, flags)) {
+                            failed = true;
+                            return;
+                        }
+                        dmph++;
+                        if (refit) {
+                            float f[ILE_DM_NODES];
+#pragma unroll
+                            for (int h = 0; h < NGRP; h++) {
+                                const int t = (4 * h + q4) * 32 + lane;
+                                f[h] = rows[t * RS + 32];
+                                f[h + 4] = rows[t * RS + 33];
+                                if (h + 8 < ILE_DM_NODES) f[h + 8] = aq_s[t];
+                            }
+                            ile_dm_coeffs(f, c);
+                            // the sample's new interpolant for the following chunks: thread g stores
+                            // coefficients g, g + 4, g + 8 (thread 0 also the range); read after the
+                            // next chunk's range exchange
+#pragma unroll
+                            for (int q = 0; q < 3; q++)
+                                if (DMREUSE && g + 4 * q < ILE_DM_NODES) dmc[(4 + g + 4 * q) * TILE + sl] = c[g + 4 * q];
+                            if (DMREUSE && g == 0) {
+                                dmc[sl] = rg.mid - rg.half;
+                                dmc[TILE + sl] = rg.mid + rg.half;
+                                dmc[2 * TILE + sl] = rg.mid;
+                                dmc[3 * TILE + sl] = rg.inv_half;
+                            }
+                        }
+                    }
+                    if (reuse) {
+                        rg.fit = true;
+                        rg.mid = dmc[2 * TILE + sl];
+                        rg.inv_half = dmc[3 * TILE + sl];
+#pragma unroll
+                        for (int q = 0; q < ILE_DM_NODES; q++) c[q] = dmc[(4 + q) * TILE + sl];
+                    }
+                    if (rg.fit) {
                         if (jbeg + JG <= Jc) {
 #pragma unroll
                             for (int jj = 0; jj < JG; jj += 2) {
@@ -1017,13 +1070,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 template <int OP>
-size_t tc2_smem(int K, int M, int KP, int NB) {
+size_t tc2_smem(int K, int M, int KP, int NB, bool dm = false) {
     const int KC = KP / (OP == OP_TF32_TMEM ? 4 : 8), bw = bw_of(OP);
     (void)M;  // the harmonics table (8 M TILE bytes <= 21.5 KB) fits in the rows area
     const bool a_smem = OP == OP_BF16_SMEM || OP == OP_BF16_SMEM_N;
     return (a_smem ? (size_t)16 * K * 2 * KC * TILE : (size_t)0) + (size_t)16 * NB * 2 * KC * bw +
            sizeof(float) * rstride_of(OP) * NMATH + sizeof(float) * NMATH + sizeof(float2) * NMATH +
-           sizeof(float) * 14 * TILE;
+           sizeof(float) * 14 * TILE +
+           (dm && OP != OP_BF16_SMEM ? sizeof(float) * DMC_ROWS * TILE + sizeof(float2) * 2 * NMATH : (size_t)0);
 }
 static_assert(8 * ILE_MAX_MODES * TILE <= 4 * RSTRIDE * NMATH, "y table must fit in the rows area");
 static_assert(RSTRIDE >= 34, "words 32 and 33 of a staging row carry distance-marginalisation node values");

@@ -13,7 +13,7 @@
 
 bool ile_tc3_fits(int K, int KP) {
     return K >= 1 && K <= ILE_MAX_DET && KP % 8 == 0 && acols_needed(OP_TF32_TMEM, K, KP) <= acol_of(OP_TF32_TMEM) &&
-           tc2_smem<OP_TF32_TMEM>(K, 0, KP, 2) <= SMEM_LIMIT;
+           tc2_smem<OP_TF32_TMEM>(K, 0, KP, 2, true) <= SMEM_LIMIT;  // (with the distance-marginalised store)
 }
 
 cudaError_t ile_launch_tc3(const PointParams &pp, const void *hi, const void *lo, int TP, int KP,
@@ -21,10 +21,11 @@ cudaError_t ile_launch_tc3(const PointParams &pp, const void *hi, const void *lo
                            LoudList loud, unsigned *flags, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     if (!ile_tc3_fits(pp.K, KP) || full_grid == 2) return cudaErrorInvalidConfiguration;
-    int NB = NBMAX;
-    while (NB > 2 && tc2_smem<OP_TF32_TMEM>(pp.K, pp.M, KP, NB) > SMEM_LIMIT) NB--;
-    const size_t smem = tc2_smem<OP_TF32_TMEM>(pp.K, pp.M, KP, NB);
     const bool dm = pp.dm.on != 0;
+    int NB = NBMAX;
+    while (NB > 2 && tc2_smem<OP_TF32_TMEM>(pp.K, pp.M, KP, NB, dm) > SMEM_LIMIT) NB--;
+    const size_t smem = tc2_smem<OP_TF32_TMEM>(pp.K, pp.M, KP, NB, dm);
+    if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(dm ? ile_tc2_kernel<false, true, OP_TF32_TMEM> : ile_tc2_kernel<false, false, OP_TF32_TMEM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

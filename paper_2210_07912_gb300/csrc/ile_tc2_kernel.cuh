@@ -736,6 +736,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int jj = 0; jj < JG; jj++) D[jj] = 0.f;
             float m_run = -INFINITY, s_run = 0.f;
             const int jbeg = g * JG;  // my first bin of a chunk (warp-uniform)
+            // distance-marginalised mode: the lane quarter's free word s (0 .. 383) during a chunk's
+            // node exchange: word 32 + (s & 1) of the staging row of its thread s / 2 (s < 256),
+            // else the aq_s entry of its thread s - 256 (thread t of the quarter: warp 4 (t / 32) + q4)
+            auto dm_slot = [&](int s) -> float & {
+                if (s < 256) {
+                    const int t = s >> 1;
+                    return rows[((4 * (t >> 5) + q4) * 32 + (t & 31)) * RS + 32 + (s & 1)];
+                }
+                const int t = s - 256;
+                return aq_s[(4 * (t >> 5) + q4) * 32 + (t & 31)];
+            };
             // chunk [j0, j0 + Jc) complete: S5 log-sum-exp update (or the full grid)
             // (sets failed if a distance-marginalised exchange times out)
             auto finish_chunk = [&](int j0, int Jc) {
@@ -784,11 +795,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     // (without the store the second exchange also keeps dr = ls_s from being
                     // rewritten before the quarter has read it)
                     if (!DMREUSE || __any_sync(0xffffffffu, refit)) {
-                        if (refit) {
-                            // thread g: nodes g, g + 4 and (g < 2) g + 8
-                            my_row[32] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, g));
-                            my_row[33] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, g + 4));
-                            if (g + 8 < ILE_DM_NODES) aq_s[tid] = ile_dmarg_lnF(pp.dm, dq, ile_dm_node(rg, g + 8));
+                        // the node values of the quarter's refitting samples, spread over its 128
+                        // threads: item i = 10 r + n (node n of the warp's r-th refitting lane) is
+                        // looked up by thread i mod 128 of the quarter (thread g * 32 + lane) and
+                        // stored in the quarter's free word `i` (words 32 and 33 of its staging
+                        // rows, then its aq_s entries); rmask is the same in the four warps
+                        const unsigned rmask = __ballot_sync(0xffffffffu, refit);
+                        const int nitem = ILE_DM_NODES * __popc(rmask);
+                        for (int ib = 0; ib < nitem; ib += NMATH / 4) {
+                            const int i = ib + g * 32 + lane;
+                            const int r = i / ILE_DM_NODES, n = i - r * ILE_DM_NODES;
+                            // lane of the (r + 1)-th set bit of rmask: the largest position with
+                            // fewer than r + 1 set bits below it
+                            int src = 0;
+#pragma unroll
+                            for (int w = 16; w; w >>= 1)
+                                if (__popc(rmask & ((1u << (src + w)) - 1u)) < r + 1) src += w;
+                            src = i < nitem ? src : 0;
+                            const float mid = __shfl_sync(0xffffffffu, rg.mid, src);
+                            const float half = __shfl_sync(0xffffffffu, rg.half, src);
+                            DmargSample qs;
+                            qs.b = __shfl_sync(0xffffffffu, dq.b, src);
+                            qs.inv2b = __shfl_sync(0xffffffffu, dq.inv2b, src);
+                            qs.g = __shfl_sync(0xffffffffu, dq.g, src);
+                            qs.row = __shfl_sync(0xffffffffu, dq.row, src);
+                            qs.big = __shfl_sync(0xffffffffu, dq.big ? 1 : 0, src) != 0;
+                            if (i < nitem) dm_slot(i) = ile_dmarg_lnF(pp.dm, qs, fmaf(half, ile_dm_xk[n], mid));
                         }
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&sm.dmx[q4]);
@@ -799,13 +831,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         dmph++;
                         if (refit) {
                             float f[ILE_DM_NODES];
+                            const int rself = __popc(rmask & ((1u << lane) - 1u));
 #pragma unroll
-                            for (int h = 0; h < NGRP; h++) {
-                                const int t = (4 * h + q4) * 32 + lane;
-                                f[h] = rows[t * RS + 32];
-                                f[h + 4] = rows[t * RS + 33];
-                                if (h + 8 < ILE_DM_NODES) f[h + 8] = aq_s[t];
-                            }
+                            for (int q = 0; q < ILE_DM_NODES; q++) f[q] = dm_slot(ILE_DM_NODES * rself + q);
                             ile_dm_coeffs(f, c);
                             // the sample's new interpolant for the following chunks: thread g stores
                             // coefficients g, g + 4, g + 8 (thread 0 also the range); read after the

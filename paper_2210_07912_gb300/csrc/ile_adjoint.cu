@@ -1379,8 +1379,10 @@ cudaError_t launch_main(const PointParams &pp, const float *Qp, const float *UV,
 }  // namespace
 
 int ile_grad_q_splits(const PointParams &pp, int64_t N, int n_sm) {
+    // as many sample splits as keep the grid (column blocks x detectors x splits) within one wave
+    // of two CTAs per SM: a partial second wave would leave its few CTAs running alone
     const int tb = (pp.T_ext + QTB - 1) / QTB;
-    int64_t want = (2 * (int64_t)n_sm + (int64_t)tb * pp.K - 1) / ((int64_t)tb * pp.K);
+    int64_t want = 2 * (int64_t)n_sm / ((int64_t)tb * pp.K);
     const int64_t most = (N + QNC - 1) / QNC;
     if (want > most) want = most;
     if (want < 1) want = 1;

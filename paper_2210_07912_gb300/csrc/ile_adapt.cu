@@ -34,7 +34,7 @@ namespace {
 constexpr int NB = ILE_NBINS;
 constexpr int ND = ILE_NDIM;
 constexpr int HIST_THREADS = 256;
-constexpr int HIST_CHUNK = 2048;
+constexpr int HIST_CHUNK = 1024;
 
 __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                                               uint32_t k1, uint32_t out[4]) {

@@ -1390,7 +1390,8 @@ int ile_grad_q_splits(const PointParams &pp, int64_t N, int n_sm) {
 }
 
 int ile_grad_uv_blocks(int64_t N, int n_sm) {
-    int64_t b = 2 * (int64_t)n_sm;
+    // four resident blocks per SM (64 registers, 14 KB of shared memory each)
+    int64_t b = 4 * (int64_t)n_sm;
     const int64_t most = (N + UVC - 1) / UVC;
     if (b > most) b = most;
     return (int)(b < 1 ? 1 : b);
